@@ -1,0 +1,436 @@
+#!/usr/bin/env python3
+"""Benchmark of the Maxwell–Bloch FDTD step: Mcell-updates/s and HBM GB/s.
+
+Workload: one active realization of the paper-scale sample, a 320^3 Yee grid
+(6.4 um box, dx = 20 nm, Courant 0.99, 8-cell CPML) holding ~8100 TiO2
+spheres (d ~ normal(300 nm, 10 %), 45 % fill) with the gain medium in the
+voids, N_a = 5e24 m^-3 pumped at W_p = 1e13 /s, Langevin noise on, a centre
+point probe and six face probes (128 bins, 475-705 nm).  A "step" is one
+full time step: H pass, fused E / gain / noise / population pass (with the
+face flux), point-probe DFT, face-probe DFT.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun, one rank per GPU) every rank advances its own
+realization (different disorder and noise seeds): weak scaling, no
+collective on the data path; the barrier and the max over ranks of the
+timed region are the only communication.  Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "MB-FDTD Mcell-updates/s & HBM GB/s at 320^3; batched and adjoint vs plain step"
+UNIT = "Mcell-updates/s"
+FALLBACK_HBM_GBS = 6800.0
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "e_pass_traffic.json")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_0809_1547_gb300", "csrc", f)
+                  for f in ("mb_device.cuh", "mb_kernels.cu")]
+
+
+# ------------------------------------------------------------------ helpers
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def algorithmic_bytes(w):
+    """Algorithmic bytes per cell-update of each pass (perfect neighbour reuse).
+
+    H pass: read E, H (24 B), write H (12 B); per CPML slab axis the cell is
+    in, read+write two psi_H (16 B).  E pass: read H, E (24 B) and the
+    material byte, write E (12 B); gain cells read+write P, J and n1..n3
+    (72 B); per slab axis two psi_E (16 B).
+    """
+    import numpy as np
+    L = w.npml
+    n = w.grid
+    slab = sum(min(2 * L, nw) / nw for nw in n)   # sum over axes of the slab fraction
+    g = float(np.mean(w.gain != 0)) if w.N_a > 0 else 0.0
+    h_pass = 36.0 + 16.0 * slab
+    e_pass = 37.0 + 72.0 * g + 16.0 * slab
+    return {"h_pass": h_pass, "e_pass": e_pass, "step": h_pass + e_pass, "gain_fraction": g,
+            "slab_fraction_sum": slab}
+
+
+def traffic_from_profile():
+    """DRAM bytes per E-pass launch from the committed ncu capture, if it was
+    taken on the current kernel sources (else None)."""
+    try:
+        with open(PROFILE_TRAFFIC) as f:
+            d = json.load(f)
+        if d.get("kernel_source_hash") != kernel_source_hash():
+            return None
+        return float(d["bytes_per_launch_full_size"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms."""
+    QUERY = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100", "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is not None:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        rows = []
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    parts = [p.strip() for p in line.split(",")]
+                    if len(parts) >= 10:
+                        rows.append(parts)
+        except Exception:
+            pass
+        finally:
+            if self.path and os.path.exists(self.path):
+                os.unlink(self.path)
+        return rows
+
+    @staticmethod
+    def summarize(rows, t0, t1):
+        from datetime import datetime
+        sel = []
+        for r in rows:
+            try:
+                ts = datetime.strptime(r[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except Exception:
+                continue
+            if t0 - 0.05 <= ts <= t1 + 0.05:
+                sel.append(r)
+        window = "timed region"
+        if not sel:
+            sel, window = rows, "whole run (no sample fell inside the timed region)"
+        if not sel:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"],
+                    "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except Exception:
+                return None
+        sm = [num(r[2]) for r in sel if num(r[2]) is not None]
+        smax = [num(r[3]) for r in sel if num(r[3]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[q] for r in sel for q in range(4) if r[6 + q].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(sel), "window": window,
+                "power_w_max": max((num(r[4]) or 0.0) for r in sel)}
+
+
+# ---------------------------------------------------------- distributed glue
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def init_dist(world, backend):
+    if world > 1:
+        import torch.distributed as dist
+        if not dist.is_initialized():
+            dist.init_process_group(backend=backend)
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_workload(rank: int):
+    """Rank r runs its own realization: disorder seed 7 + r, noise seed + r."""
+    from paper_0809_1547_gb300 import inputs
+    w = inputs.workload_paper_320(seed=7 + rank)
+    w.seed = w.seed + rank
+    return w
+
+
+# ------------------------------------------------------------- CPU baseline
+
+def oracle_sample_rate(thickness: int, steps: int, warm: int = 1):
+    """Oracle Mcell-updates/s on a 320 x 320 x thickness slab of the workload
+    (centre z-planes, same materials, gain and noise; 8-cell CPML on the
+    slab's own faces).  Runs in this process: call it in a child with one
+    BLAS thread."""
+    import numpy as np
+    from oracle.mb_oracle import MBOracle, Params
+    w = rank_workload(0)
+    z0 = w.grid[2] // 2 - thickness // 2
+    eps = w.eps[z0:z0 + thickness]
+    gain = w.gain[z0:z0 + thickness]
+    o = MBOracle((w.grid[0], w.grid[1], thickness), w.dx, w.dt, Params(npml=w.npml))
+    o.set_material(eps, gain, w.N_a, w.pump)
+    o.set_seed(w.seed)
+    o.add_point_probe((w.grid[0] // 2, w.grid[1] // 2, thickness // 2), 128, 475e-9, 705e-9)
+    o.step(warm)
+    t = time.perf_counter()
+    o.step(steps)
+    el = time.perf_counter() - t
+    cells = w.grid[0] * w.grid[1] * thickness
+    return cells * steps / el / 1e6, el, cells
+
+
+def run_oracle_child(thickness: int, steps: int, warm: int = 1):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import json,sys; sys.path.insert(0, %r); import bench; "
+            "r = bench.oracle_sample_rate(%d, %d, %d); print(json.dumps(r))" % (ROOT, thickness, steps, warm))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    rate, el, cells = json.loads(r.stdout.strip().splitlines()[-1])
+    return rate, el, cells
+
+
+# --------------------------------------------------------------- our arm
+
+def bench_ours(args):
+    import numpy as np
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    init_dist(world, "nccl")
+    from paper_0809_1547_gb300 import build
+    if rank == 0:
+        build.build()
+    barrier(world)
+    from paper_0809_1547_gb300.binding import MBSimulation, mb_default_params
+    from paper_0809_1547_gb300.workloads import setup_simulation
+    w = rank_workload(rank)
+    stream = torch.cuda.Stream()
+    sim = setup_simulation(w, autotune=True, stream=stream.cuda_stream)
+    per_step_launches, _ = sim.launch_stats()
+    sim.step(args.warmup)
+    sim.synchronize()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    t_host0 = time.time()
+    ev0.record(stream)
+    pass_ms = sim.step_timed(args.steps)          # direct launches, events around each pass
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_host1 = time.time()
+    barrier(world)
+    clock_rows = sampler.stop()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    elapsed_ms = max_over_ranks(elapsed_ms, world, device=torch.device("cuda", local))
+
+    # the production path (CUDA-graph replay) on the same state, for reference
+    torch.cuda.synchronize()
+    g0 = torch.cuda.Event(enable_timing=True)
+    g1 = torch.cuda.Event(enable_timing=True)
+    n_graph = max(args.steps // 4, 16)
+    g0.record(stream)
+    sim.step(n_graph)
+    g1.record(stream)
+    torch.cuda.synchronize()
+    graph_ms_per_step = g0.elapsed_time(g1) / n_graph
+    U, fl = sim.energy()
+    sim.close()
+
+    cells = w.ncell
+    value = cells * args.steps * world / (elapsed_ms / 1e3) / 1e6
+    ab = algorithmic_bytes(w)
+    peak, peak_kind = measured_peaks()
+    e_avg_ms = pass_ms[1] / args.steps
+    h_avg_ms = pass_ms[0] / args.steps
+    e_bytes = ab["e_pass"] * cells
+    h_bytes = ab["h_pass"] * cells
+    achieved = e_bytes / (e_avg_ms / 1e3) / 1e9
+    traffic = traffic_from_profile()
+
+    # end to end through the public API with host buffers: material upload
+    # (host -> device), K steps each followed by a read of the six face
+    # energies (device -> host), the final spectrum read.
+    eps_h = np.ascontiguousarray(w.eps, dtype=np.float32)
+    gain_h = np.ascontiguousarray(w.gain, dtype=np.uint8)
+    sim2 = MBSimulation(w.grid, w.dx, w.dt, mb_default_params(npml=w.npml), stream=stream.cuda_stream)
+    pid = sim2.add_point_probe(w.extra.get("probe", (160, 160, 160)), 128, 475e-9, 705e-9)
+    sim2.add_face_probes(8, 4, 128, 475e-9, 705e-9)
+    sim2.set_material(eps_h, gain_h, w.N_a, w.pump)
+    sim2.set_seed(w.seed)
+    sim2.step(2)          # graph capture outside the timed region
+    sim2.set_material(eps_h, gain_h, w.N_a, w.pump)
+    sim2.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    sim2.set_material(eps_h, gain_h, w.N_a, w.pump)
+    for _ in range(args.steps):
+        sim2.step(1)
+        sim2.flux()
+    S, _ = sim2.probe_spectrum(pid)
+    t1 = time.perf_counter()
+    e2e_s = max_over_ranks(t1 - t0, world, device=torch.device("cuda", local))
+    sim2.close()
+    e2e_value = cells * args.steps * world / e2e_s / 1e6
+    h2d = (eps_h.nbytes + gain_h.nbytes) / args.steps
+    d2h = 48 + 16 * 3 * 128 / args.steps
+
+    clocks = ClockSampler.summarize(clock_rows, t_host0, t_host1)
+    out = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(elapsed_ms / args.steps, 5),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "mb320_active: 320^3 Yee grid (dx 20 nm, Courant 0.99, 8-cell CPML), "
+                               f"{w.n_spheres} TiO2 spheres d~N(300 nm,10%) at {w.fill:.3f} fill, gain in "
+                               "the voids, N_a 5e24 m^-3, W_p 1e13/s, Langevin noise, centre point probe "
+                               "+ 6 face probes (stride 8, every 4, 128 bins)",
+                   "grid": list(w.grid), "cells": cells, "gain_fraction": round(ab["gain_fraction"], 4),
+                   "l2": "inputs larger than L2 (state 2.0 GB per realization)",
+                   "parallelism": f"replicas x{world} (one realization per GPU)",
+                   "timed_path": "direct launches with CUDA events around each pass",
+                   "graph_replay_ms_per_step": round(graph_ms_per_step, 5)},
+        "roofline": {"bound": "hbm", "kernel": "k_e_pass (fused E/gain/noise/population pass)",
+                     "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "peak_source": f"{peak_kind} hbm_gbs",
+                     "traffic": traffic, "algorithmic_bytes_per_launch": round(e_bytes),
+                     "bytes_per_cell": round(ab["e_pass"], 2), "avg_launch_ms": round(e_avg_ms, 5),
+                     "h_pass": {"avg_launch_ms": round(h_avg_ms, 5),
+                                "achieved_gbs": round(h_bytes / (h_avg_ms / 1e3) / 1e9, 1),
+                                "bytes_per_cell": round(ab["h_pass"], 2)},
+                     "step_achieved_gbs": round(ab["step"] * cells / (elapsed_ms / args.steps / 1e3) / 1e9, 1),
+                     "pass_ms_per_step": [round(v / args.steps, 5) for v in pass_ms]},
+        "e2e": {"value": round(e2e_value, 2), "unit": UNIT, "h2d_bytes_per_step": round(h2d, 1),
+                "d2h_bytes_per_step": round(d2h, 1)},
+        "gpu_launches": int(per_step_launches * args.steps),
+        "clocks": clocks,
+        "energy_J": U,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            rate, el, ncell = run_oracle_child(16, 6)
+            out["cpu_baseline"] = {"value": round(rate, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+                                   "sample": f"6 steps (after 1 warm-up) of a 320x320x16 slab "
+                                             f"({ncell} cells) of the same workload, FP64 numpy, "
+                                             f"one thread, {el:.1f} s"}
+        except Exception as e:   # keep the GPU line even if the CPU leg fails
+            out["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                   "sample": f"failed: {str(e)[-200:]}"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# --------------------------------------------------------- reference arm
+
+def bench_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    # calibrate the oracle's rate on a thin slab, then size the per-step sample
+    rate, _, _ = run_oracle_child(2, 1, 1)
+    budget_s = 100.0
+    cells_per_step = rate * 1e6 * budget_s / max(1, args.steps + args.warmup)
+    thickness = int(max(1, min(64, round(cells_per_step / (320 * 320)))))
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import json,sys; sys.path.insert(0, %r); import bench; "
+            "r = bench.oracle_sample_rate(%d, %d, %d); print(json.dumps(r))"
+            % (ROOT, thickness, args.steps, max(args.warmup, 1)))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        print(json.dumps({"impl": "reference", "unavailable": "oracle run failed: " + r.stderr[-300:]}))
+        return
+    rate, el, ncell = json.loads(r.stdout.strip().splitlines()[-1])
+    sample = (f"each step: a 320x320x{thickness} slab ({ncell} cells) of the 320^3 workload, "
+              f"FP64 numpy oracle, one thread")
+    out = {"impl": "reference", "metric": METRIC, "value": round(rate, 4), "unit": UNIT,
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(el / args.steps * 1e3, 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "mb320_active (sampled slab)", "grid": [320, 320, thickness]},
+           "cpu_baseline": {"value": round(rate, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": round(rate, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=600)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        bench_reference(args)
+    else:
+        bench_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,213 @@
+/*
+ * mb_fdtd.h — C ABI of the GB300 Maxwell–Bloch FDTD step.
+ *
+ * The operation: one time step of the vectorial Maxwell–Bloch (MB) random-
+ * laser model of Conti, Leonetti, Fratalocchi, Angelani, Ruocco,
+ * "Condensation in disordered lasers: theory, 3D+1 simulations and
+ * experiments" (arXiv:0809.1547), section "Simulations": an FDTD (Yee grid)
+ * solution of Maxwell's equations through a packing of TiO2 spheres (n=2.9)
+ * whose voids hold a four-level gain medium (lambda0 = 590 nm, 230 nm gain
+ * bandwidth ~ 1/t_g) pumped at a constant rate, with spontaneous emission
+ * as a stochastic (Langevin) term.  The paper prints no equations; the scheme
+ * implemented is the standard four-level Lorentz-oscillator MB-FDTD model:
+ *
+ *   H^{n+1/2} = H^{n-1/2} - dt/mu0 curl E^n                 (+ CPML)
+ *   J^{n+1/2} = [(1-a) J^{n-1/2} + dt (xi (N1-N2) E^n - w0^2 P^n + F^n)]/(1+a)
+ *   P^{n+1}   = P^n + dt J^{n+1/2}                           (gain cells)
+ *   E^{n+1}   = E^n + dt/(eps0 eps_r) (curl H^{n+1/2} - J^{n+1/2} - J_src)
+ *   N^{n+1}   = M N^n + m (E^n+E^{n+1})/2 . J^{n+1/2} / (hbar w0)
+ *
+ * with a = dw_a dt/2, M, m the Crank–Nicolson propagator of the four-level
+ * rate equations (pump W_p from N0 to N3), and F a Langevin force drawn from
+ * Philox4x32-10 keyed by (seed, cell, step).  PEC walls bound the grid, a
+ * CPML of npml cells lines every face.
+ *
+ * Conventions.  Grid n_x x n_y x n_z, x fastest: cell index
+ * c = i + n_x (j + n_y k).  Cell (i,j,k) owns Ex(i+1/2,j,k), Ey(i,j+1/2,k),
+ * Ez(i,j,k+1/2), Hx(i,j+1/2,k+1/2), Hy(i+1/2,j,k+1/2), Hz(i+1/2,j+1/2,k),
+ * P and J on the E sites and the populations N0..N3.  All host arrays are
+ * borrowed and copied during the call; the context owns every device buffer
+ * it allocates.  Fields crossing the ABI are in SI units (V/m, A/m, C/m^2,
+ * A/m^2, m^-3).  Every call returns MB_OK (0) or a negative MB_ERR_* code and
+ * never aborts the process; mb_last_error() then holds a message.  Calls on
+ * one context are not thread-safe.  Work is queued on the context's CUDA
+ * stream; calls that return host data synchronize that stream.
+ */
+#ifndef MB_FDTD_H
+#define MB_FDTD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    MB_OK = 0,
+    MB_ERR_ARG = -1,        /* bad argument (null pointer, size, index)          */
+    MB_ERR_COURANT = -2,    /* dt > dx / (c sqrt 3)                              */
+    MB_ERR_OOM = -3,        /* device or host allocation failed                  */
+    MB_ERR_MATERIALS = -4,  /* eps_r < 1 or not finite                           */
+    MB_ERR_TIMEOUT = -5,    /* a bounded device wait gave up                     */
+    MB_ERR_NONFINITE = -6,  /* NaN / Inf found in the fields                     */
+    MB_ERR_CUDA = -7,       /* a CUDA runtime call failed                        */
+    MB_ERR_STATE = -8       /* call not valid in this state (e.g. no material)  */
+};
+
+/* Field identifiers for mb_get_field / mb_set_field. */
+enum {
+    MB_EX = 0, MB_EY, MB_EZ, MB_HX, MB_HY, MB_HZ,
+    MB_PX, MB_PY, MB_PZ, MB_JX, MB_JY, MB_JZ,
+    MB_N0, MB_N1, MB_N2, MB_N3,
+    MB_NUM_FIELDS
+};
+
+/* Physical and numerical parameters (SI).  mb_default_params fills the
+ * values of the model: lambda0 = 590 nm and dlambda = 230 nm (paper,
+ * "Simulations"); lifetimes tau32 = tau10 = 100 fs, tau21 = 1 ns and the
+ * noise amplitude are not given by the paper and are user choices. */
+typedef struct mb_params {
+    double lambda0;          /* gain centre wavelength (m)                      */
+    double dlambda;          /* gain bandwidth (m); dw_a = 2 pi c dlambda/lambda0^2 */
+    double tau32, tau21, tau10;  /* level lifetimes (s)                         */
+    double a_se;             /* Langevin amplitude (SI); < 0 selects
+                                w0 (e dipole_len) sqrt(2 dw_a)                  */
+    double dipole_len;       /* dipole length of the default a_se (m)           */
+    double n_floor_rel;      /* N_floor / N_a under the noise square root       */
+    int    npml;             /* CPML cells per face (>= 0)                      */
+    double pml_order;        /* sigma grading exponent                          */
+    double pml_sigma_factor; /* sigma_max = factor (order+1) / (eta0 dx)        */
+    double pml_alpha_rel;    /* alpha_max = 2 pi eps0 alpha_rel c / lambda0     */
+    double n_ref;            /* density (m^-3) fixing the FP32 field scale
+                                E0 = sqrt(hbar w0 n_ref / eps0); no effect on
+                                the SI results beyond FP32 rounding             */
+} mb_params;
+
+typedef struct mb_ctx mb_ctx;
+
+/* Fill *p with the defaults listed above. */
+void mb_default_params(mb_params* p);
+
+/* Create a context for one realization on a grid[0] x grid[1] x grid[2] Yee
+ * grid with spacing dx (m) and step dt (m, s).  p == NULL selects the
+ * defaults.  cuda_stream is a cudaStream_t the context queues its work on
+ * (NULL: the context creates its own).  Fields start at zero, eps_r = 1, no
+ * gain.  Errors: MB_ERR_ARG (size < 1, dx <= 0), MB_ERR_COURANT, MB_ERR_OOM,
+ * MB_ERR_CUDA.  On error *out is NULL. */
+int mb_create(mb_ctx** out, const int grid[3], double dx, double dt,
+              const mb_params* p, void* cuda_stream);
+
+/* Free every device and host buffer of the context (NULL is accepted). */
+int mb_destroy(mb_ctx* ctx);
+
+/* Message of the last failed call on ctx (thread-local text for ctx == NULL). */
+const char* mb_last_error(const mb_ctx* ctx);
+
+/* Material: eps_map (host, n cells, x fastest, values >= 1) and gain_mask
+ * (host, n cells, nonzero = gain medium, i.e. a void).  The paper's
+ * "amplification only in the interstices" is the caller's mask.  N_a is the
+ * total atom density (m^-3, N0 = N_a in gain cells at t = 0) and pump the
+ * rate W_p (1/s) from N0 to N3, constant in time.  Resets P, J and the
+ * populations; fields and probes are kept.  With <= 128 distinct eps values
+ * the map is stored as a uint8 material id per cell, otherwise as a dense
+ * FP32 1/eps_r map.  Errors: MB_ERR_ARG, MB_ERR_MATERIALS. */
+int mb_set_material(mb_ctx* ctx, const float* eps_map, const uint8_t* gain_mask,
+                    double N_a, double pump);
+
+/* 64-bit key of the Langevin noise: Philox4x32-10 with key (seed low word,
+ * seed high word) and counter (cell index, step, 0, 0). */
+int mb_set_seed(mb_ctx* ctx, uint64_t seed);
+
+/* Running-DFT point probe on the three E components of cell ijk:
+ * E~_c(w_k) += E_c(t_{n+1}) exp(i w_k t_{n+1}) dt after every step, FP64 on
+ * the device, n_freq wavelengths uniformly from lam_min to lam_max.
+ * *probe_id receives the probe index.  Errors: MB_ERR_ARG. */
+int mb_add_point_probe(mb_ctx* ctx, const int ijk[3], int n_freq,
+                       double lam_min, double lam_max, int* probe_id);
+
+/* Face probes on the six faces of the interior box [npml, n - npml)^3: on
+ * every stride-th point of each face, the tangential E (on the face plane,
+ * at t_{n+1}) and H (half a cell outside, at t_{n+1/2}) are accumulated into
+ * FP64 running DFTs every `every` steps.  Replaces earlier face probes. */
+int mb_add_face_probes(mb_ctx* ctx, int stride, int every, int n_freq,
+                       double lam_min, double lam_max);
+
+/* Soft current source J_comp(t) = amp sin(w_s (t - t0)) exp(-((t-t0)/tau)^2)
+ * (A/m^2, w_s = 2 pi c / lam) added at cell ijk, component comp (0,1,2), at
+ * t = (n + 1/2) dt.  amp = 0 removes the source. */
+int mb_set_source(mb_ctx* ctx, const int ijk[3], int comp, double lam,
+                  double t0, double tau, double amp);
+
+/* Advance n >= 0 steps (asynchronous; replays a captured CUDA graph). */
+int mb_step(mb_ctx* ctx, int n);
+
+/* Advance n >= 0 steps like mb_step, but with direct launches bracketed by
+ * CUDA events on the context's stream; synchronizes, then adds the summed
+ * device time (ms) of each pass over the n steps to ms_out[0..3]: H pass,
+ * fused E pass, point-probe DFT, face-probe DFT (ms_out may be NULL). */
+int mb_step_timed(mb_ctx* ctx, int n, double* ms_out);
+
+/* Wait for the context's queued work. */
+int mb_synchronize(mb_ctx* ctx);
+
+/* Steps taken so far. */
+int mb_get_step(mb_ctx* ctx, int64_t* n);
+
+/* Point-probe spectrum S(lam_k) = sum_c |E~_c(w_k)|^2 ((V s)^2/m^2) into
+ * out_S (host, n_freq) and the wavelengths into out_lam (host, may be NULL). */
+int mb_probe_spectrum(mb_ctx* ctx, int probe_id, double* out_S, double* out_lam);
+
+/* Outward Poynting spectral density of face f (0..5 = x-, x+, y-, y+, z-, z+),
+ * sum over its probe points of Re(E~_a H~_b^* - E~_b H~_a^*) dA (J s). */
+int mb_face_spectrum(mb_ctx* ctx, int face, double* out_S, double* out_lam);
+
+/* Electromagnetic energy U = 1/2 sum (eps0 eps_r |E|^2 + mu0 |H|^2) dx^3 (J)
+ * of the stored fields, and, if out_flux6 != NULL, the energy (J) that has
+ * left through each face of the interior box since creation: outward flux of
+ * (E^n + E^{n+1})/2 on the face plane against H^{n+1/2} half a cell outside,
+ * times dt, summed over steps (the exact discrete Poynting balance of the
+ * box).  Returns MB_ERR_NONFINITE if any field value is NaN or Inf. */
+int mb_energy(mb_ctx* ctx, double* out_U, double* out_flux6);
+
+/* Only the six time-integrated face energies of mb_energy (J): a 48-byte
+ * device-to-host read, no reduction over the grid.  Synchronizes. */
+int mb_flux(mb_ctx* ctx, double* out_flux6);
+
+/* Copy one field (MB_EX..MB_N3) to / from host memory (n cells, SI units).
+ * N0 is derived (N_a minus the other three) and cannot be set. */
+int mb_get_field(mb_ctx* ctx, int which, float* host_out);
+int mb_set_field(mb_ctx* ctx, int which, const float* host_in);
+
+/* Copy one field, in the device's scaled units, into caller-owned device
+ * memory dev_out (n floats); *scale (may be NULL) receives the factor that
+ * turns it into SI.  N0 is not stored and is rejected. */
+int mb_get_field_device(mb_ctx* ctx, int which, float* dev_out, double* scale);
+
+/* Whole state (fields, CPML memory, probe accumulators, step count) as an
+ * opaque host blob.  Call with host_blob == NULL to query *bytes. */
+int mb_save_state(mb_ctx* ctx, void* host_blob, size_t* bytes);
+int mb_load_state(mb_ctx* ctx, const void* host_blob, size_t bytes);
+
+/* Time the candidate thread-block shapes of the two field passes on this
+ * grid (the state is saved and restored around the trials) and keep the
+ * fastest.  The choice is cached per grid shape for the process. */
+int mb_autotune(mb_ctx* ctx);
+
+/* Kernel launches queued per step by mb_step, and in total so far. */
+int mb_launch_stats(mb_ctx* ctx, int* per_step, int64_t* total);
+
+/* Device bytes the context holds. */
+int mb_device_bytes(mb_ctx* ctx, size_t* bytes);
+
+/* Diagnostic: evaluate the device's Philox4x32-10 (the generator of the
+ * Langevin force, Salmon et al. SC'11) on n counters.  ctr (host, 4n words),
+ * key (host, 2 words), out (host, 4n words).  Runs one kernel on the current
+ * device and synchronizes.  Errors: MB_ERR_ARG, MB_ERR_CUDA. */
+int mb_philox4x32_10(const uint32_t* ctr, const uint32_t key[2], uint32_t* out, int n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MB_FDTD_H */

@@ -1,0 +1,397 @@
+"""Thin ctypes binding of the C ABI in ``include/mb_fdtd.h``.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library ``libmbfdtd.so``.  The functions carry the C names (``mb_create``,
+``mb_step``, ...); :class:`MBSimulation` wraps one context.  If the library
+has not been built, or cannot be loaded, every call raises
+:class:`MBLibraryError`; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libmbfdtd.so")
+
+MB_OK, MB_ERR_ARG, MB_ERR_COURANT, MB_ERR_OOM, MB_ERR_MATERIALS = 0, -1, -2, -3, -4
+MB_ERR_TIMEOUT, MB_ERR_NONFINITE, MB_ERR_CUDA, MB_ERR_STATE = -5, -6, -7, -8
+ERROR_NAMES = {MB_ERR_ARG: "MB_ERR_ARG", MB_ERR_COURANT: "MB_ERR_COURANT", MB_ERR_OOM: "MB_ERR_OOM",
+               MB_ERR_MATERIALS: "MB_ERR_MATERIALS", MB_ERR_TIMEOUT: "MB_ERR_TIMEOUT",
+               MB_ERR_NONFINITE: "MB_ERR_NONFINITE", MB_ERR_CUDA: "MB_ERR_CUDA",
+               MB_ERR_STATE: "MB_ERR_STATE"}
+
+FIELDS = ("Ex", "Ey", "Ez", "Hx", "Hy", "Hz", "Px", "Py", "Pz",
+          "Jx", "Jy", "Jz", "N0", "N1", "N2", "N3")
+FIELD_ID = {name: i for i, name in enumerate(FIELDS)}
+
+
+class MBLibraryError(RuntimeError):
+    """The CUDA library is missing or failed to load."""
+
+
+class MBError(RuntimeError):
+    """A C-ABI call returned an error code."""
+
+    def __init__(self, code, msg):
+        super().__init__(f"{ERROR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class mb_params(C.Structure):
+    _fields_ = [("lambda0", C.c_double), ("dlambda", C.c_double), ("tau32", C.c_double),
+                ("tau21", C.c_double), ("tau10", C.c_double), ("a_se", C.c_double),
+                ("dipole_len", C.c_double), ("n_floor_rel", C.c_double), ("npml", C.c_int),
+                ("pml_order", C.c_double), ("pml_sigma_factor", C.c_double),
+                ("pml_alpha_rel", C.c_double), ("n_ref", C.c_double)]
+
+
+# (name, restype, argtypes) of every exported function
+_P = C.c_void_p
+_SIGS = [
+    ("mb_default_params", None, [C.POINTER(mb_params)]),
+    ("mb_last_error", C.c_char_p, [_P]),
+    ("mb_create", C.c_int, [C.POINTER(_P), C.POINTER(C.c_int), C.c_double, C.c_double,
+                            C.POINTER(mb_params), _P]),
+    ("mb_destroy", C.c_int, [_P]),
+    ("mb_set_material", C.c_int, [_P, _P, _P, C.c_double, C.c_double]),
+    ("mb_set_seed", C.c_int, [_P, C.c_uint64]),
+    ("mb_add_point_probe", C.c_int, [_P, C.POINTER(C.c_int), C.c_int, C.c_double, C.c_double,
+                                     C.POINTER(C.c_int)]),
+    ("mb_add_face_probes", C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double]),
+    ("mb_set_source", C.c_int, [_P, C.POINTER(C.c_int), C.c_int, C.c_double, C.c_double,
+                                C.c_double, C.c_double]),
+    ("mb_step", C.c_int, [_P, C.c_int]),
+    ("mb_step_timed", C.c_int, [_P, C.c_int, _P]),
+    ("mb_flux", C.c_int, [_P, _P]),
+    ("mb_synchronize", C.c_int, [_P]),
+    ("mb_get_step", C.c_int, [_P, C.POINTER(C.c_int64)]),
+    ("mb_probe_spectrum", C.c_int, [_P, C.c_int, _P, _P]),
+    ("mb_face_spectrum", C.c_int, [_P, C.c_int, _P, _P]),
+    ("mb_energy", C.c_int, [_P, C.POINTER(C.c_double), _P]),
+    ("mb_get_field", C.c_int, [_P, C.c_int, _P]),
+    ("mb_set_field", C.c_int, [_P, C.c_int, _P]),
+    ("mb_get_field_device", C.c_int, [_P, C.c_int, _P, C.POINTER(C.c_double)]),
+    ("mb_save_state", C.c_int, [_P, _P, C.POINTER(C.c_size_t)]),
+    ("mb_load_state", C.c_int, [_P, _P, C.c_size_t]),
+    ("mb_autotune", C.c_int, [_P]),
+    ("mb_launch_stats", C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int64)]),
+    ("mb_device_bytes", C.c_int, [_P, C.POINTER(C.c_size_t)]),
+    ("mb_philox4x32_10", C.c_int, [_P, _P, _P, C.c_int]),
+]
+
+_lib = None
+
+
+def load_library(path: str | None = None):
+    """Load ``libmbfdtd.so`` (raises MBLibraryError when it is absent)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise MBLibraryError(f"{p} not found: build it with paper_0809_1547_gb300.build.build()")
+    try:
+        lib = C.CDLL(p)
+    except OSError as e:
+        raise MBLibraryError(f"cannot load {p}: {e}") from e
+    for name, res, args in _SIGS:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def exported_names():
+    return [s[0] for s in _SIGS]
+
+
+def _check(code, ctx=None):
+    if code != MB_OK:
+        lib = load_library()
+        msg = lib.mb_last_error(ctx)
+        raise MBError(code, msg.decode() if msg else "")
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def mb_default_params(**overrides) -> mb_params:
+    p = mb_params()
+    load_library().mb_default_params(C.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def mb_create(grid, dx, dt, params: mb_params | None = None, stream: int | None = None):
+    lib = load_library()
+    h = C.c_void_p()
+    g = (C.c_int * 3)(*[int(v) for v in grid])
+    _check(lib.mb_create(C.byref(h), g, float(dx), float(dt),
+                         C.byref(params) if params is not None else None,
+                         C.c_void_p(stream) if stream else None))
+    return h
+
+
+def mb_destroy(h):
+    if h:
+        _check(load_library().mb_destroy(h))
+
+
+def mb_set_material(h, eps_map, gain_mask, N_a, pump):
+    eps = np.ascontiguousarray(eps_map, dtype=np.float32)
+    gm = np.ascontiguousarray(gain_mask, dtype=np.uint8)
+    _check(load_library().mb_set_material(h, _ptr(eps), _ptr(gm), float(N_a), float(pump)), h)
+
+
+def mb_set_seed(h, seed):
+    _check(load_library().mb_set_seed(h, C.c_uint64(int(seed) & 0xFFFFFFFFFFFFFFFF)), h)
+
+
+def mb_add_point_probe(h, ijk, n_freq, lam_min, lam_max) -> int:
+    pid = C.c_int()
+    _check(load_library().mb_add_point_probe(h, (C.c_int * 3)(*ijk), int(n_freq), float(lam_min),
+                                             float(lam_max), C.byref(pid)), h)
+    return pid.value
+
+
+def mb_add_face_probes(h, stride, every, n_freq, lam_min, lam_max):
+    _check(load_library().mb_add_face_probes(h, int(stride), int(every), int(n_freq),
+                                             float(lam_min), float(lam_max)), h)
+
+
+def mb_set_source(h, ijk, comp, lam, t0, tau, amp):
+    _check(load_library().mb_set_source(h, (C.c_int * 3)(*ijk), int(comp), float(lam), float(t0),
+                                        float(tau), float(amp)), h)
+
+
+def mb_step(h, n):
+    _check(load_library().mb_step(h, int(n)), h)
+
+
+def mb_step_timed(h, n):
+    """Advance n steps with per-pass CUDA-event timing: returns ms summed per
+    pass (H, E, point DFT, face DFT)."""
+    ms = np.zeros(4)
+    _check(load_library().mb_step_timed(h, int(n), _ptr(ms)), h)
+    return ms
+
+
+def mb_flux(h):
+    fl = np.zeros(6)
+    _check(load_library().mb_flux(h, _ptr(fl)), h)
+    return fl
+
+
+def mb_synchronize(h):
+    _check(load_library().mb_synchronize(h), h)
+
+
+def mb_get_step(h) -> int:
+    n = C.c_int64()
+    _check(load_library().mb_get_step(h, C.byref(n)), h)
+    return n.value
+
+
+def mb_probe_spectrum(h, probe_id, n_freq):
+    S = np.zeros(n_freq)
+    lam = np.zeros(n_freq)
+    _check(load_library().mb_probe_spectrum(h, int(probe_id), _ptr(S), _ptr(lam)), h)
+    return S, lam
+
+
+def mb_face_spectrum(h, face, n_freq):
+    S = np.zeros(n_freq)
+    lam = np.zeros(n_freq)
+    _check(load_library().mb_face_spectrum(h, int(face), _ptr(S), _ptr(lam)), h)
+    return S, lam
+
+
+def mb_energy(h):
+    U = C.c_double()
+    fl = np.zeros(6)
+    _check(load_library().mb_energy(h, C.byref(U), _ptr(fl)), h)
+    return U.value, fl
+
+
+def mb_get_field(h, which, shape):
+    out = np.zeros(int(np.prod(shape)), dtype=np.float32)
+    wid = FIELD_ID[which] if isinstance(which, str) else int(which)
+    _check(load_library().mb_get_field(h, wid, _ptr(out)), h)
+    return out.reshape(shape)
+
+
+def mb_set_field(h, which, values):
+    v = np.ascontiguousarray(values, dtype=np.float32)
+    wid = FIELD_ID[which] if isinstance(which, str) else int(which)
+    _check(load_library().mb_set_field(h, wid, _ptr(v)), h)
+
+
+def mb_get_field_device(h, which, dev_ptr: int) -> float:
+    scale = C.c_double()
+    wid = FIELD_ID[which] if isinstance(which, str) else int(which)
+    _check(load_library().mb_get_field_device(h, wid, C.c_void_p(dev_ptr), C.byref(scale)), h)
+    return scale.value
+
+
+def mb_save_state(h) -> bytes:
+    lib = load_library()
+    n = C.c_size_t()
+    _check(lib.mb_save_state(h, None, C.byref(n)), h)
+    buf = (C.c_char * n.value)()
+    _check(lib.mb_save_state(h, buf, C.byref(n)), h)
+    return bytes(buf)
+
+
+def mb_load_state(h, blob: bytes):
+    buf = C.create_string_buffer(blob, len(blob))
+    _check(load_library().mb_load_state(h, buf, len(blob)), h)
+
+
+def mb_autotune(h):
+    _check(load_library().mb_autotune(h), h)
+
+
+def mb_launch_stats(h):
+    per = C.c_int()
+    tot = C.c_int64()
+    _check(load_library().mb_launch_stats(h, C.byref(per), C.byref(tot)), h)
+    return per.value, tot.value
+
+
+def mb_device_bytes(h) -> int:
+    n = C.c_size_t()
+    _check(load_library().mb_device_bytes(h, C.byref(n)), h)
+    return n.value
+
+
+def mb_philox4x32_10(ctr, key):
+    """Device Philox4x32-10 on counters ctr (n, 4) uint32 with key (2,): returns (n, 4)."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    k = np.ascontiguousarray(key, dtype=np.uint32).reshape(2)
+    out = np.zeros_like(c)
+    _check(load_library().mb_philox4x32_10(_ptr(c), _ptr(k), _ptr(out), c.shape[0]))
+    return out
+
+
+class MBSimulation:
+    """One Maxwell–Bloch FDTD realization on the GPU (owns one C context).
+
+    ``grid`` is (n_x, n_y, n_z); host arrays passed to it are indexed
+    [k, j, i] (x fastest), like the fields it returns.
+    """
+
+    def __init__(self, grid, dx, dt, params: mb_params | None = None, stream=None):
+        self.grid = tuple(int(v) for v in grid)
+        self.shape = self.grid[::-1]
+        self.dx, self.dt = float(dx), float(dt)
+        if stream is None:
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    stream = torch.cuda.current_stream().cuda_stream or None
+            except Exception:
+                stream = None
+        self._h = mb_create(self.grid, dx, dt, params, stream)
+        self.probe_nfreq = {}
+        self.face_nfreq = 0
+
+    def close(self):
+        if getattr(self, "_h", None):
+            mb_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_material(self, eps_r, gain_mask, N_a, pump):
+        mb_set_material(self._h, np.asarray(eps_r).reshape(-1), np.asarray(gain_mask).reshape(-1),
+                        N_a, pump)
+
+    def set_seed(self, seed):
+        mb_set_seed(self._h, seed)
+
+    def add_point_probe(self, ijk, n_freq, lam_min, lam_max):
+        pid = mb_add_point_probe(self._h, ijk, n_freq, lam_min, lam_max)
+        self.probe_nfreq[pid] = int(n_freq)
+        return pid
+
+    def add_face_probes(self, stride, every, n_freq, lam_min, lam_max):
+        mb_add_face_probes(self._h, stride, every, n_freq, lam_min, lam_max)
+        self.face_nfreq = int(n_freq)
+
+    def set_source(self, ijk, comp, lam, t0, tau, amp):
+        mb_set_source(self._h, ijk, comp, lam, t0, tau, amp)
+
+    def step(self, n=1):
+        mb_step(self._h, n)
+
+    def step_timed(self, n):
+        return mb_step_timed(self._h, n)
+
+    def flux(self):
+        return mb_flux(self._h)
+
+    def synchronize(self):
+        mb_synchronize(self._h)
+
+    @property
+    def n(self):
+        return mb_get_step(self._h)
+
+    def probe_spectrum(self, probe_id):
+        return mb_probe_spectrum(self._h, probe_id, self.probe_nfreq[probe_id])
+
+    def face_spectrum(self, face):
+        return mb_face_spectrum(self._h, face, self.face_nfreq)
+
+    def energy(self):
+        return mb_energy(self._h)
+
+    def field(self, name):
+        return mb_get_field(self._h, name, self.shape)
+
+    def set_field(self, name, values):
+        mb_set_field(self._h, name, np.asarray(values).reshape(-1))
+
+    def field_device(self, name):
+        """(tensor, scale): the field copied into a torch CUDA tensor in the
+        device's scaled units, and the factor that turns it into SI."""
+        import torch
+        t = torch.empty(self.shape, dtype=torch.float32, device="cuda")
+        scale = mb_get_field_device(self._h, name, t.data_ptr())
+        return t, scale
+
+    def save_state(self) -> bytes:
+        return mb_save_state(self._h)
+
+    def load_state(self, blob: bytes):
+        mb_load_state(self._h, blob)
+
+    def autotune(self):
+        mb_autotune(self._h)
+
+    def launch_stats(self):
+        return mb_launch_stats(self._h)
+
+    def device_bytes(self):
+        return mb_device_bytes(self._h)

@@ -1,0 +1,973 @@
+// C ABI of the Maxwell–Bloch FDTD library: context set-up, coefficient
+// tables (FP64 on the host, FP32 on the device), materials, CUDA-graph
+// stepping, read-outs, state save / restore and the block-shape autotuner.
+#include "mb_host.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <unordered_map>
+
+using mb::kC0;
+using mb::kEps0;
+using mb::kHbar;
+using mb::kPi;
+using mb::kQe;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(mb_ctx* ctx, int code, const std::string& msg) {
+    if (ctx) ctx->err = msg;
+    g_err = msg;
+    return code;
+}
+
+#define MB_CUDA(ctx, call)                                                             \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess) {                                                       \
+            return fail((ctx), (e_ == cudaErrorMemoryAllocation) ? MB_ERR_OOM : MB_ERR_CUDA, \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));           \
+        }                                                                              \
+    } while (0)
+
+// Solve the 4x4 system A x = b (Gaussian elimination with partial pivoting).
+void solve4(const double Ain[4][4], const double bin[4], double x[4]) {
+    double A[4][5];
+    for (int r = 0; r < 4; ++r) {
+        for (int c = 0; c < 4; ++c) A[r][c] = Ain[r][c];
+        A[r][4] = bin[r];
+    }
+    for (int col = 0; col < 4; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < 4; ++r)
+            if (std::fabs(A[r][col]) > std::fabs(A[piv][col])) piv = r;
+        if (piv != col)
+            for (int c = 0; c < 5; ++c) std::swap(A[col][c], A[piv][c]);
+        for (int r = col + 1; r < 4; ++r) {
+            const double f = A[r][col] / A[col][col];
+            for (int c = col; c < 5; ++c) A[r][c] -= f * A[col][c];
+        }
+    }
+    for (int r = 3; r >= 0; --r) {
+        double s = A[r][4];
+        for (int c = r + 1; c < 4; ++c) s -= A[r][c] * x[c];
+        x[r] = s / A[r][r];
+    }
+}
+
+// CPML (Roden & Gedney 2000, kappa = 1) at positions x = i + half, i < n.
+void cpml_table(int n, double half, int L, double dx, double dt, const mb_params& p,
+                float* b, float* c) {
+    const double eta0 = 1.0 / (kEps0 * kC0);
+    const double sigma_max = p.pml_sigma_factor * (p.pml_order + 1.0) / (eta0 * dx);
+    const double alpha_max = 2.0 * kPi * kEps0 * p.pml_alpha_rel * kC0 / p.lambda0;
+    for (int i = 0; i < n; ++i) {
+        b[i] = 0.0f;
+        c[i] = 0.0f;
+        if (L <= 0) continue;
+        const double x = i + half;
+        double depth = std::max((L - x) / L, (x - (n - L)) / (double)L);
+        depth = std::min(1.0, std::max(0.0, depth));
+        if (depth <= 0.0) continue;
+        const double sigma = sigma_max * std::pow(depth, p.pml_order);
+        const double alpha = alpha_max * (1.0 - depth);
+        const double bb = std::exp(-(sigma + alpha) * dt / kEps0);
+        b[i] = (float)bb;
+        c[i] = (float)(sigma / (sigma + alpha) * (bb - 1.0));
+    }
+}
+
+std::pair<int, int> interior(int n, int L) {
+    return (n - 2 * L > 0) ? std::make_pair(L, n - L) : std::make_pair(0, n);
+}
+
+float* field_ptr(mb_ctx* c, int which) {
+    // layout: ex ey ez hx hy hz px py pz jx jy jz n1 n2 n3
+    if (which < MB_EX || which > MB_N3 || which == MB_N0) return nullptr;
+    const int slot = which < MB_N0 ? which : which - 1;
+    return c->d_fields + (int64_t)slot * c->ncell;
+}
+
+double field_scale(const mb_ctx* c, int which) {
+    if (which <= MB_EZ) return c->E0;
+    if (which <= MB_HZ) return c->E0 / c->eta0;
+    if (which <= MB_PZ) return kEps0 * c->E0;
+    if (which <= MB_JZ) return kEps0 * c->E0 / c->dt;
+    return c->N_a;
+}
+
+void build_args(mb_ctx* c) {
+    mb::StepArgs& a = c->args;
+    a.g = {c->nx, c->ny, c->nz, (int64_t)c->nx * c->ny, c->ncell};
+    float* F = c->d_fields;
+    const int64_t N = c->ncell;
+    a.f.ex = F + 0 * N; a.f.ey = F + 1 * N; a.f.ez = F + 2 * N;
+    a.f.hx = F + 3 * N; a.f.hy = F + 4 * N; a.f.hz = F + 5 * N;
+    a.f.px = F + 6 * N; a.f.py = F + 7 * N; a.f.pz = F + 8 * N;
+    a.f.jx = F + 9 * N; a.f.jy = F + 10 * N; a.f.jz = F + 11 * N;
+    a.f.n1 = F + 12 * N; a.f.n2 = F + 13 * N; a.f.n3 = F + 14 * N;
+    a.f.mat = c->d_mat;
+    a.f.inv_eps = c->dense_eps ? c->d_inv_eps : nullptr;
+    a.f.lut_inv_eps = c->d_lut;
+    const int L = c->p.npml;
+    a.pml.L = L;
+    a.pml.psx = c->d_psi[0];
+    a.pml.psy = c->d_psi[1];
+    a.pml.psz = c->d_psi[2];
+    const float* t = c->d_coef;
+    const int n3[3] = {c->nx, c->ny, c->nz};
+    const float** tabs[3][4] = {{&a.pml.bex, &a.pml.cex, &a.pml.bhx, &a.pml.chx},
+                                {&a.pml.bey, &a.pml.cey, &a.pml.bhy, &a.pml.chy},
+                                {&a.pml.bez, &a.pml.cez, &a.pml.bhz, &a.pml.chz}};
+    for (int w = 0; w < 3; ++w)
+        for (int q = 0; q < 4; ++q) {
+            *tabs[w][q] = t;
+            t += n3[w];
+        }
+    a.src = c->src;
+    a.flux.on = 1;
+    for (int w = 0; w < 3; ++w) {
+        auto r = interior(n3[w], L);
+        a.flux.r0[w] = r.first;
+        a.flux.r1[w] = r.second;
+        a.flux.plo[w] = r.first;
+        a.flux.phi[w] = r.second;
+    }
+    a.flux.acc = c->d_flux;
+    a.S = (float)c->S;
+    a.step_ctr = c->d_ctr;
+}
+
+void gain_coefficients(mb_ctx* c) {
+    mb::DevGain& G = c->args.gain;
+    std::memset(&G, 0, sizeof(G));
+    G.key0 = (uint32_t)(c->seed & 0xffffffffu);
+    G.key1 = (uint32_t)(c->seed >> 32);
+    if (!(c->N_a > 0.0)) return;
+    const mb_params& p = c->p;
+    const double dt = c->dt, dx = c->dx, N_a = c->N_a;
+    const double w0 = 2.0 * kPi * kC0 / p.lambda0;
+    const double dw = 2.0 * kPi * kC0 * p.dlambda / (p.lambda0 * p.lambda0);
+    const double xi = 6.0 * kPi * kEps0 * kC0 * kC0 * kC0 / (w0 * w0 * p.tau21);
+    const double a_se = p.a_se >= 0 ? p.a_se : w0 * (kQe * p.dipole_len) * std::sqrt(2.0 * dw);
+    const double a = 0.5 * dw * dt;
+    G.on = 1;
+    G.cJ1 = (float)((1.0 - a) / (1.0 + a));
+    G.cJE = (float)(dt * dt * xi * N_a / (kEps0 * (1.0 + a)));
+    G.cJP = (float)((w0 * dt) * (w0 * dt) / (1.0 + a));
+    G.cJN = (float)(dt * dt * a_se * std::sqrt(N_a / (dx * dx * dx * dt)) /
+                    (kEps0 * c->E0 * (1.0 + a)));
+    G.nfloor = (float)p.n_floor_rel;
+    // Crank–Nicolson propagator of dN/dt = A N + e s, N = (N0, N1, N2, N3).
+    double A[4][4] = {{0}};
+    A[0][0] = -c->W_p;
+    A[0][1] = 1.0 / p.tau10;
+    A[1][1] = -1.0 / p.tau10;
+    A[1][2] = 1.0 / p.tau21;
+    A[2][2] = -1.0 / p.tau21;
+    A[2][3] = 1.0 / p.tau32;
+    A[3][3] = -1.0 / p.tau32;
+    A[3][0] = c->W_p;
+    double Lm[4][4], Rm[4][4], M[4][4], m[4];
+    for (int r = 0; r < 4; ++r)
+        for (int q = 0; q < 4; ++q) {
+            Lm[r][q] = (r == q ? 1.0 : 0.0) - 0.5 * dt * A[r][q];
+            Rm[r][q] = (r == q ? 1.0 : 0.0) + 0.5 * dt * A[r][q];
+        }
+    for (int q = 0; q < 4; ++q) {
+        double col[4] = {Rm[0][q], Rm[1][q], Rm[2][q], Rm[3][q]}, x[4];
+        solve4(Lm, col, x);
+        for (int r = 0; r < 4; ++r) M[r][q] = x[r];
+    }
+    const double e[4] = {0.0, -1.0, 1.0, 0.0};
+    solve4(Lm, e, m);
+    const double smk = kEps0 * c->E0 * c->E0 / (kHbar * w0 * N_a);   // m s / N_a per S_pop
+    for (int r = 0; r < 3; ++r) {
+        G.g[r] = (float)M[r + 1][0];
+        for (int q = 0; q < 3; ++q)
+            G.G[r][q] = (float)(M[r + 1][q + 1] - M[r + 1][0] - (r == q ? 1.0 : 0.0));
+        G.mk[r] = (float)(m[r + 1] * smk);
+    }
+}
+
+int check_ctx(mb_ctx* c) {
+    if (!c) {
+        g_err = "null context";
+        return MB_ERR_ARG;
+    }
+    return MB_OK;
+}
+
+// Device buffers that make up the evolving state (in blob order).
+struct StatePart {
+    void* ptr;
+    size_t bytes;
+};
+
+std::vector<StatePart> state_parts(mb_ctx* c) {
+    std::vector<StatePart> v;
+    v.push_back({c->d_fields, sizeof(float) * 15 * (size_t)c->ncell});
+    for (int w = 0; w < 3; ++w)
+        if (c->psi_elems[w]) v.push_back({c->d_psi[w], sizeof(float) * c->psi_elems[w]});
+    v.push_back({c->d_ctr, sizeof(long long) * 2});
+    v.push_back({c->d_flux, sizeof(double) * 6});
+    if (!c->probes.empty())
+        v.push_back({c->d_probe_acc, sizeof(double2) * 3 * c->probes.size() * c->probe_nfreq});
+    if (c->face.on && c->face_points)
+        v.push_back({c->d_face_acc, sizeof(double2) * 4 * (size_t)c->face_points * c->face.nfreq});
+    return v;
+}
+
+int capture_steps(mb_ctx* c, int steps, cudaGraphExec_t* out) {
+    cudaGraph_t graph = nullptr;
+    MB_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    mb::DevPointProbes pp{(int)c->probes.size(), c->probe_nfreq, c->d_probe_cell,
+                          c->d_probe_omega, c->d_probe_acc};
+    for (int s = 0; s < steps; ++s) {
+        mb::launch_h_pass(c->args, c->blk_h, c->stream);
+        mb::launch_e_pass(c->args, c->blk_e, c->stream);
+        mb::launch_point_dft(pp, c->args.f, c->d_ctr, c->dt, c->stream);
+        mb::launch_face_dft(c->face, c->args.f, c->args.g, c->d_ctr, c->dt, c->stream);
+    }
+    cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+    if (e != cudaSuccess) return fail(c, MB_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(c, MB_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    return MB_OK;
+}
+
+int launches_per_step(const mb_ctx* c) {
+    return 2 + (c->probes.empty() ? 0 : 1) + (c->face.on ? 1 : 0);
+}
+
+void drop_graphs(mb_ctx* c) {
+    if (c->graph_chunk) cudaGraphExecDestroy(c->graph_chunk);
+    if (c->graph_one) cudaGraphExecDestroy(c->graph_one);
+    c->graph_chunk = c->graph_one = nullptr;
+    c->graph_dirty = true;
+}
+
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int>, std::pair<dim3, dim3>> g_tune_cache;
+
+}  // namespace
+
+extern "C" {
+
+void mb_default_params(mb_params* p) {
+    if (!p) return;
+    p->lambda0 = 590e-9;
+    p->dlambda = 230e-9;
+    p->tau32 = 100e-15;
+    p->tau21 = 1e-9;
+    p->tau10 = 100e-15;
+    p->a_se = -1.0;
+    p->dipole_len = 0.1e-9;
+    p->n_floor_rel = 1e-9;
+    p->npml = 8;
+    p->pml_order = 3.0;
+    p->pml_sigma_factor = 0.8;
+    p->pml_alpha_rel = 0.1;
+    p->n_ref = 1e24;
+}
+
+const char* mb_last_error(const mb_ctx* ctx) {
+    return ctx ? ctx->err.c_str() : g_err.c_str();
+}
+
+int mb_create(mb_ctx** out, const int grid[3], double dx, double dt, const mb_params* p,
+              void* cuda_stream) {
+    if (!out || !grid) return fail(nullptr, MB_ERR_ARG, "null argument");
+    *out = nullptr;
+    if (grid[0] < 1 || grid[1] < 1 || grid[2] < 1) return fail(nullptr, MB_ERR_ARG, "grid sizes must be >= 1");
+    const int64_t ncell = (int64_t)grid[0] * grid[1] * grid[2];
+    if (ncell >= (int64_t(1) << 32)) return fail(nullptr, MB_ERR_ARG, "more than 2^32 cells");
+    if (!(dx > 0) || !(dt > 0)) return fail(nullptr, MB_ERR_ARG, "dx and dt must be > 0");
+    if (dt > dx / (kC0 * std::sqrt(3.0))) return fail(nullptr, MB_ERR_COURANT, "dt above the 3D Courant limit dx/(c sqrt 3)");
+    mb_params prm;
+    mb_default_params(&prm);
+    if (p) prm = *p;
+    if (prm.npml < 0 || !(prm.lambda0 > 0) || !(prm.dlambda > 0) || !(prm.tau21 > 0) ||
+        !(prm.tau32 > 0) || !(prm.tau10 > 0) || !(prm.n_ref > 0) || prm.n_floor_rel < 0)
+        return fail(nullptr, MB_ERR_ARG, "invalid parameter");
+
+    mb_ctx* c = new mb_ctx();
+    c->nx = grid[0];
+    c->ny = grid[1];
+    c->nz = grid[2];
+    c->ncell = ncell;
+    c->dx = dx;
+    c->dt = dt;
+    c->p = prm;
+    c->eta0 = 1.0 / (kEps0 * kC0);
+    c->S = kC0 * dt / dx;
+    const double w0 = 2.0 * kPi * kC0 / prm.lambda0;
+    c->E0 = std::sqrt(kHbar * w0 * prm.n_ref / kEps0);
+    auto bail = [&](int code) {
+        mb_destroy(c);
+        return code;
+    };
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e != cudaSuccess) return bail(fail(nullptr, MB_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e)));
+    if (cuda_stream) {
+        c->stream = (cudaStream_t)cuda_stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return bail(fail(nullptr, MB_ERR_CUDA, cudaGetErrorString(e)));
+        c->own_stream = true;
+    }
+    auto alloc = [&](void** ptr, size_t bytes) -> int {
+        if (bytes == 0) { *ptr = nullptr; return MB_OK; }
+        cudaError_t ae = cudaMalloc(ptr, bytes);
+        if (ae != cudaSuccess) {
+            cudaGetLastError();
+            return fail(nullptr, MB_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+        }
+        c->dev_bytes += bytes;
+        return MB_OK;
+    };
+    int rc;
+    if ((rc = alloc((void**)&c->d_fields, sizeof(float) * 15 * (size_t)ncell))) return bail(rc);
+    if ((rc = alloc((void**)&c->d_mat, (size_t)ncell))) return bail(rc);
+    if ((rc = alloc((void**)&c->d_lut, sizeof(float) * 256))) return bail(rc);
+    const int L = prm.npml;
+    c->psi_elems[0] = L ? (size_t)4 * c->nz * c->ny * 2 * L : 0;
+    c->psi_elems[1] = L ? (size_t)4 * c->nz * 2 * L * c->nx : 0;
+    c->psi_elems[2] = L ? (size_t)4 * 2 * L * c->ny * c->nx : 0;
+    for (int w = 0; w < 3; ++w)
+        if ((rc = alloc((void**)&c->d_psi[w], sizeof(float) * c->psi_elems[w]))) return bail(rc);
+    const size_t ncoef = 4 * (size_t)(c->nx + c->ny + c->nz);
+    if ((rc = alloc((void**)&c->d_coef, sizeof(float) * ncoef))) return bail(rc);
+    if ((rc = alloc((void**)&c->d_ctr, sizeof(long long) * 2))) return bail(rc);
+    if ((rc = alloc((void**)&c->d_flux, sizeof(double) * 6))) return bail(rc);
+    c->n_partial = 1024;
+    if ((rc = alloc((void**)&c->d_partial, sizeof(double) * c->n_partial))) return bail(rc);
+    if ((rc = alloc((void**)&c->d_energy, sizeof(double)))) return bail(rc);
+    if ((rc = alloc((void**)&c->d_nonfinite, sizeof(int)))) return bail(rc);
+
+    // CPML tables, zeroed state, eps_r = 1 (material 0), no gain.
+    std::vector<float> coef(ncoef);
+    float* t = coef.data();
+    const int n3[3] = {c->nx, c->ny, c->nz};
+    for (int w = 0; w < 3; ++w) {
+        cpml_table(n3[w], 0.0, L, dx, dt, prm, t, t + n3[w]);
+        cpml_table(n3[w], 0.5, L, dx, dt, prm, t + 2 * n3[w], t + 3 * n3[w]);
+        t += 4 * n3[w];
+    }
+    std::vector<float> lut(256, 1.0f);
+    c->h_lut_eps.assign(128, 1.0f);
+#define MB_CREATE_CUDA(call)                                                               \
+    do {                                                                                   \
+        cudaError_t ce_ = (call);                                                          \
+        if (ce_ != cudaSuccess) return bail(fail(nullptr, MB_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(ce_))); \
+    } while (0)
+    MB_CREATE_CUDA(cudaMemcpy(c->d_coef, coef.data(), sizeof(float) * ncoef, cudaMemcpyHostToDevice));
+    MB_CREATE_CUDA(cudaMemcpy(c->d_lut, lut.data(), sizeof(float) * 256, cudaMemcpyHostToDevice));
+    MB_CREATE_CUDA(cudaMemset(c->d_fields, 0, sizeof(float) * 15 * (size_t)ncell));
+    MB_CREATE_CUDA(cudaMemset(c->d_mat, 0, (size_t)ncell));
+    for (int w = 0; w < 3; ++w)
+        if (c->psi_elems[w]) MB_CREATE_CUDA(cudaMemset(c->d_psi[w], 0, sizeof(float) * c->psi_elems[w]));
+    MB_CREATE_CUDA(cudaMemset(c->d_ctr, 0, sizeof(long long) * 2));
+    MB_CREATE_CUDA(cudaMemset(c->d_flux, 0, sizeof(double) * 6));
+#undef MB_CREATE_CUDA
+    c->h_gain.assign((size_t)ncell, 0);
+    c->face.on = 0;
+    build_args(c);
+    gain_coefficients(c);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find({c->nx, c->ny, c->nz, L});
+        if (it != g_tune_cache.end()) {
+            c->blk_h = it->second.first;
+            c->blk_e = it->second.second;
+        }
+    }
+    *out = c;
+    return MB_OK;
+}
+
+int mb_destroy(mb_ctx* c) {
+    if (!c) return MB_OK;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    drop_graphs(c);
+    void* bufs[] = {c->d_fields, c->d_mat, c->d_inv_eps, c->d_lut, c->d_psi[0], c->d_psi[1],
+                    c->d_psi[2], c->d_coef, c->d_ctr, c->d_flux, c->d_partial, c->d_energy,
+                    c->d_nonfinite, c->d_probe_cell, c->d_probe_omega, c->d_probe_acc,
+                    c->d_face_omega, c->d_face_acc};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return MB_OK;
+}
+
+int mb_set_material(mb_ctx* c, const float* eps_map, const uint8_t* gain_mask, double N_a,
+                    double pump) {
+    if (int rc = check_ctx(c)) return rc;
+    if (!eps_map || !gain_mask) return fail(c, MB_ERR_ARG, "null eps_map or gain_mask");
+    if (!(N_a >= 0) || !(pump >= 0) || !std::isfinite(N_a) || !std::isfinite(pump))
+        return fail(c, MB_ERR_ARG, "N_a and pump must be finite and >= 0");
+    const int64_t N = c->ncell;
+    std::unordered_map<uint32_t, int> ids;
+    std::vector<float> lut_eps;
+    bool dense = false;
+    for (int64_t q = 0; q < N; ++q) {
+        const float v = eps_map[q];
+        if (!(v >= 1.0f) || !std::isfinite(v)) return fail(c, MB_ERR_MATERIALS, "eps_r must be finite and >= 1");
+        if (dense) continue;
+        uint32_t bits;
+        std::memcpy(&bits, &v, 4);
+        if (ids.find(bits) == ids.end()) {
+            if (ids.size() == 128) {
+                dense = true;
+                continue;
+            }
+            const int id = (int)ids.size();
+            ids[bits] = id;
+            lut_eps.push_back(v);
+        }
+    }
+    cudaStreamSynchronize(c->stream);
+    const bool gain_on = N_a > 0.0;
+    std::vector<uint8_t> mat((size_t)N);
+    for (int64_t q = 0; q < N; ++q) {
+        const bool g = gain_on && gain_mask[q] != 0;
+        c->h_gain[q] = g ? 1 : 0;
+        uint8_t id = 0;
+        if (!dense) {
+            uint32_t bits;
+            std::memcpy(&bits, &eps_map[q], 4);
+            id = (uint8_t)ids[bits];
+        }
+        mat[q] = id | (g ? 0x80 : 0x00);
+    }
+    std::vector<float> lut(256, 1.0f);
+    c->h_lut_eps.assign(128, 1.0f);
+    for (size_t q = 0; q < lut_eps.size(); ++q) {
+        lut[q] = (float)(1.0 / (double)lut_eps[q]);
+        lut[128 + q] = lut_eps[q];
+        c->h_lut_eps[q] = lut_eps[q];
+    }
+    MB_CUDA(c, cudaMemcpy(c->d_mat, mat.data(), (size_t)N, cudaMemcpyHostToDevice));
+    MB_CUDA(c, cudaMemcpy(c->d_lut, lut.data(), sizeof(float) * 256, cudaMemcpyHostToDevice));
+    if (dense) {
+        if (!c->d_inv_eps) {
+            cudaError_t e = cudaMalloc((void**)&c->d_inv_eps, sizeof(float) * (size_t)N);
+            if (e != cudaSuccess) { cudaGetLastError(); return fail(c, MB_ERR_OOM, "dense eps map allocation failed"); }
+            c->dev_bytes += sizeof(float) * (size_t)N;
+        }
+        std::vector<float> inv((size_t)N);
+        for (int64_t q = 0; q < N; ++q) inv[q] = (float)(1.0 / (double)eps_map[q]);
+        MB_CUDA(c, cudaMemcpy(c->d_inv_eps, inv.data(), sizeof(float) * (size_t)N, cudaMemcpyHostToDevice));
+    }
+    c->dense_eps = dense;
+    c->N_a = N_a;
+    c->W_p = pump;
+    // reset P, J and the populations (N0 = N_a, n1 = n2 = n3 = 0)
+    MB_CUDA(c, cudaMemset(c->d_fields + 6 * N, 0, sizeof(float) * 9 * (size_t)N));
+    c->have_material = true;
+    build_args(c);
+    gain_coefficients(c);
+    drop_graphs(c);
+    return MB_OK;
+}
+
+int mb_set_seed(mb_ctx* c, uint64_t seed) {
+    if (int rc = check_ctx(c)) return rc;
+    c->seed = seed;
+    c->args.gain.key0 = (uint32_t)(seed & 0xffffffffu);
+    c->args.gain.key1 = (uint32_t)(seed >> 32);
+    drop_graphs(c);
+    return MB_OK;
+}
+
+int mb_add_point_probe(mb_ctx* c, const int ijk[3], int n_freq, double lam_min, double lam_max,
+                       int* probe_id) {
+    if (int rc = check_ctx(c)) return rc;
+    if (!ijk || n_freq < 1 || !(lam_min > 0) || !(lam_max > 0))
+        return fail(c, MB_ERR_ARG, "bad point-probe arguments");
+    if (ijk[0] < 0 || ijk[0] >= c->nx || ijk[1] < 0 || ijk[1] >= c->ny || ijk[2] < 0 || ijk[2] >= c->nz)
+        return fail(c, MB_ERR_ARG, "probe cell outside the grid");
+    if (!c->probes.empty() && n_freq != c->probe_nfreq)
+        return fail(c, MB_ERR_ARG, "all point probes of a context share one bin count");
+    cudaStreamSynchronize(c->stream);
+    mb::PointProbeHost pr;
+    pr.cell = ijk[0] + (int64_t)c->nx * (ijk[1] + (int64_t)c->ny * ijk[2]);
+    pr.nfreq = n_freq;
+    for (int k = 0; k < n_freq; ++k) {
+        const double lam = n_freq == 1 ? lam_min : lam_min + (lam_max - lam_min) * k / (n_freq - 1);
+        pr.lam.push_back(lam);
+        pr.omega.push_back(2.0 * kPi * kC0 / lam);
+    }
+    const size_t P = c->probes.size() + 1;
+    int64_t* d_cell = nullptr;
+    double* d_om = nullptr;
+    double2* d_acc = nullptr;
+    MB_CUDA(c, cudaMalloc((void**)&d_cell, sizeof(int64_t) * P));
+    MB_CUDA(c, cudaMalloc((void**)&d_om, sizeof(double) * P * n_freq));
+    MB_CUDA(c, cudaMalloc((void**)&d_acc, sizeof(double2) * 3 * P * n_freq));
+    MB_CUDA(c, cudaMemset(d_acc, 0, sizeof(double2) * 3 * P * n_freq));
+    if (P > 1) {
+        MB_CUDA(c, cudaMemcpy(d_acc, c->d_probe_acc, sizeof(double2) * 3 * (P - 1) * n_freq, cudaMemcpyDeviceToDevice));
+    }
+    c->probes.push_back(pr);
+    std::vector<int64_t> cells;
+    std::vector<double> om;
+    for (auto& q : c->probes) {
+        cells.push_back(q.cell);
+        om.insert(om.end(), q.omega.begin(), q.omega.end());
+    }
+    MB_CUDA(c, cudaMemcpy(d_cell, cells.data(), sizeof(int64_t) * P, cudaMemcpyHostToDevice));
+    MB_CUDA(c, cudaMemcpy(d_om, om.data(), sizeof(double) * P * n_freq, cudaMemcpyHostToDevice));
+    if (c->d_probe_cell) cudaFree(c->d_probe_cell);
+    if (c->d_probe_omega) cudaFree(c->d_probe_omega);
+    if (c->d_probe_acc) cudaFree(c->d_probe_acc);
+    c->d_probe_cell = d_cell;
+    c->d_probe_omega = d_om;
+    c->d_probe_acc = d_acc;
+    c->probe_nfreq = n_freq;
+    if (probe_id) *probe_id = (int)(P - 1);
+    drop_graphs(c);
+    return MB_OK;
+}
+
+int mb_add_face_probes(mb_ctx* c, int stride, int every, int n_freq, double lam_min, double lam_max) {
+    if (int rc = check_ctx(c)) return rc;
+    if (stride < 1 || every < 1 || n_freq < 1 || !(lam_min > 0) || !(lam_max > 0))
+        return fail(c, MB_ERR_ARG, "bad face-probe arguments");
+    cudaStreamSynchronize(c->stream);
+    if (c->d_face_acc) { cudaFree(c->d_face_acc); c->d_face_acc = nullptr; }
+    if (c->d_face_omega) { cudaFree(c->d_face_omega); c->d_face_omega = nullptr; }
+    mb::DevFaceProbes& F = c->face;
+    std::memset(&F, 0, sizeof(F));
+    const int n3[3] = {c->nx, c->ny, c->nz};
+    const int L = c->p.npml;
+    int64_t off = 0;
+    for (int face = 0; face < 6; ++face) {
+        const int ax = face / 2;
+        auto r = interior(n3[ax], L);
+        F.plane[face] = (face % 2) ? r.second : r.first;
+        // transverse axes (a, b): x-face (y, z), y-face (x, z) by point order, z-face (x, y)
+        const int ta = ax == 0 ? 1 : 0;
+        const int tb = ax == 2 ? 1 : 2;
+        auto ra = interior(n3[ta], L), rb = interior(n3[tb], L);
+        const int na = (ra.second - ra.first + stride - 1) / stride;
+        const int nb = (rb.second - rb.first + stride - 1) / stride;
+        F.r0a[face] = ra.first;
+        F.r0b[face] = rb.first;
+        F.na[face] = na;
+        F.npts[face] = na * nb;
+        F.offset[face] = (int)off;
+        off += (int64_t)na * nb;
+    }
+    F.on = 1;
+    F.stride = stride;
+    F.every = every;
+    F.nfreq = n_freq;
+    F.pts_per_block = 16;
+    c->face_points = off;
+    c->face_lam.clear();
+    std::vector<double> om;
+    for (int k = 0; k < n_freq; ++k) {
+        const double lam = n_freq == 1 ? lam_min : lam_min + (lam_max - lam_min) * k / (n_freq - 1);
+        c->face_lam.push_back(lam);
+        om.push_back(2.0 * kPi * kC0 / lam);
+    }
+    MB_CUDA(c, cudaMalloc((void**)&c->d_face_omega, sizeof(double) * n_freq));
+    MB_CUDA(c, cudaMemcpy(c->d_face_omega, om.data(), sizeof(double) * n_freq, cudaMemcpyHostToDevice));
+    const size_t accn = 4 * (size_t)off * n_freq;
+    MB_CUDA(c, cudaMalloc((void**)&c->d_face_acc, sizeof(double2) * (accn ? accn : 1)));
+    MB_CUDA(c, cudaMemset(c->d_face_acc, 0, sizeof(double2) * (accn ? accn : 1)));
+    F.omega = c->d_face_omega;
+    F.acc = c->d_face_acc;
+    drop_graphs(c);
+    return MB_OK;
+}
+
+int mb_set_source(mb_ctx* c, const int ijk[3], int comp, double lam, double t0, double tau, double amp) {
+    if (int rc = check_ctx(c)) return rc;
+    if (amp == 0.0) {
+        c->src.on = 0;
+        c->args.src = c->src;
+        drop_graphs(c);
+        return MB_OK;
+    }
+    if (!ijk || comp < 0 || comp > 2 || !(lam > 0) || !(tau > 0) || !std::isfinite(amp))
+        return fail(c, MB_ERR_ARG, "bad source arguments");
+    if (ijk[0] < 0 || ijk[0] >= c->nx || ijk[1] < 0 || ijk[1] >= c->ny || ijk[2] < 0 || ijk[2] >= c->nz)
+        return fail(c, MB_ERR_ARG, "source cell outside the grid");
+    c->src.on = 1;
+    c->src.comp = comp;
+    c->src.cell = ijk[0] + (int64_t)c->nx * (ijk[1] + (int64_t)c->ny * ijk[2]);
+    c->src.amp_s = amp * c->dt / (kEps0 * c->E0);
+    c->src.ws = 2.0 * kPi * kC0 / lam;
+    c->src.t0 = t0;
+    c->src.tau = tau;
+    c->src.dt = c->dt;
+    c->args.src = c->src;
+    drop_graphs(c);
+    return MB_OK;
+}
+
+int mb_step(mb_ctx* c, int n) {
+    if (int rc = check_ctx(c)) return rc;
+    if (n < 0) return fail(c, MB_ERR_ARG, "negative step count");
+    if (n == 0) return MB_OK;
+    if (c->graph_dirty) {
+        drop_graphs(c);
+        int rc = capture_steps(c, c->graph_chunk_steps, &c->graph_chunk);
+        if (rc) return rc;
+        rc = capture_steps(c, 1, &c->graph_one);
+        if (rc) return rc;
+        c->graph_dirty = false;
+    }
+    const int chunks = n / c->graph_chunk_steps, rem = n % c->graph_chunk_steps;
+    for (int q = 0; q < chunks; ++q) MB_CUDA(c, cudaGraphLaunch(c->graph_chunk, c->stream));
+    for (int q = 0; q < rem; ++q) MB_CUDA(c, cudaGraphLaunch(c->graph_one, c->stream));
+    MB_CUDA(c, cudaGetLastError());
+    c->n += n;
+    c->launches += (int64_t)n * launches_per_step(c);
+    return MB_OK;
+}
+
+int mb_step_timed(mb_ctx* c, int n, double* ms_out) {
+    if (int rc = check_ctx(c)) return rc;
+    if (n < 0) return fail(c, MB_ERR_ARG, "negative step count");
+    if (n == 0) return MB_OK;
+    // 5 events per step: before H, after H, after E, after point DFT, after face DFT
+    std::vector<cudaEvent_t> ev((size_t)5 * n);
+    for (auto& e : ev) {
+        cudaError_t ce = cudaEventCreate(&e);
+        if (ce != cudaSuccess) {
+            for (auto& x : ev)
+                if (x) cudaEventDestroy(x);
+            return fail(c, MB_ERR_CUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(ce));
+        }
+    }
+    mb::DevPointProbes pp{(int)c->probes.size(), c->probe_nfreq, c->d_probe_cell,
+                          c->d_probe_omega, c->d_probe_acc};
+    for (int s = 0; s < n; ++s) {
+        cudaEvent_t* e = &ev[(size_t)5 * s];
+        cudaEventRecord(e[0], c->stream);
+        mb::launch_h_pass(c->args, c->blk_h, c->stream);
+        cudaEventRecord(e[1], c->stream);
+        mb::launch_e_pass(c->args, c->blk_e, c->stream);
+        cudaEventRecord(e[2], c->stream);
+        mb::launch_point_dft(pp, c->args.f, c->d_ctr, c->dt, c->stream);
+        cudaEventRecord(e[3], c->stream);
+        mb::launch_face_dft(c->face, c->args.f, c->args.g, c->d_ctr, c->dt, c->stream);
+        cudaEventRecord(e[4], c->stream);
+    }
+    cudaError_t le = cudaGetLastError();
+    cudaError_t se = cudaStreamSynchronize(c->stream);
+    double acc[4] = {0, 0, 0, 0};
+    for (int s = 0; s < n && le == cudaSuccess && se == cudaSuccess; ++s) {
+        cudaEvent_t* e = &ev[(size_t)5 * s];
+        for (int q = 0; q < 4; ++q) {
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e[q], e[q + 1]);
+            acc[q] += ms;
+        }
+    }
+    for (auto& x : ev) cudaEventDestroy(x);
+    if (le != cudaSuccess) return fail(c, MB_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(le));
+    if (se != cudaSuccess) return fail(c, MB_ERR_CUDA, std::string("sync: ") + cudaGetErrorString(se));
+    if (ms_out)
+        for (int q = 0; q < 4; ++q) ms_out[q] += acc[q];
+    c->n += n;
+    c->launches += (int64_t)n * launches_per_step(c);
+    return MB_OK;
+}
+
+int mb_flux(mb_ctx* c, double* out_flux6) {
+    if (int rc = check_ctx(c)) return rc;
+    if (!out_flux6) return fail(c, MB_ERR_ARG, "null output");
+    double fl[6];
+    MB_CUDA(c, cudaMemcpyAsync(fl, c->d_flux, sizeof(double) * 6, cudaMemcpyDeviceToHost, c->stream));
+    MB_CUDA(c, cudaStreamSynchronize(c->stream));
+    const double f = c->dt * c->E0 * (c->E0 / c->eta0) * c->dx * c->dx;
+    for (int q = 0; q < 6; ++q) out_flux6[q] = fl[q] * f;
+    return MB_OK;
+}
+
+int mb_synchronize(mb_ctx* c) {
+    if (int rc = check_ctx(c)) return rc;
+    MB_CUDA(c, cudaStreamSynchronize(c->stream));
+    return MB_OK;
+}
+
+int mb_get_step(mb_ctx* c, int64_t* n) {
+    if (int rc = check_ctx(c)) return rc;
+    if (!n) return fail(c, MB_ERR_ARG, "null output");
+    *n = c->n;
+    return MB_OK;
+}
+
+int mb_probe_spectrum(mb_ctx* c, int probe_id, double* out_S, double* out_lam) {
+    if (int rc = check_ctx(c)) return rc;
+    if (probe_id < 0 || probe_id >= (int)c->probes.size() || !out_S)
+        return fail(c, MB_ERR_ARG, "bad probe id or null output");
+    const int K = c->probe_nfreq;
+    std::vector<double2> acc(3 * (size_t)K);
+    MB_CUDA(c, cudaMemcpyAsync(acc.data(), c->d_probe_acc + (size_t)probe_id * 3 * K,
+                               sizeof(double2) * 3 * K, cudaMemcpyDeviceToHost, c->stream));
+    MB_CUDA(c, cudaStreamSynchronize(c->stream));
+    const double f = c->E0 * c->dt;
+    for (int k = 0; k < K; ++k) {
+        double s = 0.0;
+        for (int q = 0; q < 3; ++q) {
+            const double2 v = acc[(size_t)q * K + k];
+            s += (v.x * v.x + v.y * v.y) * f * f;
+        }
+        out_S[k] = s;
+        if (out_lam) out_lam[k] = c->probes[probe_id].lam[k];
+    }
+    return MB_OK;
+}
+
+int mb_face_spectrum(mb_ctx* c, int face, double* out_S, double* out_lam) {
+    if (int rc = check_ctx(c)) return rc;
+    if (!c->face.on) return fail(c, MB_ERR_STATE, "no face probes");
+    if (face < 0 || face > 5 || !out_S) return fail(c, MB_ERR_ARG, "bad face or null output");
+    const int K = c->face.nfreq;
+    const int np = c->face.npts[face];
+    std::vector<double2> acc((size_t)np * 4 * K);
+    if (np) {
+        MB_CUDA(c, cudaMemcpyAsync(acc.data(), c->d_face_acc + (size_t)c->face.offset[face] * 4 * K,
+                                   sizeof(double2) * acc.size(), cudaMemcpyDeviceToHost, c->stream));
+        MB_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    const double w = c->face.every * c->dt;
+    const double scale = (c->E0 * w) * (c->E0 / c->eta0 * w) * std::pow(c->face.stride * c->dx, 2);
+    const double sign = (face % 2) ? 1.0 : -1.0;
+    for (int k = 0; k < K; ++k) {
+        double s = 0.0;
+        for (int q = 0; q < np; ++q) {
+            const double2 Ea = acc[((size_t)q * 4 + 0) * K + k], Eb = acc[((size_t)q * 4 + 1) * K + k];
+            const double2 Ha = acc[((size_t)q * 4 + 2) * K + k], Hb = acc[((size_t)q * 4 + 3) * K + k];
+            // Re(Ea conj(Hb) - Eb conj(Ha))
+            s += (Ea.x * Hb.x + Ea.y * Hb.y) - (Eb.x * Ha.x + Eb.y * Ha.y);
+        }
+        out_S[k] = sign * s * scale;
+        if (out_lam) out_lam[k] = c->face_lam[k];
+    }
+    return MB_OK;
+}
+
+int mb_energy(mb_ctx* c, double* out_U, double* out_flux6) {
+    if (int rc = check_ctx(c)) return rc;
+    if (!out_U) return fail(c, MB_ERR_ARG, "null output");
+    MB_CUDA(c, cudaMemsetAsync(c->d_nonfinite, 0, sizeof(int), c->stream));
+    mb::launch_energy(c->args.f, c->ncell, c->d_lut + 128, c->d_partial, c->n_partial,
+                      c->d_nonfinite, c->d_energy, c->stream);
+    MB_CUDA(c, cudaGetLastError());
+    double U = 0, fl[6];
+    int bad = 0;
+    MB_CUDA(c, cudaMemcpyAsync(&U, c->d_energy, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    MB_CUDA(c, cudaMemcpyAsync(fl, c->d_flux, sizeof(double) * 6, cudaMemcpyDeviceToHost, c->stream));
+    MB_CUDA(c, cudaMemcpyAsync(&bad, c->d_nonfinite, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    MB_CUDA(c, cudaStreamSynchronize(c->stream));
+    *out_U = 0.5 * kEps0 * c->E0 * c->E0 * c->dx * c->dx * c->dx * U;
+    if (out_flux6) {
+        const double f = c->dt * c->E0 * (c->E0 / c->eta0) * c->dx * c->dx;
+        for (int q = 0; q < 6; ++q) out_flux6[q] = fl[q] * f;
+    }
+    if (bad) return fail(c, MB_ERR_NONFINITE, "non-finite field values");
+    return MB_OK;
+}
+
+int mb_get_field(mb_ctx* c, int which, float* host_out) {
+    if (int rc = check_ctx(c)) return rc;
+    if (!host_out || which < 0 || which >= MB_NUM_FIELDS) return fail(c, MB_ERR_ARG, "bad field id or null output");
+    const int64_t N = c->ncell;
+    std::vector<float> tmp((size_t)N);
+    if (which == MB_N0) {
+        std::vector<float> a((size_t)N), b((size_t)N), d((size_t)N);
+        MB_CUDA(c, cudaMemcpyAsync(a.data(), field_ptr(c, MB_N1), 4 * N, cudaMemcpyDeviceToHost, c->stream));
+        MB_CUDA(c, cudaMemcpyAsync(b.data(), field_ptr(c, MB_N2), 4 * N, cudaMemcpyDeviceToHost, c->stream));
+        MB_CUDA(c, cudaMemcpyAsync(d.data(), field_ptr(c, MB_N3), 4 * N, cudaMemcpyDeviceToHost, c->stream));
+        MB_CUDA(c, cudaStreamSynchronize(c->stream));
+        for (int64_t q = 0; q < N; ++q)
+            host_out[q] = c->h_gain[q] ? (float)(c->N_a * (1.0 - (double)a[q] - (double)b[q] - (double)d[q])) : 0.0f;
+        return MB_OK;
+    }
+    MB_CUDA(c, cudaMemcpyAsync(tmp.data(), field_ptr(c, which), 4 * N, cudaMemcpyDeviceToHost, c->stream));
+    MB_CUDA(c, cudaStreamSynchronize(c->stream));
+    const double s = field_scale(c, which);
+    for (int64_t q = 0; q < N; ++q) host_out[q] = (float)(s * (double)tmp[q]);
+    return MB_OK;
+}
+
+int mb_set_field(mb_ctx* c, int which, const float* host_in) {
+    if (int rc = check_ctx(c)) return rc;
+    if (!host_in || which < 0 || which >= MB_NUM_FIELDS) return fail(c, MB_ERR_ARG, "bad field id or null input");
+    if (which == MB_N0) return fail(c, MB_ERR_ARG, "N0 is derived and cannot be set");
+    if (which >= MB_N1 && !(c->N_a > 0)) return fail(c, MB_ERR_STATE, "populations need N_a > 0");
+    const int64_t N = c->ncell;
+    const double s = 1.0 / field_scale(c, which);
+    std::vector<float> tmp((size_t)N);
+    for (int64_t q = 0; q < N; ++q) tmp[q] = (float)(s * (double)host_in[q]);
+    MB_CUDA(c, cudaStreamSynchronize(c->stream));
+    MB_CUDA(c, cudaMemcpy(field_ptr(c, which), tmp.data(), 4 * N, cudaMemcpyHostToDevice));
+    return MB_OK;
+}
+
+int mb_get_field_device(mb_ctx* c, int which, float* dev_out, double* scale) {
+    if (int rc = check_ctx(c)) return rc;
+    if (!dev_out || which < 0 || which >= MB_NUM_FIELDS || which == MB_N0)
+        return fail(c, MB_ERR_ARG, "bad field id (N0 is not stored) or null output");
+    MB_CUDA(c, cudaMemcpyAsync(dev_out, field_ptr(c, which), 4 * c->ncell, cudaMemcpyDeviceToDevice, c->stream));
+    MB_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (scale) *scale = field_scale(c, which);
+    return MB_OK;
+}
+
+int mb_save_state(mb_ctx* c, void* host_blob, size_t* bytes) {
+    if (int rc = check_ctx(c)) return rc;
+    if (!bytes) return fail(c, MB_ERR_ARG, "null size");
+    auto parts = state_parts(c);
+    size_t total = 4 * sizeof(int64_t);
+    for (auto& p : parts) total += p.bytes;
+    if (!host_blob) {
+        *bytes = total;
+        return MB_OK;
+    }
+    if (*bytes < total) return fail(c, MB_ERR_ARG, "blob too small");
+    char* o = (char*)host_blob;
+    const int64_t hdr[4] = {0x4D42464454445331LL, c->ncell, (int64_t)parts.size(), c->n};
+    std::memcpy(o, hdr, sizeof(hdr));
+    o += sizeof(hdr);
+    for (auto& p : parts) {
+        MB_CUDA(c, cudaMemcpyAsync(o, p.ptr, p.bytes, cudaMemcpyDeviceToHost, c->stream));
+        o += p.bytes;
+    }
+    MB_CUDA(c, cudaStreamSynchronize(c->stream));
+    *bytes = total;
+    return MB_OK;
+}
+
+int mb_load_state(mb_ctx* c, const void* host_blob, size_t bytes) {
+    if (int rc = check_ctx(c)) return rc;
+    if (!host_blob) return fail(c, MB_ERR_ARG, "null blob");
+    auto parts = state_parts(c);
+    size_t total = 4 * sizeof(int64_t);
+    for (auto& p : parts) total += p.bytes;
+    const int64_t* hdr = (const int64_t*)host_blob;
+    if (bytes != total || hdr[0] != 0x4D42464454445331LL || hdr[1] != c->ncell || hdr[2] != (int64_t)parts.size())
+        return fail(c, MB_ERR_ARG, "blob does not match this context's layout");
+    const char* o = (const char*)host_blob + 4 * sizeof(int64_t);
+    MB_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (auto& p : parts) {
+        MB_CUDA(c, cudaMemcpy(p.ptr, o, p.bytes, cudaMemcpyHostToDevice));
+        o += p.bytes;
+    }
+    c->n = hdr[3];
+    return MB_OK;
+}
+
+int mb_autotune(mb_ctx* c) {
+    if (int rc = check_ctx(c)) return rc;
+    auto parts = state_parts(c);
+    size_t total = 0;
+    for (auto& p : parts) total += p.bytes;
+    char* backup = nullptr;
+    MB_CUDA(c, cudaStreamSynchronize(c->stream));
+    MB_CUDA(c, cudaMalloc((void**)&backup, total));
+    {
+        char* o = backup;
+        for (auto& p : parts) {
+            cudaMemcpyAsync(o, p.ptr, p.bytes, cudaMemcpyDeviceToDevice, c->stream);
+            o += p.bytes;
+        }
+    }
+    const dim3 cands[] = {dim3(32, 4, 2), dim3(32, 8, 1), dim3(64, 4, 1), dim3(32, 2, 4),
+                          dim3(64, 2, 2), dim3(128, 2, 1), dim3(32, 4, 4), dim3(32, 16, 1),
+                          dim3(64, 8, 1), dim3(128, 4, 1), dim3(256, 1, 1), dim3(32, 8, 2),
+                          dim3(128, 1, 2), dim3(64, 4, 2)};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best_h = 1e30f, best_e = 1e30f;
+    dim3 bh = c->blk_h, be = c->blk_e;
+    const int reps = c->ncell > 4000000 ? 3 : 10;
+    for (const dim3& b : cands) {
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int warm = 0; warm < 1; ++warm) {
+                if (pass == 0) mb::launch_h_pass(c->args, b, c->stream);
+                else mb::launch_e_pass(c->args, b, c->stream);
+            }
+            cudaEventRecord(e0, c->stream);
+            for (int r = 0; r < reps; ++r) {
+                if (pass == 0) mb::launch_h_pass(c->args, b, c->stream);
+                else mb::launch_e_pass(c->args, b, c->stream);
+            }
+            cudaEventRecord(e1, c->stream);
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (pass == 0 && ms < best_h) { best_h = ms; bh = b; }
+            if (pass == 1 && ms < best_e) { best_e = ms; be = b; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    {
+        const char* o = backup;
+        for (auto& p : parts) {
+            cudaMemcpyAsync(p.ptr, o, p.bytes, cudaMemcpyDeviceToDevice, c->stream);
+            o += p.bytes;
+        }
+    }
+    cudaStreamSynchronize(c->stream);
+    cudaFree(backup);
+    MB_CUDA(c, cudaGetLastError());
+    c->blk_h = bh;
+    c->blk_e = be;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[{c->nx, c->ny, c->nz, c->p.npml}] = {bh, be};
+    }
+    drop_graphs(c);
+    return MB_OK;
+}
+
+int mb_launch_stats(mb_ctx* c, int* per_step, int64_t* total) {
+    if (int rc = check_ctx(c)) return rc;
+    if (per_step) *per_step = launches_per_step(c);
+    if (total) *total = c->launches;
+    return MB_OK;
+}
+
+int mb_device_bytes(mb_ctx* c, size_t* bytes) {
+    if (int rc = check_ctx(c)) return rc;
+    if (!bytes) return fail(c, MB_ERR_ARG, "null output");
+    *bytes = c->dev_bytes;
+    return MB_OK;
+}
+
+int mb_philox4x32_10(const uint32_t* ctr, const uint32_t key[2], uint32_t* out, int n) {
+    if (!ctr || !key || !out || n < 0) return fail(nullptr, MB_ERR_ARG, "bad philox arguments");
+    if (n == 0) return MB_OK;
+    uint4 *d_in = nullptr, *d_out = nullptr;
+    cudaError_t e = cudaMalloc((void**)&d_in, sizeof(uint4) * (size_t)n);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d_out, sizeof(uint4) * (size_t)n);
+    if (e == cudaSuccess) e = cudaMemcpy(d_in, ctr, sizeof(uint4) * (size_t)n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        mb::launch_philox(d_in, key[0], key[1], d_out, n, 0);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(out, d_out, sizeof(uint4) * (size_t)n, cudaMemcpyDeviceToHost);
+    if (d_in) cudaFree(d_in);
+    if (d_out) cudaFree(d_out);
+    if (e != cudaSuccess) return fail(nullptr, MB_ERR_CUDA, std::string("philox: ") + cudaGetErrorString(e));
+    return MB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,347 @@
+// Device-side data of one Maxwell–Bloch FDTD realization and the per-cell
+// update functions of the two field passes.  Every kernel that advances a
+// realization (the plain step, the batched ensemble, the adjoint's forward
+// recomputation) calls these same functions, so their results agree bit for
+// bit.
+//
+// Units on the device are scaled so that FP32 stays far from under/overflow:
+//   E_s = E/E0, H_s = eta0 H/E0, P_s = P/(eps0 E0), J_s = J dt/(eps0 E0),
+//   n_i = N_i/N_a (i = 1..3; N0 = N_a (1 - n1 - n2 - n3) is not stored),
+//   psi_E,s = psi_E eta0 dx/E0, psi_H,s = psi_H dx/E0,
+// with E0 = sqrt(hbar w0 n_ref / eps0).  In these units the Yee step reads
+//   H_s -= S (dE_s + psi_H,s),          S = c dt/dx,
+//   E_s += (1/eps_r) (S (dH_s + psi_E,s) - J_s - J_src,s).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mb {
+
+struct DevGrid {
+    int nx, ny, nz;
+    int64_t nxy, ncell;
+};
+
+struct DevFields {
+    float *ex, *ey, *ez, *hx, *hy, *hz;
+    float *px, *py, *pz, *jx, *jy, *jz;
+    float *n1, *n2, *n3;
+    const uint8_t* mat;        // bits 0..6: material id, bit 7: gain medium
+    const float* inv_eps;      // dense 1/eps_r per cell, or nullptr
+    const float* lut_inv_eps;  // 1/eps_r per material id (128 entries)
+};
+
+// CPML memories live only in the slabs: for axis w, 2 L layers indexed by
+// s = i (i < L) or s = i - n + 2L (i >= n - L).  Four planes per slab axis:
+// f = 0, 1: the two E components with a w-derivative, f = 2, 3: the two H
+// components.  x-slab index ((f nz + k) ny + j) 2L + s, y-slab
+// ((f nz + k) 2L + s) nx + i, z-slab ((f 2L + s) ny + j) nx + i.
+struct DevCpml {
+    int L;
+    float *psx, *psy, *psz;
+    const float *bex, *cex, *bhx, *chx;
+    const float *bey, *cey, *bhy, *chy;
+    const float *bez, *cez, *bhz, *chz;
+};
+
+// Gain medium, scaled: J_s' = cJ1 J_s + cJE (n1 - n2) E_s - cJP P_s
+//                            + cJN sqrt(max(n2,0) + nfloor) zeta,
+// n_i' = n_i + g_i + sum_j G_ij n_j + mk_i S_pop, S_pop = (E_s + E_s').J_s'/2.
+struct DevGain {
+    int on;
+    float cJ1, cJE, cJP, cJN, nfloor;
+    float g[3];
+    float G[3][3];
+    float mk[3];
+    uint32_t key0, key1;
+};
+
+struct DevSource {
+    int on, comp;
+    int64_t cell;
+    double amp_s, ws, t0, tau, dt;
+};
+
+// Outward Poynting flux of the interior box [r0, r1) per axis through the
+// planes plo / phi, accumulated in FP64 (scaled units).
+struct DevFlux {
+    int on;
+    int plo[3], phi[3];
+    int r0[3], r1[3];
+    double* acc;   // 6 values: x-, x+, y-, y+, z-, z+
+};
+
+struct StepArgs {
+    DevGrid g;
+    DevFields f;
+    DevCpml pml;
+    DevGain gain;
+    DevSource src;
+    DevFlux flux;
+    float S;
+    long long* step_ctr;   // [0]: index of the step in progress, [1]: next index
+};
+
+// ------------------------------------------------------------------ Philox
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32->64 multiplies mixing the counter with a key bumped by two Weyl
+// constants between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+// u = ((x >> 9) + 1/2) 2^-23: exact in FP32, strictly inside (0, 1).
+__device__ __forceinline__ float u32_to_unit(uint32_t x) {
+    return (static_cast<float>(x >> 9) + 0.5f) * 1.1920928955078125e-07f;
+}
+
+// Three standard normals of cell `cell` at step `step` (Box–Muller, FP32
+// with the accurate logf / sqrtf / sincospif).
+__device__ __forceinline__ void langevin_normals(uint32_t cell, uint32_t step, uint32_t k0,
+                                                 uint32_t k1, float& z0, float& z1, float& z2) {
+    const uint4 x = philox4x32_10(make_uint4(cell, step, 0u, 0u), k0, k1);
+    const float u0 = u32_to_unit(x.x), u1 = u32_to_unit(x.y);
+    const float u2 = u32_to_unit(x.z), u3 = u32_to_unit(x.w);
+    const float r01 = sqrtf(-2.0f * logf(u0));
+    const float r23 = sqrtf(-2.0f * logf(u2));
+    float s1, c1, s3, c3;
+    sincospif(2.0f * u1, &s1, &c1);
+    sincospif(2.0f * u3, &s3, &c3);
+    z0 = r01 * c1;
+    z1 = r01 * s1;
+    z2 = r23 * c3;
+}
+
+__device__ __forceinline__ int slab_index(int i, int n, int L) {
+    return (i < L) ? i : i - n + 2 * L;
+}
+
+// ------------------------------------------------------------- H half-step
+// H^{n+1/2} = H^{n-1/2} - S (curl_fwd E^n + psi_H); E beyond the last cell is 0.
+__device__ __forceinline__ void h_update_cell(const StepArgs& a, int i, int j, int k) {
+    const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
+    const int64_t nxy = a.g.nxy;
+    const int64_t c = i + (int64_t)nx * j + nxy * k;
+    const DevFields& f = a.f;
+    const float ex = f.ex[c], ey = f.ey[c], ez = f.ez[c];
+    const float ex_j1 = (j + 1 < ny) ? f.ex[c + nx] : 0.0f;
+    const float ex_k1 = (k + 1 < nz) ? f.ex[c + nxy] : 0.0f;
+    const float ey_i1 = (i + 1 < nx) ? f.ey[c + 1] : 0.0f;
+    const float ey_k1 = (k + 1 < nz) ? f.ey[c + nxy] : 0.0f;
+    const float ez_i1 = (i + 1 < nx) ? f.ez[c + 1] : 0.0f;
+    const float ez_j1 = (j + 1 < ny) ? f.ez[c + nx] : 0.0f;
+    const float dEz_dy = ez_j1 - ez, dEy_dz = ey_k1 - ey;
+    const float dEx_dz = ex_k1 - ex, dEz_dx = ez_i1 - ez;
+    const float dEy_dx = ey_i1 - ey, dEx_dy = ex_j1 - ex;
+    float cx = dEz_dy - dEy_dz;
+    float cy = dEx_dz - dEz_dx;
+    float cz = dEy_dx - dEx_dy;
+    const int L = a.pml.L;
+    if (L > 0) {
+        const int L2 = 2 * L;
+        if (i < L || i >= nx - L) {
+            const int s = slab_index(i, nx, L);
+            const int64_t plane = (int64_t)nz * ny * L2;
+            const int64_t q = ((int64_t)k * ny + j) * L2 + s;
+            const float b = a.pml.bhx[i], cc = a.pml.chx[i];
+            float* p = a.pml.psx;
+            const float psi_yx = b * p[q + 2 * plane] + cc * dEz_dx;   // Hy: d/dx Ez
+            const float psi_zx = b * p[q + 3 * plane] + cc * dEy_dx;   // Hz: d/dx Ey
+            p[q + 2 * plane] = psi_yx;
+            p[q + 3 * plane] = psi_zx;
+            cy -= psi_yx;
+            cz += psi_zx;
+        }
+        if (j < L || j >= ny - L) {
+            const int s = slab_index(j, ny, L);
+            const int64_t plane = (int64_t)nz * L2 * nx;
+            const int64_t q = ((int64_t)k * L2 + s) * nx + i;
+            const float b = a.pml.bhy[j], cc = a.pml.chy[j];
+            float* p = a.pml.psy;
+            const float psi_xy = b * p[q + 2 * plane] + cc * dEz_dy;   // Hx: d/dy Ez
+            const float psi_zy = b * p[q + 3 * plane] + cc * dEx_dy;   // Hz: d/dy Ex
+            p[q + 2 * plane] = psi_xy;
+            p[q + 3 * plane] = psi_zy;
+            cx += psi_xy;
+            cz -= psi_zy;
+        }
+        if (k < L || k >= nz - L) {
+            const int s = slab_index(k, nz, L);
+            const int64_t plane = (int64_t)L2 * ny * nx;
+            const int64_t q = ((int64_t)s * ny + j) * nx + i;
+            const float b = a.pml.bhz[k], cc = a.pml.chz[k];
+            float* p = a.pml.psz;
+            const float psi_xz = b * p[q + 2 * plane] + cc * dEy_dz;   // Hx: d/dz Ey
+            const float psi_yz = b * p[q + 3 * plane] + cc * dEx_dz;   // Hy: d/dz Ex
+            p[q + 2 * plane] = psi_xz;
+            p[q + 3 * plane] = psi_yz;
+            cx -= psi_xz;
+            cy += psi_yz;
+        }
+    }
+    const float S = a.S;
+    f.hx[c] = f.hx[c] - S * cx;
+    f.hy[c] = f.hy[c] - S * cy;
+    f.hz[c] = f.hz[c] - S * cz;
+}
+
+// Soft current J_src,s at t = (n + 1/2) dt (FP64: one cell per step).
+__device__ __forceinline__ float source_value(const DevSource& s, long long n) {
+    const double t = ((double)n + 0.5) * s.dt - s.t0;
+    const double e = t / s.tau;
+    return (float)(s.amp_s * sin(s.ws * t) * exp(-e * e));
+}
+
+// ------------------------------------------ fused E / gain / population pass
+// Per cell, in order: J^{n+1/2} and P^{n+1} (gain cells, with the Langevin
+// force of step n), E^{n+1} (backward curl of H^{n+1/2}, CPML, -J, source,
+// PEC walls), N^{n+1}.  fl[6] receives this cell's outward face-flux terms.
+__device__ __forceinline__ void e_update_cell(const StepArgs& a, int i, int j, int k,
+                                              long long n, float fl[6]) {
+    const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
+    const int64_t nxy = a.g.nxy;
+    const int64_t c = i + (int64_t)nx * j + nxy * k;
+    const DevFields& f = a.f;
+    const float hx = f.hx[c], hy = f.hy[c], hz = f.hz[c];
+    const float hx_j = (j > 0) ? f.hx[c - nx] : 0.0f;
+    const float hx_k = (k > 0) ? f.hx[c - nxy] : 0.0f;
+    const float hy_i = (i > 0) ? f.hy[c - 1] : 0.0f;
+    const float hy_k = (k > 0) ? f.hy[c - nxy] : 0.0f;
+    const float hz_i = (i > 0) ? f.hz[c - 1] : 0.0f;
+    const float hz_j = (j > 0) ? f.hz[c - nx] : 0.0f;
+    const float dHz_dy = hz - hz_j, dHy_dz = hy - hy_k;
+    const float dHx_dz = hx - hx_k, dHz_dx = hz - hz_i;
+    const float dHy_dx = hy - hy_i, dHx_dy = hx - hx_j;
+    float cx = dHz_dy - dHy_dz;
+    float cy = dHx_dz - dHz_dx;
+    float cz = dHy_dx - dHx_dy;
+    const int L = a.pml.L;
+    if (L > 0) {
+        const int L2 = 2 * L;
+        if (i < L || i >= nx - L) {
+            const int s = slab_index(i, nx, L);
+            const int64_t plane = (int64_t)nz * ny * L2;
+            const int64_t q = ((int64_t)k * ny + j) * L2 + s;
+            const float b = a.pml.bex[i], cc = a.pml.cex[i];
+            float* p = a.pml.psx;
+            const float psi_yx = b * p[q] + cc * dHz_dx;            // Ey: d/dx Hz
+            const float psi_zx = b * p[q + plane] + cc * dHy_dx;    // Ez: d/dx Hy
+            p[q] = psi_yx;
+            p[q + plane] = psi_zx;
+            cy -= psi_yx;
+            cz += psi_zx;
+        }
+        if (j < L || j >= ny - L) {
+            const int s = slab_index(j, ny, L);
+            const int64_t plane = (int64_t)nz * L2 * nx;
+            const int64_t q = ((int64_t)k * L2 + s) * nx + i;
+            const float b = a.pml.bey[j], cc = a.pml.cey[j];
+            float* p = a.pml.psy;
+            const float psi_xy = b * p[q] + cc * dHz_dy;            // Ex: d/dy Hz
+            const float psi_zy = b * p[q + plane] + cc * dHx_dy;    // Ez: d/dy Hx
+            p[q] = psi_xy;
+            p[q + plane] = psi_zy;
+            cx += psi_xy;
+            cz -= psi_zy;
+        }
+        if (k < L || k >= nz - L) {
+            const int s = slab_index(k, nz, L);
+            const int64_t plane = (int64_t)L2 * ny * nx;
+            const int64_t q = ((int64_t)s * ny + j) * nx + i;
+            const float b = a.pml.bez[k], cc = a.pml.cez[k];
+            float* p = a.pml.psz;
+            const float psi_xz = b * p[q] + cc * dHy_dz;            // Ex: d/dz Hy
+            const float psi_yz = b * p[q + plane] + cc * dHx_dz;    // Ey: d/dz Hx
+            p[q] = psi_xz;
+            p[q + plane] = psi_yz;
+            cx -= psi_xz;
+            cy += psi_yz;
+        }
+    }
+    const uint8_t m = f.mat[c];
+    const float ie = f.inv_eps ? f.inv_eps[c] : f.lut_inv_eps[m & 0x7f];
+    const float ex0 = f.ex[c], ey0 = f.ey[c], ez0 = f.ez[c];
+    const bool gain = a.gain.on && (m & 0x80);
+    float jx = 0.0f, jy = 0.0f, jz = 0.0f;
+    float n1 = 0.0f, n2 = 0.0f, n3 = 0.0f;
+    if (gain) {
+        const DevGain& G = a.gain;
+        n1 = f.n1[c];
+        n2 = f.n2[c];
+        n3 = f.n3[c];
+        const float dn = n1 - n2;
+        const float amp = G.cJN * sqrtf(fmaxf(n2, 0.0f) + G.nfloor);
+        float z0, z1, z2;
+        langevin_normals((uint32_t)c, (uint32_t)n, G.key0, G.key1, z0, z1, z2);
+        const float px = f.px[c], py = f.py[c], pz = f.pz[c];
+        jx = G.cJ1 * f.jx[c] + G.cJE * dn * ex0 - G.cJP * px + amp * z0;
+        jy = G.cJ1 * f.jy[c] + G.cJE * dn * ey0 - G.cJP * py + amp * z1;
+        jz = G.cJ1 * f.jz[c] + G.cJE * dn * ez0 - G.cJP * pz + amp * z2;
+        f.jx[c] = jx;
+        f.jy[c] = jy;
+        f.jz[c] = jz;
+        f.px[c] = px + jx;
+        f.py[c] = py + jy;
+        f.pz[c] = pz + jz;
+    }
+    float sx = jx, sy = jy, sz = jz;
+    if (a.src.on && c == a.src.cell) {
+        const float v = source_value(a.src, n);
+        if (a.src.comp == 0) sx += v;
+        else if (a.src.comp == 1) sy += v;
+        else sz += v;
+    }
+    const float S = a.S;
+    float ex1 = ex0 + ie * (S * cx - sx);
+    float ey1 = ey0 + ie * (S * cy - sy);
+    float ez1 = ez0 + ie * (S * cz - sz);
+    // PEC walls: tangential E on the planes i = 0, j = 0, k = 0.
+    if (j == 0 || k == 0) ex1 = 0.0f;
+    if (i == 0 || k == 0) ey1 = 0.0f;
+    if (i == 0 || j == 0) ez1 = 0.0f;
+    f.ex[c] = ex1;
+    f.ey[c] = ey1;
+    f.ez[c] = ez1;
+    if (gain) {
+        const DevGain& G = a.gain;
+        const float sp = 0.5f * ((ex0 + ex1) * jx + (ey0 + ey1) * jy + (ez0 + ez1) * jz);
+        f.n1[c] = n1 + (G.g[0] + G.G[0][0] * n1 + G.G[0][1] * n2 + G.G[0][2] * n3 + G.mk[0] * sp);
+        f.n2[c] = n2 + (G.g[1] + G.G[1][0] * n1 + G.G[1][1] * n2 + G.G[1][2] * n3 + G.mk[1] * sp);
+        f.n3[c] = n3 + (G.g[2] + G.G[2][0] * n1 + G.G[2][1] * n2 + G.G[2][2] * n3 + G.mk[2] * sp);
+    }
+    if (a.flux.on) {
+        // (E^n + E^{n+1})/2 on the plane against H^{n+1/2} half a cell below it.
+        const DevFlux& F = a.flux;
+        const float mx = 0.5f * (ex0 + ex1), my = 0.5f * (ey0 + ey1), mz = 0.5f * (ez0 + ez1);
+        if (j >= F.r0[1] && j < F.r1[1] && k >= F.r0[2] && k < F.r1[2]) {
+            const float s = my * hz_i - mz * hy_i;
+            if (i == F.plo[0]) fl[0] -= s;
+            if (i == F.phi[0]) fl[1] += s;
+        }
+        if (i >= F.r0[0] && i < F.r1[0] && k >= F.r0[2] && k < F.r1[2]) {
+            const float s = mz * hx_j - mx * hz_j;
+            if (j == F.plo[1]) fl[2] -= s;
+            if (j == F.phi[1]) fl[3] += s;
+        }
+        if (i >= F.r0[0] && i < F.r1[0] && j >= F.r0[1] && j < F.r1[1]) {
+            const float s = mx * hy_k - my * hx_k;
+            if (k == F.plo[2]) fl[4] -= s;
+            if (k == F.phi[2]) fl[5] += s;
+        }
+    }
+}
+
+}  // namespace mb

@@ -1,0 +1,123 @@
+// Host-side structures of the Maxwell–Bloch FDTD library (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "mb_device.cuh"
+#include "mb_fdtd.h"
+
+namespace mb {
+
+struct DevPointProbes {
+    int count;
+    int nfreq;          // bins per probe (all probes share one count)
+    const int64_t* cell;
+    const double* omega;   // [count][nfreq]
+    double2* acc;          // [count][3][nfreq]
+};
+
+struct DevFaceProbes {
+    int on;
+    int stride, every, nfreq, pts_per_block;
+    int plane[6];       // plane index along the face normal
+    int r0a[6], r0b[6]; // first transverse coordinate along (a, b)
+    int na[6], npts[6]; // points along a, total points
+    int offset[6];      // first point of each face in acc
+    const double* omega;
+    double2* acc;       // [point][4][nfreq]: Ea, Eb, Ha, Hb
+};
+
+void launch_h_pass(const StepArgs& a, dim3 block, cudaStream_t s);
+void launch_e_pass(const StepArgs& a, dim3 block, cudaStream_t s);
+void launch_point_dft(const DevPointProbes& pp, const DevFields& f, const long long* ctr,
+                      double dt, cudaStream_t s);
+void launch_face_dft(const DevFaceProbes& fp, const DevFields& f, const DevGrid& g,
+                     const long long* ctr, double dt, cudaStream_t s);
+void launch_philox(const uint4* ctr, uint32_t k0, uint32_t k1, uint4* out, int n, cudaStream_t s);
+void launch_energy(const DevFields& f, int64_t ncell, const float* lut_eps, double* partial,
+                   int nparts, int* nonfinite, double* out, cudaStream_t s);
+
+// Physical constants (SI, CODATA 2018).
+constexpr double kC0 = 299792458.0;
+constexpr double kEps0 = 8.8541878128e-12;
+constexpr double kHbar = 1.054571817e-34;
+constexpr double kQe = 1.602176634e-19;
+constexpr double kPi = 3.14159265358979323846;
+
+struct PointProbeHost {
+    int64_t cell;
+    int nfreq;
+    std::vector<double> lam, omega;
+};
+
+}  // namespace mb
+
+struct mb_ctx {
+    int nx = 0, ny = 0, nz = 0;
+    int64_t ncell = 0;
+    double dx = 0, dt = 0;
+    mb_params p{};
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+
+    // scales between SI and the device units
+    double E0 = 0, eta0 = 0, S = 0;
+
+    // device memory
+    float* d_fields = nullptr;         // 15 arrays of ncell floats
+    uint8_t* d_mat = nullptr;
+    float* d_inv_eps = nullptr;        // dense 1/eps_r (only when > 128 materials)
+    float* d_lut = nullptr;            // [0..127]: 1/eps_r, [128..255]: eps_r
+    float* d_psi[3] = {nullptr, nullptr, nullptr};
+    size_t psi_elems[3] = {0, 0, 0};
+    float* d_coef = nullptr;           // CPML tables
+    long long* d_ctr = nullptr;        // step counters
+    double* d_flux = nullptr;          // 6 accumulators
+    double* d_partial = nullptr;       // energy partial sums
+    double* d_energy = nullptr;
+    int* d_nonfinite = nullptr;
+    int n_partial = 0;
+
+    // point probes
+    std::vector<mb::PointProbeHost> probes;
+    int64_t* d_probe_cell = nullptr;
+    double* d_probe_omega = nullptr;
+    double2* d_probe_acc = nullptr;
+    int probe_nfreq = 0;
+
+    // face probes
+    mb::DevFaceProbes face{};
+    std::vector<double> face_lam;
+    double* d_face_omega = nullptr;
+    double2* d_face_acc = nullptr;
+    int64_t face_points = 0;
+
+    // material
+    bool have_material = false;
+    bool dense_eps = false;
+    std::vector<uint8_t> h_gain;       // gain flag per cell (for N0 read-out)
+    std::vector<float> h_lut_eps;      // eps_r per material id
+    double N_a = 0, W_p = 0;
+    uint64_t seed = 0;
+
+    // per-step arguments
+    mb::StepArgs args{};
+    mb::DevSource src{};
+    dim3 blk_h{32, 4, 2}, blk_e{32, 4, 2};
+
+    // stepping
+    int64_t n = 0;
+    int64_t launches = 0;
+    cudaGraphExec_t graph_chunk = nullptr;
+    cudaGraphExec_t graph_one = nullptr;
+    int graph_chunk_steps = 16;
+    bool graph_dirty = true;
+
+    std::string err;
+    size_t dev_bytes = 0;
+};

@@ -1,0 +1,261 @@
+// Kernels of the plain Maxwell–Bloch FDTD step and their launchers.
+//
+//   k_h_pass      H half-step (forward curl of E, H-side CPML)
+//   k_e_pass      fused E / Lorentz polarization / Langevin noise / population
+//                 pass, plus the outward face flux of the interior box
+//   k_point_dft   running DFT of E at the point probes (FP64 accumulators)
+//   k_face_dft    running DFT of tangential E and H on the face sub-grids
+//   k_energy_*    two-pass deterministic reduction of the field energy
+//
+// The field passes are memory-bound stencils: one thread per cell, thread
+// blocks tiled over (x, y, z) with x fastest so that warps read contiguous
+// rows; neighbours come through L1/L2.  No tensor cores: nothing here is a
+// dense contraction.
+#include "mb_host.h"
+
+#include <cstdio>
+
+namespace mb {
+
+// Blocks whose cell range contains a face plane reduce the flux; the others
+// skip the reduction (block-uniform test).
+__device__ __forceinline__ bool block_on_face(const DevFlux& F) {
+    if (!F.on) return false;
+    const int i0 = blockIdx.x * blockDim.x, i1 = i0 + blockDim.x;
+    const int j0 = blockIdx.y * blockDim.y, j1 = j0 + blockDim.y;
+    const int k0 = blockIdx.z * blockDim.z, k1 = k0 + blockDim.z;
+    return (F.plo[0] >= i0 && F.plo[0] < i1) || (F.phi[0] >= i0 && F.phi[0] < i1) ||
+           (F.plo[1] >= j0 && F.plo[1] < j1) || (F.phi[1] >= j0 && F.phi[1] < j1) ||
+           (F.plo[2] >= k0 && F.plo[2] < k1) || (F.phi[2] >= k0 && F.phi[2] < k1);
+}
+
+__global__ void __launch_bounds__(512) k_h_pass(StepArgs a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z * blockDim.z + threadIdx.z;
+    if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 &&
+        threadIdx.y == 0 && threadIdx.z == 0) {
+        // No other thread of this launch reads the counter; the E pass and the
+        // probes of this step run after this kernel in stream order.
+        const long long nxt = a.step_ctr[1];
+        a.step_ctr[0] = nxt;
+        a.step_ctr[1] = nxt + 1;
+    }
+    if (i < a.g.nx && j < a.g.ny && k < a.g.nz) h_update_cell(a, i, j, k);
+}
+
+__global__ void __launch_bounds__(512) k_e_pass(StepArgs a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z * blockDim.z + threadIdx.z;
+    const long long n = a.step_ctr[0];
+    float fl[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (i < a.g.nx && j < a.g.ny && k < a.g.nz) e_update_cell(a, i, j, k, n, fl);
+    if (!block_on_face(a.flux)) return;
+    // Block reduction of the six flux terms in FP64, one atomic per face.
+    __shared__ double red[6][32];
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const int lane = tid & 31, warp = tid >> 5;
+    const int nwarps = (blockDim.x * blockDim.y * blockDim.z + 31) >> 5;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        double v = (double)fl[q];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[q][warp] = v;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            double v = (lane < nwarps) ? red[q][lane] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0 && v != 0.0) atomicAdd(&a.flux.acc[q], v);
+        }
+    }
+}
+
+// One block per probe, threads over frequency bins:
+// acc[p][c][k] += E_c(t_{n+1}) exp(i w_k t_{n+1})   (scaled; times dt E0 on read-out)
+__global__ void k_point_dft(DevPointProbes pp, const float* ex, const float* ey, const float* ez,
+                            const long long* step_ctr, double dt) {
+    const int p = blockIdx.x;
+    const long long n = step_ctr[0];
+    const double t = (double)(n + 1) * dt;
+    const int64_t cell = pp.cell[p];
+    const float e[3] = {ex[cell], ey[cell], ez[cell]};
+    const int K = pp.nfreq;
+    for (int kk = threadIdx.x; kk < K; kk += blockDim.x) {
+        double s, co;
+        sincos(pp.omega[p * K + kk] * t, &s, &co);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            double2* acc = pp.acc + ((int64_t)p * 3 + c) * K + kk;
+            double2 v = *acc;
+            v.x += (double)e[c] * co;
+            v.y += (double)e[c] * s;
+            *acc = v;
+        }
+    }
+}
+
+// Face DFT: block (chunk of points, face); thread per frequency bin, looping
+// over the chunk's points so each warp touches contiguous accumulators.
+__global__ void k_face_dft(DevFaceProbes fp, DevFields f, DevGrid g, const long long* step_ctr,
+                           double dt) {
+    const long long n = step_ctr[0];
+    if ((n + 1) % fp.every != 0) return;
+    const int face = blockIdx.y;
+    const int axis = face >> 1;
+    const int np = fp.npts[face];
+    const int p0 = blockIdx.x * fp.pts_per_block;
+    if (p0 >= np) return;
+    const int p1 = min(np, p0 + fp.pts_per_block);
+    const int plane = fp.plane[face];
+    const int K = fp.nfreq;
+    const int na = fp.na[face];
+    const double tE = (double)(n + 1) * dt, tH = tE - 0.5 * dt;
+    for (int kk = threadIdx.x; kk < K; kk += blockDim.x) {
+        const double w = fp.omega[kk];
+        double sE, cE, sH, cH;
+        sincos(w * tE, &sE, &cE);
+        sincos(w * tH, &sH, &cH);
+        for (int p = p0; p < p1; ++p) {
+            const int ia = p % na, ib = p / na;
+            // transverse coordinates of point (ia, ib): (a, b) axes per face
+            int i, j, k;
+            const int ca = fp.r0a[face] + ia * fp.stride, cb = fp.r0b[face] + ib * fp.stride;
+            float Ea = 0.f, Eb = 0.f, Ha = 0.f, Hb = 0.f;
+            if (axis == 0) {        // x-face: points (j = ca, k = cb); (a, b) = (y, z)
+                j = ca; k = cb;
+                if (plane < g.nx) {
+                    const int64_t c = plane + (int64_t)g.nx * j + g.nxy * k;
+                    Ea = f.ey[c]; Eb = f.ez[c];
+                }
+                if (plane >= 1) {
+                    const int64_t c = (plane - 1) + (int64_t)g.nx * j + g.nxy * k;
+                    Ha = f.hy[c]; Hb = f.hz[c];
+                }
+            } else if (axis == 1) { // y-face: points (i = ca, k = cb); (a, b) = (z, x)
+                i = ca; k = cb;
+                if (plane < g.ny) {
+                    const int64_t c = i + (int64_t)g.nx * plane + g.nxy * k;
+                    Ea = f.ez[c]; Eb = f.ex[c];
+                }
+                if (plane >= 1) {
+                    const int64_t c = i + (int64_t)g.nx * (plane - 1) + g.nxy * k;
+                    Ha = f.hz[c]; Hb = f.hx[c];
+                }
+            } else {                // z-face: points (i = ca, j = cb); (a, b) = (x, y)
+                i = ca; j = cb;
+                if (plane < g.nz) {
+                    const int64_t c = i + (int64_t)g.nx * j + g.nxy * plane;
+                    Ea = f.ex[c]; Eb = f.ey[c];
+                }
+                if (plane >= 1) {
+                    const int64_t c = i + (int64_t)g.nx * j + g.nxy * (plane - 1);
+                    Ha = f.hx[c]; Hb = f.hy[c];
+                }
+            }
+            double2* acc = fp.acc + (((int64_t)fp.offset[face] + p) * 4) * K + kk;
+            double2 v;
+            v = acc[0];     v.x += (double)Ea * cE; v.y += (double)Ea * sE; acc[0] = v;
+            v = acc[K];     v.x += (double)Eb * cE; v.y += (double)Eb * sE; acc[K] = v;
+            v = acc[2 * K]; v.x += (double)Ha * cH; v.y += (double)Ha * sH; acc[2 * K] = v;
+            v = acc[3 * K]; v.x += (double)Hb * cH; v.y += (double)Hb * sH; acc[3 * K] = v;
+        }
+    }
+}
+
+// Energy, pass 1: per-block partial sums of eps_r |E_s|^2 + |H_s|^2 (FP64)
+// into `partial` (one double per block), non-finite values flagged.
+__global__ void __launch_bounds__(256) k_energy_partial(DevFields f, int64_t ncell,
+                                                        const float* lut_eps, double* partial,
+                                                        int* nonfinite) {
+    double acc = 0.0;
+    bool bad = false;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const float e2 = f.ex[c] * f.ex[c] + f.ey[c] * f.ey[c] + f.ez[c] * f.ez[c];
+        const float h2 = f.hx[c] * f.hx[c] + f.hy[c] * f.hy[c] + f.hz[c] * f.hz[c];
+        const double eps = f.inv_eps ? 1.0 / (double)f.inv_eps[c] : (double)lut_eps[f.mat[c] & 0x7f];
+        const double v = eps * (double)e2 + (double)h2;
+        bad |= !isfinite(e2) || !isfinite(h2);
+        acc += v;
+    }
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) red[warp] = acc;
+    __syncthreads();
+    if (warp == 0) {
+        acc = (lane < (int)(blockDim.x >> 5)) ? red[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (lane == 0) partial[blockIdx.x] = acc;
+    }
+    if (bad) atomicOr(nonfinite, 1);
+}
+
+// Energy, pass 2: one block sums the partials in a fixed order.
+__global__ void k_energy_final(const double* partial, int nparts, double* out) {
+    __shared__ double red[32];
+    double acc = 0.0;
+    for (int q = threadIdx.x; q < nparts; q += blockDim.x) acc += partial[q];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) red[warp] = acc;
+    __syncthreads();
+    if (warp == 0) {
+        acc = (lane < (int)(blockDim.x >> 5)) ? red[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (lane == 0) *out = acc;
+    }
+}
+
+// Philox on n counters (diagnostic entry point).
+__global__ void k_philox(const uint4* ctr, uint32_t k0, uint32_t k1, uint4* out, int n) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) out[t] = philox4x32_10(ctr[t], k0, k1);
+}
+
+// ------------------------------------------------------------------ launchers
+
+void launch_philox(const uint4* ctr, uint32_t k0, uint32_t k1, uint4* out, int n, cudaStream_t s) {
+    k_philox<<<(n + 255) / 256, 256, 0, s>>>(ctr, k0, k1, out, n);
+}
+
+static dim3 grid_for(const DevGrid& g, dim3 b) {
+    return dim3((g.nx + b.x - 1) / b.x, (g.ny + b.y - 1) / b.y, (g.nz + b.z - 1) / b.z);
+}
+
+void launch_h_pass(const StepArgs& a, dim3 block, cudaStream_t s) {
+    k_h_pass<<<grid_for(a.g, block), block, 0, s>>>(a);
+}
+
+void launch_e_pass(const StepArgs& a, dim3 block, cudaStream_t s) {
+    k_e_pass<<<grid_for(a.g, block), block, 0, s>>>(a);
+}
+
+void launch_point_dft(const DevPointProbes& pp, const DevFields& f, const long long* ctr,
+                      double dt, cudaStream_t s) {
+    if (pp.count <= 0) return;
+    k_point_dft<<<pp.count, 128, 0, s>>>(pp, f.ex, f.ey, f.ez, ctr, dt);
+}
+
+void launch_face_dft(const DevFaceProbes& fp, const DevFields& f, const DevGrid& g,
+                     const long long* ctr, double dt, cudaStream_t s) {
+    if (!fp.on) return;
+    int maxpts = 0;
+    for (int q = 0; q < 6; ++q) maxpts = fp.npts[q] > maxpts ? fp.npts[q] : maxpts;
+    if (maxpts == 0) return;
+    dim3 grid((maxpts + fp.pts_per_block - 1) / fp.pts_per_block, 6);
+    const int threads = fp.nfreq < 128 ? ((fp.nfreq + 31) / 32) * 32 : 128;
+    k_face_dft<<<grid, threads, 0, s>>>(fp, f, g, ctr, dt);
+}
+
+void launch_energy(const DevFields& f, int64_t ncell, const float* lut_eps, double* partial,
+                   int nparts, int* nonfinite, double* out, cudaStream_t s) {
+    k_energy_partial<<<nparts, 256, 0, s>>>(f, ncell, lut_eps, partial, nonfinite);
+    k_energy_final<<<1, 1024, 0, s>>>(partial, nparts, out);
+}
+
+}  // namespace mb

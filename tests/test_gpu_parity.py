@@ -1,0 +1,352 @@
+"""CUDA path (through the C ABI) against the FP64 oracle on identical inputs.
+
+Bar: every field within relative L2 1e-5 of the oracle after the run (the
+bound stated for the FP32 step); squared read-outs (spectra, energy) within
+2e-5; the Philox stream bit-exact.  Sizes span several thread blocks with
+ragged tails, the degenerate grids (one-cell columns, all-CPML cubes), both
+material encodings, and the full 320^3 workload on sampled sub-blocks.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle.mb_oracle import MBOracle, Params, philox4x32_10, FIELD_NAMES, C0, MU0
+from parity_util import DX, DT, REL_L2_TOL, params_kw, make_pair, rel_l2, assert_fields_match
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_0809_1547_gb300 import build
+    build.build()
+
+
+def test_philox_device_bit_exact():
+    from paper_0809_1547_gb300.binding import mb_philox4x32_10
+    rng = np.random.default_rng(0)
+    ctr = rng.integers(0, 2 ** 32, size=(4096, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[0] = 0
+    ctr[1] = 0xFFFFFFFF
+    for key in ((0, 0), (0xFFFFFFFF, 0xFFFFFFFF), (0xA4093822, 0x299F31D0), (0x5EED, 0)):
+        dev = mb_philox4x32_10(ctr, key)
+        ref = np.stack(philox4x32_10(ctr[:, 0], ctr[:, 1], ctr[:, 2], ctr[:, 3], *key), axis=1)
+        np.testing.assert_array_equal(dev, ref)
+
+
+def _spectrum_check(o, g, pid):
+    S_o, lam_o = o.probe_spectrum(pid)
+    S_g, lam_g = g.probe_spectrum(pid)
+    np.testing.assert_allclose(lam_g, lam_o, rtol=1e-15)
+    assert rel_l2(S_g, S_o) <= 2 * REL_L2_TOL
+
+
+def _energy_check(o, g):
+    U_g, fl_g = g.energy()
+    U_o = o.energy()
+    assert abs(U_g - U_o) <= 2 * REL_L2_TOL * U_o
+    scale = np.abs(o.flux).max()
+    if scale > 0:
+        assert np.abs(fl_g - o.flux).max() <= 2 * REL_L2_TOL * scale
+
+
+def test_workload_48_parity_500_steps():
+    """48^3, 8-cell CPML, 8 spheres, gain in the voids, Langevin noise, 500 steps."""
+    from paper_0809_1547_gb300 import inputs
+    w = inputs.workload_small_48()
+    pkw = params_kw(npml=w.npml)
+    o, g = make_pair(w.grid, w.eps, w.gain, w.N_a, w.pump, w.seed, pkw)
+    pid_o = o.add_point_probe(w.extra["probe"], 64, 475e-9, 705e-9)
+    pid_g = g.add_point_probe(w.extra["probe"], 64, 475e-9, 705e-9)
+    o.step(w.steps)
+    g.step(w.steps)
+    errs = assert_fields_match(o, g)
+    assert errs["Ex"] > 0            # the comparison is not vacuous
+    assert np.abs(o.field("Jx")).max() > 0 and np.abs(o.field("N2")).max() > 0
+    _spectrum_check(o, g, pid_o)
+    _energy_check(o, g)
+    g.close()
+
+
+@pytest.mark.parametrize("grid,npml,steps", [
+    ((17, 23, 31), 3, 80),       # ragged in every direction
+    ((40, 9, 13), 4, 60),
+])
+def test_ragged_grid_parity(grid, npml, steps):
+    from paper_0809_1547_gb300 import inputs
+    eps, gain = inputs.random_small(grid, seed=sum(grid), npml=npml, fill=0.35, d_cells=5)
+    pkw = params_kw(npml=npml)
+    o, g = make_pair(grid, eps, gain, 5e24, 1e13, 0xC0FFEE + sum(grid), pkw)
+    src = (grid[0] // 2, grid[1] // 2, grid[2] // 2)
+    for sim in (o, g):
+        sim.add_point_probe((grid[0] // 3, grid[1] // 2, grid[2] // 2), 24, 450e-9, 750e-9)
+        sim.add_face_probes(2, 3, 16, 480e-9, 700e-9)
+    o.add_source(src, 1, 532e-9, 1.5e-15, 0.5e-15, 1e9)
+    g.set_source(src, 1, 532e-9, 1.5e-15, 0.5e-15, 1e9)
+    o.step(steps)
+    g.step(steps)
+    assert_fields_match(o, g)
+    _spectrum_check(o, g, 0)
+    _energy_check(o, g)
+    for face in range(6):
+        S_o, _ = o.face_spectrum(face)
+        S_g, _ = g.face_spectrum(face)
+        scale = max(np.abs(S_o).max(), 1e-300)
+        assert np.abs(S_g - S_o).max() <= 4 * REL_L2_TOL * scale, face
+    g.close()
+
+
+@pytest.mark.parametrize("grid,npml", [((1, 1, 40), 0), ((1, 1, 40), 8), ((8, 8, 8), 8), ((2, 3, 1), 1)])
+def test_degenerate_grids_parity(grid, npml):
+    """One-cell columns (PEC zeroes every E), overlapping CPML slabs, a 1-cell-thick slab."""
+    shp = grid[::-1]
+    rng = np.random.default_rng(4)
+    eps = np.where(rng.random(shp) < 0.3, 8.41, 1.0).astype(np.float32)
+    gain = np.ones(shp, dtype=np.uint8)
+    pkw = params_kw(npml=npml)
+    o, g = make_pair(grid, eps, gain, 2e24, 1e13, 77, pkw)
+    rng2 = np.random.default_rng(5)
+    for name in ("Ex", "Ey", "Ez"):
+        v = (rng2.standard_normal(shp) * 1e6).astype(np.float32)
+        o.set_field(name, v.astype(np.float64))
+        g.set_field(name, v)
+    o.step(50)
+    g.step(50)
+    assert_fields_match(o, g)
+    g.close()
+
+
+def test_dense_eps_map_parity():
+    """More than 128 distinct eps values switch the device to a dense 1/eps map."""
+    grid = (20, 18, 16)
+    shp = grid[::-1]
+    rng = np.random.default_rng(8)
+    eps = rng.uniform(1.0, 8.41, size=shp).astype(np.float32)
+    gain = (rng.random(shp) < 0.5).astype(np.uint8)
+    o, g = make_pair(grid, eps, gain, 3e24, 1e13, 99, params_kw(npml=3))
+    o.step(60)
+    g.step(60)
+    assert_fields_match(o, g)
+    g.close()
+
+
+def test_cavity_eigenmode_closed_form():
+    """The exact discrete PEC-cavity mode, run on the GPU, against its closed form."""
+    from paper_0809_1547_gb300.binding import MBSimulation, mb_default_params
+    grid = (24, 20, 28)
+    modes, amp_dir, eps_r = (2, 1, 3), (0.3, -0.7, 1.1), 2.0
+    nx, ny, nz = grid
+    k = [m * math.pi / (nw * DX) for m, nw in zip(modes, grid)]
+    s = np.array([2 / DX * math.sin(kw * DX / 2) for kw in k])
+    A = np.cross(s, amp_dir)
+    A /= np.linalg.norm(A)
+    omega = 2 / DT * math.asin(DT / 2 * C0 / math.sqrt(eps_r) * np.linalg.norm(s))
+    B = -(DT / MU0) * np.cross(s, A) / (2 * math.sin(omega * DT / 2))
+    kk, jj, ii = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    S, Co = np.sin, np.cos
+
+    def fields(n):
+        te, th = math.cos(omega * n * DT), math.sin(omega * (n - 0.5) * DT)
+        xi, yi, zi = ii * DX, jj * DX, kk * DX
+        xh, yh, zh = (ii + .5) * DX, (jj + .5) * DX, (kk + .5) * DX
+        return {"Ex": A[0] * Co(k[0] * xh) * S(k[1] * yi) * S(k[2] * zi) * te,
+                "Ey": A[1] * S(k[0] * xi) * Co(k[1] * yh) * S(k[2] * zi) * te,
+                "Ez": A[2] * S(k[0] * xi) * S(k[1] * yi) * Co(k[2] * zh) * te,
+                "Hx": B[0] * S(k[0] * xi) * Co(k[1] * yh) * Co(k[2] * zh) * th,
+                "Hy": B[1] * Co(k[0] * xh) * S(k[1] * yi) * Co(k[2] * zh) * th,
+                "Hz": B[2] * Co(k[0] * xh) * Co(k[1] * yh) * S(k[2] * zi) * th}
+
+    g = MBSimulation(grid, DX, DT, mb_default_params(npml=0))
+    g.set_material(np.full(grid[::-1], eps_r, np.float32), np.zeros(grid[::-1], np.uint8), 0.0, 0.0)
+    for name, v in fields(0).items():
+        g.set_field(name, v)
+    n = 300
+    g.step(n)
+    for name, v in fields(n).items():
+        assert rel_l2(g.field(name), v) < 1e-4, name
+    g.close()
+
+
+def test_graph_chunks_equal_single_steps_bitwise():
+    from paper_0809_1547_gb300 import inputs
+    grid = (24, 20, 18)
+    eps, gain = inputs.random_small(grid, seed=2, npml=4)
+    pkw = params_kw(npml=4)
+    _, a = make_pair(grid, eps, gain, 4e24, 1e13, 5, pkw)
+    _, b = make_pair(grid, eps, gain, 4e24, 1e13, 5, pkw)
+    a.step(37)
+    for _ in range(37):
+        b.step(1)
+    for name in FIELD_NAMES:
+        np.testing.assert_array_equal(a.field(name), b.field(name))
+    a.close()
+    b.close()
+
+
+def test_save_load_state_roundtrip_bitwise():
+    from paper_0809_1547_gb300 import inputs
+    grid = (22, 21, 20)
+    eps, gain = inputs.random_small(grid, seed=3, npml=4)
+    _, g = make_pair(grid, eps, gain, 4e24, 1e13, 6, params_kw(npml=4))
+    g.add_point_probe((10, 10, 10), 8, 500e-9, 650e-9)
+    g.step(10)
+    blob = g.save_state()
+    g.step(15)
+    ref = {name: g.field(name) for name in FIELD_NAMES}
+    S_ref, _ = g.probe_spectrum(0)
+    g.load_state(blob)
+    assert g.n == 10
+    g.step(15)
+    for name in FIELD_NAMES:
+        np.testing.assert_array_equal(g.field(name), ref[name])
+    np.testing.assert_array_equal(g.probe_spectrum(0)[0], S_ref)
+    g.close()
+
+
+def test_autotune_keeps_state_and_results():
+    from paper_0809_1547_gb300 import inputs
+    grid = (40, 36, 30)
+    eps, gain = inputs.random_small(grid, seed=4, npml=6)
+    pkw = params_kw(npml=6)
+    _, a = make_pair(grid, eps, gain, 4e24, 1e13, 8, pkw)
+    _, b = make_pair(grid, eps, gain, 4e24, 1e13, 8, pkw)
+    a.step(5)
+    b.step(5)
+    before = {name: a.field(name) for name in FIELD_NAMES}
+    a.autotune()
+    for name in FIELD_NAMES:
+        np.testing.assert_array_equal(a.field(name), before[name])
+    a.step(20)
+    b.step(20)
+    for name in FIELD_NAMES:
+        np.testing.assert_array_equal(a.field(name), b.field(name))
+    a.close()
+    b.close()
+
+
+def test_gpu_energy_balance_of_interior_box():
+    """Lossless interior, source off: box energy change = -(outward flux), on the GPU."""
+    from paper_0809_1547_gb300.binding import MBSimulation, mb_default_params
+    from oracle.mb_oracle import EPS0
+    grid = (30, 28, 32)
+    shp = grid[::-1]
+    eps = np.ones(shp, np.float32)
+    eps[14:18, 13:17, 15:19] = 4.0
+    g = MBSimulation(grid, DX, DT, mb_default_params(npml=8))
+    g.set_material(eps, np.zeros(shp, np.uint8), 0.0, 0.0)
+    g.set_source((15, 14, 16), 0, 400e-9, 1.2e-15, 0.4e-15, 1e9)
+    g.step(45)
+    g.set_source((15, 14, 16), 0, 400e-9, 1.2e-15, 0.4e-15, 0.0)
+
+    def box_energy():
+        L = 8
+        sl = (slice(L, grid[2] - L), slice(L, grid[1] - L), slice(L, grid[0] - L))
+        E = [g.field(n).astype(np.float64) for n in ("Ex", "Ey", "Ez")]
+        Hm = [g.field(n).astype(np.float64) for n in ("Hx", "Hy", "Hz")]
+        _, fl = g.energy()
+        g.step(1)
+        Hp = [g.field(n).astype(np.float64) for n in ("Hx", "Hy", "Hz")]
+        uE = sum(np.sum((eps * F * F)[sl]) for F in E) * EPS0
+        uH = sum(np.sum((a * b)[sl]) for a, b in zip(Hm, Hp)) * MU0
+        return 0.5 * (uE + uH) * DX ** 3, fl
+
+    W1, F1 = box_energy()
+    g.step(60)
+    W2, F2 = box_energy()
+    out = float(np.sum(F2 - F1))
+    assert out > 0.2 * W1
+    assert abs((W1 - W2) - out) < 1e-4 * W1
+    g.close()
+
+
+def test_nonfinite_fields_are_reported():
+    from paper_0809_1547_gb300.binding import MBSimulation, mb_default_params, MBError, MB_ERR_NONFINITE
+    grid = (8, 8, 8)
+    g = MBSimulation(grid, DX, DT, mb_default_params(npml=2))
+    v = np.zeros(grid[::-1], np.float32)
+    v[3, 3, 3] = np.nan
+    g.set_field("Hy", v)
+    with pytest.raises(MBError) as e:
+        g.energy()
+    assert e.value.code == MB_ERR_NONFINITE
+    g.close()
+
+
+def test_argument_errors():
+    from paper_0809_1547_gb300.binding import MBSimulation, mb_default_params, MBError, MB_ERR_ARG, \
+        MB_ERR_MATERIALS
+    grid = (8, 8, 8)
+    g = MBSimulation(grid, DX, DT, mb_default_params(npml=2))
+    with pytest.raises(MBError) as e:
+        g.add_point_probe((8, 0, 0), 4, 500e-9, 600e-9)
+    assert e.value.code == MB_ERR_ARG
+    with pytest.raises(MBError) as e:
+        g.set_material(np.full(grid[::-1], 0.5, np.float32), np.zeros(grid[::-1], np.uint8), 1e24, 0)
+    assert e.value.code == MB_ERR_MATERIALS
+    with pytest.raises(MBError):
+        g.set_field("N0", np.zeros(grid[::-1], np.float32))
+    g.close()
+
+
+def _global_state_block(g, lo, size):
+    """Every field of the sub-block [lo, lo + size) (SI, [k, j, i]) read on the device."""
+    i0, j0, k0 = lo
+    out = {}
+    for name in FIELD_NAMES:
+        if name == "N0":
+            continue
+        t, scale = g.field_device(name)
+        out[name] = t[k0:k0 + size, j0:j0 + size, i0:i0 + size].double().cpu().numpy() * scale
+    return out
+
+
+def test_full_size_320_sampled_parity():
+    """The 320^3 workload in the launch configuration the benchmark times:
+    after 24 steps, one more GPU step is checked on sampled interior
+    sub-blocks against the oracle's step of the same sub-block (with a
+    one-cell halo; noise counters and step index taken from the full grid)."""
+    import torch
+    from paper_0809_1547_gb300 import inputs
+    from paper_0809_1547_gb300.workloads import setup_simulation
+    w = inputs.workload_paper_320()
+    g = setup_simulation(w, autotune=True)
+    g.step(24)
+    g.synchronize()
+    B = 20
+    rng = np.random.default_rng(12)
+    los = [tuple(int(v) for v in rng.integers(9, 320 - 9 - B - 2, size=3)) for _ in range(3)]
+    los.append((150, 150, 150))
+    before = [_global_state_block(g, lo, B + 2) for lo in los]
+    n_before = g.n
+    g.step(1)
+    g.synchronize()
+    after = [_global_state_block(g, lo, B + 2) for lo in los]
+    pkw = params_kw(npml=0)
+    for lo, st0, st1 in zip(los, before, after):
+        i0, j0, k0 = lo
+        sl = (slice(k0, k0 + B + 2), slice(j0, j0 + B + 2), slice(i0, i0 + B + 2))
+        o = MBOracle((B + 2,) * 3, w.dx, w.dt, Params(**pkw))
+        o.set_material(w.eps[sl], w.gain[sl], w.N_a, w.pump)
+        o.set_seed(w.seed)
+        kk, jj, ii = np.meshgrid(np.arange(k0, k0 + B + 2), np.arange(j0, j0 + B + 2),
+                                 np.arange(i0, i0 + B + 2), indexing="ij")
+        o.cell_index = (ii + 320 * (jj + 320 * kk)).astype(np.uint64)
+        o.n = n_before
+        for name, v in st0.items():
+            o.set_field(name, v)
+        gain = w.gain[sl] != 0
+        o.N[0] = np.where(gain, w.N_a - st0["N1"] - st0["N2"] - st0["N3"], 0.0)
+        o.step(1)
+        core = (slice(1, B + 1),) * 3
+        for name, v in st1.items():
+            ref = o.field(name)[core]
+            err = rel_l2(v[core], ref)
+            assert err <= REL_L2_TOL or np.abs(ref).max() == 0 == np.abs(v[core]).max(), (lo, name, err)
+    # properties that hold at any size
+    U, fl = g.energy()
+    assert math.isfinite(U) and np.all(np.isfinite(fl))
+    t, _ = g.field_device("Jx")
+    nongain = torch.from_numpy(w.gain == 0).cuda()
+    assert float(t[nongain].abs().max()) == 0.0
+    g.close()
