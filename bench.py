@@ -201,10 +201,10 @@ def max_over_ranks(x: float, world: int, device=None) -> float:
     return float(t.item())
 
 
-def rank_workload(rank: int):
+def rank_workload(rank: int, n: int = 320):
     """Rank r runs its own realization: disorder seed 7 + r, noise seed + r."""
     from paper_0809_1547_gb300 import inputs
-    w = inputs.workload_paper_320(seed=7 + rank)
+    w = inputs.workload_paper(n, seed=7 + rank)
     w.seed = w.seed + rank
     return w
 
@@ -259,10 +259,11 @@ def bench_ours(args):
     barrier(world)
     from paper_0809_1547_gb300.binding import MBSimulation, mb_default_params
     from paper_0809_1547_gb300.workloads import setup_simulation
-    w = rank_workload(rank)
+    w = rank_workload(rank, args.grid)
     stream = torch.cuda.Stream()
     sim = setup_simulation(w, autotune=True, stream=stream.cuda_stream)
     per_step_launches, _ = sim.launch_stats()
+    blk_h, blk_e = sim.tuning()
     sim.step(args.warmup)
     sim.synchronize()
     torch.cuda.synchronize()
@@ -341,14 +342,15 @@ def bench_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(elapsed_ms / args.steps, 5),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": "mb320_active: 320^3 Yee grid (dx 20 nm, Courant 0.99, 8-cell CPML), "
+        "config": {"workload": f"{w.name}: {w.grid[0]}^3 Yee grid (dx 20 nm, Courant 0.99, 8-cell CPML), "
                                f"{w.n_spheres} TiO2 spheres d~N(300 nm,10%) at {w.fill:.3f} fill, gain in "
                                "the voids, N_a 5e24 m^-3, W_p 1e13/s, Langevin noise, centre point probe "
                                "+ 6 face probes (stride 8, every 4, 128 bins)",
                    "grid": list(w.grid), "cells": cells, "gain_fraction": round(ab["gain_fraction"], 4),
-                   "l2": "inputs larger than L2 (state 2.0 GB per realization)",
+                   "l2": f"inputs larger than L2 (state {61 * cells / 1e9:.2f} GB per realization)",
                    "parallelism": f"replicas x{world} (one realization per GPU)",
                    "timed_path": "direct launches with CUDA events around each pass",
+                   "blocks": {"h_pass": list(blk_h), "e_pass": list(blk_e)},
                    "graph_replay_ms_per_step": round(graph_ms_per_step, 5)},
         "roofline": {"bound": "hbm", "kernel": "k_e_pass (fused E/gain/noise/population pass)",
                      "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
@@ -366,7 +368,7 @@ def bench_ours(args):
         "clocks": clocks,
         "energy_J": U,
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.grid == 320:
         try:
             rate, el, ncell = run_oracle_child(16, 6)
             out["cpu_baseline"] = {"value": round(rate, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -423,6 +425,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--grid", type=int, default=320,
+                    help="cube side of the workload (320: the paper-scale sample; smaller sides "
+                         "only for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -194,6 +194,13 @@ int mb_load_state(mb_ctx* ctx, const void* host_blob, size_t bytes);
  * fastest.  The choice is cached per grid shape for the process. */
 int mb_autotune(mb_ctx* ctx);
 
+/* Launch shape of the H pass and of the E pass, as {variant, bx, by, bz}:
+ * variant 0 = one thread per cell in (bx, by, bz) blocks; variant 1 = 2-D
+ * (bx, by) blocks whose threads each walk bz planes along z.  Read the
+ * current choice or set one (bx a multiple of 32, at most 512 threads). */
+int mb_get_tuning(mb_ctx* ctx, int tune_h[4], int tune_e[4]);
+int mb_set_tuning(mb_ctx* ctx, const int tune_h[4], const int tune_e[4]);
+
 /* Kernel launches queued per step by mb_step, and in total so far. */
 int mb_launch_stats(mb_ctx* ctx, int* per_step, int64_t* total);
 

@@ -77,6 +77,8 @@ _SIGS = [
     ("mb_save_state", C.c_int, [_P, _P, C.POINTER(C.c_size_t)]),
     ("mb_load_state", C.c_int, [_P, _P, C.c_size_t]),
     ("mb_autotune", C.c_int, [_P]),
+    ("mb_get_tuning", C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    ("mb_set_tuning", C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     ("mb_launch_stats", C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int64)]),
     ("mb_device_bytes", C.c_int, [_P, C.POINTER(C.c_size_t)]),
     ("mb_philox4x32_10", C.c_int, [_P, _P, _P, C.c_int]),
@@ -258,6 +260,18 @@ def mb_autotune(h):
     _check(load_library().mb_autotune(h), h)
 
 
+def mb_get_tuning(h):
+    """((variant, bx, by, bz), (variant, bx, by, bz)) of the H and E passes."""
+    bh = (C.c_int * 4)()
+    be = (C.c_int * 4)()
+    _check(load_library().mb_get_tuning(h, bh, be), h)
+    return tuple(bh), tuple(be)
+
+
+def mb_set_tuning(h, tune_h, tune_e):
+    _check(load_library().mb_set_tuning(h, (C.c_int * 4)(*tune_h), (C.c_int * 4)(*tune_e)), h)
+
+
 def mb_launch_stats(h):
     per = C.c_int()
     tot = C.c_int64()
@@ -392,6 +406,12 @@ class MBSimulation:
 
     def launch_stats(self):
         return mb_launch_stats(self._h)
+
+    def tuning(self):
+        return mb_get_tuning(self._h)
+
+    def set_tuning(self, tune_h, tune_e):
+        mb_set_tuning(self._h, tune_h, tune_e)
 
     def device_bytes(self):
         return mb_device_bytes(self._h)

@@ -104,7 +104,7 @@ double field_scale(const mb_ctx* c, int which) {
 
 void build_args(mb_ctx* c) {
     mb::StepArgs& a = c->args;
-    a.g = {c->nx, c->ny, c->nz, (int64_t)c->nx * c->ny, c->ncell};
+    a.g = {c->nx, c->ny, c->nz, (uint32_t)c->nx * (uint32_t)c->ny, (uint32_t)c->ncell};
     float* F = c->d_fields;
     const int64_t N = c->ncell;
     a.f.ex = F + 0 * N; a.f.ey = F + 1 * N; a.f.ez = F + 2 * N;
@@ -216,7 +216,7 @@ std::vector<StatePart> state_parts(mb_ctx* c) {
     for (int w = 0; w < 3; ++w)
         if (c->psi_elems[w]) v.push_back({c->d_psi[w], sizeof(float) * c->psi_elems[w]});
     v.push_back({c->d_ctr, sizeof(long long) * 2});
-    v.push_back({c->d_flux, sizeof(double) * 6});
+    v.push_back({c->d_flux, sizeof(double) * 6 * mb::kFluxSlots});
     if (!c->probes.empty())
         v.push_back({c->d_probe_acc, sizeof(double2) * 3 * c->probes.size() * c->probe_nfreq});
     if (c->face.on && c->face_points)
@@ -230,8 +230,8 @@ int capture_steps(mb_ctx* c, int steps, cudaGraphExec_t* out) {
     mb::DevPointProbes pp{(int)c->probes.size(), c->probe_nfreq, c->d_probe_cell,
                           c->d_probe_omega, c->d_probe_acc};
     for (int s = 0; s < steps; ++s) {
-        mb::launch_h_pass(c->args, c->blk_h, c->stream);
-        mb::launch_e_pass(c->args, c->blk_e, c->stream);
+        mb::launch_h_pass(c->args, c->tune_h, c->stream);
+        mb::launch_e_pass(c->args, c->tune_e, c->stream);
         mb::launch_point_dft(pp, c->args.f, c->d_ctr, c->dt, c->stream);
         mb::launch_face_dft(c->face, c->args.f, c->args.g, c->d_ctr, c->dt, c->stream);
     }
@@ -241,6 +241,14 @@ int capture_steps(mb_ctx* c, int steps, cudaGraphExec_t* out) {
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return fail(c, MB_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
     return MB_OK;
+}
+
+void sum_flux_slots(const double* slots, double fl[6]) {
+    for (int q = 0; q < 6; ++q) {
+        double v = 0.0;
+        for (int t = 0; t < mb::kFluxSlots; ++t) v += slots[q * mb::kFluxSlots + t];
+        fl[q] = v;
+    }
 }
 
 int launches_per_step(const mb_ctx* c) {
@@ -255,7 +263,7 @@ void drop_graphs(mb_ctx* c) {
 }
 
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, int>, std::pair<dim3, dim3>> g_tune_cache;
+std::map<std::tuple<int, int, int, int>, std::pair<mb::PassTune, mb::PassTune>> g_tune_cache;
 
 }  // namespace
 
@@ -346,7 +354,7 @@ int mb_create(mb_ctx** out, const int grid[3], double dx, double dt, const mb_pa
     const size_t ncoef = 4 * (size_t)(c->nx + c->ny + c->nz);
     if ((rc = alloc((void**)&c->d_coef, sizeof(float) * ncoef))) return bail(rc);
     if ((rc = alloc((void**)&c->d_ctr, sizeof(long long) * 2))) return bail(rc);
-    if ((rc = alloc((void**)&c->d_flux, sizeof(double) * 6))) return bail(rc);
+    if ((rc = alloc((void**)&c->d_flux, sizeof(double) * 6 * mb::kFluxSlots))) return bail(rc);
     c->n_partial = 1024;
     if ((rc = alloc((void**)&c->d_partial, sizeof(double) * c->n_partial))) return bail(rc);
     if ((rc = alloc((void**)&c->d_energy, sizeof(double)))) return bail(rc);
@@ -375,7 +383,7 @@ int mb_create(mb_ctx** out, const int grid[3], double dx, double dt, const mb_pa
     for (int w = 0; w < 3; ++w)
         if (c->psi_elems[w]) MB_CREATE_CUDA(cudaMemset(c->d_psi[w], 0, sizeof(float) * c->psi_elems[w]));
     MB_CREATE_CUDA(cudaMemset(c->d_ctr, 0, sizeof(long long) * 2));
-    MB_CREATE_CUDA(cudaMemset(c->d_flux, 0, sizeof(double) * 6));
+    MB_CREATE_CUDA(cudaMemset(c->d_flux, 0, sizeof(double) * 6 * mb::kFluxSlots));
 #undef MB_CREATE_CUDA
     c->h_gain.assign((size_t)ncell, 0);
     c->face.on = 0;
@@ -385,8 +393,8 @@ int mb_create(mb_ctx** out, const int grid[3], double dx, double dt, const mb_pa
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find({c->nx, c->ny, c->nz, L});
         if (it != g_tune_cache.end()) {
-            c->blk_h = it->second.first;
-            c->blk_e = it->second.second;
+            c->tune_h = it->second.first;
+            c->tune_e = it->second.second;
         }
     }
     *out = c;
@@ -656,9 +664,9 @@ int mb_step_timed(mb_ctx* c, int n, double* ms_out) {
     for (int s = 0; s < n; ++s) {
         cudaEvent_t* e = &ev[(size_t)5 * s];
         cudaEventRecord(e[0], c->stream);
-        mb::launch_h_pass(c->args, c->blk_h, c->stream);
+        mb::launch_h_pass(c->args, c->tune_h, c->stream);
         cudaEventRecord(e[1], c->stream);
-        mb::launch_e_pass(c->args, c->blk_e, c->stream);
+        mb::launch_e_pass(c->args, c->tune_e, c->stream);
         cudaEventRecord(e[2], c->stream);
         mb::launch_point_dft(pp, c->args.f, c->d_ctr, c->dt, c->stream);
         cudaEventRecord(e[3], c->stream);
@@ -689,9 +697,10 @@ int mb_step_timed(mb_ctx* c, int n, double* ms_out) {
 int mb_flux(mb_ctx* c, double* out_flux6) {
     if (int rc = check_ctx(c)) return rc;
     if (!out_flux6) return fail(c, MB_ERR_ARG, "null output");
-    double fl[6];
-    MB_CUDA(c, cudaMemcpyAsync(fl, c->d_flux, sizeof(double) * 6, cudaMemcpyDeviceToHost, c->stream));
+    double slots[6 * mb::kFluxSlots], fl[6];
+    MB_CUDA(c, cudaMemcpyAsync(slots, c->d_flux, sizeof(slots), cudaMemcpyDeviceToHost, c->stream));
     MB_CUDA(c, cudaStreamSynchronize(c->stream));
+    sum_flux_slots(slots, fl);
     const double f = c->dt * c->E0 * (c->E0 / c->eta0) * c->dx * c->dx;
     for (int q = 0; q < 6; ++q) out_flux6[q] = fl[q] * f;
     return MB_OK;
@@ -768,12 +777,13 @@ int mb_energy(mb_ctx* c, double* out_U, double* out_flux6) {
     mb::launch_energy(c->args.f, c->ncell, c->d_lut + 128, c->d_partial, c->n_partial,
                       c->d_nonfinite, c->d_energy, c->stream);
     MB_CUDA(c, cudaGetLastError());
-    double U = 0, fl[6];
+    double U = 0, slots[6 * mb::kFluxSlots], fl[6];
     int bad = 0;
     MB_CUDA(c, cudaMemcpyAsync(&U, c->d_energy, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    MB_CUDA(c, cudaMemcpyAsync(fl, c->d_flux, sizeof(double) * 6, cudaMemcpyDeviceToHost, c->stream));
+    MB_CUDA(c, cudaMemcpyAsync(slots, c->d_flux, sizeof(slots), cudaMemcpyDeviceToHost, c->stream));
     MB_CUDA(c, cudaMemcpyAsync(&bad, c->d_nonfinite, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     MB_CUDA(c, cudaStreamSynchronize(c->stream));
+    sum_flux_slots(slots, fl);
     *out_U = 0.5 * kEps0 * c->E0 * c->E0 * c->dx * c->dx * c->dx * U;
     if (out_flux6) {
         const double f = c->dt * c->E0 * (c->E0 / c->eta0) * c->dx * c->dx;
@@ -887,33 +897,35 @@ int mb_autotune(mb_ctx* c) {
             o += p.bytes;
         }
     }
-    const dim3 cands[] = {dim3(32, 4, 2), dim3(32, 8, 1), dim3(64, 4, 1), dim3(32, 2, 4),
-                          dim3(64, 2, 2), dim3(128, 2, 1), dim3(32, 4, 4), dim3(32, 16, 1),
-                          dim3(64, 8, 1), dim3(128, 4, 1), dim3(256, 1, 1), dim3(32, 8, 2),
-                          dim3(128, 1, 2), dim3(64, 4, 2)};
+    std::vector<mb::PassTune> cands;
+    for (dim3 b : {dim3(32, 4, 2), dim3(32, 8, 1), dim3(64, 4, 1), dim3(32, 2, 4), dim3(128, 2, 1),
+                   dim3(32, 4, 4), dim3(64, 2, 2)})
+        cands.push_back({mb::kVariant3D, b, 1});
+    for (dim3 b : {dim3(32, 4, 1), dim3(32, 8, 1), dim3(64, 4, 1), dim3(64, 2, 1), dim3(128, 2, 1),
+                   dim3(32, 16, 1), dim3(64, 8, 1), dim3(128, 4, 1), dim3(256, 1, 1)})
+        for (int kz : {4, 8, 16, 32}) cands.push_back({mb::kVariantZmarch, b, kz});
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best_h = 1e30f, best_e = 1e30f;
-    dim3 bh = c->blk_h, be = c->blk_e;
-    const int reps = c->ncell > 4000000 ? 3 : 10;
-    for (const dim3& b : cands) {
+    mb::PassTune bh = c->tune_h, be = c->tune_e;
+    const int reps = c->ncell > 4000000 ? 2 : 6;
+    for (const mb::PassTune& t : cands) {
+        if (t.variant == mb::kVariantZmarch && t.kz > 2 * c->nz) continue;
         for (int pass = 0; pass < 2; ++pass) {
-            for (int warm = 0; warm < 1; ++warm) {
-                if (pass == 0) mb::launch_h_pass(c->args, b, c->stream);
-                else mb::launch_e_pass(c->args, b, c->stream);
-            }
+            if (pass == 0) mb::launch_h_pass(c->args, t, c->stream);
+            else mb::launch_e_pass(c->args, t, c->stream);
             cudaEventRecord(e0, c->stream);
             for (int r = 0; r < reps; ++r) {
-                if (pass == 0) mb::launch_h_pass(c->args, b, c->stream);
-                else mb::launch_e_pass(c->args, b, c->stream);
+                if (pass == 0) mb::launch_h_pass(c->args, t, c->stream);
+                else mb::launch_e_pass(c->args, t, c->stream);
             }
             cudaEventRecord(e1, c->stream);
             cudaEventSynchronize(e1);
             float ms = 0;
             cudaEventElapsedTime(&ms, e0, e1);
-            if (pass == 0 && ms < best_h) { best_h = ms; bh = b; }
-            if (pass == 1 && ms < best_e) { best_e = ms; be = b; }
+            if (pass == 0 && ms < best_h) { best_h = ms; bh = t; }
+            if (pass == 1 && ms < best_e) { best_e = ms; be = t; }
         }
     }
     cudaEventDestroy(e0);
@@ -928,12 +940,48 @@ int mb_autotune(mb_ctx* c) {
     cudaStreamSynchronize(c->stream);
     cudaFree(backup);
     MB_CUDA(c, cudaGetLastError());
-    c->blk_h = bh;
-    c->blk_e = be;
+    c->tune_h = bh;
+    c->tune_e = be;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tune_cache[{c->nx, c->ny, c->nz, c->p.npml}] = {bh, be};
     }
+    drop_graphs(c);
+    return MB_OK;
+}
+
+int mb_get_tuning(mb_ctx* c, int tune_h[4], int tune_e[4]) {
+    if (int rc = check_ctx(c)) return rc;
+    if (!tune_h || !tune_e) return fail(c, MB_ERR_ARG, "null output");
+    const mb::PassTune* src[2] = {&c->tune_h, &c->tune_e};
+    int* dst[2] = {tune_h, tune_e};
+    for (int q = 0; q < 2; ++q) {
+        dst[q][0] = src[q]->variant;
+        dst[q][1] = src[q]->block.x;
+        dst[q][2] = src[q]->block.y;
+        dst[q][3] = src[q]->variant == mb::kVariantZmarch ? src[q]->kz : src[q]->block.z;
+    }
+    return MB_OK;
+}
+
+int mb_set_tuning(mb_ctx* c, const int tune_h[4], const int tune_e[4]) {
+    if (int rc = check_ctx(c)) return rc;
+    if (!tune_h || !tune_e) return fail(c, MB_ERR_ARG, "null input");
+    mb::PassTune t[2];
+    const int* src[2] = {tune_h, tune_e};
+    for (int q = 0; q < 2; ++q) {
+        const int* b = src[q];
+        if ((b[0] != mb::kVariant3D && b[0] != mb::kVariantZmarch) || b[1] < 32 || b[1] % 32 ||
+            b[2] < 1 || b[3] < 1)
+            return fail(c, MB_ERR_ARG, "bad tuning: variant 0/1, x a multiple of 32, y, z >= 1");
+        const int threads = b[1] * b[2] * (b[0] == mb::kVariant3D ? b[3] : 1);
+        if (threads > 512) return fail(c, MB_ERR_ARG, "at most 512 threads per block");
+        t[q].variant = b[0];
+        t[q].block = dim3(b[1], b[2], b[0] == mb::kVariant3D ? b[3] : 1);
+        t[q].kz = b[0] == mb::kVariantZmarch ? b[3] : 1;
+    }
+    c->tune_h = t[0];
+    c->tune_e = t[1];
     drop_graphs(c);
     return MB_OK;
 }

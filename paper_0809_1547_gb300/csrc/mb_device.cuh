@@ -18,10 +18,15 @@
 
 namespace mb {
 
+// Cell offsets are 32-bit: a realization holds fewer than 2^32 cells.
 struct DevGrid {
     int nx, ny, nz;
-    int64_t nxy, ncell;
+    uint32_t nxy, ncell;
 };
+
+// The face flux is accumulated into kFluxSlots FP64 slots per face (spread
+// over L2 to avoid serialising the atomics); read-outs sum the slots.
+constexpr int kFluxSlots = 64;
 
 struct DevFields {
     float *ex, *ey, *ez, *hx, *hy, *hz;
@@ -69,7 +74,7 @@ struct DevFlux {
     int on;
     int plo[3], phi[3];
     int r0[3], r1[3];
-    double* acc;   // 6 values: x-, x+, y-, y+, z-, z+
+    double* acc;   // [6][kFluxSlots]: faces x-, x+, y-, y+, z-, z+
 };
 
 struct StepArgs {
@@ -129,23 +134,65 @@ __device__ __forceinline__ int slab_index(int i, int n, int L) {
     return (i < L) ? i : i - n + 2 * L;
 }
 
-// ------------------------------------------------------------- H half-step
-// H^{n+1/2} = H^{n-1/2} - S (curl_fwd E^n + psi_H); E beyond the last cell is 0.
-__device__ __forceinline__ void h_update_cell(const StepArgs& a, int i, int j, int k) {
-    const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
-    const int64_t nxy = a.g.nxy;
-    const int64_t c = i + (int64_t)nx * j + nxy * k;
+// E values the H update of one cell reads: its own three components and the
+// +x / +y / +z neighbours that enter the forward differences.
+struct ENb {
+    float ex, ey, ez, ex_j1, ex_k1, ey_i1, ey_k1, ez_i1, ez_j1;
+};
+
+// H values the E update of one cell reads: its own three components and the
+// -x / -y / -z neighbours that enter the backward differences.
+struct HNb {
+    float hx, hy, hz, hx_j, hx_k, hy_i, hy_k, hz_i, hz_j;
+};
+
+// Neighbours from global memory (E is read-only during the H pass); fields
+// beyond the last cell are zero.
+__device__ __forceinline__ ENb load_e_nbrs(const StepArgs& a, int i, int j, int k, uint32_t c) {
     const DevFields& f = a.f;
-    const float ex = f.ex[c], ey = f.ey[c], ez = f.ez[c];
-    const float ex_j1 = (j + 1 < ny) ? f.ex[c + nx] : 0.0f;
-    const float ex_k1 = (k + 1 < nz) ? f.ex[c + nxy] : 0.0f;
-    const float ey_i1 = (i + 1 < nx) ? f.ey[c + 1] : 0.0f;
-    const float ey_k1 = (k + 1 < nz) ? f.ey[c + nxy] : 0.0f;
-    const float ez_i1 = (i + 1 < nx) ? f.ez[c + 1] : 0.0f;
-    const float ez_j1 = (j + 1 < ny) ? f.ez[c + nx] : 0.0f;
-    const float dEz_dy = ez_j1 - ez, dEy_dz = ey_k1 - ey;
-    const float dEx_dz = ex_k1 - ex, dEz_dx = ez_i1 - ez;
-    const float dEy_dx = ey_i1 - ey, dEx_dy = ex_j1 - ex;
+    const int nx = a.g.nx;
+    const uint32_t nxy = a.g.nxy;
+    ENb e;
+    e.ex = __ldg(f.ex + c);
+    e.ey = __ldg(f.ey + c);
+    e.ez = __ldg(f.ez + c);
+    const bool xi = i + 1 < nx, yj = j + 1 < a.g.ny, zk = k + 1 < a.g.nz;
+    e.ex_j1 = yj ? __ldg(f.ex + c + nx) : 0.0f;
+    e.ex_k1 = zk ? __ldg(f.ex + c + nxy) : 0.0f;
+    e.ey_i1 = xi ? __ldg(f.ey + c + 1) : 0.0f;
+    e.ey_k1 = zk ? __ldg(f.ey + c + nxy) : 0.0f;
+    e.ez_i1 = xi ? __ldg(f.ez + c + 1) : 0.0f;
+    e.ez_j1 = yj ? __ldg(f.ez + c + nx) : 0.0f;
+    return e;
+}
+
+// H is read-only during the E pass; fields before the first cell are zero.
+__device__ __forceinline__ HNb load_h_nbrs(const StepArgs& a, int i, int j, int k, uint32_t c) {
+    const DevFields& f = a.f;
+    const int nx = a.g.nx;
+    const uint32_t nxy = a.g.nxy;
+    HNb h;
+    h.hx = __ldg(f.hx + c);
+    h.hy = __ldg(f.hy + c);
+    h.hz = __ldg(f.hz + c);
+    h.hx_j = (j > 0) ? __ldg(f.hx + c - nx) : 0.0f;
+    h.hx_k = (k > 0) ? __ldg(f.hx + c - nxy) : 0.0f;
+    h.hy_i = (i > 0) ? __ldg(f.hy + c - 1) : 0.0f;
+    h.hy_k = (k > 0) ? __ldg(f.hy + c - nxy) : 0.0f;
+    h.hz_i = (i > 0) ? __ldg(f.hz + c - 1) : 0.0f;
+    h.hz_j = (j > 0) ? __ldg(f.hz + c - nx) : 0.0f;
+    return h;
+}
+
+// ------------------------------------------------------------- H half-step
+// H^{n+1/2} = H^{n-1/2} - S (curl_fwd E^n + psi_H) for cell c = (i, j, k).
+__device__ __forceinline__ void h_core(const StepArgs& a, int i, int j, int k, uint32_t c,
+                                       const ENb& e) {
+    const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
+    const DevFields& f = a.f;
+    const float dEz_dy = e.ez_j1 - e.ez, dEy_dz = e.ey_k1 - e.ey;
+    const float dEx_dz = e.ex_k1 - e.ex, dEz_dx = e.ez_i1 - e.ez;
+    const float dEy_dx = e.ey_i1 - e.ey, dEx_dy = e.ex_j1 - e.ex;
     float cx = dEz_dy - dEy_dz;
     float cy = dEx_dz - dEz_dx;
     float cz = dEy_dx - dEx_dy;
@@ -153,10 +200,10 @@ __device__ __forceinline__ void h_update_cell(const StepArgs& a, int i, int j, i
     if (L > 0) {
         const int L2 = 2 * L;
         if (i < L || i >= nx - L) {
-            const int s = slab_index(i, nx, L);
-            const int64_t plane = (int64_t)nz * ny * L2;
-            const int64_t q = ((int64_t)k * ny + j) * L2 + s;
-            const float b = a.pml.bhx[i], cc = a.pml.chx[i];
+            const uint32_t s = slab_index(i, nx, L);
+            const uint32_t plane = (uint32_t)nz * ny * L2;
+            const uint32_t q = ((uint32_t)k * ny + j) * L2 + s;
+            const float b = __ldg(a.pml.bhx + i), cc = __ldg(a.pml.chx + i);
             float* p = a.pml.psx;
             const float psi_yx = b * p[q + 2 * plane] + cc * dEz_dx;   // Hy: d/dx Ez
             const float psi_zx = b * p[q + 3 * plane] + cc * dEy_dx;   // Hz: d/dx Ey
@@ -166,10 +213,10 @@ __device__ __forceinline__ void h_update_cell(const StepArgs& a, int i, int j, i
             cz += psi_zx;
         }
         if (j < L || j >= ny - L) {
-            const int s = slab_index(j, ny, L);
-            const int64_t plane = (int64_t)nz * L2 * nx;
-            const int64_t q = ((int64_t)k * L2 + s) * nx + i;
-            const float b = a.pml.bhy[j], cc = a.pml.chy[j];
+            const uint32_t s = slab_index(j, ny, L);
+            const uint32_t plane = (uint32_t)nz * L2 * nx;
+            const uint32_t q = ((uint32_t)k * L2 + s) * nx + i;
+            const float b = __ldg(a.pml.bhy + j), cc = __ldg(a.pml.chy + j);
             float* p = a.pml.psy;
             const float psi_xy = b * p[q + 2 * plane] + cc * dEz_dy;   // Hx: d/dy Ez
             const float psi_zy = b * p[q + 3 * plane] + cc * dEx_dy;   // Hz: d/dy Ex
@@ -179,10 +226,10 @@ __device__ __forceinline__ void h_update_cell(const StepArgs& a, int i, int j, i
             cz -= psi_zy;
         }
         if (k < L || k >= nz - L) {
-            const int s = slab_index(k, nz, L);
-            const int64_t plane = (int64_t)L2 * ny * nx;
-            const int64_t q = ((int64_t)s * ny + j) * nx + i;
-            const float b = a.pml.bhz[k], cc = a.pml.chz[k];
+            const uint32_t s = slab_index(k, nz, L);
+            const uint32_t plane = (uint32_t)L2 * ny * nx;
+            const uint32_t q = (s * ny + j) * nx + i;
+            const float b = __ldg(a.pml.bhz + k), cc = __ldg(a.pml.chz + k);
             float* p = a.pml.psz;
             const float psi_xz = b * p[q + 2 * plane] + cc * dEy_dz;   // Hx: d/dz Ey
             const float psi_yz = b * p[q + 3 * plane] + cc * dEx_dz;   // Hy: d/dz Ex
@@ -198,6 +245,11 @@ __device__ __forceinline__ void h_update_cell(const StepArgs& a, int i, int j, i
     f.hz[c] = f.hz[c] - S * cz;
 }
 
+__device__ __forceinline__ void h_update_cell(const StepArgs& a, int i, int j, int k) {
+    const uint32_t c = (uint32_t)i + (uint32_t)a.g.nx * j + a.g.nxy * k;
+    h_core(a, i, j, k, c, load_e_nbrs(a, i, j, k, c));
+}
+
 // Soft current J_src,s at t = (n + 1/2) dt (FP64: one cell per step).
 __device__ __forceinline__ float source_value(const DevSource& s, long long n) {
     const double t = ((double)n + 0.5) * s.dt - s.t0;
@@ -209,22 +261,31 @@ __device__ __forceinline__ float source_value(const DevSource& s, long long n) {
 // Per cell, in order: J^{n+1/2} and P^{n+1} (gain cells, with the Langevin
 // force of step n), E^{n+1} (backward curl of H^{n+1/2}, CPML, -J, source,
 // PEC walls), N^{n+1}.  fl[6] receives this cell's outward face-flux terms.
-__device__ __forceinline__ void e_update_cell(const StepArgs& a, int i, int j, int k,
-                                              long long n, float fl[6]) {
+__device__ __forceinline__ void e_core(const StepArgs& a, int i, int j, int k, uint32_t c,
+                                       const HNb& h, long long n, float fl[6]) {
     const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
-    const int64_t nxy = a.g.nxy;
-    const int64_t c = i + (int64_t)nx * j + nxy * k;
     const DevFields& f = a.f;
-    const float hx = f.hx[c], hy = f.hy[c], hz = f.hz[c];
-    const float hx_j = (j > 0) ? f.hx[c - nx] : 0.0f;
-    const float hx_k = (k > 0) ? f.hx[c - nxy] : 0.0f;
-    const float hy_i = (i > 0) ? f.hy[c - 1] : 0.0f;
-    const float hy_k = (k > 0) ? f.hy[c - nxy] : 0.0f;
-    const float hz_i = (i > 0) ? f.hz[c - 1] : 0.0f;
-    const float hz_j = (j > 0) ? f.hz[c - nx] : 0.0f;
-    const float dHz_dy = hz - hz_j, dHy_dz = hy - hy_k;
-    const float dHx_dz = hx - hx_k, dHz_dx = hz - hz_i;
-    const float dHy_dx = hy - hy_i, dHx_dy = hx - hx_j;
+    const uint8_t m = __ldg(f.mat + c);
+    const bool gain = a.gain.on && (m & 0x80);
+    const float ex0 = f.ex[c], ey0 = f.ey[c], ez0 = f.ez[c];
+    float jx = 0.0f, jy = 0.0f, jz = 0.0f;
+    float px = 0.0f, py = 0.0f, pz = 0.0f;
+    float n1 = 0.0f, n2 = 0.0f, n3 = 0.0f;
+    if (gain) {
+        n1 = f.n1[c];
+        n2 = f.n2[c];
+        n3 = f.n3[c];
+        px = f.px[c];
+        py = f.py[c];
+        pz = f.pz[c];
+        jx = f.jx[c];
+        jy = f.jy[c];
+        jz = f.jz[c];
+    }
+    const float ie = f.inv_eps ? __ldg(f.inv_eps + c) : __ldg(f.lut_inv_eps + (m & 0x7f));
+    const float dHz_dy = h.hz - h.hz_j, dHy_dz = h.hy - h.hy_k;
+    const float dHx_dz = h.hx - h.hx_k, dHz_dx = h.hz - h.hz_i;
+    const float dHy_dx = h.hy - h.hy_i, dHx_dy = h.hx - h.hx_j;
     float cx = dHz_dy - dHy_dz;
     float cy = dHx_dz - dHz_dx;
     float cz = dHy_dx - dHx_dy;
@@ -232,10 +293,10 @@ __device__ __forceinline__ void e_update_cell(const StepArgs& a, int i, int j, i
     if (L > 0) {
         const int L2 = 2 * L;
         if (i < L || i >= nx - L) {
-            const int s = slab_index(i, nx, L);
-            const int64_t plane = (int64_t)nz * ny * L2;
-            const int64_t q = ((int64_t)k * ny + j) * L2 + s;
-            const float b = a.pml.bex[i], cc = a.pml.cex[i];
+            const uint32_t s = slab_index(i, nx, L);
+            const uint32_t plane = (uint32_t)nz * ny * L2;
+            const uint32_t q = ((uint32_t)k * ny + j) * L2 + s;
+            const float b = __ldg(a.pml.bex + i), cc = __ldg(a.pml.cex + i);
             float* p = a.pml.psx;
             const float psi_yx = b * p[q] + cc * dHz_dx;            // Ey: d/dx Hz
             const float psi_zx = b * p[q + plane] + cc * dHy_dx;    // Ez: d/dx Hy
@@ -245,10 +306,10 @@ __device__ __forceinline__ void e_update_cell(const StepArgs& a, int i, int j, i
             cz += psi_zx;
         }
         if (j < L || j >= ny - L) {
-            const int s = slab_index(j, ny, L);
-            const int64_t plane = (int64_t)nz * L2 * nx;
-            const int64_t q = ((int64_t)k * L2 + s) * nx + i;
-            const float b = a.pml.bey[j], cc = a.pml.cey[j];
+            const uint32_t s = slab_index(j, ny, L);
+            const uint32_t plane = (uint32_t)nz * L2 * nx;
+            const uint32_t q = ((uint32_t)k * L2 + s) * nx + i;
+            const float b = __ldg(a.pml.bey + j), cc = __ldg(a.pml.cey + j);
             float* p = a.pml.psy;
             const float psi_xy = b * p[q] + cc * dHz_dy;            // Ex: d/dy Hz
             const float psi_zy = b * p[q + plane] + cc * dHx_dy;    // Ez: d/dy Hx
@@ -258,10 +319,10 @@ __device__ __forceinline__ void e_update_cell(const StepArgs& a, int i, int j, i
             cz -= psi_zy;
         }
         if (k < L || k >= nz - L) {
-            const int s = slab_index(k, nz, L);
-            const int64_t plane = (int64_t)L2 * ny * nx;
-            const int64_t q = ((int64_t)s * ny + j) * nx + i;
-            const float b = a.pml.bez[k], cc = a.pml.cez[k];
+            const uint32_t s = slab_index(k, nz, L);
+            const uint32_t plane = (uint32_t)L2 * ny * nx;
+            const uint32_t q = (s * ny + j) * nx + i;
+            const float b = __ldg(a.pml.bez + k), cc = __ldg(a.pml.cez + k);
             float* p = a.pml.psz;
             const float psi_xz = b * p[q] + cc * dHy_dz;            // Ex: d/dz Hy
             const float psi_yz = b * p[q + plane] + cc * dHx_dz;    // Ey: d/dz Hx
@@ -271,25 +332,15 @@ __device__ __forceinline__ void e_update_cell(const StepArgs& a, int i, int j, i
             cy += psi_yz;
         }
     }
-    const uint8_t m = f.mat[c];
-    const float ie = f.inv_eps ? f.inv_eps[c] : f.lut_inv_eps[m & 0x7f];
-    const float ex0 = f.ex[c], ey0 = f.ey[c], ez0 = f.ez[c];
-    const bool gain = a.gain.on && (m & 0x80);
-    float jx = 0.0f, jy = 0.0f, jz = 0.0f;
-    float n1 = 0.0f, n2 = 0.0f, n3 = 0.0f;
     if (gain) {
         const DevGain& G = a.gain;
-        n1 = f.n1[c];
-        n2 = f.n2[c];
-        n3 = f.n3[c];
         const float dn = n1 - n2;
         const float amp = G.cJN * sqrtf(fmaxf(n2, 0.0f) + G.nfloor);
         float z0, z1, z2;
-        langevin_normals((uint32_t)c, (uint32_t)n, G.key0, G.key1, z0, z1, z2);
-        const float px = f.px[c], py = f.py[c], pz = f.pz[c];
-        jx = G.cJ1 * f.jx[c] + G.cJE * dn * ex0 - G.cJP * px + amp * z0;
-        jy = G.cJ1 * f.jy[c] + G.cJE * dn * ey0 - G.cJP * py + amp * z1;
-        jz = G.cJ1 * f.jz[c] + G.cJE * dn * ez0 - G.cJP * pz + amp * z2;
+        langevin_normals(c, (uint32_t)n, G.key0, G.key1, z0, z1, z2);
+        jx = G.cJ1 * jx + G.cJE * dn * ex0 - G.cJP * px + amp * z0;
+        jy = G.cJ1 * jy + G.cJE * dn * ey0 - G.cJP * py + amp * z1;
+        jz = G.cJ1 * jz + G.cJE * dn * ez0 - G.cJP * pz + amp * z2;
         f.jx[c] = jx;
         f.jy[c] = jy;
         f.jz[c] = jz;
@@ -298,7 +349,7 @@ __device__ __forceinline__ void e_update_cell(const StepArgs& a, int i, int j, i
         f.pz[c] = pz + jz;
     }
     float sx = jx, sy = jy, sz = jz;
-    if (a.src.on && c == a.src.cell) {
+    if (a.src.on && c == (uint32_t)a.src.cell) {
         const float v = source_value(a.src, n);
         if (a.src.comp == 0) sx += v;
         else if (a.src.comp == 1) sy += v;
@@ -327,19 +378,41 @@ __device__ __forceinline__ void e_update_cell(const StepArgs& a, int i, int j, i
         const DevFlux& F = a.flux;
         const float mx = 0.5f * (ex0 + ex1), my = 0.5f * (ey0 + ey1), mz = 0.5f * (ez0 + ez1);
         if (j >= F.r0[1] && j < F.r1[1] && k >= F.r0[2] && k < F.r1[2]) {
-            const float s = my * hz_i - mz * hy_i;
+            const float s = my * h.hz_i - mz * h.hy_i;
             if (i == F.plo[0]) fl[0] -= s;
             if (i == F.phi[0]) fl[1] += s;
         }
         if (i >= F.r0[0] && i < F.r1[0] && k >= F.r0[2] && k < F.r1[2]) {
-            const float s = mz * hx_j - mx * hz_j;
+            const float s = mz * h.hx_j - mx * h.hz_j;
             if (j == F.plo[1]) fl[2] -= s;
             if (j == F.phi[1]) fl[3] += s;
         }
         if (i >= F.r0[0] && i < F.r1[0] && j >= F.r0[1] && j < F.r1[1]) {
-            const float s = mx * hy_k - my * hx_k;
+            const float s = mx * h.hy_k - my * h.hx_k;
             if (k == F.plo[2]) fl[4] -= s;
             if (k == F.phi[2]) fl[5] += s;
+        }
+    }
+}
+
+__device__ __forceinline__ void e_update_cell(const StepArgs& a, int i, int j, int k,
+                                              long long n, float fl[6]) {
+    const uint32_t c = (uint32_t)i + (uint32_t)a.g.nx * j + a.g.nxy * k;
+    e_core(a, i, j, k, c, load_h_nbrs(a, i, j, k, c), n, fl);
+}
+
+// Warp-level flux reduction: FP32 sums within the warp (skipped for faces
+// no lane touches), one FP64 atomic per warp and face into a slot.  Every
+// lane of the warp must call it.
+__device__ __forceinline__ void flux_warp_reduce(const DevFlux& F, const float fl[6], unsigned slot) {
+    const unsigned full = 0xffffffffu;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        float v = fl[q];
+        if (__any_sync(full, v != 0.0f)) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(full, v, o);
+            if ((threadIdx.x & 31) == 0) atomicAdd(F.acc + q * kFluxSlots + (slot % kFluxSlots), (double)v);
         }
     }
 }

@@ -31,8 +31,19 @@ struct DevFaceProbes {
     double2* acc;       // [point][4][nfreq]: Ea, Eb, Ha, Hb
 };
 
-void launch_h_pass(const StepArgs& a, dim3 block, cudaStream_t s);
-void launch_e_pass(const StepArgs& a, dim3 block, cudaStream_t s);
+// Launch shape of one field pass: the 3-D tiled variant (one thread per
+// cell, block = (bx, by, bz)) or the z-marching variant (2-D block (bx, by),
+// each thread walks kz planes).
+constexpr int kVariant3D = 0;
+constexpr int kVariantZmarch = 1;
+struct PassTune {
+    int variant;
+    dim3 block;
+    int kz;
+};
+
+void launch_h_pass(const StepArgs& a, const PassTune& t, cudaStream_t s);
+void launch_e_pass(const StepArgs& a, const PassTune& t, cudaStream_t s);
 void launch_point_dft(const DevPointProbes& pp, const DevFields& f, const long long* ctr,
                       double dt, cudaStream_t s);
 void launch_face_dft(const DevFaceProbes& fp, const DevFields& f, const DevGrid& g,
@@ -108,7 +119,8 @@ struct mb_ctx {
     // per-step arguments
     mb::StepArgs args{};
     mb::DevSource src{};
-    dim3 blk_h{32, 4, 2}, blk_e{32, 4, 2};
+    mb::PassTune tune_h{mb::kVariantZmarch, dim3(32, 8, 1), 16};
+    mb::PassTune tune_e{mb::kVariantZmarch, dim3(32, 4, 1), 16};
 
     // stepping
     int64_t n = 0;

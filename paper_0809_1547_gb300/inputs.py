@@ -183,14 +183,20 @@ def workload_small_48(seed: int = 1) -> Workload:
                     {"probe": (24, 24, 24)})
 
 
-def workload_paper_320(seed: int = 7) -> Workload:
-    """320^3 (6.4 um box), ~8100 spheres d ~ normal(300 nm, 10 %) at ~45 % fill,
-    gain in the voids, N_a = 5e24 m^-3 (above threshold), active run."""
+def workload_paper(n: int = 320, seed: int = 7) -> Workload:
+    """n^3 box (dx = 20 nm; n = 320 is the paper-scale 6.4 um sample with ~8100
+    spheres), d ~ normal(300 nm, 10 %) at ~45 % fill, gain in the voids,
+    N_a = 5e24 m^-3 (above threshold), active run."""
     dx = DX_DEFAULT
-    grid = (320, 320, 320)
-    n = n_spheres_for_fill(grid, dx, 0.45, 300e-9, 0.10)
-    return _packed_box(grid, n, 300e-9, 0.10, seed, dx, 8, "mb320_active", 5e24, 1e13, 0xACE5, 20000,
-                       probe=(160, 160, 160))
+    grid = (n, n, n)
+    count = n_spheres_for_fill(grid, dx, 0.45, 300e-9, 0.10)
+    return _packed_box(grid, count, 300e-9, 0.10, seed, dx, 8, f"mb{n}_active", 5e24, 1e13, 0xACE5,
+                       20000, probe=(n // 2, n // 2, n // 2))
+
+
+def workload_paper_320(seed: int = 7) -> Workload:
+    """The paper-scale sample: 320^3 (6.4 um box), ~8100 spheres."""
+    return workload_paper(320, seed)
 
 
 def workload_adjoint_96(seed: int = 3) -> Workload:

@@ -107,8 +107,17 @@ def test_degenerate_grids_parity(grid, npml):
     pkw = params_kw(npml=npml)
     o, g = make_pair(grid, eps, gain, 2e24, 1e13, 77, pkw)
     rng2 = np.random.default_rng(5)
+    # a physical start: tangential E vanishes on the PEC planes i = 0, j = 0, k = 0
+    # (a wall value there would leave a static field whose CPML response is
+    # the difference of two nearly equal terms, beyond FP32 resolution)
     for name in ("Ex", "Ey", "Ez"):
         v = (rng2.standard_normal(shp) * 1e6).astype(np.float32)
+        if name != "Ex":
+            v[:, :, 0] = 0
+        if name != "Ey":
+            v[:, 0, :] = 0
+        if name != "Ez":
+            v[0, :, :] = 0
         o.set_field(name, v.astype(np.float64))
         g.set_field(name, v)
     o.step(50)
@@ -163,8 +172,14 @@ def test_cavity_eigenmode_closed_form():
         g.set_field(name, v)
     n = 300
     g.step(n)
+    # errors are measured against the mode's amplitude: at a temporal node the
+    # instantaneous field is ~0 and a relative norm of it would mean nothing
+    amp = {name: np.linalg.norm(v) for name, v in fields(0).items()}
+    ampE = max(amp["Ex"], amp["Ey"], amp["Ez"])
+    ampH = np.linalg.norm([np.linalg.norm(v) for v in fields(0.5).values()][3:])
     for name, v in fields(n).items():
-        assert rel_l2(g.field(name), v) < 1e-4, name
+        scale = ampE if name[0] == "E" else ampH
+        assert np.linalg.norm(g.field(name) - v) <= 1e-5 * scale, name
     g.close()
 
 
