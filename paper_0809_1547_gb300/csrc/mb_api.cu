@@ -142,6 +142,8 @@ void build_args(mb_ctx* c) {
     a.flux.acc = c->d_flux;
     a.S = (float)c->S;
     a.step_ctr = c->d_ctr;
+    a.glist.cell = c->d_glist;
+    a.glist.count = c->glist_count;
 }
 
 void gain_coefficients(mb_ctx* c) {
@@ -408,7 +410,7 @@ int mb_destroy(mb_ctx* c) {
     void* bufs[] = {c->d_fields, c->d_mat, c->d_inv_eps, c->d_lut, c->d_psi[0], c->d_psi[1],
                     c->d_psi[2], c->d_coef, c->d_ctr, c->d_flux, c->d_partial, c->d_energy,
                     c->d_nonfinite, c->d_probe_cell, c->d_probe_omega, c->d_probe_acc,
-                    c->d_face_omega, c->d_face_acc};
+                    c->d_face_omega, c->d_face_acc, c->d_glist};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -478,6 +480,25 @@ int mb_set_material(mb_ctx* c, const float* eps_map, const uint8_t* gain_mask, d
     c->dense_eps = dense;
     c->N_a = N_a;
     c->W_p = pump;
+    // gain cells in increasing order: the Lorentz update runs over this list
+    std::vector<uint32_t> glist;
+    for (int64_t q = 0; q < N; ++q)
+        if (c->h_gain[q]) glist.push_back((uint32_t)q);
+    if (glist.size() > c->glist_count || !c->d_glist) {
+        if (c->d_glist) {
+            cudaFree(c->d_glist);
+            c->dev_bytes -= sizeof(uint32_t) * c->glist_capacity;
+            c->d_glist = nullptr;
+        }
+        const size_t cap = glist.empty() ? 1 : glist.size();
+        cudaError_t e = cudaMalloc((void**)&c->d_glist, sizeof(uint32_t) * cap);
+        if (e != cudaSuccess) { cudaGetLastError(); return fail(c, MB_ERR_OOM, "gain list allocation failed"); }
+        c->glist_capacity = cap;
+        c->dev_bytes += sizeof(uint32_t) * cap;
+    }
+    if (!glist.empty())
+        MB_CUDA(c, cudaMemcpy(c->d_glist, glist.data(), sizeof(uint32_t) * glist.size(), cudaMemcpyHostToDevice));
+    c->glist_count = (uint32_t)glist.size();
     // reset P, J and the populations (N0 = N_a, n1 = n2 = n3 = 0)
     MB_CUDA(c, cudaMemset(c->d_fields + 6 * N, 0, sizeof(float) * 9 * (size_t)N));
     c->have_material = true;

@@ -1,8 +1,8 @@
-// Device-side data of one Maxwell–Bloch FDTD realization and the per-cell
-// update functions of the two field passes.  Every kernel that advances a
-// realization (the plain step, the batched ensemble, the adjoint's forward
-// recomputation) calls these same functions, so their results agree bit for
-// bit.
+// Device-side data of one Maxwell–Bloch FDTD realization and the arithmetic
+// of the two field passes.  Every kernel that advances a realization (the
+// plain step in all its launch variants, the batched ensemble, the adjoint's
+// forward recomputation) composes the same helpers below, so their results
+// agree bit for bit.
 //
 // Units on the device are scaled so that FP32 stays far from under/overflow:
 //   E_s = E/E0, H_s = eta0 H/E0, P_s = P/(eps0 E0), J_s = J dt/(eps0 E0),
@@ -77,15 +77,26 @@ struct DevFlux {
     double* acc;   // [6][kFluxSlots]: faces x-, x+, y-, y+, z-, z+
 };
 
+// Gain cells in increasing cell order (static for a material): the Lorentz
+// update runs over this list so that whole warps do gain work.
+struct DevGainList {
+    const uint32_t* cell;
+    uint32_t count;
+};
+
 struct StepArgs {
     DevGrid g;
     DevFields f;
     DevCpml pml;
     DevGain gain;
+    DevGainList glist;
     DevSource src;
     DevFlux flux;
     float S;
-    long long* step_ctr;   // [0]: index of the step in progress, [1]: next index
+    // [0]: steps completed so far = index n of the step in progress; the
+    // last block of the E pass increments it.  [1]: blocks of the current E
+    // pass that have finished (reset to 0 by the last one).
+    long long* step_ctr;
 };
 
 // ------------------------------------------------------------------ Philox
@@ -113,21 +124,29 @@ __device__ __forceinline__ float u32_to_unit(uint32_t x) {
     return (static_cast<float>(x >> 9) + 0.5f) * 1.1920928955078125e-07f;
 }
 
-// Three standard normals of cell `cell` at step `step` (Box–Muller, FP32
-// with the accurate logf / sqrtf / sincospif).
+// Three standard normals of cell `cell` at step `step`: Box–Muller,
+// z0 + i z1 = sqrt(-2 ln u0) exp(2 pi i u1), z2 = sqrt(-2 ln u2) cos(2 pi u3).
+// FP32 on the special-function unit: ln via __logf (absolute error below
+// 2^-21 on [0.5, 2], 3 ulp elsewhere), sqrt(q) as q rsqrt(q) (q > 0 since
+// u < 1), and the angle taken as 2 pi (u - 1/2) in [-pi, pi), where __sincosf
+// is accurate to 2^-21 absolute: cos(2 pi u) = -cos(2 pi (u - 1/2)), likewise
+// for sin.  The resulting normals differ from exact ones by ~1e-7 in rms.
 __device__ __forceinline__ void langevin_normals(uint32_t cell, uint32_t step, uint32_t k0,
                                                  uint32_t k1, float& z0, float& z1, float& z2) {
     const uint4 x = philox4x32_10(make_uint4(cell, step, 0u, 0u), k0, k1);
     const float u0 = u32_to_unit(x.x), u1 = u32_to_unit(x.y);
     const float u2 = u32_to_unit(x.z), u3 = u32_to_unit(x.w);
-    const float r01 = sqrtf(-2.0f * logf(u0));
-    const float r23 = sqrtf(-2.0f * logf(u2));
-    float s1, c1, s3, c3;
-    sincospif(2.0f * u1, &s1, &c1);
-    sincospif(2.0f * u3, &s3, &c3);
-    z0 = r01 * c1;
-    z1 = r01 * s1;
-    z2 = r23 * c3;
+    const float q01 = -2.0f * __logf(u0);
+    const float q23 = -2.0f * __logf(u2);
+    const float r01 = q01 * rsqrtf(q01);
+    const float r23 = q23 * rsqrtf(q23);
+    const float two_pi = 6.283185307179586f;
+    float s1, c1;
+    __sincosf(two_pi * (u1 - 0.5f), &s1, &c1);
+    const float c3 = __cosf(two_pi * (u3 - 0.5f));
+    z0 = -r01 * c1;
+    z1 = -r01 * s1;
+    z2 = -r23 * c3;
 }
 
 __device__ __forceinline__ int slab_index(int i, int n, int L) {
@@ -185,60 +204,71 @@ __device__ __forceinline__ HNb load_h_nbrs(const StepArgs& a, int i, int j, int 
 }
 
 // ------------------------------------------------------------- H half-step
+// CPML of the H update at cell (i, j, k): advances psi_H and adds it to the
+// curl components.  d = (dEz_dy, dEy_dz, dEx_dz, dEz_dx, dEy_dx, dEx_dy).
+__device__ __forceinline__ void h_pml(const StepArgs& a, int i, int j, int k, const float d[6],
+                                      float& cx, float& cy, float& cz) {
+    const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
+    const int L = a.pml.L;
+    const int L2 = 2 * L;
+    if (i < L || i >= nx - L) {
+        const uint32_t s = slab_index(i, nx, L);
+        const uint32_t plane = (uint32_t)nz * ny * L2;
+        const uint32_t q = ((uint32_t)k * ny + j) * L2 + s;
+        const float b = __ldg(a.pml.bhx + i), cc = __ldg(a.pml.chx + i);
+        float* p = a.pml.psx;
+        const float psi_yx = b * p[q + 2 * plane] + cc * d[3];   // Hy: d/dx Ez
+        const float psi_zx = b * p[q + 3 * plane] + cc * d[4];   // Hz: d/dx Ey
+        p[q + 2 * plane] = psi_yx;
+        p[q + 3 * plane] = psi_zx;
+        cy -= psi_yx;
+        cz += psi_zx;
+    }
+    if (j < L || j >= ny - L) {
+        const uint32_t s = slab_index(j, ny, L);
+        const uint32_t plane = (uint32_t)nz * L2 * nx;
+        const uint32_t q = ((uint32_t)k * L2 + s) * nx + i;
+        const float b = __ldg(a.pml.bhy + j), cc = __ldg(a.pml.chy + j);
+        float* p = a.pml.psy;
+        const float psi_xy = b * p[q + 2 * plane] + cc * d[0];   // Hx: d/dy Ez
+        const float psi_zy = b * p[q + 3 * plane] + cc * d[5];   // Hz: d/dy Ex
+        p[q + 2 * plane] = psi_xy;
+        p[q + 3 * plane] = psi_zy;
+        cx += psi_xy;
+        cz -= psi_zy;
+    }
+    if (k < L || k >= nz - L) {
+        const uint32_t s = slab_index(k, nz, L);
+        const uint32_t plane = (uint32_t)L2 * ny * nx;
+        const uint32_t q = (s * ny + j) * nx + i;
+        const float b = __ldg(a.pml.bhz + k), cc = __ldg(a.pml.chz + k);
+        float* p = a.pml.psz;
+        const float psi_xz = b * p[q + 2 * plane] + cc * d[1];   // Hx: d/dz Ey
+        const float psi_yz = b * p[q + 3 * plane] + cc * d[2];   // Hy: d/dz Ex
+        p[q + 2 * plane] = psi_xz;
+        p[q + 3 * plane] = psi_yz;
+        cx -= psi_xz;
+        cy += psi_yz;
+    }
+}
+
 // H^{n+1/2} = H^{n-1/2} - S (curl_fwd E^n + psi_H) for cell c = (i, j, k).
+// PML: the cell may lie in a CPML slab (false only when it surely does not).
+template <bool PML>
 __device__ __forceinline__ void h_core(const StepArgs& a, int i, int j, int k, uint32_t c,
                                        const ENb& e) {
-    const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
     const DevFields& f = a.f;
-    const float dEz_dy = e.ez_j1 - e.ez, dEy_dz = e.ey_k1 - e.ey;
-    const float dEx_dz = e.ex_k1 - e.ex, dEz_dx = e.ez_i1 - e.ez;
-    const float dEy_dx = e.ey_i1 - e.ey, dEx_dy = e.ex_j1 - e.ex;
-    float cx = dEz_dy - dEy_dz;
-    float cy = dEx_dz - dEz_dx;
-    float cz = dEy_dx - dEx_dy;
-    const int L = a.pml.L;
-    if (L > 0) {
-        const int L2 = 2 * L;
-        if (i < L || i >= nx - L) {
-            const uint32_t s = slab_index(i, nx, L);
-            const uint32_t plane = (uint32_t)nz * ny * L2;
-            const uint32_t q = ((uint32_t)k * ny + j) * L2 + s;
-            const float b = __ldg(a.pml.bhx + i), cc = __ldg(a.pml.chx + i);
-            float* p = a.pml.psx;
-            const float psi_yx = b * p[q + 2 * plane] + cc * dEz_dx;   // Hy: d/dx Ez
-            const float psi_zx = b * p[q + 3 * plane] + cc * dEy_dx;   // Hz: d/dx Ey
-            p[q + 2 * plane] = psi_yx;
-            p[q + 3 * plane] = psi_zx;
-            cy -= psi_yx;
-            cz += psi_zx;
-        }
-        if (j < L || j >= ny - L) {
-            const uint32_t s = slab_index(j, ny, L);
-            const uint32_t plane = (uint32_t)nz * L2 * nx;
-            const uint32_t q = ((uint32_t)k * L2 + s) * nx + i;
-            const float b = __ldg(a.pml.bhy + j), cc = __ldg(a.pml.chy + j);
-            float* p = a.pml.psy;
-            const float psi_xy = b * p[q + 2 * plane] + cc * dEz_dy;   // Hx: d/dy Ez
-            const float psi_zy = b * p[q + 3 * plane] + cc * dEx_dy;   // Hz: d/dy Ex
-            p[q + 2 * plane] = psi_xy;
-            p[q + 3 * plane] = psi_zy;
-            cx += psi_xy;
-            cz -= psi_zy;
-        }
-        if (k < L || k >= nz - L) {
-            const uint32_t s = slab_index(k, nz, L);
-            const uint32_t plane = (uint32_t)L2 * ny * nx;
-            const uint32_t q = (s * ny + j) * nx + i;
-            const float b = __ldg(a.pml.bhz + k), cc = __ldg(a.pml.chz + k);
-            float* p = a.pml.psz;
-            const float psi_xz = b * p[q + 2 * plane] + cc * dEy_dz;   // Hx: d/dz Ey
-            const float psi_yz = b * p[q + 3 * plane] + cc * dEx_dz;   // Hy: d/dz Ex
-            p[q + 2 * plane] = psi_xz;
-            p[q + 3 * plane] = psi_yz;
-            cx -= psi_xz;
-            cy += psi_yz;
-        }
-    }
+    float d[6];
+    d[0] = e.ez_j1 - e.ez;   // dEz_dy
+    d[1] = e.ey_k1 - e.ey;   // dEy_dz
+    d[2] = e.ex_k1 - e.ex;   // dEx_dz
+    d[3] = e.ez_i1 - e.ez;   // dEz_dx
+    d[4] = e.ey_i1 - e.ey;   // dEy_dx
+    d[5] = e.ex_j1 - e.ex;   // dEx_dy
+    float cx = d[0] - d[1];
+    float cy = d[2] - d[3];
+    float cz = d[4] - d[5];
+    if (PML && a.pml.L > 0) h_pml(a, i, j, k, d, cx, cy, cz);
     const float S = a.S;
     f.hx[c] = f.hx[c] - S * cx;
     f.hy[c] = f.hy[c] - S * cy;
@@ -247,7 +277,7 @@ __device__ __forceinline__ void h_core(const StepArgs& a, int i, int j, int k, u
 
 __device__ __forceinline__ void h_update_cell(const StepArgs& a, int i, int j, int k) {
     const uint32_t c = (uint32_t)i + (uint32_t)a.g.nx * j + a.g.nxy * k;
-    h_core(a, i, j, k, c, load_e_nbrs(a, i, j, k, c));
+    h_core<true>(a, i, j, k, c, load_e_nbrs(a, i, j, k, c));
 }
 
 // Soft current J_src,s at t = (n + 1/2) dt (FP64: one cell per step).
@@ -257,98 +287,106 @@ __device__ __forceinline__ float source_value(const DevSource& s, long long n) {
     return (float)(s.amp_s * sin(s.ws * t) * exp(-e * e));
 }
 
-// ------------------------------------------ fused E / gain / population pass
-// Per cell, in order: J^{n+1/2} and P^{n+1} (gain cells, with the Langevin
-// force of step n), E^{n+1} (backward curl of H^{n+1/2}, CPML, -J, source,
-// PEC walls), N^{n+1}.  fl[6] receives this cell's outward face-flux terms.
-__device__ __forceinline__ void e_core(const StepArgs& a, int i, int j, int k, uint32_t c,
-                                       const HNb& h, long long n, float fl[6]) {
+// --------------------------------------------- gain medium (gain cells only)
+// Lorentz polarization with the Langevin force of step n:
+// J^{n+1/2} (in j*) and P^{n+1} (in p*) from J^{n-1/2}, P^n, E^n, N^n.
+__device__ __forceinline__ void lorentz_step(const DevGain& G, uint32_t c, long long n,
+                                             float ex0, float ey0, float ez0, float n1, float n2,
+                                             float& jx, float& jy, float& jz,
+                                             float& px, float& py, float& pz) {
+    const float dn = n1 - n2;
+    const float amp = G.cJN * sqrtf(fmaxf(n2, 0.0f) + G.nfloor);
+    float z0, z1, z2;
+    langevin_normals(c, (uint32_t)n, G.key0, G.key1, z0, z1, z2);
+    jx = G.cJ1 * jx + G.cJE * dn * ex0 - G.cJP * px + amp * z0;
+    jy = G.cJ1 * jy + G.cJE * dn * ey0 - G.cJP * py + amp * z1;
+    jz = G.cJ1 * jz + G.cJE * dn * ez0 - G.cJP * pz + amp * z2;
+    px = px + jx;
+    py = py + jy;
+    pz = pz + jz;
+}
+
+// Crank–Nicolson populations driven by S_pop = (E^n + E^{n+1}) . J^{n+1/2} / 2.
+__device__ __forceinline__ void population_step(const DevGain& G, float ex0, float ey0, float ez0,
+                                                float ex1, float ey1, float ez1, float jx,
+                                                float jy, float jz, float& n1, float& n2,
+                                                float& n3) {
+    const float sp = 0.5f * ((ex0 + ex1) * jx + (ey0 + ey1) * jy + (ez0 + ez1) * jz);
+    const float a1 = n1 + (G.g[0] + G.G[0][0] * n1 + G.G[0][1] * n2 + G.G[0][2] * n3 + G.mk[0] * sp);
+    const float a2 = n2 + (G.g[1] + G.G[1][0] * n1 + G.G[1][1] * n2 + G.G[1][2] * n3 + G.mk[1] * sp);
+    const float a3 = n3 + (G.g[2] + G.G[2][0] * n1 + G.G[2][1] * n2 + G.G[2][2] * n3 + G.mk[2] * sp);
+    n1 = a1;
+    n2 = a2;
+    n3 = a3;
+}
+
+// --------------------------------------------------------------- E update
+// CPML of the E update: advances psi_E and adds it to the curl components.
+// d = (dHz_dy, dHy_dz, dHx_dz, dHz_dx, dHy_dx, dHx_dy).
+__device__ __forceinline__ void e_pml(const StepArgs& a, int i, int j, int k, const float d[6],
+                                      float& cx, float& cy, float& cz) {
     const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
-    const DevFields& f = a.f;
-    const uint8_t m = __ldg(f.mat + c);
-    const bool gain = a.gain.on && (m & 0x80);
-    const float ex0 = f.ex[c], ey0 = f.ey[c], ez0 = f.ez[c];
-    float jx = 0.0f, jy = 0.0f, jz = 0.0f;
-    float px = 0.0f, py = 0.0f, pz = 0.0f;
-    float n1 = 0.0f, n2 = 0.0f, n3 = 0.0f;
-    if (gain) {
-        n1 = f.n1[c];
-        n2 = f.n2[c];
-        n3 = f.n3[c];
-        px = f.px[c];
-        py = f.py[c];
-        pz = f.pz[c];
-        jx = f.jx[c];
-        jy = f.jy[c];
-        jz = f.jz[c];
-    }
-    const float ie = f.inv_eps ? __ldg(f.inv_eps + c) : __ldg(f.lut_inv_eps + (m & 0x7f));
-    const float dHz_dy = h.hz - h.hz_j, dHy_dz = h.hy - h.hy_k;
-    const float dHx_dz = h.hx - h.hx_k, dHz_dx = h.hz - h.hz_i;
-    const float dHy_dx = h.hy - h.hy_i, dHx_dy = h.hx - h.hx_j;
-    float cx = dHz_dy - dHy_dz;
-    float cy = dHx_dz - dHz_dx;
-    float cz = dHy_dx - dHx_dy;
     const int L = a.pml.L;
-    if (L > 0) {
-        const int L2 = 2 * L;
-        if (i < L || i >= nx - L) {
-            const uint32_t s = slab_index(i, nx, L);
-            const uint32_t plane = (uint32_t)nz * ny * L2;
-            const uint32_t q = ((uint32_t)k * ny + j) * L2 + s;
-            const float b = __ldg(a.pml.bex + i), cc = __ldg(a.pml.cex + i);
-            float* p = a.pml.psx;
-            const float psi_yx = b * p[q] + cc * dHz_dx;            // Ey: d/dx Hz
-            const float psi_zx = b * p[q + plane] + cc * dHy_dx;    // Ez: d/dx Hy
-            p[q] = psi_yx;
-            p[q + plane] = psi_zx;
-            cy -= psi_yx;
-            cz += psi_zx;
-        }
-        if (j < L || j >= ny - L) {
-            const uint32_t s = slab_index(j, ny, L);
-            const uint32_t plane = (uint32_t)nz * L2 * nx;
-            const uint32_t q = ((uint32_t)k * L2 + s) * nx + i;
-            const float b = __ldg(a.pml.bey + j), cc = __ldg(a.pml.cey + j);
-            float* p = a.pml.psy;
-            const float psi_xy = b * p[q] + cc * dHz_dy;            // Ex: d/dy Hz
-            const float psi_zy = b * p[q + plane] + cc * dHx_dy;    // Ez: d/dy Hx
-            p[q] = psi_xy;
-            p[q + plane] = psi_zy;
-            cx += psi_xy;
-            cz -= psi_zy;
-        }
-        if (k < L || k >= nz - L) {
-            const uint32_t s = slab_index(k, nz, L);
-            const uint32_t plane = (uint32_t)L2 * ny * nx;
-            const uint32_t q = (s * ny + j) * nx + i;
-            const float b = __ldg(a.pml.bez + k), cc = __ldg(a.pml.cez + k);
-            float* p = a.pml.psz;
-            const float psi_xz = b * p[q] + cc * dHy_dz;            // Ex: d/dz Hy
-            const float psi_yz = b * p[q + plane] + cc * dHx_dz;    // Ey: d/dz Hx
-            p[q] = psi_xz;
-            p[q + plane] = psi_yz;
-            cx -= psi_xz;
-            cy += psi_yz;
-        }
+    const int L2 = 2 * L;
+    if (i < L || i >= nx - L) {
+        const uint32_t s = slab_index(i, nx, L);
+        const uint32_t plane = (uint32_t)nz * ny * L2;
+        const uint32_t q = ((uint32_t)k * ny + j) * L2 + s;
+        const float b = __ldg(a.pml.bex + i), cc = __ldg(a.pml.cex + i);
+        float* p = a.pml.psx;
+        const float psi_yx = b * p[q] + cc * d[3];            // Ey: d/dx Hz
+        const float psi_zx = b * p[q + plane] + cc * d[4];    // Ez: d/dx Hy
+        p[q] = psi_yx;
+        p[q + plane] = psi_zx;
+        cy -= psi_yx;
+        cz += psi_zx;
     }
-    if (gain) {
-        const DevGain& G = a.gain;
-        const float dn = n1 - n2;
-        const float amp = G.cJN * sqrtf(fmaxf(n2, 0.0f) + G.nfloor);
-        float z0, z1, z2;
-        langevin_normals(c, (uint32_t)n, G.key0, G.key1, z0, z1, z2);
-        jx = G.cJ1 * jx + G.cJE * dn * ex0 - G.cJP * px + amp * z0;
-        jy = G.cJ1 * jy + G.cJE * dn * ey0 - G.cJP * py + amp * z1;
-        jz = G.cJ1 * jz + G.cJE * dn * ez0 - G.cJP * pz + amp * z2;
-        f.jx[c] = jx;
-        f.jy[c] = jy;
-        f.jz[c] = jz;
-        f.px[c] = px + jx;
-        f.py[c] = py + jy;
-        f.pz[c] = pz + jz;
+    if (j < L || j >= ny - L) {
+        const uint32_t s = slab_index(j, ny, L);
+        const uint32_t plane = (uint32_t)nz * L2 * nx;
+        const uint32_t q = ((uint32_t)k * L2 + s) * nx + i;
+        const float b = __ldg(a.pml.bey + j), cc = __ldg(a.pml.cey + j);
+        float* p = a.pml.psy;
+        const float psi_xy = b * p[q] + cc * d[0];            // Ex: d/dy Hz
+        const float psi_zy = b * p[q + plane] + cc * d[5];    // Ez: d/dy Hx
+        p[q] = psi_xy;
+        p[q + plane] = psi_zy;
+        cx += psi_xy;
+        cz -= psi_zy;
     }
-    float sx = jx, sy = jy, sz = jz;
+    if (k < L || k >= nz - L) {
+        const uint32_t s = slab_index(k, nz, L);
+        const uint32_t plane = (uint32_t)L2 * ny * nx;
+        const uint32_t q = (s * ny + j) * nx + i;
+        const float b = __ldg(a.pml.bez + k), cc = __ldg(a.pml.cez + k);
+        float* p = a.pml.psz;
+        const float psi_xz = b * p[q] + cc * d[1];            // Ex: d/dz Hy
+        const float psi_yz = b * p[q + plane] + cc * d[2];    // Ey: d/dz Hx
+        p[q] = psi_xz;
+        p[q + plane] = psi_yz;
+        cx -= psi_xz;
+        cy += psi_yz;
+    }
+}
+
+// E^{n+1} from E^n, the backward curl of H^{n+1/2} (+ psi_E), the total
+// current (Lorentz J^{n+1/2} plus source) and the PEC walls.
+template <bool PML>
+__device__ __forceinline__ void e_field_step(const StepArgs& a, int i, int j, int k, uint32_t c,
+                                             const HNb& h, float ie, float ex0, float ey0,
+                                             float ez0, float sx, float sy, float sz, long long n,
+                                             float& ex1, float& ey1, float& ez1) {
+    float d[6];
+    d[0] = h.hz - h.hz_j;   // dHz_dy
+    d[1] = h.hy - h.hy_k;   // dHy_dz
+    d[2] = h.hx - h.hx_k;   // dHx_dz
+    d[3] = h.hz - h.hz_i;   // dHz_dx
+    d[4] = h.hy - h.hy_i;   // dHy_dx
+    d[5] = h.hx - h.hx_j;   // dHx_dy
+    float cx = d[0] - d[1];
+    float cy = d[2] - d[3];
+    float cz = d[4] - d[5];
+    if (PML && a.pml.L > 0) e_pml(a, i, j, k, d, cx, cy, cz);
     if (a.src.on && c == (uint32_t)a.src.cell) {
         const float v = source_value(a.src, n);
         if (a.src.comp == 0) sx += v;
@@ -356,49 +394,97 @@ __device__ __forceinline__ void e_core(const StepArgs& a, int i, int j, int k, u
         else sz += v;
     }
     const float S = a.S;
-    float ex1 = ex0 + ie * (S * cx - sx);
-    float ey1 = ey0 + ie * (S * cy - sy);
-    float ez1 = ez0 + ie * (S * cz - sz);
+    ex1 = ex0 + ie * (S * cx - sx);
+    ey1 = ey0 + ie * (S * cy - sy);
+    ez1 = ez0 + ie * (S * cz - sz);
     // PEC walls: tangential E on the planes i = 0, j = 0, k = 0.
     if (j == 0 || k == 0) ex1 = 0.0f;
     if (i == 0 || k == 0) ey1 = 0.0f;
     if (i == 0 || j == 0) ez1 = 0.0f;
+}
+
+// Outward face-flux terms of cell (i, j, k): (E^n + E^{n+1})/2 on the face
+// plane against H^{n+1/2} half a cell below it, added into fl[6].
+__device__ __forceinline__ void flux_terms(const DevFlux& F, int i, int j, int k, const HNb& h,
+                                           float ex0, float ey0, float ez0, float ex1, float ey1,
+                                           float ez1, float fl[6]) {
+    const float mx = 0.5f * (ex0 + ex1), my = 0.5f * (ey0 + ey1), mz = 0.5f * (ez0 + ez1);
+    if (j >= F.r0[1] && j < F.r1[1] && k >= F.r0[2] && k < F.r1[2]) {
+        const float s = my * h.hz_i - mz * h.hy_i;
+        if (i == F.plo[0]) fl[0] -= s;
+        if (i == F.phi[0]) fl[1] += s;
+    }
+    if (i >= F.r0[0] && i < F.r1[0] && k >= F.r0[2] && k < F.r1[2]) {
+        const float s = mz * h.hx_j - mx * h.hz_j;
+        if (j == F.plo[1]) fl[2] -= s;
+        if (j == F.phi[1]) fl[3] += s;
+    }
+    if (i >= F.r0[0] && i < F.r1[0] && j >= F.r0[1] && j < F.r1[1]) {
+        const float s = mx * h.hy_k - my * h.hx_k;
+        if (k == F.plo[2]) fl[4] -= s;
+        if (k == F.phi[2]) fl[5] += s;
+    }
+}
+
+// ------------------------------------------------- Lorentz step, gain cells
+// J^{n+1/2} and P^{n+1} of gain cell c with the Langevin force of step n.
+// It reads only time-n state (E^n, P^n, J^{n-1/2}, N^n), so it runs in the
+// H half-step launch, before the E pass overwrites E.
+__device__ __forceinline__ void gain_cell_step(const StepArgs& a, uint32_t c, long long n) {
+    const DevFields& f = a.f;
+    const float ex0 = __ldg(f.ex + c), ey0 = __ldg(f.ey + c), ez0 = __ldg(f.ez + c);
+    const float n1 = f.n1[c], n2 = f.n2[c];
+    float px = f.px[c], py = f.py[c], pz = f.pz[c];
+    float jx = f.jx[c], jy = f.jy[c], jz = f.jz[c];
+    lorentz_step(a.gain, c, n, ex0, ey0, ez0, n1, n2, jx, jy, jz, px, py, pz);
+    f.jx[c] = jx;
+    f.jy[c] = jy;
+    f.jz[c] = jz;
+    f.px[c] = px;
+    f.py[c] = py;
+    f.pz[c] = pz;
+}
+
+// ------------------------------------------------ E / population pass
+// One cell, after the gain cells' Lorentz step of this time step: E^{n+1}
+// with the current J^{n+1/2}, then N^{n+1}; with FLUX, the face-flux terms.
+template <bool FLUX, bool PML>
+__device__ __forceinline__ void e_core(const StepArgs& a, int i, int j, int k, uint32_t c,
+                                       const HNb& h, long long n, float fl[6]) {
+    const DevFields& f = a.f;
+    const uint8_t m = __ldg(f.mat + c);
+    const bool gain = a.gain.on && (m & 0x80);
+    const float ex0 = f.ex[c], ey0 = f.ey[c], ez0 = f.ez[c];
+    float jx = 0.0f, jy = 0.0f, jz = 0.0f;
+    float n1 = 0.0f, n2 = 0.0f, n3 = 0.0f;
+    if (gain) {
+        jx = f.jx[c];
+        jy = f.jy[c];
+        jz = f.jz[c];
+        n1 = f.n1[c];
+        n2 = f.n2[c];
+        n3 = f.n3[c];
+    }
+    const float ie = f.inv_eps ? __ldg(f.inv_eps + c) : __ldg(f.lut_inv_eps + (m & 0x7f));
+    float ex1, ey1, ez1;
+    e_field_step<PML>(a, i, j, k, c, h, ie, ex0, ey0, ez0, jx, jy, jz, n, ex1, ey1, ez1);
     f.ex[c] = ex1;
     f.ey[c] = ey1;
     f.ez[c] = ez1;
     if (gain) {
-        const DevGain& G = a.gain;
-        const float sp = 0.5f * ((ex0 + ex1) * jx + (ey0 + ey1) * jy + (ez0 + ez1) * jz);
-        f.n1[c] = n1 + (G.g[0] + G.G[0][0] * n1 + G.G[0][1] * n2 + G.G[0][2] * n3 + G.mk[0] * sp);
-        f.n2[c] = n2 + (G.g[1] + G.G[1][0] * n1 + G.G[1][1] * n2 + G.G[1][2] * n3 + G.mk[1] * sp);
-        f.n3[c] = n3 + (G.g[2] + G.G[2][0] * n1 + G.G[2][1] * n2 + G.G[2][2] * n3 + G.mk[2] * sp);
+        population_step(a.gain, ex0, ey0, ez0, ex1, ey1, ez1, jx, jy, jz, n1, n2, n3);
+        f.n1[c] = n1;
+        f.n2[c] = n2;
+        f.n3[c] = n3;
     }
-    if (a.flux.on) {
-        // (E^n + E^{n+1})/2 on the plane against H^{n+1/2} half a cell below it.
-        const DevFlux& F = a.flux;
-        const float mx = 0.5f * (ex0 + ex1), my = 0.5f * (ey0 + ey1), mz = 0.5f * (ez0 + ez1);
-        if (j >= F.r0[1] && j < F.r1[1] && k >= F.r0[2] && k < F.r1[2]) {
-            const float s = my * h.hz_i - mz * h.hy_i;
-            if (i == F.plo[0]) fl[0] -= s;
-            if (i == F.phi[0]) fl[1] += s;
-        }
-        if (i >= F.r0[0] && i < F.r1[0] && k >= F.r0[2] && k < F.r1[2]) {
-            const float s = mz * h.hx_j - mx * h.hz_j;
-            if (j == F.plo[1]) fl[2] -= s;
-            if (j == F.phi[1]) fl[3] += s;
-        }
-        if (i >= F.r0[0] && i < F.r1[0] && j >= F.r0[1] && j < F.r1[1]) {
-            const float s = mx * h.hy_k - my * h.hx_k;
-            if (k == F.plo[2]) fl[4] -= s;
-            if (k == F.phi[2]) fl[5] += s;
-        }
-    }
+    if (FLUX && a.flux.on) flux_terms(a.flux, i, j, k, h, ex0, ey0, ez0, ex1, ey1, ez1, fl);
 }
 
+template <bool FLUX>
 __device__ __forceinline__ void e_update_cell(const StepArgs& a, int i, int j, int k,
                                               long long n, float fl[6]) {
     const uint32_t c = (uint32_t)i + (uint32_t)a.g.nx * j + a.g.nxy * k;
-    e_core(a, i, j, k, c, load_h_nbrs(a, i, j, k, c), n, fl);
+    e_core<FLUX, true>(a, i, j, k, c, load_h_nbrs(a, i, j, k, c), n, fl);
 }
 
 // Warp-level flux reduction: FP32 sums within the warp (skipped for faces

@@ -42,6 +42,15 @@ struct PassTune {
     int kz;
 };
 
+// Grid of the H + gain launch: nH H tiles (tile grid gx x gy x gz) and nG
+// gain blocks, each over q consecutive entries of the gain list.
+struct HGLayout {
+    int gx, gy, gz;
+    int nH, nG;
+    int q;
+};
+
+HGLayout hg_layout(const StepArgs& a, const PassTune& t);
 void launch_h_pass(const StepArgs& a, const PassTune& t, cudaStream_t s);
 void launch_e_pass(const StepArgs& a, const PassTune& t, cudaStream_t s);
 void launch_point_dft(const DevPointProbes& pp, const DevFields& f, const long long* ctr,
@@ -87,6 +96,9 @@ struct mb_ctx {
     float* d_psi[3] = {nullptr, nullptr, nullptr};
     size_t psi_elems[3] = {0, 0, 0};
     float* d_coef = nullptr;           // CPML tables
+    uint32_t* d_glist = nullptr;       // gain cells, increasing order
+    uint32_t glist_count = 0;
+    size_t glist_capacity = 0;
     long long* d_ctr = nullptr;        // step counters
     double* d_flux = nullptr;          // 6 accumulators
     double* d_partial = nullptr;       // energy partial sums

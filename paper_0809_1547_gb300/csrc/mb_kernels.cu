@@ -1,163 +1,26 @@
-// Kernels of the plain Maxwell–Bloch FDTD step and their launchers.
+// Probe, read-out and diagnostic kernels of the Maxwell–Bloch FDTD step
+// (the two field passes live in mb_passes.cu):
 //
-//   k_h_pass      H half-step (forward curl of E, H-side CPML)
-//   k_e_pass      fused E / Lorentz polarization / Langevin noise / population
-//                 pass, plus the outward face flux of the interior box
 //   k_point_dft   running DFT of E at the point probes (FP64 accumulators)
 //   k_face_dft    running DFT of tangential E and H on the face sub-grids
 //   k_energy_*    two-pass deterministic reduction of the field energy
+//   k_philox      the noise generator on given counters
 //
-// The field passes are memory-bound stencils: one thread per cell, thread
-// blocks tiled over (x, y, z) with x fastest so that warps read contiguous
-// rows; neighbours come through L1/L2.  No tensor cores: nothing here is a
-// dense contraction.
+// The probes run after the E pass of step n, whose last block has already
+// advanced the step counter to n + 1: E^{n+1} is sampled at t_{n+1}.
 #include "mb_host.h"
 
 #include <cstdio>
 
 namespace mb {
 
-// Blocks whose cell range contains a face plane reduce the flux; the others
-// skip the reduction (block-uniform test).  kz: planes per block along z.
-__device__ __forceinline__ bool block_on_face(const DevFlux& F, int kz) {
-    if (!F.on) return false;
-    const int i0 = blockIdx.x * blockDim.x, i1 = i0 + blockDim.x;
-    const int j0 = blockIdx.y * blockDim.y, j1 = j0 + blockDim.y;
-    const int k0 = blockIdx.z * kz, k1 = k0 + kz;
-    return (F.plo[0] >= i0 && F.plo[0] < i1) || (F.phi[0] >= i0 && F.phi[0] < i1) ||
-           (F.plo[1] >= j0 && F.plo[1] < j1) || (F.phi[1] >= j0 && F.phi[1] < j1) ||
-           (F.plo[2] >= k0 && F.plo[2] < k1) || (F.phi[2] >= k0 && F.phi[2] < k1);
-}
-
-__device__ __forceinline__ void bump_step_counter(const StepArgs& a) {
-    if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 &&
-        threadIdx.y == 0 && threadIdx.z == 0) {
-        // No other thread of this launch reads the counter; the E pass and the
-        // probes of this step run after this kernel in stream order.
-        const long long nxt = a.step_ctr[1];
-        a.step_ctr[0] = nxt;
-        a.step_ctr[1] = nxt + 1;
-    }
-}
-
-__device__ __forceinline__ unsigned warp_slot() {
-    const unsigned b = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-    const unsigned w = (threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z)) >> 5;
-    return b * 7u + w;
-}
-
-// ---- 3-D tiled variant: one thread per cell, neighbours through L1/L2.
-__global__ void __launch_bounds__(512) k_h_pass(StepArgs a) {
-    bump_step_counter(a);
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k = blockIdx.z * blockDim.z + threadIdx.z;
-    if (i < a.g.nx && j < a.g.ny && k < a.g.nz) h_update_cell(a, i, j, k);
-}
-
-__global__ void __launch_bounds__(512) k_e_pass(StepArgs a) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k = blockIdx.z * blockDim.z + threadIdx.z;
-    const long long n = a.step_ctr[0];
-    float fl[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    if (i < a.g.nx && j < a.g.ny && k < a.g.nz) e_update_cell(a, i, j, k, n, fl);
-    if (block_on_face(a.flux, blockDim.z)) flux_warp_reduce(a.flux, fl, warp_slot());
-}
-
-// ---- z-marching variant: 2-D tiles over (x, y); each thread walks kz planes
-// of its column, carrying the neighbour plane in registers.
-__global__ void __launch_bounds__(512) k_h_zmarch(StepArgs a, int kz) {
-    bump_step_counter(a);
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
-    if (i >= nx || j >= ny) return;
-    const int k0 = blockIdx.z * kz;
-    const int k1 = min(nz, k0 + kz);
-    const uint32_t nxy = a.g.nxy;
-    const float* __restrict__ Ex = a.f.ex;
-    const float* __restrict__ Ey = a.f.ey;
-    const float* __restrict__ Ez = a.f.ez;
-    const bool xi = i + 1 < nx, yj = j + 1 < ny;
-    uint32_t c = (uint32_t)i + (uint32_t)nx * j + nxy * k0;
-    float ex_c = __ldg(Ex + c), ey_c = __ldg(Ey + c);
-    for (int k = k0; k < k1; ++k, c += nxy) {
-        ENb e;
-        const bool zk = k + 1 < nz;
-        e.ex = ex_c;
-        e.ey = ey_c;
-        e.ez = __ldg(Ez + c);
-        e.ex_k1 = zk ? __ldg(Ex + c + nxy) : 0.0f;
-        e.ey_k1 = zk ? __ldg(Ey + c + nxy) : 0.0f;
-        e.ex_j1 = yj ? __ldg(Ex + c + nx) : 0.0f;
-        e.ey_i1 = xi ? __ldg(Ey + c + 1) : 0.0f;
-        e.ez_i1 = xi ? __ldg(Ez + c + 1) : 0.0f;
-        e.ez_j1 = yj ? __ldg(Ez + c + nx) : 0.0f;
-        h_core(a, i, j, k, c, e);
-        ex_c = e.ex_k1;
-        ey_c = e.ey_k1;
-    }
-}
-
-__global__ void __launch_bounds__(512) k_e_zmarch(StepArgs a, int kz) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
-    const bool valid = i < nx && j < ny;     // no early exit: the flux reduction is warp-wide
-    const long long n = a.step_ctr[0];
-    const int k0 = blockIdx.z * kz;
-    const int k1 = min(nz, k0 + kz);
-    const uint32_t nxy = a.g.nxy;
-    const float* __restrict__ Hx = a.f.hx;
-    const float* __restrict__ Hy = a.f.hy;
-    const float* __restrict__ Hz = a.f.hz;
-    const bool face = block_on_face(a.flux, kz);
-    const bool face_xy = face && ((a.flux.plo[0] >= (int)(blockIdx.x * blockDim.x) &&
-                                   a.flux.plo[0] < (int)((blockIdx.x + 1) * blockDim.x)) ||
-                                  (a.flux.phi[0] >= (int)(blockIdx.x * blockDim.x) &&
-                                   a.flux.phi[0] < (int)((blockIdx.x + 1) * blockDim.x)) ||
-                                  (a.flux.plo[1] >= (int)(blockIdx.y * blockDim.y) &&
-                                   a.flux.plo[1] < (int)((blockIdx.y + 1) * blockDim.y)) ||
-                                  (a.flux.phi[1] >= (int)(blockIdx.y * blockDim.y) &&
-                                   a.flux.phi[1] < (int)((blockIdx.y + 1) * blockDim.y)));
-    const unsigned slot = warp_slot();
-    uint32_t c = valid ? (uint32_t)i + (uint32_t)nx * j + nxy * k0 : 0u;
-    float hx_km1 = 0.0f, hy_km1 = 0.0f;
-    if (valid && k0 > 0) {
-        hx_km1 = __ldg(Hx + c - nxy);
-        hy_km1 = __ldg(Hy + c - nxy);
-    }
-    for (int k = k0; k < k1; ++k) {
-        float fl[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        if (valid) {
-            HNb h;
-            h.hx = __ldg(Hx + c);
-            h.hy = __ldg(Hy + c);
-            h.hz = __ldg(Hz + c);
-            h.hx_k = hx_km1;
-            h.hy_k = hy_km1;
-            h.hx_j = (j > 0) ? __ldg(Hx + c - nx) : 0.0f;
-            h.hz_j = (j > 0) ? __ldg(Hz + c - nx) : 0.0f;
-            h.hy_i = (i > 0) ? __ldg(Hy + c - 1) : 0.0f;
-            h.hz_i = (i > 0) ? __ldg(Hz + c - 1) : 0.0f;
-            e_core(a, i, j, k, c, h, n, fl);
-            hx_km1 = h.hx;
-            hy_km1 = h.hy;
-            c += nxy;
-        }
-        if (face_xy || (face && (k == a.flux.plo[2] || k == a.flux.phi[2])))
-            flux_warp_reduce(a.flux, fl, slot);
-    }
-}
-
 // One block per probe, threads over frequency bins:
 // acc[p][c][k] += E_c(t_{n+1}) exp(i w_k t_{n+1})   (scaled; times dt E0 on read-out)
 __global__ void k_point_dft(DevPointProbes pp, const float* ex, const float* ey, const float* ez,
                             const long long* step_ctr, double dt) {
     const int p = blockIdx.x;
-    const long long n = step_ctr[0];
-    const double t = (double)(n + 1) * dt;
+    const long long n1 = step_ctr[0];          // n + 1
+    const double t = (double)n1 * dt;
     const int64_t cell = pp.cell[p];
     const float e[3] = {ex[cell], ey[cell], ez[cell]};
     const int K = pp.nfreq;
@@ -179,8 +42,8 @@ __global__ void k_point_dft(DevPointProbes pp, const float* ex, const float* ey,
 // over the chunk's points so each warp touches contiguous accumulators.
 __global__ void k_face_dft(DevFaceProbes fp, DevFields f, DevGrid g, const long long* step_ctr,
                            double dt) {
-    const long long n = step_ctr[0];
-    if ((n + 1) % fp.every != 0) return;
+    const long long n1 = step_ctr[0];         // n + 1
+    if (n1 % fp.every != 0) return;
     const int face = blockIdx.y;
     const int axis = face >> 1;
     const int np = fp.npts[face];
@@ -190,7 +53,7 @@ __global__ void k_face_dft(DevFaceProbes fp, DevFields f, DevGrid g, const long 
     const int plane = fp.plane[face];
     const int K = fp.nfreq;
     const int na = fp.na[face];
-    const double tE = (double)(n + 1) * dt, tH = tE - 0.5 * dt;
+    const double tE = (double)n1 * dt, tH = tE - 0.5 * dt;
     for (int kk = threadIdx.x; kk < K; kk += blockDim.x) {
         const double w = fp.omega[kk];
         double sE, cE, sH, cH;
@@ -298,30 +161,6 @@ __global__ void k_philox(const uint4* ctr, uint32_t k0, uint32_t k1, uint4* out,
 
 void launch_philox(const uint4* ctr, uint32_t k0, uint32_t k1, uint4* out, int n, cudaStream_t s) {
     k_philox<<<(n + 255) / 256, 256, 0, s>>>(ctr, k0, k1, out, n);
-}
-
-void launch_h_pass(const StepArgs& a, const PassTune& t, cudaStream_t s) {
-    if (t.variant == kVariantZmarch) {
-        dim3 grid((a.g.nx + t.block.x - 1) / t.block.x, (a.g.ny + t.block.y - 1) / t.block.y,
-                  (a.g.nz + t.kz - 1) / t.kz);
-        k_h_zmarch<<<grid, dim3(t.block.x, t.block.y, 1), 0, s>>>(a, t.kz);
-    } else {
-        dim3 grid((a.g.nx + t.block.x - 1) / t.block.x, (a.g.ny + t.block.y - 1) / t.block.y,
-                  (a.g.nz + t.block.z - 1) / t.block.z);
-        k_h_pass<<<grid, t.block, 0, s>>>(a);
-    }
-}
-
-void launch_e_pass(const StepArgs& a, const PassTune& t, cudaStream_t s) {
-    if (t.variant == kVariantZmarch) {
-        dim3 grid((a.g.nx + t.block.x - 1) / t.block.x, (a.g.ny + t.block.y - 1) / t.block.y,
-                  (a.g.nz + t.kz - 1) / t.kz);
-        k_e_zmarch<<<grid, dim3(t.block.x, t.block.y, 1), 0, s>>>(a, t.kz);
-    } else {
-        dim3 grid((a.g.nx + t.block.x - 1) / t.block.x, (a.g.ny + t.block.y - 1) / t.block.y,
-                  (a.g.nz + t.block.z - 1) / t.block.z);
-        k_e_pass<<<grid, t.block, 0, s>>>(a);
-    }
 }
 
 void launch_point_dft(const DevPointProbes& pp, const DevFields& f, const long long* ctr,
