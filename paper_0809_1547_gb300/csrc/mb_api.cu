@@ -142,6 +142,7 @@ void build_args(mb_ctx* c) {
     a.flux.acc = c->d_flux;
     a.S = (float)c->S;
     a.step_ctr = c->d_ctr;
+    a.err = c->d_err;
     a.glist.cell = c->d_glist;
     a.glist.count = c->glist_count;
 }
@@ -226,6 +227,29 @@ std::vector<StatePart> state_parts(mb_ctx* c) {
     return v;
 }
 
+// Tensor maps for a TMA tuning (encoded once per tile shape), else nullptr.
+const mb::TmaMapsE* tma_for(mb_ctx* c, const mb::PassTune& t) {
+    if (t.variant != mb::kVariantTma) return nullptr;
+    const auto key = std::make_pair((int)t.block.x, (int)t.block.y);
+    auto it = c->tma_maps.find(key);
+    if (it != c->tma_maps.end()) return &it->second;
+    mb::TmaMapsE m;
+    if (!mb::encode_tma_e(c->args, t.block.x, t.block.y, &m)) return nullptr;
+    return &(c->tma_maps[key] = m);
+}
+
+// Device error flag (a bounded wait gave up): MB_ERR_TIMEOUT, flag cleared.
+int check_device_error(mb_ctx* c) {
+    int e = 0;
+    MB_CUDA(c, cudaMemcpyAsync(&e, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    MB_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (e) {
+        cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
+        return fail(c, MB_ERR_TIMEOUT, "a bounded device wait gave up (results of that step are invalid)");
+    }
+    return MB_OK;
+}
+
 int capture_steps(mb_ctx* c, int steps, cudaGraphExec_t* out) {
     cudaGraph_t graph = nullptr;
     MB_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
@@ -233,7 +257,7 @@ int capture_steps(mb_ctx* c, int steps, cudaGraphExec_t* out) {
                           c->d_probe_omega, c->d_probe_acc};
     for (int s = 0; s < steps; ++s) {
         mb::launch_h_pass(c->args, c->tune_h, c->stream);
-        mb::launch_e_pass(c->args, c->tune_e, c->stream);
+        mb::launch_e_pass(c->args, c->tune_e, tma_for(c, c->tune_e), c->stream);
         mb::launch_point_dft(pp, c->args.f, c->d_ctr, c->dt, c->stream);
         mb::launch_face_dft(c->face, c->args.f, c->args.g, c->d_ctr, c->dt, c->stream);
     }
@@ -361,6 +385,7 @@ int mb_create(mb_ctx** out, const int grid[3], double dx, double dt, const mb_pa
     if ((rc = alloc((void**)&c->d_partial, sizeof(double) * c->n_partial))) return bail(rc);
     if ((rc = alloc((void**)&c->d_energy, sizeof(double)))) return bail(rc);
     if ((rc = alloc((void**)&c->d_nonfinite, sizeof(int)))) return bail(rc);
+    if ((rc = alloc((void**)&c->d_err, sizeof(int)))) return bail(rc);
 
     // CPML tables, zeroed state, eps_r = 1 (material 0), no gain.
     std::vector<float> coef(ncoef);
@@ -385,6 +410,7 @@ int mb_create(mb_ctx** out, const int grid[3], double dx, double dt, const mb_pa
     for (int w = 0; w < 3; ++w)
         if (c->psi_elems[w]) MB_CREATE_CUDA(cudaMemset(c->d_psi[w], 0, sizeof(float) * c->psi_elems[w]));
     MB_CREATE_CUDA(cudaMemset(c->d_ctr, 0, sizeof(long long) * 2));
+    MB_CREATE_CUDA(cudaMemset(c->d_err, 0, sizeof(int)));
     MB_CREATE_CUDA(cudaMemset(c->d_flux, 0, sizeof(double) * 6 * mb::kFluxSlots));
 #undef MB_CREATE_CUDA
     c->h_gain.assign((size_t)ncell, 0);
@@ -410,7 +436,7 @@ int mb_destroy(mb_ctx* c) {
     void* bufs[] = {c->d_fields, c->d_mat, c->d_inv_eps, c->d_lut, c->d_psi[0], c->d_psi[1],
                     c->d_psi[2], c->d_coef, c->d_ctr, c->d_flux, c->d_partial, c->d_energy,
                     c->d_nonfinite, c->d_probe_cell, c->d_probe_omega, c->d_probe_acc,
-                    c->d_face_omega, c->d_face_acc, c->d_glist};
+                    c->d_face_omega, c->d_face_acc, c->d_glist, c->d_src_wave, c->d_err};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -632,14 +658,32 @@ int mb_set_source(mb_ctx* c, const int ijk[3], int comp, double lam, double t0, 
         return fail(c, MB_ERR_ARG, "bad source arguments");
     if (ijk[0] < 0 || ijk[0] >= c->nx || ijk[1] < 0 || ijk[1] >= c->ny || ijk[2] < 0 || ijk[2] >= c->nz)
         return fail(c, MB_ERR_ARG, "source cell outside the grid");
+    // Tabulate the scaled current J dt/(eps0 E0) at t = (n + 1/2) dt in FP64
+    // over the steps where |t - t0| < 12 tau (the envelope is below 1e-62 outside).
+    const double amp_s = amp * c->dt / (kEps0 * c->E0);
+    const double ws = 2.0 * kPi * kC0 / lam;
+    const long long n0 = std::max(0LL, (long long)std::floor((t0 - 12.0 * tau) / c->dt - 0.5));
+    const long long n1 = (long long)std::ceil((t0 + 12.0 * tau) / c->dt - 0.5) + 1;
+    if (n1 <= n0 || n1 - n0 > (1LL << 24)) return fail(c, MB_ERR_ARG, "source window empty or too long");
+    std::vector<float> wave((size_t)(n1 - n0));
+    for (long long n = n0; n < n1; ++n) {
+        const double t = ((double)n + 0.5) * c->dt - t0;
+        const double e = t / tau;
+        wave[(size_t)(n - n0)] = (float)(amp_s * std::sin(ws * t) * std::exp(-e * e));
+    }
+    cudaStreamSynchronize(c->stream);
+    if (c->d_src_wave) {
+        cudaFree(c->d_src_wave);
+        c->d_src_wave = nullptr;
+    }
+    MB_CUDA(c, cudaMalloc((void**)&c->d_src_wave, sizeof(float) * wave.size()));
+    MB_CUDA(c, cudaMemcpy(c->d_src_wave, wave.data(), sizeof(float) * wave.size(), cudaMemcpyHostToDevice));
     c->src.on = 1;
     c->src.comp = comp;
     c->src.cell = ijk[0] + (int64_t)c->nx * (ijk[1] + (int64_t)c->ny * ijk[2]);
-    c->src.amp_s = amp * c->dt / (kEps0 * c->E0);
-    c->src.ws = 2.0 * kPi * kC0 / lam;
-    c->src.t0 = t0;
-    c->src.tau = tau;
-    c->src.dt = c->dt;
+    c->src.n0 = n0;
+    c->src.count = (int)(n1 - n0);
+    c->src.wave = c->d_src_wave;
     c->args.src = c->src;
     drop_graphs(c);
     return MB_OK;
@@ -687,7 +731,7 @@ int mb_step_timed(mb_ctx* c, int n, double* ms_out) {
         cudaEventRecord(e[0], c->stream);
         mb::launch_h_pass(c->args, c->tune_h, c->stream);
         cudaEventRecord(e[1], c->stream);
-        mb::launch_e_pass(c->args, c->tune_e, c->stream);
+        mb::launch_e_pass(c->args, c->tune_e, tma_for(c, c->tune_e), c->stream);
         cudaEventRecord(e[2], c->stream);
         mb::launch_point_dft(pp, c->args.f, c->d_ctr, c->dt, c->stream);
         cudaEventRecord(e[3], c->stream);
@@ -712,7 +756,7 @@ int mb_step_timed(mb_ctx* c, int n, double* ms_out) {
         for (int q = 0; q < 4; ++q) ms_out[q] += acc[q];
     c->n += n;
     c->launches += (int64_t)n * launches_per_step(c);
-    return MB_OK;
+    return check_device_error(c);
 }
 
 int mb_flux(mb_ctx* c, double* out_flux6) {
@@ -724,13 +768,13 @@ int mb_flux(mb_ctx* c, double* out_flux6) {
     sum_flux_slots(slots, fl);
     const double f = c->dt * c->E0 * (c->E0 / c->eta0) * c->dx * c->dx;
     for (int q = 0; q < 6; ++q) out_flux6[q] = fl[q] * f;
-    return MB_OK;
+    return check_device_error(c);
 }
 
 int mb_synchronize(mb_ctx* c) {
     if (int rc = check_ctx(c)) return rc;
     MB_CUDA(c, cudaStreamSynchronize(c->stream));
-    return MB_OK;
+    return check_device_error(c);
 }
 
 int mb_get_step(mb_ctx* c, int64_t* n) {
@@ -811,7 +855,7 @@ int mb_energy(mb_ctx* c, double* out_U, double* out_flux6) {
         for (int q = 0; q < 6; ++q) out_flux6[q] = fl[q] * f;
     }
     if (bad) return fail(c, MB_ERR_NONFINITE, "non-finite field values");
-    return MB_OK;
+    return check_device_error(c);
 }
 
 int mb_get_field(mb_ctx* c, int which, float* host_out) {
@@ -925,6 +969,11 @@ int mb_autotune(mb_ctx* c) {
     for (dim3 b : {dim3(32, 4, 1), dim3(32, 8, 1), dim3(64, 4, 1), dim3(64, 2, 1), dim3(128, 2, 1),
                    dim3(32, 16, 1), dim3(64, 8, 1), dim3(128, 4, 1), dim3(256, 1, 1)})
         for (int kz : {4, 8, 16, 32}) cands.push_back({mb::kVariantZmarch, b, kz});
+    std::vector<mb::PassTune> cands_e_only;
+    if (mb::tma_e_supported(c->args))
+        for (dim3 b : {dim3(32, 4, 1), dim3(32, 8, 1), dim3(64, 4, 1), dim3(64, 8, 1), dim3(128, 2, 1),
+                       dim3(128, 4, 1)})
+            for (int kz : {8, 16, 32, 64}) cands_e_only.push_back({mb::kVariantTma, b, kz});
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -935,11 +984,11 @@ int mb_autotune(mb_ctx* c) {
         if (t.variant == mb::kVariantZmarch && t.kz > 2 * c->nz) continue;
         for (int pass = 0; pass < 2; ++pass) {
             if (pass == 0) mb::launch_h_pass(c->args, t, c->stream);
-            else mb::launch_e_pass(c->args, t, c->stream);
+            else mb::launch_e_pass(c->args, t, tma_for(c, t), c->stream);
             cudaEventRecord(e0, c->stream);
             for (int r = 0; r < reps; ++r) {
                 if (pass == 0) mb::launch_h_pass(c->args, t, c->stream);
-                else mb::launch_e_pass(c->args, t, c->stream);
+                else mb::launch_e_pass(c->args, t, tma_for(c, t), c->stream);
             }
             cudaEventRecord(e1, c->stream);
             cudaEventSynchronize(e1);
@@ -948,6 +997,17 @@ int mb_autotune(mb_ctx* c) {
             if (pass == 0 && ms < best_h) { best_h = ms; bh = t; }
             if (pass == 1 && ms < best_e) { best_e = ms; be = t; }
         }
+    }
+    for (const mb::PassTune& t : cands_e_only) {
+        if (t.kz > 2 * c->nz || !tma_for(c, t)) continue;
+        mb::launch_e_pass(c->args, t, tma_for(c, t), c->stream);
+        cudaEventRecord(e0, c->stream);
+        for (int r = 0; r < reps; ++r) mb::launch_e_pass(c->args, t, tma_for(c, t), c->stream);
+        cudaEventRecord(e1, c->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_e) { best_e = ms; be = t; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -992,14 +1052,19 @@ int mb_set_tuning(mb_ctx* c, const int tune_h[4], const int tune_e[4]) {
     const int* src[2] = {tune_h, tune_e};
     for (int q = 0; q < 2; ++q) {
         const int* b = src[q];
-        if ((b[0] != mb::kVariant3D && b[0] != mb::kVariantZmarch) || b[1] < 32 || b[1] % 32 ||
-            b[2] < 1 || b[3] < 1)
-            return fail(c, MB_ERR_ARG, "bad tuning: variant 0/1, x a multiple of 32, y, z >= 1");
+        const bool tma = b[0] == mb::kVariantTma;
+        if ((b[0] != mb::kVariant3D && b[0] != mb::kVariantZmarch && !(tma && q == 1)) ||
+            b[1] < 32 || b[1] % 32 || b[2] < 1 || b[3] < 1)
+            return fail(c, MB_ERR_ARG,
+                        "bad tuning: variant 0/1 (2 for the E pass), x a multiple of 32, y, z >= 1");
         const int threads = b[1] * b[2] * (b[0] == mb::kVariant3D ? b[3] : 1);
         if (threads > 512) return fail(c, MB_ERR_ARG, "at most 512 threads per block");
         t[q].variant = b[0];
         t[q].block = dim3(b[1], b[2], b[0] == mb::kVariant3D ? b[3] : 1);
-        t[q].kz = b[0] == mb::kVariantZmarch ? b[3] : 1;
+        t[q].kz = b[0] == mb::kVariant3D ? 1 : b[3];
+        if (tma && !tma_for(c, t[q]))
+            return fail(c, MB_ERR_ARG, "TMA E pass needs n_x % 16 == 0 and a tile of 32x4, 32x8, "
+                                       "64x4, 64x8, 128x2 or 128x4");
     }
     c->tune_h = t[0];
     c->tune_e = t[1];

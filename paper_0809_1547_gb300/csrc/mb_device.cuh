@@ -62,10 +62,15 @@ struct DevGain {
     uint32_t key0, key1;
 };
 
+// Soft current source: the scaled current of step n is wave[n - n0] for
+// n0 <= n < n0 + count and zero elsewhere (tabulated on the host in FP64 over
+// the window where the Gaussian envelope is above ~1e-60).
 struct DevSource {
     int on, comp;
     int64_t cell;
-    double amp_s, ws, t0, tau, dt;
+    long long n0;
+    int count;
+    const float* wave;
 };
 
 // Outward Poynting flux of the interior box [r0, r1) per axis through the
@@ -97,6 +102,8 @@ struct StepArgs {
     // last block of the E pass increments it.  [1]: blocks of the current E
     // pass that have finished (reset to 0 by the last one).
     long long* step_ctr;
+    // Set (bit 0) when a bounded device wait gave up; read by the host.
+    int* err;
 };
 
 // ------------------------------------------------------------------ Philox
@@ -280,11 +287,10 @@ __device__ __forceinline__ void h_update_cell(const StepArgs& a, int i, int j, i
     h_core<true>(a, i, j, k, c, load_e_nbrs(a, i, j, k, c));
 }
 
-// Soft current J_src,s at t = (n + 1/2) dt (FP64: one cell per step).
+// Soft current J_src,s at t = (n + 1/2) dt.
 __device__ __forceinline__ float source_value(const DevSource& s, long long n) {
-    const double t = ((double)n + 0.5) * s.dt - s.t0;
-    const double e = t / s.tau;
-    return (float)(s.amp_s * sin(s.ws * t) * exp(-e * e));
+    const long long q = n - s.n0;
+    return (q >= 0 && q < s.count) ? __ldg(s.wave + q) : 0.0f;
 }
 
 // --------------------------------------------- gain medium (gain cells only)
@@ -448,6 +454,29 @@ __device__ __forceinline__ void gain_cell_step(const StepArgs& a, uint32_t c, lo
 // ------------------------------------------------ E / population pass
 // One cell, after the gain cells' Lorentz step of this time step: E^{n+1}
 // with the current J^{n+1/2}, then N^{n+1}; with FLUX, the face-flux terms.
+// The E / population update of cell c from its loaded inputs: material byte
+// m, E^n, and for gain cells J^{n+1/2} and n1..n3 at time n.
+template <bool FLUX, bool PML>
+__device__ __forceinline__ void e_apply(const StepArgs& a, int i, int j, int k, uint32_t c,
+                                        const HNb& h, uint8_t m, float ex0, float ey0, float ez0,
+                                        bool gain, float jx, float jy, float jz, float n1, float n2,
+                                        float n3, long long n, float fl[6]) {
+    const DevFields& f = a.f;
+    const float ie = f.inv_eps ? __ldg(f.inv_eps + c) : __ldg(f.lut_inv_eps + (m & 0x7f));
+    float ex1, ey1, ez1;
+    e_field_step<PML>(a, i, j, k, c, h, ie, ex0, ey0, ez0, jx, jy, jz, n, ex1, ey1, ez1);
+    f.ex[c] = ex1;
+    f.ey[c] = ey1;
+    f.ez[c] = ez1;
+    if (gain) {
+        population_step(a.gain, ex0, ey0, ez0, ex1, ey1, ez1, jx, jy, jz, n1, n2, n3);
+        f.n1[c] = n1;
+        f.n2[c] = n2;
+        f.n3[c] = n3;
+    }
+    if (FLUX && a.flux.on) flux_terms(a.flux, i, j, k, h, ex0, ey0, ez0, ex1, ey1, ez1, fl);
+}
+
 template <bool FLUX, bool PML>
 __device__ __forceinline__ void e_core(const StepArgs& a, int i, int j, int k, uint32_t c,
                                        const HNb& h, long long n, float fl[6]) {
@@ -465,19 +494,7 @@ __device__ __forceinline__ void e_core(const StepArgs& a, int i, int j, int k, u
         n2 = f.n2[c];
         n3 = f.n3[c];
     }
-    const float ie = f.inv_eps ? __ldg(f.inv_eps + c) : __ldg(f.lut_inv_eps + (m & 0x7f));
-    float ex1, ey1, ez1;
-    e_field_step<PML>(a, i, j, k, c, h, ie, ex0, ey0, ez0, jx, jy, jz, n, ex1, ey1, ez1);
-    f.ex[c] = ex1;
-    f.ey[c] = ey1;
-    f.ez[c] = ez1;
-    if (gain) {
-        population_step(a.gain, ex0, ey0, ez0, ex1, ey1, ez1, jx, jy, jz, n1, n2, n3);
-        f.n1[c] = n1;
-        f.n2[c] = n2;
-        f.n3[c] = n3;
-    }
-    if (FLUX && a.flux.on) flux_terms(a.flux, i, j, k, h, ex0, ey0, ez0, ex1, ey1, ez1, fl);
+    e_apply<FLUX, PML>(a, i, j, k, c, h, m, ex0, ey0, ez0, gain, jx, jy, jz, n1, n2, n3, n, fl);
 }
 
 template <bool FLUX>

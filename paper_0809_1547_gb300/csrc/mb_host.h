@@ -1,10 +1,13 @@
 // Host-side structures of the Maxwell–Bloch FDTD library (internal).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "mb_device.cuh"
@@ -36,11 +39,38 @@ struct DevFaceProbes {
 // each thread walks kz planes).
 constexpr int kVariant3D = 0;
 constexpr int kVariantZmarch = 1;
+constexpr int kVariantTma = 2;   // E pass only: TMA-staged z-walk (nx % 16 == 0)
 struct PassTune {
     int variant;
     dim3 block;
     int kz;
 };
+
+// Polls of a bounded mbarrier wait before the kernel gives up (~0.1-1 s).
+constexpr int kWaitLimit = 1 << 20;
+
+// Tensor maps of the TMA E pass: H boxes (BX+4) x (BY+1) (with the -x/-y
+// halo), E and material boxes BX x BY, one plane deep.
+struct TmaMapsE {
+    CUtensorMap hx, hy, hz, ex, ey, ez, mat;
+};
+
+// Shared-memory stage of the TMA E pass (each sub-buffer 128-byte aligned).
+template <int BX, int BY>
+struct TmaLayoutE {
+    static constexpr int kHW = (BX + 4) * (BY + 1);
+    static constexpr int kEW = BX * BY;
+    static constexpr int kHBytes = (kHW * 4 + 127) / 128 * 128;
+    static constexpr int kEBytes = (kEW * 4 + 127) / 128 * 128;
+    static constexpr int kMBytes = (kEW + 127) / 128 * 128;
+    static constexpr int kStage = 3 * kHBytes + 3 * kEBytes + kMBytes;
+    static constexpr int kTx = 3 * kHW * 4 + 3 * kEW * 4 + kEW;   // bytes per stage
+    static constexpr int smem_bytes(int stages) { return stages * kStage + 64 + 128; }
+};
+constexpr int kTmaStages = 3;
+
+bool tma_e_supported(const StepArgs& a);
+bool encode_tma_e(const StepArgs& a, int bx, int by, TmaMapsE* out);
 
 // Grid of the H + gain launch: nH H tiles (tile grid gx x gy x gz) and nG
 // gain blocks, each over q consecutive entries of the gain list.
@@ -52,7 +82,8 @@ struct HGLayout {
 
 HGLayout hg_layout(const StepArgs& a, const PassTune& t);
 void launch_h_pass(const StepArgs& a, const PassTune& t, cudaStream_t s);
-void launch_e_pass(const StepArgs& a, const PassTune& t, cudaStream_t s);
+// tma: tensor maps for t's tile shape when t.variant == kVariantTma
+void launch_e_pass(const StepArgs& a, const PassTune& t, const TmaMapsE* tma, cudaStream_t s);
 void launch_point_dft(const DevPointProbes& pp, const DevFields& f, const long long* ctr,
                       double dt, cudaStream_t s);
 void launch_face_dft(const DevFaceProbes& fp, const DevFields& f, const DevGrid& g,
@@ -131,6 +162,9 @@ struct mb_ctx {
     // per-step arguments
     mb::StepArgs args{};
     mb::DevSource src{};
+    float* d_src_wave = nullptr;       // tabulated source current
+    int* d_err = nullptr;              // device error flag (bounded waits)
+    std::map<std::pair<int, int>, mb::TmaMapsE> tma_maps;   // per TMA tile shape
     mb::PassTune tune_h{mb::kVariantZmarch, dim3(32, 8, 1), 16};
     mb::PassTune tune_e{mb::kVariantZmarch, dim3(32, 4, 1), 16};
 

@@ -13,8 +13,13 @@
 // registers.  Every variant composes the same per-cell helpers, so all of
 // them produce the same bits.
 #include "mb_host.h"
+#include "mb_tma.cuh"
+
+#include <cudaTypedefs.h>
 
 namespace mb {
+
+constexpr int kGainPerThread = 2;   // gain cells per thread in a gain block
 
 // Block b of the H + gain grid is a gain block (returns true, idx = its
 // index) or an H block (returns false, idx = its index).  Gain blocks are
@@ -36,12 +41,52 @@ __device__ __forceinline__ int linear_tid() {
     return threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
 }
 
+// A gain block advances q = kGainPerThread * threads consecutive entries of
+// the gain list; each thread loads all its cells before computing any, so
+// that several cells' loads are in flight at once.
 __device__ __forceinline__ void gain_block(const StepArgs& a, unsigned gidx, int q, long long n) {
     const int T = blockDim.x * blockDim.y * blockDim.z;
-    const uint32_t base = gidx * (uint32_t)q;
-    for (int r = linear_tid(); r < q; r += T) {
-        const uint32_t e = base + (uint32_t)r;
-        if (e < a.glist.count) gain_cell_step(a, __ldg(a.glist.cell + e), n);
+    const uint32_t base = gidx * (uint32_t)q + (uint32_t)linear_tid();
+    const DevFields& f = a.f;
+    uint32_t cs[kGainPerThread];
+    bool ok[kGainPerThread];
+#pragma unroll
+    for (int r = 0; r < kGainPerThread; ++r) {
+        const uint32_t e = base + (uint32_t)(r * T);
+        ok[r] = e < a.glist.count;
+        cs[r] = ok[r] ? __ldg(a.glist.cell + e) : 0u;
+    }
+    float ex[kGainPerThread], ey[kGainPerThread], ez[kGainPerThread], n1[kGainPerThread],
+        n2[kGainPerThread], px[kGainPerThread], py[kGainPerThread], pz[kGainPerThread],
+        jx[kGainPerThread], jy[kGainPerThread], jz[kGainPerThread];
+#pragma unroll
+    for (int r = 0; r < kGainPerThread; ++r) {
+        if (!ok[r]) continue;
+        const uint32_t c = cs[r];
+        ex[r] = __ldg(f.ex + c);
+        ey[r] = __ldg(f.ey + c);
+        ez[r] = __ldg(f.ez + c);
+        n1[r] = f.n1[c];
+        n2[r] = f.n2[c];
+        px[r] = f.px[c];
+        py[r] = f.py[c];
+        pz[r] = f.pz[c];
+        jx[r] = f.jx[c];
+        jy[r] = f.jy[c];
+        jz[r] = f.jz[c];
+    }
+#pragma unroll
+    for (int r = 0; r < kGainPerThread; ++r) {
+        if (!ok[r]) continue;
+        const uint32_t c = cs[r];
+        lorentz_step(a.gain, c, n, ex[r], ey[r], ez[r], n1[r], n2[r], jx[r], jy[r], jz[r], px[r],
+                     py[r], pz[r]);
+        f.jx[c] = jx[r];
+        f.jy[c] = jy[r];
+        f.jz[c] = jz[r];
+        f.px[c] = px[r];
+        f.py[c] = py[r];
+        f.pz[c] = pz[r];
     }
 }
 
@@ -101,7 +146,38 @@ __global__ void __launch_bounds__(512) k_hg_zmarch(StepArgs a, HGLayout lay, int
     const bool pml_xy = tile_in_xy_slab(a, bx * blockDim.x, blockDim.x, by * blockDim.y, blockDim.y);
     uint32_t c = (uint32_t)i + (uint32_t)nx * j + nxy * k0;
     float ex_c = __ldg(Ex + c), ey_c = __ldg(Ey + c);
-    for (int k = k0; k < k1; ++k, c += nxy) {
+    int k = k0;
+    // two planes per iteration: all loads of both are issued before either update
+    for (; k + 1 < k1; k += 2, c += 2 * nxy) {
+        ENb e0, e1;
+        const bool zk = k + 2 < nz;
+        e0.ex = ex_c;
+        e0.ey = ey_c;
+        e0.ez = __ldg(Ez + c);
+        e0.ex_k1 = __ldg(Ex + c + nxy);
+        e0.ey_k1 = __ldg(Ey + c + nxy);
+        e0.ex_j1 = yj ? __ldg(Ex + c + nx) : 0.0f;
+        e0.ey_i1 = xi ? __ldg(Ey + c + 1) : 0.0f;
+        e0.ez_i1 = xi ? __ldg(Ez + c + 1) : 0.0f;
+        e0.ez_j1 = yj ? __ldg(Ez + c + nx) : 0.0f;
+        const uint32_t c1 = c + nxy;
+        e1.ex = e0.ex_k1;
+        e1.ey = e0.ey_k1;
+        e1.ez = __ldg(Ez + c1);
+        e1.ex_k1 = zk ? __ldg(Ex + c1 + nxy) : 0.0f;
+        e1.ey_k1 = zk ? __ldg(Ey + c1 + nxy) : 0.0f;
+        e1.ex_j1 = yj ? __ldg(Ex + c1 + nx) : 0.0f;
+        e1.ey_i1 = xi ? __ldg(Ey + c1 + 1) : 0.0f;
+        e1.ez_i1 = xi ? __ldg(Ez + c1 + 1) : 0.0f;
+        e1.ez_j1 = yj ? __ldg(Ez + c1 + nx) : 0.0f;
+        if (pml_xy || plane_in_z_slab(a, k)) h_core<true>(a, i, j, k, c, e0);
+        else h_core<false>(a, i, j, k, c, e0);
+        if (pml_xy || plane_in_z_slab(a, k + 1)) h_core<true>(a, i, j, k + 1, c1, e1);
+        else h_core<false>(a, i, j, k + 1, c1, e1);
+        ex_c = e1.ex_k1;
+        ey_c = e1.ey_k1;
+    }
+    if (k < k1) {
         ENb e;
         const bool zk = k + 1 < nz;
         e.ex = ex_c;
@@ -115,8 +191,6 @@ __global__ void __launch_bounds__(512) k_hg_zmarch(StepArgs a, HGLayout lay, int
         e.ez_j1 = yj ? __ldg(Ez + c + nx) : 0.0f;
         if (pml_xy || plane_in_z_slab(a, k)) h_core<true>(a, i, j, k, c, e);
         else h_core<false>(a, i, j, k, c, e);
-        ex_c = e.ex_k1;
-        ey_c = e.ey_k1;
     }
 }
 
@@ -233,6 +307,139 @@ __global__ void __launch_bounds__(512, 2) k_e_zmarch(StepArgs a, int kz) {
     finish_step(a);
 }
 
+// ------------------------------------------------- TMA-staged E pass
+// 2-D tile of BX x BY cells walking kz planes.  One thread streams each
+// plane's H (with a -x / -y halo), E and material tiles into an S-slot
+// shared-memory ring with bulk tensor copies (cp.async.bulk.tensor) that
+// complete on per-slot mbarriers, S - 1 planes ahead of the compute.  The
+// -z neighbour plane of Hx, Hy stays in registers; J and n of gain cells
+// are loaded one plane ahead, once that plane's material tile has landed.
+template <int BX, int BY, int S>
+__global__ void __launch_bounds__(BX * BY) k_e_tma(StepArgs a, const __grid_constant__ TmaMapsE maps,
+                                                   int kz) {
+    using Lay = TmaLayoutE<BX, BY>;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + S * Lay::kStage);
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + BX * ty;
+    const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
+    const int i = x0 + tx, j = y0 + ty;
+    const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
+    const uint32_t nxy = a.g.nxy;
+    const bool valid = i < nx && j < ny;
+    const int k0 = blockIdx.z * kz, k1 = min(nz, k0 + kz);
+    const long long n = a.step_ctr[0];
+    const bool face = tile_on_face(a.flux, x0, x0 + BX, y0, y0 + BY, k0, k1);
+    const bool pml_xy = tile_in_xy_slab(a, x0, BX, y0, BY);
+    const bool gain_on = a.gain.on;
+    const DevFields& f = a.f;
+
+    auto issue = [&](int s, int k) {
+        unsigned char* p = smem + s * Lay::kStage;
+        mbar_arrive_expect_tx(&bar[s], Lay::kTx);
+        tma_load_3d(p + 0 * Lay::kHBytes, &maps.hx, x0 - 4, y0 - 1, k, &bar[s]);
+        tma_load_3d(p + 1 * Lay::kHBytes, &maps.hy, x0 - 4, y0 - 1, k, &bar[s]);
+        tma_load_3d(p + 2 * Lay::kHBytes, &maps.hz, x0 - 4, y0 - 1, k, &bar[s]);
+        unsigned char* q = p + 3 * Lay::kHBytes;
+        tma_load_3d(q + 0 * Lay::kEBytes, &maps.ex, x0, y0, k, &bar[s]);
+        tma_load_3d(q + 1 * Lay::kEBytes, &maps.ey, x0, y0, k, &bar[s]);
+        tma_load_3d(q + 2 * Lay::kEBytes, &maps.ez, x0, y0, k, &bar[s]);
+        tma_load_3d(q + 3 * Lay::kEBytes, &maps.mat, x0, y0, k, &bar[s]);
+    };
+    auto mat_of = [&](int s) -> uint8_t {
+        return (smem + s * Lay::kStage + 3 * Lay::kHBytes + 3 * Lay::kEBytes)[tid];
+    };
+
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) mbar_init(&bar[s], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (tid == 0)
+        for (int s = 0; s < S && k0 + s < k1; ++s) issue(s, k0 + s);
+
+    uint32_t c = valid ? (uint32_t)i + (uint32_t)nx * j + nxy * k0 : 0u;
+    float hx_km1 = 0.0f, hy_km1 = 0.0f;
+    if (valid && k0 > 0) {
+        hx_km1 = __ldg(f.hx + c - nxy);
+        hy_km1 = __ldg(f.hy + c - nxy);
+    }
+    bool fail = !mbar_wait_bounded(&bar[0], 0, kWaitLimit);
+    bool pg = valid && gain_on && (mat_of(0) & 0x80);
+    float pj[3] = {0.f, 0.f, 0.f}, pn[3] = {0.f, 0.f, 0.f};
+    if (pg) {
+        pj[0] = f.jx[c]; pj[1] = f.jy[c]; pj[2] = f.jz[c];
+        pn[0] = f.n1[c]; pn[1] = f.n2[c]; pn[2] = f.n3[c];
+    }
+    float fl[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int it = 0, k = k0; k < k1; ++it, ++k) {
+        const int s = it % S;
+        bool ng = false;
+        float nj[3] = {0.f, 0.f, 0.f}, nn[3] = {0.f, 0.f, 0.f};
+        if (k + 1 < k1) {
+            const int s1 = (it + 1) % S;
+            fail |= !mbar_wait_bounded(&bar[s1], ((it + 1) / S) & 1, kWaitLimit);
+            ng = valid && gain_on && (mat_of(s1) & 0x80);
+            if (ng) {
+                const uint32_t c1 = c + nxy;
+                nj[0] = f.jx[c1]; nj[1] = f.jy[c1]; nj[2] = f.jz[c1];
+                nn[0] = f.n1[c1]; nn[1] = f.n2[c1]; nn[2] = f.n3[c1];
+            }
+        }
+        if (valid && !fail) {
+            const unsigned char* p = smem + s * Lay::kStage;
+            const float* Hx = reinterpret_cast<const float*>(p);
+            const float* Hy = reinterpret_cast<const float*>(p + Lay::kHBytes);
+            const float* Hz = reinterpret_cast<const float*>(p + 2 * Lay::kHBytes);
+            const float* Ex = reinterpret_cast<const float*>(p + 3 * Lay::kHBytes);
+            const float* Ey = reinterpret_cast<const float*>(p + 3 * Lay::kHBytes + Lay::kEBytes);
+            const float* Ez = reinterpret_cast<const float*>(p + 3 * Lay::kHBytes + 2 * Lay::kEBytes);
+            const int hc = (ty + 1) * (BX + 4) + tx + 4;
+            HNb h;
+            h.hx = Hx[hc];
+            h.hy = Hy[hc];
+            h.hz = Hz[hc];
+            h.hy_i = Hy[hc - 1];
+            h.hz_i = Hz[hc - 1];
+            h.hx_j = Hx[hc - (BX + 4)];
+            h.hz_j = Hz[hc - (BX + 4)];
+            h.hx_k = hx_km1;
+            h.hy_k = hy_km1;
+            const uint8_t m = mat_of(s);
+            if (face)
+                e_apply<true, true>(a, i, j, k, c, h, m, Ex[tid], Ey[tid], Ez[tid], pg, pj[0], pj[1],
+                                    pj[2], pn[0], pn[1], pn[2], n, fl);
+            else if (pml_xy || plane_in_z_slab(a, k))
+                e_apply<false, true>(a, i, j, k, c, h, m, Ex[tid], Ey[tid], Ez[tid], pg, pj[0], pj[1],
+                                     pj[2], pn[0], pn[1], pn[2], n, fl);
+            else
+                e_apply<false, false>(a, i, j, k, c, h, m, Ex[tid], Ey[tid], Ez[tid], pg, pj[0],
+                                      pj[1], pj[2], pn[0], pn[1], pn[2], n, fl);
+            hx_km1 = h.hx;
+            hy_km1 = h.hy;
+        }
+        __syncthreads();   // slot s is free again
+        if (tid == 0 && k + S < k1) issue(s, k + S);
+        pg = ng;
+        pj[0] = nj[0]; pj[1] = nj[1]; pj[2] = nj[2];
+        pn[0] = nn[0]; pn[1] = nn[1]; pn[2] = nn[2];
+        c += nxy;
+    }
+    if (fail) {
+        // A wait gave up: record it, then give the copies still in flight a
+        // bounded chance to land before the block's shared memory is released.
+        if (tid == 0) atomicOr(a.err, 1);
+        const int planes = k1 - k0;
+        for (int s = 0; s < S && s < planes; ++s) {
+            const int uses = (planes - s + S - 1) / S;
+            mbar_wait_bounded(&bar[s], (uses - 1) & 1, kWaitLimit);
+        }
+    }
+    if (face) flux_warp_reduce(a.flux, fl, warp_slot());
+    finish_step(a);
+}
+
 // -------------------------------------------------------------- launchers
 
 HGLayout hg_layout(const StepArgs& a, const PassTune& t) {
@@ -243,7 +450,7 @@ HGLayout hg_layout(const StepArgs& a, const PassTune& t) {
     L.gz = (a.g.nz + zdiv - 1) / zdiv;
     L.nH = L.gx * L.gy * L.gz;
     const int threads = t.block.x * t.block.y * (t.variant == kVariantZmarch ? 1 : t.block.z);
-    L.q = threads * 4;
+    L.q = threads * kGainPerThread;
     L.nG = (a.gain.on && a.glist.count) ? (int)((a.glist.count + L.q - 1) / L.q) : 0;
     return L;
 }
@@ -258,7 +465,75 @@ void launch_h_pass(const StepArgs& a, const PassTune& t, cudaStream_t s) {
     }
 }
 
-void launch_e_pass(const StepArgs& a, const PassTune& t, cudaStream_t s) {
+template <int BX, int BY>
+static void launch_e_tma(const StepArgs& a, const PassTune& t, const TmaMapsE& maps, cudaStream_t s) {
+    const int smem = TmaLayoutE<BX, BY>::smem_bytes(kTmaStages);
+    static bool attr_set = false;   // per instantiation, once per process
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_e_tma<BX, BY, kTmaStages>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem);
+        attr_set = true;
+    }
+    dim3 grid((a.g.nx + BX - 1) / BX, (a.g.ny + BY - 1) / BY, (a.g.nz + t.kz - 1) / t.kz);
+    k_e_tma<BX, BY, kTmaStages><<<grid, dim3(BX, BY, 1), smem, s>>>(a, maps, t.kz);
+}
+
+bool tma_e_supported(const StepArgs& a) {
+    // 16-byte global strides for the float and the uint8 maps
+    return a.g.nx % 16 == 0;
+}
+
+// The driver's tensor-map encoder, found through the runtime (no libcuda link).
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+static bool encode_box(CUtensorMap* m, CUtensorMapDataType dt, const void* base, int esize,
+                       const DevGrid& g, int bw, int bh) {
+    auto enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
+    const cuuint64_t strides[2] = {(cuuint64_t)g.nx * esize, (cuuint64_t)g.nx * g.ny * esize};
+    const cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)bh, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return enc(m, dt, 3, const_cast<void*>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool encode_tma_e(const StepArgs& a, int bx, int by, TmaMapsE* out) {
+    if (!tma_e_supported(a)) return false;
+    const DevFields& f = a.f;
+    const CUtensorMapDataType F32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    bool ok = encode_box(&out->hx, F32, f.hx, 4, a.g, bx + 4, by + 1) &&
+              encode_box(&out->hy, F32, f.hy, 4, a.g, bx + 4, by + 1) &&
+              encode_box(&out->hz, F32, f.hz, 4, a.g, bx + 4, by + 1) &&
+              encode_box(&out->ex, F32, f.ex, 4, a.g, bx, by) &&
+              encode_box(&out->ey, F32, f.ey, 4, a.g, bx, by) &&
+              encode_box(&out->ez, F32, f.ez, 4, a.g, bx, by) &&
+              encode_box(&out->mat, CU_TENSOR_MAP_DATA_TYPE_UINT8, f.mat, 1, a.g, bx, by);
+    return ok;
+}
+
+void launch_e_pass(const StepArgs& a, const PassTune& t, const TmaMapsE* tma, cudaStream_t s) {
+    if (t.variant == kVariantTma && tma) {
+        const int bx = t.block.x, by = t.block.y;
+        if (bx == 32 && by == 4) return launch_e_tma<32, 4>(a, t, *tma, s);
+        if (bx == 32 && by == 8) return launch_e_tma<32, 8>(a, t, *tma, s);
+        if (bx == 64 && by == 4) return launch_e_tma<64, 4>(a, t, *tma, s);
+        if (bx == 64 && by == 8) return launch_e_tma<64, 8>(a, t, *tma, s);
+        if (bx == 128 && by == 2) return launch_e_tma<128, 2>(a, t, *tma, s);
+        if (bx == 128 && by == 4) return launch_e_tma<128, 4>(a, t, *tma, s);
+    }
     if (t.variant == kVariantZmarch) {
         dim3 grid((a.g.nx + t.block.x - 1) / t.block.x, (a.g.ny + t.block.y - 1) / t.block.y,
                   (a.g.nz + t.kz - 1) / t.kz);
