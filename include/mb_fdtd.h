@@ -195,9 +195,14 @@ int mb_load_state(mb_ctx* ctx, const void* host_blob, size_t bytes);
 int mb_autotune(mb_ctx* ctx);
 
 /* Launch shape of the H pass and of the E pass, as {variant, bx, by, bz}:
- * variant 0 = one thread per cell in (bx, by, bz) blocks; variant 1 = 2-D
- * (bx, by) blocks whose threads each walk bz planes along z.  Read the
- * current choice or set one (bx a multiple of 32, at most 512 threads). */
+ * variant 0 = one thread per cell in (bx, by, bz) blocks; 1 = 2-D (bx, by)
+ * blocks whose threads each walk bz planes along z; 2 (E pass only, n_x a
+ * multiple of 16) = the same walk with the planes staged in shared memory
+ * by bulk tensor copies (TMA), tiles 32x4, 32x8, 64x4, 64x8, 128x2, 128x4;
+ * 3 (n_x a multiple of 4) = the walk over quads of 4 x-cells with 16-byte
+ * accesses, bx counting quads.  Every variant gives the same bits.  Read
+ * the current choice or set one (bx a multiple of 32, at most 512 threads,
+ * 256 for variant 3). */
 int mb_get_tuning(mb_ctx* ctx, int tune_h[4], int tune_e[4]);
 int mb_set_tuning(mb_ctx* ctx, const int tune_h[4], const int tune_e[4]);
 

@@ -22,7 +22,9 @@ LIB_NAME = "libmbfdtd.so"
 LIB_PATH = os.path.join(PKG, LIB_NAME)
 
 ARCH_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3",
+# -fmad=false: every fused multiply-add in the kernels is an explicit fmaf, so
+# all launch variants of a cell update round identically.
+CU_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3",
             "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
 
 

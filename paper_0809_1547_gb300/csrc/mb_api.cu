@@ -969,6 +969,10 @@ int mb_autotune(mb_ctx* c) {
     for (dim3 b : {dim3(32, 4, 1), dim3(32, 8, 1), dim3(64, 4, 1), dim3(64, 2, 1), dim3(128, 2, 1),
                    dim3(32, 16, 1), dim3(64, 8, 1), dim3(128, 4, 1), dim3(256, 1, 1)})
         for (int kz : {4, 8, 16, 32}) cands.push_back({mb::kVariantZmarch, b, kz});
+    if (mb::vec_supported(c->args))
+        for (dim3 b : {dim3(32, 2, 1), dim3(32, 4, 1), dim3(32, 8, 1), dim3(64, 2, 1), dim3(64, 4, 1),
+                       dim3(128, 2, 1)})
+            for (int kz : {4, 8, 16, 32}) cands.push_back({mb::kVariantVec, b, kz});
     std::vector<mb::PassTune> cands_e_only;
     if (mb::tma_e_supported(c->args))
         for (dim3 b : {dim3(32, 4, 1), dim3(32, 8, 1), dim3(64, 4, 1), dim3(64, 8, 1), dim3(128, 2, 1),
@@ -981,7 +985,7 @@ int mb_autotune(mb_ctx* c) {
     mb::PassTune bh = c->tune_h, be = c->tune_e;
     const int reps = c->ncell > 4000000 ? 2 : 6;
     for (const mb::PassTune& t : cands) {
-        if (t.variant == mb::kVariantZmarch && t.kz > 2 * c->nz) continue;
+        if (t.variant != mb::kVariant3D && t.kz > 2 * c->nz) continue;
         for (int pass = 0; pass < 2; ++pass) {
             if (pass == 0) mb::launch_h_pass(c->args, t, c->stream);
             else mb::launch_e_pass(c->args, t, tma_for(c, t), c->stream);
@@ -1040,7 +1044,7 @@ int mb_get_tuning(mb_ctx* c, int tune_h[4], int tune_e[4]) {
         dst[q][0] = src[q]->variant;
         dst[q][1] = src[q]->block.x;
         dst[q][2] = src[q]->block.y;
-        dst[q][3] = src[q]->variant == mb::kVariantZmarch ? src[q]->kz : src[q]->block.z;
+        dst[q][3] = src[q]->variant == mb::kVariant3D ? (int)src[q]->block.z : src[q]->kz;
     }
     return MB_OK;
 }
@@ -1053,12 +1057,16 @@ int mb_set_tuning(mb_ctx* c, const int tune_h[4], const int tune_e[4]) {
     for (int q = 0; q < 2; ++q) {
         const int* b = src[q];
         const bool tma = b[0] == mb::kVariantTma;
-        if ((b[0] != mb::kVariant3D && b[0] != mb::kVariantZmarch && !(tma && q == 1)) ||
+        const bool vec = b[0] == mb::kVariantVec;
+        if (vec && !mb::vec_supported(c->args))
+            return fail(c, MB_ERR_ARG, "the quad-vectorised passes need n_x % 4 == 0");
+        if ((b[0] != mb::kVariant3D && b[0] != mb::kVariantZmarch && !vec && !(tma && q == 1)) ||
             b[1] < 32 || b[1] % 32 || b[2] < 1 || b[3] < 1)
             return fail(c, MB_ERR_ARG,
                         "bad tuning: variant 0/1 (2 for the E pass), x a multiple of 32, y, z >= 1");
         const int threads = b[1] * b[2] * (b[0] == mb::kVariant3D ? b[3] : 1);
-        if (threads > 512) return fail(c, MB_ERR_ARG, "at most 512 threads per block");
+        if (threads > (vec ? 256 : 512))
+            return fail(c, MB_ERR_ARG, "at most 512 threads per block (256 for the quad variant)");
         t[q].variant = b[0];
         t[q].block = dim3(b[1], b[2], b[0] == mb::kVariant3D ? b[3] : 1);
         t[q].kz = b[0] == mb::kVariant3D ? 1 : b[3];

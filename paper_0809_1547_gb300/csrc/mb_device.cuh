@@ -2,7 +2,9 @@
 // of the two field passes.  Every kernel that advances a realization (the
 // plain step in all its launch variants, the batched ensemble, the adjoint's
 // forward recomputation) composes the same helpers below, so their results
-// agree bit for bit.
+// agree bit for bit.  The library is compiled with -fmad=false: every fused
+// multiply-add is an explicit fmaf, so no kernel's inlining context can
+// change the rounding.
 //
 // Units on the device are scaled so that FP32 stays far from under/overflow:
 //   E_s = E/E0, H_s = eta0 H/E0, P_s = P/(eps0 E0), J_s = J dt/(eps0 E0),
@@ -224,8 +226,8 @@ __device__ __forceinline__ void h_pml(const StepArgs& a, int i, int j, int k, co
         const uint32_t q = ((uint32_t)k * ny + j) * L2 + s;
         const float b = __ldg(a.pml.bhx + i), cc = __ldg(a.pml.chx + i);
         float* p = a.pml.psx;
-        const float psi_yx = b * p[q + 2 * plane] + cc * d[3];   // Hy: d/dx Ez
-        const float psi_zx = b * p[q + 3 * plane] + cc * d[4];   // Hz: d/dx Ey
+        const float psi_yx = fmaf(b, p[q + 2 * plane], cc * d[3]);   // Hy: d/dx Ez
+        const float psi_zx = fmaf(b, p[q + 3 * plane], cc * d[4]);   // Hz: d/dx Ey
         p[q + 2 * plane] = psi_yx;
         p[q + 3 * plane] = psi_zx;
         cy -= psi_yx;
@@ -237,8 +239,8 @@ __device__ __forceinline__ void h_pml(const StepArgs& a, int i, int j, int k, co
         const uint32_t q = ((uint32_t)k * L2 + s) * nx + i;
         const float b = __ldg(a.pml.bhy + j), cc = __ldg(a.pml.chy + j);
         float* p = a.pml.psy;
-        const float psi_xy = b * p[q + 2 * plane] + cc * d[0];   // Hx: d/dy Ez
-        const float psi_zy = b * p[q + 3 * plane] + cc * d[5];   // Hz: d/dy Ex
+        const float psi_xy = fmaf(b, p[q + 2 * plane], cc * d[0]);   // Hx: d/dy Ez
+        const float psi_zy = fmaf(b, p[q + 3 * plane], cc * d[5]);   // Hz: d/dy Ex
         p[q + 2 * plane] = psi_xy;
         p[q + 3 * plane] = psi_zy;
         cx += psi_xy;
@@ -250,8 +252,8 @@ __device__ __forceinline__ void h_pml(const StepArgs& a, int i, int j, int k, co
         const uint32_t q = (s * ny + j) * nx + i;
         const float b = __ldg(a.pml.bhz + k), cc = __ldg(a.pml.chz + k);
         float* p = a.pml.psz;
-        const float psi_xz = b * p[q + 2 * plane] + cc * d[1];   // Hx: d/dz Ey
-        const float psi_yz = b * p[q + 3 * plane] + cc * d[2];   // Hy: d/dz Ex
+        const float psi_xz = fmaf(b, p[q + 2 * plane], cc * d[1]);   // Hx: d/dz Ey
+        const float psi_yz = fmaf(b, p[q + 3 * plane], cc * d[2]);   // Hy: d/dz Ex
         p[q + 2 * plane] = psi_xz;
         p[q + 3 * plane] = psi_yz;
         cx -= psi_xz;
@@ -259,12 +261,12 @@ __device__ __forceinline__ void h_pml(const StepArgs& a, int i, int j, int k, co
     }
 }
 
-// H^{n+1/2} = H^{n-1/2} - S (curl_fwd E^n + psi_H) for cell c = (i, j, k).
-// PML: the cell may lie in a CPML slab (false only when it surely does not).
+// H^{n+1/2} = H^{n-1/2} - S (curl_fwd E^n + psi_H) for cell (i, j, k), on
+// H values held in registers.  PML: the cell may lie in a CPML slab (false
+// only when it surely does not).
 template <bool PML>
-__device__ __forceinline__ void h_core(const StepArgs& a, int i, int j, int k, uint32_t c,
-                                       const ENb& e) {
-    const DevFields& f = a.f;
+__device__ __forceinline__ void h_compute(const StepArgs& a, int i, int j, int k, const ENb& e,
+                                          float& hx, float& hy, float& hz) {
     float d[6];
     d[0] = e.ez_j1 - e.ez;   // dEz_dy
     d[1] = e.ey_k1 - e.ey;   // dEy_dz
@@ -277,9 +279,21 @@ __device__ __forceinline__ void h_core(const StepArgs& a, int i, int j, int k, u
     float cz = d[4] - d[5];
     if (PML && a.pml.L > 0) h_pml(a, i, j, k, d, cx, cy, cz);
     const float S = a.S;
-    f.hx[c] = f.hx[c] - S * cx;
-    f.hy[c] = f.hy[c] - S * cy;
-    f.hz[c] = f.hz[c] - S * cz;
+    hx = fmaf(-S, cx, hx);
+    hy = fmaf(-S, cy, hy);
+    hz = fmaf(-S, cz, hz);
+}
+
+// The same update read from and written to global memory at cell c.
+template <bool PML>
+__device__ __forceinline__ void h_core(const StepArgs& a, int i, int j, int k, uint32_t c,
+                                       const ENb& e) {
+    const DevFields& f = a.f;
+    float hx = f.hx[c], hy = f.hy[c], hz = f.hz[c];
+    h_compute<PML>(a, i, j, k, e, hx, hy, hz);
+    f.hx[c] = hx;
+    f.hy[c] = hy;
+    f.hz[c] = hz;
 }
 
 __device__ __forceinline__ void h_update_cell(const StepArgs& a, int i, int j, int k) {
@@ -304,9 +318,10 @@ __device__ __forceinline__ void lorentz_step(const DevGain& G, uint32_t c, long 
     const float amp = G.cJN * sqrtf(fmaxf(n2, 0.0f) + G.nfloor);
     float z0, z1, z2;
     langevin_normals(c, (uint32_t)n, G.key0, G.key1, z0, z1, z2);
-    jx = G.cJ1 * jx + G.cJE * dn * ex0 - G.cJP * px + amp * z0;
-    jy = G.cJ1 * jy + G.cJE * dn * ey0 - G.cJP * py + amp * z1;
-    jz = G.cJ1 * jz + G.cJE * dn * ez0 - G.cJP * pz + amp * z2;
+    const float kE = G.cJE * dn;
+    jx = fmaf(amp, z0, fmaf(-G.cJP, px, fmaf(kE, ex0, G.cJ1 * jx)));
+    jy = fmaf(amp, z1, fmaf(-G.cJP, py, fmaf(kE, ey0, G.cJ1 * jy)));
+    jz = fmaf(amp, z2, fmaf(-G.cJP, pz, fmaf(kE, ez0, G.cJ1 * jz)));
     px = px + jx;
     py = py + jy;
     pz = pz + jz;
@@ -317,10 +332,15 @@ __device__ __forceinline__ void population_step(const DevGain& G, float ex0, flo
                                                 float ex1, float ey1, float ez1, float jx,
                                                 float jy, float jz, float& n1, float& n2,
                                                 float& n3) {
-    const float sp = 0.5f * ((ex0 + ex1) * jx + (ey0 + ey1) * jy + (ez0 + ez1) * jz);
-    const float a1 = n1 + (G.g[0] + G.G[0][0] * n1 + G.G[0][1] * n2 + G.G[0][2] * n3 + G.mk[0] * sp);
-    const float a2 = n2 + (G.g[1] + G.G[1][0] * n1 + G.G[1][1] * n2 + G.G[1][2] * n3 + G.mk[1] * sp);
-    const float a3 = n3 + (G.g[2] + G.G[2][0] * n1 + G.G[2][1] * n2 + G.G[2][2] * n3 + G.mk[2] * sp);
+    const float sp =
+        0.5f * fmaf(ez0 + ez1, jz, fmaf(ey0 + ey1, jy, (ex0 + ex1) * jx));
+    float d[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+        d[r] = fmaf(G.mk[r], sp, fmaf(G.G[r][2], n3, fmaf(G.G[r][1], n2, fmaf(G.G[r][0], n1, G.g[r]))));
+    const float a1 = n1 + d[0];
+    const float a2 = n2 + d[1];
+    const float a3 = n3 + d[2];
     n1 = a1;
     n2 = a2;
     n3 = a3;
@@ -340,8 +360,8 @@ __device__ __forceinline__ void e_pml(const StepArgs& a, int i, int j, int k, co
         const uint32_t q = ((uint32_t)k * ny + j) * L2 + s;
         const float b = __ldg(a.pml.bex + i), cc = __ldg(a.pml.cex + i);
         float* p = a.pml.psx;
-        const float psi_yx = b * p[q] + cc * d[3];            // Ey: d/dx Hz
-        const float psi_zx = b * p[q + plane] + cc * d[4];    // Ez: d/dx Hy
+        const float psi_yx = fmaf(b, p[q], cc * d[3]);            // Ey: d/dx Hz
+        const float psi_zx = fmaf(b, p[q + plane], cc * d[4]);    // Ez: d/dx Hy
         p[q] = psi_yx;
         p[q + plane] = psi_zx;
         cy -= psi_yx;
@@ -353,8 +373,8 @@ __device__ __forceinline__ void e_pml(const StepArgs& a, int i, int j, int k, co
         const uint32_t q = ((uint32_t)k * L2 + s) * nx + i;
         const float b = __ldg(a.pml.bey + j), cc = __ldg(a.pml.cey + j);
         float* p = a.pml.psy;
-        const float psi_xy = b * p[q] + cc * d[0];            // Ex: d/dy Hz
-        const float psi_zy = b * p[q + plane] + cc * d[5];    // Ez: d/dy Hx
+        const float psi_xy = fmaf(b, p[q], cc * d[0]);            // Ex: d/dy Hz
+        const float psi_zy = fmaf(b, p[q + plane], cc * d[5]);    // Ez: d/dy Hx
         p[q] = psi_xy;
         p[q + plane] = psi_zy;
         cx += psi_xy;
@@ -366,8 +386,8 @@ __device__ __forceinline__ void e_pml(const StepArgs& a, int i, int j, int k, co
         const uint32_t q = (s * ny + j) * nx + i;
         const float b = __ldg(a.pml.bez + k), cc = __ldg(a.pml.cez + k);
         float* p = a.pml.psz;
-        const float psi_xz = b * p[q] + cc * d[1];            // Ex: d/dz Hy
-        const float psi_yz = b * p[q + plane] + cc * d[2];    // Ey: d/dz Hx
+        const float psi_xz = fmaf(b, p[q], cc * d[1]);            // Ex: d/dz Hy
+        const float psi_yz = fmaf(b, p[q + plane], cc * d[2]);    // Ey: d/dz Hx
         p[q] = psi_xz;
         p[q + plane] = psi_yz;
         cx -= psi_xz;
@@ -400,9 +420,9 @@ __device__ __forceinline__ void e_field_step(const StepArgs& a, int i, int j, in
         else sz += v;
     }
     const float S = a.S;
-    ex1 = ex0 + ie * (S * cx - sx);
-    ey1 = ey0 + ie * (S * cy - sy);
-    ez1 = ez0 + ie * (S * cz - sz);
+    ex1 = fmaf(ie, fmaf(S, cx, -sx), ex0);
+    ey1 = fmaf(ie, fmaf(S, cy, -sy), ey0);
+    ez1 = fmaf(ie, fmaf(S, cz, -sz), ez0);
     // PEC walls: tangential E on the planes i = 0, j = 0, k = 0.
     if (j == 0 || k == 0) ex1 = 0.0f;
     if (i == 0 || k == 0) ey1 = 0.0f;
@@ -416,17 +436,17 @@ __device__ __forceinline__ void flux_terms(const DevFlux& F, int i, int j, int k
                                            float ez1, float fl[6]) {
     const float mx = 0.5f * (ex0 + ex1), my = 0.5f * (ey0 + ey1), mz = 0.5f * (ez0 + ez1);
     if (j >= F.r0[1] && j < F.r1[1] && k >= F.r0[2] && k < F.r1[2]) {
-        const float s = my * h.hz_i - mz * h.hy_i;
+        const float s = fmaf(my, h.hz_i, -(mz * h.hy_i));
         if (i == F.plo[0]) fl[0] -= s;
         if (i == F.phi[0]) fl[1] += s;
     }
     if (i >= F.r0[0] && i < F.r1[0] && k >= F.r0[2] && k < F.r1[2]) {
-        const float s = mz * h.hx_j - mx * h.hz_j;
+        const float s = fmaf(mz, h.hx_j, -(mx * h.hz_j));
         if (j == F.plo[1]) fl[2] -= s;
         if (j == F.phi[1]) fl[3] += s;
     }
     if (i >= F.r0[0] && i < F.r1[0] && j >= F.r0[1] && j < F.r1[1]) {
-        const float s = mx * h.hy_k - my * h.hx_k;
+        const float s = fmaf(mx, h.hy_k, -(my * h.hx_k));
         if (k == F.plo[2]) fl[4] -= s;
         if (k == F.phi[2]) fl[5] += s;
     }
@@ -456,25 +476,38 @@ __device__ __forceinline__ void gain_cell_step(const StepArgs& a, uint32_t c, lo
 // with the current J^{n+1/2}, then N^{n+1}; with FLUX, the face-flux terms.
 // The E / population update of cell c from its loaded inputs: material byte
 // m, E^n, and for gain cells J^{n+1/2} and n1..n3 at time n.
+// In registers: E^{n+1} into ex1..ez1 and, for gain cells, N^{n+1} into
+// n1..n3 (in place); face-flux terms into fl with FLUX.
+template <bool FLUX, bool PML>
+__device__ __forceinline__ void e_compute(const StepArgs& a, int i, int j, int k, uint32_t c,
+                                          const HNb& h, uint8_t m, float ex0, float ey0, float ez0,
+                                          bool gain, float jx, float jy, float jz, float& n1,
+                                          float& n2, float& n3, long long n, float fl[6],
+                                          float& ex1, float& ey1, float& ez1) {
+    const DevFields& f = a.f;
+    const float ie = f.inv_eps ? __ldg(f.inv_eps + c) : __ldg(f.lut_inv_eps + (m & 0x7f));
+    e_field_step<PML>(a, i, j, k, c, h, ie, ex0, ey0, ez0, jx, jy, jz, n, ex1, ey1, ez1);
+    if (gain) population_step(a.gain, ex0, ey0, ez0, ex1, ey1, ez1, jx, jy, jz, n1, n2, n3);
+    if (FLUX && a.flux.on) flux_terms(a.flux, i, j, k, h, ex0, ey0, ez0, ex1, ey1, ez1, fl);
+}
+
 template <bool FLUX, bool PML>
 __device__ __forceinline__ void e_apply(const StepArgs& a, int i, int j, int k, uint32_t c,
                                         const HNb& h, uint8_t m, float ex0, float ey0, float ez0,
                                         bool gain, float jx, float jy, float jz, float n1, float n2,
                                         float n3, long long n, float fl[6]) {
     const DevFields& f = a.f;
-    const float ie = f.inv_eps ? __ldg(f.inv_eps + c) : __ldg(f.lut_inv_eps + (m & 0x7f));
     float ex1, ey1, ez1;
-    e_field_step<PML>(a, i, j, k, c, h, ie, ex0, ey0, ez0, jx, jy, jz, n, ex1, ey1, ez1);
+    e_compute<FLUX, PML>(a, i, j, k, c, h, m, ex0, ey0, ez0, gain, jx, jy, jz, n1, n2, n3, n, fl,
+                         ex1, ey1, ez1);
     f.ex[c] = ex1;
     f.ey[c] = ey1;
     f.ez[c] = ez1;
     if (gain) {
-        population_step(a.gain, ex0, ey0, ez0, ex1, ey1, ez1, jx, jy, jz, n1, n2, n3);
         f.n1[c] = n1;
         f.n2[c] = n2;
         f.n3[c] = n3;
     }
-    if (FLUX && a.flux.on) flux_terms(a.flux, i, j, k, h, ex0, ey0, ez0, ex1, ey1, ez1, fl);
 }
 
 template <bool FLUX, bool PML>

@@ -40,6 +40,7 @@ struct DevFaceProbes {
 constexpr int kVariant3D = 0;
 constexpr int kVariantZmarch = 1;
 constexpr int kVariantTma = 2;   // E pass only: TMA-staged z-walk (nx % 16 == 0)
+constexpr int kVariantVec = 3;   // z-walk over quads of 4 x-cells, 16-byte accesses (nx % 4 == 0)
 struct PassTune {
     int variant;
     dim3 block;
@@ -70,6 +71,7 @@ struct TmaLayoutE {
 constexpr int kTmaStages = 3;
 
 bool tma_e_supported(const StepArgs& a);
+bool vec_supported(const StepArgs& a);
 bool encode_tma_e(const StepArgs& a, int bx, int by, TmaMapsE* out);
 
 // Grid of the H + gain launch: nH H tiles (tile grid gx x gy x gz) and nG

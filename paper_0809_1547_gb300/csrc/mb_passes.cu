@@ -307,6 +307,202 @@ __global__ void __launch_bounds__(512, 2) k_e_zmarch(StepArgs a, int kz) {
     finish_step(a);
 }
 
+// ----------------------------------------------- quad-vectorised z-walks
+// Each thread owns a quad of 4 consecutive x-cells (n_x % 4 == 0, so quads
+// are 16-byte aligned) and moves them with 16-byte loads and stores, which
+// stream at the full HBM rate where 4-byte accesses do not.  Warps lie along
+// x: the +x (-x) neighbour of a quad's last (first) cell is the next
+// (previous) lane's first (last) element, exchanged by shuffle; lane 31
+// (lane 0) reads it from memory.  Lanes past the grid edge still take part
+// in the shuffles with zeros.
+
+__device__ __forceinline__ float4 ldg4(const float* p) {
+    return __ldg(reinterpret_cast<const float4*>(p));
+}
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+__device__ __forceinline__ float& el(float4& v, int q) { return reinterpret_cast<float*>(&v)[q]; }
+__device__ __forceinline__ float elc(const float4& v, int q) {
+    return reinterpret_cast<const float*>(&v)[q];
+}
+
+__global__ void __launch_bounds__(256) k_hg_vec(StepArgs a, HGLayout lay, int kz) {
+    const long long n = a.step_ctr[0];
+    unsigned idx;
+    if (hg_block_kind(lay, blockIdx.x, idx)) {
+        gain_block(a, idx, lay.q, n);
+        return;
+    }
+    const unsigned full = 0xffffffffu;
+    const int bx = idx % lay.gx, by = (idx / lay.gx) % lay.gy, bz = idx / (lay.gx * lay.gy);
+    const int lane = threadIdx.x & 31;
+    const int i0 = 4 * (bx * blockDim.x + threadIdx.x);
+    const int j = by * blockDim.y + threadIdx.y;
+    const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
+    const bool valid = i0 < nx && j < ny;
+    const bool yj = j + 1 < ny;
+    const int k0 = bz * kz;
+    const int k1 = min(nz, k0 + kz);
+    const uint32_t nxy = a.g.nxy;
+    const DevFields& f = a.f;
+    const bool pml_xy = tile_in_xy_slab(a, 4 * bx * blockDim.x, 4 * blockDim.x, by * blockDim.y, blockDim.y);
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    uint32_t c = valid ? (uint32_t)i0 + (uint32_t)nx * j + nxy * k0 : 0u;
+    float4 ex = valid ? ldg4(f.ex + c) : zero, ey = valid ? ldg4(f.ey + c) : zero;
+    for (int k = k0; k < k1; ++k, c += nxy) {
+        const bool zk = k + 1 < nz;
+        const float4 ez = valid ? ldg4(f.ez + c) : zero;
+        const float4 exk = (valid && zk) ? ldg4(f.ex + c + nxy) : zero;
+        const float4 eyk = (valid && zk) ? ldg4(f.ey + c + nxy) : zero;
+        const float4 exj = (valid && yj) ? ldg4(f.ex + c + nx) : zero;
+        const float4 ezj = (valid && yj) ? ldg4(f.ez + c + nx) : zero;
+        float ey_n = __shfl_down_sync(full, ey.x, 1);
+        float ez_n = __shfl_down_sync(full, ez.x, 1);
+        const bool xn = i0 + 4 < nx;
+        if (lane == 31) {
+            ey_n = (valid && xn) ? __ldg(f.ey + c + 4) : 0.0f;
+            ez_n = (valid && xn) ? __ldg(f.ez + c + 4) : 0.0f;
+        } else if (!xn) {
+            ey_n = 0.0f;
+            ez_n = 0.0f;
+        }
+        if (valid) {
+            float4 hx = ld4(f.hx + c), hy = ld4(f.hy + c), hz = ld4(f.hz + c);
+            const bool pml = pml_xy || plane_in_z_slab(a, k);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                ENb e;
+                e.ex = elc(ex, q);
+                e.ey = elc(ey, q);
+                e.ez = elc(ez, q);
+                e.ex_j1 = elc(exj, q);
+                e.ex_k1 = elc(exk, q);
+                e.ey_i1 = q < 3 ? elc(ey, q + 1) : ey_n;
+                e.ey_k1 = elc(eyk, q);
+                e.ez_i1 = q < 3 ? elc(ez, q + 1) : ez_n;
+                e.ez_j1 = elc(ezj, q);
+                if (pml) h_compute<true>(a, i0 + q, j, k, e, el(hx, q), el(hy, q), el(hz, q));
+                else h_compute<false>(a, i0 + q, j, k, e, el(hx, q), el(hy, q), el(hz, q));
+            }
+            st4(f.hx + c, hx);
+            st4(f.hy + c, hy);
+            st4(f.hz + c, hz);
+        }
+        ex = exk;
+        ey = eyk;
+    }
+}
+
+// The four cells of one quad: E^{n+1} into ex1..ez1, populations in place.
+template <bool FACE, bool PML>
+__device__ __forceinline__ void e_quad(const StepArgs& a, int i0, int j, int k, uint32_t c,
+                                       const float4& hx, const float4& hy, const float4& hz,
+                                       const float4& hxj, const float4& hzj, const float4& hxk,
+                                       const float4& hyk, float hy_p, float hz_p, const float4& ex,
+                                       const float4& ey, const float4& ez, uint32_t m4,
+                                       const float4& jx, const float4& jy, const float4& jz,
+                                       float4& n1, float4& n2, float4& n3, long long n, float fl[6],
+                                       float4& ex1, float4& ey1, float4& ez1) {
+    const bool gain_on = a.gain.on;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        HNb h;
+        h.hx = elc(hx, q);
+        h.hy = elc(hy, q);
+        h.hz = elc(hz, q);
+        h.hx_j = elc(hxj, q);
+        h.hx_k = elc(hxk, q);
+        h.hy_i = q > 0 ? elc(hy, q - 1) : hy_p;
+        h.hy_k = elc(hyk, q);
+        h.hz_i = q > 0 ? elc(hz, q - 1) : hz_p;
+        h.hz_j = elc(hzj, q);
+        const uint8_t m = (uint8_t)(m4 >> (8 * q));
+        const bool g = gain_on && (m & 0x80);
+        e_compute<FACE, PML>(a, i0 + q, j, k, c + q, h, m, elc(ex, q), elc(ey, q), elc(ez, q), g,
+                             g ? elc(jx, q) : 0.0f, g ? elc(jy, q) : 0.0f, g ? elc(jz, q) : 0.0f,
+                             el(n1, q), el(n2, q), el(n3, q), n, fl, el(ex1, q), el(ey1, q),
+                             el(ez1, q));
+    }
+}
+
+template <bool FACE>
+__device__ __forceinline__ void e_vec_walk(const StepArgs& a, int i0, int j, int k0, int k1, bool valid,
+                                           bool pml_xy, long long n, float fl[6]) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int nx = a.g.nx;
+    const uint32_t nxy = a.g.nxy;
+    const DevFields& f = a.f;
+    const bool gain_on = a.gain.on;
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    uint32_t c = valid ? (uint32_t)i0 + (uint32_t)nx * j + nxy * k0 : 0u;
+    float4 hxk = (valid && k0 > 0) ? ldg4(f.hx + c - nxy) : zero;
+    float4 hyk = (valid && k0 > 0) ? ldg4(f.hy + c - nxy) : zero;
+    for (int k = k0; k < k1; ++k, c += nxy) {
+        const float4 hx = valid ? ldg4(f.hx + c) : zero;
+        const float4 hy = valid ? ldg4(f.hy + c) : zero;
+        const float4 hz = valid ? ldg4(f.hz + c) : zero;
+        const float4 hxj = (valid && j > 0) ? ldg4(f.hx + c - nx) : zero;
+        const float4 hzj = (valid && j > 0) ? ldg4(f.hz + c - nx) : zero;
+        float hy_p = __shfl_up_sync(full, hy.w, 1);
+        float hz_p = __shfl_up_sync(full, hz.w, 1);
+        if (lane == 0) {
+            hy_p = (valid && i0 > 0) ? __ldg(f.hy + c - 1) : 0.0f;
+            hz_p = (valid && i0 > 0) ? __ldg(f.hz + c - 1) : 0.0f;
+        }
+        if (valid) {
+            const float4 ex = ld4(f.ex + c), ey = ld4(f.ey + c), ez = ld4(f.ez + c);
+            const uint32_t m4 = __ldg(reinterpret_cast<const uint32_t*>(f.mat + c));
+            const bool any_gain = gain_on && (m4 & 0x80808080u);
+            float4 jx = zero, jy = zero, jz = zero, n1 = zero, n2 = zero, n3 = zero;
+            if (any_gain) {
+                jx = ld4(f.jx + c); jy = ld4(f.jy + c); jz = ld4(f.jz + c);
+                n1 = ld4(f.n1 + c); n2 = ld4(f.n2 + c); n3 = ld4(f.n3 + c);
+            }
+            float4 ex1, ey1, ez1;
+            if (FACE || pml_xy || plane_in_z_slab(a, k))
+                e_quad<FACE, true>(a, i0, j, k, c, hx, hy, hz, hxj, hzj, hxk, hyk, hy_p, hz_p, ex, ey,
+                                   ez, m4, jx, jy, jz, n1, n2, n3, n, fl, ex1, ey1, ez1);
+            else
+                e_quad<false, false>(a, i0, j, k, c, hx, hy, hz, hxj, hzj, hxk, hyk, hy_p, hz_p, ex,
+                                     ey, ez, m4, jx, jy, jz, n1, n2, n3, n, fl, ex1, ey1, ez1);
+            st4(f.ex + c, ex1);
+            st4(f.ey + c, ey1);
+            st4(f.ez + c, ez1);
+            if (any_gain) {
+                st4(f.n1 + c, n1);
+                st4(f.n2 + c, n2);
+                st4(f.n3 + c, n3);
+            }
+        }
+        hxk = hx;
+        hyk = hy;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_e_vec(StepArgs a, int kz) {
+    const int i0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const bool valid = i0 < a.g.nx && j < a.g.ny;   // no early exit: shuffles and flux are warp-wide
+    const long long n = a.step_ctr[0];
+    const int k0 = blockIdx.z * kz;
+    const int k1 = min(a.g.nz, k0 + kz);
+    const int x0 = 4 * blockIdx.x * blockDim.x, xw = 4 * blockDim.x;
+    const int y0 = blockIdx.y * blockDim.y;
+    const bool face = tile_on_face(a.flux, x0, x0 + xw, y0, y0 + blockDim.y, k0, k1);
+    const bool pml_xy = tile_in_xy_slab(a, x0, xw, y0, blockDim.y);
+    if (face) {
+        float fl[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        e_vec_walk<true>(a, i0, j, k0, k1, valid, pml_xy, n, fl);
+        flux_warp_reduce(a.flux, fl, warp_slot());
+    } else {
+        e_vec_walk<false>(a, i0, j, k0, k1, valid, pml_xy, n, nullptr);
+    }
+    finish_step(a);
+}
+
+bool vec_supported(const StepArgs& a) { return a.g.nx % 4 == 0; }
+
 // ------------------------------------------------- TMA-staged E pass
 // 2-D tile of BX x BY cells walking kz planes.  One thread streams each
 // plane's H (with a -x / -y halo), E and material tiles into an S-slot
@@ -444,12 +640,13 @@ __global__ void __launch_bounds__(BX * BY) k_e_tma(StepArgs a, const __grid_cons
 
 HGLayout hg_layout(const StepArgs& a, const PassTune& t) {
     HGLayout L;
-    L.gx = (a.g.nx + t.block.x - 1) / t.block.x;
+    const int cells_x = t.block.x * (t.variant == kVariantVec ? 4 : 1);
+    L.gx = (a.g.nx + cells_x - 1) / cells_x;
     L.gy = (a.g.ny + t.block.y - 1) / t.block.y;
-    const int zdiv = t.variant == kVariantZmarch ? t.kz : (int)t.block.z;
+    const int zdiv = t.variant == kVariant3D ? (int)t.block.z : t.kz;
     L.gz = (a.g.nz + zdiv - 1) / zdiv;
     L.nH = L.gx * L.gy * L.gz;
-    const int threads = t.block.x * t.block.y * (t.variant == kVariantZmarch ? 1 : t.block.z);
+    const int threads = t.block.x * t.block.y * (t.variant == kVariant3D ? t.block.z : 1);
     L.q = threads * kGainPerThread;
     L.nG = (a.gain.on && a.glist.count) ? (int)((a.glist.count + L.q - 1) / L.q) : 0;
     return L;
@@ -458,7 +655,9 @@ HGLayout hg_layout(const StepArgs& a, const PassTune& t) {
 void launch_h_pass(const StepArgs& a, const PassTune& t, cudaStream_t s) {
     const HGLayout L = hg_layout(a, t);
     const unsigned blocks = (unsigned)(L.nH + L.nG);
-    if (t.variant == kVariantZmarch) {
+    if (t.variant == kVariantVec && vec_supported(a)) {
+        k_hg_vec<<<blocks, dim3(t.block.x, t.block.y, 1), 0, s>>>(a, L, t.kz);
+    } else if (t.variant == kVariantZmarch || t.variant == kVariantVec) {
         k_hg_zmarch<<<blocks, dim3(t.block.x, t.block.y, 1), 0, s>>>(a, L, t.kz);
     } else {
         k_hg_3d<<<blocks, t.block, 0, s>>>(a, L);
@@ -534,7 +733,11 @@ void launch_e_pass(const StepArgs& a, const PassTune& t, const TmaMapsE* tma, cu
         if (bx == 128 && by == 2) return launch_e_tma<128, 2>(a, t, *tma, s);
         if (bx == 128 && by == 4) return launch_e_tma<128, 4>(a, t, *tma, s);
     }
-    if (t.variant == kVariantZmarch) {
+    if (t.variant == kVariantVec && vec_supported(a)) {
+        dim3 grid((a.g.nx + 4 * t.block.x - 1) / (4 * t.block.x), (a.g.ny + t.block.y - 1) / t.block.y,
+                  (a.g.nz + t.kz - 1) / t.kz);
+        k_e_vec<<<grid, dim3(t.block.x, t.block.y, 1), 0, s>>>(a, t.kz);
+    } else if (t.variant != kVariant3D) {
         dim3 grid((a.g.nx + t.block.x - 1) / t.block.x, (a.g.ny + t.block.y - 1) / t.block.y,
                   (a.g.nz + t.kz - 1) / t.kz);
         k_e_zmarch<<<grid, dim3(t.block.x, t.block.y, 1), 0, s>>>(a, t.kz);

@@ -200,6 +200,38 @@ def test_graph_chunks_equal_single_steps_bitwise():
     b.close()
 
 
+@pytest.mark.parametrize("grid", [(64, 20, 24), (96, 17, 13)])
+def test_launch_variants_are_bitwise_identical(grid):
+    """3-D tiles, z-walks, TMA-staged and quad-vectorised passes give the same bits."""
+    from paper_0809_1547_gb300 import inputs
+    eps, gain = inputs.random_small(grid, seed=6, npml=4, d_cells=5)
+    pkw = params_kw(npml=4)
+    _, g = make_pair(grid, eps, gain, 4e24, 1e13, 11, pkw)
+    g.set_source((grid[0] // 2, grid[1] // 2, grid[2] // 2), 2, 532e-9, 1.5e-15, 0.5e-15, 1e9)
+    g.add_face_probes(2, 1, 8, 500e-9, 650e-9)
+    g.step(4)
+    blob = g.save_state()
+    ref_tune = ((1, 32, 4, 8), (1, 32, 4, 8))
+    tunes = [((0, 32, 4, 2), (0, 32, 4, 2)), ((3, 32, 4, 8), (3, 32, 4, 8)),
+             ((3, 64, 2, 16), (3, 32, 8, 4)), ((1, 64, 2, 4), (1, 32, 2, 16))]
+    if grid[0] % 16 == 0:
+        tunes += [((1, 32, 4, 8), (2, 32, 4, 8)), ((1, 32, 4, 8), (2, 64, 8, 16))]
+    results = {}
+    for tune in [ref_tune] + tunes:
+        g.load_state(blob)
+        g.set_tuning(*tune)
+        g.step(9)
+        results[tune] = {name: g.field(name) for name in FIELD_NAMES}
+    for tune in tunes:
+        for name in FIELD_NAMES:
+            a, b = results[ref_tune][name], results[tune][name]
+            if not np.array_equal(a, b):
+                where = np.argwhere(a != b)[0]
+                raise AssertionError(f"{tune} differs in {name} at [k,j,i]={tuple(where)}: "
+                                     f"{a[tuple(where)]!r} vs {b[tuple(where)]!r}")
+    g.close()
+
+
 def test_save_load_state_roundtrip_bitwise():
     from paper_0809_1547_gb300 import inputs
     grid = (22, 21, 20)
