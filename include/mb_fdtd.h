@@ -218,6 +218,30 @@ int mb_device_bytes(mb_ctx* ctx, size_t* bytes);
  * device and synchronizes.  Errors: MB_ERR_ARG, MB_ERR_CUDA. */
 int mb_philox4x32_10(const uint32_t* ctr, const uint32_t key[2], uint32_t* out, int n);
 
+/* The paper has no counterpart of this call: it is a service for callers
+ * that cannot allocate device memory — code running while a framework's
+ * caching allocator owns the device memory, code that must not pay the
+ * device-wide synchronisation of cudaMalloc / cudaFree, code under a
+ * per-process memory limit.  It computes what mb_energy reduces, from
+ * caller-owned device arrays, without allocating anything:
+ *   d_out[0] = sum_c (w_c (Ex^2 + Ey^2 + Ez^2) + Hx^2 + Hy^2 + Hz^2)   (FP64)
+ *   d_out[1] = 1.0 if any value was NaN/Inf, else 0.0
+ * with w_c = d_eps_r[c] (d_eps_r may be NULL: w = 1).  With the context's
+ * scaled fields (mb_get_field_device) and eps_r, U = eps0 E0^2 dx^3 d_out[0]/2
+ * where E0 is the scale of MB_EX.  All pointers are device pointers the
+ * caller owns (n cells of float; d_out 2 doubles); the work is queued on
+ * cuda_stream (NULL: the legacy default stream) and not waited for.
+ * Scratch: a static device array of 8192 partial sums (64 KB) that every GPU
+ * loading the library holds until exit; hence ncell <= 67,108,864
+ * (MB_ERR_ARG beyond).  The first call on a device, with that device
+ * current, looks up the array's device address; make that first call before
+ * any stream capture.  Calls share the array: calls that overlap on the GPU
+ * (different streams or threads) race and must be serialised by the caller.
+ * Errors: MB_ERR_ARG, MB_ERR_CUDA; the message is mb_last_error(NULL). */
+int mb_energy_sum_noalloc(const float* d_ex, const float* d_ey, const float* d_ez,
+                          const float* d_hx, const float* d_hy, const float* d_hz,
+                          const float* d_eps_r, int64_t ncell, double* d_out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -82,6 +82,7 @@ _SIGS = [
     ("mb_launch_stats", C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int64)]),
     ("mb_device_bytes", C.c_int, [_P, C.POINTER(C.c_size_t)]),
     ("mb_philox4x32_10", C.c_int, [_P, _P, _P, C.c_int]),
+    ("mb_energy_sum_noalloc", C.c_int, [_P, _P, _P, _P, _P, _P, _P, C.c_int64, _P, _P]),
 ]
 
 _lib = None
@@ -292,6 +293,15 @@ def mb_philox4x32_10(ctr, key):
     out = np.zeros_like(c)
     _check(load_library().mb_philox4x32_10(_ptr(c), _ptr(k), _ptr(out), c.shape[0]))
     return out
+
+
+def mb_energy_sum_noalloc(ex, ey, ez, hx, hy, hz, eps_r, ncell, out, stream=0):
+    """Energy sum from caller-owned device arrays without any allocation (see
+    include/mb_fdtd.h); arguments are device addresses (ints), eps_r may be 0."""
+    _check(load_library().mb_energy_sum_noalloc(
+        C.c_void_p(ex), C.c_void_p(ey), C.c_void_p(ez), C.c_void_p(hx), C.c_void_p(hy),
+        C.c_void_p(hz), C.c_void_p(eps_r) if eps_r else None, int(ncell), C.c_void_p(out),
+        C.c_void_p(stream) if stream else None))
 
 
 class MBSimulation:

@@ -293,6 +293,9 @@ std::map<std::tuple<int, int, int, int>, std::pair<mb::PassTune, mb::PassTune>> 
 
 }  // namespace
 
+// (internal) message for mb_last_error(NULL) from calls without a context
+void mb::set_thread_error(const std::string& msg) { g_err = msg; }
+
 extern "C" {
 
 void mb_default_params(mb_params* p) {

@@ -94,6 +94,9 @@ void launch_philox(const uint4* ctr, uint32_t k0, uint32_t k1, uint4* out, int n
 void launch_energy(const DevFields& f, int64_t ncell, const float* lut_eps, double* partial,
                    int nparts, int* nonfinite, double* out, cudaStream_t s);
 
+// Message returned by mb_last_error(NULL) on this thread.
+void set_thread_error(const std::string& msg);
+
 // Physical constants (SI, CODATA 2018).
 constexpr double kC0 = 299792458.0;
 constexpr double kEps0 = 8.8541878128e-12;
