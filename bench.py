@@ -36,9 +36,9 @@ if ROOT not in sys.path:
 METRIC = "MB-FDTD Mcell-updates/s & HBM GB/s at 320^3; batched and adjoint vs plain step"
 UNIT = "Mcell-updates/s"
 FALLBACK_HBM_GBS = 6800.0
-PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "e_pass_traffic.json")
+PROFILE_DIR = os.path.join(ROOT, "profiles")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_0809_1547_gb300", "csrc", f)
-                  for f in ("mb_device.cuh", "mb_kernels.cu")]
+                  for f in ("mb_device.cuh", "mb_passes.cu", "mb_tma.cuh")]
 
 
 # ------------------------------------------------------------------ helpers
@@ -62,33 +62,41 @@ def measured_peaks():
 
 
 def algorithmic_bytes(w):
-    """Algorithmic bytes per cell-update of each pass (perfect neighbour reuse).
+    """Algorithmic bytes per cell of one step (perfect neighbour reuse), per launch.
 
-    H pass: read E, H (24 B), write H (12 B); per CPML slab axis the cell is
-    in, read+write two psi_H (16 B).  E pass: read H, E (24 B) and the
-    material byte, write E (12 B); gain cells read+write P, J and n1..n3
-    (72 B); per slab axis two psi_E (16 B).
+    H launch (H half-step + Lorentz/Langevin update of the gain cells): read E
+    and H, write H (36 B); per CPML slab axis the cell lies in, read+write two
+    psi_H (16 B); gain cells read+write P and J and read n1, n2 (56 B).
+    E launch (E update + populations): read H and E, write E, read the
+    material byte (37 B); per slab axis two psi_E (16 B); gain cells read J
+    and read+write n1..n3 (36 B).
+    Fused minimum of the whole step (every array touched once): 73 B + 32 B
+    per slab axis + 72 B per gain cell (P, J, n1..n3 read+write).
     """
     import numpy as np
     L = w.npml
     n = w.grid
     slab = sum(min(2 * L, nw) / nw for nw in n)   # sum over axes of the slab fraction
     g = float(np.mean(w.gain != 0)) if w.N_a > 0 else 0.0
-    h_pass = 36.0 + 16.0 * slab
-    e_pass = 37.0 + 72.0 * g + 16.0 * slab
-    return {"h_pass": h_pass, "e_pass": e_pass, "step": h_pass + e_pass, "gain_fraction": g,
-            "slab_fraction_sum": slab}
+    h_launch = 36.0 + 16.0 * slab + 56.0 * g
+    e_launch = 37.0 + 16.0 * slab + 36.0 * g
+    fused = 73.0 + 32.0 * slab + 72.0 * g
+    return {"h_launch": h_launch, "e_launch": e_launch, "step_fused_minimum": fused,
+            "gain_fraction": g, "slab_fraction_sum": slab}
 
 
-def traffic_from_profile():
-    """DRAM bytes per E-pass launch from the committed ncu capture, if it was
-    taken on the current kernel sources (else None)."""
+def traffic_from_profile(kernel: str):
+    """DRAM bytes per launch of `kernel` at full size from the committed ncu
+    summary profiles/<kernel>_traffic.md, if it was taken on the current
+    kernel sources (else None)."""
+    import re
     try:
-        with open(PROFILE_TRAFFIC) as f:
-            d = json.load(f)
-        if d.get("kernel_source_hash") != kernel_source_hash():
+        with open(os.path.join(PROFILE_DIR, f"{kernel}_traffic.md")) as f:
+            text = f.read()
+        h = re.search(r"kernel_source_hash:\s*(\w+)", text).group(1)
+        if h != kernel_source_hash():
             return None
-        return float(d["bytes_per_launch_full_size"])
+        return float(re.search(r"bytes_per_launch_full_size:\s*([0-9.eE+]+)", text).group(1))
     except Exception:
         return None
 
@@ -261,7 +269,10 @@ def bench_ours(args):
     from paper_0809_1547_gb300.workloads import setup_simulation
     w = rank_workload(rank, args.grid)
     stream = torch.cuda.Stream()
-    sim = setup_simulation(w, autotune=True, stream=stream.cuda_stream)
+    sim = setup_simulation(w, autotune=not args.tune, stream=stream.cuda_stream)
+    if args.tune:
+        th, te = (tuple(int(v) for v in part.split(",")) for part in args.tune.split(":"))
+        sim.set_tuning(th, te)
     per_step_launches, _ = sim.launch_stats()
     blk_h, blk_e = sim.tuning()
     sim.step(args.warmup)
@@ -302,12 +313,19 @@ def bench_ours(args):
     value = cells * args.steps * world / (elapsed_ms / 1e3) / 1e6
     ab = algorithmic_bytes(w)
     peak, peak_kind = measured_peaks()
-    e_avg_ms = pass_ms[1] / args.steps
     h_avg_ms = pass_ms[0] / args.steps
-    e_bytes = ab["e_pass"] * cells
-    h_bytes = ab["h_pass"] * cells
-    achieved = e_bytes / (e_avg_ms / 1e3) / 1e9
-    traffic = traffic_from_profile()
+    e_avg_ms = pass_ms[1] / args.steps
+    launches = {"k_hg (H half-step + gain-cell Lorentz/Langevin)": (h_avg_ms, ab["h_launch"], "k_hg"),
+                "k_e (E update + populations + face flux)": (e_avg_ms, ab["e_launch"], "k_e")}
+    dom_name = max(launches, key=lambda k: launches[k][0])
+    dom_ms, dom_bpc, dom_key = launches[dom_name]
+    dom_bytes = dom_bpc * cells
+    achieved = dom_bytes / (dom_ms / 1e3) / 1e9
+    traffic = traffic_from_profile(dom_key)
+    step_ms = elapsed_ms / args.steps
+    other = {k: {"avg_launch_ms": round(v[0], 5), "bytes_per_cell": round(v[1], 2),
+                 "achieved_gbs": round(v[1] * cells / (v[0] / 1e3) / 1e9, 1)}
+             for k, v in launches.items()}
 
     # end to end through the public API with host buffers: material upload
     # (host -> device), K steps each followed by a read of the six face
@@ -352,15 +370,16 @@ def bench_ours(args):
                    "timed_path": "direct launches with CUDA events around each pass",
                    "blocks": {"h_pass": list(blk_h), "e_pass": list(blk_e)},
                    "graph_replay_ms_per_step": round(graph_ms_per_step, 5)},
-        "roofline": {"bound": "hbm", "kernel": "k_e_pass (fused E/gain/noise/population pass)",
+        "roofline": {"bound": "hbm", "kernel": dom_name,
                      "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "peak_source": f"{peak_kind} hbm_gbs",
-                     "traffic": traffic, "algorithmic_bytes_per_launch": round(e_bytes),
-                     "bytes_per_cell": round(ab["e_pass"], 2), "avg_launch_ms": round(e_avg_ms, 5),
-                     "h_pass": {"avg_launch_ms": round(h_avg_ms, 5),
-                                "achieved_gbs": round(h_bytes / (h_avg_ms / 1e3) / 1e9, 1),
-                                "bytes_per_cell": round(ab["h_pass"], 2)},
-                     "step_achieved_gbs": round(ab["step"] * cells / (elapsed_ms / args.steps / 1e3) / 1e9, 1),
+                     "frac": round(achieved / peak, 4), "peak_source": f"{peak_kind} hbm_gbs (of measured)"
+                     if peak_kind == "measured" else "fallback 6.8 TB/s (of fallback)",
+                     "traffic": traffic, "algorithmic_bytes_per_launch": round(dom_bytes),
+                     "bytes_per_cell": round(dom_bpc, 2), "avg_launch_ms": round(dom_ms, 5),
+                     "launches": other,
+                     "step": {"fused_minimum_bytes_per_cell": round(ab["step_fused_minimum"], 2),
+                              "achieved_gbs": round(ab["step_fused_minimum"] * cells / (step_ms / 1e3) / 1e9, 1),
+                              "frac": round(ab["step_fused_minimum"] * cells / (step_ms / 1e3) / 1e9 / peak, 4)},
                      "pass_ms_per_step": [round(v / args.steps, 5) for v in pass_ms]},
         "e2e": {"value": round(e2e_value, 2), "unit": UNIT, "h2d_bytes_per_step": round(h2d, 1),
                 "d2h_bytes_per_step": round(d2h, 1)},
@@ -425,6 +444,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tune", default="",
+                    help="fixed launch shapes 'v,bx,by,bz:v,bx,by,bz' (H launch : E launch) "
+                         "instead of the autotuner; for profiling a chosen variant")
     ap.add_argument("--grid", type=int, default=320,
                     help="cube side of the workload (320: the paper-scale sample; smaller sides "
                          "only for profiling)")
