@@ -218,6 +218,47 @@ int mb_device_bytes(mb_ctx* ctx, size_t* bytes);
  * device and synchronizes.  Errors: MB_ERR_ARG, MB_ERR_CUDA. */
 int mb_philox4x32_10(const uint32_t* ctr, const uint32_t key[2], uint32_t* out, int n);
 
+/* ------------------------------------------------------------------------
+ * Batched ensemble.  The paper's pump sweep ("spectra for two pumping
+ * levels", Fig. 2b,c; linewidth versus pump, Fig. 5b) and disorder
+ * averages need many realizations; a batch advances B of them, on grids of
+ * any (uneven) sizes, together: every mb_batch_step launch runs n steps of
+ * all instances in one persistent cooperative kernel (per step: all H tiles
+ * and gain cells, a grid barrier, all E tiles, a grid barrier), replayed
+ * from a CUDA graph.  Each instance is an ordinary context (obtained with
+ * mb_batch_instance) whose fields, probes and read-outs behave as with
+ * mb_step — the fields are bit-identical to stepping the instance alone.
+ * Supported inside a batch: point probes, sources, the face flux and energy;
+ * mb_batch_step returns MB_ERR_STATE when a member has face probes, has no
+ * material yet, or was stepped outside the batch.  A barrier that waits
+ * longer than ~1 s makes the launch end and mb_batch_synchronize return
+ * MB_ERR_TIMEOUT. */
+typedef struct mb_batch mb_batch;
+
+/* B instances; grids holds 3 ints per instance.  Errors as mb_create. */
+int mb_batch_create(mb_batch** out, int B, const int* grids, double dx, double dt,
+                    const mb_params* p, void* cuda_stream);
+int mb_batch_destroy(mb_batch* batch);
+
+/* Material, pump and noise seed of instance b (see mb_set_material). */
+int mb_batch_set_instance(mb_batch* batch, int b, const float* eps_map,
+                          const uint8_t* gain_mask, double N_a, double pump, uint64_t seed);
+
+/* The context of instance b (owned by the batch; do not destroy it).  Probes
+ * and sources added to it, and its read-outs, work as for a single context;
+ * step it only through the batch. */
+int mb_batch_instance(mb_batch* batch, int b, mb_ctx** ctx);
+
+/* Advance every instance n steps (asynchronous). */
+int mb_batch_step(mb_batch* batch, int n);
+
+/* Wait for the batch's work; MB_ERR_TIMEOUT if a grid barrier gave up. */
+int mb_batch_synchronize(mb_batch* batch);
+
+/* Time the candidate tile shapes of the persistent kernel (states are saved
+ * and restored around the trials) and keep the fastest. */
+int mb_batch_autotune(mb_batch* batch);
+
 /* The paper has no counterpart of this call: it is a service for callers
  * that cannot allocate device memory — code running while a framework's
  * caching allocator owns the device memory, code that must not pay the

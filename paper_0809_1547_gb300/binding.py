@@ -83,6 +83,15 @@ _SIGS = [
     ("mb_device_bytes", C.c_int, [_P, C.POINTER(C.c_size_t)]),
     ("mb_philox4x32_10", C.c_int, [_P, _P, _P, C.c_int]),
     ("mb_energy_sum_noalloc", C.c_int, [_P, _P, _P, _P, _P, _P, _P, C.c_int64, _P, _P]),
+    ("mb_batch_create", C.c_int, [C.POINTER(_P), C.c_int, C.POINTER(C.c_int), C.c_double,
+                                  C.c_double, C.POINTER(mb_params), _P]),
+    ("mb_batch_destroy", C.c_int, [_P]),
+    ("mb_batch_set_instance", C.c_int, [_P, C.c_int, _P, _P, C.c_double, C.c_double,
+                                        C.c_uint64]),
+    ("mb_batch_instance", C.c_int, [_P, C.c_int, C.POINTER(_P)]),
+    ("mb_batch_step", C.c_int, [_P, C.c_int]),
+    ("mb_batch_synchronize", C.c_int, [_P]),
+    ("mb_batch_autotune", C.c_int, [_P]),
 ]
 
 _lib = None
@@ -304,6 +313,48 @@ def mb_energy_sum_noalloc(ex, ey, ez, hx, hy, hz, eps_r, ncell, out, stream=0):
         C.c_void_p(stream) if stream else None))
 
 
+def mb_batch_create(grids, dx, dt, params: mb_params | None = None, stream: int | None = None):
+    lib = load_library()
+    h = C.c_void_p()
+    flat = [int(v) for g in grids for v in g]
+    g = (C.c_int * len(flat))(*flat)
+    _check(lib.mb_batch_create(C.byref(h), len(grids), g, float(dx), float(dt),
+                               C.byref(params) if params is not None else None,
+                               C.c_void_p(stream) if stream else None))
+    return h
+
+
+def mb_batch_destroy(h):
+    if h:
+        _check(load_library().mb_batch_destroy(h))
+
+
+def mb_batch_set_instance(h, b, eps_map, gain_mask, N_a, pump, seed):
+    eps = np.ascontiguousarray(eps_map, dtype=np.float32)
+    gm = np.ascontiguousarray(gain_mask, dtype=np.uint8)
+    _check(load_library().mb_batch_set_instance(h, int(b), _ptr(eps), _ptr(gm), float(N_a),
+                                                float(pump),
+                                                C.c_uint64(int(seed) & 0xFFFFFFFFFFFFFFFF)))
+
+
+def mb_batch_instance(h, b):
+    ctx = C.c_void_p()
+    _check(load_library().mb_batch_instance(h, int(b), C.byref(ctx)))
+    return ctx
+
+
+def mb_batch_step(h, n):
+    _check(load_library().mb_batch_step(h, int(n)))
+
+
+def mb_batch_synchronize(h):
+    _check(load_library().mb_batch_synchronize(h))
+
+
+def mb_batch_autotune(h):
+    _check(load_library().mb_batch_autotune(h))
+
+
 class MBSimulation:
     """One Maxwell–Bloch FDTD realization on the GPU (owns one C context).
 
@@ -311,10 +362,16 @@ class MBSimulation:
     [k, j, i] (x fastest), like the fields it returns.
     """
 
-    def __init__(self, grid, dx, dt, params: mb_params | None = None, stream=None):
+    def __init__(self, grid, dx, dt, params: mb_params | None = None, stream=None, _handle=None):
         self.grid = tuple(int(v) for v in grid)
         self.shape = self.grid[::-1]
         self.dx, self.dt = float(dx), float(dt)
+        self.probe_nfreq = {}
+        self.face_nfreq = 0
+        self._owned = _handle is None
+        if _handle is not None:   # a context owned by an MBBatch
+            self._h = _handle
+            return
         if stream is None:
             try:
                 import torch
@@ -323,12 +380,11 @@ class MBSimulation:
             except Exception:
                 stream = None
         self._h = mb_create(self.grid, dx, dt, params, stream)
-        self.probe_nfreq = {}
-        self.face_nfreq = 0
 
     def close(self):
         if getattr(self, "_h", None):
-            mb_destroy(self._h)
+            if self._owned:
+                mb_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -425,3 +481,59 @@ class MBSimulation:
 
     def device_bytes(self):
         return mb_device_bytes(self._h)
+
+
+class MBBatch:
+    """An ensemble of realizations on grids of any sizes, advanced together by
+    one persistent launch per :meth:`step` (``mb_batch_*`` in the C ABI).
+    ``instances[b]`` is an :class:`MBSimulation` view of member b: set its
+    probes and sources and read it out as usual, but step it only through the
+    batch."""
+
+    def __init__(self, grids, dx, dt, params: mb_params | None = None, stream=None):
+        if stream is None:
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    stream = torch.cuda.current_stream().cuda_stream or None
+            except Exception:
+                stream = None
+        self.grids = [tuple(int(v) for v in g) for g in grids]
+        self._h = mb_batch_create(self.grids, dx, dt, params, stream)
+        self.instances = [MBSimulation(g, dx, dt, _handle=mb_batch_instance(self._h, b))
+                          for b, g in enumerate(self.grids)]
+
+    def __len__(self):
+        return len(self.instances)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            for s in self.instances:
+                s.close()
+            mb_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_instance(self, b, eps_r, gain_mask, N_a, pump, seed):
+        mb_batch_set_instance(self._h, b, np.asarray(eps_r).reshape(-1),
+                              np.asarray(gain_mask).reshape(-1), N_a, pump, seed)
+
+    def step(self, n=1):
+        mb_batch_step(self._h, n)
+
+    def synchronize(self):
+        mb_batch_synchronize(self._h)
+
+    def autotune(self):
+        mb_batch_autotune(self._h)

@@ -296,6 +296,30 @@ std::map<std::tuple<int, int, int, int>, std::pair<mb::PassTune, mb::PassTune>> 
 // (internal) message for mb_last_error(NULL) from calls without a context
 void mb::set_thread_error(const std::string& msg) { g_err = msg; }
 
+size_t mb::state_device_bytes(mb_ctx* c) {
+    size_t total = 0;
+    for (auto& p : state_parts(c)) total += p.bytes;
+    return total;
+}
+
+int mb::state_snapshot(mb_ctx* c, void* d_dst) {
+    char* o = static_cast<char*>(d_dst);
+    for (auto& p : state_parts(c)) {
+        MB_CUDA(c, cudaMemcpyAsync(o, p.ptr, p.bytes, cudaMemcpyDeviceToDevice, c->stream));
+        o += p.bytes;
+    }
+    return MB_OK;
+}
+
+int mb::state_restore(mb_ctx* c, const void* d_src) {
+    const char* o = static_cast<const char*>(d_src);
+    for (auto& p : state_parts(c)) {
+        MB_CUDA(c, cudaMemcpyAsync(p.ptr, o, p.bytes, cudaMemcpyDeviceToDevice, c->stream));
+        o += p.bytes;
+    }
+    return MB_OK;
+}
+
 extern "C" {
 
 void mb_default_params(mb_params* p) {

@@ -1,0 +1,336 @@
+// C ABI of the batched ensemble: B realizations (ordinary contexts sharing
+// the batch's stream) advanced together by one persistent launch per call.
+#include "mb_host.h"
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+struct mb_batch {
+    std::vector<mb_ctx*> inst;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int sms = 0;
+    // device copies of the instances' step arguments, probes and work lists
+    mb::StepArgs* d_inst = nullptr;
+    mb::DevPointProbes* d_probes = nullptr;
+    int4* d_items1 = nullptr;
+    int4* d_items2 = nullptr;
+    int* d_tiles = nullptr;
+    unsigned* d_bar = nullptr;
+    int* d_err = nullptr;
+    long long* d_ctr = nullptr;
+    int n1 = 0, n2 = 0;
+    dim3 block{32, 4, 1};
+    int kz = 16;
+    int blocks = 0;
+    bool dirty = true;
+    cudaGraphExec_t graph_chunk = nullptr;
+    int graph_steps = 32;
+    bool graph_ok = true;
+    int64_t n = 0;
+    std::string err;
+};
+
+namespace {
+
+int bfail(mb_batch* b, int code, const std::string& msg) {
+    if (b) b->err = msg;
+    mb::set_thread_error(msg);
+    return code;
+}
+
+#define MB_BCUDA(b, call)                                                                  \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return bfail((b), e_ == cudaErrorMemoryAllocation ? MB_ERR_OOM : MB_ERR_CUDA, \
+                         std::string(#call) + ": " + cudaGetErrorString(e_));              \
+    } while (0)
+
+void free_arrays(mb_batch* b) {
+    void* bufs[] = {b->d_inst, b->d_probes, b->d_items1, b->d_items2, b->d_tiles};
+    for (void* p : bufs)
+        if (p) cudaFree(p);
+    b->d_inst = nullptr;
+    b->d_probes = nullptr;
+    b->d_items1 = b->d_items2 = nullptr;
+    b->d_tiles = nullptr;
+    if (b->graph_chunk) cudaGraphExecDestroy(b->graph_chunk);
+    b->graph_chunk = nullptr;
+}
+
+mb::BatchArgs batch_args(mb_batch* b, int nsteps) {
+    mb::BatchArgs a{};
+    a.inst = b->d_inst;
+    a.probes = b->d_probes;
+    a.ninst = (int)b->inst.size();
+    a.items1 = b->d_items1;
+    a.n1 = b->n1;
+    a.items2 = b->d_items2;
+    a.n2 = b->n2;
+    a.tiles = b->d_tiles;
+    a.kz = b->kz;
+    a.gq = (int)(b->block.x * b->block.y) * mb::kGainPerThread;
+    a.bar = b->d_bar;
+    a.err = b->d_err;
+    a.ctr = b->d_ctr;
+    a.nsteps = nsteps;
+    a.dt = b->inst[0]->dt;
+    return a;
+}
+
+// Device copies of the instances' arguments and the two work lists.
+int rebuild(mb_batch* b) {
+    free_arrays(b);
+    const int B = (int)b->inst.size();
+    std::vector<mb::StepArgs> args;
+    std::vector<mb::DevPointProbes> probes;
+    std::vector<int> tiles;
+    std::vector<int4> items1, items2;
+    const int threads = (int)(b->block.x * b->block.y);
+    const int gq = threads * mb::kGainPerThread;
+    for (int q = 0; q < B; ++q) {
+        mb_ctx* c = b->inst[q];
+        if (!c->have_material) return bfail(b, MB_ERR_STATE, "batch member without material");
+        if (c->face.on) return bfail(b, MB_ERR_STATE, "face probes are not advanced inside a batch");
+        args.push_back(c->args);
+        probes.push_back({(int)c->probes.size(), c->probe_nfreq, c->d_probe_cell, c->d_probe_omega,
+                          c->d_probe_acc});
+        const int gx = (c->nx + b->block.x - 1) / b->block.x;
+        const int gy = (c->ny + b->block.y - 1) / b->block.y;
+        const int gz = (c->nz + b->kz - 1) / b->kz;
+        tiles.push_back(gx);
+        tiles.push_back(gy);
+        const long long nH = (long long)gx * gy * gz;
+        const long long nG = (c->args.gain.on && c->glist_count) ? (c->glist_count + gq - 1) / gq : 0;
+        // H tiles and gain chunks interleaved by progress through the instance
+        for (long long t = 0; t < nH + nG; ++t) {
+            const long long g0 = t * nG / (nH + nG), g1 = (t + 1) * nG / (nH + nG);
+            if (g1 > g0) items1.push_back(make_int4(q, 1, (int)g0, 0));
+            else items1.push_back(make_int4(q, 0, (int)(t - g0), 0));
+        }
+        for (long long t = 0; t < nH; ++t) items2.push_back(make_int4(q, 2, (int)t, 0));
+    }
+    MB_BCUDA(b, cudaMalloc((void**)&b->d_inst, sizeof(mb::StepArgs) * B));
+    MB_BCUDA(b, cudaMalloc((void**)&b->d_probes, sizeof(mb::DevPointProbes) * B));
+    MB_BCUDA(b, cudaMalloc((void**)&b->d_tiles, sizeof(int) * tiles.size()));
+    MB_BCUDA(b, cudaMalloc((void**)&b->d_items1, sizeof(int4) * items1.size()));
+    MB_BCUDA(b, cudaMalloc((void**)&b->d_items2, sizeof(int4) * items2.size()));
+    MB_BCUDA(b, cudaMemcpyAsync(b->d_inst, args.data(), sizeof(mb::StepArgs) * B, cudaMemcpyHostToDevice, b->stream));
+    MB_BCUDA(b, cudaMemcpyAsync(b->d_probes, probes.data(), sizeof(mb::DevPointProbes) * B, cudaMemcpyHostToDevice, b->stream));
+    MB_BCUDA(b, cudaMemcpyAsync(b->d_tiles, tiles.data(), sizeof(int) * tiles.size(), cudaMemcpyHostToDevice, b->stream));
+    MB_BCUDA(b, cudaMemcpyAsync(b->d_items1, items1.data(), sizeof(int4) * items1.size(), cudaMemcpyHostToDevice, b->stream));
+    MB_BCUDA(b, cudaMemcpyAsync(b->d_items2, items2.data(), sizeof(int4) * items2.size(), cudaMemcpyHostToDevice, b->stream));
+    MB_BCUDA(b, cudaStreamSynchronize(b->stream));
+    b->n1 = (int)items1.size();
+    b->n2 = (int)items2.size();
+    const int per_sm = mb::batch_blocks_per_sm(b->block);
+    if (per_sm < 1) return bfail(b, MB_ERR_CUDA, "persistent kernel does not fit on an SM with this block");
+    b->blocks = per_sm * b->sms;
+    b->dirty = false;
+    return MB_OK;
+}
+
+int check_lockstep(mb_batch* b) {
+    for (mb_ctx* c : b->inst)
+        if (c->n != b->n)
+            return bfail(b, MB_ERR_STATE, "an instance was stepped outside the batch");
+    return MB_OK;
+}
+
+int launch_steps(mb_batch* b, int nsteps) {
+    const mb::BatchArgs a = batch_args(b, nsteps);
+    cudaError_t e = mb::launch_batch(a, b->block, b->blocks, b->stream);
+    if (e != cudaSuccess) return bfail(b, MB_ERR_CUDA, std::string("batch launch: ") + cudaGetErrorString(e));
+    return MB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mb_batch_create(mb_batch** out, int B, const int* grids, double dx, double dt, const mb_params* p,
+                    void* cuda_stream) {
+    if (!out || !grids || B < 1) return bfail(nullptr, MB_ERR_ARG, "bad batch arguments");
+    *out = nullptr;
+    mb_batch* b = new mb_batch();
+    auto bail = [&](int rc) {
+        mb_batch_destroy(b);
+        return rc;
+    };
+    if (cuda_stream) {
+        b->stream = (cudaStream_t)cuda_stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return bail(bfail(nullptr, MB_ERR_CUDA, cudaGetErrorString(e)));
+        b->own_stream = true;
+    }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+    for (int q = 0; q < B; ++q) {
+        mb_ctx* c = nullptr;
+        int rc = mb_create(&c, grids + 3 * q, dx, dt, p, b->stream);
+        if (rc) return bail(rc);
+        b->inst.push_back(c);
+    }
+    cudaError_t e = cudaMalloc((void**)&b->d_bar, sizeof(unsigned) * 2);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_ctr, sizeof(long long));
+    if (e == cudaSuccess) e = cudaMemset(b->d_bar, 0, sizeof(unsigned) * 2);
+    if (e == cudaSuccess) e = cudaMemset(b->d_err, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(b->d_ctr, 0, sizeof(long long));
+    if (e != cudaSuccess) return bail(bfail(nullptr, MB_ERR_OOM, cudaGetErrorString(e)));
+    *out = b;
+    return MB_OK;
+}
+
+int mb_batch_destroy(mb_batch* b) {
+    if (!b) return MB_OK;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    free_arrays(b);
+    for (mb_ctx* c : b->inst) mb_destroy(c);
+    void* bufs[] = {b->d_bar, b->d_err, b->d_ctr};
+    for (void* p : bufs)
+        if (p) cudaFree(p);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+    return MB_OK;
+}
+
+int mb_batch_set_instance(mb_batch* b, int q, const float* eps_map, const uint8_t* gain_mask, double N_a,
+                          double pump, uint64_t seed) {
+    if (!b || q < 0 || q >= (int)b->inst.size()) return bfail(b, MB_ERR_ARG, "bad instance index");
+    int rc = mb_set_material(b->inst[q], eps_map, gain_mask, N_a, pump);
+    if (rc) return bfail(b, rc, mb_last_error(b->inst[q]));
+    rc = mb_set_seed(b->inst[q], seed);
+    if (rc) return bfail(b, rc, mb_last_error(b->inst[q]));
+    b->dirty = true;
+    return MB_OK;
+}
+
+int mb_batch_instance(mb_batch* b, int q, mb_ctx** ctx) {
+    if (!b || !ctx || q < 0 || q >= (int)b->inst.size()) return bfail(b, MB_ERR_ARG, "bad instance index");
+    *ctx = b->inst[q];
+    b->dirty = true;   // the caller may add probes or a source
+    return MB_OK;
+}
+
+int mb_batch_step(mb_batch* b, int n) {
+    if (!b || n < 0) return bfail(b, MB_ERR_ARG, "bad batch step arguments");
+    if (n == 0) return MB_OK;
+    if (int rc = check_lockstep(b)) return rc;
+    if (b->dirty)
+        if (int rc = rebuild(b)) return rc;
+    // the batch counter follows the instances' own step count
+    const long long n0 = (long long)b->n;
+    MB_BCUDA(b, cudaMemcpyAsync(b->d_ctr, &n0, sizeof(long long), cudaMemcpyHostToDevice, b->stream));
+    int left = n;
+    if (b->graph_ok && left >= b->graph_steps) {
+        if (!b->graph_chunk) {
+            cudaGraph_t g = nullptr;
+            bool ok = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+            if (ok) {
+                const mb::BatchArgs a = batch_args(b, b->graph_steps);
+                cudaError_t le = mb::launch_batch(a, b->block, b->blocks, b->stream);
+                cudaError_t ce = cudaStreamEndCapture(b->stream, &g);
+                ok = le == cudaSuccess && ce == cudaSuccess &&
+                     cudaGraphInstantiate(&b->graph_chunk, g, 0) == cudaSuccess;
+                if (g) cudaGraphDestroy(g);
+            }
+            if (!ok) {   // cooperative launches not capturable here: launch directly
+                cudaGetLastError();
+                b->graph_ok = false;
+                b->graph_chunk = nullptr;
+            }
+        }
+        while (b->graph_chunk && left >= b->graph_steps) {
+            MB_BCUDA(b, cudaGraphLaunch(b->graph_chunk, b->stream));
+            left -= b->graph_steps;
+        }
+    }
+    if (left > 0)
+        if (int rc = launch_steps(b, left)) return rc;
+    b->n += n;
+    for (mb_ctx* c : b->inst) {
+        c->n += n;
+        c->launches += 1;
+    }
+    return MB_OK;
+}
+
+int mb_batch_synchronize(mb_batch* b) {
+    if (!b) return bfail(nullptr, MB_ERR_ARG, "null batch");
+    MB_BCUDA(b, cudaStreamSynchronize(b->stream));
+    int e = 0;
+    MB_BCUDA(b, cudaMemcpy(&e, b->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) {
+        cudaMemset(b->d_err, 0, sizeof(int));
+        cudaMemset(b->d_bar, 0, sizeof(unsigned) * 2);
+        return bfail(b, MB_ERR_TIMEOUT, "a grid barrier of the batched launch gave up");
+    }
+    return MB_OK;
+}
+
+int mb_batch_autotune(mb_batch* b) {
+    if (!b) return bfail(nullptr, MB_ERR_ARG, "null batch");
+    if (int rc = check_lockstep(b)) return rc;
+    MB_BCUDA(b, cudaStreamSynchronize(b->stream));
+    size_t total = 0;
+    for (mb_ctx* c : b->inst) total += mb::state_device_bytes(c);
+    char* backup = nullptr;
+    MB_BCUDA(b, cudaMalloc((void**)&backup, total));
+    {
+        char* o = backup;
+        for (mb_ctx* c : b->inst) {
+            mb::state_snapshot(c, o);
+            o += mb::state_device_bytes(c);
+        }
+    }
+    struct Cand { dim3 block; int kz; };
+    const Cand cands[] = {{dim3(32, 4, 1), 16}, {dim3(32, 4, 1), 8}, {dim3(32, 8, 1), 8},
+                          {dim3(64, 2, 1), 16}, {dim3(32, 2, 1), 16}, {dim3(64, 4, 1), 8},
+                          {dim3(32, 8, 1), 16}};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    Cand pick{b->block, b->kz};
+    const long long n0 = (long long)b->n;
+    for (const Cand& cd : cands) {
+        b->block = cd.block;
+        b->kz = cd.kz;
+        if (rebuild(b)) continue;
+        cudaMemcpyAsync(b->d_ctr, &n0, sizeof(long long), cudaMemcpyHostToDevice, b->stream);
+        if (launch_steps(b, 1)) continue;
+        cudaEventRecord(e0, b->stream);
+        if (launch_steps(b, 2)) continue;
+        cudaEventRecord(e1, b->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            pick = cd;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    {
+        const char* o = backup;
+        for (mb_ctx* c : b->inst) {
+            mb::state_restore(c, o);
+            o += mb::state_device_bytes(c);
+        }
+    }
+    cudaStreamSynchronize(b->stream);
+    cudaFree(backup);
+    b->block = pick.block;
+    b->kz = pick.kz;
+    b->dirty = true;
+    MB_BCUDA(b, cudaGetLastError());
+    return MB_OK;
+}
+
+}  // extern "C"

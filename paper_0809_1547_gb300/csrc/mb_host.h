@@ -23,6 +23,31 @@ struct DevPointProbes {
     double2* acc;          // [count][3][nfreq]
 };
 
+// Running DFT of probe p (one block, threads over bins) with E_c^{n1} at
+// t = n1 dt: acc[p][c][k] += E_c exp(i w_k t) (scaled; times dt E0 on read-out).
+__device__ __forceinline__ void point_dft_block(const DevPointProbes& pp, int p, const float* ex,
+                                                const float* ey, const float* ez, long long n1,
+                                                double dt) {
+    const double t = (double)n1 * dt;
+    const int64_t cell = pp.cell[p];
+    const float e[3] = {ex[cell], ey[cell], ez[cell]};
+    const int K = pp.nfreq;
+    const int T = blockDim.x * blockDim.y * blockDim.z;
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    for (int kk = tid; kk < K; kk += T) {
+        double s, co;
+        sincos(pp.omega[p * K + kk] * t, &s, &co);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            double2* acc = pp.acc + ((int64_t)p * 3 + c) * K + kk;
+            double2 v = *acc;
+            v.x += (double)e[c] * co;
+            v.y += (double)e[c] * s;
+            *acc = v;
+        }
+    }
+}
+
 struct DevFaceProbes {
     int on;
     int stride, every, nfreq, pts_per_block;
@@ -90,12 +115,42 @@ void launch_point_dft(const DevPointProbes& pp, const DevFields& f, const long l
                       double dt, cudaStream_t s);
 void launch_face_dft(const DevFaceProbes& fp, const DevFields& f, const DevGrid& g,
                      const long long* ctr, double dt, cudaStream_t s);
+// Batched ensemble: instances advanced together by one persistent launch.
+// Work items (int4): x = instance, y = kind (0 H tile, 1 gain chunk, 2 E
+// tile), z = tile / chunk index.
+struct BatchArgs {
+    const StepArgs* inst;          // [ninst], device
+    const DevPointProbes* probes;  // [ninst], device (count 0: no probe)
+    int ninst;
+    const int4* items1;            // phase 1: H tiles and gain chunks
+    int n1;
+    const int4* items2;            // phase 2: E tiles
+    int n2;
+    const int* tiles;              // [ninst][2]: tile-grid gx, gy of each instance
+    int kz, gq;
+    unsigned* bar;                 // grid barrier: [0] arrivals, [1] generation
+    int* err;
+    long long* ctr;                // steps completed by the batch
+    int nsteps;
+    double dt;
+};
+constexpr int kBarrierSpinLimit = 1 << 22;   // ~0.3-1 s with 64 ns sleeps
+constexpr int kGainPerThread = 2;             // gain cells per thread in a gain block
+cudaError_t launch_batch(const BatchArgs& b, dim3 block, int blocks, cudaStream_t s);
+int batch_blocks_per_sm(dim3 block);
+
 void launch_philox(const uint4* ctr, uint32_t k0, uint32_t k1, uint4* out, int n, cudaStream_t s);
 void launch_energy(const DevFields& f, int64_t ncell, const float* lut_eps, double* partial,
                    int nparts, int* nonfinite, double* out, cudaStream_t s);
 
 // Message returned by mb_last_error(NULL) on this thread.
 void set_thread_error(const std::string& msg);
+
+// Whole evolving state of a context as one device blob (for device-side
+// snapshots: autotuning, adjoint checkpoints).
+size_t state_device_bytes(mb_ctx* c);
+int state_snapshot(mb_ctx* c, void* d_dst);          // device -> device, on c's stream
+int state_restore(mb_ctx* c, const void* d_src);     // device -> device, on c's stream
 
 // Physical constants (SI, CODATA 2018).
 constexpr double kC0 = 299792458.0;

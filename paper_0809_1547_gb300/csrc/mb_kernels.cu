@@ -18,24 +18,7 @@ namespace mb {
 // acc[p][c][k] += E_c(t_{n+1}) exp(i w_k t_{n+1})   (scaled; times dt E0 on read-out)
 __global__ void k_point_dft(DevPointProbes pp, const float* ex, const float* ey, const float* ez,
                             const long long* step_ctr, double dt) {
-    const int p = blockIdx.x;
-    const long long n1 = step_ctr[0];          // n + 1
-    const double t = (double)n1 * dt;
-    const int64_t cell = pp.cell[p];
-    const float e[3] = {ex[cell], ey[cell], ez[cell]};
-    const int K = pp.nfreq;
-    for (int kk = threadIdx.x; kk < K; kk += blockDim.x) {
-        double s, co;
-        sincos(pp.omega[p * K + kk] * t, &s, &co);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            double2* acc = pp.acc + ((int64_t)p * 3 + c) * K + kk;
-            double2 v = *acc;
-            v.x += (double)e[c] * co;
-            v.y += (double)e[c] * s;
-            *acc = v;
-        }
-    }
+    point_dft_block(pp, blockIdx.x, ex, ey, ez, step_ctr[0], dt);   // counter = n + 1
 }
 
 // Face DFT: block (chunk of points, face); thread per frequency bin, looping

@@ -19,8 +19,6 @@
 
 namespace mb {
 
-constexpr int kGainPerThread = 2;   // gain cells per thread in a gain block
-
 // Block b of the H + gain grid is a gain block (returns true, idx = its
 // index) or an H block (returns false, idx = its index).  Gain blocks are
 // spread evenly through the grid so both kinds advance through the domain
@@ -124,14 +122,8 @@ __global__ void __launch_bounds__(512) k_hg_3d(StepArgs a, HGLayout lay) {
     else h_core<false>(a, i, j, k, c, e);
 }
 
-__global__ void __launch_bounds__(512) k_hg_zmarch(StepArgs a, HGLayout lay, int kz) {
-    const long long n = a.step_ctr[0];
-    unsigned idx;
-    if (hg_block_kind(lay, blockIdx.x, idx)) {
-        gain_block(a, idx, lay.q, n);
-        return;
-    }
-    const int bx = idx % lay.gx, by = (idx / lay.gx) % lay.gy, bz = idx / (lay.gx * lay.gy);
+// H walk of tile (bx, by, bz): a 2-D block over (x, y), kz planes per thread.
+__device__ __forceinline__ void h_tile_zmarch(const StepArgs& a, int bx, int by, int bz, int kz) {
     const int i = bx * blockDim.x + threadIdx.x;
     const int j = by * blockDim.y + threadIdx.y;
     const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
@@ -192,6 +184,16 @@ __global__ void __launch_bounds__(512) k_hg_zmarch(StepArgs a, HGLayout lay, int
         if (pml_xy || plane_in_z_slab(a, k)) h_core<true>(a, i, j, k, c, e);
         else h_core<false>(a, i, j, k, c, e);
     }
+}
+
+__global__ void __launch_bounds__(512) k_hg_zmarch(StepArgs a, HGLayout lay, int kz) {
+    const long long n = a.step_ctr[0];
+    unsigned idx;
+    if (hg_block_kind(lay, blockIdx.x, idx)) {
+        gain_block(a, idx, lay.q, n);
+        return;
+    }
+    h_tile_zmarch(a, idx % lay.gx, (idx / lay.gx) % lay.gy, idx / (lay.gx * lay.gy), kz);
 }
 
 // ------------------------------------------------------------ E launches
@@ -284,27 +286,141 @@ __device__ __forceinline__ void e_walk(const StepArgs& a, int i, int j, int k0, 
     }
 }
 
-__global__ void __launch_bounds__(512, 2) k_e_zmarch(StepArgs a, int kz) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+// E walk of tile (bx, by, bz) for step n (flux of face tiles included).
+// Every thread of the block must call it (warp-wide flux reduction).
+__device__ __forceinline__ void e_tile_zmarch(const StepArgs& a, int bx, int by, int bz, int kz,
+                                              long long n, unsigned slot) {
+    const int i = bx * blockDim.x + threadIdx.x;
+    const int j = by * blockDim.y + threadIdx.y;
     const int nz = a.g.nz;
-    const bool valid = i < a.g.nx && j < a.g.ny;   // no early exit: warp-wide flux reduction
-    const long long n = a.step_ctr[0];
-    const int k0 = blockIdx.z * kz;
+    const bool valid = i < a.g.nx && j < a.g.ny;
+    const int k0 = bz * kz;
     const int k1 = min(nz, k0 + kz);
-    const int i0 = blockIdx.x * blockDim.x, j0 = blockIdx.y * blockDim.y;
+    const int i0 = bx * blockDim.x, j0 = by * blockDim.y;
     const bool face = tile_on_face(a.flux, i0, i0 + blockDim.x, j0, j0 + blockDim.y, k0, k1);
     const bool pml_xy = tile_in_xy_slab(a, i0, blockDim.x, j0, blockDim.y);
     if (face) {
         float fl[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         if (valid) e_walk<true, true>(a, i, j, k0, k1, n, fl);
-        flux_warp_reduce(a.flux, fl, warp_slot());
+        flux_warp_reduce(a.flux, fl, slot);
     } else if (valid) {
         float* none = nullptr;
         if (pml_xy) e_walk<false, true>(a, i, j, k0, k1, n, none);
         else e_walk<false, false>(a, i, j, k0, k1, n, none);
     }
+}
+
+__global__ void __launch_bounds__(512, 2) k_e_zmarch(StepArgs a, int kz) {
+    const long long n = a.step_ctr[0];
+    e_tile_zmarch(a, blockIdx.x, blockIdx.y, blockIdx.z, kz, n, warp_slot());
     finish_step(a);
+}
+
+// ---------------------------------------------------- batched ensemble
+// Grid-wide barrier of a co-resident (cooperative) grid, with a bounded
+// wait: false when the other blocks did not all arrive within the limit.
+__device__ bool grid_barrier(unsigned* bar, unsigned nblocks) {
+    __shared__ int ok_s;
+    __syncthreads();
+    if (linear_tid() == 0) {
+        volatile unsigned* gen = bar + 1;
+        const unsigned g = *gen;
+        __threadfence();
+        int ok = 1;
+        if (atomicAdd(bar, 1u) == nblocks - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            for (int it = 0; *gen == g; ++it) {
+                if (it > kBarrierSpinLimit) {
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+// n steps of every instance in one launch.  Per step: phase 1 = the point
+// probes of the previous step (they read E only) + all instances' H tiles
+// and gain chunks; barrier; phase 2 = all E tiles; barrier.  Work items are
+// dealt round-robin over the blocks, so grids of uneven size balance.  A
+// barrier that times out sets the error flag and the block leaves; the other
+// blocks then time out at their next barrier, so the launch always ends.
+__global__ void __launch_bounds__(256) k_batch(BatchArgs B) {
+    const unsigned nb = gridDim.x;
+    const long long n0 = B.ctr[0];
+    for (int s = 0; s < B.nsteps; ++s) {
+        const long long n = n0 + s;
+        if (s > 0)
+            for (int p = blockIdx.x; p < B.ninst; p += nb)
+                for (int q = 0; q < B.probes[p].count; ++q)
+                    point_dft_block(B.probes[p], q, B.inst[p].f.ex, B.inst[p].f.ey, B.inst[p].f.ez, n,
+                                    B.dt);
+        for (int w = blockIdx.x; w < B.n1; w += nb) {
+            const int4 it = B.items1[w];
+            const StepArgs& a = B.inst[it.x];
+            if (it.y == 0) {
+                const int gx = B.tiles[2 * it.x], gy = B.tiles[2 * it.x + 1];
+                h_tile_zmarch(a, it.z % gx, (it.z / gx) % gy, it.z / (gx * gy), B.kz);
+            } else {
+                gain_block(a, (unsigned)it.z, B.gq, n);
+            }
+        }
+        if (!grid_barrier(B.bar, nb)) {
+            if (linear_tid() == 0) atomicOr(B.err, 1);
+            return;
+        }
+        for (int w = blockIdx.x; w < B.n2; w += nb) {
+            const int4 it = B.items2[w];
+            const StepArgs& a = B.inst[it.x];
+            const int gx = B.tiles[2 * it.x], gy = B.tiles[2 * it.x + 1];
+            e_tile_zmarch(a, it.z % gx, (it.z / gx) % gy, it.z / (gx * gy), B.kz, n,
+                          (unsigned)w * 7u + (linear_tid() >> 5));
+        }
+        if (!grid_barrier(B.bar, nb)) {
+            if (linear_tid() == 0) atomicOr(B.err, 1);
+            return;
+        }
+    }
+    const long long n_end = n0 + B.nsteps;
+    for (int p = blockIdx.x; p < B.ninst; p += nb)
+        for (int q = 0; q < B.probes[p].count; ++q)
+            point_dft_block(B.probes[p], q, B.inst[p].f.ex, B.inst[p].f.ey, B.inst[p].f.ez, n_end,
+                            B.dt);
+    if (blockIdx.x == 0) {
+        // every block read n0 before the first barrier; nsteps >= 1
+        for (int p = linear_tid(); p < B.ninst; p += blockDim.x * blockDim.y) B.inst[p].step_ctr[0] = n_end;
+        if (linear_tid() == 0) B.ctr[0] = n_end;
+    }
+}
+
+int batch_blocks_per_sm(dim3 block) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch, block.x * block.y * block.z, 0) !=
+        cudaSuccess)
+        return 0;
+    return n;
+}
+
+cudaError_t launch_batch(const BatchArgs& b, dim3 block, int blocks, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blocks, 1, 1);
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;   // all blocks co-resident: the barrier is safe
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_batch, b);
 }
 
 // ----------------------------------------------- quad-vectorised z-walks
