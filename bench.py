@@ -387,6 +387,8 @@ def bench_ours(args):
         "clocks": clocks,
         "energy_J": U,
     }
+    if not args.no_batched:
+        out["batched"] = bench_batched(stream, args.batched_steps, args.warmup)
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.grid == 320:
         try:
             rate, el, ncell = run_oracle_child(16, 6)
@@ -402,6 +404,80 @@ def bench_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+# ------------------------------------------------------ batched ensemble
+
+def bench_batched(stream, steps: int, warmup: int):
+    """The ensemble (16 N_a levels log-spaced 5e23-2e25 m^-3 x 5 disorder
+    seeds, cubes of side 96-160, 45 % fill, gain in the voids, a centre probe
+    each) advanced by the batched persistent launch, against the plain
+    single-context step of the same 80 realizations one after another."""
+    import numpy as np
+    import torch
+    from paper_0809_1547_gb300 import inputs
+    from paper_0809_1547_gb300.binding import MBBatch, MBSimulation, mb_default_params
+    ws = inputs.workload_batch()
+    p = mb_default_params(npml=ws[0].npml)
+    cells = sum(int(np.prod(w.grid)) for w in ws)
+
+    def centre(w):
+        return tuple(v // 2 for v in w.grid)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    b = MBBatch([w.grid for w in ws], ws[0].dx, ws[0].dt, p, stream=stream.cuda_stream)
+    for q, w in enumerate(ws):
+        b.set_instance(q, w.eps, w.gain, w.N_a, w.pump, w.seed)
+        b.instances[q].add_point_probe(centre(w), 128, 475e-9, 705e-9)
+    b.autotune()
+    b.step(warmup)
+    b.synchronize()
+    batch_ms = timed(lambda: b.step(steps))
+    b.synchronize()
+    tune = b.tuning()
+    b.close()
+
+    sims = []
+    for w in ws:
+        s_ = MBSimulation(w.grid, w.dx, w.dt, p, stream=stream.cuda_stream)
+        s_.set_material(w.eps, w.gain, w.N_a, w.pump)
+        s_.set_seed(w.seed)
+        s_.add_point_probe(centre(w), 128, 475e-9, 705e-9)
+        s_.autotune()
+        s_.step(warmup)
+        sims.append(s_)
+
+    def plain():
+        for s_ in sims:
+            s_.step(steps)
+    plain_ms = timed(plain)
+    for s_ in sims:
+        s_.close()
+    v_batch = cells * steps / (batch_ms / 1e3) / 1e6
+    v_plain = cells * steps / (plain_ms / 1e3) / 1e6
+    sides = sorted({w.grid[0] for w in ws})
+    return {"workload": f"{len(ws)} realizations: 16 N_a levels (5e23-2e25 m^-3, log-spaced) x 5 "
+                        f"disorder seeds, cubes of side {sides} (dx 20 nm, 45% fill, d 300 nm, "
+                        "8-cell CPML), gain in the voids, W_p 1e13/s, Langevin noise, a centre "
+                        "probe (128 bins) each",
+            "instances": len(ws), "cells_per_step": cells, "steps": steps, "warmup": warmup,
+            "value": round(v_batch, 2), "unit": UNIT, "ms_per_step": round(batch_ms / steps, 4),
+            "launches_per_call": 1, "tile_bx_by_kz": list(tune),
+            "plain_single_instance": {"value": round(v_plain, 2), "unit": UNIT,
+                                      "ms_per_step": round(plain_ms / steps, 4),
+                                      "how": "each realization's own context stepped by mb_step "
+                                             "(autotuned, graph replay), one after another"},
+            "ratio_vs_plain": round(v_batch / v_plain, 4),
+            "l2": "inputs larger than L2"}
 
 
 # --------------------------------------------------------- reference arm
@@ -444,6 +520,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-ensemble leg")
+    ap.add_argument("--batched-steps", type=int, default=40)
     ap.add_argument("--tune", default="",
                     help="fixed launch shapes 'v,bx,by,bz:v,bx,by,bz' (H launch : E launch) "
                          "instead of the autotuner; for profiling a chosen variant")

@@ -259,6 +259,10 @@ int mb_batch_synchronize(mb_batch* batch);
  * and restored around the trials) and keep the fastest. */
 int mb_batch_autotune(mb_batch* batch);
 
+/* Tile shape of the persistent kernel: out3 = {bx, by, kz} (a block of bx x by
+ * threads walks kz z-planes of one tile). */
+int mb_batch_get_tuning(mb_batch* batch, int* out3);
+
 /* The paper has no counterpart of this call: it is a service for callers
  * that cannot allocate device memory — code running while a framework's
  * caching allocator owns the device memory, code that must not pay the

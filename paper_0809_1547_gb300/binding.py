@@ -92,6 +92,7 @@ _SIGS = [
     ("mb_batch_step", C.c_int, [_P, C.c_int]),
     ("mb_batch_synchronize", C.c_int, [_P]),
     ("mb_batch_autotune", C.c_int, [_P]),
+    ("mb_batch_get_tuning", C.c_int, [_P, C.POINTER(C.c_int)]),
 ]
 
 _lib = None
@@ -355,6 +356,13 @@ def mb_batch_autotune(h):
     _check(load_library().mb_batch_autotune(h))
 
 
+def mb_batch_get_tuning(h):
+    """(bx, by, kz) of the persistent kernel."""
+    t = (C.c_int * 3)()
+    _check(load_library().mb_batch_get_tuning(h, t))
+    return tuple(t)
+
+
 class MBSimulation:
     """One Maxwell–Bloch FDTD realization on the GPU (owns one C context).
 
@@ -537,3 +545,6 @@ class MBBatch:
 
     def autotune(self):
         mb_batch_autotune(self._h)
+
+    def tuning(self):
+        return mb_batch_get_tuning(self._h)

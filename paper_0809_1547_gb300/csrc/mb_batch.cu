@@ -18,6 +18,7 @@ struct mb_batch {
     int4* d_items2 = nullptr;
     int* d_tiles = nullptr;
     unsigned* d_bar = nullptr;
+    unsigned long long* d_tick = nullptr;
     int* d_err = nullptr;
     long long* d_ctr = nullptr;
     int n1 = 0, n2 = 0;
@@ -71,8 +72,9 @@ mb::BatchArgs batch_args(mb_batch* b, int nsteps) {
     a.n2 = b->n2;
     a.tiles = b->d_tiles;
     a.kz = b->kz;
-    a.gq = (int)(b->block.x * b->block.y) * mb::kGainPerThread;
+    a.gq = (int)(b->block.x * b->block.y) * mb::kBatchGainPerThread;
     a.bar = b->d_bar;
+    a.tick = b->d_tick;
     a.err = b->d_err;
     a.ctr = b->d_ctr;
     a.nsteps = nsteps;
@@ -89,7 +91,7 @@ int rebuild(mb_batch* b) {
     std::vector<int> tiles;
     std::vector<int4> items1, items2;
     const int threads = (int)(b->block.x * b->block.y);
-    const int gq = threads * mb::kGainPerThread;
+    const int gq = threads * mb::kBatchGainPerThread;
     for (int q = 0; q < B; ++q) {
         mb_ctx* c = b->inst[q];
         if (!c->have_material) return bfail(b, MB_ERR_STATE, "batch member without material");
@@ -104,14 +106,31 @@ int rebuild(mb_batch* b) {
         tiles.push_back(gy);
         const long long nH = (long long)gx * gy * gz;
         const long long nG = (c->args.gain.on && c->glist_count) ? (c->glist_count + gq - 1) / gq : 0;
-        // H tiles and gain chunks interleaved by progress through the instance
-        for (long long t = 0; t < nH + nG; ++t) {
-            const long long g0 = t * nG / (nH + nG), g1 = (t + 1) * nG / (nH + nG);
-            if (g1 > g0) items1.push_back(make_int4(q, 1, (int)g0, 0));
-            else items1.push_back(make_int4(q, 0, (int)(t - g0), 0));
+        const double gfrac = c->ncell ? (double)c->glist_count / (double)c->ncell : 0.0;
+        const int L = c->p.npml;
+        for (long long t = 0; t < nH; ++t) {
+            // estimated bytes of the tile: cells x (bytes per cell, with 16 B
+            // per CPML slab axis the tile touches)
+            const int bx = (int)(t % gx), by = (int)((t / gx) % gy), bz = (int)(t / ((long long)gx * gy));
+            const int i0 = bx * (int)b->block.x, j0 = by * (int)b->block.y, k0 = bz * b->kz;
+            const int cx = std::min((int)b->block.x, c->nx - i0), cy = std::min((int)b->block.y, c->ny - j0),
+                      cz = std::min(b->kz, c->nz - k0);
+            const int axes = (L > 0 && (i0 < L || i0 + (int)b->block.x > c->nx - L)) +
+                             (L > 0 && (j0 < L || j0 + (int)b->block.y > c->ny - L)) +
+                             (L > 0 && (k0 < L || k0 + b->kz > c->nz - L));
+            const double cells = (double)cx * cy * cz;
+            items1.push_back(make_int4(q, 0, (int)t, (int)(cells * (36 + 16 * axes))));
+            items2.push_back(make_int4(q, 2, (int)t, (int)(cells * (37 + 16 * axes + 36 * gfrac))));
         }
-        for (long long t = 0; t < nH; ++t) items2.push_back(make_int4(q, 2, (int)t, 0));
+        for (long long t = 0; t < nG; ++t) {
+            const long long cells = std::min<long long>(gq, (long long)c->glist_count - t * gq);
+            items1.push_back(make_int4(q, 1, (int)t, (int)(cells * 56)));
+        }
     }
+    // largest items first: the phase ends with small ones, so blocks finish together
+    auto by_cost = [](const int4& u, const int4& v) { return u.w > v.w; };
+    std::stable_sort(items1.begin(), items1.end(), by_cost);
+    std::stable_sort(items2.begin(), items2.end(), by_cost);
     MB_BCUDA(b, cudaMalloc((void**)&b->d_inst, sizeof(mb::StepArgs) * B));
     MB_BCUDA(b, cudaMalloc((void**)&b->d_probes, sizeof(mb::DevPointProbes) * B));
     MB_BCUDA(b, cudaMalloc((void**)&b->d_tiles, sizeof(int) * tiles.size()));
@@ -177,6 +196,8 @@ int mb_batch_create(mb_batch** out, int B, const int* grids, double dx, double d
     }
     cudaError_t e = cudaMalloc((void**)&b->d_bar, sizeof(unsigned) * 2);
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_tick, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(b->d_tick, 0, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_ctr, sizeof(long long));
     if (e == cudaSuccess) e = cudaMemset(b->d_bar, 0, sizeof(unsigned) * 2);
     if (e == cudaSuccess) e = cudaMemset(b->d_err, 0, sizeof(int));
@@ -191,7 +212,7 @@ int mb_batch_destroy(mb_batch* b) {
     if (b->stream) cudaStreamSynchronize(b->stream);
     free_arrays(b);
     for (mb_ctx* c : b->inst) mb_destroy(c);
-    void* bufs[] = {b->d_bar, b->d_err, b->d_ctr};
+    void* bufs[] = {b->d_bar, b->d_err, b->d_ctr, b->d_tick};
     for (void* p : bufs)
         if (p) cudaFree(p);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
@@ -268,6 +289,7 @@ int mb_batch_synchronize(mb_batch* b) {
     if (e) {
         cudaMemset(b->d_err, 0, sizeof(int));
         cudaMemset(b->d_bar, 0, sizeof(unsigned) * 2);
+        cudaMemset(b->d_tick, 0, sizeof(unsigned long long));
         return bfail(b, MB_ERR_TIMEOUT, "a grid barrier of the batched launch gave up");
     }
     return MB_OK;
@@ -291,7 +313,7 @@ int mb_batch_autotune(mb_batch* b) {
     struct Cand { dim3 block; int kz; };
     const Cand cands[] = {{dim3(32, 4, 1), 16}, {dim3(32, 4, 1), 8}, {dim3(32, 8, 1), 8},
                           {dim3(64, 2, 1), 16}, {dim3(32, 2, 1), 16}, {dim3(64, 4, 1), 8},
-                          {dim3(32, 8, 1), 16}};
+                          {dim3(32, 8, 1), 16}, {dim3(32, 4, 1), 32}, {dim3(64, 4, 1), 16}};
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -330,6 +352,14 @@ int mb_batch_autotune(mb_batch* b) {
     b->kz = pick.kz;
     b->dirty = true;
     MB_BCUDA(b, cudaGetLastError());
+    return MB_OK;
+}
+
+int mb_batch_get_tuning(mb_batch* b, int* out3) {
+    if (!b || !out3) return bfail(b, MB_ERR_ARG, "null argument");
+    out3[0] = (int)b->block.x;
+    out3[1] = (int)b->block.y;
+    out3[2] = b->kz;
     return MB_OK;
 }
 

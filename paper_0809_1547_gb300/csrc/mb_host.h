@@ -117,7 +117,7 @@ void launch_face_dft(const DevFaceProbes& fp, const DevFields& f, const DevGrid&
                      const long long* ctr, double dt, cudaStream_t s);
 // Batched ensemble: instances advanced together by one persistent launch.
 // Work items (int4): x = instance, y = kind (0 H tile, 1 gain chunk, 2 E
-// tile), z = tile / chunk index.
+// tile), z = tile / chunk index, w = estimated cost (bytes).
 struct BatchArgs {
     const StepArgs* inst;          // [ninst], device
     const DevPointProbes* probes;  // [ninst], device (count 0: no probe)
@@ -129,6 +129,7 @@ struct BatchArgs {
     const int* tiles;              // [ninst][2]: tile-grid gx, gy of each instance
     int kz, gq;
     unsigned* bar;                 // grid barrier: [0] arrivals, [1] generation
+    unsigned long long* tick;      // work-item tickets (zero between launches)
     int* err;
     long long* ctr;                // steps completed by the batch
     int nsteps;
@@ -136,6 +137,7 @@ struct BatchArgs {
 };
 constexpr int kBarrierSpinLimit = 1 << 22;   // ~0.3-1 s with 64 ns sleeps
 constexpr int kGainPerThread = 2;             // gain cells per thread in a gain block
+constexpr int kBatchGainPerThread = 1;        // the same inside the persistent kernel
 cudaError_t launch_batch(const BatchArgs& b, dim3 block, int blocks, cudaStream_t s);
 int batch_blocks_per_sm(dim3 block);
 
