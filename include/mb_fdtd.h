@@ -263,6 +263,34 @@ int mb_batch_autotune(mb_batch* batch);
  * threads walks kz z-planes of one tile). */
 int mb_batch_get_tuning(mb_batch* batch, int* out3);
 
+/* ------------------------------------------------------------------------
+ * Adjoint gradient of emitted energy.  The paper observes emission through
+ * probe planes ("Simulations" paragraph, spectra of Figs. 1-2) and varies the
+ * pump (Figs. 2, 5); this call differentiates that read-out.  Objective: the
+ * energy (J) crossing the plane z = z_plane dx in +z during the next n_steps
+ * steps, over the interior rectangle (the CPML-free x, y range), with the
+ * same discrete Poynting pairing as the face flux ((E^n + E^{n+1})/2 on the
+ * plane against H^{n+1/2} half a cell below it); z_plane < 0 selects the
+ * box's +z face, n_z - npml.
+ *
+ * The context advances n_steps exactly as mb_step would (probes and flux
+ * included); then a reverse-time discrete adjoint of the FP32 step runs back
+ * over the window.  Forward checkpoints are kept every ckpt_every steps
+ * (<= 0: 200); each segment is recomputed and its states stored (48 bytes
+ * per cell per step) before its reverse sweep.  Noise and sources are held
+ * fixed: the gradient is that of the realization with this seed.
+ *   d_grad_eps  device array of n_cells floats (x fastest) or NULL:
+ *               dJ/d eps_r of every cell, in J per unit eps_r (each cell's
+ *               eps_r taken as its own variable), accumulated in FP64;
+ *   grad_pump   host double or NULL: dJ/dW_p in J s;
+ *   J_out       host double or NULL: the objective J.
+ * Device memory for checkpoints, the segment store and the adjoint fields is
+ * allocated for the call and freed before it returns.  Synchronous.
+ * Errors: MB_ERR_ARG (n_steps < 1, plane outside 1 <= p < n_z), MB_ERR_STATE
+ * (no material), MB_ERR_OOM, MB_ERR_CUDA. */
+int mb_adjoint_energy_zface(mb_ctx* ctx, int n_steps, int ckpt_every, int z_plane,
+                            float* d_grad_eps, double* grad_pump, double* J_out);
+
 /* The paper has no counterpart of this call: it is a service for callers
  * that cannot allocate device memory — code running while a framework's
  * caching allocator owns the device memory, code that must not pay the

@@ -93,6 +93,8 @@ _SIGS = [
     ("mb_batch_synchronize", C.c_int, [_P]),
     ("mb_batch_autotune", C.c_int, [_P]),
     ("mb_batch_get_tuning", C.c_int, [_P, C.POINTER(C.c_int)]),
+    ("mb_adjoint_energy_zface", C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P,
+                                          C.POINTER(C.c_double), C.POINTER(C.c_double)]),
 ]
 
 _lib = None
@@ -363,6 +365,16 @@ def mb_batch_get_tuning(h):
     return tuple(t)
 
 
+def mb_adjoint_energy_zface(h, n_steps, ckpt_every=200, z_plane=-1, d_grad_eps: int = 0):
+    """(J, dJ/dW_p); dJ/deps_r written to the device array at d_grad_eps (if non-zero)."""
+    gp = C.c_double()
+    J = C.c_double()
+    _check(load_library().mb_adjoint_energy_zface(h, int(n_steps), int(ckpt_every), int(z_plane),
+                                                  C.c_void_p(d_grad_eps) if d_grad_eps else None,
+                                                  C.byref(gp), C.byref(J)), h)
+    return J.value, gp.value
+
+
 class MBSimulation:
     """One Maxwell–Bloch FDTD realization on the GPU (owns one C context).
 
@@ -489,6 +501,14 @@ class MBSimulation:
 
     def device_bytes(self):
         return mb_device_bytes(self._h)
+
+    def adjoint_energy_zface(self, n_steps, ckpt_every=200, z_plane=-1):
+        """Advance n_steps; return (J, grad_eps as a torch CUDA tensor shaped
+        like the grid [k, j, i], dJ/dW_p)."""
+        import torch
+        g = torch.empty(self.shape, dtype=torch.float32, device="cuda")
+        J, gp = mb_adjoint_energy_zface(self._h, n_steps, ckpt_every, z_plane, g.data_ptr())
+        return J, g, gp
 
 
 class MBBatch:

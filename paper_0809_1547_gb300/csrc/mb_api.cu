@@ -147,6 +147,34 @@ void build_args(mb_ctx* c) {
     a.glist.count = c->glist_count;
 }
 
+// Crank–Nicolson propagator of dN/dt = A N + e s, N = (N0, N1, N2, N3):
+// M = L^-1 R, m = L^-1 e (times dt on use), L = I - (dt/2) A, R = I + (dt/2) A.
+void cn_propagator(const mb_params& p, double W_p, double dt, double M[4][4], double m[4],
+                   double Lm[4][4]) {
+    double A[4][4] = {{0}};
+    A[0][0] = -W_p;
+    A[0][1] = 1.0 / p.tau10;
+    A[1][1] = -1.0 / p.tau10;
+    A[1][2] = 1.0 / p.tau21;
+    A[2][2] = -1.0 / p.tau21;
+    A[2][3] = 1.0 / p.tau32;
+    A[3][3] = -1.0 / p.tau32;
+    A[3][0] = W_p;
+    double Rm[4][4];
+    for (int r = 0; r < 4; ++r)
+        for (int q = 0; q < 4; ++q) {
+            Lm[r][q] = (r == q ? 1.0 : 0.0) - 0.5 * dt * A[r][q];
+            Rm[r][q] = (r == q ? 1.0 : 0.0) + 0.5 * dt * A[r][q];
+        }
+    for (int q = 0; q < 4; ++q) {
+        double col[4] = {Rm[0][q], Rm[1][q], Rm[2][q], Rm[3][q]}, x[4];
+        solve4(Lm, col, x);
+        for (int r = 0; r < 4; ++r) M[r][q] = x[r];
+    }
+    const double e[4] = {0.0, -1.0, 1.0, 0.0};
+    solve4(Lm, e, m);
+}
+
 void gain_coefficients(mb_ctx* c) {
     mb::DevGain& G = c->args.gain;
     std::memset(&G, 0, sizeof(G));
@@ -167,29 +195,8 @@ void gain_coefficients(mb_ctx* c) {
     G.cJN = (float)(dt * dt * a_se * std::sqrt(N_a / (dx * dx * dx * dt)) /
                     (kEps0 * c->E0 * (1.0 + a)));
     G.nfloor = (float)p.n_floor_rel;
-    // Crank–Nicolson propagator of dN/dt = A N + e s, N = (N0, N1, N2, N3).
-    double A[4][4] = {{0}};
-    A[0][0] = -c->W_p;
-    A[0][1] = 1.0 / p.tau10;
-    A[1][1] = -1.0 / p.tau10;
-    A[1][2] = 1.0 / p.tau21;
-    A[2][2] = -1.0 / p.tau21;
-    A[2][3] = 1.0 / p.tau32;
-    A[3][3] = -1.0 / p.tau32;
-    A[3][0] = c->W_p;
-    double Lm[4][4], Rm[4][4], M[4][4], m[4];
-    for (int r = 0; r < 4; ++r)
-        for (int q = 0; q < 4; ++q) {
-            Lm[r][q] = (r == q ? 1.0 : 0.0) - 0.5 * dt * A[r][q];
-            Rm[r][q] = (r == q ? 1.0 : 0.0) + 0.5 * dt * A[r][q];
-        }
-    for (int q = 0; q < 4; ++q) {
-        double col[4] = {Rm[0][q], Rm[1][q], Rm[2][q], Rm[3][q]}, x[4];
-        solve4(Lm, col, x);
-        for (int r = 0; r < 4; ++r) M[r][q] = x[r];
-    }
-    const double e[4] = {0.0, -1.0, 1.0, 0.0};
-    solve4(Lm, e, m);
+    double M[4][4], m[4], Lm[4][4];
+    cn_propagator(p, c->W_p, dt, M, m, Lm);
     const double smk = kEps0 * c->E0 * c->E0 / (kHbar * w0 * N_a);   // m s / N_a per S_pop
     for (int r = 0; r < 3; ++r) {
         G.g[r] = (float)M[r + 1][0];
@@ -295,6 +302,34 @@ std::map<std::tuple<int, int, int, int>, std::pair<mb::PassTune, mb::PassTune>> 
 
 // (internal) message for mb_last_error(NULL) from calls without a context
 void mb::set_thread_error(const std::string& msg) { g_err = msg; }
+
+void mb::gain_pump_derivative(const mb_ctx* c, float dg[3], float dG[3][3], float dmk[3]) {
+    // dM/dW = (dt/2) L^-1 A_W (I + M), dm/dW = (dt/2) L^-1 A_W m with
+    // A_W = dA/dW_p (pump N0 -> N3), mapped to the reduced (n1, n2, n3) form
+    // as the propagator itself.
+    const double dt = c->dt;
+    double M[4][4], m[4], Lm[4][4];
+    cn_propagator(c->p, c->W_p, dt, M, m, Lm);
+    double dM[4][4], dm[4];
+    for (int q = 0; q < 4; ++q) {
+        const double top = (q == 0 ? 1.0 : 0.0) + M[0][q];   // row 0 of (I + M)
+        const double rhs[4] = {-0.5 * dt * top, 0.0, 0.0, 0.5 * dt * top};
+        double x[4];
+        solve4(Lm, rhs, x);
+        for (int r = 0; r < 4; ++r) dM[r][q] = x[r];
+    }
+    {
+        const double rhs[4] = {-0.5 * dt * m[0], 0.0, 0.0, 0.5 * dt * m[0]};
+        solve4(Lm, rhs, dm);
+    }
+    const double w0 = 2.0 * kPi * kC0 / c->p.lambda0;
+    const double smk = c->N_a > 0 ? kEps0 * c->E0 * c->E0 / (kHbar * w0 * c->N_a) : 0.0;
+    for (int r = 0; r < 3; ++r) {
+        dg[r] = (float)dM[r + 1][0];
+        for (int q = 0; q < 3; ++q) dG[r][q] = (float)(dM[r + 1][q + 1] - dM[r + 1][0]);
+        dmk[r] = (float)(dm[r + 1] * smk);
+    }
+}
 
 size_t mb::state_device_bytes(mb_ctx* c) {
     size_t total = 0;

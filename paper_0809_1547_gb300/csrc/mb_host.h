@@ -148,6 +148,9 @@ void launch_energy(const DevFields& f, int64_t ncell, const float* lut_eps, doub
 // Message returned by mb_last_error(NULL) on this thread.
 void set_thread_error(const std::string& msg);
 
+// d/dW_p of the reduced population propagator (g, G, mk of DevGain).
+void gain_pump_derivative(const mb_ctx* c, float dg[3], float dG[3][3], float dmk[3]);
+
 // Whole evolving state of a context as one device blob (for device-side
 // snapshots: autotuning, adjoint checkpoints).
 size_t state_device_bytes(mb_ctx* c);
