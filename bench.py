@@ -389,6 +389,8 @@ def bench_ours(args):
     }
     if not args.no_batched:
         out["batched"] = bench_batched(stream, args.batched_steps, args.warmup)
+    if not args.no_adjoint:
+        out["adjoint"] = bench_adjoint(stream, args.warmup)
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.grid == 320:
         try:
             rate, el, ncell = run_oracle_child(16, 6)
@@ -480,6 +482,64 @@ def bench_batched(stream, steps: int, warmup: int):
             "l2": "inputs larger than L2"}
 
 
+# ---------------------------------------------------------------- adjoint
+
+def bench_adjoint(stream, warmup: int):
+    """Gradient of the energy through the +z face w.r.t. eps (per cell) and the
+    pump on the 96^3 workload (225 spheres, 45 % fill, gain in the voids,
+    fixed pump and noise seed), 4000 steps with checkpoints every 200 steps,
+    against the plain step of the same realization over the same steps."""
+    import torch
+    from paper_0809_1547_gb300 import inputs
+    from paper_0809_1547_gb300.binding import MBSimulation, mb_default_params
+    w = inputs.workload_adjoint_96()
+    K = w.extra["ckpt_every"]
+    cells = w.ncell
+
+    def make():
+        s_ = MBSimulation(w.grid, w.dx, w.dt, mb_default_params(npml=w.npml), stream=stream.cuda_stream)
+        s_.set_material(w.eps, w.gain, w.N_a, w.pump)
+        s_.set_seed(w.seed)
+        s_.autotune()
+        return s_
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), r
+
+    s_ = make()
+    for _ in range(max(1, warmup // 3)):
+        s_.adjoint_energy_zface(2 * K, K)          # warm-up (allocations, graphs)
+    s_.close()
+    s_ = make()
+    adj_ms, (J, G, gp) = timed(lambda: s_.adjoint_energy_zface(w.steps, K))
+    s_.close()
+    p_ = make()
+    p_.step(warmup)
+    plain_ms, _ = timed(lambda: p_.step(w.steps))
+    p_.close()
+    v_adj = cells * w.steps / (adj_ms / 1e3) / 1e6
+    v_plain = cells * w.steps / (plain_ms / 1e3) / 1e6
+    return {"workload": f"{w.name}: {w.grid[0]}^3 (dx 20 nm, 8-cell CPML), {w.n_spheres} TiO2 spheres "
+                        f"d 300 nm at {w.fill:.3f} fill, gain in the voids, N_a 5e24 m^-3, W_p 1e13/s, "
+                        f"Langevin noise; gradient of the energy through the +z face w.r.t. eps (every "
+                        f"cell) and W_p over {w.steps} steps, checkpoints every {K}",
+            "value": round(v_adj, 2), "unit": UNIT, "ms_total": round(adj_ms, 2),
+            "ms_per_step": round(adj_ms / w.steps, 5),
+            "what": "forward sweep with checkpoints + per-segment recomputation + reverse sweep",
+            "plain_single_instance": {"value": round(v_plain, 2), "unit": UNIT,
+                                      "ms_per_step": round(plain_ms / w.steps, 5)},
+            "ratio_vs_plain": round(v_adj / v_plain, 4),
+            "objective_J": J, "grad_pump": gp,
+            "l2": "state (57 MB) below L2 size; segment store (8.5 GB) above"}
+
+
 # --------------------------------------------------------- reference arm
 
 def bench_reference(args):
@@ -522,6 +582,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-ensemble leg")
     ap.add_argument("--batched-steps", type=int, default=40)
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint leg")
     ap.add_argument("--tune", default="",
                     help="fixed launch shapes 'v,bx,by,bz:v,bx,by,bz' (H launch : E launch) "
                          "instead of the autotuner; for profiling a chosen variant")

@@ -52,7 +52,7 @@ struct AdjArgs {
     float dg[3], dG[3][3], dmk[3];
     int zp, rx0, rx1, ry0, ry1;
     float S;
-    long long n;                // index of the forward step being reversed
+    const long long* n_ptr;     // index of the forward step being reversed (device)
 };
 
 constexpr int kAccSlots = 64;
@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(256) k_adj_point(AdjArgs a) {
             l0z += kE * tz;
             const float ldn = G.cJE * (e0x * tx + e0y * ty + e0z * tz);
             float z0, z1, z2;
-            langevin_normals(c, (uint32_t)a.n, G.key0, G.key1, z0, z1, z2);
+            langevin_normals(c, (uint32_t)*a.n_ptr, G.key0, G.key1, z0, z1, z2);
             const float damp = n2 > 0.0f ? 0.5f * G.cJN * rsqrtf(n2 + G.nfloor) : 0.0f;
             a.ln[c] = ln1 + ldn;
             a.ln[c + N] = ln2 - ldn + damp * (z0 * tx + z1 * ty + z2 * tz);
@@ -417,7 +417,9 @@ extern "C" int mb_adjoint_energy_zface(mb_ctx* c, int n_steps, int ckpt_every, i
     float* adj = nullptr;
     double* geps = nullptr;
     double* acc = nullptr;
-    const int64_t n0 = c->n;
+    long long* slot_n = nullptr;
+    cudaGraphExec_t seg_graph = nullptr;
+    bool graph_ok = true;
     mb::AdjArgs a{};
     mb::StepArgs fa = c->args;
     mb::PassTune th = c->tune_h, te = c->tune_e;
@@ -430,6 +432,7 @@ extern "C" int mb_adjoint_energy_zface(mb_ctx* c, int n_steps, int ckpt_every, i
     MB_ACUDA(c, cudaMalloc((void**)&adj, sizeof(float) * (18 * N + psi_total)));
     MB_ACUDA(c, cudaMalloc((void**)&geps, sizeof(double) * N));
     MB_ACUDA(c, cudaMalloc((void**)&acc, sizeof(double) * 2 * mb::kAccSlots));
+    MB_ACUDA(c, cudaMalloc((void**)&slot_n, sizeof(long long) * (K + 1)));
 
     // forward sweep with a checkpoint at the start of every segment
     for (int m = 0; m < nseg; ++m) {
@@ -472,37 +475,71 @@ extern "C" int mb_adjoint_energy_zface(mb_ctx* c, int n_steps, int ckpt_every, i
     a.ry1 = c->args.flux.r1[1];
     a.S = c->args.S;
 
-    for (int m = nseg - 1; m >= 0; --m) {
-        const int s0 = m * K, len = std::min(K, n_steps - s0);
-        if ((rc = mb::state_restore(c, ckpt + sb * m))) goto done;
+    {
+        // One segment: recompute from its checkpoint (already restored into the
+        // context), keeping every state and the step counter, then reverse it.
         const float* F = c->d_fields;
-        auto keep = [&](int t) -> cudaError_t {
-            float* dst = store + slot * t;
-            cudaError_t e = cudaMemcpyAsync(dst, F, sizeof(float) * 6 * N, cudaMemcpyDeviceToDevice, c->stream);
-            if (e != cudaSuccess) return e;
-            return cudaMemcpyAsync(dst + 6 * N, F + 9 * N, sizeof(float) * 6 * N, cudaMemcpyDeviceToDevice,
-                                   c->stream);
-        };
-        MB_ACUDA(c, keep(0));
-        for (int t = 0; t < len; ++t) {
-            mb::launch_h_pass(fa, th, c->stream);
-            mb::launch_e_pass(fa, te, nullptr, c->stream);
-            MB_ACUDA(c, keep(t + 1));
-        }
-        for (int t = len - 1; t >= 0; --t) {
-            auto fields = [&](int q) {
-                const float* b = store + slot * q;
-                return mb::FwdFields{b, b + N, b + 2 * N, b + 3 * N, b + 4 * N, b + 5 * N,
-                                     b + 6 * N, b + 7 * N, b + 8 * N, b + 9 * N, b + 10 * N, b + 11 * N};
+        auto enqueue_segment = [&](int len) -> cudaError_t {
+            auto keep = [&](int t) -> cudaError_t {
+                float* dst = store + slot * t;
+                cudaError_t e = cudaMemcpyAsync(dst, F, sizeof(float) * 6 * N, cudaMemcpyDeviceToDevice,
+                                                c->stream);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(dst + 6 * N, F + 9 * N, sizeof(float) * 6 * N,
+                                        cudaMemcpyDeviceToDevice, c->stream);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(slot_n + t, c->d_ctr, sizeof(long long), cudaMemcpyDeviceToDevice,
+                                        c->stream);
+                return e;
             };
-            a.x0 = fields(t);
-            a.x1 = fields(t + 1);
-            a.n = (long long)(n0 + s0 + t);
-            mb::k_adj_point<<<grd, blk, 0, c->stream>>>(a);
-            mb::k_adj_h<<<grd, blk, 0, c->stream>>>(a);
-            mb::k_adj_e<<<grd, blk, 0, c->stream>>>(a);
+            cudaError_t e = keep(0);
+            for (int t = 0; t < len && e == cudaSuccess; ++t) {
+                mb::launch_h_pass(fa, th, c->stream);
+                mb::launch_e_pass(fa, te, nullptr, c->stream);
+                e = keep(t + 1);
+            }
+            for (int t = len - 1; t >= 0 && e == cudaSuccess; --t) {
+                auto fields = [&](int q) {
+                    const float* b = store + slot * q;
+                    return mb::FwdFields{b, b + N, b + 2 * N, b + 3 * N, b + 4 * N, b + 5 * N,
+                                         b + 6 * N, b + 7 * N, b + 8 * N, b + 9 * N, b + 10 * N, b + 11 * N};
+                };
+                a.x0 = fields(t);
+                a.x1 = fields(t + 1);
+                a.n_ptr = slot_n + t;
+                mb::k_adj_point<<<grd, blk, 0, c->stream>>>(a);
+                mb::k_adj_h<<<grd, blk, 0, c->stream>>>(a);
+                mb::k_adj_e<<<grd, blk, 0, c->stream>>>(a);
+                e = cudaGetLastError();
+            }
+            return e;
+        };
+        for (int m = nseg - 1; m >= 0; --m) {
+            const int s0 = m * K, len = std::min(K, n_steps - s0);
+            if ((rc = mb::state_restore(c, ckpt + sb * m))) goto done;
+            if (len == K && graph_ok && !seg_graph) {
+                // full segments repeat the same launches: capture them once
+                cudaGraph_t g = nullptr;
+                graph_ok = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+                if (graph_ok) {
+                    const cudaError_t le = enqueue_segment(K);
+                    const cudaError_t ce = cudaStreamEndCapture(c->stream, &g);
+                    graph_ok = le == cudaSuccess && ce == cudaSuccess &&
+                               cudaGraphInstantiate(&seg_graph, g, 0) == cudaSuccess;
+                    if (g) cudaGraphDestroy(g);
+                }
+                if (!graph_ok) {
+                    cudaGetLastError();
+                    if (seg_graph) cudaGraphExecDestroy(seg_graph);
+                    seg_graph = nullptr;
+                }
+            }
+            if (len == K && seg_graph) {
+                MB_ACUDA(c, cudaGraphLaunch(seg_graph, c->stream));
+            } else {
+                MB_ACUDA(c, enqueue_segment(len));
+            }
         }
-        MB_ACUDA(c, cudaGetLastError());
     }
     // back to the state after the forward sweep
     if ((rc = mb::state_restore(c, ckpt + sb * nseg))) goto done;
@@ -525,7 +562,8 @@ extern "C" int mb_adjoint_energy_zface(mb_ctx* c, int n_steps, int ckpt_every, i
     }
 done:
     if (c->stream) cudaStreamSynchronize(c->stream);
-    void* bufs[] = {ckpt, store, adj, geps, acc};
+    if (seg_graph) cudaGraphExecDestroy(seg_graph);
+    void* bufs[] = {ckpt, store, adj, geps, acc, slot_n};
     for (void* p : bufs)
         if (p) cudaFree(p);
     return rc;
