@@ -85,13 +85,13 @@ def algorithmic_bytes(w):
             "gain_fraction": g, "slab_fraction_sum": slab}
 
 
-def traffic_from_profile(kernel: str):
-    """DRAM bytes per launch of `kernel` at full size from the committed ncu
-    summary profiles/<kernel>_traffic.md, if it was taken on the current
-    kernel sources (else None)."""
+def traffic_from_profile(kernel: str, workload: str = "mb320_active"):
+    """DRAM bytes per launch of `kernel` on `workload` from the committed ncu
+    summary profiles/<kernel>_traffic_<workload>.md, if it was taken on the
+    current kernel sources (else None)."""
     import re
     try:
-        with open(os.path.join(PROFILE_DIR, f"{kernel}_traffic.md")) as f:
+        with open(os.path.join(PROFILE_DIR, f"{kernel}_traffic_{workload}.md")) as f:
             text = f.read()
         h = re.search(r"kernel_source_hash:\s*(\w+)", text).group(1)
         if h != kernel_source_hash():
@@ -321,7 +321,7 @@ def bench_ours(args):
     dom_ms, dom_bpc, dom_key = launches[dom_name]
     dom_bytes = dom_bpc * cells
     achieved = dom_bytes / (dom_ms / 1e3) / 1e9
-    traffic = traffic_from_profile(dom_key)
+    traffic = traffic_from_profile(dom_key, w.name) if args.grid == 320 else None
     step_ms = elapsed_ms / args.steps
     other = {k: {"avg_launch_ms": round(v[0], 5), "bytes_per_cell": round(v[1], 2),
                  "achieved_gbs": round(v[1] * cells / (v[0] / 1e3) / 1e9, 1)}
@@ -393,9 +393,9 @@ def bench_ours(args):
         out["adjoint"] = bench_adjoint(stream, args.warmup)
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.grid == 320:
         try:
-            rate, el, ncell = run_oracle_child(16, 6)
+            rate, el, ncell = run_oracle_child(32, 17)
             out["cpu_baseline"] = {"value": round(rate, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
-                                   "sample": f"6 steps (after 1 warm-up) of a 320x320x16 slab "
+                                   "sample": f"17 steps (after 1 warm-up) of a 320x320x32 slab "
                                              f"({ncell} cells) of the same workload, FP64 numpy, "
                                              f"one thread, {el:.1f} s"}
         except Exception as e:   # keep the GPU line even if the CPU leg fails

@@ -77,18 +77,17 @@ __device__ __forceinline__ unsigned block_slot() {
 }
 
 // ------------------------------------------------------------------- R1
-__global__ void __launch_bounds__(256) k_adj_point(AdjArgs a) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k = blockIdx.z;
-    const bool valid = i < a.g.nx && j < a.g.ny;
+// Pointwise part of the reverse of the step (x0 -> x1) at cell (i, j, k),
+// given lambda_E of x1 in l1x..l1z; every lane of the warp must call it
+// (valid false for lanes outside the grid).
+__device__ __forceinline__ void adj_point_cell(const AdjArgs& a, int i, int j, int k, bool valid,
+                                               float l1x, float l1y, float l1z) {
     float obj = 0.0f, gw = 0.0f;
     if (valid) {
         const uint32_t N = a.g.ncell;
         const uint32_t c = (uint32_t)i + (uint32_t)a.g.nx * j + a.g.nxy * k;
         const float e0x = __ldg(a.x0.ex + c), e0y = __ldg(a.x0.ey + c), e0z = __ldg(a.x0.ez + c);
         const float e1x = __ldg(a.x1.ex + c), e1y = __ldg(a.x1.ey + c), e1z = __ldg(a.x1.ez + c);
-        float l1x = a.le[c], l1y = a.le[c + N], l1z = a.le[c + 2 * N];
         float l0x = 0.0f, l0y = 0.0f, l0z = 0.0f;
         // objective: mx Hy(k-1) - my Hx(k-1) on the plane k = zp
         if (k == a.zp && i >= a.rx0 && i < a.rx1 && j >= a.ry0 && j < a.ry1) {
@@ -205,6 +204,22 @@ __global__ void __launch_bounds__(256) k_adj_point(AdjArgs a) {
     const unsigned slot = block_slot();
     warp_acc(a.acc, obj, slot);
     warp_acc(a.acc + kAccSlots, gw, slot);
+}
+
+__global__ void __launch_bounds__(256) k_adj_point(AdjArgs a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    const bool valid = i < a.g.nx && j < a.g.ny;
+    float l1x = 0.0f, l1y = 0.0f, l1z = 0.0f;
+    if (valid) {
+        const uint32_t N = a.g.ncell;
+        const uint32_t c = (uint32_t)i + (uint32_t)a.g.nx * j + a.g.nxy * k;
+        l1x = a.le[c];
+        l1y = a.le[c + N];
+        l1z = a.le[c + 2 * N];
+    }
+    adj_point_cell(a, i, j, k, valid, l1x, l1y, l1z);
 }
 
 // ------------------------------------------------------------------- R2
@@ -348,6 +363,20 @@ __device__ __forceinline__ WCoef v_coef(const AdjArgs& a, int i, int j, int k) {
     return v;
 }
 
+// lambda_E of x^n at cell (i, j, k): the partial value left in le by R1 plus
+// the transposed H update (backward differences of the V coefficients).
+__device__ __forceinline__ void adj_e_gather(const AdjArgs& a, int i, int j, int k, uint32_t c,
+                                             float& lx, float& ly, float& lz) {
+    const uint32_t N = a.g.ncell;
+    const WCoef v0 = v_coef(a, i, j, k);
+    const WCoef vi = v_coef(a, i - 1, j, k);
+    const WCoef vj = v_coef(a, i, j - 1, k);
+    const WCoef vk = v_coef(a, i, j, k - 1);
+    lx = a.le[c] + ((vk.yz - v0.yz) + (vj.zy - v0.zy));
+    ly = a.le[c + N] + ((vk.xz - v0.xz) + (vi.zx - v0.zx));
+    lz = a.le[c + 2 * N] + ((vj.xy - v0.xy) + (vi.yx - v0.yx));
+}
+
 __global__ void __launch_bounds__(256) k_adj_e(AdjArgs a) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -355,13 +384,51 @@ __global__ void __launch_bounds__(256) k_adj_e(AdjArgs a) {
     if (i >= a.g.nx || j >= a.g.ny) return;
     const uint32_t N = a.g.ncell;
     const uint32_t c = (uint32_t)i + (uint32_t)a.g.nx * j + a.g.nxy * k;
-    const WCoef v0 = v_coef(a, i, j, k);
-    const WCoef vi = v_coef(a, i - 1, j, k);
-    const WCoef vj = v_coef(a, i, j - 1, k);
-    const WCoef vk = v_coef(a, i, j, k - 1);
-    a.le[c] += (vk.yz - v0.yz) + (vj.zy - v0.zy);
-    a.le[c + N] += (vk.xz - v0.xz) + (vi.zx - v0.zx);
-    a.le[c + 2 * N] += (vj.xy - v0.xy) + (vi.yx - v0.yx);
+    float lx, ly, lz;
+    adj_e_gather(a, i, j, k, c, lx, ly, lz);
+    a.le[c] = lx;
+    a.le[c + N] = ly;
+    a.le[c + 2 * N] = lz;
+}
+
+// R3 of step n fused with R1 of step n - 1 (a's x0, x1, n_ptr describe
+// step n - 1): lambda_E of x^n stays in registers.  R3 reads lambda_H and the
+// psi_H memories of neighbours, which R1 does not write.
+__global__ void __launch_bounds__(256) k_adj_e_point(AdjArgs a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    const bool valid = i < a.g.nx && j < a.g.ny;
+    float lx = 0.0f, ly = 0.0f, lz = 0.0f;
+    if (valid) adj_e_gather(a, i, j, k, (uint32_t)i + (uint32_t)a.g.nx * j + a.g.nxy * k, lx, ly, lz);
+    adj_point_cell(a, i, j, k, valid, lx, ly, lz);
+}
+
+// Store slot of one step: E, H (arrays 0..5) and J, n1..n3 (arrays 9..14)
+// of the field block, and the step counter.  16-byte moves when n_cells is
+// a multiple of 4 (every array then starts 16-byte aligned).
+__global__ void k_keep(const float* __restrict__ F, float* __restrict__ dst, uint32_t n,
+                       const long long* __restrict__ ctr, long long* __restrict__ slot_n) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *slot_n = *ctr;
+    const size_t n6 = 6 * (size_t)n;
+    const size_t t0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    if ((n & 3u) == 0) {
+        const size_t q6 = n6 / 4;
+        const float4* a = reinterpret_cast<const float4*>(F);
+        const float4* b = reinterpret_cast<const float4*>(F + 9 * (size_t)n);
+        float4* d = reinterpret_cast<float4*>(dst);
+        for (size_t t = t0; t < q6; t += stride) {
+            d[t] = a[t];
+            d[t + q6] = b[t];
+        }
+    } else {
+        const float* b = F + 9 * (size_t)n;
+        for (size_t t = t0; t < n6; t += stride) {
+            dst[t] = F[t];
+            dst[t + n6] = b[t];
+        }
+    }
 }
 
 // Output: grad[c] = scale * geps[c].
@@ -409,7 +476,7 @@ extern "C" int mb_adjoint_energy_zface(mb_ctx* c, int n_steps, int ckpt_every, i
     const size_t N = (size_t)c->ncell;
     const size_t sb = mb::state_device_bytes(c);
     const size_t slot = 12 * N;   // floats per stored step: E, H, J, n1..n3
-    size_t psi_total = c->psi_elems[0] + c->psi_elems[1] + c->psi_elems[2];
+    const size_t psi_total = c->psi_elems[0] + c->psi_elems[1] + c->psi_elems[2];
 
     int rc = MB_OK;
     char* ckpt = nullptr;
@@ -422,10 +489,61 @@ extern "C" int mb_adjoint_energy_zface(mb_ctx* c, int n_steps, int ckpt_every, i
     bool graph_ok = true;
     mb::AdjArgs a{};
     mb::StepArgs fa = c->args;
-    mb::PassTune th = c->tune_h, te = c->tune_e;
+    const mb::PassTune th = c->tune_h, te = c->tune_e;
+    const mb::TmaMapsE* tma = mb::tma_maps(c, te);
+    const mb::PassTune te_r =
+        (te.variant == mb::kVariantTma && !tma) ? mb::PassTune{mb::kVariantZmarch, dim3(32, 4, 1), 16} : te;
     double acc_h[2 * mb::kAccSlots];
     const dim3 blk(32, 8, 1);
     const dim3 grd((c->nx + 31) / 32, (c->ny + 7) / 8, c->nz);
+    const float* F = c->d_fields;
+
+    // keep(t): the context's E, H, J, n1..n3 and step counter into store slot t
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int keep_blocks = (int)std::max<size_t>(1, std::min<size_t>((6 * N / 4 + 255) / 256, (size_t)sms * 8));
+    auto keep = [&](int t) -> cudaError_t {
+        mb::k_keep<<<keep_blocks, 256, 0, c->stream>>>(F, store + slot * t, (uint32_t)N, c->d_ctr, slot_n + t);
+        return cudaGetLastError();
+    };
+    auto step_args = [&](int t) {
+        auto fields = [&](int q) {
+            const float* b = store + slot * q;
+            return mb::FwdFields{b, b + N, b + 2 * N, b + 3 * N, b + 4 * N, b + 5 * N,
+                                 b + 6 * N, b + 7 * N, b + 8 * N, b + 9 * N, b + 10 * N, b + 11 * N};
+        };
+        a.x0 = fields(t);
+        a.x1 = fields(t + 1);
+        a.n_ptr = slot_n + t;
+    };
+    // the reverse of stored steps len-1 .. 0: R1, then per step R2 and R3
+    // fused with the next step's R1
+    auto reverse = [&](int len) -> cudaError_t {
+        step_args(len - 1);
+        mb::k_adj_point<<<grd, blk, 0, c->stream>>>(a);
+        for (int t = len - 1; t >= 0; --t) {
+            mb::k_adj_h<<<grd, blk, 0, c->stream>>>(a);
+            if (t > 0) {
+                step_args(t - 1);
+                mb::k_adj_e_point<<<grd, blk, 0, c->stream>>>(a);
+            } else {
+                mb::k_adj_e<<<grd, blk, 0, c->stream>>>(a);
+            }
+        }
+        return cudaGetLastError();
+    };
+    // recompute a segment from the checkpoint restored into the context
+    // (same pass kernels, probes and flux off), keeping every state
+    auto recompute = [&](int len) -> cudaError_t {
+        cudaError_t e = keep(0);
+        for (int t = 0; t < len && e == cudaSuccess; ++t) {
+            mb::launch_h_pass(fa, th, c->stream);
+            mb::launch_e_pass(fa, te_r, te_r.variant == mb::kVariantTma ? tma : nullptr, c->stream);
+            e = keep(t + 1);
+        }
+        return e;
+    };
 
     MB_ACUDA(c, cudaMalloc((void**)&ckpt, sb * (nseg + 1)));
     MB_ACUDA(c, cudaMalloc((void**)&store, sizeof(float) * slot * (K + 1)));
@@ -434,10 +552,19 @@ extern "C" int mb_adjoint_energy_zface(mb_ctx* c, int n_steps, int ckpt_every, i
     MB_ACUDA(c, cudaMalloc((void**)&acc, sizeof(double) * 2 * mb::kAccSlots));
     MB_ACUDA(c, cudaMalloc((void**)&slot_n, sizeof(long long) * (K + 1)));
 
-    // forward sweep with a checkpoint at the start of every segment
-    for (int m = 0; m < nseg; ++m) {
+    // forward sweep: a checkpoint at the start of every segment but the last,
+    // whose states are kept as it runs (it is reversed first)
+    for (int m = 0; m + 1 < nseg; ++m) {
         if ((rc = mb::state_snapshot(c, ckpt + sb * m))) goto done;
-        if ((rc = mb_step(c, std::min(K, n_steps - m * K)))) goto done;
+        if ((rc = mb_step(c, K))) goto done;
+    }
+    {
+        const int len = n_steps - (nseg - 1) * K;
+        MB_ACUDA(c, keep(0));
+        for (int t = 0; t < len; ++t) {
+            MB_ACUDA(c, mb::enqueue_step(c));
+            MB_ACUDA(c, keep(t + 1));
+        }
     }
     if ((rc = mb::state_snapshot(c, ckpt + sb * nseg))) goto done;
 
@@ -445,10 +572,7 @@ extern "C" int mb_adjoint_energy_zface(mb_ctx* c, int n_steps, int ckpt_every, i
     MB_ACUDA(c, cudaMemsetAsync(geps, 0, sizeof(double) * N, c->stream));
     MB_ACUDA(c, cudaMemsetAsync(acc, 0, sizeof(double) * 2 * mb::kAccSlots, c->stream));
 
-    // recomputation: same per-cell arithmetic, no probes or flux
     fa.flux.on = 0;
-    if (te.variant == mb::kVariantTma) te = mb::PassTune{mb::kVariantZmarch, dim3(32, 4, 1), 16};
-
     a.g = c->args.g;
     a.L = c->p.npml;
     a.mat = c->d_mat;
@@ -475,70 +599,34 @@ extern "C" int mb_adjoint_energy_zface(mb_ctx* c, int n_steps, int ckpt_every, i
     a.ry1 = c->args.flux.r1[1];
     a.S = c->args.S;
 
-    {
-        // One segment: recompute from its checkpoint (already restored into the
-        // context), keeping every state and the step counter, then reverse it.
-        const float* F = c->d_fields;
-        auto enqueue_segment = [&](int len) -> cudaError_t {
-            auto keep = [&](int t) -> cudaError_t {
-                float* dst = store + slot * t;
-                cudaError_t e = cudaMemcpyAsync(dst, F, sizeof(float) * 6 * N, cudaMemcpyDeviceToDevice,
-                                                c->stream);
-                if (e == cudaSuccess)
-                    e = cudaMemcpyAsync(dst + 6 * N, F + 9 * N, sizeof(float) * 6 * N,
-                                        cudaMemcpyDeviceToDevice, c->stream);
-                if (e == cudaSuccess)
-                    e = cudaMemcpyAsync(slot_n + t, c->d_ctr, sizeof(long long), cudaMemcpyDeviceToDevice,
-                                        c->stream);
-                return e;
-            };
-            cudaError_t e = keep(0);
-            for (int t = 0; t < len && e == cudaSuccess; ++t) {
-                mb::launch_h_pass(fa, th, c->stream);
-                mb::launch_e_pass(fa, te, nullptr, c->stream);
-                e = keep(t + 1);
+    // the last segment is in the store already
+    MB_ACUDA(c, reverse(n_steps - (nseg - 1) * K));
+    for (int m = nseg - 2; m >= 0; --m) {
+        if ((rc = mb::state_restore(c, ckpt + sb * m))) goto done;
+        if (graph_ok && !seg_graph) {
+            // every earlier segment is full and repeats the same launches:
+            // capture recomputation + reverse once
+            cudaGraph_t g = nullptr;
+            graph_ok = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+            if (graph_ok) {
+                cudaError_t le = recompute(K);
+                if (le == cudaSuccess) le = reverse(K);
+                const cudaError_t ce = cudaStreamEndCapture(c->stream, &g);
+                graph_ok = le == cudaSuccess && ce == cudaSuccess &&
+                           cudaGraphInstantiate(&seg_graph, g, 0) == cudaSuccess;
+                if (g) cudaGraphDestroy(g);
             }
-            for (int t = len - 1; t >= 0 && e == cudaSuccess; --t) {
-                auto fields = [&](int q) {
-                    const float* b = store + slot * q;
-                    return mb::FwdFields{b, b + N, b + 2 * N, b + 3 * N, b + 4 * N, b + 5 * N,
-                                         b + 6 * N, b + 7 * N, b + 8 * N, b + 9 * N, b + 10 * N, b + 11 * N};
-                };
-                a.x0 = fields(t);
-                a.x1 = fields(t + 1);
-                a.n_ptr = slot_n + t;
-                mb::k_adj_point<<<grd, blk, 0, c->stream>>>(a);
-                mb::k_adj_h<<<grd, blk, 0, c->stream>>>(a);
-                mb::k_adj_e<<<grd, blk, 0, c->stream>>>(a);
-                e = cudaGetLastError();
+            if (!graph_ok) {
+                cudaGetLastError();
+                if (seg_graph) cudaGraphExecDestroy(seg_graph);
+                seg_graph = nullptr;
             }
-            return e;
-        };
-        for (int m = nseg - 1; m >= 0; --m) {
-            const int s0 = m * K, len = std::min(K, n_steps - s0);
-            if ((rc = mb::state_restore(c, ckpt + sb * m))) goto done;
-            if (len == K && graph_ok && !seg_graph) {
-                // full segments repeat the same launches: capture them once
-                cudaGraph_t g = nullptr;
-                graph_ok = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
-                if (graph_ok) {
-                    const cudaError_t le = enqueue_segment(K);
-                    const cudaError_t ce = cudaStreamEndCapture(c->stream, &g);
-                    graph_ok = le == cudaSuccess && ce == cudaSuccess &&
-                               cudaGraphInstantiate(&seg_graph, g, 0) == cudaSuccess;
-                    if (g) cudaGraphDestroy(g);
-                }
-                if (!graph_ok) {
-                    cudaGetLastError();
-                    if (seg_graph) cudaGraphExecDestroy(seg_graph);
-                    seg_graph = nullptr;
-                }
-            }
-            if (len == K && seg_graph) {
-                MB_ACUDA(c, cudaGraphLaunch(seg_graph, c->stream));
-            } else {
-                MB_ACUDA(c, enqueue_segment(len));
-            }
+        }
+        if (seg_graph) {
+            MB_ACUDA(c, cudaGraphLaunch(seg_graph, c->stream));
+        } else {
+            MB_ACUDA(c, recompute(K));
+            MB_ACUDA(c, reverse(K));
         }
     }
     // back to the state after the forward sweep

@@ -331,6 +331,20 @@ void mb::gain_pump_derivative(const mb_ctx* c, float dg[3], float dG[3][3], floa
     }
 }
 
+const mb::TmaMapsE* mb::tma_maps(mb_ctx* c, const mb::PassTune& t) { return tma_for(c, t); }
+
+cudaError_t mb::enqueue_step(mb_ctx* c) {
+    mb::DevPointProbes pp{(int)c->probes.size(), c->probe_nfreq, c->d_probe_cell,
+                          c->d_probe_omega, c->d_probe_acc};
+    mb::launch_h_pass(c->args, c->tune_h, c->stream);
+    mb::launch_e_pass(c->args, c->tune_e, tma_for(c, c->tune_e), c->stream);
+    mb::launch_point_dft(pp, c->args.f, c->d_ctr, c->dt, c->stream);
+    mb::launch_face_dft(c->face, c->args.f, c->args.g, c->d_ctr, c->dt, c->stream);
+    c->n += 1;
+    c->launches += launches_per_step(c);
+    return cudaGetLastError();
+}
+
 size_t mb::state_device_bytes(mb_ctx* c) {
     size_t total = 0;
     for (auto& p : state_parts(c)) total += p.bytes;

@@ -148,6 +148,14 @@ void launch_energy(const DevFields& f, int64_t ncell, const float* lut_eps, doub
 // Message returned by mb_last_error(NULL) on this thread.
 void set_thread_error(const std::string& msg);
 
+// Tensor maps of the context's TMA E pass for tuning t (nullptr if t is not
+// a TMA tuning or the maps cannot be encoded).
+const TmaMapsE* tma_maps(mb_ctx* c, const PassTune& t);
+
+// Enqueue one full step exactly as mb_step runs it, without a graph (the two
+// passes with the context's tuning, then the probes); advances the count.
+cudaError_t enqueue_step(mb_ctx* c);
+
 // d/dW_p of the reduced population propagator (g, G, mk of DevGain).
 void gain_pump_derivative(const mb_ctx* c, float dg[3], float dG[3][3], float dmk[3]);
 
