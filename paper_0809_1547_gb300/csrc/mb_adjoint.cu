@@ -490,7 +490,7 @@ extern "C" int mb_adjoint_energy_zface(mb_ctx* c, int n_steps, int ckpt_every, i
     mb::AdjArgs a{};
     mb::StepArgs fa = c->args;
     const mb::PassTune th = c->tune_h, te = c->tune_e;
-    const mb::TmaMapsE* tma = mb::tma_maps(c, te);
+    const mb::TmaMaps* tma = mb::tma_maps(c, te);
     const mb::PassTune te_r =
         (te.variant == mb::kVariantTma && !tma) ? mb::PassTune{mb::kVariantZmarch, dim3(32, 4, 1), 16} : te;
     double acc_h[2 * mb::kAccSlots];
@@ -538,7 +538,7 @@ extern "C" int mb_adjoint_energy_zface(mb_ctx* c, int n_steps, int ckpt_every, i
     auto recompute = [&](int len) -> cudaError_t {
         cudaError_t e = keep(0);
         for (int t = 0; t < len && e == cudaSuccess; ++t) {
-            mb::launch_h_pass(fa, th, c->stream);
+            mb::launch_h_pass(fa, th, th.variant == mb::kVariantTma ? mb::tma_maps(c, th) : nullptr, c->stream);
             mb::launch_e_pass(fa, te_r, te_r.variant == mb::kVariantTma ? tma : nullptr, c->stream);
             e = keep(t + 1);
         }

@@ -235,13 +235,13 @@ std::vector<StatePart> state_parts(mb_ctx* c) {
 }
 
 // Tensor maps for a TMA tuning (encoded once per tile shape), else nullptr.
-const mb::TmaMapsE* tma_for(mb_ctx* c, const mb::PassTune& t) {
+const mb::TmaMaps* tma_for(mb_ctx* c, const mb::PassTune& t) {
     if (t.variant != mb::kVariantTma) return nullptr;
     const auto key = std::make_pair((int)t.block.x, (int)t.block.y);
     auto it = c->tma_maps.find(key);
     if (it != c->tma_maps.end()) return &it->second;
-    mb::TmaMapsE m;
-    if (!mb::encode_tma_e(c->args, t.block.x, t.block.y, &m)) return nullptr;
+    mb::TmaMaps m;
+    if (!mb::encode_tma(c->args, t.block.x, t.block.y, &m)) return nullptr;
     return &(c->tma_maps[key] = m);
 }
 
@@ -263,7 +263,7 @@ int capture_steps(mb_ctx* c, int steps, cudaGraphExec_t* out) {
     mb::DevPointProbes pp{(int)c->probes.size(), c->probe_nfreq, c->d_probe_cell,
                           c->d_probe_omega, c->d_probe_acc};
     for (int s = 0; s < steps; ++s) {
-        mb::launch_h_pass(c->args, c->tune_h, c->stream);
+        mb::launch_h_pass(c->args, c->tune_h, tma_for(c, c->tune_h), c->stream);
         mb::launch_e_pass(c->args, c->tune_e, tma_for(c, c->tune_e), c->stream);
         mb::launch_point_dft(pp, c->args.f, c->d_ctr, c->dt, c->stream);
         mb::launch_face_dft(c->face, c->args.f, c->args.g, c->d_ctr, c->dt, c->stream);
@@ -331,12 +331,12 @@ void mb::gain_pump_derivative(const mb_ctx* c, float dg[3], float dG[3][3], floa
     }
 }
 
-const mb::TmaMapsE* mb::tma_maps(mb_ctx* c, const mb::PassTune& t) { return tma_for(c, t); }
+const mb::TmaMaps* mb::tma_maps(mb_ctx* c, const mb::PassTune& t) { return tma_for(c, t); }
 
 cudaError_t mb::enqueue_step(mb_ctx* c) {
     mb::DevPointProbes pp{(int)c->probes.size(), c->probe_nfreq, c->d_probe_cell,
                           c->d_probe_omega, c->d_probe_acc};
-    mb::launch_h_pass(c->args, c->tune_h, c->stream);
+    mb::launch_h_pass(c->args, c->tune_h, tma_for(c, c->tune_h), c->stream);
     mb::launch_e_pass(c->args, c->tune_e, tma_for(c, c->tune_e), c->stream);
     mb::launch_point_dft(pp, c->args.f, c->d_ctr, c->dt, c->stream);
     mb::launch_face_dft(c->face, c->args.f, c->args.g, c->d_ctr, c->dt, c->stream);
@@ -805,7 +805,7 @@ int mb_step_timed(mb_ctx* c, int n, double* ms_out) {
     for (int s = 0; s < n; ++s) {
         cudaEvent_t* e = &ev[(size_t)5 * s];
         cudaEventRecord(e[0], c->stream);
-        mb::launch_h_pass(c->args, c->tune_h, c->stream);
+        mb::launch_h_pass(c->args, c->tune_h, tma_for(c, c->tune_h), c->stream);
         cudaEventRecord(e[1], c->stream);
         mb::launch_e_pass(c->args, c->tune_e, tma_for(c, c->tune_e), c->stream);
         cudaEventRecord(e[2], c->stream);
@@ -1049,11 +1049,10 @@ int mb_autotune(mb_ctx* c) {
         for (dim3 b : {dim3(32, 2, 1), dim3(32, 4, 1), dim3(32, 8, 1), dim3(64, 2, 1), dim3(64, 4, 1),
                        dim3(128, 2, 1)})
             for (int kz : {4, 8, 16, 32}) cands.push_back({mb::kVariantVec, b, kz});
-    std::vector<mb::PassTune> cands_e_only;
     if (mb::tma_e_supported(c->args))
         for (dim3 b : {dim3(32, 4, 1), dim3(32, 8, 1), dim3(64, 4, 1), dim3(64, 8, 1), dim3(128, 2, 1),
                        dim3(128, 4, 1)})
-            for (int kz : {8, 16, 32, 64}) cands_e_only.push_back({mb::kVariantTma, b, kz});
+            for (int kz : {8, 16, 32, 64}) cands.push_back({mb::kVariantTma, b, kz});
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -1062,12 +1061,13 @@ int mb_autotune(mb_ctx* c) {
     const int reps = c->ncell > 4000000 ? 2 : 6;
     for (const mb::PassTune& t : cands) {
         if (t.variant != mb::kVariant3D && t.kz > 2 * c->nz) continue;
+        if (t.variant == mb::kVariantTma && !tma_for(c, t)) continue;
         for (int pass = 0; pass < 2; ++pass) {
-            if (pass == 0) mb::launch_h_pass(c->args, t, c->stream);
+            if (pass == 0) mb::launch_h_pass(c->args, t, tma_for(c, t), c->stream);
             else mb::launch_e_pass(c->args, t, tma_for(c, t), c->stream);
             cudaEventRecord(e0, c->stream);
             for (int r = 0; r < reps; ++r) {
-                if (pass == 0) mb::launch_h_pass(c->args, t, c->stream);
+                if (pass == 0) mb::launch_h_pass(c->args, t, tma_for(c, t), c->stream);
                 else mb::launch_e_pass(c->args, t, tma_for(c, t), c->stream);
             }
             cudaEventRecord(e1, c->stream);
@@ -1077,17 +1077,6 @@ int mb_autotune(mb_ctx* c) {
             if (pass == 0 && ms < best_h) { best_h = ms; bh = t; }
             if (pass == 1 && ms < best_e) { best_e = ms; be = t; }
         }
-    }
-    for (const mb::PassTune& t : cands_e_only) {
-        if (t.kz > 2 * c->nz || !tma_for(c, t)) continue;
-        mb::launch_e_pass(c->args, t, tma_for(c, t), c->stream);
-        cudaEventRecord(e0, c->stream);
-        for (int r = 0; r < reps; ++r) mb::launch_e_pass(c->args, t, tma_for(c, t), c->stream);
-        cudaEventRecord(e1, c->stream);
-        cudaEventSynchronize(e1);
-        float ms = 0;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best_e) { best_e = ms; be = t; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1136,10 +1125,10 @@ int mb_set_tuning(mb_ctx* c, const int tune_h[4], const int tune_e[4]) {
         const bool vec = b[0] == mb::kVariantVec;
         if (vec && !mb::vec_supported(c->args))
             return fail(c, MB_ERR_ARG, "the quad-vectorised passes need n_x % 4 == 0");
-        if ((b[0] != mb::kVariant3D && b[0] != mb::kVariantZmarch && !vec && !(tma && q == 1)) ||
+        if ((b[0] != mb::kVariant3D && b[0] != mb::kVariantZmarch && !vec && !tma) ||
             b[1] < 32 || b[1] % 32 || b[2] < 1 || b[3] < 1)
             return fail(c, MB_ERR_ARG,
-                        "bad tuning: variant 0/1 (2 for the E pass), x a multiple of 32, y, z >= 1");
+                        "bad tuning: variant 0..3, x a multiple of 32, y, z >= 1");
         const int threads = b[1] * b[2] * (b[0] == mb::kVariant3D ? b[3] : 1);
         if (threads > (vec ? 256 : 512))
             return fail(c, MB_ERR_ARG, "at most 512 threads per block (256 for the quad variant)");
@@ -1147,7 +1136,7 @@ int mb_set_tuning(mb_ctx* c, const int tune_h[4], const int tune_e[4]) {
         t[q].block = dim3(b[1], b[2], b[0] == mb::kVariant3D ? b[3] : 1);
         t[q].kz = b[0] == mb::kVariant3D ? 1 : b[3];
         if (tma && !tma_for(c, t[q]))
-            return fail(c, MB_ERR_ARG, "TMA E pass needs n_x % 16 == 0 and a tile of 32x4, 32x8, "
+            return fail(c, MB_ERR_ARG, "the TMA passes need n_x % 16 == 0 and a tile of 32x4, 32x8, "
                                        "64x4, 64x8, 128x2 or 128x4");
     }
     c->tune_h = t[0];

@@ -64,7 +64,7 @@ struct DevFaceProbes {
 // each thread walks kz planes).
 constexpr int kVariant3D = 0;
 constexpr int kVariantZmarch = 1;
-constexpr int kVariantTma = 2;   // E pass only: TMA-staged z-walk (nx % 16 == 0)
+constexpr int kVariantTma = 2;   // TMA-staged z-walk (nx % 16 == 0)
 constexpr int kVariantVec = 3;   // z-walk over quads of 4 x-cells, 16-byte accesses (nx % 4 == 0)
 struct PassTune {
     int variant;
@@ -75,10 +75,13 @@ struct PassTune {
 // Polls of a bounded mbarrier wait before the kernel gives up (~0.1-1 s).
 constexpr int kWaitLimit = 1 << 20;
 
-// Tensor maps of the TMA E pass: H boxes (BX+4) x (BY+1) (with the -x/-y
-// halo), E and material boxes BX x BY, one plane deep.
-struct TmaMapsE {
-    CUtensorMap hx, hy, hz, ex, ey, ez, mat;
+// Tensor maps of one tile shape (bx, by) for both TMA-staged passes.  E
+// pass: H with its -x/-y halo (boxes (bx+4) x (by+1) from (x0-4, y0-1)), E
+// and the material byte (bx x by).  H pass: E with its +x/+y halo (boxes
+// (bx+4) x (by+1) from (x0, y0)) and H (bx x by).  One plane deep.
+struct TmaMaps {
+    CUtensorMap hx, hy, hz, ex, ey, ez, mat;   // E pass
+    CUtensorMap ebx, eby, ebz, hsx, hsy, hsz;  // H pass
 };
 
 // Shared-memory stage of the TMA E pass (each sub-buffer 128-byte aligned).
@@ -93,11 +96,25 @@ struct TmaLayoutE {
     static constexpr int kTx = 3 * kHW * 4 + 3 * kEW * 4 + kEW;   // bytes per stage
     static constexpr int smem_bytes(int stages) { return stages * kStage + 64 + 128; }
 };
+
+// Shared-memory stage of the TMA H pass: E with the +x/+y halo and H of one
+// plane; the tile's top stage (plane k1) carries E only.
+template <int BX, int BY>
+struct TmaLayoutH {
+    static constexpr int kEW = (BX + 4) * (BY + 1);
+    static constexpr int kHW = BX * BY;
+    static constexpr int kEBytes = (kEW * 4 + 127) / 128 * 128;
+    static constexpr int kHBytes = (kHW * 4 + 127) / 128 * 128;
+    static constexpr int kStage = 3 * kEBytes + 3 * kHBytes;
+    static constexpr int kTxE = 3 * kEW * 4;
+    static constexpr int kTx = kTxE + 3 * kHW * 4;
+    static constexpr int smem_bytes(int stages) { return stages * kStage + 64 + 128; }
+};
 constexpr int kTmaStages = 3;
 
 bool tma_e_supported(const StepArgs& a);
 bool vec_supported(const StepArgs& a);
-bool encode_tma_e(const StepArgs& a, int bx, int by, TmaMapsE* out);
+bool encode_tma(const StepArgs& a, int bx, int by, TmaMaps* out);
 
 // Grid of the H + gain launch: nH H tiles (tile grid gx x gy x gz) and nG
 // gain blocks, each over q consecutive entries of the gain list.
@@ -108,9 +125,10 @@ struct HGLayout {
 };
 
 HGLayout hg_layout(const StepArgs& a, const PassTune& t);
-void launch_h_pass(const StepArgs& a, const PassTune& t, cudaStream_t s);
 // tma: tensor maps for t's tile shape when t.variant == kVariantTma
-void launch_e_pass(const StepArgs& a, const PassTune& t, const TmaMapsE* tma, cudaStream_t s);
+void launch_h_pass(const StepArgs& a, const PassTune& t, const TmaMaps* tma, cudaStream_t s);
+// tma: tensor maps for t's tile shape when t.variant == kVariantTma
+void launch_e_pass(const StepArgs& a, const PassTune& t, const TmaMaps* tma, cudaStream_t s);
 void launch_point_dft(const DevPointProbes& pp, const DevFields& f, const long long* ctr,
                       double dt, cudaStream_t s);
 void launch_face_dft(const DevFaceProbes& fp, const DevFields& f, const DevGrid& g,
@@ -150,7 +168,7 @@ void set_thread_error(const std::string& msg);
 
 // Tensor maps of the context's TMA E pass for tuning t (nullptr if t is not
 // a TMA tuning or the maps cannot be encoded).
-const TmaMapsE* tma_maps(mb_ctx* c, const PassTune& t);
+const TmaMaps* tma_maps(mb_ctx* c, const PassTune& t);
 
 // Enqueue one full step exactly as mb_step runs it, without a graph (the two
 // passes with the context's tuning, then the probes); advances the count.
@@ -237,7 +255,7 @@ struct mb_ctx {
     mb::DevSource src{};
     float* d_src_wave = nullptr;       // tabulated source current
     int* d_err = nullptr;              // device error flag (bounded waits)
-    std::map<std::pair<int, int>, mb::TmaMapsE> tma_maps;   // per TMA tile shape
+    std::map<std::pair<int, int>, mb::TmaMaps> tma_maps;   // per TMA tile shape
     mb::PassTune tune_h{mb::kVariantZmarch, dim3(32, 8, 1), 16};
     mb::PassTune tune_e{mb::kVariantZmarch, dim3(32, 4, 1), 16};
 

@@ -676,7 +676,7 @@ bool vec_supported(const StepArgs& a) { return a.g.nx % 4 == 0; }
 // -z neighbour plane of Hx, Hy stays in registers; J and n of gain cells
 // are loaded one plane ahead, once that plane's material tile has landed.
 template <int BX, int BY, int S>
-__global__ void __launch_bounds__(BX * BY) k_e_tma(StepArgs a, const __grid_constant__ TmaMapsE maps,
+__global__ void __launch_bounds__(BX * BY, 1280 / (BX * BY)) k_e_tma(StepArgs a, const __grid_constant__ TmaMaps maps,
                                                    int kz) {
     using Lay = TmaLayoutE<BX, BY>;
     extern __shared__ unsigned char smem_raw[];
@@ -801,6 +801,106 @@ __global__ void __launch_bounds__(BX * BY) k_e_tma(StepArgs a, const __grid_cons
     finish_step(a);
 }
 
+// ------------------------------------------------------- TMA-staged H pass
+// One thread per (i, j) walks the tile's planes; one thread streams the
+// planes k0 .. k1 of E (with the +x/+y halo) and k0 .. k1-1 of H into an
+// S-slot shared-memory ring with cp.async.bulk.tensor completing on
+// mbarriers.  Plane p needs E of planes p and p+1, so iteration p waits for
+// slot p+1 and frees slot p.  E beyond the grid is the TMA zero fill.  Gain
+// blocks of the same launch run the Lorentz step as in the other variants.
+template <int BX, int BY, int S>
+__global__ void __launch_bounds__(BX * BY) k_hg_tma(StepArgs a, const __grid_constant__ TmaMaps maps,
+                                                    HGLayout lay, int kz) {
+    const long long n = a.step_ctr[0];
+    unsigned idx;
+    if (hg_block_kind(lay, blockIdx.x, idx)) {
+        gain_block(a, idx, lay.q, n);
+        return;
+    }
+    using Lay = TmaLayoutH<BX, BY>;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + S * Lay::kStage);
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + BX * ty;
+    const int bx = idx % lay.gx, by = (idx / lay.gx) % lay.gy, bz = idx / (lay.gx * lay.gy);
+    const int x0 = bx * BX, y0 = by * BY;
+    const int i = x0 + tx, j = y0 + ty;
+    const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
+    const uint32_t nxy = a.g.nxy;
+    const bool valid = i < nx && j < ny;
+    const int k0 = bz * kz, k1 = min(nz, k0 + kz);
+    const int planes = k1 - k0, total = planes + 1;
+    const bool pml_xy = tile_in_xy_slab(a, x0, BX, y0, BY);
+    const DevFields& f = a.f;
+
+    auto issue = [&](int s, int p) {
+        unsigned char* q = smem + s * Lay::kStage;
+        const int k = k0 + p;
+        mbar_arrive_expect_tx(&bar[s], p < planes ? Lay::kTx : Lay::kTxE);
+        tma_load_3d(q + 0 * Lay::kEBytes, &maps.ebx, x0, y0, k, &bar[s]);
+        tma_load_3d(q + 1 * Lay::kEBytes, &maps.eby, x0, y0, k, &bar[s]);
+        tma_load_3d(q + 2 * Lay::kEBytes, &maps.ebz, x0, y0, k, &bar[s]);
+        if (p < planes) {
+            unsigned char* h = q + 3 * Lay::kEBytes;
+            tma_load_3d(h + 0 * Lay::kHBytes, &maps.hsx, x0, y0, k, &bar[s]);
+            tma_load_3d(h + 1 * Lay::kHBytes, &maps.hsy, x0, y0, k, &bar[s]);
+            tma_load_3d(h + 2 * Lay::kHBytes, &maps.hsz, x0, y0, k, &bar[s]);
+        }
+    };
+
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) mbar_init(&bar[s], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (tid == 0)
+        for (int s = 0; s < S && s < total; ++s) issue(s, s);
+
+    uint32_t c = valid ? (uint32_t)i + (uint32_t)nx * j + nxy * k0 : 0u;
+    bool fail = !mbar_wait_bounded(&bar[0], 0, kWaitLimit);
+    const int own = ty * (BX + 4) + tx;
+    for (int p = 0; p < planes; ++p) {
+        const int s = p % S, s1 = (p + 1) % S;
+        const int k = k0 + p;
+        fail |= !mbar_wait_bounded(&bar[s1], ((p + 1) / S) & 1, kWaitLimit);
+        if (valid && !fail) {
+            const float* E0 = reinterpret_cast<const float*>(smem + s * Lay::kStage);
+            const float* E1 = reinterpret_cast<const float*>(smem + s1 * Lay::kStage);
+            const float* Hs = reinterpret_cast<const float*>(smem + s * Lay::kStage + 3 * Lay::kEBytes);
+            constexpr int EW = Lay::kEBytes / 4, HW = Lay::kHBytes / 4;
+            ENb e;
+            e.ex = E0[own];
+            e.ey = E0[EW + own];
+            e.ez = E0[2 * EW + own];
+            e.ex_j1 = E0[own + BX + 4];
+            e.ez_j1 = E0[2 * EW + own + BX + 4];
+            e.ey_i1 = E0[EW + own + 1];
+            e.ez_i1 = E0[2 * EW + own + 1];
+            e.ex_k1 = E1[own];
+            e.ey_k1 = E1[EW + own];
+            float hx = Hs[tid], hy = Hs[HW + tid], hz = Hs[2 * HW + tid];
+            if (pml_xy || plane_in_z_slab(a, k)) h_compute<true>(a, i, j, k, e, hx, hy, hz);
+            else h_compute<false>(a, i, j, k, e, hx, hy, hz);
+            f.hx[c] = hx;
+            f.hy[c] = hy;
+            f.hz[c] = hz;
+        }
+        __syncthreads();   // slot s is free again
+        if (tid == 0 && p + S < total) issue(s, p + S);
+        c += nxy;
+    }
+    if (fail) {
+        // A wait gave up: record it, then give the copies still in flight a
+        // bounded chance to land before the block's shared memory is released.
+        if (tid == 0) atomicOr(a.err, 1);
+        for (int s = 0; s < S && s < total; ++s) {
+            const int uses = (total - s + S - 1) / S;
+            mbar_wait_bounded(&bar[s], (uses - 1) & 1, kWaitLimit);
+        }
+    }
+}
+
 // -------------------------------------------------------------- launchers
 
 HGLayout hg_layout(const StepArgs& a, const PassTune& t) {
@@ -817,12 +917,34 @@ HGLayout hg_layout(const StepArgs& a, const PassTune& t) {
     return L;
 }
 
-void launch_h_pass(const StepArgs& a, const PassTune& t, cudaStream_t s) {
+template <int BX, int BY>
+static void launch_h_tma(const StepArgs& a, const HGLayout& L, int kz, const TmaMaps& maps,
+                         cudaStream_t s) {
+    const int smem = TmaLayoutH<BX, BY>::smem_bytes(kTmaStages);
+    static bool attr_set = false;   // per instantiation, once per process
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_hg_tma<BX, BY, kTmaStages>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem);
+        attr_set = true;
+    }
+    k_hg_tma<BX, BY, kTmaStages><<<(unsigned)(L.nH + L.nG), dim3(BX, BY, 1), smem, s>>>(a, maps, L, kz);
+}
+
+void launch_h_pass(const StepArgs& a, const PassTune& t, const TmaMaps* tma, cudaStream_t s) {
     const HGLayout L = hg_layout(a, t);
     const unsigned blocks = (unsigned)(L.nH + L.nG);
+    if (t.variant == kVariantTma && tma) {
+        const int bx = t.block.x, by = t.block.y;
+        if (bx == 32 && by == 4) return launch_h_tma<32, 4>(a, L, t.kz, *tma, s);
+        if (bx == 32 && by == 8) return launch_h_tma<32, 8>(a, L, t.kz, *tma, s);
+        if (bx == 64 && by == 4) return launch_h_tma<64, 4>(a, L, t.kz, *tma, s);
+        if (bx == 64 && by == 8) return launch_h_tma<64, 8>(a, L, t.kz, *tma, s);
+        if (bx == 128 && by == 2) return launch_h_tma<128, 2>(a, L, t.kz, *tma, s);
+        if (bx == 128 && by == 4) return launch_h_tma<128, 4>(a, L, t.kz, *tma, s);
+    }
     if (t.variant == kVariantVec && vec_supported(a)) {
         k_hg_vec<<<blocks, dim3(t.block.x, t.block.y, 1), 0, s>>>(a, L, t.kz);
-    } else if (t.variant == kVariantZmarch || t.variant == kVariantVec) {
+    } else if (t.variant != kVariant3D) {
         k_hg_zmarch<<<blocks, dim3(t.block.x, t.block.y, 1), 0, s>>>(a, L, t.kz);
     } else {
         k_hg_3d<<<blocks, t.block, 0, s>>>(a, L);
@@ -830,7 +952,7 @@ void launch_h_pass(const StepArgs& a, const PassTune& t, cudaStream_t s) {
 }
 
 template <int BX, int BY>
-static void launch_e_tma(const StepArgs& a, const PassTune& t, const TmaMapsE& maps, cudaStream_t s) {
+static void launch_e_tma(const StepArgs& a, const PassTune& t, const TmaMaps& maps, cudaStream_t s) {
     const int smem = TmaLayoutE<BX, BY>::smem_bytes(kTmaStages);
     static bool attr_set = false;   // per instantiation, once per process
     if (!attr_set) {
@@ -874,11 +996,17 @@ static bool encode_box(CUtensorMap* m, CUtensorMapDataType dt, const void* base,
                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-bool encode_tma_e(const StepArgs& a, int bx, int by, TmaMapsE* out) {
+bool encode_tma(const StepArgs& a, int bx, int by, TmaMaps* out) {
     if (!tma_e_supported(a)) return false;
     const DevFields& f = a.f;
     const CUtensorMapDataType F32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-    bool ok = encode_box(&out->hx, F32, f.hx, 4, a.g, bx + 4, by + 1) &&
+    bool ok = encode_box(&out->ebx, F32, f.ex, 4, a.g, bx + 4, by + 1) &&
+              encode_box(&out->eby, F32, f.ey, 4, a.g, bx + 4, by + 1) &&
+              encode_box(&out->ebz, F32, f.ez, 4, a.g, bx + 4, by + 1) &&
+              encode_box(&out->hsx, F32, f.hx, 4, a.g, bx, by) &&
+              encode_box(&out->hsy, F32, f.hy, 4, a.g, bx, by) &&
+              encode_box(&out->hsz, F32, f.hz, 4, a.g, bx, by) &&
+              encode_box(&out->hx, F32, f.hx, 4, a.g, bx + 4, by + 1) &&
               encode_box(&out->hy, F32, f.hy, 4, a.g, bx + 4, by + 1) &&
               encode_box(&out->hz, F32, f.hz, 4, a.g, bx + 4, by + 1) &&
               encode_box(&out->ex, F32, f.ex, 4, a.g, bx, by) &&
@@ -888,7 +1016,7 @@ bool encode_tma_e(const StepArgs& a, int bx, int by, TmaMapsE* out) {
     return ok;
 }
 
-void launch_e_pass(const StepArgs& a, const PassTune& t, const TmaMapsE* tma, cudaStream_t s) {
+void launch_e_pass(const StepArgs& a, const PassTune& t, const TmaMaps* tma, cudaStream_t s) {
     if (t.variant == kVariantTma && tma) {
         const int bx = t.block.x, by = t.block.y;
         if (bx == 32 && by == 4) return launch_e_tma<32, 4>(a, t, *tma, s);

@@ -215,7 +215,9 @@ def test_launch_variants_are_bitwise_identical(grid):
     tunes = [((0, 32, 4, 2), (0, 32, 4, 2)), ((3, 32, 4, 8), (3, 32, 4, 8)),
              ((3, 64, 2, 16), (3, 32, 8, 4)), ((1, 64, 2, 4), (1, 32, 2, 16))]
     if grid[0] % 16 == 0:
-        tunes += [((1, 32, 4, 8), (2, 32, 4, 8)), ((1, 32, 4, 8), (2, 64, 8, 16))]
+        tunes += [((1, 32, 4, 8), (2, 32, 4, 8)), ((1, 32, 4, 8), (2, 64, 8, 16)),
+                  ((2, 32, 4, 8), (1, 32, 4, 8)), ((2, 64, 8, 16), (2, 32, 8, 4)),
+                  ((2, 128, 2, 3), (0, 32, 4, 2)), ((2, 32, 8, 64), (2, 128, 4, 5))]
     results = {}
     for tune in [ref_tune] + tunes:
         g.load_state(blob)
@@ -334,6 +336,12 @@ def test_argument_errors():
     assert e.value.code == MB_ERR_MATERIALS
     with pytest.raises(MBError):
         g.set_field("N0", np.zeros(grid[::-1], np.float32))
+    for bad in (((2, 32, 4, 8), (1, 32, 4, 8)),       # TMA passes need n_x % 16 == 0
+                ((1, 48, 4, 8), (1, 32, 4, 8)),       # x not a multiple of 32
+                ((2, 32, 16, 8), (1, 32, 4, 8))):     # no such TMA tile (and n_x = 8)
+        with pytest.raises(MBError) as e:
+            g.set_tuning(*bad)
+        assert e.value.code == MB_ERR_ARG
     g.close()
 
 
