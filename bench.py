@@ -38,7 +38,7 @@ UNIT = "Mcell-updates/s"
 FALLBACK_HBM_GBS = 6800.0
 PROFILE_DIR = os.path.join(ROOT, "profiles")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_0809_1547_gb300", "csrc", f)
-                  for f in ("mb_device.cuh", "mb_passes.cu", "mb_tma.cuh")]
+                  for f in ("mb_device.cuh", "mb_tiles.cuh", "mb_passes.cu", "mb_tma.cuh")]
 
 
 # ------------------------------------------------------------------ helpers

@@ -13,93 +13,12 @@
 // registers.  Every variant composes the same per-cell helpers, so all of
 // them produce the same bits.
 #include "mb_host.h"
+#include "mb_tiles.cuh"
 #include "mb_tma.cuh"
 
 #include <cudaTypedefs.h>
 
 namespace mb {
-
-// Block b of the H + gain grid is a gain block (returns true, idx = its
-// index) or an H block (returns false, idx = its index).  Gain blocks are
-// spread evenly through the grid so both kinds advance through the domain
-// together and the gain blocks' E^n reads find the H blocks' lines in L2.
-__device__ __forceinline__ bool hg_block_kind(const HGLayout& L, unsigned b, unsigned& idx) {
-    const unsigned long long tot = (unsigned long long)L.nH + L.nG;
-    const unsigned g0 = (unsigned)((unsigned long long)b * L.nG / tot);
-    const unsigned g1 = (unsigned)((unsigned long long)(b + 1) * L.nG / tot);
-    if (g1 > g0) {
-        idx = g0;
-        return true;
-    }
-    idx = b - g0;
-    return false;
-}
-
-__device__ __forceinline__ int linear_tid() {
-    return threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
-}
-
-// A gain block advances q = PER * threads consecutive entries of the gain
-// list; each thread loads all its PER cells before computing any, so that
-// several cells' loads are in flight at once.
-template <int PER = kGainPerThread>
-__device__ __forceinline__ void gain_block(const StepArgs& a, unsigned gidx, int q, long long n) {
-    const int T = blockDim.x * blockDim.y * blockDim.z;
-    const uint32_t base = gidx * (uint32_t)q + (uint32_t)linear_tid();
-    const DevFields& f = a.f;
-    uint32_t cs[PER];
-    bool ok[PER];
-#pragma unroll
-    for (int r = 0; r < PER; ++r) {
-        const uint32_t e = base + (uint32_t)(r * T);
-        ok[r] = e < a.glist.count;
-        cs[r] = ok[r] ? __ldg(a.glist.cell + e) : 0u;
-    }
-    float ex[PER], ey[PER], ez[PER], n1[PER],
-        n2[PER], px[PER], py[PER], pz[PER],
-        jx[PER], jy[PER], jz[PER];
-#pragma unroll
-    for (int r = 0; r < PER; ++r) {
-        if (!ok[r]) continue;
-        const uint32_t c = cs[r];
-        ex[r] = __ldg(f.ex + c);
-        ey[r] = __ldg(f.ey + c);
-        ez[r] = __ldg(f.ez + c);
-        n1[r] = f.n1[c];
-        n2[r] = f.n2[c];
-        px[r] = f.px[c];
-        py[r] = f.py[c];
-        pz[r] = f.pz[c];
-        jx[r] = f.jx[c];
-        jy[r] = f.jy[c];
-        jz[r] = f.jz[c];
-    }
-#pragma unroll
-    for (int r = 0; r < PER; ++r) {
-        if (!ok[r]) continue;
-        const uint32_t c = cs[r];
-        lorentz_step(a.gain, c, n, ex[r], ey[r], ez[r], n1[r], n2[r], jx[r], jy[r], jz[r], px[r],
-                     py[r], pz[r]);
-        f.jx[c] = jx[r];
-        f.jy[c] = jy[r];
-        f.jz[c] = jz[r];
-        f.px[c] = px[r];
-        f.py[c] = py[r];
-        f.pz[c] = pz[r];
-    }
-}
-
-// Does the tile [i0, i0+bx) x [j0, j0+by) touch an x or y CPML slab?
-__device__ __forceinline__ bool tile_in_xy_slab(const StepArgs& a, int i0, int bx, int j0, int by) {
-    const int L = a.pml.L;
-    return L > 0 && (i0 < L || i0 + bx > a.g.nx - L || j0 < L || j0 + by > a.g.ny - L);
-}
-
-__device__ __forceinline__ bool plane_in_z_slab(const StepArgs& a, int k) {
-    const int L = a.pml.L;
-    return L > 0 && (k < L || k >= a.g.nz - L);
-}
-
 // ------------------------------------------------------ H + gain launches
 
 __global__ void __launch_bounds__(512) k_hg_3d(StepArgs a, HGLayout lay) {
@@ -123,70 +42,6 @@ __global__ void __launch_bounds__(512) k_hg_3d(StepArgs a, HGLayout lay) {
     else h_core<false>(a, i, j, k, c, e);
 }
 
-// H walk of tile (bx, by, bz): a 2-D block over (x, y), kz planes per thread.
-__device__ __forceinline__ void h_tile_zmarch(const StepArgs& a, int bx, int by, int bz, int kz) {
-    const int i = bx * blockDim.x + threadIdx.x;
-    const int j = by * blockDim.y + threadIdx.y;
-    const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
-    if (i >= nx || j >= ny) return;
-    const int k0 = bz * kz;
-    const int k1 = min(nz, k0 + kz);
-    const uint32_t nxy = a.g.nxy;
-    const float* __restrict__ Ex = a.f.ex;
-    const float* __restrict__ Ey = a.f.ey;
-    const float* __restrict__ Ez = a.f.ez;
-    const bool xi = i + 1 < nx, yj = j + 1 < ny;
-    const bool pml_xy = tile_in_xy_slab(a, bx * blockDim.x, blockDim.x, by * blockDim.y, blockDim.y);
-    uint32_t c = (uint32_t)i + (uint32_t)nx * j + nxy * k0;
-    float ex_c = __ldg(Ex + c), ey_c = __ldg(Ey + c);
-    int k = k0;
-    // two planes per iteration: all loads of both are issued before either update
-    for (; k + 1 < k1; k += 2, c += 2 * nxy) {
-        ENb e0, e1;
-        const bool zk = k + 2 < nz;
-        e0.ex = ex_c;
-        e0.ey = ey_c;
-        e0.ez = __ldg(Ez + c);
-        e0.ex_k1 = __ldg(Ex + c + nxy);
-        e0.ey_k1 = __ldg(Ey + c + nxy);
-        e0.ex_j1 = yj ? __ldg(Ex + c + nx) : 0.0f;
-        e0.ey_i1 = xi ? __ldg(Ey + c + 1) : 0.0f;
-        e0.ez_i1 = xi ? __ldg(Ez + c + 1) : 0.0f;
-        e0.ez_j1 = yj ? __ldg(Ez + c + nx) : 0.0f;
-        const uint32_t c1 = c + nxy;
-        e1.ex = e0.ex_k1;
-        e1.ey = e0.ey_k1;
-        e1.ez = __ldg(Ez + c1);
-        e1.ex_k1 = zk ? __ldg(Ex + c1 + nxy) : 0.0f;
-        e1.ey_k1 = zk ? __ldg(Ey + c1 + nxy) : 0.0f;
-        e1.ex_j1 = yj ? __ldg(Ex + c1 + nx) : 0.0f;
-        e1.ey_i1 = xi ? __ldg(Ey + c1 + 1) : 0.0f;
-        e1.ez_i1 = xi ? __ldg(Ez + c1 + 1) : 0.0f;
-        e1.ez_j1 = yj ? __ldg(Ez + c1 + nx) : 0.0f;
-        if (pml_xy || plane_in_z_slab(a, k)) h_core<true>(a, i, j, k, c, e0);
-        else h_core<false>(a, i, j, k, c, e0);
-        if (pml_xy || plane_in_z_slab(a, k + 1)) h_core<true>(a, i, j, k + 1, c1, e1);
-        else h_core<false>(a, i, j, k + 1, c1, e1);
-        ex_c = e1.ex_k1;
-        ey_c = e1.ey_k1;
-    }
-    if (k < k1) {
-        ENb e;
-        const bool zk = k + 1 < nz;
-        e.ex = ex_c;
-        e.ey = ey_c;
-        e.ez = __ldg(Ez + c);
-        e.ex_k1 = zk ? __ldg(Ex + c + nxy) : 0.0f;
-        e.ey_k1 = zk ? __ldg(Ey + c + nxy) : 0.0f;
-        e.ex_j1 = yj ? __ldg(Ex + c + nx) : 0.0f;
-        e.ey_i1 = xi ? __ldg(Ey + c + 1) : 0.0f;
-        e.ez_i1 = xi ? __ldg(Ez + c + 1) : 0.0f;
-        e.ez_j1 = yj ? __ldg(Ez + c + nx) : 0.0f;
-        if (pml_xy || plane_in_z_slab(a, k)) h_core<true>(a, i, j, k, c, e);
-        else h_core<false>(a, i, j, k, c, e);
-    }
-}
-
 __global__ void __launch_bounds__(512) k_hg_zmarch(StepArgs a, HGLayout lay, int kz) {
     const long long n = a.step_ctr[0];
     unsigned idx;
@@ -198,35 +53,6 @@ __global__ void __launch_bounds__(512) k_hg_zmarch(StepArgs a, HGLayout lay, int
 }
 
 // ------------------------------------------------------------ E launches
-
-// Blocks whose cell range contains a face plane reduce the flux (uniform).
-__device__ __forceinline__ bool tile_on_face(const DevFlux& F, int i0, int i1, int j0, int j1,
-                                             int k0, int k1) {
-    if (!F.on) return false;
-    return (F.plo[0] >= i0 && F.plo[0] < i1) || (F.phi[0] >= i0 && F.phi[0] < i1) ||
-           (F.plo[1] >= j0 && F.plo[1] < j1) || (F.phi[1] >= j0 && F.phi[1] < j1) ||
-           (F.plo[2] >= k0 && F.plo[2] < k1) || (F.phi[2] >= k0 && F.phi[2] < k1);
-}
-
-__device__ __forceinline__ unsigned warp_slot() {
-    const unsigned b = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-    return b * 7u + (unsigned)(linear_tid() >> 5);
-}
-
-// The last block of the E launch to finish advances the step counter.  No
-// block waits for another: each one only counts itself out.
-__device__ __forceinline__ void finish_step(const StepArgs& a) {
-    __syncthreads();
-    if (linear_tid() == 0) {
-        __threadfence();
-        const unsigned long long nb = (unsigned long long)gridDim.x * gridDim.y * gridDim.z;
-        const unsigned long long t = atomicAdd((unsigned long long*)(a.step_ctr + 1), 1ULL);
-        if (t == nb - 1) {
-            atomicExch((unsigned long long*)(a.step_ctr + 1), 0ULL);
-            atomicAdd((unsigned long long*)a.step_ctr, 1ULL);
-        }
-    }
-}
 
 __global__ void __launch_bounds__(512, 2) k_e_3d(StepArgs a) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -250,226 +76,10 @@ __global__ void __launch_bounds__(512, 2) k_e_3d(StepArgs a) {
     finish_step(a);
 }
 
-// Walk of one column (i, j) over planes [k0, k1).  FACE: the block holds
-// face-plane cells (flux terms summed into fl over the walk); PML_XY: the
-// tile touches an x or y CPML slab (else only z-slab planes take the CPML
-// code).
-template <bool FACE, bool PML_XY>
-__device__ __forceinline__ void e_walk(const StepArgs& a, int i, int j, int k0, int k1, long long n,
-                                       float fl[6]) {
-    const int nx = a.g.nx;
-    const uint32_t nxy = a.g.nxy;
-    const float* __restrict__ Hx = a.f.hx;
-    const float* __restrict__ Hy = a.f.hy;
-    const float* __restrict__ Hz = a.f.hz;
-    uint32_t c = (uint32_t)i + (uint32_t)nx * j + nxy * k0;
-    float hx_km1 = 0.0f, hy_km1 = 0.0f;
-    if (k0 > 0) {
-        hx_km1 = __ldg(Hx + c - nxy);
-        hy_km1 = __ldg(Hy + c - nxy);
-    }
-    for (int k = k0; k < k1; ++k, c += nxy) {
-        HNb h;
-        h.hx = __ldg(Hx + c);
-        h.hy = __ldg(Hy + c);
-        h.hz = __ldg(Hz + c);
-        h.hx_k = hx_km1;
-        h.hy_k = hy_km1;
-        h.hx_j = (j > 0) ? __ldg(Hx + c - nx) : 0.0f;
-        h.hz_j = (j > 0) ? __ldg(Hz + c - nx) : 0.0f;
-        h.hy_i = (i > 0) ? __ldg(Hy + c - 1) : 0.0f;
-        h.hz_i = (i > 0) ? __ldg(Hz + c - 1) : 0.0f;
-        if (FACE || PML_XY) e_core<FACE, true>(a, i, j, k, c, h, n, fl);
-        else if (plane_in_z_slab(a, k)) e_core<false, true>(a, i, j, k, c, h, n, fl);
-        else e_core<false, false>(a, i, j, k, c, h, n, fl);
-        hx_km1 = h.hx;
-        hy_km1 = h.hy;
-    }
-}
-
-// E walk of tile (bx, by, bz) for step n (flux of face tiles included).
-// Every thread of the block must call it (warp-wide flux reduction).
-__device__ __forceinline__ void e_tile_zmarch(const StepArgs& a, int bx, int by, int bz, int kz,
-                                              long long n, unsigned slot) {
-    const int i = bx * blockDim.x + threadIdx.x;
-    const int j = by * blockDim.y + threadIdx.y;
-    const int nz = a.g.nz;
-    const bool valid = i < a.g.nx && j < a.g.ny;
-    const int k0 = bz * kz;
-    const int k1 = min(nz, k0 + kz);
-    const int i0 = bx * blockDim.x, j0 = by * blockDim.y;
-    const bool face = tile_on_face(a.flux, i0, i0 + blockDim.x, j0, j0 + blockDim.y, k0, k1);
-    const bool pml_xy = tile_in_xy_slab(a, i0, blockDim.x, j0, blockDim.y);
-    if (face) {
-        float fl[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        if (valid) e_walk<true, true>(a, i, j, k0, k1, n, fl);
-        flux_warp_reduce(a.flux, fl, slot);
-    } else if (valid) {
-        float* none = nullptr;
-        if (pml_xy) e_walk<false, true>(a, i, j, k0, k1, n, none);
-        else e_walk<false, false>(a, i, j, k0, k1, n, none);
-    }
-}
-
 __global__ void __launch_bounds__(512, 2) k_e_zmarch(StepArgs a, int kz) {
     const long long n = a.step_ctr[0];
     e_tile_zmarch(a, blockIdx.x, blockIdx.y, blockIdx.z, kz, n, warp_slot());
     finish_step(a);
-}
-
-// ---------------------------------------------------- batched ensemble
-// Grid-wide barrier of a co-resident (cooperative) grid, with a bounded
-// wait: false when the other blocks did not all arrive within the limit.
-__device__ bool grid_barrier(unsigned* bar, unsigned nblocks) {
-    __shared__ int ok_s;
-    __syncthreads();
-    if (linear_tid() == 0) {
-        volatile unsigned* gen = bar + 1;
-        const unsigned g = *gen;
-        __threadfence();
-        int ok = 1;
-        if (atomicAdd(bar, 1u) == nblocks - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
-            for (int it = 0; *gen == g; ++it) {
-                if (it > kBarrierSpinLimit) {
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(64);
-            }
-        }
-        __threadfence();
-        ok_s = ok;
-    }
-    __syncthreads();
-    return ok_s != 0;
-}
-
-// Arguments of the item's instance, copied into shared memory: global
-// stores cannot alias them there, so the field pointers need not stay in
-// registers or be reloaded after every store.
-template <int TAG>
-__device__ __forceinline__ const StepArgs& stage_args(const StepArgs* src) {
-    static_assert(sizeof(StepArgs) % 8 == 0, "StepArgs is copied in 8-byte words");
-    __shared__ StepArgs sa;
-    const unsigned long long* s8 = reinterpret_cast<const unsigned long long*>(src);
-    unsigned long long* d8 = reinterpret_cast<unsigned long long*>(&sa);
-    const int T = blockDim.x * blockDim.y * blockDim.z;
-    for (int t = linear_tid(); t < (int)(sizeof(StepArgs) / 8); t += T) d8[t] = s8[t];
-    __syncthreads();
-    return sa;
-}
-
-// Work items of the persistent kernel, each its own (not inlined) function
-// so that the register allocation of one phase does not burden the others.
-// The caller has synchronised the block since the previous item.
-__device__ __noinline__ void batch_probe_item(const BatchArgs& B, int p, long long n) {
-    const StepArgs& a = B.inst[p];
-    for (int q = 0; q < B.probes[p].count; ++q)
-        point_dft_block(B.probes[p], q, a.f.ex, a.f.ey, a.f.ez, n, B.dt);
-}
-
-__device__ __noinline__ void batch_h_item(const BatchArgs& B, int4 it) {
-    const StepArgs& a = stage_args<0>(B.inst + it.x);
-    const int gx = B.tiles[2 * it.x], gy = B.tiles[2 * it.x + 1];
-    h_tile_zmarch(a, it.z % gx, (it.z / gx) % gy, it.z / (gx * gy), B.kz);
-}
-
-__device__ __noinline__ void batch_gain_item(const BatchArgs& B, int4 it, long long n) {
-    gain_block<kBatchGainPerThread>(stage_args<1>(B.inst + it.x), (unsigned)it.z, B.gq, n);
-}
-
-__device__ __noinline__ void batch_e_item(const BatchArgs& B, int4 it, long long n, unsigned slot) {
-    const StepArgs& a = stage_args<2>(B.inst + it.x);
-    const int gx = B.tiles[2 * it.x], gy = B.tiles[2 * it.x + 1];
-    e_tile_zmarch(a, it.z % gx, (it.z / gx) % gy, it.z / (gx * gy), B.kz, n, slot);
-}
-
-// Next work item of this block in the current phase: tickets are drawn from
-// one counter; tickets [base, base + n) are the phase's items, and every
-// block draws exactly one ticket past them before it leaves the phase, so the
-// next phase starts at base + n + gridDim.x.  Returns -1 when the phase is
-// exhausted.
-__device__ __forceinline__ int next_item(unsigned long long* tick, unsigned long long base, int n) {
-    __shared__ int item_s;
-    __syncthreads();   // the previous item is finished by every thread
-    if (linear_tid() == 0) {
-        const unsigned long long t = atomicAdd(tick, 1ull) - base;
-        item_s = t < (unsigned long long)n ? (int)t : -1;
-    }
-    __syncthreads();
-    return item_s;
-}
-
-// n steps of every instance in one launch.  Per step: phase 1 = the point
-// probes of the previous step (they read E only) + all instances' H tiles
-// and gain chunks; barrier; phase 2 = all E tiles; barrier.  Blocks draw
-// items from a shared counter (largest items first in the lists), so grids
-// of uneven size and cost balance.  A barrier that times out sets the error
-// flag and the block leaves; the other blocks then time out at their next
-// barrier, so the launch always ends.
-__global__ void __launch_bounds__(256, 4) k_batch(const __grid_constant__ BatchArgs B) {
-    const unsigned nb = gridDim.x;
-    const long long n0 = B.ctr[0];
-    unsigned long long base = 0;
-    for (int s = 0; s < B.nsteps; ++s) {
-        const long long n = n0 + s;
-        if (s > 0)
-            for (int p = blockIdx.x; p < B.ninst; p += nb) batch_probe_item(B, p, n);
-        for (int w; (w = next_item(B.tick, base, B.n1)) >= 0;) {
-            const int4 it = B.items1[w];
-            if (it.y == 0) batch_h_item(B, it);
-            else batch_gain_item(B, it, n);
-        }
-        base += (unsigned long long)B.n1 + nb;
-        if (!grid_barrier(B.bar, nb)) {
-            if (linear_tid() == 0) atomicOr(B.err, 1);
-            return;
-        }
-        for (int w; (w = next_item(B.tick, base, B.n2)) >= 0;)
-            batch_e_item(B, B.items2[w], n, (unsigned)w * 7u + (linear_tid() >> 5));
-        base += (unsigned long long)B.n2 + nb;
-        if (!grid_barrier(B.bar, nb)) {
-            if (linear_tid() == 0) atomicOr(B.err, 1);
-            return;
-        }
-    }
-    const long long n_end = n0 + B.nsteps;
-    for (int p = blockIdx.x; p < B.ninst; p += nb) batch_probe_item(B, p, n_end);
-    if (blockIdx.x == 0) {
-        // every block read n0 before the first barrier and drew its last
-        // ticket before the last one; nsteps >= 1
-        for (int p = linear_tid(); p < B.ninst; p += blockDim.x * blockDim.y) B.inst[p].step_ctr[0] = n_end;
-        if (linear_tid() == 0) {
-            B.ctr[0] = n_end;
-            *B.tick = 0ull;
-        }
-    }
-}
-
-int batch_blocks_per_sm(dim3 block) {
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch, block.x * block.y * block.z, 0) !=
-        cudaSuccess)
-        return 0;
-    return n;
-}
-
-cudaError_t launch_batch(const BatchArgs& b, dim3 block, int blocks, cudaStream_t s) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(blocks, 1, 1);
-    cfg.blockDim = block;
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;   // all blocks co-resident: the barrier is safe
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_batch, b);
 }
 
 // ----------------------------------------------- quad-vectorised z-walks
