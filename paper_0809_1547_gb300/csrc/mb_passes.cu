@@ -286,7 +286,7 @@ bool vec_supported(const StepArgs& a) { return a.g.nx % 4 == 0; }
 // -z neighbour plane of Hx, Hy stays in registers; J and n of gain cells
 // are loaded one plane ahead, once that plane's material tile has landed.
 template <int BX, int BY, int S>
-__global__ void __launch_bounds__(BX * BY, 1280 / (BX * BY)) k_e_tma(StepArgs a, const __grid_constant__ TmaMaps maps,
+__global__ void __launch_bounds__(BX * BY) k_e_tma(StepArgs a, const __grid_constant__ TmaMaps maps,
                                                    int kz) {
     using Lay = TmaLayoutE<BX, BY>;
     extern __shared__ unsigned char smem_raw[];
