@@ -106,31 +106,17 @@ int rebuild(mb_batch* b) {
         tiles.push_back(gy);
         const long long nH = (long long)gx * gy * gz;
         const long long nG = (c->args.gain.on && c->glist_count) ? (c->glist_count + gq - 1) / gq : 0;
-        const double gfrac = c->ncell ? (double)c->glist_count / (double)c->ncell : 0.0;
-        const int L = c->p.npml;
-        for (long long t = 0; t < nH; ++t) {
-            // estimated bytes of the tile: cells x (bytes per cell, with 16 B
-            // per CPML slab axis the tile touches)
-            const int bx = (int)(t % gx), by = (int)((t / gx) % gy), bz = (int)(t / ((long long)gx * gy));
-            const int i0 = bx * (int)b->block.x, j0 = by * (int)b->block.y, k0 = bz * b->kz;
-            const int cx = std::min((int)b->block.x, c->nx - i0), cy = std::min((int)b->block.y, c->ny - j0),
-                      cz = std::min(b->kz, c->nz - k0);
-            const int axes = (L > 0 && (i0 < L || i0 + (int)b->block.x > c->nx - L)) +
-                             (L > 0 && (j0 < L || j0 + (int)b->block.y > c->ny - L)) +
-                             (L > 0 && (k0 < L || k0 + b->kz > c->nz - L));
-            const double cells = (double)cx * cy * cz;
-            items1.push_back(make_int4(q, 0, (int)t, (int)(cells * (36 + 16 * axes))));
-            items2.push_back(make_int4(q, 2, (int)t, (int)(cells * (37 + 16 * axes + 36 * gfrac))));
+        // H tiles and gain chunks interleaved by progress through the
+        // instance (a gain chunk re-reads E^n where the H tiles next to it in
+        // the list read it, so the line is still in L2); E tiles in tile order
+        // (neighbouring tiles share halo lines).
+        for (long long t = 0; t < nH + nG; ++t) {
+            const long long g0 = t * nG / (nH + nG), g1 = (t + 1) * nG / (nH + nG);
+            if (g1 > g0) items1.push_back(make_int4(q, 1, (int)g0, 0));
+            else items1.push_back(make_int4(q, 0, (int)(t - g0), 0));
         }
-        for (long long t = 0; t < nG; ++t) {
-            const long long cells = std::min<long long>(gq, (long long)c->glist_count - t * gq);
-            items1.push_back(make_int4(q, 1, (int)t, (int)(cells * 56)));
-        }
+        for (long long t = 0; t < nH; ++t) items2.push_back(make_int4(q, 2, (int)t, 0));
     }
-    // largest items first: the phase ends with small ones, so blocks finish together
-    auto by_cost = [](const int4& u, const int4& v) { return u.w > v.w; };
-    std::stable_sort(items1.begin(), items1.end(), by_cost);
-    std::stable_sort(items2.begin(), items2.end(), by_cost);
     MB_BCUDA(b, cudaMalloc((void**)&b->d_inst, sizeof(mb::StepArgs) * B));
     MB_BCUDA(b, cudaMalloc((void**)&b->d_probes, sizeof(mb::DevPointProbes) * B));
     MB_BCUDA(b, cudaMalloc((void**)&b->d_tiles, sizeof(int) * tiles.size()));

@@ -96,8 +96,8 @@ __device__ __forceinline__ int next_item(unsigned long long* tick, unsigned long
 // n steps of every instance in one launch.  Per step: phase 1 = the point
 // probes of the previous step (they read E only) + all instances' H tiles
 // and gain chunks; barrier; phase 2 = all E tiles; barrier.  Blocks draw
-// items from a shared counter (largest items first in the lists), so grids
-// of uneven size and cost balance.  A barrier that times out sets the error
+// items from a shared counter in list order (which keeps neighbouring tiles
+// together for L2 reuse), so grids of uneven size and cost balance.  A barrier that times out sets the error
 // flag and the block leaves; the other blocks then time out at their next
 // barrier, so the launch always ends.
 __global__ void __launch_bounds__(256, 4) k_batch(const __grid_constant__ BatchArgs B) {

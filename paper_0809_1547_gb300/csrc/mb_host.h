@@ -135,7 +135,7 @@ void launch_face_dft(const DevFaceProbes& fp, const DevFields& f, const DevGrid&
                      const long long* ctr, double dt, cudaStream_t s);
 // Batched ensemble: instances advanced together by one persistent launch.
 // Work items (int4): x = instance, y = kind (0 H tile, 1 gain chunk, 2 E
-// tile), z = tile / chunk index, w = estimated cost (bytes).
+// tile), z = tile / chunk index.
 struct BatchArgs {
     const StepArgs* inst;          // [ninst], device
     const DevPointProbes* probes;  // [ninst], device (count 0: no probe)
