@@ -30,9 +30,13 @@ One step n -> n+1, in this order (every array is FP64, indexed [k, j, i]):
   4. E^{n+1}   = E^n + dt/(eps0 eps_r) (curl_bwd H^{n+1/2} + CPML psi_E - J^{n+1/2} - J_src)
   5. N^{n+1}   = M N^n + m s,  s = (1/hbar w0) 1/2 (E^n + E^{n+1}) . J^{n+1/2}
      with M = (I - dt A/2)^-1 (I + dt A/2), m = dt (I - dt A/2)^-1 e (Crank–Nicolson)
-  6. probes: running DFT of E^{n+1} at t_{n+1}; outward Poynting flux of the
-     interior box, with (E^n + E^{n+1})/2 on each face plane and H^{n+1/2} on
-     the adjacent half-plane (the pairing of the Yee curls across the plane).
+  6. probes: running DFT of E^{n+1} at t_{n+1} (points, face sub-grids and
+     whole z-planes); outward Poynting flux of the interior box, with
+     (E^n + E^{n+1})/2 on each face plane and H^{n+1/2} on the adjacent
+     half-plane (the pairing of the Yee curls across the plane).
+Read-outs also include the energy density of a z-plane (a snapshot of the
+sample's middle section, Fig. 2a) and the mode map of a plane probe (the
+field of a mode under CW excitation, inset of Fig. 1).
 
 Yee ownership: cell (i,j,k) owns Ex(i+1/2,j,k), Ey(i,j+1/2,k), Ez(i,j,k+1/2),
 Hx(i,j+1/2,k+1/2), Hy(i+1/2,j,k+1/2), Hz(i+1/2,j+1/2,k); P and J sit on the E
@@ -52,7 +56,10 @@ state / matrix-exponential limits of the rate equations; the closed-form
 transfer function of the Lorentz recursion; the stationary variance of the
 noise-driven recursion; CPML reflection against a larger box; the running DFT
 against its geometric-sum closed form; the face flux against the exact
-discrete energy balance of the interior box.
+discrete energy balance of the interior box; the plane snapshot against the
+total energy, the plane DFT against point probes, the CW waveform's closed
+form, a CW-driven box's mode map at the drive frequency and its quadratic
+scaling (tests/test_oracle_modemap.py).
 Parity unpinned: the composition of all of these in a long noisy run has no
 closed form; it is pinned only through its parts.
 """
@@ -265,6 +272,15 @@ def source_waveform(t, lam, t0, tau, amp):
     return amp * math.sin(ws * (t - t0)) * math.exp(-((t - t0) / tau) ** 2)
 
 
+def source_waveform_cw(t, lam, t0, tau, amp):
+    """Continuous-wave soft current switched on at t0 with a smooth rise:
+    amp sin(w_s (t - t0)) (1 - exp(-((t - t0)/tau)^2)) for t >= t0, else 0."""
+    if t < t0:
+        return 0.0
+    ws = 2.0 * math.pi * C0 / lam
+    return amp * math.sin(ws * (t - t0)) * (1.0 - math.exp(-((t - t0) / tau) ** 2))
+
+
 def lambda_grid(n_freq: int, lam_min: float, lam_max: float) -> np.ndarray:
     """Probe wavelengths: n_freq points uniformly spaced from lam_min to lam_max."""
     if n_freq == 1:
@@ -320,6 +336,7 @@ class MBOracle:
         self.point_probes = []   # dicts: ijk, omegas, lams, acc (3, K) complex
         self.sources = []        # dicts: ijk, comp, lam, t0, tau, amp
         self.face_probes = None  # dict: stride, every, omegas, lams, faces
+        self.plane_probes = []   # dicts: k, every, omegas, lams, acc (K, 3, ny, nx) complex
         self.flux = np.zeros(6)  # outward energy through x-,x+,y-,y+,z-,z+ faces
 
     # ------------------------------------------------------------- set-up
@@ -348,7 +365,23 @@ class MBOracle:
 
     def add_source(self, ijk, comp, lam, t0, tau, amp):
         self.sources.append({"ijk": tuple(int(v) for v in ijk), "comp": int(comp),
-                             "lam": lam, "t0": t0, "tau": tau, "amp": amp})
+                             "lam": lam, "t0": t0, "tau": tau, "amp": amp, "kind": "pulse"})
+
+    def add_source_cw(self, ijk, comp, lam, t0, tau, amp, n_steps):
+        """CW soft current (source_waveform_cw) for the n_steps steps from the
+        first one whose half-step time t_{n+1/2} is >= t0; zero afterwards."""
+        n0 = max(0, math.ceil(t0 / self.dt - 0.5))
+        self.sources.append({"ijk": tuple(int(v) for v in ijk), "comp": int(comp),
+                             "lam": lam, "t0": t0, "tau": tau, "amp": amp, "kind": "cw",
+                             "n0": n0, "n1": n0 + int(n_steps)})
+
+    def add_plane_probe(self, k, every, n_freq, lam_min, lam_max) -> int:
+        """Running DFT of E on the whole plane z = k (every `every` steps)."""
+        lams = lambda_grid(n_freq, lam_min, lam_max)
+        self.plane_probes.append({"k": int(k), "every": int(every), "lams": lams,
+                                  "omegas": 2.0 * math.pi * C0 / lams,
+                                  "acc": np.zeros((n_freq, 3, self.ny, self.nx), dtype=np.complex128)})
+        return len(self.plane_probes) - 1
 
     def add_face_probes(self, stride, every, n_freq, lam_min, lam_max):
         lams = lambda_grid(n_freq, lam_min, lam_max)
@@ -404,7 +437,12 @@ class MBOracle:
         t_half = (self.n + 0.5) * dt
         for s in self.sources:
             i, j, k = s["ijk"]
-            Jtot[s["comp"]][k, j, i] += source_waveform(t_half, s["lam"], s["t0"], s["tau"], s["amp"])
+            if s["kind"] == "cw":
+                if s["n0"] <= self.n < s["n1"]:
+                    Jtot[s["comp"]][k, j, i] += source_waveform_cw(t_half, s["lam"], s["t0"], s["tau"],
+                                                                   s["amp"])
+            else:
+                Jtot[s["comp"]][k, j, i] += source_waveform(t_half, s["lam"], s["t0"], s["tau"], s["amp"])
 
         # 4. E^{n+1} = E^n + dt/(eps0 eps_r) (curl H^{n+1/2} - J) (backward differences) + CPML.
         dHz_dy = d_bwd(Hz, AX_Y) / dx
@@ -447,6 +485,11 @@ class MBOracle:
             i, j, k = pr["ijk"]
             for c in range(3):
                 pr["acc"][c] = dft_accumulate(pr["acc"][c], self.E[c][k, j, i], pr["omegas"], t, self.dt)
+        for pp in self.plane_probes:
+            if self.n % pp["every"] == 0:
+                ph = np.exp(1j * pp["omegas"] * t) * (pp["every"] * self.dt)       # E^{n+1} at t_{n+1}
+                for c in range(3):
+                    pp["acc"][:, c] += self.E[c][pp["k"]][None, :, :] * ph[:, None, None]
         E_mid = [0.5 * (a + b) for a, b in zip(E_old, self.E)]
         self.flux += self.dt * np.array(self.face_fluxes(E_mid))
         fp = self.face_probes
@@ -533,6 +576,18 @@ class MBOracle:
         S = np.real(Ea * np.conj(Hb) - Eb * np.conj(Ha))
         S = S.reshape(-1, K).sum(axis=0) * (fp["stride"] * self.dx) ** 2
         return (S if face % 2 == 1 else -S), fp["lams"].copy()
+
+    def plane_mode_map(self, probe_id: int, bin_: int) -> np.ndarray:
+        """Sum over components of |DFT of E|^2 on the probe's plane, (ny, nx)."""
+        acc = self.plane_probes[probe_id]["acc"][bin_]
+        return np.sum(np.abs(acc) ** 2, axis=0)
+
+    def plane_energy_density(self, k: int) -> np.ndarray:
+        """Energy density (J/m^3) of the cells of plane z = k with the stored
+        fields: 1/2 (eps0 eps_r |E|^2 + mu0 |H|^2), the per-cell terms of energy()."""
+        uE = sum(F[k] * F[k] for F in self.E) * EPS0 * self.eps_r[k]
+        uH = sum(F[k] * F[k] for F in self.H) * MU0
+        return 0.5 * (uE + uH)
 
     def energy(self) -> float:
         """U = 1/2 sum (eps0 eps_r |E|^2 + mu0 |H|^2) dx^3 with the stored fields."""
