@@ -139,13 +139,44 @@ int mb_add_face_probes(mb_ctx* ctx, int stride, int every, int n_freq,
 int mb_set_source(mb_ctx* ctx, const int ijk[3], int comp, double lam,
                   double t0, double tau, double amp);
 
+/* Continuous-wave soft current (the excitation that shows the field of a
+ * long-living mode, inset of the paper's Fig. 1 at 586.5 nm):
+ * J_comp(t) = amp sin(w_s (t - t0)) (1 - exp(-((t - t0)/tau)^2)) for t >= t0
+ * (A/m^2, w_s = 2 pi c / lam; tau is the rise time), at t = (n + 1/2) dt, for
+ * the n_steps steps from the first one whose t_{n+1/2} >= t0, zero after.
+ * Replaces any source; amp = 0 removes it.  Errors: MB_ERR_ARG (t0 < 0, tau
+ * <= 0, 1 <= n_steps <= 2^24 violated, cell outside the grid). */
+int mb_set_source_cw(mb_ctx* ctx, const int ijk[3], int comp, double lam, double t0,
+                     double tau, double amp, int n_steps);
+
+/* Whole-plane probe on the plane z = k dx (the sample's middle section for
+ * k = n_z/2): running FP64 DFTs of Ex, Ey, Ez on every cell of the plane,
+ * at t_{n+1}, every `every` steps, n_freq (1..64) wavelengths evenly spaced
+ * from lam_min to lam_max.  *probe_id receives its index.  Plane probes are
+ * kept by save/load and are not advanced inside a batch.
+ * Errors: MB_ERR_ARG, MB_ERR_OOM. */
+int mb_add_plane_probe(mb_ctx* ctx, int k, int every, int n_freq, double lam_min,
+                       double lam_max, int* probe_id);
+
+/* Mode map of a plane probe at frequency bin `bin`: out_map[i + n_x j] =
+ * sum over components of |sum_n E_c(t_n) exp(i w t_n) every dt|^2 in
+ * (V s/m)^2 (host array of n_x n_y doubles).  Synchronizes. */
+int mb_plane_mode_map(mb_ctx* ctx, int probe_id, int bin, double* out_map);
+
+/* Snapshot of the energy density on the plane z = k dx (the middle-section
+ * snapshot of the paper's Fig. 2a): out[i + n_x j] = (eps0 eps_r |E|^2 +
+ * mu0 |H|^2)/2 of each cell's own components (J/m^3; the per-cell terms of
+ * mb_energy), host array of n_x n_y doubles.  Synchronizes. */
+int mb_plane_energy_density(mb_ctx* ctx, int k, double* out);
+
 /* Advance n >= 0 steps (asynchronous; replays a captured CUDA graph). */
 int mb_step(mb_ctx* ctx, int n);
 
 /* Advance n >= 0 steps like mb_step, but with direct launches bracketed by
  * CUDA events on the context's stream; synchronizes, then adds the summed
  * device time (ms) of each pass over the n steps to ms_out[0..3]: H pass,
- * fused E pass, point-probe DFT, face-probe DFT (ms_out may be NULL). */
+ * fused E pass, point-probe DFT, face- and plane-probe DFTs (ms_out may be
+ * NULL). */
 int mb_step_timed(mb_ctx* ctx, int n, double* ms_out);
 
 /* Wait for the context's queued work. */
@@ -229,7 +260,7 @@ int mb_philox4x32_10(const uint32_t* ctr, const uint32_t key[2], uint32_t* out, 
  * mb_batch_instance) whose fields, probes and read-outs behave as with
  * mb_step — the fields are bit-identical to stepping the instance alone.
  * Supported inside a batch: point probes, sources, the face flux and energy;
- * mb_batch_step returns MB_ERR_STATE when a member has face probes, has no
+ * mb_batch_step returns MB_ERR_STATE when a member has face or plane probes, has no
  * material yet, or was stepped outside the batch.  A barrier that waits
  * longer than ~1 s makes the launch end and mb_batch_synchronize return
  * MB_ERR_TIMEOUT. */

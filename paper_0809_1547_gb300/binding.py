@@ -63,6 +63,12 @@ _SIGS = [
     ("mb_add_face_probes", C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double]),
     ("mb_set_source", C.c_int, [_P, C.POINTER(C.c_int), C.c_int, C.c_double, C.c_double,
                                 C.c_double, C.c_double]),
+    ("mb_set_source_cw", C.c_int, [_P, C.POINTER(C.c_int), C.c_int, C.c_double, C.c_double,
+                                   C.c_double, C.c_double, C.c_int]),
+    ("mb_add_plane_probe", C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
+                                     C.POINTER(C.c_int)]),
+    ("mb_plane_mode_map", C.c_int, [_P, C.c_int, C.c_int, _P]),
+    ("mb_plane_energy_density", C.c_int, [_P, C.c_int, _P]),
     ("mb_step", C.c_int, [_P, C.c_int]),
     ("mb_step_timed", C.c_int, [_P, C.c_int, _P]),
     ("mb_flux", C.c_int, [_P, _P]),
@@ -184,6 +190,30 @@ def mb_add_face_probes(h, stride, every, n_freq, lam_min, lam_max):
 def mb_set_source(h, ijk, comp, lam, t0, tau, amp):
     _check(load_library().mb_set_source(h, (C.c_int * 3)(*ijk), int(comp), float(lam), float(t0),
                                         float(tau), float(amp)), h)
+
+
+def mb_set_source_cw(h, ijk, comp, lam, t0, tau, amp, n_steps):
+    _check(load_library().mb_set_source_cw(h, (C.c_int * 3)(*ijk), int(comp), float(lam), float(t0),
+                                           float(tau), float(amp), int(n_steps)), h)
+
+
+def mb_add_plane_probe(h, k, every, n_freq, lam_min, lam_max) -> int:
+    pid = C.c_int()
+    _check(load_library().mb_add_plane_probe(h, int(k), int(every), int(n_freq), float(lam_min),
+                                             float(lam_max), C.byref(pid)), h)
+    return pid.value
+
+
+def mb_plane_mode_map(h, probe_id, bin_, shape):
+    out = np.zeros(int(np.prod(shape)))
+    _check(load_library().mb_plane_mode_map(h, int(probe_id), int(bin_), _ptr(out)), h)
+    return out.reshape(shape)
+
+
+def mb_plane_energy_density(h, k, shape):
+    out = np.zeros(int(np.prod(shape)))
+    _check(load_library().mb_plane_energy_density(h, int(k), _ptr(out)), h)
+    return out.reshape(shape)
 
 
 def mb_step(h, n):
@@ -441,6 +471,20 @@ class MBSimulation:
 
     def set_source(self, ijk, comp, lam, t0, tau, amp):
         mb_set_source(self._h, ijk, comp, lam, t0, tau, amp)
+
+    def set_source_cw(self, ijk, comp, lam, t0, tau, amp, n_steps):
+        mb_set_source_cw(self._h, ijk, comp, lam, t0, tau, amp, n_steps)
+
+    def add_plane_probe(self, k, every, n_freq, lam_min, lam_max):
+        return mb_add_plane_probe(self._h, k, every, n_freq, lam_min, lam_max)
+
+    def plane_mode_map(self, probe_id, bin_):
+        """(n_y, n_x) mode map of a plane probe at one frequency bin."""
+        return mb_plane_mode_map(self._h, probe_id, bin_, self.shape[1:])
+
+    def plane_energy_density(self, k):
+        """(n_y, n_x) energy density (J/m^3) of the plane z = k."""
+        return mb_plane_energy_density(self._h, k, self.shape[1:])
 
     def step(self, n=1):
         mb_step(self._h, n)

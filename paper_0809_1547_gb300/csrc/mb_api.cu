@@ -231,6 +231,8 @@ std::vector<StatePart> state_parts(mb_ctx* c) {
         v.push_back({c->d_probe_acc, sizeof(double2) * 3 * c->probes.size() * c->probe_nfreq});
     if (c->face.on && c->face_points)
         v.push_back({c->d_face_acc, sizeof(double2) * 4 * (size_t)c->face_points * c->face.nfreq});
+    for (const mb::DevPlaneProbe& q : c->planes)
+        v.push_back({q.acc, sizeof(double2) * 3 * (size_t)q.nfreq * c->nx * c->ny});
     return v;
 }
 
@@ -257,16 +259,23 @@ int check_device_error(mb_ctx* c) {
     return MB_OK;
 }
 
+// The probes of one step, after its E pass: point DFTs, face DFTs, plane DFTs.
+void launch_probes(mb_ctx* c) {
+    mb::DevPointProbes pp{(int)c->probes.size(), c->probe_nfreq, c->d_probe_cell,
+                          c->d_probe_omega, c->d_probe_acc};
+    mb::launch_point_dft(pp, c->args.f, c->d_ctr, c->dt, c->stream);
+    mb::launch_face_dft(c->face, c->args.f, c->args.g, c->d_ctr, c->dt, c->stream);
+    for (const mb::DevPlaneProbe& q : c->planes)
+        mb::launch_plane_dft(q, c->args.f, c->args.g, c->d_ctr, c->dt, c->stream);
+}
+
 int capture_steps(mb_ctx* c, int steps, cudaGraphExec_t* out) {
     cudaGraph_t graph = nullptr;
     MB_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-    mb::DevPointProbes pp{(int)c->probes.size(), c->probe_nfreq, c->d_probe_cell,
-                          c->d_probe_omega, c->d_probe_acc};
     for (int s = 0; s < steps; ++s) {
         mb::launch_h_pass(c->args, c->tune_h, tma_for(c, c->tune_h), c->stream);
         mb::launch_e_pass(c->args, c->tune_e, tma_for(c, c->tune_e), c->stream);
-        mb::launch_point_dft(pp, c->args.f, c->d_ctr, c->dt, c->stream);
-        mb::launch_face_dft(c->face, c->args.f, c->args.g, c->d_ctr, c->dt, c->stream);
+        launch_probes(c);
     }
     cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
     if (e != cudaSuccess) return fail(c, MB_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
@@ -285,7 +294,7 @@ void sum_flux_slots(const double* slots, double fl[6]) {
 }
 
 int launches_per_step(const mb_ctx* c) {
-    return 2 + (c->probes.empty() ? 0 : 1) + (c->face.on ? 1 : 0);
+    return 2 + (c->probes.empty() ? 0 : 1) + (c->face.on ? 1 : 0) + (int)c->planes.size();
 }
 
 void drop_graphs(mb_ctx* c) {
@@ -334,12 +343,9 @@ void mb::gain_pump_derivative(const mb_ctx* c, float dg[3], float dG[3][3], floa
 const mb::TmaMaps* mb::tma_maps(mb_ctx* c, const mb::PassTune& t) { return tma_for(c, t); }
 
 cudaError_t mb::enqueue_step(mb_ctx* c) {
-    mb::DevPointProbes pp{(int)c->probes.size(), c->probe_nfreq, c->d_probe_cell,
-                          c->d_probe_omega, c->d_probe_acc};
     mb::launch_h_pass(c->args, c->tune_h, tma_for(c, c->tune_h), c->stream);
     mb::launch_e_pass(c->args, c->tune_e, tma_for(c, c->tune_e), c->stream);
-    mb::launch_point_dft(pp, c->args.f, c->d_ctr, c->dt, c->stream);
-    mb::launch_face_dft(c->face, c->args.f, c->args.g, c->d_ctr, c->dt, c->stream);
+    launch_probes(c);
     c->n += 1;
     c->launches += launches_per_step(c);
     return cudaGetLastError();
@@ -515,6 +521,10 @@ int mb_destroy(mb_ctx* c) {
                     c->d_face_omega, c->d_face_acc, c->d_glist, c->d_src_wave, c->d_err};
     for (void* b : bufs)
         if (b) cudaFree(b);
+    for (const mb::DevPlaneProbe& q : c->planes) {
+        cudaFree(const_cast<double*>(q.omega));
+        cudaFree(q.acc);
+    }
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
     return MB_OK;
@@ -765,6 +775,114 @@ int mb_set_source(mb_ctx* c, const int ijk[3], int comp, double lam, double t0, 
     return MB_OK;
 }
 
+int mb_set_source_cw(mb_ctx* c, const int ijk[3], int comp, double lam, double t0, double tau,
+                     double amp, int n_steps) {
+    if (int rc = check_ctx(c)) return rc;
+    if (amp == 0.0) return mb_set_source(c, ijk, comp, lam, t0, tau, 0.0);
+    if (!ijk || comp < 0 || comp > 2 || !(lam > 0) || !(tau > 0) || !std::isfinite(amp) ||
+        !(t0 >= 0) || n_steps < 1 || n_steps > (1 << 24))
+        return fail(c, MB_ERR_ARG, "bad CW source arguments");
+    if (ijk[0] < 0 || ijk[0] >= c->nx || ijk[1] < 0 || ijk[1] >= c->ny || ijk[2] < 0 || ijk[2] >= c->nz)
+        return fail(c, MB_ERR_ARG, "source cell outside the grid");
+    // n_steps steps from the first one whose t_{n+1/2} >= t0, tabulated in FP64
+    const double amp_s = amp * c->dt / (kEps0 * c->E0);
+    const double ws = 2.0 * kPi * kC0 / lam;
+    const long long n0 = std::max(0LL, (long long)std::ceil(t0 / c->dt - 0.5));
+    std::vector<float> wave((size_t)n_steps);
+    for (long long q = 0; q < n_steps; ++q) {
+        const double t = ((double)(n0 + q) + 0.5) * c->dt - t0;
+        const double e = t / tau;
+        wave[(size_t)q] = t < 0 ? 0.0f : (float)(amp_s * std::sin(ws * t) * (1.0 - std::exp(-e * e)));
+    }
+    cudaStreamSynchronize(c->stream);
+    if (c->d_src_wave) {
+        cudaFree(c->d_src_wave);
+        c->d_src_wave = nullptr;
+    }
+    MB_CUDA(c, cudaMalloc((void**)&c->d_src_wave, sizeof(float) * wave.size()));
+    MB_CUDA(c, cudaMemcpy(c->d_src_wave, wave.data(), sizeof(float) * wave.size(), cudaMemcpyHostToDevice));
+    c->src.on = 1;
+    c->src.comp = comp;
+    c->src.cell = ijk[0] + (int64_t)c->nx * (ijk[1] + (int64_t)c->ny * ijk[2]);
+    c->src.n0 = n0;
+    c->src.count = n_steps;
+    c->src.wave = c->d_src_wave;
+    c->args.src = c->src;
+    drop_graphs(c);
+    return MB_OK;
+}
+
+int mb_add_plane_probe(mb_ctx* c, int k, int every, int n_freq, double lam_min, double lam_max,
+                       int* probe_id) {
+    if (int rc = check_ctx(c)) return rc;
+    if (k < 0 || k >= c->nz || every < 1 || n_freq < 1 || n_freq > mb::kPlaneMaxFreq ||
+        !(lam_min > 0) || !(lam_max > 0) || !probe_id)
+        return fail(c, MB_ERR_ARG, "bad plane-probe arguments (1 <= n_freq <= 64, 0 <= k < n_z)");
+    std::vector<double> lam, om;
+    for (int q = 0; q < n_freq; ++q) {
+        const double l = n_freq == 1 ? lam_min : lam_min + (lam_max - lam_min) * q / (n_freq - 1);
+        lam.push_back(l);
+        om.push_back(2.0 * kPi * kC0 / l);
+    }
+    cudaStreamSynchronize(c->stream);
+    double* d_om = nullptr;
+    double2* d_acc = nullptr;
+    const size_t accn = 3 * (size_t)n_freq * c->nx * c->ny;
+    cudaError_t e = cudaMalloc((void**)&d_om, sizeof(double) * n_freq);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d_acc, sizeof(double2) * accn);
+    if (e == cudaSuccess) e = cudaMemcpy(d_om, om.data(), sizeof(double) * n_freq, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(d_acc, 0, sizeof(double2) * accn);
+    if (e != cudaSuccess) {
+        if (d_om) cudaFree(d_om);
+        if (d_acc) cudaFree(d_acc);
+        return fail(c, e == cudaErrorMemoryAllocation ? MB_ERR_OOM : MB_ERR_CUDA, cudaGetErrorString(e));
+    }
+    c->planes.push_back(mb::DevPlaneProbe{k, every, n_freq, d_om, d_acc});
+    c->plane_lam.push_back(lam);
+    *probe_id = (int)c->planes.size() - 1;
+    drop_graphs(c);
+    return MB_OK;
+}
+
+int mb_plane_mode_map(mb_ctx* c, int probe_id, int bin, double* out_map) {
+    if (int rc = check_ctx(c)) return rc;
+    if (probe_id < 0 || probe_id >= (int)c->planes.size() || !out_map)
+        return fail(c, MB_ERR_ARG, "bad plane probe");
+    const mb::DevPlaneProbe& q = c->planes[probe_id];
+    if (bin < 0 || bin >= q.nfreq) return fail(c, MB_ERR_ARG, "bad frequency bin");
+    const size_t nxy = (size_t)c->nx * c->ny;
+    std::vector<double2> acc(3 * nxy);
+    MB_CUDA(c, cudaMemcpyAsync(acc.data(), q.acc + (size_t)bin * 3 * nxy, sizeof(double2) * 3 * nxy,
+                               cudaMemcpyDeviceToHost, c->stream));
+    MB_CUDA(c, cudaStreamSynchronize(c->stream));
+    const double w = c->E0 * q.every * c->dt;   // scaled sample -> V/m, times the DFT weight
+    for (size_t p = 0; p < nxy; ++p) {
+        double v = 0.0;
+        for (int comp = 0; comp < 3; ++comp) {
+            const double2 a = acc[comp * nxy + p];
+            v += a.x * a.x + a.y * a.y;
+        }
+        out_map[p] = v * w * w;
+    }
+    return check_device_error(c);
+}
+
+int mb_plane_energy_density(mb_ctx* c, int k, double* out) {
+    if (int rc = check_ctx(c)) return rc;
+    if (k < 0 || k >= c->nz || !out) return fail(c, MB_ERR_ARG, "bad plane");
+    const size_t nxy = (size_t)c->nx * c->ny;
+    double* d = nullptr;
+    MB_CUDA(c, cudaMalloc((void**)&d, sizeof(double) * nxy));
+    mb::launch_plane_energy(c->args.f, c->args.g, k, c->d_lut + 128, d, c->stream);
+    cudaError_t e = cudaMemcpyAsync(out, d, sizeof(double) * nxy, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(c, MB_ERR_CUDA, cudaGetErrorString(e));
+    const double u0 = kEps0 * c->E0 * c->E0;
+    for (size_t p = 0; p < nxy; ++p) out[p] *= u0;
+    return check_device_error(c);
+}
+
 int mb_step(mb_ctx* c, int n) {
     if (int rc = check_ctx(c)) return rc;
     if (n < 0) return fail(c, MB_ERR_ARG, "negative step count");
@@ -812,6 +930,8 @@ int mb_step_timed(mb_ctx* c, int n, double* ms_out) {
         mb::launch_point_dft(pp, c->args.f, c->d_ctr, c->dt, c->stream);
         cudaEventRecord(e[3], c->stream);
         mb::launch_face_dft(c->face, c->args.f, c->args.g, c->d_ctr, c->dt, c->stream);
+        for (const mb::DevPlaneProbe& q : c->planes)
+            mb::launch_plane_dft(q, c->args.f, c->args.g, c->d_ctr, c->dt, c->stream);
         cudaEventRecord(e[4], c->stream);
     }
     cudaError_t le = cudaGetLastError();

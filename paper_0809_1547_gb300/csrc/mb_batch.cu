@@ -95,7 +95,8 @@ int rebuild(mb_batch* b) {
     for (int q = 0; q < B; ++q) {
         mb_ctx* c = b->inst[q];
         if (!c->have_material) return bfail(b, MB_ERR_STATE, "batch member without material");
-        if (c->face.on) return bfail(b, MB_ERR_STATE, "face probes are not advanced inside a batch");
+        if (c->face.on || !c->planes.empty())
+            return bfail(b, MB_ERR_STATE, "face and plane probes are not advanced inside a batch");
         args.push_back(c->args);
         probes.push_back({(int)c->probes.size(), c->probe_nfreq, c->d_probe_cell, c->d_probe_omega,
                           c->d_probe_acc});

@@ -59,6 +59,15 @@ struct DevFaceProbes {
     double2* acc;       // [point][4][nfreq]: Ea, Eb, Ha, Hb
 };
 
+// Whole-plane probe: running DFT of (Ex, Ey, Ez) on every cell of the plane
+// z = k, every `every` steps (scaled; times every dt E0 on read-out).
+constexpr int kPlaneMaxFreq = 64;
+struct DevPlaneProbe {
+    int k, every, nfreq;
+    const double* omega;   // [nfreq]
+    double2* acc;          // [nfreq][3][ny][nx]
+};
+
 // Launch shape of one field pass: the 3-D tiled variant (one thread per
 // cell, block = (bx, by, bz)) or the z-marching variant (2-D block (bx, by),
 // each thread walks kz planes).
@@ -159,6 +168,11 @@ constexpr int kBatchGainPerThread = 1;        // the same inside the persistent 
 cudaError_t launch_batch(const BatchArgs& b, dim3 block, int blocks, cudaStream_t s);
 int batch_blocks_per_sm(dim3 block);
 
+void launch_plane_dft(const DevPlaneProbe& pp, const DevFields& f, const DevGrid& g,
+                      const long long* ctr, double dt, cudaStream_t s);
+// Energy density of the cells of plane z = k in units of eps0 E0^2 (FP64).
+void launch_plane_energy(const DevFields& f, const DevGrid& g, int k, const float* lut_eps,
+                         double* out, cudaStream_t s);
 void launch_philox(const uint4* ctr, uint32_t k0, uint32_t k1, uint4* out, int n, cudaStream_t s);
 void launch_energy(const DevFields& f, int64_t ncell, const float* lut_eps, double* partial,
                    int nparts, int* nonfinite, double* out, cudaStream_t s);
@@ -234,6 +248,10 @@ struct mb_ctx {
     double* d_probe_omega = nullptr;
     double2* d_probe_acc = nullptr;
     int probe_nfreq = 0;
+
+    // whole-plane probes (mode maps)
+    std::vector<mb::DevPlaneProbe> planes;   // device pointers owned here
+    std::vector<std::vector<double>> plane_lam;
 
     // face probes
     mb::DevFaceProbes face{};

@@ -3,6 +3,8 @@
 //
 //   k_point_dft   running DFT of E at the point probes (FP64 accumulators)
 //   k_face_dft    running DFT of tangential E and H on the face sub-grids
+//   k_plane_dft   running DFT of E on a whole z-plane (mode maps)
+//   k_plane_energy  energy density of the cells of a z-plane (snapshots)
 //   k_energy_*    two-pass deterministic reduction of the field energy
 //   k_philox      the noise generator on given counters
 //
@@ -161,6 +163,61 @@ void launch_face_dft(const DevFaceProbes& fp, const DevFields& f, const DevGrid&
     dim3 grid((maxpts + fp.pts_per_block - 1) / fp.pts_per_block, 6);
     const int threads = fp.nfreq < 128 ? ((fp.nfreq + 31) / 32) * 32 : 128;
     k_face_dft<<<grid, threads, 0, s>>>(fp, f, g, ctr, dt);
+}
+
+// Plane DFT: one thread per plane cell; the block forms the phase factors
+// exp(i w_k t_{n+1}) once in shared memory.
+__global__ void k_plane_dft(DevPlaneProbe pp, DevFields f, DevGrid g, const long long* step_ctr,
+                            double dt) {
+    const long long n1 = step_ctr[0];         // n + 1
+    if (n1 % pp.every != 0) return;
+    __shared__ double2 ph[kPlaneMaxFreq];
+    const double t = (double)n1 * dt;
+    for (int kk = threadIdx.x; kk < pp.nfreq; kk += blockDim.x) {
+        double s_, c_;
+        sincos(pp.omega[kk] * t, &s_, &c_);
+        ph[kk] = make_double2(c_, s_);
+    }
+    __syncthreads();
+    const uint32_t nxy = g.nxy;
+    const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= nxy) return;
+    const uint32_t c = p + nxy * (uint32_t)pp.k;
+    const double e[3] = {(double)f.ex[c], (double)f.ey[c], (double)f.ez[c]};
+    for (int kk = 0; kk < pp.nfreq; ++kk) {
+        const double2 w = ph[kk];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            double2* a = pp.acc + ((size_t)kk * 3 + q) * nxy + p;
+            double2 v = *a;
+            v.x += e[q] * w.x;
+            v.y += e[q] * w.y;
+            *a = v;
+        }
+    }
+}
+
+// Energy density of plane z = k: (eps_r |E|^2 + |H|^2) / 2 in units of eps0 E0^2.
+__global__ void k_plane_energy(DevFields f, DevGrid g, int k, const float* lut_eps, double* out) {
+    const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= g.nxy) return;
+    const uint32_t c = p + g.nxy * (uint32_t)k;
+    const double eps = f.inv_eps ? 1.0 / (double)f.inv_eps[c] : (double)lut_eps[f.mat[c] & 0x7f];
+    const double ex = f.ex[c], ey = f.ey[c], ez = f.ez[c];
+    const double hx = f.hx[c], hy = f.hy[c], hz = f.hz[c];
+    out[p] = 0.5 * (eps * (ex * ex + ey * ey + ez * ez) + (hx * hx + hy * hy + hz * hz));
+}
+
+void launch_plane_dft(const DevPlaneProbe& pp, const DevFields& f, const DevGrid& g,
+                      const long long* ctr, double dt, cudaStream_t s) {
+    const unsigned blocks = (g.nxy + 255) / 256;
+    k_plane_dft<<<blocks, 256, 0, s>>>(pp, f, g, ctr, dt);
+}
+
+void launch_plane_energy(const DevFields& f, const DevGrid& g, int k, const float* lut_eps,
+                         double* out, cudaStream_t s) {
+    const unsigned blocks = (g.nxy + 255) / 256;
+    k_plane_energy<<<blocks, 256, 0, s>>>(f, g, k, lut_eps, out);
 }
 
 void launch_energy(const DevFields& f, int64_t ncell, const float* lut_eps, double* partial,
