@@ -387,6 +387,8 @@ def bench_ours(args):
         "clocks": clocks,
         "energy_J": U,
     }
+    if not args.no_passive and args.grid == 320:
+        out["passive"] = bench_passive(w, stream, max(50, args.steps // 3), args.warmup)
     if not args.no_batched:
         out["batched"] = bench_batched(stream, args.batched_steps, args.warmup)
     if not args.no_adjoint:
@@ -480,6 +482,63 @@ def bench_batched(stream, steps: int, warmup: int):
                                              "(autotuned, graph replay), one after another"},
             "ratio_vs_plain": round(v_batch / v_plain, 4),
             "l2": "inputs larger than L2"}
+
+
+# ---------------------------------------------------------------- passive
+
+def bench_passive(w, stream, steps: int, warmup: int):
+    """The 320^3 sample with the gain off (N_a = 0): (a) the response to the
+    single-cycle 532 nm pulse (tau = 1 fs, t0 = 4 tau) at the centre with the
+    centre probe and the six face probes; (b) CW excitation at 586.5 nm
+    (rise time 4 fs) with a whole-plane probe on the middle section z = n/2
+    (one bin at 586.5 nm, every step): the mode map of a long-living mode."""
+    import torch
+    from paper_0809_1547_gb300.binding import MBSimulation, mb_default_params
+    from paper_0809_1547_gb300.workloads import setup_simulation
+    cells = w.ncell
+    mid = tuple(v // 2 for v in w.grid)
+    out = {}
+
+    def run(sim):
+        sim.step(warmup)
+        sim.synchronize()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ms = sim.step_timed(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), ms
+
+    import copy
+    wp = copy.copy(w)
+    wp.N_a = 0.0
+    sim = setup_simulation(wp, autotune=True, stream=stream.cuda_stream)
+    sim.set_source(mid, 2, 532e-9, 4e-15, 1e-15, 1e9)
+    el, ms = run(sim)
+    sim.close()
+    out["pulse"] = {"value": round(cells * steps / (el / 1e3) / 1e6, 2), "unit": UNIT,
+                    "ms_per_step": round(el / steps, 5),
+                    "pass_ms_per_step": [round(v / steps, 5) for v in ms]}
+    sim = MBSimulation(w.grid, w.dx, w.dt, mb_default_params(npml=w.npml), stream=stream.cuda_stream)
+    sim.set_material(w.eps, w.gain, 0.0, 0.0)
+    sim.set_seed(w.seed)
+    sim.autotune()
+    sim.set_source_cw(mid, 2, 586.5e-9, 0.0, 4e-15, 1e9, steps + warmup + 10)
+    sim.add_plane_probe(mid[2], 1, 1, 586.5e-9, 586.5e-9)
+    el, ms = run(sim)
+    m = sim.plane_mode_map(0, 0)
+    sim.close()
+    out["cw_mode_map"] = {"value": round(cells * steps / (el / 1e3) / 1e6, 2), "unit": UNIT,
+                          "ms_per_step": round(el / steps, 5),
+                          "plane_probe_ms_per_step": round(ms[3] / steps, 5),
+                          "plane_cells": w.grid[0] * w.grid[1], "map_max": float(m.max())}
+    out["workload"] = (f"{w.name} geometry with the gain off (N_a = 0): (a) single-cycle 532 nm "
+                       "pulse at the centre, centre probe + 6 face probes; (b) CW at 586.5 nm at the "
+                       "centre with a whole-plane DFT probe on the middle section (1 bin, every step)")
+    out["steps"] = steps
+    return out
 
 
 # ---------------------------------------------------------------- adjoint
@@ -583,6 +642,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-ensemble leg")
     ap.add_argument("--batched-steps", type=int, default=40)
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint leg")
+    ap.add_argument("--no-passive", action="store_true", help="skip the passive (pulse, CW) leg")
     ap.add_argument("--tune", default="",
                     help="fixed launch shapes 'v,bx,by,bz:v,bx,by,bz' (H launch : E launch) "
                          "instead of the autotuner; for profiling a chosen variant")
