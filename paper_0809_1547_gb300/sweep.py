@@ -1,0 +1,122 @@
+"""Pump sweep over a batched ensemble: emission peak, linewidth and threshold
+versus the atomic density N_a (the simulation side of the paper's Fig. 5b,
+"Experimental results" paragraph: linewidth as a standard deviation and by a
+Gaussian fit of the spectrum).
+
+Every realization of the ensemble (N_a levels x disorder seeds) runs in one
+MBBatch; each carries a centre point probe whose running DFT (on the GPU)
+gives its spectrum.  The statistics of the spectra are host-side
+reductions of a few hundred numbers per realization:
+
+    peak       the bin of largest S
+    std width  sqrt(sum S (w - wbar)^2 / sum S), wbar the S-weighted mean
+    Gaussian   a parabola fitted to ln S over the bins with S >= 0.1 max S:
+               sigma = sqrt(-1 / (2 c)) for the quadratic coefficient c < 0
+    threshold  the lowest N_a whose mean std width is at most half of the
+               lowest level's (gain narrowing)
+
+    python -m paper_0809_1547_gb300.sweep --steps 8000 --out sweep.json
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import time
+
+import numpy as np
+
+C0 = 299_792_458.0
+LAM_MIN, LAM_MAX, N_FREQ = 475e-9, 705e-9, 128
+
+
+def spectral_stats(S: np.ndarray, lam: np.ndarray, frac: float = 0.1) -> dict:
+    """Statistics of spectra S (instances x bins) on wavelengths lam (bins)."""
+    S = np.atleast_2d(np.asarray(S, dtype=np.float64))
+    w = 2.0 * math.pi * C0 / np.asarray(lam, dtype=np.float64)
+    kpk = np.argmax(S, axis=1)
+    tot = S.sum(axis=1)
+    wbar = (S @ w) / tot
+    var = (S * (w[None, :] - wbar[:, None]) ** 2).sum(axis=1) / tot
+    gauss = np.full(S.shape[0], np.nan)
+    for q in range(S.shape[0]):
+        sel = S[q] >= frac * S[q, kpk[q]]
+        if sel.sum() >= 3:
+            ws = w[sel]
+            c2, _, _ = np.polyfit(ws - ws.mean(), np.log(S[q, sel]), 2)
+            if c2 < 0:
+                gauss[q] = math.sqrt(-0.5 / c2)
+    return {"peak_w": w[kpk], "peak_lam": np.asarray(lam)[kpk], "peak_S": S[np.arange(S.shape[0]), kpk],
+            "std_w": np.sqrt(var), "gauss_w": gauss, "total": tot}
+
+
+def summarize(levels, stats: dict) -> tuple[list, float | None]:
+    """Per N_a level (ascending): means over the realizations at that level."""
+    levels = np.asarray(levels, dtype=np.float64)
+    rows = []
+    for L in np.unique(levels):
+        m = levels == L
+        g = stats["gauss_w"][m]
+        g = g[np.isfinite(g)]
+        rows.append({"N_a": float(L), "n": int(m.sum()),
+                     "peak_lam_nm": float(np.mean(stats["peak_lam"][m]) * 1e9),
+                     "peak_w": float(np.mean(stats["peak_w"][m])),
+                     "std_w": float(np.mean(stats["std_w"][m])),
+                     "std_w_spread": float(np.std(stats["std_w"][m])),
+                     "gauss_w": float(np.mean(g)) if g.size else None,
+                     "emitted": float(np.mean(stats["total"][m]))})
+    base = rows[0]["std_w"]
+    thr = next((r["N_a"] for r in rows if r["std_w"] <= 0.5 * base), None)
+    return rows, thr
+
+
+def run_pump_sweep(workloads, steps: int, stream=None, autotune: bool = True):
+    """Advance every workload of the ensemble `steps` steps in one MBBatch
+    and return (levels, spectra, lam, seconds)."""
+    from .binding import MBBatch, mb_default_params
+    b = MBBatch([w.grid for w in workloads], workloads[0].dx, workloads[0].dt,
+                mb_default_params(npml=workloads[0].npml), stream=stream)
+    try:
+        for q, w in enumerate(workloads):
+            b.set_instance(q, w.eps, w.gain, w.N_a, w.pump, w.seed)
+            b.instances[q].add_point_probe(tuple(v // 2 for v in w.grid), N_FREQ, LAM_MIN, LAM_MAX)
+        if autotune:
+            b.autotune()
+        t0 = time.perf_counter()
+        b.step(steps)
+        b.synchronize()
+        secs = time.perf_counter() - t0
+        spectra, lam = [], None
+        for inst in b.instances:
+            S, lam = inst.probe_spectrum(0)
+            spectra.append(S)
+    finally:
+        b.close()
+    return [w.N_a for w in workloads], np.array(spectra), lam, secs
+
+
+def main():
+    from . import inputs
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--n-pump", type=int, default=16)
+    ap.add_argument("--n-seed", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--out", default="")
+    args = ap.parse_args()
+    ws = inputs.workload_batch(n_pump=args.n_pump, n_seed=args.n_seed)
+    levels, spectra, lam, secs = run_pump_sweep(ws, args.steps)
+    stats = spectral_stats(spectra, lam)
+    rows, thr = summarize(levels, stats)
+    cells = sum(int(np.prod(w.grid)) for w in ws)
+    out = {"instances": len(ws), "steps": args.steps, "seconds": secs,
+           "mcell_updates_per_s": cells * args.steps / secs / 1e6, "threshold_N_a": thr,
+           "levels": rows}
+    text = json.dumps(out, indent=1)
+    if args.out:
+        with open(args.out, "w") as f:
+            f.write(text)
+    print(text)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,44 @@
+"""Pins of the oracle's spectral statistics (CPU): closed forms."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle.mb_analysis import gaussian_fit, peak, std_width, sweep_table
+
+
+def test_sampled_gaussian_gives_back_centre_and_width():
+    w = np.linspace(3.0e15, 3.4e15, 401)
+    mu, sig = 3.19e15, 7.0e12
+    S = 2.5 * np.exp(-0.5 * ((w - mu) / sig) ** 2)
+    c, s = gaussian_fit(S, w)
+    assert c == pytest.approx(mu, rel=1e-10)
+    assert s == pytest.approx(sig, rel=1e-8)
+    assert std_width(S, w) == pytest.approx(sig, rel=1e-6)   # fully inside the window
+    pw, pS = peak(S, w)
+    assert abs(pw - mu) <= (w[1] - w[0]) and pS == pytest.approx(2.5, rel=1e-3)
+
+
+def test_flat_spectrum_std_width_is_uniform():
+    w = np.arange(1000, dtype=np.float64)
+    assert std_width(np.ones(1000), w) == pytest.approx(math.sqrt((1000 ** 2 - 1) / 12.0), rel=1e-12)
+    assert gaussian_fit(np.ones(1000), w) == (None, None)    # no curvature
+
+
+def test_two_lines_std_width_is_half_the_spacing():
+    w = np.linspace(0.0, 10.0, 11)
+    S = np.zeros(11)
+    S[2] = S[8] = 1.0
+    assert std_width(S, w) == pytest.approx(3.0, rel=1e-12)
+
+
+def test_sweep_threshold_is_first_level_that_halves_the_width():
+    w = np.linspace(-50.0, 50.0, 201)
+    def g(sig):
+        return np.exp(-0.5 * (w / sig) ** 2)
+    levels = [1, 1, 2, 2, 3, 3]
+    spectra = [g(20), g(20), g(14), g(14), g(8), g(8)]
+    rows, thr = sweep_table(levels, spectra, w)
+    assert [r["level"] for r in rows] == [1.0, 2.0, 3.0]
+    assert thr == 3.0
+    assert rows[2]["gauss_w"] == pytest.approx(8.0, rel=1e-8)
