@@ -9,7 +9,6 @@
 #include <cstring>
 #include <map>
 #include <mutex>
-#include <unordered_map>
 
 using mb::kC0;
 using mb::kEps0;
@@ -537,39 +536,54 @@ int mb_set_material(mb_ctx* c, const float* eps_map, const uint8_t* gain_mask, d
     if (!(N_a >= 0) || !(pump >= 0) || !std::isfinite(N_a) || !std::isfinite(pump))
         return fail(c, MB_ERR_ARG, "N_a and pump must be finite and >= 0");
     const int64_t N = c->ncell;
-    std::unordered_map<uint32_t, int> ids;
+    // Material ids by the bit pattern of eps_r: up to 128 distinct values
+    // share a LUT, more switch to a dense 1/eps map.  Packings hold a few
+    // values in long runs, so the last value is checked first, then the
+    // (short) table.
+    std::vector<uint32_t> keys;
     std::vector<float> lut_eps;
+    std::vector<uint8_t> mat((size_t)N);
     bool dense = false;
+    uint32_t last_bits = 0;
+    int last_id = -1;
+    const bool gain_on = N_a > 0.0;
     for (int64_t q = 0; q < N; ++q) {
         const float v = eps_map[q];
         if (!(v >= 1.0f) || !std::isfinite(v)) return fail(c, MB_ERR_MATERIALS, "eps_r must be finite and >= 1");
-        if (dense) continue;
-        uint32_t bits;
-        std::memcpy(&bits, &v, 4);
-        if (ids.find(bits) == ids.end()) {
-            if (ids.size() == 128) {
-                dense = true;
-                continue;
-            }
-            const int id = (int)ids.size();
-            ids[bits] = id;
-            lut_eps.push_back(v);
-        }
-    }
-    cudaStreamSynchronize(c->stream);
-    const bool gain_on = N_a > 0.0;
-    std::vector<uint8_t> mat((size_t)N);
-    for (int64_t q = 0; q < N; ++q) {
-        const bool g = gain_on && gain_mask[q] != 0;
-        c->h_gain[q] = g ? 1 : 0;
-        uint8_t id = 0;
+        int id = 0;
         if (!dense) {
             uint32_t bits;
-            std::memcpy(&bits, &eps_map[q], 4);
-            id = (uint8_t)ids[bits];
+            std::memcpy(&bits, &v, 4);
+            if (last_id >= 0 && bits == last_bits) {
+                id = last_id;
+            } else {
+                id = -1;
+                for (size_t t = 0; t < keys.size(); ++t)
+                    if (keys[t] == bits) {
+                        id = (int)t;
+                        break;
+                    }
+                if (id < 0) {
+                    if (keys.size() == 128) {
+                        dense = true;
+                        id = 0;
+                    } else {
+                        id = (int)keys.size();
+                        keys.push_back(bits);
+                        lut_eps.push_back(v);
+                    }
+                }
+                last_bits = bits;
+                last_id = dense ? -1 : id;
+            }
         }
-        mat[q] = id | (g ? 0x80 : 0x00);
+        const bool g = gain_on && gain_mask[q] != 0;
+        c->h_gain[q] = g ? 1 : 0;
+        mat[q] = (uint8_t)id | (g ? 0x80 : 0x00);
     }
+    if (dense)
+        for (int64_t q = 0; q < N; ++q) mat[q] &= 0x80;   // ids unused with the dense map
+    cudaStreamSynchronize(c->stream);
     std::vector<float> lut(256, 1.0f);
     c->h_lut_eps.assign(128, 1.0f);
     for (size_t q = 0; q < lut_eps.size(); ++q) {
