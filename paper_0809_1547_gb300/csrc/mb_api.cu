@@ -9,6 +9,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <thread>
 
 using mb::kC0;
 using mb::kEps0;
@@ -537,52 +538,91 @@ int mb_set_material(mb_ctx* c, const float* eps_map, const uint8_t* gain_mask, d
         return fail(c, MB_ERR_ARG, "N_a and pump must be finite and >= 0");
     const int64_t N = c->ncell;
     // Material ids by the bit pattern of eps_r: up to 128 distinct values
-    // share a LUT, more switch to a dense 1/eps map.  Packings hold a few
-    // values in long runs, so the last value is checked first, then the
-    // (short) table.
-    std::vector<uint32_t> keys;
-    std::vector<float> lut_eps;
-    std::vector<uint8_t> mat((size_t)N);
-    bool dense = false;
-    uint32_t last_bits = 0;
-    int last_id = -1;
+    // share a LUT, more switch to a dense 1/eps map.  Host threads over
+    // chunks of cells: (1) each collects its distinct values (a packing
+    // holds a few values in long runs: the last value is checked first, then
+    // a short table), merged in chunk order; (2) each maps its cells to ids
+    // and lists its gain cells, concatenated in chunk order (increasing).
     const bool gain_on = N_a > 0.0;
-    for (int64_t q = 0; q < N; ++q) {
-        const float v = eps_map[q];
-        if (!(v >= 1.0f) || !std::isfinite(v)) return fail(c, MB_ERR_MATERIALS, "eps_r must be finite and >= 1");
-        int id = 0;
-        if (!dense) {
-            uint32_t bits;
-            std::memcpy(&bits, &v, 4);
-            if (last_id >= 0 && bits == last_bits) {
-                id = last_id;
-            } else {
-                id = -1;
-                for (size_t t = 0; t < keys.size(); ++t)
-                    if (keys[t] == bits) {
-                        id = (int)t;
-                        break;
+    const int nthr = (int)std::max<int64_t>(1, std::min<int64_t>(
+        {(int64_t)std::max(1u, std::thread::hardware_concurrency()), 16, N / (1 << 18) + 1}));
+    std::vector<std::pair<int64_t, int64_t>> chunk(nthr);
+    for (int t = 0; t < nthr; ++t) chunk[t] = {N * t / nthr, N * (t + 1) / nthr};
+    std::vector<std::vector<uint32_t>> seen(nthr);
+    std::vector<char> bad(nthr, 0);
+    auto find_key = [](const std::vector<uint32_t>& keys, uint32_t bits) -> int {
+        for (size_t t = 0; t < keys.size(); ++t)
+            if (keys[t] == bits) return (int)t;
+        return -1;
+    };
+    {
+        std::vector<std::thread> pool;
+        for (int t = 0; t < nthr; ++t)
+            pool.emplace_back([&, t]() {
+                uint32_t last = 0;
+                bool have = false;
+                for (int64_t q = chunk[t].first; q < chunk[t].second; ++q) {
+                    const float v = eps_map[q];
+                    if (!(v >= 1.0f) || !std::isfinite(v)) {
+                        bad[t] = 1;
+                        return;
                     }
-                if (id < 0) {
-                    if (keys.size() == 128) {
-                        dense = true;
-                        id = 0;
-                    } else {
-                        id = (int)keys.size();
-                        keys.push_back(bits);
-                        lut_eps.push_back(v);
-                    }
+                    uint32_t bits;
+                    std::memcpy(&bits, &v, 4);
+                    if (have && bits == last) continue;
+                    last = bits;
+                    have = true;
+                    if (seen[t].size() <= 128 && find_key(seen[t], bits) < 0) seen[t].push_back(bits);
                 }
-                last_bits = bits;
-                last_id = dense ? -1 : id;
-            }
-        }
-        const bool g = gain_on && gain_mask[q] != 0;
-        c->h_gain[q] = g ? 1 : 0;
-        mat[q] = (uint8_t)id | (g ? 0x80 : 0x00);
+            });
+        for (auto& th : pool) th.join();
     }
-    if (dense)
-        for (int64_t q = 0; q < N; ++q) mat[q] &= 0x80;   // ids unused with the dense map
+    for (int t = 0; t < nthr; ++t)
+        if (bad[t]) return fail(c, MB_ERR_MATERIALS, "eps_r must be finite and >= 1");
+    std::vector<uint32_t> keys;
+    bool dense = false;
+    for (int t = 0; t < nthr && !dense; ++t)
+        for (uint32_t bits : seen[t])
+            if (find_key(keys, bits) < 0) {
+                if (keys.size() == 128) {
+                    dense = true;
+                    break;
+                }
+                keys.push_back(bits);
+            }
+    std::vector<float> lut_eps;
+    for (uint32_t bits : keys) {
+        float v;
+        std::memcpy(&v, &bits, 4);
+        lut_eps.push_back(v);
+    }
+    std::vector<uint8_t> mat((size_t)N);
+    std::vector<std::vector<uint32_t>> gparts(nthr);
+    {
+        std::vector<std::thread> pool;
+        for (int t = 0; t < nthr; ++t)
+            pool.emplace_back([&, t]() {
+                uint32_t last = 0;
+                int last_id = -1;
+                for (int64_t q = chunk[t].first; q < chunk[t].second; ++q) {
+                    int id = 0;
+                    if (!dense) {
+                        uint32_t bits;
+                        std::memcpy(&bits, &eps_map[q], 4);
+                        if (last_id < 0 || bits != last) {
+                            last = bits;
+                            last_id = find_key(keys, bits);
+                        }
+                        id = last_id;
+                    }
+                    const bool g = gain_on && gain_mask[q] != 0;
+                    c->h_gain[q] = g ? 1 : 0;
+                    mat[q] = (uint8_t)id | (g ? 0x80 : 0x00);
+                    if (g) gparts[t].push_back((uint32_t)q);
+                }
+            });
+        for (auto& th : pool) th.join();
+    }
     cudaStreamSynchronize(c->stream);
     std::vector<float> lut(256, 1.0f);
     c->h_lut_eps.assign(128, 1.0f);
@@ -608,8 +648,12 @@ int mb_set_material(mb_ctx* c, const float* eps_map, const uint8_t* gain_mask, d
     c->W_p = pump;
     // gain cells in increasing order: the Lorentz update runs over this list
     std::vector<uint32_t> glist;
-    for (int64_t q = 0; q < N; ++q)
-        if (c->h_gain[q]) glist.push_back((uint32_t)q);
+    {
+        size_t total = 0;
+        for (auto& g : gparts) total += g.size();
+        glist.reserve(total);
+        for (auto& g : gparts) glist.insert(glist.end(), g.begin(), g.end());
+    }
     if (glist.size() > c->glist_count || !c->d_glist) {
         if (c->d_glist) {
             cudaFree(c->d_glist);
