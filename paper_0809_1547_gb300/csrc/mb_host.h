@@ -103,7 +103,9 @@ struct TmaLayoutE {
     static constexpr int kMBytes = (kEW + 127) / 128 * 128;
     static constexpr int kStage = 3 * kHBytes + 3 * kEBytes + kMBytes;
     static constexpr int kTx = 3 * kHW * 4 + 3 * kEW * 4 + kEW;   // bytes per stage
-    static constexpr int smem_bytes(int stages) { return stages * kStage + 64 + 128; }
+    // gain-cell J and n1..n3 of two planes (cp.async double buffer)
+    static constexpr int kGBytes = 2 * 6 * kEW * 4;
+    static constexpr int smem_bytes(int stages) { return stages * kStage + kGBytes + 64 + 128; }
 };
 
 // Shared-memory stage of the TMA H pass: E with the +x/+y halo and H of one

@@ -289,11 +289,15 @@ template <int BX, int BY, int S>
 __global__ void __launch_bounds__(BX * BY) k_e_tma(StepArgs a, const __grid_constant__ TmaMaps maps,
                                                    int kz) {
     using Lay = TmaLayoutE<BX, BY>;
+    constexpr int NW = BX * BY / 32;
     extern __shared__ unsigned char smem_raw[];
+    __shared__ float wfl[6][NW];   // per-warp face-flux partials, summed plane by plane
     unsigned char* smem = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + S * Lay::kStage);
+    float* gbuf = reinterpret_cast<float*>(smem + S * Lay::kStage);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + S * Lay::kStage + Lay::kGBytes);
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + BX * ty;
+    const int warp = tid >> 5;
     const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
     const int i = x0 + tx, j = y0 + ty;
     const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
@@ -321,11 +325,22 @@ __global__ void __launch_bounds__(BX * BY) k_e_tma(StepArgs a, const __grid_cons
     auto mat_of = [&](int s) -> uint8_t {
         return (smem + s * Lay::kStage + 3 * Lay::kHBytes + 3 * Lay::kEBytes)[tid];
     };
+    // J and n1..n3 of a gain cell, one plane ahead, into buffer b (no registers held)
+    auto gslot = [&](int b, int q) -> float* { return gbuf + (b * 6 + q) * (BX * BY) + tid; };
+    auto prefetch_gain = [&](int b, uint32_t cc) {
+        cp_async_4(gslot(b, 0), f.jx + cc);
+        cp_async_4(gslot(b, 1), f.jy + cc);
+        cp_async_4(gslot(b, 2), f.jz + cc);
+        cp_async_4(gslot(b, 3), f.n1 + cc);
+        cp_async_4(gslot(b, 4), f.n2 + cc);
+        cp_async_4(gslot(b, 5), f.n3 + cc);
+    };
 
     if (tid == 0) {
         for (int s = 0; s < S; ++s) mbar_init(&bar[s], 1);
         fence_barrier_init();
     }
+    if (tid < 6 * NW) wfl[tid / NW][tid % NW] = 0.0f;
     __syncthreads();
     if (tid == 0)
         for (int s = 0; s < S && k0 + s < k1; ++s) issue(s, k0 + s);
@@ -338,26 +353,20 @@ __global__ void __launch_bounds__(BX * BY) k_e_tma(StepArgs a, const __grid_cons
     }
     bool fail = !mbar_wait_bounded(&bar[0], 0, kWaitLimit);
     bool pg = valid && gain_on && (mat_of(0) & 0x80);
-    float pj[3] = {0.f, 0.f, 0.f}, pn[3] = {0.f, 0.f, 0.f};
-    if (pg) {
-        pj[0] = f.jx[c]; pj[1] = f.jy[c]; pj[2] = f.jz[c];
-        pn[0] = f.n1[c]; pn[1] = f.n2[c]; pn[2] = f.n3[c];
-    }
-    float fl[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (pg) prefetch_gain(0, c);
+    cp_async_commit();
     for (int it = 0, k = k0; k < k1; ++it, ++k) {
         const int s = it % S;
+        cp_async_wait_all();   // this plane's gain values (own thread's copies)
         bool ng = false;
-        float nj[3] = {0.f, 0.f, 0.f}, nn[3] = {0.f, 0.f, 0.f};
         if (k + 1 < k1) {
             const int s1 = (it + 1) % S;
             fail |= !mbar_wait_bounded(&bar[s1], ((it + 1) / S) & 1, kWaitLimit);
             ng = valid && gain_on && (mat_of(s1) & 0x80);
-            if (ng) {
-                const uint32_t c1 = c + nxy;
-                nj[0] = f.jx[c1]; nj[1] = f.jy[c1]; nj[2] = f.jz[c1];
-                nn[0] = f.n1[c1]; nn[1] = f.n2[c1]; nn[2] = f.n3[c1];
-            }
+            if (ng) prefetch_gain((it + 1) & 1, c + nxy);
         }
+        cp_async_commit();
+        float fl[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         if (valid && !fail) {
             const unsigned char* p = smem + s * Lay::kStage;
             const float* Hx = reinterpret_cast<const float*>(p);
@@ -378,25 +387,47 @@ __global__ void __launch_bounds__(BX * BY) k_e_tma(StepArgs a, const __grid_cons
             h.hx_k = hx_km1;
             h.hy_k = hy_km1;
             const uint8_t m = mat_of(s);
+            const int b = it & 1;
+            float jx = 0.f, jy = 0.f, jz = 0.f, n1 = 0.f, n2 = 0.f, n3 = 0.f;
+            if (pg) {
+                jx = *gslot(b, 0);
+                jy = *gslot(b, 1);
+                jz = *gslot(b, 2);
+                n1 = *gslot(b, 3);
+                n2 = *gslot(b, 4);
+                n3 = *gslot(b, 5);
+            }
             if (face)
-                e_apply<true, true>(a, i, j, k, c, h, m, Ex[tid], Ey[tid], Ez[tid], pg, pj[0], pj[1],
-                                    pj[2], pn[0], pn[1], pn[2], n, fl);
+                e_apply<true, true>(a, i, j, k, c, h, m, Ex[tid], Ey[tid], Ez[tid], pg, jx, jy, jz, n1,
+                                    n2, n3, n, fl);
             else if (pml_xy || plane_in_z_slab(a, k))
-                e_apply<false, true>(a, i, j, k, c, h, m, Ex[tid], Ey[tid], Ez[tid], pg, pj[0], pj[1],
-                                     pj[2], pn[0], pn[1], pn[2], n, fl);
+                e_apply<false, true>(a, i, j, k, c, h, m, Ex[tid], Ey[tid], Ez[tid], pg, jx, jy, jz, n1,
+                                     n2, n3, n, fl);
             else
-                e_apply<false, false>(a, i, j, k, c, h, m, Ex[tid], Ey[tid], Ez[tid], pg, pj[0],
-                                      pj[1], pj[2], pn[0], pn[1], pn[2], n, fl);
+                e_apply<false, false>(a, i, j, k, c, h, m, Ex[tid], Ey[tid], Ez[tid], pg, jx, jy, jz,
+                                      n1, n2, n3, n, fl);
             hx_km1 = h.hx;
             hy_km1 = h.hy;
+        }
+        if (face) {
+            // this plane's flux terms: warp sums, added to the warp's partials
+            const unsigned full = 0xffffffffu;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+                float v = fl[q];
+                if (__any_sync(full, v != 0.0f)) {
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(full, v, o);
+                    if ((tid & 31) == 0) wfl[q][warp] += v;
+                }
+            }
         }
         __syncthreads();   // slot s is free again
         if (tid == 0 && k + S < k1) issue(s, k + S);
         pg = ng;
-        pj[0] = nj[0]; pj[1] = nj[1]; pj[2] = nj[2];
-        pn[0] = nn[0]; pn[1] = nn[1]; pn[2] = nn[2];
         c += nxy;
     }
+    cp_async_wait_all();
     if (fail) {
         // A wait gave up: record it, then give the copies still in flight a
         // bounded chance to land before the block's shared memory is released.
@@ -407,7 +438,12 @@ __global__ void __launch_bounds__(BX * BY) k_e_tma(StepArgs a, const __grid_cons
             mbar_wait_bounded(&bar[s], (uses - 1) & 1, kWaitLimit);
         }
     }
-    if (face) flux_warp_reduce(a.flux, fl, warp_slot());
+    if (face && (tid & 31) == 0) {
+        const unsigned slot = warp_slot();
+#pragma unroll
+        for (int q = 0; q < 6; ++q)
+            if (wfl[q][warp] != 0.0f) atomicAdd(a.flux.acc + q * kFluxSlots + (slot % kFluxSlots), (double)wfl[q][warp]);
+    }
     finish_step(a);
 }
 
