@@ -31,9 +31,11 @@ namespace mb {
 
 namespace {
 
-// Forward fields of one stored step (P is not needed by the reverse sweep).
+// Forward fields of one stored step: E, J, n1..n3 of every cell and Hx, Hy
+// of the objective's H layer (k = z_plane - 1, indexed i + n_x j); P and the
+// rest of H enter the reverse sweep only linearly.
 struct FwdFields {
-    const float *ex, *ey, *ez, *hx, *hy, *hz, *jx, *jy, *jz, *n1, *n2, *n3;
+    const float *ex, *ey, *ez, *jx, *jy, *jz, *n1, *n2, *n3, *hpx, *hpy;
 };
 
 struct AdjArgs {
@@ -91,7 +93,8 @@ __device__ __forceinline__ void adj_point_cell(const AdjArgs& a, int i, int j, i
         float l0x = 0.0f, l0y = 0.0f, l0z = 0.0f;
         // objective: mx Hy(k-1) - my Hx(k-1) on the plane k = zp
         if (k == a.zp && i >= a.rx0 && i < a.rx1 && j >= a.ry0 && j < a.ry1) {
-            const float hxk = __ldg(a.x1.hx + c - a.g.nxy), hyk = __ldg(a.x1.hy + c - a.g.nxy);
+            const uint32_t cp = (uint32_t)i + (uint32_t)a.g.nx * j;
+            const float hxk = __ldg(a.x1.hpx + cp), hyk = __ldg(a.x1.hpy + cp);
             l1x += 0.5f * hyk;
             l1y -= 0.5f * hxk;
             l0x += 0.5f * hyk;
@@ -404,29 +407,37 @@ __global__ void __launch_bounds__(256) k_adj_e_point(AdjArgs a) {
     adj_point_cell(a, i, j, k, valid, lx, ly, lz);
 }
 
-// Store slot of one step: E, H (arrays 0..5) and J, n1..n3 (arrays 9..14)
-// of the field block, and the step counter.  16-byte moves when n_cells is
-// a multiple of 4 (every array then starts 16-byte aligned).
+// Store slot of one step: E (arrays 0..2) and J, n1..n3 (arrays 9..14) of
+// the field block, Hx and Hy of plane kp, and the step counter.  16-byte
+// moves when n_cells and the plane size are multiples of 4 (every array then
+// starts 16-byte aligned).
 __global__ void k_keep(const float* __restrict__ F, float* __restrict__ dst, uint32_t n,
-                       const long long* __restrict__ ctr, long long* __restrict__ slot_n) {
+                       uint32_t nxy, int kp, const long long* __restrict__ ctr,
+                       long long* __restrict__ slot_n) {
     if (blockIdx.x == 0 && threadIdx.x == 0) *slot_n = *ctr;
-    const size_t n6 = 6 * (size_t)n;
+    const size_t n3 = 3 * (size_t)n, n6 = 6 * (size_t)n;
     const size_t t0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const size_t stride = (size_t)gridDim.x * blockDim.x;
-    if ((n & 3u) == 0) {
-        const size_t q6 = n6 / 4;
+    const float* hpx = F + 3 * (size_t)n + (size_t)nxy * kp;
+    const float* hpy = F + 4 * (size_t)n + (size_t)nxy * kp;
+    float* dp = dst + 9 * (size_t)n;
+    if ((n & 3u) == 0 && (nxy & 3u) == 0) {
         const float4* a = reinterpret_cast<const float4*>(F);
         const float4* b = reinterpret_cast<const float4*>(F + 9 * (size_t)n);
         float4* d = reinterpret_cast<float4*>(dst);
-        for (size_t t = t0; t < q6; t += stride) {
-            d[t] = a[t];
-            d[t + q6] = b[t];
+        for (size_t t = t0; t < n3 / 4; t += stride) d[t] = a[t];
+        for (size_t t = t0; t < n6 / 4; t += stride) d[n3 / 4 + t] = b[t];
+        for (size_t t = t0; t < nxy / 4; t += stride) {
+            reinterpret_cast<float4*>(dp)[t] = reinterpret_cast<const float4*>(hpx)[t];
+            reinterpret_cast<float4*>(dp + nxy)[t] = reinterpret_cast<const float4*>(hpy)[t];
         }
     } else {
         const float* b = F + 9 * (size_t)n;
-        for (size_t t = t0; t < n6; t += stride) {
-            dst[t] = F[t];
-            dst[t + n6] = b[t];
+        for (size_t t = t0; t < n3; t += stride) dst[t] = F[t];
+        for (size_t t = t0; t < n6; t += stride) dst[n3 + t] = b[t];
+        for (size_t t = t0; t < nxy; t += stride) {
+            dp[t] = hpx[t];
+            dp[nxy + t] = hpy[t];
         }
     }
 }
@@ -475,7 +486,8 @@ extern "C" int mb_adjoint_energy_zface(mb_ctx* c, int n_steps, int ckpt_every, i
     const int nseg = (n_steps + K - 1) / K;
     const size_t N = (size_t)c->ncell;
     const size_t sb = mb::state_device_bytes(c);
-    const size_t slot = 12 * N;   // floats per stored step: E, H, J, n1..n3
+    const size_t nxy = (size_t)c->nx * c->ny;
+    const size_t slot = 9 * N + 2 * nxy;   // floats per stored step: E, J, n1..n3, Hx/Hy of one plane
     const size_t psi_total = c->psi_elems[0] + c->psi_elems[1] + c->psi_elems[2];
 
     int rc = MB_OK;
@@ -489,29 +501,32 @@ extern "C" int mb_adjoint_energy_zface(mb_ctx* c, int n_steps, int ckpt_every, i
     bool graph_ok = true;
     mb::AdjArgs a{};
     mb::StepArgs fa = c->args;
-    const mb::PassTune th = c->tune_h, te = c->tune_e;
-    const mb::TmaMaps* tma = mb::tma_maps(c, te);
-    const mb::PassTune te_r =
-        (te.variant == mb::kVariantTma && !tma) ? mb::PassTune{mb::kVariantZmarch, dim3(32, 4, 1), 16} : te;
+    // launch shapes of the recomputation (tuned below for its own regime)
+    mb::PassTune th = c->tune_h, te_r = c->tune_e;
+    auto maps_for = [&](const mb::PassTune& t) -> const mb::TmaMaps* {
+        return t.variant == mb::kVariantTma ? mb::tma_maps(c, t) : nullptr;
+    };
     double acc_h[2 * mb::kAccSlots];
     const dim3 blk(32, 8, 1);
     const dim3 grd((c->nx + 31) / 32, (c->ny + 7) / 8, c->nz);
     const float* F = c->d_fields;
 
-    // keep(t): the context's E, H, J, n1..n3 and step counter into store slot t
+    // keep(t): the context's E, J, n1..n3, the objective's H layer and the
+    // step counter into store slot t
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int keep_blocks = (int)std::max<size_t>(1, std::min<size_t>((6 * N / 4 + 255) / 256, (size_t)sms * 8));
     auto keep = [&](int t) -> cudaError_t {
-        mb::k_keep<<<keep_blocks, 256, 0, c->stream>>>(F, store + slot * t, (uint32_t)N, c->d_ctr, slot_n + t);
+        mb::k_keep<<<keep_blocks, 256, 0, c->stream>>>(F, store + slot * t, (uint32_t)N, (uint32_t)nxy,
+                                                       zp - 1, c->d_ctr, slot_n + t);
         return cudaGetLastError();
     };
     auto step_args = [&](int t) {
         auto fields = [&](int q) {
             const float* b = store + slot * q;
             return mb::FwdFields{b, b + N, b + 2 * N, b + 3 * N, b + 4 * N, b + 5 * N,
-                                 b + 6 * N, b + 7 * N, b + 8 * N, b + 9 * N, b + 10 * N, b + 11 * N};
+                                 b + 6 * N, b + 7 * N, b + 8 * N, b + 9 * N, b + 9 * N + nxy};
         };
         a.x0 = fields(t);
         a.x1 = fields(t + 1);
@@ -538,8 +553,8 @@ extern "C" int mb_adjoint_energy_zface(mb_ctx* c, int n_steps, int ckpt_every, i
     auto recompute = [&](int len) -> cudaError_t {
         cudaError_t e = keep(0);
         for (int t = 0; t < len && e == cudaSuccess; ++t) {
-            mb::launch_h_pass(fa, th, th.variant == mb::kVariantTma ? mb::tma_maps(c, th) : nullptr, c->stream);
-            mb::launch_e_pass(fa, te_r, te_r.variant == mb::kVariantTma ? tma : nullptr, c->stream);
+            mb::launch_h_pass(fa, th, maps_for(th), c->stream);
+            mb::launch_e_pass(fa, te_r, maps_for(te_r), c->stream);
             e = keep(t + 1);
         }
         return e;
@@ -558,6 +573,57 @@ extern "C" int mb_adjoint_energy_zface(mb_ctx* c, int n_steps, int ckpt_every, i
         if ((rc = mb::state_snapshot(c, ckpt + sb * m))) goto done;
         if ((rc = mb_step(c, K))) goto done;
     }
+    fa.flux.on = 0;
+    if (nseg > 1) {
+        // The recomputation streams from HBM (the segment store evicts the
+        // state from L2), unlike the plain step the context was tuned for:
+        // time candidate shapes in its own sequence (store, H, E) from the
+        // start of the last segment, then put the state back (the store is
+        // still empty).
+        if ((rc = mb::state_snapshot(c, ckpt + sb * (nseg - 1)))) goto done;
+        std::vector<mb::PassTune> cand = {c->tune_h, c->tune_e};
+        for (int kz : {4, 8, 16}) cand.push_back({mb::kVariantZmarch, dim3(32, 4, 1), kz});
+        cand.push_back({mb::kVariantZmarch, dim3(32, 8, 1), 8});
+        cand.push_back({mb::kVariantZmarch, dim3(64, 4, 1), 8});
+        if (mb::tma_e_supported(fa))
+            for (dim3 b : {dim3(32, 4, 1), dim3(64, 4, 1), dim3(32, 8, 1)})
+                for (int kz : {4, 8, 16}) cand.push_back({mb::kVariantTma, b, kz});
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        for (int pass = 0; pass < 2; ++pass) {
+            float best = 1e30f;
+            mb::PassTune pick = pass == 0 ? th : te_r;
+            for (const mb::PassTune& t : cand) {
+                if (t.kz > 2 * c->nz || (t.variant == mb::kVariantTma && !maps_for(t))) continue;
+                float tot = 0.0f;
+                for (int r = 0; r < 3; ++r) {
+                    MB_ACUDA(c, keep(0));
+                    if (pass == 1) mb::launch_h_pass(fa, th, maps_for(th), c->stream);
+                    cudaEventRecord(e0, c->stream);
+                    if (pass == 0) mb::launch_h_pass(fa, t, maps_for(t), c->stream);
+                    else mb::launch_e_pass(fa, t, maps_for(t), c->stream);
+                    cudaEventRecord(e1, c->stream);
+                    if (pass == 0) mb::launch_e_pass(fa, te_r, maps_for(te_r), c->stream);
+                    cudaEventSynchronize(e1);
+                    float ms = 0.0f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (r > 0) tot += ms;
+                }
+                if (tot < best) {
+                    best = tot;
+                    pick = t;
+                }
+            }
+            if (pass == 0) th = pick;
+            else te_r = pick;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        MB_ACUDA(c, cudaGetLastError());
+        if ((rc = mb::state_restore(c, ckpt + sb * (nseg - 1)))) goto done;
+    }
+
     {
         const int len = n_steps - (nseg - 1) * K;
         MB_ACUDA(c, keep(0));
@@ -572,7 +638,6 @@ extern "C" int mb_adjoint_energy_zface(mb_ctx* c, int n_steps, int ckpt_every, i
     MB_ACUDA(c, cudaMemsetAsync(geps, 0, sizeof(double) * N, c->stream));
     MB_ACUDA(c, cudaMemsetAsync(acc, 0, sizeof(double) * 2 * mb::kAccSlots, c->stream));
 
-    fa.flux.on = 0;
     a.g = c->args.g;
     a.L = c->p.npml;
     a.mat = c->d_mat;
