@@ -387,6 +387,8 @@ def bench_ours(args):
         "clocks": clocks,
         "energy_J": U,
     }
+    if not args.no_large and args.grid == 320:
+        out["large_448"] = bench_large(stream, max(50, args.steps // 6), args.warmup)
     if not args.no_passive and args.grid == 320:
         out["passive"] = bench_passive(w, stream, max(50, args.steps // 3), args.warmup)
     if not args.no_batched:
@@ -482,6 +484,48 @@ def bench_batched(stream, steps: int, warmup: int):
                                              "(autotuned, graph replay), one after another"},
             "ratio_vs_plain": round(v_batch / v_plain, 4),
             "l2": "inputs larger than L2"}
+
+
+# ------------------------------------------------------------ large sweep
+
+def bench_large(stream, steps: int, warmup: int):
+    """The 448^3 sample (8.96 um box, ~22.9k spheres d = 300 nm at 45 % fill,
+    gain in the voids, N_a 5e24 m^-3, noise on; 90 M cells, 5.8 GB of FP32
+    state): Mcell-updates/s and the passes' algorithmic HBM rates."""
+    import torch
+    from paper_0809_1547_gb300 import inputs
+    from paper_0809_1547_gb300.workloads import setup_simulation
+    w = inputs.workload_large_448()
+    sim = setup_simulation(w, autotune=True, stream=stream.cuda_stream)
+    sim.step(warmup)
+    sim.synchronize()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ms = sim.step_timed(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    el = e0.elapsed_time(e1)
+    blocks = sim.tuning()
+    sim.close()
+    cells = w.ncell
+    ab = algorithmic_bytes(w)
+    peak, _ = measured_peaks()
+    h_ms, e_ms = ms[0] / steps, ms[1] / steps
+    gbs = lambda b, t: b * cells / (t / 1e3) / 1e9
+    return {"workload": f"{w.name}: {w.grid[0]}^3 Yee grid, {w.n_spheres} TiO2 spheres d 300 nm at "
+                        f"{w.fill:.3f} fill, gain in the voids, N_a 5e24 m^-3, W_p 1e13/s, Langevin "
+                        "noise, centre probe + 6 face probes",
+            "cells": cells, "steps": steps, "value": round(cells * steps / (el / 1e3) / 1e6, 2),
+            "unit": UNIT, "ms_per_step": round(el / steps, 5),
+            "h_pass": {"ms": round(h_ms, 5), "gbs": round(gbs(ab["h_launch"], h_ms), 1),
+                       "frac": round(gbs(ab["h_launch"], h_ms) / peak, 4)},
+            "e_pass": {"ms": round(e_ms, 5), "gbs": round(gbs(ab["e_launch"], e_ms), 1),
+                       "frac": round(gbs(ab["e_launch"], e_ms) / peak, 4)},
+            "step_fused_minimum_frac": round(gbs(ab["step_fused_minimum"], el / steps) / peak, 4),
+            "blocks": {"h_pass": list(blocks[0]), "e_pass": list(blocks[1])},
+            "l2": "inputs larger than L2 (5.8 GB state)"}
 
 
 # ---------------------------------------------------------------- passive
@@ -643,6 +687,7 @@ def main():
     ap.add_argument("--batched-steps", type=int, default=40)
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint leg")
     ap.add_argument("--no-passive", action="store_true", help="skip the passive (pulse, CW) leg")
+    ap.add_argument("--no-large", action="store_true", help="skip the 448^3 leg")
     ap.add_argument("--tune", default="",
                     help="fixed launch shapes 'v,bx,by,bz:v,bx,by,bz' (H launch : E launch) "
                          "instead of the autotuner; for profiling a chosen variant")
