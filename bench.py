@@ -387,6 +387,8 @@ def bench_ours(args):
         "clocks": clocks,
         "energy_J": U,
     }
+    if args.grid == 320:
+        out["gp_theory"] = bench_gp()
     if not args.no_large and args.grid == 320:
         out["large_448"] = bench_large(stream, max(50, args.steps // 6), args.warmup)
     if not args.no_passive and args.grid == 320:
@@ -484,6 +486,28 @@ def bench_batched(stream, steps: int, warmup: int):
                                              "(autotuned, graph replay), one after another"},
             "ratio_vs_plain": round(v_batch / v_plain, 4),
             "l2": "inputs larger than L2"}
+
+
+# ------------------------------------------------------------- theory side
+
+def bench_gp(n_E: int = 512, n_grid: int = 2047):
+    """Bound states of -phi'' + tau^2 phi + phi^3 = E phi for n_E eigenvalues
+    (log-spaced 1.005-400) on n_grid points each, FP64 on the GPU, and the
+    theory curves (linewidth, peak) of kappa = 0.14 from them."""
+    import numpy as np
+    from paper_0809_1547_gb300 import gp
+    E = np.geomspace(1.005, 400.0, n_E)
+    gp.spectral_features(E[:8], n_grid)                      # warm-up
+    t0 = time.perf_counter()
+    w, pk = gp.spectral_features(E, n_grid)
+    secs = time.perf_counter() - t0
+    kappa = 0.14
+    p = gp.p_threshold(kappa) * np.array([1.01, 2.0, 5.0, 20.0])
+    c = gp.theory_curves(p, kappa, n_grid)
+    return {"what": f"{n_E} eigenvalues E in [1.005, 400], {n_grid}-point grids, Newton in FP64",
+            "ms": round(secs * 1e3, 2), "eigenvalues_per_s": round(n_E / secs, 1),
+            "kappa": kappa, "p_th": c["p_th"], "p_over_p_th": [1.01, 2.0, 5.0, 20.0],
+            "W_tg": [float(v) for v in c["W_tg"]], "S_p": [float(v) for v in c["S_p"]]}
 
 
 # ------------------------------------------------------------ large sweep

@@ -322,6 +322,24 @@ int mb_batch_get_tuning(mb_batch* batch, int* out3);
 int mb_adjoint_energy_zface(mb_ctx* ctx, int n_steps, int ckpt_every, int z_plane,
                             float* d_grad_eps, double* grad_pump, double* J_out);
 
+/* ------------------------------------------------------------------------
+ * Theory side: the bound state phi(tau) > 0 of
+ *     -phi'' + tau^2 phi + phi^3 = E phi        (the paper's Eq. g5)
+ * for each eigenvalue E[q] > 1 (bound states exist above threshold), on
+ * n_grid points tau_i = -L + i h, i = 1..n_grid, h = 2L/(n_grid + 1),
+ * L = sqrt(E) + 8, phi(+-L) = 0, second-order differences, solved in FP64 on
+ * the GPU by Newton's method (one thread per eigenvalue).  Outputs (host
+ * arrays of nE doubles): w_phi[q], the standard deviation of |phi~|^2 in the
+ * frequency Omega / 2 pi, and p_phi[q] = |phi~(0)|^2 / (4 pi^2), with phi~
+ * the Fourier transform of phi — the normalised spectral waist and peak of
+ * the paper's Figs. 3 and 5 (W = w_phi sqrt(kappa) / (p^{1/4} t_g), S_p =
+ * t_g^2 p_phi / gamma_S).  phi_out (host, nE x n_grid doubles) may be NULL.
+ * Synchronous.  Errors: MB_ERR_ARG (E <= 1 or not finite, n_grid outside
+ * 16..2^20), MB_ERR_STATE (Newton did not reach a bound state), MB_ERR_OOM,
+ * MB_ERR_CUDA. */
+int mb_gp_features(const double* E, int nE, int n_grid, double* w_phi, double* p_phi,
+                   double* phi_out);
+
 /* The paper has no counterpart of this call: it is a service for callers
  * that cannot allocate device memory — code running while a framework's
  * caching allocator owns the device memory, code that must not pay the

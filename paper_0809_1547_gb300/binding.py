@@ -99,6 +99,7 @@ _SIGS = [
     ("mb_batch_synchronize", C.c_int, [_P]),
     ("mb_batch_autotune", C.c_int, [_P]),
     ("mb_batch_get_tuning", C.c_int, [_P, C.POINTER(C.c_int)]),
+    ("mb_gp_features", C.c_int, [_P, C.c_int, C.c_int, _P, _P, _P]),
     ("mb_adjoint_energy_zface", C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P,
                                           C.POINTER(C.c_double), C.POINTER(C.c_double)]),
 ]
@@ -403,6 +404,17 @@ def mb_adjoint_energy_zface(h, n_steps, ckpt_every=200, z_plane=-1, d_grad_eps: 
                                                   C.c_void_p(d_grad_eps) if d_grad_eps else None,
                                                   C.byref(gp), C.byref(J)), h)
     return J.value, gp.value
+
+
+def mb_gp_features(E, n_grid=2047, want_phi=False):
+    """(w_phi, p_phi[, phi]) of the bound states for the eigenvalues E (> 1)."""
+    Ev = np.ascontiguousarray(np.atleast_1d(E), dtype=np.float64)
+    w = np.zeros(len(Ev))
+    p = np.zeros(len(Ev))
+    phi = np.zeros((len(Ev), int(n_grid))) if want_phi else None
+    _check(load_library().mb_gp_features(_ptr(Ev), len(Ev), int(n_grid), _ptr(w), _ptr(p),
+                                         _ptr(phi) if want_phi else None))
+    return (w, p, phi) if want_phi else (w, p)
 
 
 class MBSimulation:
