@@ -77,13 +77,19 @@ def thomas(a, b, c, d):
 
 
 def newton(phi, tau, h, E, tol=1e-12, max_iter=60):
+    """Newton steps until the residual is below tol max(1, E) or the step
+    stagnates at rounding level (|delta| <= 1e-14 max(1, max phi)); accepted
+    if the final residual is below 1e-9 max(1, E)."""
     off = np.full(len(phi), -1.0 / h ** 2)
     for _ in range(max_iter):
         F = residual(phi, tau, h, E)
         if np.max(np.abs(F)) < tol * max(1.0, E):
             return phi, True
         diag = 2.0 / h ** 2 + tau ** 2 + 3.0 * phi ** 2 - E
-        phi = phi - thomas(off, diag, off, F)
+        delta = thomas(off, diag, off, F)
+        phi = phi - delta
+        if np.max(np.abs(delta)) <= 1e-14 * max(1.0, phi.max()):
+            break
     return phi, np.max(np.abs(residual(phi, tau, h, E))) < 1e-9 * max(1.0, E)
 
 

@@ -8,8 +8,10 @@
 // iteration, all in FP64; one thread per eigenvalue, its arrays in global
 // scratch.  Newton starts from the larger of the Thomas-Fermi profile
 // sqrt(max(E - tau^2, 0)) and the first-order solution near threshold
-// 2^{1/4} sqrt(E - 1) exp(-tau^2 / 2); a result that collapses towards the
-// trivial solution phi = 0 is reported as not converged.
+// 2^{1/4} sqrt(E - 1) exp(-tau^2 / 2) and stops when the residual is below
+// 1e-12 max(1, E) or the step stagnates at rounding level; a result whose
+// residual stays above 1e-9 max(1, E), or that collapses towards the trivial
+// solution phi = 0, is reported as not converged.
 #include "mb_host.h"
 
 #include <cmath>
@@ -75,15 +77,19 @@ __global__ void k_gp_solve(const double* Es, int nE, int n, double* phi_all, dou
             dp[i] = (dp[i] - off * dp[i - 1]) / m;
         }
         double x = dp[n - 1];
+        double dmax = fabs(x), pmx = 0.0;
         phi[n - 1] -= x;
         for (int i = n - 2; i >= 0; --i) {
             x = dp[i] - cp[i] * x;
             phi[i] -= x;
+            dmax = fmax(dmax, fabs(x));
+            pmx = fmax(pmx, phi[i]);
         }
+        if (dmax <= 1e-14 * fmax(1.0, pmx)) break;   // stagnated at rounding level
     }
     if (!ok) {
         // the residual's rounding floor (~1/h^2 times eps) can lie above tol:
-        // accept a solution whose residual is below 1e-9 max(1, E)
+        // once the steps stagnate, accept a residual below 1e-9 max(1, E)
         double rmax = 0.0;
         for (int i = 0; i < n; ++i) {
             const double t = -L + h * (i + 1);
