@@ -322,6 +322,16 @@ int mb_batch_get_tuning(mb_batch* batch, int* out3);
 int mb_adjoint_energy_zface(mb_ctx* ctx, int n_steps, int ckpt_every, int z_plane,
                             float* d_grad_eps, double* grad_pump, double* J_out);
 
+/* Self-test of the bounded device waits (no counterpart in the paper): runs
+ * the batched kernel's grid barrier against a block that never arrives
+ * (which = 0, a cooperative grid of up to 8 blocks) or the TMA kernels'
+ * mbarrier wait against a transaction that never completes (which = 1, one
+ * block), with at most `limit` polls (1 .. 2^22), and stores in *gave_up the
+ * number of blocks whose wait ended unfulfilled (the grid's size, or 1).
+ * Nothing faults or hangs: the waits end by themselves and the device stays
+ * usable.  Synchronizes the device.  Errors: MB_ERR_ARG, MB_ERR_CUDA. */
+int mb_selftest_bounded_waits(int which, int limit, int* gave_up);
+
 /* ------------------------------------------------------------------------
  * Theory side: the bound state phi(tau) > 0 of
  *     -phi'' + tau^2 phi + phi^3 = E phi        (the paper's Eq. g5)

@@ -100,6 +100,7 @@ _SIGS = [
     ("mb_batch_autotune", C.c_int, [_P]),
     ("mb_batch_get_tuning", C.c_int, [_P, C.POINTER(C.c_int)]),
     ("mb_gp_features", C.c_int, [_P, C.c_int, C.c_int, _P, _P, _P]),
+    ("mb_selftest_bounded_waits", C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_int)]),
     ("mb_adjoint_energy_zface", C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P,
                                           C.POINTER(C.c_double), C.POINTER(C.c_double)]),
 ]
@@ -404,6 +405,14 @@ def mb_adjoint_energy_zface(h, n_steps, ckpt_every=200, z_plane=-1, d_grad_eps: 
                                                   C.c_void_p(d_grad_eps) if d_grad_eps else None,
                                                   C.byref(gp), C.byref(J)), h)
     return J.value, gp.value
+
+
+def mb_selftest_bounded_waits(which, limit=4096):
+    """Blocks whose bounded wait gave up on an event that never comes
+    (which 0: grid barrier, 1: mbarrier)."""
+    n = C.c_int()
+    _check(load_library().mb_selftest_bounded_waits(int(which), int(limit), C.byref(n)))
+    return n.value
 
 
 def mb_gp_features(E, n_grid=2047, want_phi=False):

@@ -342,6 +342,37 @@ int mb_batch_autotune(mb_batch* b) {
     return MB_OK;
 }
 
+int mb_selftest_bounded_waits(int which, int limit, int* gave_up) {
+    if ((which != 0 && which != 1) || limit < 1 || limit > mb::kBarrierSpinLimit || !gave_up)
+        return bfail(nullptr, MB_ERR_ARG, "which must be 0 or 1, 1 <= limit <= 2^22, gave_up non-null");
+    unsigned* bar = nullptr;
+    int* d = nullptr;
+    int blocks = 1;
+    cudaError_t e = cudaMalloc((void**)&bar, sizeof(unsigned) * 2);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(bar, 0, sizeof(unsigned) * 2);
+    if (e == cudaSuccess) e = cudaMemset(d, 0, sizeof(int));
+    if (e == cudaSuccess) {
+        if (which == 0) {
+            int dev = 0, sms = 1;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            blocks = std::min(sms, 8);
+            e = mb::launch_selftest_barrier(bar, blocks, limit, d, nullptr);
+        } else {
+            e = mb::launch_selftest_mbarrier(limit, d, nullptr);
+        }
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    int n = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&n, d, sizeof(int), cudaMemcpyDeviceToHost);
+    if (bar) cudaFree(bar);
+    if (d) cudaFree(d);
+    if (e != cudaSuccess) return bfail(nullptr, MB_ERR_CUDA, cudaGetErrorString(e));
+    *gave_up = n;
+    return MB_OK;
+}
+
 int mb_batch_get_tuning(mb_batch* b, int* out3) {
     if (!b || !out3) return bfail(b, MB_ERR_ARG, "null argument");
     out3[0] = (int)b->block.x;

@@ -3,13 +3,14 @@
 // barriers between the phases.
 #include "mb_host.h"
 #include "mb_tiles.cuh"
+#include "mb_tma.cuh"
 
 namespace mb {
 
 // ---------------------------------------------------- batched ensemble
 // Grid-wide barrier of a co-resident (cooperative) grid, with a bounded
-// wait: false when the other blocks did not all arrive within the limit.
-__device__ bool grid_barrier(unsigned* bar, unsigned nblocks) {
+// wait: false when the other blocks did not all arrive within `limit` polls.
+__device__ bool grid_barrier(unsigned* bar, unsigned nblocks, int limit = kBarrierSpinLimit) {
     __shared__ int ok_s;
     __syncthreads();
     if (linear_tid() == 0) {
@@ -23,7 +24,7 @@ __device__ bool grid_barrier(unsigned* bar, unsigned nblocks) {
             atomicAdd(bar + 1, 1u);
         } else {
             for (int it = 0; *gen == g; ++it) {
-                if (it > kBarrierSpinLimit) {
+                if (it > limit) {
                     ok = 0;
                     break;
                 }
@@ -159,6 +160,45 @@ cudaError_t launch_batch(const BatchArgs& b, dim3 block, int blocks, cudaStream_
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, k_batch, b);
+}
+
+// ------------------------------------------------- bounded-wait self-test
+// The waits of the batched and TMA kernels must end by themselves when the
+// awaited event never comes.  These kernels run the same wait code against
+// events that cannot happen and record whether it gave up.
+// Grid barrier counting one block more than the grid holds.
+__global__ void k_selftest_barrier(unsigned* bar, int limit, int* gave_up) {
+    if (!grid_barrier(bar, gridDim.x + 1, limit) && linear_tid() == 0) atomicAdd(gave_up, 1);
+}
+
+// An mbarrier that expects one arrival that never comes.
+__global__ void k_selftest_mbarrier(int limit, int* gave_up) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    const bool done = mbar_wait_bounded(&bar, 0, limit);
+    if (!done && threadIdx.x == 0) atomicAdd(gave_up, 1);
+}
+
+cudaError_t launch_selftest_barrier(unsigned* bar, int blocks, int limit, int* gave_up, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blocks, 1, 1);
+    cfg.blockDim = dim3(64, 1, 1);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_selftest_barrier, bar, limit, gave_up);
+}
+
+cudaError_t launch_selftest_mbarrier(int limit, int* gave_up, cudaStream_t s) {
+    k_selftest_mbarrier<<<1, 32, 0, s>>>(limit, gave_up);
+    return cudaGetLastError();
 }
 
 }  // namespace mb

@@ -168,6 +168,11 @@ constexpr int kBarrierSpinLimit = 1 << 22;   // ~0.3-1 s with 64 ns sleeps
 constexpr int kGainPerThread = 2;             // gain cells per thread in a gain block
 constexpr int kBatchGainPerThread = 1;        // the same inside the persistent kernel
 cudaError_t launch_batch(const BatchArgs& b, dim3 block, int blocks, cudaStream_t s);
+// Bounded-wait self-tests: a grid barrier that one phantom block never
+// reaches, an mbarrier that is never completed; gave_up counts the blocks
+// whose wait ended unfulfilled.
+cudaError_t launch_selftest_barrier(unsigned* bar, int blocks, int limit, int* gave_up, cudaStream_t s);
+cudaError_t launch_selftest_mbarrier(int limit, int* gave_up, cudaStream_t s);
 int batch_blocks_per_sm(dim3 block);
 
 void launch_plane_dft(const DevPlaneProbe& pp, const DevFields& f, const DevGrid& g,
