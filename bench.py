@@ -416,7 +416,8 @@ def bench_ours(args):
 
 # ------------------------------------------------------ batched ensemble
 
-def bench_batched(stream, steps: int, warmup: int):
+def bench_batched(stream, steps: int, warmup: int, n_pump: int = 16, n_seed: int = 5,
+                  autotune: bool = True, plain: bool = True):
     """The ensemble (16 N_a levels log-spaced 5e23-2e25 m^-3 x 5 disorder
     seeds, cubes of side 96-160, 45 % fill, gain in the voids, a centre probe
     each) advanced by the batched persistent launch, against the plain
@@ -425,7 +426,7 @@ def bench_batched(stream, steps: int, warmup: int):
     import torch
     from paper_0809_1547_gb300 import inputs
     from paper_0809_1547_gb300.binding import MBBatch, MBSimulation, mb_default_params
-    ws = inputs.workload_batch()
+    ws = inputs.workload_batch(n_pump=n_pump, n_seed=n_seed)
     p = mb_default_params(npml=ws[0].npml)
     cells = sum(int(np.prod(w.grid)) for w in ws)
 
@@ -446,13 +447,18 @@ def bench_batched(stream, steps: int, warmup: int):
     for q, w in enumerate(ws):
         b.set_instance(q, w.eps, w.gain, w.N_a, w.pump, w.seed)
         b.instances[q].add_point_probe(centre(w), 128, 475e-9, 705e-9)
-    b.autotune()
+    if autotune:
+        b.autotune()
     b.step(warmup)
     b.synchronize()
     batch_ms = timed(lambda: b.step(steps))
     b.synchronize()
     tune = b.tuning()
     b.close()
+    if not plain:
+        return {"instances": len(ws), "cells_per_step": cells, "steps": steps,
+                "value": round(cells * steps / (batch_ms / 1e3) / 1e6, 2), "unit": UNIT,
+                "tile_bx_by_kz": list(tune)}
 
     sims = []
     for w in ws:
@@ -611,7 +617,7 @@ def bench_passive(w, stream, steps: int, warmup: int):
 
 # ---------------------------------------------------------------- adjoint
 
-def bench_adjoint(stream, warmup: int):
+def bench_adjoint(stream, warmup: int, autotune: bool = True):
     """Gradient of the energy through the +z face w.r.t. eps (per cell) and the
     pump on the 96^3 workload (225 spheres, 45 % fill, gain in the voids,
     fixed pump and noise seed), 4000 steps with checkpoints every 200 steps,
@@ -627,7 +633,8 @@ def bench_adjoint(stream, warmup: int):
         s_ = MBSimulation(w.grid, w.dx, w.dt, mb_default_params(npml=w.npml), stream=stream.cuda_stream)
         s_.set_material(w.eps, w.gain, w.N_a, w.pump)
         s_.set_seed(w.seed)
-        s_.autotune()
+        if autotune:
+            s_.autotune()
         return s_
 
     def timed(fn):
@@ -700,6 +707,26 @@ def bench_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_only(args):
+    """One leg on its own (for profiling): its dict on one JSON line."""
+    import torch
+    from paper_0809_1547_gb300 import build
+    build.build()
+    stream = torch.cuda.Stream()
+    if args.only == "batched":
+        out = bench_batched(stream, args.batched_steps, args.warmup, args.batched_pump,
+                            args.batched_seeds, autotune=not args.no_autotune, plain=False)
+    elif args.only == "adjoint":
+        out = bench_adjoint(stream, args.warmup, autotune=not args.no_autotune)
+    elif args.only == "passive":
+        out = bench_passive(rank_workload(0, 320), stream, max(50, args.steps // 3), args.warmup)
+    elif args.only == "large":
+        out = bench_large(stream, max(50, args.steps // 6), args.warmup)
+    else:
+        out = bench_gp()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -712,6 +739,12 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint leg")
     ap.add_argument("--no-passive", action="store_true", help="skip the passive (pulse, CW) leg")
     ap.add_argument("--no-large", action="store_true", help="skip the 448^3 leg")
+    ap.add_argument("--only", choices=("batched", "adjoint", "passive", "large", "gp"), default="",
+                    help="run one leg alone and print its result (profiling)")
+    ap.add_argument("--batched-pump", type=int, default=16, help="N_a levels of the ensemble")
+    ap.add_argument("--batched-seeds", type=int, default=5, help="disorder seeds of the ensemble")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="--only batched/adjoint: default launch shapes (no tuning launches)")
     ap.add_argument("--tune", default="",
                     help="fixed launch shapes 'v,bx,by,bz:v,bx,by,bz' (H launch : E launch) "
                          "instead of the autotuner; for profiling a chosen variant")
@@ -721,6 +754,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.only:
+        run_only(args)
+        return
     if args.impl == "reference":
         bench_reference(args)
     else:
