@@ -38,7 +38,8 @@ UNIT = "Mcell-updates/s"
 FALLBACK_HBM_GBS = 6800.0
 PROFILE_DIR = os.path.join(ROOT, "profiles")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_0809_1547_gb300", "csrc", f)
-                  for f in ("mb_device.cuh", "mb_tiles.cuh", "mb_passes.cu", "mb_tma.cuh")]
+                  for f in ("mb_device.cuh", "mb_tiles.cuh", "mb_passes.cu", "mb_tma.cuh",
+                            "mb_fused.cu")]
 
 
 # ------------------------------------------------------------------ helpers
@@ -70,8 +71,11 @@ def algorithmic_bytes(w):
     E launch (E update + populations): read H and E, write E, read the
     material byte (37 B); per slab axis two psi_E (16 B); gain cells read J
     and read+write n1..n3 (36 B).
-    Fused minimum of the whole step (every array touched once): 73 B + 32 B
-    per slab axis + 72 B per gain cell (P, J, n1..n3 read+write).
+    Two-pass minimum of the whole step (the two launches above with E^n read
+    once by the gain work): 73 B + 32 B per slab axis + 72 B per gain cell.
+    Single-pass step (one launch per step): read E and H, write E and H to
+    the other copy, read the material byte (49 B); per slab axis four psi
+    read+write (32 B); gain cells read+write P, J and n1..n3 (72 B).
     """
     import numpy as np
     L = w.npml
@@ -80,9 +84,10 @@ def algorithmic_bytes(w):
     g = float(np.mean(w.gain != 0)) if w.N_a > 0 else 0.0
     h_launch = 36.0 + 16.0 * slab + 56.0 * g
     e_launch = 37.0 + 16.0 * slab + 36.0 * g
-    fused = 73.0 + 32.0 * slab + 72.0 * g
-    return {"h_launch": h_launch, "e_launch": e_launch, "step_fused_minimum": fused,
-            "gain_fraction": g, "slab_fraction_sum": slab}
+    two_pass = 73.0 + 32.0 * slab + 72.0 * g
+    single = 49.0 + 32.0 * slab + 72.0 * g
+    return {"h_launch": h_launch, "e_launch": e_launch, "step_two_pass_minimum": two_pass,
+            "single_pass_launch": single, "gain_fraction": g, "slab_fraction_sum": slab}
 
 
 def traffic_from_profile(kernel: str, workload: str = "mb320_active"):
@@ -273,6 +278,11 @@ def bench_ours(args):
     if args.tune:
         th, te = (tuple(int(v) for v in part.split(",")) for part in args.tune.split(":"))
         sim.set_tuning(th, te)
+    if args.single_pass == "off":
+        sim.set_single_pass((0, 32, 8, 16))
+    elif args.single_pass:
+        sim.set_single_pass((1,) + tuple(int(v) for v in args.single_pass.split(",")))
+    single = sim.single_pass()
     per_step_launches, _ = sim.launch_stats()
     blk_h, blk_e = sim.tuning()
     sim.step(args.warmup)
@@ -315,8 +325,15 @@ def bench_ours(args):
     peak, peak_kind = measured_peaks()
     h_avg_ms = pass_ms[0] / args.steps
     e_avg_ms = pass_ms[1] / args.steps
-    launches = {"k_hg (H half-step + gain-cell Lorentz/Langevin)": (h_avg_ms, ab["h_launch"], "k_hg"),
-                "k_e (E update + populations + face flux)": (e_avg_ms, ab["e_launch"], "k_e")}
+    if single[0]:
+        # steps run in pairs of single-pass launches (an odd K ends with one two-pass step)
+        n_single = args.steps - args.steps % 2
+        launches = {"k_step_fused (H half-step + Lorentz/Langevin + E + populations + face flux, "
+                    "one launch per step)": (h_avg_ms * args.steps / max(n_single, 1),
+                                             ab["single_pass_launch"], "k_step_fused")}
+    else:
+        launches = {"k_hg (H half-step + gain-cell Lorentz/Langevin)": (h_avg_ms, ab["h_launch"], "k_hg"),
+                    "k_e (E update + populations + face flux)": (e_avg_ms, ab["e_launch"], "k_e")}
     dom_name = max(launches, key=lambda k: launches[k][0])
     dom_ms, dom_bpc, dom_key = launches[dom_name]
     dom_bytes = dom_bpc * cells
@@ -367,8 +384,9 @@ def bench_ours(args):
                    "grid": list(w.grid), "cells": cells, "gain_fraction": round(ab["gain_fraction"], 4),
                    "l2": f"inputs larger than L2 (state {61 * cells / 1e9:.2f} GB per realization)",
                    "parallelism": f"replicas x{world} (one realization per GPU)",
-                   "timed_path": "direct launches with CUDA events around each pass",
-                   "blocks": {"h_pass": list(blk_h), "e_pass": list(blk_e)},
+                   "timed_path": "direct launches with CUDA events around each launch",
+                   "blocks": {"h_pass": list(blk_h), "e_pass": list(blk_e),
+                              "single_pass": list(single)},
                    "graph_replay_ms_per_step": round(graph_ms_per_step, 5)},
         "roofline": {"bound": "hbm", "kernel": dom_name,
                      "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
@@ -377,9 +395,9 @@ def bench_ours(args):
                      "traffic": traffic, "algorithmic_bytes_per_launch": round(dom_bytes),
                      "bytes_per_cell": round(dom_bpc, 2), "avg_launch_ms": round(dom_ms, 5),
                      "launches": other,
-                     "step": {"fused_minimum_bytes_per_cell": round(ab["step_fused_minimum"], 2),
-                              "achieved_gbs": round(ab["step_fused_minimum"] * cells / (step_ms / 1e3) / 1e9, 1),
-                              "frac": round(ab["step_fused_minimum"] * cells / (step_ms / 1e3) / 1e9 / peak, 4)},
+                     "step": {"single_pass_bytes_per_cell": round(ab["single_pass_launch"], 2),
+                              "achieved_gbs": round(ab["single_pass_launch"] * cells / (step_ms / 1e3) / 1e9, 1),
+                              "frac": round(ab["single_pass_launch"] * cells / (step_ms / 1e3) / 1e9 / peak, 4)},
                      "pass_ms_per_step": [round(v / args.steps, 5) for v in pass_ms]},
         "e2e": {"value": round(e2e_value, 2), "unit": UNIT, "h2d_bytes_per_step": round(h2d, 1),
                 "d2h_bytes_per_step": round(d2h, 1)},
@@ -538,23 +556,31 @@ def bench_large(stream, steps: int, warmup: int):
     torch.cuda.synchronize()
     el = e0.elapsed_time(e1)
     blocks = sim.tuning()
+    single = sim.single_pass()
     sim.close()
     cells = w.ncell
     ab = algorithmic_bytes(w)
     peak, _ = measured_peaks()
-    h_ms, e_ms = ms[0] / steps, ms[1] / steps
     gbs = lambda b, t: b * cells / (t / 1e3) / 1e9
+    if single[0]:
+        n_single = steps - steps % 2
+        f_ms = ms[0] / steps * steps / max(n_single, 1)
+        launches = {"single_pass": {"ms": round(f_ms, 5), "gbs": round(gbs(ab["single_pass_launch"], f_ms), 1),
+                                    "frac": round(gbs(ab["single_pass_launch"], f_ms) / peak, 4)}}
+    else:
+        h_ms, e_ms = ms[0] / steps, ms[1] / steps
+        launches = {"h_pass": {"ms": round(h_ms, 5), "gbs": round(gbs(ab["h_launch"], h_ms), 1),
+                               "frac": round(gbs(ab["h_launch"], h_ms) / peak, 4)},
+                    "e_pass": {"ms": round(e_ms, 5), "gbs": round(gbs(ab["e_launch"], e_ms), 1),
+                               "frac": round(gbs(ab["e_launch"], e_ms) / peak, 4)}}
     return {"workload": f"{w.name}: {w.grid[0]}^3 Yee grid, {w.n_spheres} TiO2 spheres d 300 nm at "
                         f"{w.fill:.3f} fill, gain in the voids, N_a 5e24 m^-3, W_p 1e13/s, Langevin "
                         "noise, centre probe + 6 face probes",
             "cells": cells, "steps": steps, "value": round(cells * steps / (el / 1e3) / 1e6, 2),
             "unit": UNIT, "ms_per_step": round(el / steps, 5),
-            "h_pass": {"ms": round(h_ms, 5), "gbs": round(gbs(ab["h_launch"], h_ms), 1),
-                       "frac": round(gbs(ab["h_launch"], h_ms) / peak, 4)},
-            "e_pass": {"ms": round(e_ms, 5), "gbs": round(gbs(ab["e_launch"], e_ms), 1),
-                       "frac": round(gbs(ab["e_launch"], e_ms) / peak, 4)},
-            "step_fused_minimum_frac": round(gbs(ab["step_fused_minimum"], el / steps) / peak, 4),
-            "blocks": {"h_pass": list(blocks[0]), "e_pass": list(blocks[1])},
+            "launches": launches,
+            "step_single_pass_frac": round(gbs(ab["single_pass_launch"], el / steps) / peak, 4),
+            "blocks": {"h_pass": list(blocks[0]), "e_pass": list(blocks[1]), "single_pass": list(single)},
             "l2": "inputs larger than L2 (5.8 GB state)"}
 
 
@@ -748,6 +774,9 @@ def main():
     ap.add_argument("--tune", default="",
                     help="fixed launch shapes 'v,bx,by,bz:v,bx,by,bz' (H launch : E launch) "
                          "instead of the autotuner; for profiling a chosen variant")
+    ap.add_argument("--single-pass", default="",
+                    help="'bx,by,kz': force the single-pass step with that tile; 'off': force the "
+                         "two passes; default: the autotuner decides")
     ap.add_argument("--grid", type=int, default=320,
                     help="cube side of the workload (320: the paper-scale sample; smaller sides "
                          "only for profiling)")

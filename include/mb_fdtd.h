@@ -176,7 +176,9 @@ int mb_step(mb_ctx* ctx, int n);
  * CUDA events on the context's stream; synchronizes, then adds the summed
  * device time (ms) of each pass over the n steps to ms_out[0..3]: H pass,
  * fused E pass, point-probe DFT, face- and plane-probe DFTs (ms_out may be
- * NULL). */
+ * NULL).  With the single-pass step (mb_set_single_pass) ms_out[0] is the
+ * single-pass launches (and ms_out[0..1] the two passes of an odd n's last
+ * step). */
 int mb_step_timed(mb_ctx* ctx, int n, double* ms_out);
 
 /* Wait for the context's queued work. */
@@ -227,15 +229,31 @@ int mb_autotune(mb_ctx* ctx);
 
 /* Launch shape of the H pass and of the E pass, as {variant, bx, by, bz}:
  * variant 0 = one thread per cell in (bx, by, bz) blocks; 1 = 2-D (bx, by)
- * blocks whose threads each walk bz planes along z; 2 (E pass only, n_x a
- * multiple of 16) = the same walk with the planes staged in shared memory
- * by bulk tensor copies (TMA), tiles 32x4, 32x8, 64x4, 64x8, 128x2, 128x4;
+ * blocks whose threads each walk bz planes along z; 2 (n_x a multiple of
+ * 16) = the same walk with the planes staged in shared memory by bulk
+ * tensor copies (TMA), tiles 32x4, 32x8, 64x4, 64x8, 128x2, 128x4;
  * 3 (n_x a multiple of 4) = the walk over quads of 4 x-cells with 16-byte
  * accesses, bx counting quads.  Every variant gives the same bits.  Read
  * the current choice or set one (bx a multiple of 32, at most 512 threads,
  * 256 for variant 3). */
 int mb_get_tuning(mb_ctx* ctx, int tune_h[4], int tune_e[4]);
 int mb_set_tuning(mb_ctx* ctx, const int tune_h[4], const int tune_e[4]);
+
+/* Single-pass step: the H half-step, the gain cells' Lorentz / Langevin
+ * update and the E / population update of one time step (the step of the
+ * "Simulations" paragraph) in one launch.  It reads the context's E, H and
+ * CPML memories and writes a second copy of them (allocated on first use:
+ * 24 bytes per cell plus the CPML memories); the next step writes back, so
+ * mb_step runs such steps in pairs and the state is in the context's own
+ * arrays after every call (an odd last step runs the two passes).  P, J and
+ * the populations are updated in place.  Fields, probes and energy equal
+ * the two-pass step's bit for bit (the face-flux sums agree to the FP32
+ * rounding of their partial sums).  tune = {on (0 or 1), bx, by, kz}: tiles of bx x by columns
+ * (32x4, 32x8, 64x4 or 64x8) walking kz planes; needs n_x a multiple of 16.
+ * mb_autotune selects it when it is the faster.  Errors: MB_ERR_ARG (bad
+ * tile or grid), MB_ERR_OOM (second copy). */
+int mb_get_single_pass(mb_ctx* ctx, int tune[4]);
+int mb_set_single_pass(mb_ctx* ctx, const int tune[4]);
 
 /* Kernel launches queued per step by mb_step, and in total so far. */
 int mb_launch_stats(mb_ctx* ctx, int* per_step, int64_t* total);

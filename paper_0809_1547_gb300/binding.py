@@ -85,6 +85,8 @@ _SIGS = [
     ("mb_autotune", C.c_int, [_P]),
     ("mb_get_tuning", C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     ("mb_set_tuning", C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    ("mb_get_single_pass", C.c_int, [_P, C.POINTER(C.c_int)]),
+    ("mb_set_single_pass", C.c_int, [_P, C.POINTER(C.c_int)]),
     ("mb_launch_stats", C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int64)]),
     ("mb_device_bytes", C.c_int, [_P, C.POINTER(C.c_size_t)]),
     ("mb_philox4x32_10", C.c_int, [_P, _P, _P, C.c_int]),
@@ -315,6 +317,17 @@ def mb_get_tuning(h):
 
 def mb_set_tuning(h, tune_h, tune_e):
     _check(load_library().mb_set_tuning(h, (C.c_int * 4)(*tune_h), (C.c_int * 4)(*tune_e)), h)
+
+
+def mb_get_single_pass(h):
+    """(on, bx, by, kz) of the single-pass step."""
+    t = (C.c_int * 4)()
+    _check(load_library().mb_get_single_pass(h, t), h)
+    return tuple(t)
+
+
+def mb_set_single_pass(h, tune):
+    _check(load_library().mb_set_single_pass(h, (C.c_int * 4)(*tune)), h)
 
 
 def mb_launch_stats(h):
@@ -563,6 +576,14 @@ class MBSimulation:
 
     def set_tuning(self, tune_h, tune_e):
         mb_set_tuning(self._h, tune_h, tune_e)
+
+    def single_pass(self):
+        """(on, bx, by, kz) of the single-pass step."""
+        return mb_get_single_pass(self._h)
+
+    def set_single_pass(self, tune):
+        """tune = (on, bx, by, kz); on = 0 returns to the two passes."""
+        mb_set_single_pass(self._h, tune)
 
     def device_bytes(self):
         return mb_device_bytes(self._h)

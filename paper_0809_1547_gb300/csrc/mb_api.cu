@@ -259,23 +259,101 @@ int check_device_error(mb_ctx* c) {
     return MB_OK;
 }
 
-// The probes of one step, after its E pass: point DFTs, face DFTs, plane DFTs.
-void launch_probes(mb_ctx* c) {
+// The probes of one step, after its E pass: point DFTs, face DFTs, plane DFTs
+// of the fields in a (the context's arrays, or the single-pass step's second
+// copy after the first step of a pair).
+void launch_probes(mb_ctx* c, const mb::StepArgs& a) {
     mb::DevPointProbes pp{(int)c->probes.size(), c->probe_nfreq, c->d_probe_cell,
                           c->d_probe_omega, c->d_probe_acc};
-    mb::launch_point_dft(pp, c->args.f, c->d_ctr, c->dt, c->stream);
-    mb::launch_face_dft(c->face, c->args.f, c->args.g, c->d_ctr, c->dt, c->stream);
+    mb::launch_point_dft(pp, a.f, c->d_ctr, c->dt, c->stream);
+    mb::launch_face_dft(c->face, a.f, a.g, c->d_ctr, c->dt, c->stream);
     for (const mb::DevPlaneProbe& q : c->planes)
-        mb::launch_plane_dft(q, c->args.f, c->args.g, c->d_ctr, c->dt, c->stream);
+        mb::launch_plane_dft(q, a.f, a.g, c->d_ctr, c->dt, c->stream);
 }
 
-int capture_steps(mb_ctx* c, int steps, cudaGraphExec_t* out) {
+void launch_probes(mb_ctx* c) { launch_probes(c, c->args); }
+
+// ---- single-pass step: the second copy of E, H and the CPML memories
+
+// Step arguments over the second copy (P, J, populations, material, tables
+// and counters shared with the context's own arguments).
+mb::StepArgs second_args(const mb_ctx* c) {
+    mb::StepArgs b = c->args;
+    const int64_t N = c->ncell;
+    float* F = c->d_fields2;
+    b.f.ex = F + 0 * N; b.f.ey = F + 1 * N; b.f.ez = F + 2 * N;
+    b.f.hx = F + 3 * N; b.f.hy = F + 4 * N; b.f.hz = F + 5 * N;
+    b.pml.psx = c->d_psi2[0];
+    b.pml.psy = c->d_psi2[1];
+    b.pml.psz = c->d_psi2[2];
+    return b;
+}
+
+mb::DevPing ping_of(const mb::StepArgs& a) {
+    return mb::DevPing{a.f.ex, a.f.ey, a.f.ez, a.f.hx, a.f.hy, a.f.hz,
+                       mb::PsiOut{a.pml.psx, a.pml.psy, a.pml.psz}};
+}
+
+// Allocates the second copy on first use.
+int ensure_second_copy(mb_ctx* c) {
+    if (c->d_fields2) return MB_OK;
+    const size_t fb = sizeof(float) * 6 * (size_t)c->ncell;
+    cudaError_t e = cudaMalloc((void**)&c->d_fields2, fb);
+    for (int w = 0; w < 3 && e == cudaSuccess; ++w)
+        if (c->psi_elems[w]) e = cudaMalloc((void**)&c->d_psi2[w], sizeof(float) * c->psi_elems[w]);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(c->d_fields2);
+        for (int w = 0; w < 3; ++w) cudaFree(c->d_psi2[w]);
+        c->d_fields2 = nullptr;
+        c->d_psi2[0] = c->d_psi2[1] = c->d_psi2[2] = nullptr;
+        return fail(c, MB_ERR_OOM, "cudaMalloc of the single-pass step's second field copy failed");
+    }
+    c->dev_bytes += fb;
+    for (int w = 0; w < 3; ++w) c->dev_bytes += sizeof(float) * c->psi_elems[w];
+    return MB_OK;
+}
+
+// Tensor maps of the single-pass step for tile shape t over (first copy,
+// second copy), encoded once per shape; nullptr if unsupported.
+const std::pair<mb::TmaFusedMaps, mb::TmaFusedMaps>* fused_maps_for(mb_ctx* c, const mb::PassTune& t) {
+    if (!c->d_fields2) return nullptr;
+    const auto key = std::make_pair((int)t.block.x, (int)t.block.y);
+    auto it = c->fused_maps.find(key);
+    if (it != c->fused_maps.end()) return &it->second;
+    std::pair<mb::TmaFusedMaps, mb::TmaFusedMaps> m;
+    if (!mb::encode_fused(c->args, t.block.x, t.block.y, &m.first) ||
+        !mb::encode_fused(second_args(c), t.block.x, t.block.y, &m.second))
+        return nullptr;
+    return &(c->fused_maps[key] = m);
+}
+
+// Two single-pass steps (first copy -> second -> first), each followed by
+// the probes of the copy it wrote.
+void enqueue_fused_pair(mb_ctx* c, const mb::PassTune& t,
+                        const std::pair<mb::TmaFusedMaps, mb::TmaFusedMaps>& m) {
+    const mb::StepArgs b = second_args(c);
+    mb::launch_fused_step(c->args, ping_of(b), t, m.first, c->stream);
+    launch_probes(c, b);
+    mb::launch_fused_step(b, ping_of(c->args), t, m.second, c->stream);
+    launch_probes(c, c->args);
+}
+
+// Captures `steps` steps: two-pass steps, or with the single-pass step
+// (steps even) steps / 2 pairs.
+int capture_steps(mb_ctx* c, int steps, cudaGraphExec_t* out, bool fused = false) {
     cudaGraph_t graph = nullptr;
+    const std::pair<mb::TmaFusedMaps, mb::TmaFusedMaps>* fm = fused ? fused_maps_for(c, c->tune_f) : nullptr;
+    if (fused && !fm) return fail(c, MB_ERR_STATE, "single-pass step maps unavailable");
     MB_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-    for (int s = 0; s < steps; ++s) {
-        mb::launch_h_pass(c->args, c->tune_h, tma_for(c, c->tune_h), c->stream);
-        mb::launch_e_pass(c->args, c->tune_e, tma_for(c, c->tune_e), c->stream);
-        launch_probes(c);
+    if (fused) {
+        for (int s = 0; s < steps / 2; ++s) enqueue_fused_pair(c, c->tune_f, *fm);
+    } else {
+        for (int s = 0; s < steps; ++s) {
+            mb::launch_h_pass(c->args, c->tune_h, tma_for(c, c->tune_h), c->stream);
+            mb::launch_e_pass(c->args, c->tune_e, tma_for(c, c->tune_e), c->stream);
+            launch_probes(c);
+        }
     }
     cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
     if (e != cudaSuccess) return fail(c, MB_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
@@ -293,19 +371,26 @@ void sum_flux_slots(const double* slots, double fl[6]) {
     }
 }
 
-int launches_per_step(const mb_ctx* c) {
-    return 2 + (c->probes.empty() ? 0 : 1) + (c->face.on ? 1 : 0) + (int)c->planes.size();
+// Launches of one step: the field launches (2 for the two passes, 1 for the
+// single-pass step) plus the probes.
+int launches_per_step(const mb_ctx* c, bool fused = false) {
+    return (fused ? 1 : 2) + (c->probes.empty() ? 0 : 1) + (c->face.on ? 1 : 0) + (int)c->planes.size();
 }
 
 void drop_graphs(mb_ctx* c) {
     if (c->graph_chunk) cudaGraphExecDestroy(c->graph_chunk);
     if (c->graph_one) cudaGraphExecDestroy(c->graph_one);
-    c->graph_chunk = c->graph_one = nullptr;
+    if (c->graph_pair) cudaGraphExecDestroy(c->graph_pair);
+    c->graph_chunk = c->graph_one = c->graph_pair = nullptr;
     c->graph_dirty = true;
 }
 
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, int>, std::pair<mb::PassTune, mb::PassTune>> g_tune_cache;
+struct TuneSet {
+    mb::PassTune h, e, f;
+    bool fused;
+};
+std::map<std::tuple<int, int, int, int>, TuneSet> g_tune_cache;
 
 }  // namespace
 
@@ -503,8 +588,11 @@ int mb_create(mb_ctx** out, const int grid[3], double dx, double dt, const mb_pa
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find({c->nx, c->ny, c->nz, L});
         if (it != g_tune_cache.end()) {
-            c->tune_h = it->second.first;
-            c->tune_e = it->second.second;
+            c->tune_h = it->second.h;
+            c->tune_e = it->second.e;
+            c->tune_f = it->second.f;
+            c->use_fused = it->second.fused && ensure_second_copy(c) == MB_OK &&
+                           fused_maps_for(c, c->tune_f);
         }
     }
     *out = c;
@@ -518,7 +606,8 @@ int mb_destroy(mb_ctx* c) {
     void* bufs[] = {c->d_fields, c->d_mat, c->d_inv_eps, c->d_lut, c->d_psi[0], c->d_psi[1],
                     c->d_psi[2], c->d_coef, c->d_ctr, c->d_flux, c->d_partial, c->d_energy,
                     c->d_nonfinite, c->d_probe_cell, c->d_probe_omega, c->d_probe_acc,
-                    c->d_face_omega, c->d_face_acc, c->d_glist, c->d_src_wave, c->d_err};
+                    c->d_face_omega, c->d_face_acc, c->d_glist, c->d_src_wave, c->d_err,
+                    c->d_fields2, c->d_psi2[0], c->d_psi2[1], c->d_psi2[2]};
     for (void* b : bufs)
         if (b) cudaFree(b);
     for (const mb::DevPlaneProbe& q : c->planes) {
@@ -945,20 +1034,25 @@ int mb_step(mb_ctx* c, int n) {
     if (int rc = check_ctx(c)) return rc;
     if (n < 0) return fail(c, MB_ERR_ARG, "negative step count");
     if (n == 0) return MB_OK;
+    const bool fused = c->use_fused;
     if (c->graph_dirty) {
         drop_graphs(c);
-        int rc = capture_steps(c, c->graph_chunk_steps, &c->graph_chunk);
+        int rc = capture_steps(c, c->graph_chunk_steps, &c->graph_chunk, fused);
         if (rc) return rc;
         rc = capture_steps(c, 1, &c->graph_one);
         if (rc) return rc;
+        if (fused && (rc = capture_steps(c, 2, &c->graph_pair, true))) return rc;
         c->graph_dirty = false;
     }
     const int chunks = n / c->graph_chunk_steps, rem = n % c->graph_chunk_steps;
+    const int pairs = fused ? rem / 2 : 0, singles = rem - 2 * pairs;
     for (int q = 0; q < chunks; ++q) MB_CUDA(c, cudaGraphLaunch(c->graph_chunk, c->stream));
-    for (int q = 0; q < rem; ++q) MB_CUDA(c, cudaGraphLaunch(c->graph_one, c->stream));
+    for (int q = 0; q < pairs; ++q) MB_CUDA(c, cudaGraphLaunch(c->graph_pair, c->stream));
+    for (int q = 0; q < singles; ++q) MB_CUDA(c, cudaGraphLaunch(c->graph_one, c->stream));
     MB_CUDA(c, cudaGetLastError());
     c->n += n;
-    c->launches += (int64_t)n * launches_per_step(c);
+    c->launches += (int64_t)(n - singles) * launches_per_step(c, fused) +
+                   (int64_t)singles * launches_per_step(c);
     return MB_OK;
 }
 
@@ -978,18 +1072,33 @@ int mb_step_timed(mb_ctx* c, int n, double* ms_out) {
     }
     mb::DevPointProbes pp{(int)c->probes.size(), c->probe_nfreq, c->d_probe_cell,
                           c->d_probe_omega, c->d_probe_acc};
+    const std::pair<mb::TmaFusedMaps, mb::TmaFusedMaps>* fm =
+        c->use_fused ? fused_maps_for(c, c->tune_f) : nullptr;
+    const int fused_steps = fm ? n - n % 2 : 0;
+    const mb::StepArgs second = fm ? second_args(c) : c->args;
     for (int s = 0; s < n; ++s) {
         cudaEvent_t* e = &ev[(size_t)5 * s];
+        // a single-pass step writes the other copy: even steps of a pair the
+        // second one, odd steps the context's own arrays
+        const bool fused = s < fused_steps;
+        const mb::StepArgs& out = (fused && s % 2 == 0) ? second : c->args;
         cudaEventRecord(e[0], c->stream);
-        mb::launch_h_pass(c->args, c->tune_h, tma_for(c, c->tune_h), c->stream);
-        cudaEventRecord(e[1], c->stream);
-        mb::launch_e_pass(c->args, c->tune_e, tma_for(c, c->tune_e), c->stream);
+        if (fused) {
+            const mb::StepArgs& in = s % 2 == 0 ? c->args : second;
+            mb::launch_fused_step(in, ping_of(out), c->tune_f, s % 2 == 0 ? fm->first : fm->second,
+                                  c->stream);
+            cudaEventRecord(e[1], c->stream);
+        } else {
+            mb::launch_h_pass(c->args, c->tune_h, tma_for(c, c->tune_h), c->stream);
+            cudaEventRecord(e[1], c->stream);
+            mb::launch_e_pass(c->args, c->tune_e, tma_for(c, c->tune_e), c->stream);
+        }
         cudaEventRecord(e[2], c->stream);
-        mb::launch_point_dft(pp, c->args.f, c->d_ctr, c->dt, c->stream);
+        mb::launch_point_dft(pp, out.f, c->d_ctr, c->dt, c->stream);
         cudaEventRecord(e[3], c->stream);
-        mb::launch_face_dft(c->face, c->args.f, c->args.g, c->d_ctr, c->dt, c->stream);
+        mb::launch_face_dft(c->face, out.f, out.g, c->d_ctr, c->dt, c->stream);
         for (const mb::DevPlaneProbe& q : c->planes)
-            mb::launch_plane_dft(q, c->args.f, c->args.g, c->d_ctr, c->dt, c->stream);
+            mb::launch_plane_dft(q, out.f, out.g, c->d_ctr, c->dt, c->stream);
         cudaEventRecord(e[4], c->stream);
     }
     cudaError_t le = cudaGetLastError();
@@ -1009,7 +1118,8 @@ int mb_step_timed(mb_ctx* c, int n, double* ms_out) {
     if (ms_out)
         for (int q = 0; q < 4; ++q) ms_out[q] += acc[q];
     c->n += n;
-    c->launches += (int64_t)n * launches_per_step(c);
+    c->launches += (int64_t)fused_steps * launches_per_step(c, true) +
+                   (int64_t)(n - fused_steps) * launches_per_step(c);
     return check_device_error(c);
 }
 
@@ -1256,6 +1366,32 @@ int mb_autotune(mb_ctx* c) {
             if (pass == 1 && ms < best_e) { best_e = ms; be = t; }
         }
     }
+    // the single-pass step against the best pair of passes
+    mb::PassTune bf = c->tune_f;
+    float best_f = 1e30f;
+    if (mb::tma_e_supported(c->args) && ensure_second_copy(c) == MB_OK) {
+        const mb::StepArgs second = second_args(c);
+        for (dim3 b : {dim3(32, 4, 1), dim3(32, 8, 1), dim3(64, 4, 1), dim3(64, 8, 1)})
+            for (int kz : {16, 32, 64, 128}) {
+                const mb::PassTune t{mb::kVariantTma, b, kz};
+                if (kz > 2 * c->nz) continue;
+                const auto* fm = fused_maps_for(c, t);
+                if (!fm) continue;
+                mb::launch_fused_step(c->args, ping_of(second), t, fm->first, c->stream);
+                cudaEventRecord(e0, c->stream);
+                for (int r = 0; r < reps; ++r)
+                    mb::launch_fused_step(c->args, ping_of(second), t, fm->first, c->stream);
+                cudaEventRecord(e1, c->stream);
+                cudaEventSynchronize(e1);
+                float ms = 0;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best_f) { best_f = ms; bf = t; }
+            }
+    } else {
+        cudaGetLastError();
+        c->err.clear();
+    }
+    const bool fused = best_f < best_h + best_e;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     {
@@ -1270,10 +1406,44 @@ int mb_autotune(mb_ctx* c) {
     MB_CUDA(c, cudaGetLastError());
     c->tune_h = bh;
     c->tune_e = be;
+    c->tune_f = bf;
+    c->use_fused = fused;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune_cache[{c->nx, c->ny, c->nz, c->p.npml}] = {bh, be};
+        g_tune_cache[{c->nx, c->ny, c->nz, c->p.npml}] = TuneSet{bh, be, bf, fused};
     }
+    drop_graphs(c);
+    return MB_OK;
+}
+
+int mb_get_single_pass(mb_ctx* c, int tune[4]) {
+    if (int rc = check_ctx(c)) return rc;
+    if (!tune) return fail(c, MB_ERR_ARG, "null output");
+    tune[0] = c->use_fused ? 1 : 0;
+    tune[1] = c->tune_f.block.x;
+    tune[2] = c->tune_f.block.y;
+    tune[3] = c->tune_f.kz;
+    return MB_OK;
+}
+
+int mb_set_single_pass(mb_ctx* c, const int tune[4]) {
+    if (int rc = check_ctx(c)) return rc;
+    if (!tune) return fail(c, MB_ERR_ARG, "null input");
+    if (tune[0] != 0 && tune[0] != 1) return fail(c, MB_ERR_ARG, "tune[0] must be 0 or 1");
+    if (tune[0] == 0) {
+        c->use_fused = false;
+        drop_graphs(c);
+        return MB_OK;
+    }
+    if (!mb::fused_tile_supported(tune[1], tune[2]) || tune[3] < 1)
+        return fail(c, MB_ERR_ARG, "single-pass tiles are 32x4, 32x8, 64x4 or 64x8, kz >= 1");
+    if (!mb::tma_e_supported(c->args))
+        return fail(c, MB_ERR_ARG, "the single-pass step needs n_x % 16 == 0");
+    if (int rc = ensure_second_copy(c)) return rc;
+    const mb::PassTune t{mb::kVariantTma, dim3(tune[1], tune[2], 1), tune[3]};
+    if (!fused_maps_for(c, t)) return fail(c, MB_ERR_ARG, "tensor maps of the single-pass step cannot be encoded");
+    c->tune_f = t;
+    c->use_fused = true;
     drop_graphs(c);
     return MB_OK;
 }
@@ -1325,7 +1495,7 @@ int mb_set_tuning(mb_ctx* c, const int tune_h[4], const int tune_e[4]) {
 
 int mb_launch_stats(mb_ctx* c, int* per_step, int64_t* total) {
     if (int rc = check_ctx(c)) return rc;
-    if (per_step) *per_step = launches_per_step(c);
+    if (per_step) *per_step = launches_per_step(c, c->use_fused);
     if (total) *total = c->launches;
     return MB_OK;
 }

@@ -108,6 +108,25 @@ struct StepArgs {
     int* err;
 };
 
+// Where a cell update writes the CPML memories it advances: the step's own
+// arrays (in-place passes) or the other copy of them (single-pass step).
+struct PsiOut {
+    float *x, *y, *z;
+};
+
+__device__ __forceinline__ PsiOut psi_in_place(const StepArgs& a) {
+    return PsiOut{a.pml.psx, a.pml.psy, a.pml.psz};
+}
+
+// Destination of the single-pass step: E^{n+1}, H^{n+1/2} and the advanced
+// CPML memories go to a second copy of those arrays (the source copy is
+// read-only during the launch, so tiles can recompute their neighbours'
+// edge H values from it); P, J and the populations stay in place.
+struct DevPing {
+    float *ex, *ey, *ez, *hx, *hy, *hz;
+    PsiOut psi;
+};
+
 // ------------------------------------------------------------------ Philox
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
 // 32x32->64 multiplies mixing the counter with a key bumped by two Weyl
@@ -215,8 +234,11 @@ __device__ __forceinline__ HNb load_h_nbrs(const StepArgs& a, int i, int j, int 
 // ------------------------------------------------------------- H half-step
 // CPML of the H update at cell (i, j, k): advances psi_H and adds it to the
 // curl components.  d = (dEz_dy, dEy_dz, dEx_dz, dEz_dx, dEy_dx, dEx_dy).
+// Reads the memories of the step's own arrays (a.pml) and, with WR, writes
+// the advanced ones to o (the same arrays for an in-place step).
+template <bool WR>
 __device__ __forceinline__ void h_pml(const StepArgs& a, int i, int j, int k, const float d[6],
-                                      float& cx, float& cy, float& cz) {
+                                      float& cx, float& cy, float& cz, const PsiOut& o) {
     const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
     const int L = a.pml.L;
     const int L2 = 2 * L;
@@ -225,11 +247,13 @@ __device__ __forceinline__ void h_pml(const StepArgs& a, int i, int j, int k, co
         const uint32_t plane = (uint32_t)nz * ny * L2;
         const uint32_t q = ((uint32_t)k * ny + j) * L2 + s;
         const float b = __ldg(a.pml.bhx + i), cc = __ldg(a.pml.chx + i);
-        float* p = a.pml.psx;
+        const float* p = a.pml.psx;
         const float psi_yx = fmaf(b, p[q + 2 * plane], cc * d[3]);   // Hy: d/dx Ez
         const float psi_zx = fmaf(b, p[q + 3 * plane], cc * d[4]);   // Hz: d/dx Ey
-        p[q + 2 * plane] = psi_yx;
-        p[q + 3 * plane] = psi_zx;
+        if (WR) {
+            o.x[q + 2 * plane] = psi_yx;
+            o.x[q + 3 * plane] = psi_zx;
+        }
         cy -= psi_yx;
         cz += psi_zx;
     }
@@ -238,11 +262,13 @@ __device__ __forceinline__ void h_pml(const StepArgs& a, int i, int j, int k, co
         const uint32_t plane = (uint32_t)nz * L2 * nx;
         const uint32_t q = ((uint32_t)k * L2 + s) * nx + i;
         const float b = __ldg(a.pml.bhy + j), cc = __ldg(a.pml.chy + j);
-        float* p = a.pml.psy;
+        const float* p = a.pml.psy;
         const float psi_xy = fmaf(b, p[q + 2 * plane], cc * d[0]);   // Hx: d/dy Ez
         const float psi_zy = fmaf(b, p[q + 3 * plane], cc * d[5]);   // Hz: d/dy Ex
-        p[q + 2 * plane] = psi_xy;
-        p[q + 3 * plane] = psi_zy;
+        if (WR) {
+            o.y[q + 2 * plane] = psi_xy;
+            o.y[q + 3 * plane] = psi_zy;
+        }
         cx += psi_xy;
         cz -= psi_zy;
     }
@@ -251,11 +277,13 @@ __device__ __forceinline__ void h_pml(const StepArgs& a, int i, int j, int k, co
         const uint32_t plane = (uint32_t)L2 * ny * nx;
         const uint32_t q = (s * ny + j) * nx + i;
         const float b = __ldg(a.pml.bhz + k), cc = __ldg(a.pml.chz + k);
-        float* p = a.pml.psz;
+        const float* p = a.pml.psz;
         const float psi_xz = fmaf(b, p[q + 2 * plane], cc * d[1]);   // Hx: d/dz Ey
         const float psi_yz = fmaf(b, p[q + 3 * plane], cc * d[2]);   // Hy: d/dz Ex
-        p[q + 2 * plane] = psi_xz;
-        p[q + 3 * plane] = psi_yz;
+        if (WR) {
+            o.z[q + 2 * plane] = psi_xz;
+            o.z[q + 3 * plane] = psi_yz;
+        }
         cx -= psi_xz;
         cy += psi_yz;
     }
@@ -263,10 +291,10 @@ __device__ __forceinline__ void h_pml(const StepArgs& a, int i, int j, int k, co
 
 // H^{n+1/2} = H^{n-1/2} - S (curl_fwd E^n + psi_H) for cell (i, j, k), on
 // H values held in registers.  PML: the cell may lie in a CPML slab (false
-// only when it surely does not).
-template <bool PML>
-__device__ __forceinline__ void h_compute(const StepArgs& a, int i, int j, int k, const ENb& e,
-                                          float& hx, float& hy, float& hz) {
+// only when it surely does not).  The advanced CPML memories go to o (WR).
+template <bool PML, bool WR>
+__device__ __forceinline__ void h_compute_to(const StepArgs& a, int i, int j, int k, const ENb& e,
+                                             float& hx, float& hy, float& hz, const PsiOut& o) {
     float d[6];
     d[0] = e.ez_j1 - e.ez;   // dEz_dy
     d[1] = e.ey_k1 - e.ey;   // dEy_dz
@@ -277,11 +305,17 @@ __device__ __forceinline__ void h_compute(const StepArgs& a, int i, int j, int k
     float cx = d[0] - d[1];
     float cy = d[2] - d[3];
     float cz = d[4] - d[5];
-    if (PML && a.pml.L > 0) h_pml(a, i, j, k, d, cx, cy, cz);
+    if (PML && a.pml.L > 0) h_pml<WR>(a, i, j, k, d, cx, cy, cz, o);
     const float S = a.S;
     hx = fmaf(-S, cx, hx);
     hy = fmaf(-S, cy, hy);
     hz = fmaf(-S, cz, hz);
+}
+
+template <bool PML>
+__device__ __forceinline__ void h_compute(const StepArgs& a, int i, int j, int k, const ENb& e,
+                                          float& hx, float& hy, float& hz) {
+    h_compute_to<PML, true>(a, i, j, k, e, hx, hy, hz, psi_in_place(a));
 }
 
 // The same update read from and written to global memory at cell c.
@@ -350,7 +384,7 @@ __device__ __forceinline__ void population_step(const DevGain& G, float ex0, flo
 // CPML of the E update: advances psi_E and adds it to the curl components.
 // d = (dHz_dy, dHy_dz, dHx_dz, dHz_dx, dHy_dx, dHx_dy).
 __device__ __forceinline__ void e_pml(const StepArgs& a, int i, int j, int k, const float d[6],
-                                      float& cx, float& cy, float& cz) {
+                                      float& cx, float& cy, float& cz, const PsiOut& o) {
     const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
     const int L = a.pml.L;
     const int L2 = 2 * L;
@@ -359,11 +393,11 @@ __device__ __forceinline__ void e_pml(const StepArgs& a, int i, int j, int k, co
         const uint32_t plane = (uint32_t)nz * ny * L2;
         const uint32_t q = ((uint32_t)k * ny + j) * L2 + s;
         const float b = __ldg(a.pml.bex + i), cc = __ldg(a.pml.cex + i);
-        float* p = a.pml.psx;
+        const float* p = a.pml.psx;
         const float psi_yx = fmaf(b, p[q], cc * d[3]);            // Ey: d/dx Hz
         const float psi_zx = fmaf(b, p[q + plane], cc * d[4]);    // Ez: d/dx Hy
-        p[q] = psi_yx;
-        p[q + plane] = psi_zx;
+        o.x[q] = psi_yx;
+        o.x[q + plane] = psi_zx;
         cy -= psi_yx;
         cz += psi_zx;
     }
@@ -372,11 +406,11 @@ __device__ __forceinline__ void e_pml(const StepArgs& a, int i, int j, int k, co
         const uint32_t plane = (uint32_t)nz * L2 * nx;
         const uint32_t q = ((uint32_t)k * L2 + s) * nx + i;
         const float b = __ldg(a.pml.bey + j), cc = __ldg(a.pml.cey + j);
-        float* p = a.pml.psy;
+        const float* p = a.pml.psy;
         const float psi_xy = fmaf(b, p[q], cc * d[0]);            // Ex: d/dy Hz
         const float psi_zy = fmaf(b, p[q + plane], cc * d[5]);    // Ez: d/dy Hx
-        p[q] = psi_xy;
-        p[q + plane] = psi_zy;
+        o.y[q] = psi_xy;
+        o.y[q + plane] = psi_zy;
         cx += psi_xy;
         cz -= psi_zy;
     }
@@ -385,11 +419,11 @@ __device__ __forceinline__ void e_pml(const StepArgs& a, int i, int j, int k, co
         const uint32_t plane = (uint32_t)L2 * ny * nx;
         const uint32_t q = (s * ny + j) * nx + i;
         const float b = __ldg(a.pml.bez + k), cc = __ldg(a.pml.cez + k);
-        float* p = a.pml.psz;
+        const float* p = a.pml.psz;
         const float psi_xz = fmaf(b, p[q], cc * d[1]);            // Ex: d/dz Hy
         const float psi_yz = fmaf(b, p[q + plane], cc * d[2]);    // Ey: d/dz Hx
-        p[q] = psi_xz;
-        p[q + plane] = psi_yz;
+        o.z[q] = psi_xz;
+        o.z[q + plane] = psi_yz;
         cx -= psi_xz;
         cy += psi_yz;
     }
@@ -401,7 +435,7 @@ template <bool PML>
 __device__ __forceinline__ void e_field_step(const StepArgs& a, int i, int j, int k, uint32_t c,
                                              const HNb& h, float ie, float ex0, float ey0,
                                              float ez0, float sx, float sy, float sz, long long n,
-                                             float& ex1, float& ey1, float& ez1) {
+                                             float& ex1, float& ey1, float& ez1, const PsiOut& o) {
     float d[6];
     d[0] = h.hz - h.hz_j;   // dHz_dy
     d[1] = h.hy - h.hy_k;   // dHy_dz
@@ -412,7 +446,7 @@ __device__ __forceinline__ void e_field_step(const StepArgs& a, int i, int j, in
     float cx = d[0] - d[1];
     float cy = d[2] - d[3];
     float cz = d[4] - d[5];
-    if (PML && a.pml.L > 0) e_pml(a, i, j, k, d, cx, cy, cz);
+    if (PML && a.pml.L > 0) e_pml(a, i, j, k, d, cx, cy, cz, o);
     if (a.src.on && c == (uint32_t)a.src.cell) {
         const float v = source_value(a.src, n);
         if (a.src.comp == 0) sx += v;
@@ -478,17 +512,41 @@ __device__ __forceinline__ void gain_cell_step(const StepArgs& a, uint32_t c, lo
 // m, E^n, and for gain cells J^{n+1/2} and n1..n3 at time n.
 // In registers: E^{n+1} into ex1..ez1 and, for gain cells, N^{n+1} into
 // n1..n3 (in place); face-flux terms into fl with FLUX.
+// With 1/eps_r of the cell given (ie); the advanced CPML memories go to o.
+template <bool FLUX, bool PML>
+__device__ __forceinline__ void e_compute_ie(const StepArgs& a, int i, int j, int k, uint32_t c,
+                                             const HNb& h, float ie, float ex0, float ey0,
+                                             float ez0, bool gain, float jx, float jy, float jz,
+                                             float& n1, float& n2, float& n3, long long n,
+                                             float fl[6], float& ex1, float& ey1, float& ez1,
+                                             const PsiOut& o) {
+    e_field_step<PML>(a, i, j, k, c, h, ie, ex0, ey0, ez0, jx, jy, jz, n, ex1, ey1, ez1, o);
+    if (gain) population_step(a.gain, ex0, ey0, ez0, ex1, ey1, ez1, jx, jy, jz, n1, n2, n3);
+    if (FLUX && a.flux.on) flux_terms(a.flux, i, j, k, h, ex0, ey0, ez0, ex1, ey1, ez1, fl);
+}
+
+// The advanced CPML memories go to o.
+template <bool FLUX, bool PML>
+__device__ __forceinline__ void e_compute_to(const StepArgs& a, int i, int j, int k, uint32_t c,
+                                             const HNb& h, uint8_t m, float ex0, float ey0,
+                                             float ez0, bool gain, float jx, float jy, float jz,
+                                             float& n1, float& n2, float& n3, long long n,
+                                             float fl[6], float& ex1, float& ey1, float& ez1,
+                                             const PsiOut& o) {
+    const DevFields& f = a.f;
+    const float ie = f.inv_eps ? __ldg(f.inv_eps + c) : __ldg(f.lut_inv_eps + (m & 0x7f));
+    e_compute_ie<FLUX, PML>(a, i, j, k, c, h, ie, ex0, ey0, ez0, gain, jx, jy, jz, n1, n2, n3, n,
+                            fl, ex1, ey1, ez1, o);
+}
+
 template <bool FLUX, bool PML>
 __device__ __forceinline__ void e_compute(const StepArgs& a, int i, int j, int k, uint32_t c,
                                           const HNb& h, uint8_t m, float ex0, float ey0, float ez0,
                                           bool gain, float jx, float jy, float jz, float& n1,
                                           float& n2, float& n3, long long n, float fl[6],
                                           float& ex1, float& ey1, float& ez1) {
-    const DevFields& f = a.f;
-    const float ie = f.inv_eps ? __ldg(f.inv_eps + c) : __ldg(f.lut_inv_eps + (m & 0x7f));
-    e_field_step<PML>(a, i, j, k, c, h, ie, ex0, ey0, ez0, jx, jy, jz, n, ex1, ey1, ez1);
-    if (gain) population_step(a.gain, ex0, ey0, ez0, ex1, ey1, ez1, jx, jy, jz, n1, n2, n3);
-    if (FLUX && a.flux.on) flux_terms(a.flux, i, j, k, h, ex0, ey0, ez0, ex1, ey1, ez1, fl);
+    e_compute_to<FLUX, PML>(a, i, j, k, c, h, m, ex0, ey0, ez0, gain, jx, jy, jz, n1, n2, n3, n,
+                            fl, ex1, ey1, ez1, psi_in_place(a));
 }
 
 template <bool FLUX, bool PML>

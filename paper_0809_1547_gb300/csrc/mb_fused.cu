@@ -1,0 +1,365 @@
+// Single-pass Maxwell–Bloch step: the H half-step, the Lorentz / Langevin
+// update of the gain cells and the E / population update of one time step in
+// one launch, so each cell's E and H cross HBM once per step (read one copy,
+// write the other) instead of twice.
+//
+// A block owns a BX x BY tile of (i, j) columns and walks planes k0 .. k1-1.
+// One thread streams, S - 1 planes ahead, each plane's E (with a one-cell
+// halo on every side), H^{n-1/2} (with its -x/-y halo) and material tile from
+// the source copy into an S-slot shared-memory ring (cp.async.bulk.tensor on
+// mbarriers).  Plane k then takes four steps:
+//   1. H^{n+1/2} of the tile's own cells (E of planes k and k+1), written to
+//      the destination copy and to a shared tile; threads of the first warps
+//      also compute H^{n+1/2} of the row j = y0-1 and the column i = x0-1,
+//      which the E update of the tile's edge cells needs (the neighbouring
+//      tiles compute the same values from the same inputs, bit for bit);
+//   2. for gain cells, J^{n+1/2} and P^{n+1} (E^n from the ring, P, J and the
+//      populations prefetched one plane ahead with cp.async), in place;
+//   3. after a block barrier, E^{n+1} from the shared H tile and the own H of
+//      plane k-1 (registers), the populations N^{n+1}, and in blocks that
+//      hold face cells of the flux box their outward Poynting terms (summed
+//      per warp and plane into shared partials, added to the FP64 face slots
+//      once per block);
+//   4. a barrier frees the ring slot for plane k + S.
+// The first plane of a block needs H^{n+1/2} of plane k0-1 at its own cells:
+// recomputed from the source copy (never written: the block below owns it).
+// Because no block writes what another reads, the launch needs no ordering
+// between blocks.  Every cell update is the helpers of the two-pass launches,
+// so the result equals theirs bit for bit.
+#include "mb_host.h"
+#include "mb_tiles.cuh"
+#include "mb_tma.cuh"
+
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+
+namespace mb {
+
+template <int BX, int BY>
+struct FusedLayout {
+    static constexpr int kEX = BX + 8, kEY = BY + 2;   // E box from (x0-4, y0-1)
+    static constexpr int kHX = BX + 4, kHY = BY + 1;   // H box from (x0-4, y0-1)
+    static constexpr int kEW = kEX * kEY, kHW = kHX * kHY, kMW = BX * BY;
+    static constexpr int kEBytes = (kEW * 4 + 127) / 128 * 128;
+    static constexpr int kHBytes = (kHW * 4 + 127) / 128 * 128;
+    static constexpr int kMBytes = (kMW + 127) / 128 * 128;
+    static constexpr int kStage = 3 * kEBytes + 3 * kHBytes + kMBytes;
+    static constexpr int kTxE = 3 * kEW * 4;                  // top stage: E only
+    static constexpr int kTx = kTxE + 3 * kHW * 4 + kMW;
+    // H^{n+1/2} of the tile with its -x/-y halo: [3][BY+1][BX+1]
+    static constexpr int kNX = BX + 1, kNW = (BX + 1) * (BY + 1);
+    static constexpr int kNBytes = (3 * kNW * 4 + 127) / 128 * 128;
+    // P, J, n1..n3 of gain cells, two planes (cp.async double buffer)
+    static constexpr int kGBytes = 2 * 9 * kMW * 4;
+    static constexpr int smem_bytes(int stages) {
+        return stages * kStage + kGBytes + kNBytes + 64 + 128;
+    }
+};
+
+template <int BX, int BY, int S>
+__global__ void __launch_bounds__(BX * BY) k_step_fused(StepArgs a, DevPing d,
+                                                        const __grid_constant__ TmaFusedMaps maps,
+                                                        int kz) {
+    using Lay = FusedLayout<BX, BY>;
+    constexpr int T = BX * BY;
+    static_assert(BX + BY <= T, "the halo row and column need BX + BY threads");
+    constexpr int NW = T / 32;
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ float wfl[6][NW];   // per-warp face-flux partials
+    unsigned char* smem = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    float* gbuf = reinterpret_cast<float*>(smem + S * Lay::kStage);
+    float* hn = reinterpret_cast<float*>(smem + S * Lay::kStage + Lay::kGBytes);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + S * Lay::kStage + Lay::kGBytes + Lay::kNBytes);
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + BX * ty;
+    const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
+    const int i = x0 + tx, j = y0 + ty;
+    const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
+    const uint32_t nxy = a.g.nxy;
+    const bool valid = i < nx && j < ny;
+    const int k0 = blockIdx.z * kz, k1 = min(nz, k0 + kz);
+    const int planes = k1 - k0, total = planes + 1;
+    const long long n = a.step_ctr[0];
+    const bool face = tile_on_face(a.flux, x0, x0 + BX, y0, y0 + BY, k0, k1);
+    // the tile with its halo row and column touches an x or y CPML slab
+    const bool pml_xy = tile_in_xy_slab(a, x0 - 1, BX + 1, y0 - 1, BY + 1);
+    const bool gain_on = a.gain.on;
+    const DevFields& f = a.f;
+
+    auto issue = [&](int s, int p) {
+        unsigned char* q = smem + s * Lay::kStage;
+        const int k = k0 + p;
+        mbar_arrive_expect_tx(&bar[s], p < planes ? Lay::kTx : Lay::kTxE);
+        tma_load_3d(q + 0 * Lay::kEBytes, &maps.ex, x0 - 4, y0 - 1, k, &bar[s]);
+        tma_load_3d(q + 1 * Lay::kEBytes, &maps.ey, x0 - 4, y0 - 1, k, &bar[s]);
+        tma_load_3d(q + 2 * Lay::kEBytes, &maps.ez, x0 - 4, y0 - 1, k, &bar[s]);
+        if (p < planes) {
+            unsigned char* h = q + 3 * Lay::kEBytes;
+            tma_load_3d(h + 0 * Lay::kHBytes, &maps.hx, x0 - 4, y0 - 1, k, &bar[s]);
+            tma_load_3d(h + 1 * Lay::kHBytes, &maps.hy, x0 - 4, y0 - 1, k, &bar[s]);
+            tma_load_3d(h + 2 * Lay::kHBytes, &maps.hz, x0 - 4, y0 - 1, k, &bar[s]);
+            tma_load_3d(h + 3 * Lay::kHBytes, &maps.mat, x0, y0, k, &bar[s]);
+        }
+    };
+    auto mat_of = [&](int s) -> uint8_t {
+        return (smem + s * Lay::kStage + 3 * Lay::kEBytes + 3 * Lay::kHBytes)[tid];
+    };
+    auto gslot = [&](int b, int q) -> float* { return gbuf + (b * 9 + q) * T + tid; };
+    auto prefetch_gain = [&](int b, uint32_t cc) {
+        cp_async_4(gslot(b, 0), f.px + cc);
+        cp_async_4(gslot(b, 1), f.py + cc);
+        cp_async_4(gslot(b, 2), f.pz + cc);
+        cp_async_4(gslot(b, 3), f.jx + cc);
+        cp_async_4(gslot(b, 4), f.jy + cc);
+        cp_async_4(gslot(b, 5), f.jz + cc);
+        cp_async_4(gslot(b, 6), f.n1 + cc);
+        cp_async_4(gslot(b, 7), f.n2 + cc);
+        cp_async_4(gslot(b, 8), f.n3 + cc);
+    };
+
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) mbar_init(&bar[s], 1);
+        fence_barrier_init();
+    }
+    if (tid < 6 * NW) wfl[tid / NW][tid % NW] = 0.0f;
+    __syncthreads();
+    if (tid == 0)
+        for (int s = 0; s < S && s < total; ++s) issue(s, s);
+
+    uint32_t c = valid ? (uint32_t)i + (uint32_t)nx * j + nxy * k0 : 0u;
+    // H^{n+1/2} of plane k0-1 at this cell (zero below the first plane)
+    float hx_km1 = 0.0f, hy_km1 = 0.0f;
+    if (valid && k0 > 0) {
+        const uint32_t cm = c - nxy;
+        const ENb e = load_e_nbrs(a, i, j, k0 - 1, cm);
+        float hx = __ldg(f.hx + cm), hy = __ldg(f.hy + cm), hz = __ldg(f.hz + cm);
+        const PsiOut none{nullptr, nullptr, nullptr};
+        if (pml_xy || plane_in_z_slab(a, k0 - 1)) h_compute_to<true, false>(a, i, j, k0 - 1, e, hx, hy, hz, none);
+        else h_compute_to<false, false>(a, i, j, k0 - 1, e, hx, hy, hz, none);
+        hx_km1 = hx;
+        hy_km1 = hy;
+    }
+
+    // Edge work: threads tid < BX take the cell (x0 + tid, y0 - 1) of the
+    // halo row, threads BX <= tid < BX + BY the cell (x0 - 1, y0 + tid - BX)
+    // of the halo column; cells outside the grid hold H = 0.
+    const bool row = tid < BX, col = !row && tid < BX + BY;
+    const int hi = row ? x0 + tid : x0 - 1;
+    const int hj = row ? y0 - 1 : y0 + (tid - BX);
+    const bool halo = (row || col) && hi >= 0 && hj >= 0 && hi < nx && hj < ny;
+    const int halo_e = row ? tid + 4 : (tid - BX + 1) * Lay::kEX + 3;
+    const int halo_h = row ? tid + 4 : (tid - BX + 1) * Lay::kHX + 3;
+    const int halo_n = row ? tid + 1 : (tid - BX + 1) * Lay::kNX;
+    const int own_e = (ty + 1) * Lay::kEX + tx + 4;
+    const int own_h = (ty + 1) * Lay::kHX + tx + 4;
+    const int own_n = (ty + 1) * Lay::kNX + tx + 1;
+    constexpr int EW = Lay::kEBytes / 4, HW = Lay::kHBytes / 4, NN = Lay::kNW;
+
+    bool fail = !mbar_wait_bounded(&bar[0], 0, kWaitLimit);
+    bool pg = valid && gain_on && !fail && (mat_of(0) & 0x80);
+    if (pg) prefetch_gain(0, c);
+    cp_async_commit();
+    for (int p = 0; p < planes; ++p) {
+        const int s = p % S, s1 = (p + 1) % S;
+        const int k = k0 + p;
+        cp_async_wait_all();   // this plane's gain values (own thread's copies)
+        fail |= !mbar_wait_bounded(&bar[s1], ((p + 1) / S) & 1, kWaitLimit);
+        bool ng = false;
+        if (p + 1 < planes) {
+            ng = valid && gain_on && !fail && (mat_of(s1) & 0x80);
+            if (ng) prefetch_gain((p + 1) & 1, c + nxy);
+        }
+        cp_async_commit();
+        const float* E0 = reinterpret_cast<const float*>(smem + s * Lay::kStage);
+        const float* E1 = reinterpret_cast<const float*>(smem + s1 * Lay::kStage);
+        const float* H0 = reinterpret_cast<const float*>(smem + s * Lay::kStage + 3 * Lay::kEBytes);
+        const bool pml = pml_xy || plane_in_z_slab(a, k);
+
+        // 1. H^{n+1/2}: own cell, then the halo row / column
+        float hx = 0.0f, hy = 0.0f, hz = 0.0f;
+        if (valid && !fail) {
+            ENb e;
+            e.ex = E0[own_e];
+            e.ey = E0[EW + own_e];
+            e.ez = E0[2 * EW + own_e];
+            e.ex_j1 = E0[own_e + Lay::kEX];
+            e.ez_j1 = E0[2 * EW + own_e + Lay::kEX];
+            e.ey_i1 = E0[EW + own_e + 1];
+            e.ez_i1 = E0[2 * EW + own_e + 1];
+            e.ex_k1 = E1[own_e];
+            e.ey_k1 = E1[EW + own_e];
+            hx = H0[own_h];
+            hy = H0[HW + own_h];
+            hz = H0[2 * HW + own_h];
+            if (pml) h_compute_to<true, true>(a, i, j, k, e, hx, hy, hz, d.psi);
+            else h_compute_to<false, true>(a, i, j, k, e, hx, hy, hz, d.psi);
+            d.hx[c] = hx;
+            d.hy[c] = hy;
+            d.hz[c] = hz;
+        }
+        hn[own_n] = hx;
+        hn[NN + own_n] = hy;
+        hn[2 * NN + own_n] = hz;
+        if (row || col) {
+            float qx = 0.0f, qy = 0.0f, qz = 0.0f;
+            if (halo && !fail) {
+                ENb e;
+                e.ex = E0[halo_e];
+                e.ey = E0[EW + halo_e];
+                e.ez = E0[2 * EW + halo_e];
+                e.ex_j1 = E0[halo_e + Lay::kEX];
+                e.ez_j1 = E0[2 * EW + halo_e + Lay::kEX];
+                e.ey_i1 = E0[EW + halo_e + 1];
+                e.ez_i1 = E0[2 * EW + halo_e + 1];
+                e.ex_k1 = E1[halo_e];
+                e.ey_k1 = E1[EW + halo_e];
+                qx = H0[halo_h];
+                qy = H0[HW + halo_h];
+                qz = H0[2 * HW + halo_h];
+                const PsiOut none{nullptr, nullptr, nullptr};
+                if (pml) h_compute_to<true, false>(a, hi, hj, k, e, qx, qy, qz, none);
+                else h_compute_to<false, false>(a, hi, hj, k, e, qx, qy, qz, none);
+            }
+            hn[halo_n] = qx;
+            hn[NN + halo_n] = qy;
+            hn[2 * NN + halo_n] = qz;
+        }
+
+        // 2. J^{n+1/2}, P^{n+1} of a gain cell (time-n state only)
+        const int b = p & 1;
+        float jx = 0.f, jy = 0.f, jz = 0.f, n1 = 0.f, n2 = 0.f, n3 = 0.f;
+        if (pg && !fail) {
+            float px = *gslot(b, 0), py = *gslot(b, 1), pz = *gslot(b, 2);
+            jx = *gslot(b, 3);
+            jy = *gslot(b, 4);
+            jz = *gslot(b, 5);
+            n1 = *gslot(b, 6);
+            n2 = *gslot(b, 7);
+            n3 = *gslot(b, 8);
+            lorentz_step(a.gain, c, n, E0[own_e], E0[EW + own_e], E0[2 * EW + own_e], n1, n2, jx,
+                         jy, jz, px, py, pz);
+            f.px[c] = px;
+            f.py[c] = py;
+            f.pz[c] = pz;
+            f.jx[c] = jx;
+            f.jy[c] = jy;
+            f.jz[c] = jz;
+        }
+        __syncthreads();   // the H tile is complete
+
+        // 3. E^{n+1}, N^{n+1}, face flux
+        float fl[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (valid && !fail) {
+            HNb h;
+            h.hx = hx;
+            h.hy = hy;
+            h.hz = hz;
+            h.hy_i = hn[NN + own_n - 1];
+            h.hz_i = hn[2 * NN + own_n - 1];
+            h.hx_j = hn[own_n - Lay::kNX];
+            h.hz_j = hn[2 * NN + own_n - Lay::kNX];
+            h.hx_k = hx_km1;
+            h.hy_k = hy_km1;
+            const uint8_t m = mat_of(s);
+            const float ex0 = E0[own_e], ey0 = E0[EW + own_e], ez0 = E0[2 * EW + own_e];
+            float ex1, ey1, ez1;
+            if (face)
+                e_compute_to<true, true>(a, i, j, k, c, h, m, ex0, ey0, ez0, pg, jx, jy, jz, n1, n2,
+                                         n3, n, fl, ex1, ey1, ez1, d.psi);
+            else if (pml)
+                e_compute_to<false, true>(a, i, j, k, c, h, m, ex0, ey0, ez0, pg, jx, jy, jz, n1, n2,
+                                          n3, n, fl, ex1, ey1, ez1, d.psi);
+            else
+                e_compute_to<false, false>(a, i, j, k, c, h, m, ex0, ey0, ez0, pg, jx, jy, jz, n1,
+                                           n2, n3, n, fl, ex1, ey1, ez1, d.psi);
+            d.ex[c] = ex1;
+            d.ey[c] = ey1;
+            d.ez[c] = ez1;
+            if (pg) {
+                f.n1[c] = n1;
+                f.n2[c] = n2;
+                f.n3[c] = n3;
+            }
+            hx_km1 = hx;
+            hy_km1 = hy;
+        }
+        if (face) {
+            // this plane's flux terms: warp sums, added to the warp's partials
+            const unsigned full = 0xffffffffu;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+                float v = fl[q];
+                if (__any_sync(full, v != 0.0f)) {
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(full, v, o);
+                    if ((tid & 31) == 0) wfl[q][tid >> 5] += v;
+                }
+            }
+        }
+        __syncthreads();   // ring slot s and the H tile are free again
+        if (tid == 0 && p + S < total) issue(s, p + S);
+        pg = ng;
+        c += nxy;
+    }
+    cp_async_wait_all();
+    if (fail) {
+        // A wait gave up: record it, then give the copies still in flight a
+        // bounded chance to land before the block's shared memory is released.
+        if (tid == 0) atomicOr(a.err, 1);
+        for (int s = 0; s < S && s < total; ++s) {
+            const int uses = (total - s + S - 1) / S;
+            mbar_wait_bounded(&bar[s], (uses - 1) & 1, kWaitLimit);
+        }
+    }
+    if (face && (tid & 31) == 0) {
+        const unsigned slot = warp_slot();
+#pragma unroll
+        for (int q = 0; q < 6; ++q)
+            if (wfl[q][tid >> 5] != 0.0f)
+                atomicAdd(a.flux.acc + q * kFluxSlots + (slot % kFluxSlots), (double)wfl[q][tid >> 5]);
+    }
+    finish_step(a);
+}
+
+template <int BX, int BY>
+static void launch_fused(const StepArgs& a, const DevPing& d, int kz, const TmaFusedMaps& maps,
+                         cudaStream_t s) {
+    const int smem = FusedLayout<BX, BY>::smem_bytes(kTmaStages);
+    static bool attr_set = false;   // per instantiation, once per process
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_step_fused<BX, BY, kTmaStages>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        attr_set = true;
+    }
+    dim3 grid((a.g.nx + BX - 1) / BX, (a.g.ny + BY - 1) / BY, (a.g.nz + kz - 1) / kz);
+    k_step_fused<BX, BY, kTmaStages><<<grid, dim3(BX, BY, 1), smem, s>>>(a, d, maps, kz);
+}
+
+bool fused_tile_supported(int bx, int by) {
+    return (bx == 32 || bx == 64) && (by == 4 || by == 8);
+}
+
+bool encode_fused(const StepArgs& a, int bx, int by, TmaFusedMaps* out) {
+    if (!tma_e_supported(a) || !fused_tile_supported(bx, by)) return false;
+    const DevFields& f = a.f;
+    const CUtensorMapDataType F32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    return encode_box(&out->ex, F32, f.ex, 4, a.g, bx + 8, by + 2) &&
+           encode_box(&out->ey, F32, f.ey, 4, a.g, bx + 8, by + 2) &&
+           encode_box(&out->ez, F32, f.ez, 4, a.g, bx + 8, by + 2) &&
+           encode_box(&out->hx, F32, f.hx, 4, a.g, bx + 4, by + 1) &&
+           encode_box(&out->hy, F32, f.hy, 4, a.g, bx + 4, by + 1) &&
+           encode_box(&out->hz, F32, f.hz, 4, a.g, bx + 4, by + 1) &&
+           encode_box(&out->mat, CU_TENSOR_MAP_DATA_TYPE_UINT8, f.mat, 1, a.g, bx, by);
+}
+
+void launch_fused_step(const StepArgs& a, const DevPing& d, const PassTune& t,
+                       const TmaFusedMaps& maps, cudaStream_t s) {
+    const int bx = t.block.x, by = t.block.y;
+    if (bx == 32 && by == 4) launch_fused<32, 4>(a, d, t.kz, maps, s);
+    else if (bx == 32 && by == 8) launch_fused<32, 8>(a, d, t.kz, maps, s);
+    else if (bx == 64 && by == 4) launch_fused<64, 4>(a, d, t.kz, maps, s);
+    else if (bx == 64 && by == 8) launch_fused<64, 8>(a, d, t.kz, maps, s);
+}
+
+}  // namespace mb

@@ -126,6 +126,24 @@ constexpr int kTmaStages = 3;
 bool tma_e_supported(const StepArgs& a);
 bool vec_supported(const StepArgs& a);
 bool encode_tma(const StepArgs& a, int bx, int by, TmaMaps* out);
+// 3-D tensor map over one (nx, ny, nz) array of esize-byte elements with a
+// (bw, bh, 1) box, zero fill beyond the array.
+bool encode_box(CUtensorMap* m, CUtensorMapDataType dt, const void* base, int esize,
+                const DevGrid& g, int bw, int bh);
+
+// Single-pass step (H half-step, Lorentz update, E / population update in
+// one launch) reading one copy of E / H / CPML memories and writing the
+// other.  Tensor maps of one tile shape (bx, by) over the source copy: E
+// with a one-cell halo on every side (boxes (bx+8) x (by+2) from
+// (x0-4, y0-1)), H with its -x/-y halo ((bx+4) x (by+1) from (x0-4, y0-1))
+// and the material byte (bx x by).
+struct TmaFusedMaps {
+    CUtensorMap ex, ey, ez, hx, hy, hz, mat;
+};
+bool fused_tile_supported(int bx, int by);
+bool encode_fused(const StepArgs& a, int bx, int by, TmaFusedMaps* out);
+void launch_fused_step(const StepArgs& a, const DevPing& d, const PassTune& t,
+                       const TmaFusedMaps& maps, cudaStream_t s);
 
 // Grid of the H + gain launch: nH H tiles (tile grid gx x gy x gz) and nG
 // gain blocks, each over q consecutive entries of the gain list.
@@ -283,6 +301,16 @@ struct mb_ctx {
     std::map<std::pair<int, int>, mb::TmaMaps> tma_maps;   // per TMA tile shape
     mb::PassTune tune_h{mb::kVariantZmarch, dim3(32, 8, 1), 16};
     mb::PassTune tune_e{mb::kVariantZmarch, dim3(32, 4, 1), 16};
+
+    // single-pass step: steps go in pairs (this copy -> second copy -> this
+    // copy), so the state is back in d_fields / d_psi after every call; an
+    // odd step runs the two passes in place
+    bool use_fused = false;
+    mb::PassTune tune_f{mb::kVariantTma, dim3(32, 8, 1), 32};
+    float* d_fields2 = nullptr;        // second copy of E, H (6 arrays)
+    float* d_psi2[3] = {nullptr, nullptr, nullptr};
+    std::map<std::pair<int, int>, std::pair<mb::TmaFusedMaps, mb::TmaFusedMaps>> fused_maps;
+    cudaGraphExec_t graph_pair = nullptr;
 
     // stepping
     int64_t n = 0;

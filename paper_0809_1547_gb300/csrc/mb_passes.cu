@@ -629,8 +629,8 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     return fn;
 }
 
-static bool encode_box(CUtensorMap* m, CUtensorMapDataType dt, const void* base, int esize,
-                       const DevGrid& g, int bw, int bh) {
+bool encode_box(CUtensorMap* m, CUtensorMapDataType dt, const void* base, int esize,
+                const DevGrid& g, int bw, int bh) {
     auto enc = tensor_map_encoder();
     if (!enc) return false;
     const cuuint64_t dims[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
