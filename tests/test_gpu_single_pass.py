@@ -1,0 +1,142 @@
+"""The single-pass step (H half-step, Lorentz update and E / population
+update in one launch, E / H / CPML memories ping-ponged between two copies)
+against the two-pass step, bit for bit, and against the FP64 oracle.
+
+Cases: tiles whose halo row / column cross CPML slabs, the grid's low
+walls and ragged y / z tails; chunks of kz planes that split the z range
+(the first plane recomputes the plane below); odd step counts (the last
+step runs the two passes); every probe kind; the dense 1/eps map.
+"""
+import numpy as np
+import pytest
+
+from oracle.mb_oracle import FIELD_NAMES
+from parity_util import DX, DT, params_kw, make_pair, assert_fields_match
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_0809_1547_gb300 import build
+    build.build()
+
+
+def _setup(grid, npml, seed, dense=False):
+    from paper_0809_1547_gb300 import inputs
+    eps, gain = inputs.random_small(grid, seed=seed, npml=npml, d_cells=5)
+    if dense:
+        rng = np.random.default_rng(seed)
+        eps = np.where(eps > 1.0, eps + rng.random(eps.shape).astype(np.float32) * 0.5, 1.0)
+        eps = eps.astype(np.float32)
+    _, g = make_pair(grid, eps, gain, 4e24, 1e13, 11 + seed, params_kw(npml=npml))
+    g.set_source((grid[0] // 2, grid[1] // 2, grid[2] // 2), 2, 532e-9, 1.0e-15, 0.4e-15, 1e9)
+    g.add_point_probe((grid[0] // 3, grid[1] // 2, grid[2] // 2), 16, 480e-9, 700e-9)
+    g.add_face_probes(2, 1, 8, 500e-9, 650e-9)
+    g.add_plane_probe(grid[2] // 2, 2, 4, 520e-9, 640e-9)
+    return g
+
+
+def _snapshot(g):
+    out = {name: g.field(name) for name in FIELD_NAMES}
+    out["point"] = g.probe_spectrum(0)[0]
+    out["faces"] = [g.face_spectrum(f)[0] for f in range(6)]
+    out["plane"] = g.plane_mode_map(0, 1)
+    out["energy"] = g.energy()
+    return out
+
+
+def _assert_same(ref, got, what):
+    for name in FIELD_NAMES:
+        a, b = ref[name], got[name]
+        if not np.array_equal(a, b):
+            where = tuple(np.argwhere(a != b)[0])
+            raise AssertionError(f"{what}: {name} differs at [k,j,i]={where}: {a[where]!r} vs {b[where]!r}")
+    np.testing.assert_array_equal(got["point"], ref["point"], err_msg=what)
+    for f in range(6):
+        np.testing.assert_array_equal(got["faces"][f], ref["faces"][f], err_msg=f"{what} face {f}")
+    np.testing.assert_array_equal(got["plane"], ref["plane"], err_msg=what)
+    # energy is a sum of identical fields; the face flux adds FP32 per-warp
+    # partials (grouped by the tile shape) into FP64 slots in launch order,
+    # so it is fixed to FP32 rounding only
+    assert got["energy"][0] == pytest.approx(ref["energy"][0], rel=1e-12)
+    np.testing.assert_allclose(got["energy"][1], ref["energy"][1], rtol=1e-6,
+                               atol=1e-6 * np.abs(ref["energy"][1]).max())
+
+
+@pytest.mark.parametrize("grid,npml", [((64, 20, 24), 4), ((96, 17, 13), 4), ((32, 40, 35), 6)])
+def test_single_pass_equals_two_passes_bitwise(grid, npml):
+    g = _setup(grid, npml, seed=sum(grid))
+    g.step(4)
+    blob = g.save_state()
+    g.set_tuning((1, 32, 4, 8), (1, 32, 4, 8))
+    g.set_single_pass((0, 32, 8, 32))
+    g.step(11)
+    ref = _snapshot(g)
+    tunes = [(1, 32, 8, 64), (1, 32, 4, 8), (1, 64, 8, 5), (1, 64, 4, 1), (1, 32, 8, 3)]
+    for tune in tunes:
+        g.load_state(blob)
+        g.set_single_pass(tune)
+        assert g.single_pass() == tune
+        g.step(11)                     # 5 pairs and one two-pass step
+        _assert_same(ref, _snapshot(g), f"single pass {tune}")
+        g.load_state(blob)
+        for _ in range(5):
+            g.step(2)                  # pairs only, one per call
+        g.step(1)
+        _assert_same(ref, _snapshot(g), f"single pass {tune}, pair by pair")
+    g.close()
+
+
+def test_single_pass_dense_eps_map_bitwise():
+    g = _setup((48, 24, 20), 4, seed=9, dense=True)
+    g.step(3)
+    blob = g.save_state()
+    g.set_single_pass((0, 32, 8, 32))
+    g.step(8)
+    ref = _snapshot(g)
+    g.load_state(blob)
+    g.set_single_pass((1, 32, 8, 6))
+    g.step(8)
+    _assert_same(ref, _snapshot(g), "dense eps")
+    g.close()
+
+
+def test_single_pass_workload_48_oracle_parity():
+    """48^3 workload, 500 steps with the single-pass step, against the oracle."""
+    from paper_0809_1547_gb300 import inputs
+    w = inputs.workload_small_48()
+    o, g = make_pair(w.grid, w.eps, w.gain, w.N_a, w.pump, w.seed, params_kw(npml=w.npml))
+    g.set_single_pass((1, 32, 8, 16))
+    pid = g.add_point_probe(w.extra["probe"], 64, 475e-9, 705e-9)
+    o.add_point_probe(w.extra["probe"], 64, 475e-9, 705e-9)
+    o.step(w.steps)
+    g.step(w.steps)
+    errs = assert_fields_match(o, g)
+    assert errs["Ex"] > 0
+    S_o, _ = o.probe_spectrum(pid)
+    S_g, _ = g.probe_spectrum(pid)
+    assert np.linalg.norm(S_g - S_o) <= 2e-5 * np.linalg.norm(S_o)
+    per_step, total = g.launch_stats()
+    assert per_step == 2                     # the step and the point probe
+    g.close()
+
+
+def test_single_pass_argument_errors():
+    from paper_0809_1547_gb300.binding import MBSimulation, mb_default_params, MBError, MB_ERR_ARG
+    g = MBSimulation((8, 8, 8), DX, DT, mb_default_params(npml=2))
+    with pytest.raises(MBError) as e:
+        g.set_single_pass((1, 32, 8, 8))        # n_x % 16 != 0
+    assert e.value.code == MB_ERR_ARG
+    g.close()
+    g = MBSimulation((32, 8, 8), DX, DT, mb_default_params(npml=2))
+    for bad in ((1, 128, 2, 8), (1, 32, 16, 8), (1, 32, 8, 0), (2, 32, 8, 8)):
+        with pytest.raises(MBError) as e:
+            g.set_single_pass(bad)
+        assert e.value.code == MB_ERR_ARG
+    assert g.single_pass()[0] == 0
+    g.set_single_pass((1, 32, 4, 4))
+    assert g.single_pass() == (1, 32, 4, 4)
+    g.set_single_pass((0, 32, 4, 4))
+    assert g.single_pass()[0] == 0
+    g.close()
