@@ -489,6 +489,8 @@ extern "C" int mb_adjoint_energy_zface(mb_ctx* c, int n_steps, int ckpt_every, i
     const size_t nxy = (size_t)c->nx * c->ny;
     const size_t slot = 9 * N + 2 * nxy;   // floats per stored step: E, J, n1..n3, Hx/Hy of one plane
     const size_t psi_total = c->psi_elems[0] + c->psi_elems[1] + c->psi_elems[2];
+    // the sweeps below step the context in place (state in its own arrays)
+    const bool was_single_pass = mb::hold_in_place(c);
 
     int rc = MB_OK;
     char* ckpt = nullptr;
@@ -719,5 +721,6 @@ done:
     void* bufs[] = {ckpt, store, adj, geps, acc, slot_n};
     for (void* p : bufs)
         if (p) cudaFree(p);
+    mb::restore_single_pass(c, was_single_pass);
     return rc;
 }

@@ -87,11 +87,28 @@ std::pair<int, int> interior(int n, int L) {
     return (n - 2 * L > 0) ? std::make_pair(L, n - L) : std::make_pair(0, n);
 }
 
+// E, H block (6 arrays) and CPML memories of copy p (0: the context's own
+// arrays, 1: the single-pass step's second copy).
+float* eh_of(const mb_ctx* c, int p) { return p ? c->d_fields2 : c->d_fields; }
+float* psi_of(const mb_ctx* c, int p, int w) { return p ? c->d_psi2[w] : c->d_psi[w]; }
+
 float* field_ptr(mb_ctx* c, int which) {
-    // layout: ex ey ez hx hy hz px py pz jx jy jz n1 n2 n3
+    // layout: ex ey ez hx hy hz (current copy), px py pz jx jy jz n1 n2 n3
     if (which < MB_EX || which > MB_N3 || which == MB_N0) return nullptr;
     const int slot = which < MB_N0 ? which : which - 1;
+    if (slot < 6) return eh_of(c, c->parity) + (int64_t)slot * c->ncell;
     return c->d_fields + (int64_t)slot * c->ncell;
+}
+
+// Points the step arguments' E, H and CPML memories at copy p.
+void point_args_at(mb::StepArgs& a, const mb_ctx* c, int p) {
+    const int64_t N = c->ncell;
+    float* F = eh_of(c, p);
+    a.f.ex = F + 0 * N; a.f.ey = F + 1 * N; a.f.ez = F + 2 * N;
+    a.f.hx = F + 3 * N; a.f.hy = F + 4 * N; a.f.hz = F + 5 * N;
+    a.pml.psx = psi_of(c, p, 0);
+    a.pml.psy = psi_of(c, p, 1);
+    a.pml.psz = psi_of(c, p, 2);
 }
 
 double field_scale(const mb_ctx* c, int which) {
@@ -107,8 +124,6 @@ void build_args(mb_ctx* c) {
     a.g = {c->nx, c->ny, c->nz, (uint32_t)c->nx * (uint32_t)c->ny, (uint32_t)c->ncell};
     float* F = c->d_fields;
     const int64_t N = c->ncell;
-    a.f.ex = F + 0 * N; a.f.ey = F + 1 * N; a.f.ez = F + 2 * N;
-    a.f.hx = F + 3 * N; a.f.hy = F + 4 * N; a.f.hz = F + 5 * N;
     a.f.px = F + 6 * N; a.f.py = F + 7 * N; a.f.pz = F + 8 * N;
     a.f.jx = F + 9 * N; a.f.jy = F + 10 * N; a.f.jz = F + 11 * N;
     a.f.n1 = F + 12 * N; a.f.n2 = F + 13 * N; a.f.n3 = F + 14 * N;
@@ -117,9 +132,7 @@ void build_args(mb_ctx* c) {
     a.f.lut_inv_eps = c->d_lut;
     const int L = c->p.npml;
     a.pml.L = L;
-    a.pml.psx = c->d_psi[0];
-    a.pml.psy = c->d_psi[1];
-    a.pml.psz = c->d_psi[2];
+    point_args_at(a, c, c->parity);
     const float* t = c->d_coef;
     const int n3[3] = {c->nx, c->ny, c->nz};
     const float** tabs[3][4] = {{&a.pml.bex, &a.pml.cex, &a.pml.bhx, &a.pml.chx},
@@ -222,9 +235,10 @@ struct StatePart {
 
 std::vector<StatePart> state_parts(mb_ctx* c) {
     std::vector<StatePart> v;
-    v.push_back({c->d_fields, sizeof(float) * 15 * (size_t)c->ncell});
+    v.push_back({eh_of(c, c->parity), sizeof(float) * 6 * (size_t)c->ncell});
+    v.push_back({c->d_fields + 6 * c->ncell, sizeof(float) * 9 * (size_t)c->ncell});
     for (int w = 0; w < 3; ++w)
-        if (c->psi_elems[w]) v.push_back({c->d_psi[w], sizeof(float) * c->psi_elems[w]});
+        if (c->psi_elems[w]) v.push_back({psi_of(c, c->parity, w), sizeof(float) * c->psi_elems[w]});
     v.push_back({c->d_ctr, sizeof(long long) * 2});
     v.push_back({c->d_flux, sizeof(double) * 6 * mb::kFluxSlots});
     if (!c->probes.empty())
@@ -236,10 +250,11 @@ std::vector<StatePart> state_parts(mb_ctx* c) {
     return v;
 }
 
-// Tensor maps for a TMA tuning (encoded once per tile shape), else nullptr.
+// Tensor maps for a TMA tuning over the current copy (encoded once per tile
+// shape and copy), else nullptr.
 const mb::TmaMaps* tma_for(mb_ctx* c, const mb::PassTune& t) {
     if (t.variant != mb::kVariantTma) return nullptr;
-    const auto key = std::make_pair((int)t.block.x, (int)t.block.y);
+    const auto key = std::make_tuple((int)t.block.x, (int)t.block.y, c->parity);
     auto it = c->tma_maps.find(key);
     if (it != c->tma_maps.end()) return &it->second;
     mb::TmaMaps m;
@@ -273,19 +288,13 @@ void launch_probes(mb_ctx* c, const mb::StepArgs& a) {
 
 void launch_probes(mb_ctx* c) { launch_probes(c, c->args); }
 
-// ---- single-pass step: the second copy of E, H and the CPML memories
+// ---- single-pass step: the two copies of E, H and the CPML memories
 
-// Step arguments over the second copy (P, J, populations, material, tables
-// and counters shared with the context's own arguments).
-mb::StepArgs second_args(const mb_ctx* c) {
+// Step arguments over copy p (P, J, populations, material, tables and
+// counters shared with the context's own arguments).
+mb::StepArgs view_of(const mb_ctx* c, int p) {
     mb::StepArgs b = c->args;
-    const int64_t N = c->ncell;
-    float* F = c->d_fields2;
-    b.f.ex = F + 0 * N; b.f.ey = F + 1 * N; b.f.ez = F + 2 * N;
-    b.f.hx = F + 3 * N; b.f.hy = F + 4 * N; b.f.hz = F + 5 * N;
-    b.pml.psx = c->d_psi2[0];
-    b.pml.psy = c->d_psi2[1];
-    b.pml.psz = c->d_psi2[2];
+    point_args_at(b, c, p);
     return b;
 }
 
@@ -314,48 +323,67 @@ int ensure_second_copy(mb_ctx* c) {
     return MB_OK;
 }
 
-// Tensor maps of the single-pass step for tile shape t over (first copy,
-// second copy), encoded once per shape; nullptr if unsupported.
+// Tensor maps of the single-pass step for tile shape t reading (copy 0,
+// copy 1), encoded once per shape; nullptr if unsupported.
 const std::pair<mb::TmaFusedMaps, mb::TmaFusedMaps>* fused_maps_for(mb_ctx* c, const mb::PassTune& t) {
     if (!c->d_fields2) return nullptr;
     const auto key = std::make_pair((int)t.block.x, (int)t.block.y);
     auto it = c->fused_maps.find(key);
     if (it != c->fused_maps.end()) return &it->second;
     std::pair<mb::TmaFusedMaps, mb::TmaFusedMaps> m;
-    if (!mb::encode_fused(c->args, t.block.x, t.block.y, &m.first) ||
-        !mb::encode_fused(second_args(c), t.block.x, t.block.y, &m.second))
+    if (!mb::encode_fused(view_of(c, 0), t.block.x, t.block.y, &m.first) ||
+        !mb::encode_fused(view_of(c, 1), t.block.x, t.block.y, &m.second))
         return nullptr;
     return &(c->fused_maps[key] = m);
 }
 
-// Two single-pass steps (first copy -> second -> first), each followed by
-// the probes of the copy it wrote.
-void enqueue_fused_pair(mb_ctx* c, const mb::PassTune& t,
-                        const std::pair<mb::TmaFusedMaps, mb::TmaFusedMaps>& m) {
-    const mb::StepArgs b = second_args(c);
-    mb::launch_fused_step(c->args, ping_of(b), t, m.first, c->stream);
-    launch_probes(c, b);
-    mb::launch_fused_step(b, ping_of(c->args), t, m.second, c->stream);
-    launch_probes(c, c->args);
+// One single-pass step from copy p to copy 1 - p, then the probes of the
+// copy it wrote.
+void enqueue_fused(mb_ctx* c, int p, const std::pair<mb::TmaFusedMaps, mb::TmaFusedMaps>& m) {
+    const mb::StepArgs in = view_of(c, p), out = view_of(c, 1 - p);
+    mb::launch_fused_step(in, ping_of(out), c->tune_f, p ? m.second : m.first, c->stream);
+    launch_probes(c, out);
 }
 
-// Captures `steps` steps: two-pass steps, or with the single-pass step
-// (steps even) steps / 2 pairs.
-int capture_steps(mb_ctx* c, int steps, cudaGraphExec_t* out, bool fused = false) {
+// Is the single-pass step usable now (second copy allocated, maps encoded)?
+// Falls back to the two passes when not.
+bool fused_ready(mb_ctx* c) {
+    if (!c->use_fused) return false;
+    if (ensure_second_copy(c) != MB_OK || !fused_maps_for(c, c->tune_f)) {
+        c->err.clear();
+        c->use_fused = false;
+        return false;
+    }
+    return true;
+}
+
+// Captures `steps` steps starting from copy p: single-pass steps (each
+// flipping the copy) or two-pass steps in place.
+int capture_steps(mb_ctx* c, int steps, int p, bool fused, cudaGraphExec_t* out) {
     cudaGraph_t graph = nullptr;
     const std::pair<mb::TmaFusedMaps, mb::TmaFusedMaps>* fm = fused ? fused_maps_for(c, c->tune_f) : nullptr;
     if (fused && !fm) return fail(c, MB_ERR_STATE, "single-pass step maps unavailable");
-    MB_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-    if (fused) {
-        for (int s = 0; s < steps / 2; ++s) enqueue_fused_pair(c, c->tune_f, *fm);
-    } else {
+    const int saved = c->parity;
+    c->parity = p;   // two-pass graphs run on copy p
+    point_args_at(c->args, c, p);
+    const mb::TmaMaps* mh = fused ? nullptr : tma_for(c, c->tune_h);
+    const mb::TmaMaps* me = fused ? nullptr : tma_for(c, c->tune_e);
+    cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
         for (int s = 0; s < steps; ++s) {
-            mb::launch_h_pass(c->args, c->tune_h, tma_for(c, c->tune_h), c->stream);
-            mb::launch_e_pass(c->args, c->tune_e, tma_for(c, c->tune_e), c->stream);
-            launch_probes(c);
+            if (fused) {
+                enqueue_fused(c, p, *fm);
+                p = 1 - p;
+            } else {
+                mb::launch_h_pass(c->args, c->tune_h, mh, c->stream);
+                mb::launch_e_pass(c->args, c->tune_e, me, c->stream);
+                launch_probes(c);
+            }
         }
+        e = cudaStreamEndCapture(c->stream, &graph);
     }
-    cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+    c->parity = saved;
+    point_args_at(c->args, c, saved);
     if (e != cudaSuccess) return fail(c, MB_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
     e = cudaGraphInstantiate(out, graph, 0);
     cudaGraphDestroy(graph);
@@ -378,11 +406,31 @@ int launches_per_step(const mb_ctx* c, bool fused = false) {
 }
 
 void drop_graphs(mb_ctx* c) {
-    if (c->graph_chunk) cudaGraphExecDestroy(c->graph_chunk);
-    if (c->graph_one) cudaGraphExecDestroy(c->graph_one);
-    if (c->graph_pair) cudaGraphExecDestroy(c->graph_pair);
-    c->graph_chunk = c->graph_one = c->graph_pair = nullptr;
-    c->graph_dirty = true;
+    for (int p = 0; p < 2; ++p) {
+        if (c->graph_chunk[p]) cudaGraphExecDestroy(c->graph_chunk[p]);
+        if (c->graph_one[p]) cudaGraphExecDestroy(c->graph_one[p]);
+        c->graph_chunk[p] = c->graph_one[p] = nullptr;
+    }
+}
+
+// The step graphs starting from copy p in the current mode (captured on
+// first use).
+int step_graphs(mb_ctx* c, int p, bool fused) {
+    if (c->graph_fused != fused) {
+        drop_graphs(c);
+        c->graph_fused = fused;
+    }
+    int rc = MB_OK;
+    if (!c->graph_chunk[p] && (rc = capture_steps(c, c->graph_chunk_steps, p, fused, &c->graph_chunk[p])))
+        return rc;
+    if (!c->graph_one[p] && (rc = capture_steps(c, 1, p, fused, &c->graph_one[p]))) return rc;
+    return MB_OK;
+}
+
+// Makes copy p the current one.
+void set_parity(mb_ctx* c, int p) {
+    c->parity = p;
+    point_args_at(c->args, c, p);
 }
 
 std::mutex g_tune_mu;
@@ -426,6 +474,23 @@ void mb::gain_pump_derivative(const mb_ctx* c, float dg[3], float dG[3][3], floa
 }
 
 const mb::TmaMaps* mb::tma_maps(mb_ctx* c, const mb::PassTune& t) { return tma_for(c, t); }
+
+bool mb::hold_in_place(mb_ctx* c) {
+    const bool on = c->use_fused;
+    if (c->parity) {
+        const size_t N = (size_t)c->ncell;
+        cudaMemcpyAsync(c->d_fields, c->d_fields2, sizeof(float) * 6 * N, cudaMemcpyDeviceToDevice, c->stream);
+        for (int w = 0; w < 3; ++w)
+            if (c->psi_elems[w])
+                cudaMemcpyAsync(c->d_psi[w], c->d_psi2[w], sizeof(float) * c->psi_elems[w],
+                                cudaMemcpyDeviceToDevice, c->stream);
+        set_parity(c, 0);
+    }
+    c->use_fused = false;
+    return on;
+}
+
+void mb::restore_single_pass(mb_ctx* c, bool on) { c->use_fused = on; }
 
 cudaError_t mb::enqueue_step(mb_ctx* c) {
     mb::launch_h_pass(c->args, c->tune_h, tma_for(c, c->tune_h), c->stream);
@@ -591,8 +656,7 @@ int mb_create(mb_ctx** out, const int grid[3], double dx, double dt, const mb_pa
             c->tune_h = it->second.h;
             c->tune_e = it->second.e;
             c->tune_f = it->second.f;
-            c->use_fused = it->second.fused && ensure_second_copy(c) == MB_OK &&
-                           fused_maps_for(c, c->tune_f);
+            c->use_fused = it->second.fused;   // second copy allocated at the first step
         }
     }
     *out = c;
@@ -1034,25 +1098,20 @@ int mb_step(mb_ctx* c, int n) {
     if (int rc = check_ctx(c)) return rc;
     if (n < 0) return fail(c, MB_ERR_ARG, "negative step count");
     if (n == 0) return MB_OK;
-    const bool fused = c->use_fused;
-    if (c->graph_dirty) {
-        drop_graphs(c);
-        int rc = capture_steps(c, c->graph_chunk_steps, &c->graph_chunk, fused);
-        if (rc) return rc;
-        rc = capture_steps(c, 1, &c->graph_one);
-        if (rc) return rc;
-        if (fused && (rc = capture_steps(c, 2, &c->graph_pair, true))) return rc;
-        c->graph_dirty = false;
-    }
+    const bool fused = fused_ready(c);
+    int p = c->parity;
     const int chunks = n / c->graph_chunk_steps, rem = n % c->graph_chunk_steps;
-    const int pairs = fused ? rem / 2 : 0, singles = rem - 2 * pairs;
-    for (int q = 0; q < chunks; ++q) MB_CUDA(c, cudaGraphLaunch(c->graph_chunk, c->stream));
-    for (int q = 0; q < pairs; ++q) MB_CUDA(c, cudaGraphLaunch(c->graph_pair, c->stream));
-    for (int q = 0; q < singles; ++q) MB_CUDA(c, cudaGraphLaunch(c->graph_one, c->stream));
+    if (int rc = step_graphs(c, p, fused)) return rc;
+    for (int q = 0; q < chunks; ++q) MB_CUDA(c, cudaGraphLaunch(c->graph_chunk[p], c->stream));
+    for (int q = 0; q < rem; ++q) {
+        if (int rc = step_graphs(c, p, fused)) return rc;
+        MB_CUDA(c, cudaGraphLaunch(c->graph_one[p], c->stream));
+        if (fused) p = 1 - p;
+    }
     MB_CUDA(c, cudaGetLastError());
+    set_parity(c, p);
     c->n += n;
-    c->launches += (int64_t)(n - singles) * launches_per_step(c, fused) +
-                   (int64_t)singles * launches_per_step(c);
+    c->launches += (int64_t)n * launches_per_step(c, fused);
     return MB_OK;
 }
 
@@ -1072,22 +1131,19 @@ int mb_step_timed(mb_ctx* c, int n, double* ms_out) {
     }
     mb::DevPointProbes pp{(int)c->probes.size(), c->probe_nfreq, c->d_probe_cell,
                           c->d_probe_omega, c->d_probe_acc};
-    const std::pair<mb::TmaFusedMaps, mb::TmaFusedMaps>* fm =
-        c->use_fused ? fused_maps_for(c, c->tune_f) : nullptr;
-    const int fused_steps = fm ? n - n % 2 : 0;
-    const mb::StepArgs second = fm ? second_args(c) : c->args;
+    const bool fused = fused_ready(c);
+    const std::pair<mb::TmaFusedMaps, mb::TmaFusedMaps>* fm = fused ? fused_maps_for(c, c->tune_f) : nullptr;
+    int p = c->parity;
     for (int s = 0; s < n; ++s) {
         cudaEvent_t* e = &ev[(size_t)5 * s];
-        // a single-pass step writes the other copy: even steps of a pair the
-        // second one, odd steps the context's own arrays
-        const bool fused = s < fused_steps;
-        const mb::StepArgs& out = (fused && s % 2 == 0) ? second : c->args;
+        // a single-pass step reads copy p and writes the other one
+        const mb::StepArgs in = view_of(c, p);
+        const mb::StepArgs out = fused ? view_of(c, 1 - p) : in;
         cudaEventRecord(e[0], c->stream);
         if (fused) {
-            const mb::StepArgs& in = s % 2 == 0 ? c->args : second;
-            mb::launch_fused_step(in, ping_of(out), c->tune_f, s % 2 == 0 ? fm->first : fm->second,
-                                  c->stream);
+            mb::launch_fused_step(in, ping_of(out), c->tune_f, p ? fm->second : fm->first, c->stream);
             cudaEventRecord(e[1], c->stream);
+            p = 1 - p;
         } else {
             mb::launch_h_pass(c->args, c->tune_h, tma_for(c, c->tune_h), c->stream);
             cudaEventRecord(e[1], c->stream);
@@ -1113,13 +1169,13 @@ int mb_step_timed(mb_ctx* c, int n, double* ms_out) {
         }
     }
     for (auto& x : ev) cudaEventDestroy(x);
+    set_parity(c, p);
     if (le != cudaSuccess) return fail(c, MB_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(le));
     if (se != cudaSuccess) return fail(c, MB_ERR_CUDA, std::string("sync: ") + cudaGetErrorString(se));
     if (ms_out)
         for (int q = 0; q < 4; ++q) ms_out[q] += acc[q];
     c->n += n;
-    c->launches += (int64_t)fused_steps * launches_per_step(c, true) +
-                   (int64_t)(n - fused_steps) * launches_per_step(c);
+    c->launches += (int64_t)n * launches_per_step(c, fused);
     return check_device_error(c);
 }
 
@@ -1370,17 +1426,19 @@ int mb_autotune(mb_ctx* c) {
     mb::PassTune bf = c->tune_f;
     float best_f = 1e30f;
     if (mb::tma_e_supported(c->args) && ensure_second_copy(c) == MB_OK) {
-        const mb::StepArgs second = second_args(c);
+        // current copy -> other copy, repeated (the other copy is scratch)
+        const mb::StepArgs other = view_of(c, 1 - c->parity);
         for (dim3 b : {dim3(32, 4, 1), dim3(32, 8, 1), dim3(64, 4, 1), dim3(64, 8, 1)})
-            for (int kz : {16, 32, 64, 128}) {
+            for (int kz : {8, 16, 32, 64}) {
                 const mb::PassTune t{mb::kVariantTma, b, kz};
                 if (kz > 2 * c->nz) continue;
                 const auto* fm = fused_maps_for(c, t);
                 if (!fm) continue;
-                mb::launch_fused_step(c->args, ping_of(second), t, fm->first, c->stream);
+                const mb::TmaFusedMaps& m = c->parity ? fm->second : fm->first;
+                mb::launch_fused_step(c->args, ping_of(other), t, m, c->stream);
                 cudaEventRecord(e0, c->stream);
                 for (int r = 0; r < reps; ++r)
-                    mb::launch_fused_step(c->args, ping_of(second), t, fm->first, c->stream);
+                    mb::launch_fused_step(c->args, ping_of(other), t, m, c->stream);
                 cudaEventRecord(e1, c->stream);
                 cudaEventSynchronize(e1);
                 float ms = 0;

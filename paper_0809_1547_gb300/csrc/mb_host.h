@@ -7,6 +7,7 @@
 
 #include <map>
 #include <string>
+#include <tuple>
 #include <utility>
 #include <vector>
 
@@ -213,6 +214,12 @@ const TmaMaps* tma_maps(mb_ctx* c, const PassTune& t);
 // passes with the context's tuning, then the probes); advances the count.
 cudaError_t enqueue_step(mb_ctx* c);
 
+// Brings the state back into the context's own copy (d_fields, d_psi) and
+// switches the single-pass step off (returning whether it was on), so that
+// every later step runs in place; restore_single_pass undoes the switch.
+bool hold_in_place(mb_ctx* c);
+void restore_single_pass(mb_ctx* c, bool on);
+
 // d/dW_p of the reduced population propagator (g, G, mk of DevGain).
 void gain_pump_derivative(const mb_ctx* c, float dg[3], float dG[3][3], float dmk[3]);
 
@@ -298,27 +305,29 @@ struct mb_ctx {
     mb::DevSource src{};
     float* d_src_wave = nullptr;       // tabulated source current
     int* d_err = nullptr;              // device error flag (bounded waits)
-    std::map<std::pair<int, int>, mb::TmaMaps> tma_maps;   // per TMA tile shape
+    std::map<std::tuple<int, int, int>, mb::TmaMaps> tma_maps;   // per TMA tile shape and copy
     mb::PassTune tune_h{mb::kVariantZmarch, dim3(32, 8, 1), 16};
     mb::PassTune tune_e{mb::kVariantZmarch, dim3(32, 4, 1), 16};
 
-    // single-pass step: steps go in pairs (this copy -> second copy -> this
-    // copy), so the state is back in d_fields / d_psi after every call; an
-    // odd step runs the two passes in place
+    // single-pass step: each step reads one copy of E, H and the CPML
+    // memories and writes the other; `parity` says which copy holds the
+    // current state (0: d_fields / d_psi, 1: d_fields2 / d_psi2) and args
+    // always points at it.  P, J and the populations have one copy.
     bool use_fused = false;
     mb::PassTune tune_f{mb::kVariantTma, dim3(32, 8, 1), 32};
     float* d_fields2 = nullptr;        // second copy of E, H (6 arrays)
     float* d_psi2[3] = {nullptr, nullptr, nullptr};
+    int parity = 0;
     std::map<std::pair<int, int>, std::pair<mb::TmaFusedMaps, mb::TmaFusedMaps>> fused_maps;
-    cudaGraphExec_t graph_pair = nullptr;
 
     // stepping
     int64_t n = 0;
     int64_t launches = 0;
-    cudaGraphExec_t graph_chunk = nullptr;
-    cudaGraphExec_t graph_one = nullptr;
-    int graph_chunk_steps = 16;
-    bool graph_dirty = true;
+    // per parity of the starting copy (the pointers baked into a graph)
+    cudaGraphExec_t graph_chunk[2] = {nullptr, nullptr};
+    cudaGraphExec_t graph_one[2] = {nullptr, nullptr};
+    bool graph_fused = false;          // mode the graphs were captured in
+    int graph_chunk_steps = 16;        // even: a chunk returns to its starting copy
 
     std::string err;
     size_t dev_bytes = 0;

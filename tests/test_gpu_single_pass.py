@@ -4,8 +4,9 @@ against the two-pass step, bit for bit, and against the FP64 oracle.
 
 Cases: tiles whose halo row / column cross CPML slabs, the grid's low
 walls and ragged y / z tails; chunks of kz planes that split the z range
-(the first plane recomputes the plane below); odd step counts (the last
-step runs the two passes); every probe kind; the dense 1/eps map.
+(the first plane recomputes the plane below); odd step counts (the state
+then sits in the second copy) with field access, save / load, mode switches
+and the adjoint from there; every probe kind; the dense 1/eps map.
 """
 import numpy as np
 import pytest
@@ -78,13 +79,16 @@ def test_single_pass_equals_two_passes_bitwise(grid, npml):
         g.load_state(blob)
         g.set_single_pass(tune)
         assert g.single_pass() == tune
-        g.step(11)                     # 5 pairs and one two-pass step
+        g.step(11)                     # ends in the second copy
         _assert_same(ref, _snapshot(g), f"single pass {tune}")
         g.load_state(blob)
-        for _ in range(5):
-            g.step(2)                  # pairs only, one per call
-        g.step(1)
-        _assert_same(ref, _snapshot(g), f"single pass {tune}, pair by pair")
+        for _ in range(11):
+            g.step(1)                  # one step per call, the copy flips each time
+        _assert_same(ref, _snapshot(g), f"single pass {tune}, step by step")
+        g.load_state(blob)
+        g.step_timed(5)                # direct launches
+        g.step(6)
+        _assert_same(ref, _snapshot(g), f"single pass {tune}, timed + graphs")
     g.close()
 
 
@@ -140,3 +144,45 @@ def test_single_pass_argument_errors():
     g.set_single_pass((0, 32, 4, 4))
     assert g.single_pass()[0] == 0
     g.close()
+
+
+def test_single_pass_state_in_second_copy():
+    """Odd step counts leave the state in the second copy: reads, writes,
+    snapshots, mode switches and the adjoint all see the current state."""
+    grid, npml = (48, 20, 18), 4
+    g = _setup(grid, npml, seed=21)
+    r = _setup(grid, npml, seed=21)
+    g.set_single_pass((1, 32, 4, 5))
+    r.set_single_pass((0, 32, 4, 5))
+    for sim in (g, r):
+        sim.step(3)
+    _assert_same(_snapshot(r), _snapshot(g), "after 3 steps")
+    blob = g.save_state()
+    v = g.field("Ey")
+    v[5:9, 6:10, 20:30] += 1e3
+    for sim in (g, r):
+        sim.set_field("Ey", v)
+        sim.step(5)
+    _assert_same(_snapshot(r), _snapshot(g), "after set_field + 5 steps")
+    for sim in (g, r):
+        sim.load_state(blob)
+        sim.step(1)
+    g.set_single_pass((0, 32, 4, 5))
+    for sim in (g, r):
+        sim.step(2)
+    _assert_same(_snapshot(r), _snapshot(g), "two passes from the second copy")
+    g.set_single_pass((1, 64, 4, 7))
+    for sim in (g, r):
+        sim.step(1)
+    res = [sim.adjoint_energy_zface(12, 4) for sim in (g, r)]
+    # same forward states; the FP64 sums of J and dJ/dW_p add in atomic order
+    assert res[0][0] == pytest.approx(res[1][0], rel=1e-12)
+    assert res[0][2] == pytest.approx(res[1][2], rel=1e-12)
+    ga, gb = res[0][1].cpu().numpy(), res[1][1].cpu().numpy()
+    np.testing.assert_allclose(ga, gb, rtol=1e-6, atol=1e-6 * np.abs(gb).max())
+    assert g.single_pass() == (1, 64, 4, 7)
+    for sim in (g, r):
+        sim.step(3)
+    _assert_same(_snapshot(r), _snapshot(g), "after the adjoint")
+    g.close()
+    r.close()
