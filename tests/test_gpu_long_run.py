@@ -1,0 +1,47 @@
+"""Long noise-driven run against the oracle: the statistics the paper reads
+off its runs (the emission spectrum's peak and width at the centre probe,
+the energy emitted through the faces of the interior box) after 2000 steps
+of the 48^3 workload, on the single-pass step.  Fields of a long chaotic
+run need not stay within 1e-5 of the FP64 oracle; the criterion for long
+runs is the peak within one DFT bin and the width and emitted energy within
+5 %."""
+import numpy as np
+import pytest
+
+from oracle import mb_analysis as O
+from parity_util import params_kw, make_pair, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_0809_1547_gb300 import build
+    build.build()
+
+
+def test_long_run_statistics_match_oracle():
+    from paper_0809_1547_gb300 import inputs
+    w = inputs.workload_small_48()
+    steps = 2000
+    o, g = make_pair(w.grid, w.eps, w.gain, w.N_a, w.pump, w.seed, params_kw(npml=w.npml))
+    g.set_single_pass((1, 32, 4, 8))
+    pid = g.add_point_probe(w.extra["probe"], 64, 475e-9, 705e-9)
+    o.add_point_probe(w.extra["probe"], 64, 475e-9, 705e-9)
+    o.step(steps)
+    g.step(steps)
+    S_o, lam = o.probe_spectrum(pid)
+    S_g, lam_g = g.probe_spectrum(pid)
+    np.testing.assert_allclose(lam_g, lam, rtol=1e-15)
+    om = O.omegas_of(lam)
+    assert abs(O.peak(S_g, om)[0] - O.peak(S_o, om)[0]) <= abs(om[1] - om[0]) * 1.0001
+    assert O.std_width(S_g, om) == pytest.approx(O.std_width(S_o, om), rel=0.05)
+    _, fl_g = g.energy()
+    emitted_o, emitted_g = float(np.sum(o.flux)), float(np.sum(fl_g))
+    assert emitted_o > 0
+    assert emitted_g == pytest.approx(emitted_o, rel=0.05)
+    # the populations moved (the run is pumped and noisy, not trivial)
+    assert np.abs(o.field("N3")).max() > 0
+    print(f"2000 steps: spectrum rel-L2 {rel_l2(S_g, S_o):.2e}, Ex rel-L2 "
+          f"{rel_l2(g.field('Ex'), o.field('Ex')):.2e}")
+    g.close()
