@@ -129,7 +129,8 @@ int mb_add_point_probe(mb_ctx* ctx, const int ijk[3], int n_freq,
 /* Face probes on the six faces of the interior box [npml, n - npml)^3: on
  * every stride-th point of each face, the tangential E (on the face plane,
  * at t_{n+1}) and H (half a cell outside, at t_{n+1/2}) are accumulated into
- * FP64 running DFTs every `every` steps.  Replaces earlier face probes. */
+ * FP64 running DFTs every `every` steps (1 <= n_freq <= 4096).  Replaces
+ * earlier face probes. */
 int mb_add_face_probes(mb_ctx* ctx, int stride, int every, int n_freq,
                        double lam_min, double lam_max);
 

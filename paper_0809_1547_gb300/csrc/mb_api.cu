@@ -892,8 +892,8 @@ int mb_add_point_probe(mb_ctx* c, const int ijk[3], int n_freq, double lam_min, 
 
 int mb_add_face_probes(mb_ctx* c, int stride, int every, int n_freq, double lam_min, double lam_max) {
     if (int rc = check_ctx(c)) return rc;
-    if (stride < 1 || every < 1 || n_freq < 1 || !(lam_min > 0) || !(lam_max > 0))
-        return fail(c, MB_ERR_ARG, "bad face-probe arguments");
+    if (stride < 1 || every < 1 || n_freq < 1 || n_freq > 4096 || !(lam_min > 0) || !(lam_max > 0))
+        return fail(c, MB_ERR_ARG, "bad face-probe arguments (1 <= n_freq <= 4096)");
     cudaStreamSynchronize(c->stream);
     if (c->d_face_acc) { cudaFree(c->d_face_acc); c->d_face_acc = nullptr; }
     if (c->d_face_omega) { cudaFree(c->d_face_omega); c->d_face_omega = nullptr; }
@@ -923,7 +923,7 @@ int mb_add_face_probes(mb_ctx* c, int stride, int every, int n_freq, double lam_
     F.stride = stride;
     F.every = every;
     F.nfreq = n_freq;
-    F.pts_per_block = 16;
+    F.pts_per_block = 32;
     c->face_points = off;
     c->face_lam.clear();
     std::vector<double> om;

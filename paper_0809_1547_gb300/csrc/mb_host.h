@@ -24,18 +24,19 @@ struct DevPointProbes {
     double2* acc;          // [count][3][nfreq]
 };
 
-// Running DFT of probe p (one block, threads over bins) with E_c^{n1} at
+// Running DFT of probe p (one block, threads over bins; with k_step > 0 the
+// block takes bins k_begin + tid, stepping by k_step) with E_c^{n1} at
 // t = n1 dt: acc[p][c][k] += E_c exp(i w_k t) (scaled; times dt E0 on read-out).
 __device__ __forceinline__ void point_dft_block(const DevPointProbes& pp, int p, const float* ex,
                                                 const float* ey, const float* ez, long long n1,
-                                                double dt) {
+                                                double dt, int k_begin = 0, int k_step = 0) {
     const double t = (double)n1 * dt;
     const int64_t cell = pp.cell[p];
     const float e[3] = {ex[cell], ey[cell], ez[cell]};
     const int K = pp.nfreq;
     const int T = blockDim.x * blockDim.y * blockDim.z;
     const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
-    for (int kk = tid; kk < K; kk += T) {
+    for (int kk = k_begin + tid; kk < K; kk += (k_step > 0 ? k_step : T)) {
         double s, co;
         sincos(pp.omega[p * K + kk] * t, &s, &co);
 #pragma unroll

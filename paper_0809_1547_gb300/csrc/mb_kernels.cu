@@ -16,19 +16,25 @@
 
 namespace mb {
 
-// One block per probe, threads over frequency bins:
+// Blocks (probe, group of 32 bins), a thread per bin (the FP64 sincos of
+// every bin spread over many SMs):
 // acc[p][c][k] += E_c(t_{n+1}) exp(i w_k t_{n+1})   (scaled; times dt E0 on read-out)
-__global__ void k_point_dft(DevPointProbes pp, const float* ex, const float* ey, const float* ez,
-                            const long long* step_ctr, double dt) {
-    point_dft_block(pp, blockIdx.x, ex, ey, ez, step_ctr[0], dt);   // counter = n + 1
+__global__ void __launch_bounds__(32) k_point_dft(DevPointProbes pp, const float* ex, const float* ey,
+                                                  const float* ez, const long long* step_ctr, double dt) {
+    point_dft_block(pp, blockIdx.x, ex, ey, ez, step_ctr[0], dt,   // counter = n + 1
+                    blockIdx.y * 32, gridDim.y * 32);
 }
 
-// Face DFT: block (chunk of points, face); thread per frequency bin, looping
-// over the chunk's points so each warp touches contiguous accumulators.
-__global__ void k_face_dft(DevFaceProbes fp, DevFields f, DevGrid g, const long long* step_ctr,
-                           double dt) {
+// Face DFT: block (chunk of points, face).  The block first forms the
+// phase factors exp(i w_k t) of every bin at the E and H sample times in
+// shared memory (one FP64 sincos per thread: FP64 is a slow pipe on this
+// GPU), then its threads run over (point, bin) pairs, bins fastest, so each
+// warp touches contiguous accumulators.
+__global__ void __launch_bounds__(256) k_face_dft(DevFaceProbes fp, DevFields f, DevGrid g,
+                                                  const long long* step_ctr, double dt) {
     const long long n1 = step_ctr[0];         // n + 1
     if (n1 % fp.every != 0) return;
+    extern __shared__ double2 ph[];           // [0, K): E times, [K, 2K): H times
     const int face = blockIdx.y;
     const int axis = face >> 1;
     const int np = fp.npts[face];
@@ -39,12 +45,17 @@ __global__ void k_face_dft(DevFaceProbes fp, DevFields f, DevGrid g, const long 
     const int K = fp.nfreq;
     const int na = fp.na[face];
     const double tE = (double)n1 * dt, tH = tE - 0.5 * dt;
-    for (int kk = threadIdx.x; kk < K; kk += blockDim.x) {
-        const double w = fp.omega[kk];
-        double sE, cE, sH, cH;
-        sincos(w * tE, &sE, &cE);
-        sincos(w * tH, &sH, &cH);
-        for (int p = p0; p < p1; ++p) {
+    for (int q = threadIdx.x; q < 2 * K; q += blockDim.x) {
+        double s_, c_;
+        sincos(fp.omega[q % K] * (q < K ? tE : tH), &s_, &c_);
+        ph[q] = make_double2(c_, s_);
+    }
+    __syncthreads();
+    const int work = K * (p1 - p0);
+    for (int q = threadIdx.x; q < work; q += blockDim.x) {
+        const int kk = q % K, p = p0 + q / K;
+        const double cE = ph[kk].x, sE = ph[kk].y, cH = ph[K + kk].x, sH = ph[K + kk].y;
+        {
             const int ia = p % na, ib = p / na;
             // transverse coordinates of point (ia, ib): (a, b) axes per face
             int i, j, k;
@@ -151,7 +162,7 @@ void launch_philox(const uint4* ctr, uint32_t k0, uint32_t k1, uint4* out, int n
 void launch_point_dft(const DevPointProbes& pp, const DevFields& f, const long long* ctr,
                       double dt, cudaStream_t s) {
     if (pp.count <= 0) return;
-    k_point_dft<<<pp.count, 128, 0, s>>>(pp, f.ex, f.ey, f.ez, ctr, dt);
+    k_point_dft<<<dim3(pp.count, (pp.nfreq + 31) / 32, 1), 32, 0, s>>>(pp, f.ex, f.ey, f.ez, ctr, dt);
 }
 
 void launch_face_dft(const DevFaceProbes& fp, const DevFields& f, const DevGrid& g,
@@ -161,8 +172,13 @@ void launch_face_dft(const DevFaceProbes& fp, const DevFields& f, const DevGrid&
     for (int q = 0; q < 6; ++q) maxpts = fp.npts[q] > maxpts ? fp.npts[q] : maxpts;
     if (maxpts == 0) return;
     dim3 grid((maxpts + fp.pts_per_block - 1) / fp.pts_per_block, 6);
-    const int threads = fp.nfreq < 128 ? ((fp.nfreq + 31) / 32) * 32 : 128;
-    k_face_dft<<<grid, threads, 0, s>>>(fp, f, g, ctr, dt);
+    const size_t smem = sizeof(double2) * 2 * (size_t)fp.nfreq;
+    static size_t attr_set = 48 * 1024;   // largest dynamic shared memory allowed so far
+    if (smem > attr_set) {
+        cudaFuncSetAttribute(k_face_dft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr_set = smem;
+    }
+    k_face_dft<<<grid, 256, smem, s>>>(fp, f, g, ctr, dt);
 }
 
 // Plane DFT: one thread per plane cell; the block forms the phase factors
