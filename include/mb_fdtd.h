@@ -204,9 +204,19 @@ int mb_face_spectrum(mb_ctx* ctx, int face, double* out_S, double* out_lam);
  * box).  Returns MB_ERR_NONFINITE if any field value is NaN or Inf. */
 int mb_energy(mb_ctx* ctx, double* out_U, double* out_flux6);
 
-/* Only the six time-integrated face energies of mb_energy (J): a 48-byte
- * device-to-host read, no reduction over the grid.  Synchronizes. */
+/* Only the six time-integrated face energies of mb_energy (J): summed on
+ * the device, a 48-byte device-to-host read, no reduction over the grid.
+ * Synchronizes. */
 int mb_flux(mb_ctx* ctx, double* out_flux6);
+
+/* The same six values, asynchronously: queued on the context's stream after
+ * the work already queued; host_out6 (6 doubles, caller-owned, pinned host
+ * memory for a truly asynchronous copy) holds them once the stream has
+ * passed this point (after mb_synchronize, or an event recorded on the
+ * context's stream after this call).  The buffer must stay valid until then.
+ * Device-side wait failures are reported by the next synchronizing call.
+ * Errors: MB_ERR_ARG (null output), MB_ERR_CUDA. */
+int mb_flux_async(mb_ctx* ctx, double* host_out6);
 
 /* Copy one field (MB_EX..MB_N3) to / from host memory (n cells, SI units).
  * N0 is derived (N_a minus the other three) and cannot be set. */

@@ -85,6 +85,7 @@ _SIGS = [
     ("mb_autotune", C.c_int, [_P]),
     ("mb_get_tuning", C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     ("mb_set_tuning", C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    ("mb_flux_async", C.c_int, [_P, _P]),
     ("mb_get_single_pass", C.c_int, [_P, C.POINTER(C.c_int)]),
     ("mb_set_single_pass", C.c_int, [_P, C.POINTER(C.c_int)]),
     ("mb_launch_stats", C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int64)]),
@@ -236,6 +237,12 @@ def mb_flux(h):
     fl = np.zeros(6)
     _check(load_library().mb_flux(h, _ptr(fl)), h)
     return fl
+
+
+def mb_flux_async(h, out_ptr: int):
+    """Queue the read of the six face energies into the 6-double host buffer
+    at out_ptr (pinned memory); valid once the stream has passed this call."""
+    _check(load_library().mb_flux_async(h, C.c_void_p(out_ptr)), h)
 
 
 def mb_synchronize(h):
@@ -528,6 +535,16 @@ class MBSimulation:
 
     def flux(self):
         return mb_flux(self._h)
+
+    def flux_async(self, out):
+        """Queue the read of the six face energies (J) into `out`, a pinned
+        torch CPU tensor of 6 float64 (complete once the simulation's stream
+        passes this point, e.g. after an event recorded on it)."""
+        import torch
+        if not (isinstance(out, torch.Tensor) and out.dtype == torch.float64 and out.numel() >= 6
+                and out.device.type == "cpu" and out.is_contiguous()):
+            raise ValueError("out must be a contiguous CPU float64 tensor of 6 values")
+        mb_flux_async(self._h, out.data_ptr())
 
     def synchronize(self):
         mb_synchronize(self._h)

@@ -613,6 +613,7 @@ int mb_create(mb_ctx** out, const int grid[3], double dx, double dt, const mb_pa
     if ((rc = alloc((void**)&c->d_coef, sizeof(float) * ncoef))) return bail(rc);
     if ((rc = alloc((void**)&c->d_ctr, sizeof(long long) * 2))) return bail(rc);
     if ((rc = alloc((void**)&c->d_flux, sizeof(double) * 6 * mb::kFluxSlots))) return bail(rc);
+    if ((rc = alloc((void**)&c->d_flux_out, sizeof(double) * 6))) return bail(rc);
     c->n_partial = 1024;
     if ((rc = alloc((void**)&c->d_partial, sizeof(double) * c->n_partial))) return bail(rc);
     if ((rc = alloc((void**)&c->d_energy, sizeof(double)))) return bail(rc);
@@ -671,7 +672,7 @@ int mb_destroy(mb_ctx* c) {
                     c->d_psi[2], c->d_coef, c->d_ctr, c->d_flux, c->d_partial, c->d_energy,
                     c->d_nonfinite, c->d_probe_cell, c->d_probe_omega, c->d_probe_acc,
                     c->d_face_omega, c->d_face_acc, c->d_glist, c->d_src_wave, c->d_err,
-                    c->d_fields2, c->d_psi2[0], c->d_psi2[1], c->d_psi2[2]};
+                    c->d_fields2, c->d_psi2[0], c->d_psi2[1], c->d_psi2[2], c->d_flux_out};
     for (void* b : bufs)
         if (b) cudaFree(b);
     for (const mb::DevPlaneProbe& q : c->planes) {
@@ -1179,16 +1180,29 @@ int mb_step_timed(mb_ctx* c, int n, double* ms_out) {
     return check_device_error(c);
 }
 
+// The six face energies (J) summed and scaled on the device into d_flux_out.
+void enqueue_flux_out(mb_ctx* c) {
+    const double f = c->dt * c->E0 * (c->E0 / c->eta0) * c->dx * c->dx;
+    mb::launch_flux_sum(c->d_flux, c->d_flux_out, f, c->stream);
+}
+
 int mb_flux(mb_ctx* c, double* out_flux6) {
     if (int rc = check_ctx(c)) return rc;
     if (!out_flux6) return fail(c, MB_ERR_ARG, "null output");
-    double slots[6 * mb::kFluxSlots], fl[6];
-    MB_CUDA(c, cudaMemcpyAsync(slots, c->d_flux, sizeof(slots), cudaMemcpyDeviceToHost, c->stream));
+    enqueue_flux_out(c);
+    MB_CUDA(c, cudaMemcpyAsync(out_flux6, c->d_flux_out, sizeof(double) * 6, cudaMemcpyDeviceToHost,
+                               c->stream));
     MB_CUDA(c, cudaStreamSynchronize(c->stream));
-    sum_flux_slots(slots, fl);
-    const double f = c->dt * c->E0 * (c->E0 / c->eta0) * c->dx * c->dx;
-    for (int q = 0; q < 6; ++q) out_flux6[q] = fl[q] * f;
     return check_device_error(c);
+}
+
+int mb_flux_async(mb_ctx* c, double* host_out6) {
+    if (int rc = check_ctx(c)) return rc;
+    if (!host_out6) return fail(c, MB_ERR_ARG, "null output");
+    enqueue_flux_out(c);
+    MB_CUDA(c, cudaMemcpyAsync(host_out6, c->d_flux_out, sizeof(double) * 6, cudaMemcpyDeviceToHost,
+                               c->stream));
+    return MB_OK;
 }
 
 int mb_synchronize(mb_ctx* c) {

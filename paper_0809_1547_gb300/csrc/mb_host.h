@@ -201,6 +201,8 @@ void launch_plane_dft(const DevPlaneProbe& pp, const DevFields& f, const DevGrid
 void launch_plane_energy(const DevFields& f, const DevGrid& g, int k, const float* lut_eps,
                          double* out, cudaStream_t s);
 void launch_philox(const uint4* ctr, uint32_t k0, uint32_t k1, uint4* out, int n, cudaStream_t s);
+// out[q] = scale * sum_t slots[q kFluxSlots + t] (slots in order), q < 6.
+void launch_flux_sum(const double* slots, double* out, double scale, cudaStream_t s);
 void launch_energy(const DevFields& f, int64_t ncell, const float* lut_eps, double* partial,
                    int nparts, int* nonfinite, double* out, cudaStream_t s);
 
@@ -269,7 +271,8 @@ struct mb_ctx {
     uint32_t glist_count = 0;
     size_t glist_capacity = 0;
     long long* d_ctr = nullptr;        // step counters
-    double* d_flux = nullptr;          // 6 accumulators
+    double* d_flux = nullptr;          // 6 faces x kFluxSlots accumulators
+    double* d_flux_out = nullptr;      // the 6 face energies in joules (read-back staging)
     double* d_partial = nullptr;       // energy partial sums
     double* d_energy = nullptr;
     int* d_nonfinite = nullptr;

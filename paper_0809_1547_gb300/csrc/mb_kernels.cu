@@ -236,6 +236,18 @@ void launch_plane_energy(const DevFields& f, const DevGrid& g, int k, const floa
     k_plane_energy<<<blocks, 256, 0, s>>>(f, g, k, lut_eps, out);
 }
 
+__global__ void k_flux_sum(const double* slots, double* out, double scale) {
+    const int q = threadIdx.x;
+    if (q >= 6) return;
+    double v = 0.0;
+    for (int t = 0; t < kFluxSlots; ++t) v += slots[q * kFluxSlots + t];
+    out[q] = v * scale;
+}
+
+void launch_flux_sum(const double* slots, double* out, double scale, cudaStream_t s) {
+    k_flux_sum<<<1, 32, 0, s>>>(slots, out, scale);
+}
+
 void launch_energy(const DevFields& f, int64_t ncell, const float* lut_eps, double* partial,
                    int nparts, int* nonfinite, double* out, cudaStream_t s) {
     k_energy_partial<<<nparts, 256, 0, s>>>(f, ncell, lut_eps, partial, nonfinite);

@@ -186,3 +186,21 @@ def test_single_pass_state_in_second_copy():
     _assert_same(_snapshot(r), _snapshot(g), "after the adjoint")
     g.close()
     r.close()
+
+
+def test_flux_async_matches_flux():
+    """The asynchronous read-back of the face energies equals the synchronous one."""
+    import torch
+    g = _setup((32, 20, 18), 4, seed=33)
+    g.set_single_pass((1, 32, 4, 4))
+    out = torch.zeros(6, dtype=torch.float64).pin_memory()
+    for _ in range(3):
+        g.step(5)
+        g.flux_async(out)
+        g.synchronize()
+        ref = g.flux()
+        np.testing.assert_array_equal(out.numpy(), ref)
+    assert np.abs(ref).max() > 0
+    with pytest.raises(ValueError):
+        g.flux_async(torch.zeros(6, dtype=torch.float32))
+    g.close()
