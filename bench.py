@@ -86,8 +86,12 @@ def algorithmic_bytes(w):
     e_launch = 37.0 + 16.0 * slab + 36.0 * g
     two_pass = 73.0 + 32.0 * slab + 72.0 * g
     single = 49.0 + 32.0 * slab + 72.0 * g
+    # the step's reference byte count: two passes with perfect neighbour
+    # reuse, all four populations stored, 64 B per slab axis
+    reference = 73.0 + 80.0 * g + 64.0 * slab
     return {"h_launch": h_launch, "e_launch": e_launch, "step_two_pass_minimum": two_pass,
-            "single_pass_launch": single, "gain_fraction": g, "slab_fraction_sum": slab}
+            "single_pass_launch": single, "step_reference": reference, "gain_fraction": g,
+            "slab_fraction_sum": slab}
 
 
 def traffic_from_profile(kernel: str, workload: str = "mb320_active"):
@@ -409,7 +413,13 @@ def bench_ours(args):
                      "launches": other,
                      "step": {"single_pass_bytes_per_cell": round(ab["single_pass_launch"], 2),
                               "achieved_gbs": round(ab["single_pass_launch"] * cells / (step_ms / 1e3) / 1e9, 1),
-                              "frac": round(ab["single_pass_launch"] * cells / (step_ms / 1e3) / 1e9 / peak, 4)},
+                              "frac": round(ab["single_pass_launch"] * cells / (step_ms / 1e3) / 1e9 / peak, 4),
+                              "reference_bytes_per_cell": round(ab["step_reference"], 2),
+                              "reference_gbs": round(ab["step_reference"] * cells / (step_ms / 1e3) / 1e9, 1),
+                              "reference_frac": round(ab["step_reference"] * cells / (step_ms / 1e3) / 1e9 / peak, 4),
+                              "reference_definition": "Mcell-updates/s x (73 + 80 g + 64 f) B/cell / peak: the "
+                                                      "two-pass step's bytes with perfect neighbour reuse "
+                                                      "(g gain fraction, f summed CPML slab fractions)"},
                      "pass_ms_per_step": [round(v / args.steps, 5) for v in pass_ms]},
         "e2e": {"value": round(e2e_value, 2), "unit": UNIT, "h2d_bytes_per_step": round(h2d, 1),
                 "d2h_bytes_per_step": round(d2h, 1)},
