@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <thread>
 
@@ -693,90 +694,103 @@ int mb_set_material(mb_ctx* c, const float* eps_map, const uint8_t* gain_mask, d
     const int64_t N = c->ncell;
     // Material ids by the bit pattern of eps_r: up to 128 distinct values
     // share a LUT, more switch to a dense 1/eps map.  Host threads over
-    // chunks of cells: (1) each collects its distinct values (a packing
-    // holds a few values in long runs: the last value is checked first, then
-    // a short table), merged in chunk order; (2) each maps its cells to ids
-    // and lists its gain cells, concatenated in chunk order (increasing).
+    // chunks of cells.  Pass A: each thread validates its cells, gives them
+    // ids in a table of its own (a packing holds a few values in long runs:
+    // the last value is checked first, then the short table), sets the gain
+    // bit and counts its gain cells.  The tables merge in chunk order (ids =
+    // order of first appearance).  Pass B: each thread maps its ids to the
+    // merged ones and writes its gain cells, in increasing order, into its
+    // segment of the list.
     const bool gain_on = N_a > 0.0;
     const int nthr = (int)std::max<int64_t>(1, std::min<int64_t>(
         {(int64_t)std::max(1u, std::thread::hardware_concurrency()), 16, N / (1 << 18) + 1}));
     std::vector<std::pair<int64_t, int64_t>> chunk(nthr);
     for (int t = 0; t < nthr; ++t) chunk[t] = {N * t / nthr, N * (t + 1) / nthr};
     std::vector<std::vector<uint32_t>> seen(nthr);
-    std::vector<char> bad(nthr, 0);
+    std::vector<char> bad(nthr, 0), over(nthr, 0);
+    std::vector<int64_t> ngain(nthr, 0);
+    std::unique_ptr<uint8_t[]> mat(new uint8_t[(size_t)N]);
     auto find_key = [](const std::vector<uint32_t>& keys, uint32_t bits) -> int {
         for (size_t t = 0; t < keys.size(); ++t)
             if (keys[t] == bits) return (int)t;
         return -1;
     };
-    {
+    auto run = [&](auto&& body) {
         std::vector<std::thread> pool;
-        for (int t = 0; t < nthr; ++t)
-            pool.emplace_back([&, t]() {
-                uint32_t last = 0;
-                bool have = false;
-                for (int64_t q = chunk[t].first; q < chunk[t].second; ++q) {
-                    const float v = eps_map[q];
-                    if (!(v >= 1.0f) || !std::isfinite(v)) {
-                        bad[t] = 1;
-                        return;
-                    }
-                    uint32_t bits;
-                    std::memcpy(&bits, &v, 4);
-                    if (have && bits == last) continue;
-                    last = bits;
-                    have = true;
-                    if (seen[t].size() <= 128 && find_key(seen[t], bits) < 0) seen[t].push_back(bits);
-                }
-            });
+        for (int t = 0; t < nthr; ++t) pool.emplace_back(body, t);
         for (auto& th : pool) th.join();
-    }
+    };
+    run([&](int t) {
+        std::vector<uint32_t>& keys = seen[t];
+        uint32_t last = 0;
+        int last_id = -1;
+        int64_t cnt = 0;
+        for (int64_t q = chunk[t].first; q < chunk[t].second; ++q) {
+            const float v = eps_map[q];
+            if (!(v >= 1.0f) || !std::isfinite(v)) {
+                bad[t] = 1;
+                return;
+            }
+            uint32_t bits;
+            std::memcpy(&bits, &v, 4);
+            if (last_id < 0 || bits != last) {
+                last = bits;
+                last_id = find_key(keys, bits);
+                if (last_id < 0) {
+                    if (keys.size() < 128) {
+                        last_id = (int)keys.size();
+                        keys.push_back(bits);
+                    } else {
+                        over[t] = 1;   // more than 128 values: dense map
+                        last_id = 0;
+                    }
+                }
+            }
+            const bool g = gain_on && gain_mask[q] != 0;
+            c->h_gain[q] = g ? 1 : 0;
+            mat[q] = (uint8_t)last_id | (g ? 0x80 : 0x00);
+            cnt += g;
+        }
+        ngain[t] = cnt;
+    });
     for (int t = 0; t < nthr; ++t)
         if (bad[t]) return fail(c, MB_ERR_MATERIALS, "eps_r must be finite and >= 1");
     std::vector<uint32_t> keys;
     bool dense = false;
-    for (int t = 0; t < nthr && !dense; ++t)
+    for (int t = 0; t < nthr && !dense; ++t) {
+        dense = over[t] != 0;
         for (uint32_t bits : seen[t])
-            if (find_key(keys, bits) < 0) {
+            if (!dense && find_key(keys, bits) < 0) {
                 if (keys.size() == 128) {
                     dense = true;
                     break;
                 }
                 keys.push_back(bits);
             }
+    }
     std::vector<float> lut_eps;
     for (uint32_t bits : keys) {
         float v;
         std::memcpy(&v, &bits, 4);
         lut_eps.push_back(v);
     }
-    std::vector<uint8_t> mat((size_t)N);
-    std::vector<std::vector<uint32_t>> gparts(nthr);
-    {
-        std::vector<std::thread> pool;
-        for (int t = 0; t < nthr; ++t)
-            pool.emplace_back([&, t]() {
-                uint32_t last = 0;
-                int last_id = -1;
-                for (int64_t q = chunk[t].first; q < chunk[t].second; ++q) {
-                    int id = 0;
-                    if (!dense) {
-                        uint32_t bits;
-                        std::memcpy(&bits, &eps_map[q], 4);
-                        if (last_id < 0 || bits != last) {
-                            last = bits;
-                            last_id = find_key(keys, bits);
-                        }
-                        id = last_id;
-                    }
-                    const bool g = gain_on && gain_mask[q] != 0;
-                    c->h_gain[q] = g ? 1 : 0;
-                    mat[q] = (uint8_t)id | (g ? 0x80 : 0x00);
-                    if (g) gparts[t].push_back((uint32_t)q);
-                }
-            });
-        for (auto& th : pool) th.join();
-    }
+    std::vector<int64_t> goff(nthr + 1, 0);
+    for (int t = 0; t < nthr; ++t) goff[t + 1] = goff[t] + ngain[t];
+    std::vector<uint32_t> glist((size_t)goff[nthr]);
+    run([&](int t) {
+        uint8_t remap[128];
+        bool identity = true;
+        for (size_t q = 0; q < seen[t].size(); ++q) {
+            remap[q] = dense ? 0 : (uint8_t)find_key(keys, seen[t][q]);
+            identity &= remap[q] == (uint8_t)q;
+        }
+        uint32_t* out = glist.data() + goff[t];
+        for (int64_t q = chunk[t].first; q < chunk[t].second; ++q) {
+            const uint8_t m = mat[q];
+            if (!identity) mat[q] = (uint8_t)(remap[m & 0x7f] | (m & 0x80));
+            if (m & 0x80) *out++ = (uint32_t)q;
+        }
+    });
     cudaStreamSynchronize(c->stream);
     std::vector<float> lut(256, 1.0f);
     c->h_lut_eps.assign(128, 1.0f);
@@ -785,7 +799,7 @@ int mb_set_material(mb_ctx* c, const float* eps_map, const uint8_t* gain_mask, d
         lut[128 + q] = lut_eps[q];
         c->h_lut_eps[q] = lut_eps[q];
     }
-    MB_CUDA(c, cudaMemcpy(c->d_mat, mat.data(), (size_t)N, cudaMemcpyHostToDevice));
+    MB_CUDA(c, cudaMemcpy(c->d_mat, mat.get(), (size_t)N, cudaMemcpyHostToDevice));
     MB_CUDA(c, cudaMemcpy(c->d_lut, lut.data(), sizeof(float) * 256, cudaMemcpyHostToDevice));
     if (dense) {
         if (!c->d_inv_eps) {
@@ -801,13 +815,6 @@ int mb_set_material(mb_ctx* c, const float* eps_map, const uint8_t* gain_mask, d
     c->N_a = N_a;
     c->W_p = pump;
     // gain cells in increasing order: the Lorentz update runs over this list
-    std::vector<uint32_t> glist;
-    {
-        size_t total = 0;
-        for (auto& g : gparts) total += g.size();
-        glist.reserve(total);
-        for (auto& g : gparts) glist.insert(glist.end(), g.begin(), g.end());
-    }
     if (glist.size() > c->glist_count || !c->d_glist) {
         if (c->d_glist) {
             cudaFree(c->d_glist);
