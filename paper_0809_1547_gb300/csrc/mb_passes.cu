@@ -615,7 +615,7 @@ bool tma_e_supported(const StepArgs& a) {
     return a.g.nx % 16 == 0;
 }
 
-// The driver's tensor-map encoder, found through the runtime (no libcuda link).
+// The CUDA driver API's tensor-map encoder, found through the runtime (no libcuda link).
 static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {
