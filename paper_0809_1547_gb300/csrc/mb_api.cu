@@ -278,16 +278,19 @@ int check_device_error(mb_ctx* c) {
 // The probes of one step, after its E pass: point DFTs, face DFTs, plane DFTs
 // of the fields in a (the context's arrays, or the single-pass step's second
 // copy after the first step of a pair).
-void launch_probes(mb_ctx* c, const mb::StepArgs& a) {
+// ctr: the counter holding the step index of the fields sampled (the main
+// counter, or the sample slot of a single-pass step's output copy).
+void launch_probes(mb_ctx* c, const mb::StepArgs& a, const long long* ctr, cudaStream_t s) {
     mb::DevPointProbes pp{(int)c->probes.size(), c->probe_nfreq, c->d_probe_cell,
                           c->d_probe_omega, c->d_probe_acc};
-    mb::launch_point_dft(pp, a.f, c->d_ctr, c->dt, c->stream);
-    mb::launch_face_dft(c->face, a.f, a.g, c->d_ctr, c->dt, c->stream);
-    for (const mb::DevPlaneProbe& q : c->planes)
-        mb::launch_plane_dft(q, a.f, a.g, c->d_ctr, c->dt, c->stream);
+    mb::launch_point_dft(pp, a.f, ctr, c->dt, s);
+    mb::launch_face_dft(c->face, a.f, a.g, ctr, c->dt, s);
+    for (const mb::DevPlaneProbe& q : c->planes) mb::launch_plane_dft(q, a.f, a.g, ctr, c->dt, s);
 }
 
-void launch_probes(mb_ctx* c) { launch_probes(c, c->args); }
+void launch_probes(mb_ctx* c) { launch_probes(c, c->args, c->d_ctr, c->stream); }
+
+bool has_probes(const mb_ctx* c) { return !c->probes.empty() || c->face.on || !c->planes.empty(); }
 
 // ---- single-pass step: the two copies of E, H and the CPML memories
 
@@ -299,9 +302,10 @@ mb::StepArgs view_of(const mb_ctx* c, int p) {
     return b;
 }
 
-mb::DevPing ping_of(const mb::StepArgs& a) {
+// Destination of a single-pass step writing copy q (viewed by a).
+mb::DevPing ping_of(const mb_ctx* c, const mb::StepArgs& a, int q) {
     return mb::DevPing{a.f.ex, a.f.ey, a.f.ez, a.f.hx, a.f.hy, a.f.hz,
-                       mb::PsiOut{a.pml.psx, a.pml.psy, a.pml.psz}};
+                       mb::PsiOut{a.pml.psx, a.pml.psy, a.pml.psz}, c->d_ctr + 2 + q};
 }
 
 // Allocates the second copy on first use.
@@ -338,12 +342,15 @@ const std::pair<mb::TmaFusedMaps, mb::TmaFusedMaps>* fused_maps_for(mb_ctx* c, c
     return &(c->fused_maps[key] = m);
 }
 
-// One single-pass step from copy p to copy 1 - p, then the probes of the
-// copy it wrote.
-void enqueue_fused(mb_ctx* c, int p, const std::pair<mb::TmaFusedMaps, mb::TmaFusedMaps>& m) {
-    const mb::StepArgs in = view_of(c, p), out = view_of(c, 1 - p);
-    mb::launch_fused_step(in, ping_of(out), c->tune_f, p ? m.second : m.first, c->stream);
-    launch_probes(c, out);
+// Events for a captured chunk of `steps` single-pass steps (created once).
+void ensure_events(mb_ctx* c, int steps) {
+    while ((int)c->fork_ev.size() < steps) {
+        cudaEvent_t a = nullptr, b = nullptr;
+        cudaEventCreateWithFlags(&a, cudaEventDisableTiming);
+        cudaEventCreateWithFlags(&b, cudaEventDisableTiming);
+        c->fork_ev.push_back(a);
+        c->join_ev.push_back(b);
+    }
 }
 
 // Is the single-pass step usable now (second copy allocated, maps encoded)?
@@ -369,11 +376,28 @@ int capture_steps(mb_ctx* c, int steps, int p, bool fused, cudaGraphExec_t* out)
     point_args_at(c->args, c, p);
     const mb::TmaMaps* mh = fused ? nullptr : tma_for(c, c->tune_h);
     const mb::TmaMaps* me = fused ? nullptr : tma_for(c, c->tune_e);
+    // Single-pass steps: the probes of step s read only the copy it wrote,
+    // which step s + 1 only reads, so they run on the second stream beside
+    // step s + 1; step s + 2 (which rewrites that copy) waits for them, and
+    // the chunk ends with the second stream joined.
+    const bool fork = fused && has_probes(c) && c->aux_stream;
+    if (fork) ensure_events(c, steps);
     cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         for (int s = 0; s < steps; ++s) {
             if (fused) {
-                enqueue_fused(c, p, *fm);
+                const mb::StepArgs in = view_of(c, p), out = view_of(c, 1 - p);
+                if (fork && s >= 2) cudaStreamWaitEvent(c->stream, c->join_ev[s - 2], 0);
+                mb::launch_fused_step(in, ping_of(c, out, 1 - p), c->tune_f, p ? fm->second : fm->first,
+                                      c->stream);
+                if (fork) {
+                    cudaEventRecord(c->fork_ev[s], c->stream);
+                    cudaStreamWaitEvent(c->aux_stream, c->fork_ev[s], 0);
+                    launch_probes(c, out, c->d_ctr + 2 + (1 - p), c->aux_stream);
+                    cudaEventRecord(c->join_ev[s], c->aux_stream);
+                } else {
+                    launch_probes(c, out, c->d_ctr + 2 + (1 - p), c->stream);
+                }
                 p = 1 - p;
             } else {
                 mb::launch_h_pass(c->args, c->tune_h, mh, c->stream);
@@ -381,6 +405,7 @@ int capture_steps(mb_ctx* c, int steps, int p, bool fused, cudaGraphExec_t* out)
                 launch_probes(c);
             }
         }
+        if (fork) cudaStreamWaitEvent(c->stream, c->join_ev[steps - 1], 0);
         e = cudaStreamEndCapture(c->stream, &graph);
     }
     c->parity = saved;
@@ -612,7 +637,7 @@ int mb_create(mb_ctx** out, const int grid[3], double dx, double dt, const mb_pa
         if ((rc = alloc((void**)&c->d_psi[w], sizeof(float) * c->psi_elems[w]))) return bail(rc);
     const size_t ncoef = 4 * (size_t)(c->nx + c->ny + c->nz);
     if ((rc = alloc((void**)&c->d_coef, sizeof(float) * ncoef))) return bail(rc);
-    if ((rc = alloc((void**)&c->d_ctr, sizeof(long long) * 2))) return bail(rc);
+    if ((rc = alloc((void**)&c->d_ctr, sizeof(long long) * 4))) return bail(rc);
     if ((rc = alloc((void**)&c->d_flux, sizeof(double) * 6 * mb::kFluxSlots))) return bail(rc);
     if ((rc = alloc((void**)&c->d_flux_out, sizeof(double) * 6))) return bail(rc);
     c->n_partial = 1024;
@@ -643,7 +668,8 @@ int mb_create(mb_ctx** out, const int grid[3], double dx, double dt, const mb_pa
     MB_CREATE_CUDA(cudaMemset(c->d_mat, 0, (size_t)ncell));
     for (int w = 0; w < 3; ++w)
         if (c->psi_elems[w]) MB_CREATE_CUDA(cudaMemset(c->d_psi[w], 0, sizeof(float) * c->psi_elems[w]));
-    MB_CREATE_CUDA(cudaMemset(c->d_ctr, 0, sizeof(long long) * 2));
+    MB_CREATE_CUDA(cudaMemset(c->d_ctr, 0, sizeof(long long) * 4));
+    MB_CREATE_CUDA(cudaStreamCreateWithFlags(&c->aux_stream, cudaStreamNonBlocking));
     MB_CREATE_CUDA(cudaMemset(c->d_err, 0, sizeof(int)));
     MB_CREATE_CUDA(cudaMemset(c->d_flux, 0, sizeof(double) * 6 * mb::kFluxSlots));
 #undef MB_CREATE_CUDA
@@ -681,6 +707,9 @@ int mb_destroy(mb_ctx* c) {
         cudaFree(q.acc);
     }
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    if (c->aux_stream) cudaStreamDestroy(c->aux_stream);
+    for (cudaEvent_t ev : c->fork_ev) cudaEventDestroy(ev);
+    for (cudaEvent_t ev : c->join_ev) cudaEventDestroy(ev);
     delete c;
     return MB_OK;
 }
@@ -1149,7 +1178,8 @@ int mb_step_timed(mb_ctx* c, int n, double* ms_out) {
         const mb::StepArgs out = fused ? view_of(c, 1 - p) : in;
         cudaEventRecord(e[0], c->stream);
         if (fused) {
-            mb::launch_fused_step(in, ping_of(out), c->tune_f, p ? fm->second : fm->first, c->stream);
+            mb::launch_fused_step(in, ping_of(c, out, 1 - p), c->tune_f, p ? fm->second : fm->first,
+                                  c->stream);
             cudaEventRecord(e[1], c->stream);
             p = 1 - p;
         } else {
@@ -1158,11 +1188,11 @@ int mb_step_timed(mb_ctx* c, int n, double* ms_out) {
             mb::launch_e_pass(c->args, c->tune_e, tma_for(c, c->tune_e), c->stream);
         }
         cudaEventRecord(e[2], c->stream);
-        mb::launch_point_dft(pp, out.f, c->d_ctr, c->dt, c->stream);
+        const long long* ctr = fused ? c->d_ctr + 2 + p : c->d_ctr;   // p: the copy just written
+        mb::launch_point_dft(pp, out.f, ctr, c->dt, c->stream);
         cudaEventRecord(e[3], c->stream);
-        mb::launch_face_dft(c->face, out.f, out.g, c->d_ctr, c->dt, c->stream);
-        for (const mb::DevPlaneProbe& q : c->planes)
-            mb::launch_plane_dft(q, out.f, out.g, c->d_ctr, c->dt, c->stream);
+        mb::launch_face_dft(c->face, out.f, out.g, ctr, c->dt, c->stream);
+        for (const mb::DevPlaneProbe& q : c->planes) mb::launch_plane_dft(q, out.f, out.g, ctr, c->dt, c->stream);
         cudaEventRecord(e[4], c->stream);
     }
     cudaError_t le = cudaGetLastError();
@@ -1456,10 +1486,10 @@ int mb_autotune(mb_ctx* c) {
                 const auto* fm = fused_maps_for(c, t);
                 if (!fm) continue;
                 const mb::TmaFusedMaps& m = c->parity ? fm->second : fm->first;
-                mb::launch_fused_step(c->args, ping_of(other), t, m, c->stream);
+                const mb::DevPing dst = ping_of(c, other, 1 - c->parity);
+                mb::launch_fused_step(c->args, dst, t, m, c->stream);
                 cudaEventRecord(e0, c->stream);
-                for (int r = 0; r < reps; ++r)
-                    mb::launch_fused_step(c->args, ping_of(other), t, m, c->stream);
+                for (int r = 0; r < reps; ++r) mb::launch_fused_step(c->args, dst, t, m, c->stream);
                 cudaEventRecord(e1, c->stream);
                 cudaEventSynchronize(e1);
                 float ms = 0;

@@ -125,6 +125,10 @@ __device__ __forceinline__ PsiOut psi_in_place(const StepArgs& a) {
 struct DevPing {
     float *ex, *ey, *ez, *hx, *hy, *hz;
     PsiOut psi;
+    // the step count after this step is also stored here, for the probes of
+    // the copy the step writes (they may run during the next step, which
+    // advances the main counter)
+    long long* sample;
 };
 
 // ------------------------------------------------------------------ Philox

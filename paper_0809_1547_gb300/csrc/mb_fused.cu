@@ -319,7 +319,7 @@ __global__ void __launch_bounds__(BX * BY) k_step_fused(StepArgs a, DevPing d,
             if (wfl[q][tid >> 5] != 0.0f)
                 atomicAdd(a.flux.acc + q * kFluxSlots + (slot % kFluxSlots), (double)wfl[q][tid >> 5]);
     }
-    finish_step(a);
+    finish_step(a, d.sample);
 }
 
 template <int BX, int BY>

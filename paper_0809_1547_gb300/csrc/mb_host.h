@@ -270,7 +270,10 @@ struct mb_ctx {
     uint32_t* d_glist = nullptr;       // gain cells, increasing order
     uint32_t glist_count = 0;
     size_t glist_capacity = 0;
-    long long* d_ctr = nullptr;        // step counters
+    // step counters: [0] steps completed, [1] finished blocks of the current
+    // launch, [2 + q] the step count when copy q was last written by the
+    // single-pass step (the probes of that copy sample it)
+    long long* d_ctr = nullptr;
     double* d_flux = nullptr;          // 6 faces x kFluxSlots accumulators
     double* d_flux_out = nullptr;      // the 6 face energies in joules (read-back staging)
     double* d_partial = nullptr;       // energy partial sums
@@ -327,6 +330,10 @@ struct mb_ctx {
     // stepping
     int64_t n = 0;
     int64_t launches = 0;
+    // the single-pass step's probes run on a second stream, concurrently
+    // with the next step (fork / join events of a captured chunk)
+    cudaStream_t aux_stream = nullptr;
+    std::vector<cudaEvent_t> fork_ev, join_ev;
     // per parity of the starting copy (the pointers baked into a graph)
     cudaGraphExec_t graph_chunk[2] = {nullptr, nullptr};
     cudaGraphExec_t graph_one[2] = {nullptr, nullptr};

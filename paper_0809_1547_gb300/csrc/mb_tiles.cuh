@@ -172,9 +172,10 @@ __device__ __forceinline__ unsigned warp_slot() {
     return b * 7u + (unsigned)(linear_tid() >> 5);
 }
 
-// The last block of the E launch to finish advances the step counter.  No
-// block waits for another: each one only counts itself out.
-__device__ __forceinline__ void finish_step(const StepArgs& a) {
+// The last block of the E launch to finish advances the step counter (and
+// stores the new count in *sample when given).  No block waits for another:
+// each one only counts itself out.
+__device__ __forceinline__ void finish_step(const StepArgs& a, long long* sample = nullptr) {
     __syncthreads();
     if (linear_tid() == 0) {
         __threadfence();
@@ -182,7 +183,8 @@ __device__ __forceinline__ void finish_step(const StepArgs& a) {
         const unsigned long long t = atomicAdd((unsigned long long*)(a.step_ctr + 1), 1ULL);
         if (t == nb - 1) {
             atomicExch((unsigned long long*)(a.step_ctr + 1), 0ULL);
-            atomicAdd((unsigned long long*)a.step_ctr, 1ULL);
+            const unsigned long long prev = atomicAdd((unsigned long long*)a.step_ctr, 1ULL);
+            if (sample) *sample = (long long)prev + 1;
         }
     }
 }
