@@ -252,12 +252,13 @@ int mb_set_tuning(mb_ctx* ctx, const int tune_h[4], const int tune_e[4]);
 
 /* Single-pass step: the H half-step, the gain cells' Lorentz / Langevin
  * update and the E / population update of one time step (the step of the
- * "Simulations" paragraph) in one launch.  It reads the context's E, H and
- * CPML memories and writes a second copy of them (allocated on first use:
- * 24 bytes per cell plus the CPML memories); the next step writes back, so
- * mb_step runs such steps in pairs and the state is in the context's own
- * arrays after every call (an odd last step runs the two passes).  P, J and
- * the populations are updated in place.  Fields, probes and energy equal
+ * "Simulations" paragraph) in one launch.  It reads the current copy of E,
+ * H and the CPML memories and writes a second copy of them (allocated on
+ * the first such step: 24 bytes per cell plus the CPML memories), which
+ * becomes the current one; every call of this header (fields, snapshots,
+ * probes, energy, the adjoint) follows the current copy, so the alternation
+ * is invisible to the caller.  P, J and the populations are updated in
+ * place.  Fields, probes and energy equal
  * the two-pass step's bit for bit (the face-flux sums agree to the FP32
  * rounding of their partial sums).  tune = {on (0 or 1), bx, by, kz}: tiles of bx x by columns
  * (32x4, 32x8, 64x4 or 64x8) walking kz planes; needs n_x a multiple of 16.
