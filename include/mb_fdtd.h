@@ -178,8 +178,7 @@ int mb_step(mb_ctx* ctx, int n);
  * device time (ms) of each pass over the n steps to ms_out[0..3]: H pass,
  * fused E pass, point-probe DFT, face- and plane-probe DFTs (ms_out may be
  * NULL).  With the single-pass step (mb_set_single_pass) ms_out[0] is the
- * single-pass launches (and ms_out[0..1] the two passes of an odd n's last
- * step). */
+ * single-pass launches and ms_out[1] stays ~0. */
 int mb_step_timed(mb_ctx* ctx, int n, double* ms_out);
 
 /* Wait for the context's queued work. */
