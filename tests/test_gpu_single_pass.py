@@ -204,3 +204,39 @@ def test_flux_async_matches_flux():
     with pytest.raises(ValueError):
         g.flux_async(torch.zeros(6, dtype=torch.float32))
     g.close()
+
+
+@pytest.mark.parametrize("grid,npml,tune", [
+    ((16, 5, 3), 1, (1, 32, 4, 2)),     # narrower than a tile, ragged y, three planes
+    ((32, 1, 1), 0, (1, 32, 8, 4)),     # one row, one plane, no CPML
+    ((48, 9, 2), 2, (1, 64, 8, 1)),     # a tile wider than the grid, one-plane chunks
+    ((16, 16, 40), 8, (1, 32, 4, 64)),  # all-CPML cross-section, chunk longer than n_z
+])
+def test_single_pass_small_and_degenerate_grids_bitwise(grid, npml, tune):
+    from paper_0809_1547_gb300.binding import MBSimulation, mb_default_params
+    shp = grid[::-1]
+    rng = np.random.default_rng(sum(grid))
+    eps = np.where(rng.random(shp) < 0.3, 8.41, 1.0).astype(np.float32)
+    gain = (rng.random(shp) < 0.6).astype(np.uint8)
+    sims = []
+    for mode in ((0, 32, 4, 8), tune):
+        g = MBSimulation(grid, DX, DT, mb_default_params(npml=npml))
+        g.set_material(eps, gain, 4e24, 1e13)
+        g.set_seed(91)
+        g.set_single_pass(mode)
+        rng2 = np.random.default_rng(5)
+        for name in ("Ex", "Ey", "Ez"):
+            v = (rng2.standard_normal(shp) * 1e6).astype(np.float32)
+            if name != "Ex":
+                v[:, :, 0] = 0
+            if name != "Ey":
+                v[:, 0, :] = 0
+            if name != "Ez":
+                v[0, :, :] = 0
+            g.set_field(name, v)
+        g.step(7)
+        sims.append(g)
+    for name in FIELD_NAMES:
+        np.testing.assert_array_equal(sims[1].field(name), sims[0].field(name), err_msg=f"{grid} {name}")
+    for g in sims:
+        g.close()
