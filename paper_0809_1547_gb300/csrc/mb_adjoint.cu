@@ -88,13 +88,13 @@ __device__ __forceinline__ void adj_point_cell(const AdjArgs& a, int i, int j, i
     if (valid) {
         const uint32_t N = a.g.ncell;
         const uint32_t c = (uint32_t)i + (uint32_t)a.g.nx * j + a.g.nxy * k;
-        const float e0x = __ldg(a.x0.ex + c), e0y = __ldg(a.x0.ey + c), e0z = __ldg(a.x0.ez + c);
-        const float e1x = __ldg(a.x1.ex + c), e1y = __ldg(a.x1.ey + c), e1z = __ldg(a.x1.ez + c);
+        const float e0x = __ldcs(a.x0.ex + c), e0y = __ldcs(a.x0.ey + c), e0z = __ldcs(a.x0.ez + c);
+        const float e1x = __ldcs(a.x1.ex + c), e1y = __ldcs(a.x1.ey + c), e1z = __ldcs(a.x1.ez + c);
         float l0x = 0.0f, l0y = 0.0f, l0z = 0.0f;
         // objective: mx Hy(k-1) - my Hx(k-1) on the plane k = zp
         if (k == a.zp && i >= a.rx0 && i < a.rx1 && j >= a.ry0 && j < a.ry1) {
             const uint32_t cp = (uint32_t)i + (uint32_t)a.g.nx * j;
-            const float hxk = __ldg(a.x1.hpx + cp), hyk = __ldg(a.x1.hpy + cp);
+            const float hxk = __ldcs(a.x1.hpx + cp), hyk = __ldcs(a.x1.hpy + cp);
             l1x += 0.5f * hyk;
             l1y -= 0.5f * hxk;
             l0x += 0.5f * hyk;
@@ -108,12 +108,12 @@ __device__ __forceinline__ void adj_point_cell(const AdjArgs& a, int i, int j, i
         float n1 = 0.0f, n2 = 0.0f, n3 = 0.0f, ln1 = 0.0f, ln2 = 0.0f, ln3 = 0.0f;
         if (gain) {
             // populations: n' = n + g + G n + mk sp
-            j1x = __ldg(a.x1.jx + c);
-            j1y = __ldg(a.x1.jy + c);
-            j1z = __ldg(a.x1.jz + c);
-            n1 = __ldg(a.x0.n1 + c);
-            n2 = __ldg(a.x0.n2 + c);
-            n3 = __ldg(a.x0.n3 + c);
+            j1x = __ldcs(a.x1.jx + c);
+            j1y = __ldcs(a.x1.jy + c);
+            j1z = __ldcs(a.x1.jz + c);
+            n1 = __ldcs(a.x0.n1 + c);
+            n2 = __ldcs(a.x0.n2 + c);
+            n3 = __ldcs(a.x0.n3 + c);
             const float lq[3] = {a.ln[c], a.ln[c + N], a.ln[c + 2 * N]};
             const float sp = 0.5f * ((e0x + e1x) * j1x + (e0y + e1y) * j1y + (e0z + e1z) * j1z);
             const float nq[3] = {n1, n2, n3};
@@ -292,8 +292,8 @@ __global__ void __launch_bounds__(256) k_adj_h(AdjArgs a) {
     // objective: H sites of the layer k = zp - 1
     if (k + 1 == a.zp && i >= a.rx0 && i < a.rx1 && j >= a.ry0 && j < a.ry1) {
         const uint32_t cu = c + a.g.nxy;
-        hy += 0.5f * (__ldg(a.x0.ex + cu) + __ldg(a.x1.ex + cu));
-        hx -= 0.5f * (__ldg(a.x0.ey + cu) + __ldg(a.x1.ey + cu));
+        hy += 0.5f * (__ldcs(a.x0.ex + cu) + __ldcs(a.x1.ex + cu));
+        hx -= 0.5f * (__ldcs(a.x0.ey + cu) + __ldcs(a.x1.ey + cu));
     }
     const WCoef w0 = w_coef(a, i, j, k);
     const WCoef wi = w_coef(a, i + 1, j, k);
@@ -410,7 +410,9 @@ __global__ void __launch_bounds__(256) k_adj_e_point(AdjArgs a) {
 // Store slot of one step: E (arrays 0..2) and J, n1..n3 (arrays 9..14) of
 // the field block, Hx and Hy of plane kp, and the step counter.  16-byte
 // moves when n_cells and the plane size are multiples of 4 (every array then
-// starts 16-byte aligned).
+// starts 16-byte aligned).  The stores are marked streaming (evict first), so
+// the segment store (gigabytes) does not push the recomputed state out of
+// L2; the reverse kernels read the stored states the same way.
 __global__ void k_keep(const float* __restrict__ F, float* __restrict__ dst, uint32_t n,
                        uint32_t nxy, int kp, const long long* __restrict__ ctr,
                        long long* __restrict__ slot_n) {
@@ -425,19 +427,19 @@ __global__ void k_keep(const float* __restrict__ F, float* __restrict__ dst, uin
         const float4* a = reinterpret_cast<const float4*>(F);
         const float4* b = reinterpret_cast<const float4*>(F + 9 * (size_t)n);
         float4* d = reinterpret_cast<float4*>(dst);
-        for (size_t t = t0; t < n3 / 4; t += stride) d[t] = a[t];
-        for (size_t t = t0; t < n6 / 4; t += stride) d[n3 / 4 + t] = b[t];
+        for (size_t t = t0; t < n3 / 4; t += stride) __stcs(d + t, a[t]);
+        for (size_t t = t0; t < n6 / 4; t += stride) __stcs(d + n3 / 4 + t, b[t]);
         for (size_t t = t0; t < nxy / 4; t += stride) {
-            reinterpret_cast<float4*>(dp)[t] = reinterpret_cast<const float4*>(hpx)[t];
-            reinterpret_cast<float4*>(dp + nxy)[t] = reinterpret_cast<const float4*>(hpy)[t];
+            __stcs(reinterpret_cast<float4*>(dp) + t, reinterpret_cast<const float4*>(hpx)[t]);
+            __stcs(reinterpret_cast<float4*>(dp + nxy) + t, reinterpret_cast<const float4*>(hpy)[t]);
         }
     } else {
         const float* b = F + 9 * (size_t)n;
-        for (size_t t = t0; t < n3; t += stride) dst[t] = F[t];
-        for (size_t t = t0; t < n6; t += stride) dst[n3 + t] = b[t];
+        for (size_t t = t0; t < n3; t += stride) __stcs(dst + t, F[t]);
+        for (size_t t = t0; t < n6; t += stride) __stcs(dst + n3 + t, b[t]);
         for (size_t t = t0; t < nxy; t += stride) {
-            dp[t] = hpx[t];
-            dp[nxy + t] = hpy[t];
+            __stcs(dp + t, hpx[t]);
+            __stcs(dp + nxy + t, hpy[t]);
         }
     }
 }
