@@ -269,6 +269,12 @@ int mb_set_single_pass(mb_ctx* ctx, const int tune[4]);
 /* Kernel launches queued per step by mb_step, and in total so far. */
 int mb_launch_stats(mb_ctx* ctx, int* per_step, int64_t* total);
 
+/* Test hook: the n-th device allocation made by mb_create or by the
+ * single-pass step's second copy from now on (n = 0: the next one) fails as
+ * if the device were out of memory (MB_ERR_OOM, nothing leaked); n < 0
+ * switches the injection off.  Process-wide. */
+void mb_debug_fail_alloc(int n);
+
 /* Device bytes the context holds. */
 int mb_device_bytes(mb_ctx* ctx, size_t* bytes);
 

@@ -86,6 +86,7 @@ _SIGS = [
     ("mb_get_tuning", C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     ("mb_set_tuning", C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     ("mb_flux_async", C.c_int, [_P, _P]),
+    ("mb_debug_fail_alloc", None, [C.c_int]),
     ("mb_get_single_pass", C.c_int, [_P, C.POINTER(C.c_int)]),
     ("mb_set_single_pass", C.c_int, [_P, C.POINTER(C.c_int)]),
     ("mb_launch_stats", C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int64)]),
@@ -243,6 +244,11 @@ def mb_flux_async(h, out_ptr: int):
     """Queue the read of the six face energies into the 6-double host buffer
     at out_ptr (pinned memory); valid once the stream has passed this call."""
     _check(load_library().mb_flux_async(h, C.c_void_p(out_ptr)), h)
+
+
+def mb_debug_fail_alloc(n: int):
+    """Test hook: make the n-th device allocation from now on fail (n < 0: off)."""
+    load_library().mb_debug_fail_alloc(int(n))
 
 
 def mb_synchronize(h):

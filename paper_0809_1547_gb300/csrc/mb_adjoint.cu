@@ -23,6 +23,8 @@
 // The three use the forward states x^n and x^{n+1} kept by the segment store.
 #include "mb_host.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
 #include <string>
 #include <vector>
@@ -456,6 +458,11 @@ __global__ void k_adj_out(const double* geps, float* out, uint32_t n, double sca
 
 namespace {
 
+struct NvtxScope {
+    explicit NvtxScope(const char* name) { nvtxRangePushA(name); }
+    ~NvtxScope() { nvtxRangePop(); }
+};
+
 int afail(mb_ctx* c, int code, const std::string& msg) {
     c->err = msg;
     mb::set_thread_error(msg);
@@ -491,6 +498,7 @@ extern "C" int mb_adjoint_energy_zface(mb_ctx* c, int n_steps, int ckpt_every, i
     const size_t nxy = (size_t)c->nx * c->ny;
     const size_t slot = 9 * N + 2 * nxy;   // floats per stored step: E, J, n1..n3, Hx/Hy of one plane
     const size_t psi_total = c->psi_elems[0] + c->psi_elems[1] + c->psi_elems[2];
+    NvtxScope range("mb_adjoint_energy_zface");
     // the sweeps below step the context in place (state in its own arrays)
     const bool was_single_pass = mb::hold_in_place(c);
 

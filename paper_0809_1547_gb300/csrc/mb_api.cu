@@ -5,6 +5,7 @@
 #include "mb_ctx.h"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -22,6 +23,16 @@ using mb::kQe;
 namespace mbi {
 
 thread_local std::string g_err;
+// allocations left before an injected failure (-1: none)
+std::atomic<int> g_fail_alloc_after{-1};
+
+bool inject_alloc_failure() {
+    int v = g_fail_alloc_after.load();
+    while (v >= 0) {
+        if (g_fail_alloc_after.compare_exchange_weak(v, v - 1)) return v == 0;
+    }
+    return false;
+}
 
 int fail(mb_ctx* ctx, int code, const std::string& msg) {
     if (ctx) ctx->err = msg;
@@ -431,7 +442,7 @@ int mb_create(mb_ctx** out, const int grid[3], double dx, double dt, const mb_pa
     }
     auto alloc = [&](void** ptr, size_t bytes) -> int {
         if (bytes == 0) { *ptr = nullptr; return MB_OK; }
-        cudaError_t ae = cudaMalloc(ptr, bytes);
+        cudaError_t ae = inject_alloc_failure() ? cudaErrorMemoryAllocation : cudaMalloc(ptr, bytes);
         if (ae != cudaSuccess) {
             cudaGetLastError();
             return fail(nullptr, MB_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
@@ -531,6 +542,7 @@ int mb_destroy(mb_ctx* c) {
 int mb_set_material(mb_ctx* c, const float* eps_map, const uint8_t* gain_mask, double N_a,
                     double pump) {
     if (int rc = check_ctx(c)) return rc;
+    NvtxRange range("mb_set_material");
     if (!eps_map || !gain_mask) return fail(c, MB_ERR_ARG, "null eps_map or gain_mask");
     if (!(N_a >= 0) || !(pump >= 0) || !std::isfinite(N_a) || !std::isfinite(pump))
         return fail(c, MB_ERR_ARG, "N_a and pump must be finite and >= 0");
@@ -1145,6 +1157,8 @@ int mb_load_state(mb_ctx* c, const void* host_blob, size_t bytes) {
     c->n = hdr[3];
     return MB_OK;
 }
+
+void mb_debug_fail_alloc(int n) { g_fail_alloc_after.store(n < 0 ? -1 : n); }
 
 int mb_device_bytes(mb_ctx* c, size_t* bytes) {
     if (int rc = check_ctx(c)) return rc;

@@ -10,9 +10,24 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "mb_host.h"
 
 namespace mbi {
+
+// NVTX range over a host call (seen by profilers that record NVTX; no cost
+// otherwise).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
+// Allocation-failure injection for tests (mb_debug_fail_alloc): true when
+// the next device allocation of a context should fail.
+bool inject_alloc_failure();
 
 // Records msg as the context's (and the thread's) last error; returns code.
 int fail(mb_ctx* ctx, int code, const std::string& msg);

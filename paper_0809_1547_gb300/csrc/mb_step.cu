@@ -31,7 +31,8 @@ mb::DevPing ping_of(const mb_ctx* c, const mb::StepArgs& a, int q) {
 int ensure_second_copy(mb_ctx* c) {
     if (c->d_fields2) return MB_OK;
     const size_t fb = sizeof(float) * 6 * (size_t)c->ncell;
-    cudaError_t e = cudaMalloc((void**)&c->d_fields2, fb);
+    cudaError_t e = inject_alloc_failure() ? cudaErrorMemoryAllocation
+                                           : cudaMalloc((void**)&c->d_fields2, fb);
     for (int w = 0; w < 3 && e == cudaSuccess; ++w)
         if (c->psi_elems[w]) e = cudaMalloc((void**)&c->d_psi2[w], sizeof(float) * c->psi_elems[w]);
     if (e != cudaSuccess) {
@@ -190,6 +191,7 @@ extern "C" {
 
 int mb_step(mb_ctx* c, int n) {
     if (int rc = check_ctx(c)) return rc;
+    NvtxRange range("mb_step");
     if (n < 0) return fail(c, MB_ERR_ARG, "negative step count");
     if (n == 0) return MB_OK;
     const bool fused = fused_ready(c);
@@ -211,6 +213,7 @@ int mb_step(mb_ctx* c, int n) {
 
 int mb_step_timed(mb_ctx* c, int n, double* ms_out) {
     if (int rc = check_ctx(c)) return rc;
+    NvtxRange range("mb_step_timed");
     if (n < 0) return fail(c, MB_ERR_ARG, "negative step count");
     if (n == 0) return MB_OK;
     // 5 events per step: before H, after H, after E, after point DFT, after face DFT
@@ -276,6 +279,7 @@ int mb_step_timed(mb_ctx* c, int n, double* ms_out) {
 
 int mb_autotune(mb_ctx* c) {
     if (int rc = check_ctx(c)) return rc;
+    NvtxRange range("mb_autotune");
     auto parts = state_parts(c);
     size_t total = 0;
     for (auto& p : parts) total += p.bytes;
