@@ -4,7 +4,8 @@ Bar: every field within relative L2 1e-5 of the oracle after the run (the
 bound stated for the FP32 step); squared read-outs (spectra, energy) within
 2e-5; the Philox stream bit-exact.  Sizes span several thread blocks with
 ragged tails, the degenerate grids (one-cell columns, all-CPML cubes), both
-material encodings, and the full 320^3 workload on sampled sub-blocks.
+material encodings, and the full 320^3 and 448^3 workloads on sampled
+sub-blocks.
 """
 import math
 
@@ -357,22 +358,18 @@ def _global_state_block(g, lo, size):
     return out
 
 
-def test_full_size_320_sampled_parity():
-    """The 320^3 workload in the launch configuration the benchmark times:
-    after 24 steps, one more GPU step is checked on sampled interior
-    sub-blocks against the oracle's step of the same sub-block (with a
-    one-cell halo; noise counters and step index taken from the full grid)."""
+def _sampled_step_parity(w, n_pre, los, B):
+    """Advance workload w by n_pre steps in the launch configuration the
+    benchmark times (autotuned), then check one more GPU step on the interior
+    sub-blocks starting at los (edge B) against the oracle's step of the same
+    sub-block (with a one-cell halo; noise counters and step index taken from
+    the full grid); then properties that hold at any size."""
     import torch
-    from paper_0809_1547_gb300 import inputs
     from paper_0809_1547_gb300.workloads import setup_simulation
-    w = inputs.workload_paper_320()
+    nx, ny, nz = w.grid
     g = setup_simulation(w, autotune=True)
-    g.step(24)
+    g.step(n_pre)
     g.synchronize()
-    B = 20
-    rng = np.random.default_rng(12)
-    los = [tuple(int(v) for v in rng.integers(9, 320 - 9 - B - 2, size=3)) for _ in range(3)]
-    los.append((150, 150, 150))
     before = [_global_state_block(g, lo, B + 2) for lo in los]
     n_before = g.n
     g.step(1)
@@ -387,7 +384,7 @@ def test_full_size_320_sampled_parity():
         o.set_seed(w.seed)
         kk, jj, ii = np.meshgrid(np.arange(k0, k0 + B + 2), np.arange(j0, j0 + B + 2),
                                  np.arange(i0, i0 + B + 2), indexing="ij")
-        o.cell_index = (ii + 320 * (jj + 320 * kk)).astype(np.uint64)
+        o.cell_index = (ii + nx * (jj + ny * kk)).astype(np.uint64)
         o.n = n_before
         for name, v in st0.items():
             o.set_field(name, v)
@@ -399,10 +396,35 @@ def test_full_size_320_sampled_parity():
             ref = o.field(name)[core]
             err = rel_l2(v[core], ref)
             assert err <= REL_L2_TOL or np.abs(ref).max() == 0 == np.abs(v[core]).max(), (lo, name, err)
-    # properties that hold at any size
     U, fl = g.energy()
     assert math.isfinite(U) and np.all(np.isfinite(fl))
     t, _ = g.field_device("Jx")
     nongain = torch.from_numpy(w.gain == 0).cuda()
     assert float(t[nongain].abs().max()) == 0.0
     g.close()
+
+
+def test_full_size_320_sampled_parity():
+    """The 320^3 workload (~8100 spheres, 32.8 M cells) after 24 steps: one
+    more step checked on three random interior sub-blocks and the centre."""
+    from paper_0809_1547_gb300 import inputs
+    w = inputs.workload_paper_320()
+    B = 20
+    rng = np.random.default_rng(12)
+    los = [tuple(int(v) for v in rng.integers(9, 320 - 9 - B - 2, size=3)) for _ in range(3)]
+    los.append((150, 150, 150))
+    _sampled_step_parity(w, 24, los, B)
+
+
+def test_full_size_448_sampled_parity():
+    """The 448^3 sweep workload (~22.9k spheres, 89.9 M cells, 5.8 GB of
+    state) after 16 steps: one more step checked on sub-blocks at random
+    interior positions, across tile and plane-chunk boundaries (x = 31|32,
+    y = 3|4, z = 15|16 of the launch's tiles) and at the far interior corner."""
+    from paper_0809_1547_gb300 import inputs
+    w = inputs.workload_large_448()
+    B = 16
+    rng = np.random.default_rng(448)
+    los = [tuple(int(v) for v in rng.integers(9, 448 - 9 - B - 2, size=3)) for _ in range(2)]
+    los += [(216, 214, 214), (448 - 9 - B - 2,) * 3]
+    _sampled_step_parity(w, 16, los, B)
