@@ -302,6 +302,7 @@ def bench_ours(args):
     t_host0 = time.time()
     ev0.record(stream)
     sim.step(args.steps)                          # the production path: CUDA-graph replay
+    sim.join_probes()                             # the last steps' probe DFTs inside the region
     ev1.record(stream)
     torch.cuda.synchronize()
     t_host1 = time.time()
@@ -513,6 +514,7 @@ def bench_batched(stream, steps: int, warmup: int, n_pump: int = 16, n_seed: int
     def plain():
         for s_ in sims:
             s_.step(steps)
+            s_.join_probes()
     plain_ms = timed(plain)
     for s_ in sims:
         s_.close()
@@ -574,6 +576,7 @@ def bench_large(stream, steps: int, warmup: int):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     sim.step(steps)                    # graph replay, as mb_step runs
+    sim.join_probes()
     e1.record(stream)
     torch.cuda.synchronize()
     el = e0.elapsed_time(e1)
@@ -630,6 +633,7 @@ def bench_passive(w, stream, steps: int, warmup: int):
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         sim.step(steps)                # graph replay, as mb_step runs
+        sim.join_probes()
         e1.record(stream)
         torch.cuda.synchronize()
         el = e0.elapsed_time(e1)
@@ -706,7 +710,7 @@ def bench_adjoint(stream, warmup: int, autotune: bool = True):
     s_.close()
     p_ = make()
     p_.step(warmup)
-    plain_ms, _ = timed(lambda: p_.step(w.steps))
+    plain_ms, _ = timed(lambda: (p_.step(w.steps), p_.join_probes()))
     p_.close()
     v_adj = cells * w.steps / (adj_ms / 1e3) / 1e6
     v_plain = cells * w.steps / (plain_ms / 1e3) / 1e6

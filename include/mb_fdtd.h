@@ -170,8 +170,23 @@ int mb_plane_mode_map(mb_ctx* ctx, int probe_id, int bin, double* out_map);
  * mb_energy), host array of n_x n_y doubles.  Synchronizes. */
 int mb_plane_energy_density(mb_ctx* ctx, int k, double* out);
 
-/* Advance n >= 0 steps (asynchronous; replays a captured CUDA graph). */
+/* Advance n >= 0 steps (asynchronous on the context's stream; whole chunks
+ * of steps replay a captured CUDA graph).  With the single-pass step, the
+ * probe DFTs of the steps after the last whole chunk (e.g. every step of
+ * mb_step(ctx, 1)) run on the context's second stream beside the next step
+ * (they read only the copy that step wrote, which the next step only reads)
+ * and may still run when the context's stream passes this call: every later
+ * call on the context except mb_step and mb_flux_async first orders the
+ * context's stream after them, and mb_join_probes does only that.  The
+ * fields, the step count and the face energies are final on the context's
+ * stream as usual. */
 int mb_step(mb_ctx* ctx, int n);
+
+/* Order the context's stream after the probe launches mb_step left running
+ * on the second stream (enqueues event waits; does not block the host): an
+ * event the caller records on the context's stream afterwards covers all of
+ * the context's work so far.  Errors: MB_ERR_ARG (null context). */
+int mb_join_probes(mb_ctx* ctx);
 
 /* Advance n >= 0 steps like mb_step, but with direct launches bracketed by
  * CUDA events on the context's stream; synchronizes, then adds the summed
@@ -181,7 +196,8 @@ int mb_step(mb_ctx* ctx, int n);
  * single-pass launches and ms_out[1] stays ~0. */
 int mb_step_timed(mb_ctx* ctx, int n, double* ms_out);
 
-/* Wait for the context's queued work. */
+/* Wait for the context's queued work (the probe launches on its second
+ * stream included). */
 int mb_synchronize(mb_ctx* ctx);
 
 /* Steps taken so far. */
@@ -209,10 +225,14 @@ int mb_energy(mb_ctx* ctx, double* out_U, double* out_flux6);
 int mb_flux(mb_ctx* ctx, double* out_flux6);
 
 /* The same six values, asynchronously: queued on the context's stream after
- * the work already queued; host_out6 (6 doubles, caller-owned, pinned host
- * memory for a truly asynchronous copy) holds them once the stream has
- * passed this point (after mb_synchronize, or an event recorded on the
- * context's stream after this call).  The buffer must stay valid until then.
+ * the work already queued; host_out6 (6 doubles, caller-owned) holds them
+ * once the stream has passed this point (after mb_synchronize, or an event
+ * recorded on the context's stream after this call).  In page-locked host
+ * memory (cudaHostAlloc, cudaHostRegister, torch pin_memory) the summing
+ * kernel writes them there directly; other memory gets a device-to-host
+ * copy.  It does not wait for probes left running by mb_step (the face
+ * energies are accumulated by the field step itself).  The buffer must stay
+ * valid until then.
  * Device-side wait failures are reported by the next synchronizing call.
  * Errors: MB_ERR_ARG (null output), MB_ERR_CUDA. */
 int mb_flux_async(mb_ctx* ctx, double* host_out6);

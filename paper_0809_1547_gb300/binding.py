@@ -73,6 +73,7 @@ _SIGS = [
     ("mb_step_timed", C.c_int, [_P, C.c_int, _P]),
     ("mb_flux", C.c_int, [_P, _P]),
     ("mb_synchronize", C.c_int, [_P]),
+    ("mb_join_probes", C.c_int, [_P]),
     ("mb_get_step", C.c_int, [_P, C.POINTER(C.c_int64)]),
     ("mb_probe_spectrum", C.c_int, [_P, C.c_int, _P, _P]),
     ("mb_face_spectrum", C.c_int, [_P, C.c_int, _P, _P]),
@@ -253,6 +254,12 @@ def mb_debug_fail_alloc(n: int):
 
 def mb_synchronize(h):
     _check(load_library().mb_synchronize(h), h)
+
+
+def mb_join_probes(h):
+    """Order the context's stream after probe launches mb_step left running
+    on its second stream (no host wait)."""
+    _check(load_library().mb_join_probes(h), h)
 
 
 def mb_get_step(h) -> int:
@@ -554,6 +561,11 @@ class MBSimulation:
 
     def synchronize(self):
         mb_synchronize(self._h)
+
+    def join_probes(self):
+        """Make the simulation's stream wait for the probe DFTs that step()
+        left running beside later steps (enqueued only)."""
+        mb_join_probes(self._h)
 
     @property
     def n(self):

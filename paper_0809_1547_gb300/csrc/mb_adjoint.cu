@@ -487,6 +487,7 @@ extern "C" int mb_adjoint_energy_zface(mb_ctx* c, int n_steps, int ckpt_every, i
         mb::set_thread_error("null context");
         return MB_ERR_ARG;
     }
+    mb::join_probes(c);
     if (n_steps < 1) return afail(c, MB_ERR_ARG, "n_steps must be >= 1");
     if (!c->have_material) return afail(c, MB_ERR_STATE, "no material set");
     const int zp = z_plane < 0 ? c->args.flux.phi[2] : z_plane;

@@ -8,6 +8,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <condition_variable>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -224,11 +225,17 @@ void gain_coefficients(mb_ctx* c) {
     }
 }
 
-int check_ctx(mb_ctx* c) {
+int check_ctx_nojoin(mb_ctx* c) {
     if (!c) {
         g_err = "null context";
         return MB_ERR_ARG;
     }
+    return MB_OK;
+}
+
+int check_ctx(mb_ctx* c) {
+    if (int rc = check_ctx_nojoin(c)) return rc;
+    mb::join_probes(c);
     return MB_OK;
 }
 
@@ -498,7 +505,7 @@ int mb_create(mb_ctx** out, const int grid[3], double dx, double dt, const mb_pa
     MB_CREATE_CUDA(cudaMemset(c->d_err, 0, sizeof(int)));
     MB_CREATE_CUDA(cudaMemset(c->d_flux, 0, sizeof(double) * 6 * mb::kFluxSlots));
 #undef MB_CREATE_CUDA
-    c->h_gain.assign((size_t)ncell, 0);
+    c->h_mat.assign((size_t)ncell, 0);
     c->face.on = 0;
     build_args(c);
     gain_coefficients(c);
@@ -518,7 +525,10 @@ int mb_create(mb_ctx** out, const int grid[3], double dx, double dt, const mb_pa
 
 int mb_destroy(mb_ctx* c) {
     if (!c) return MB_OK;
-    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->stream) {
+        mb::join_probes(c);
+        cudaStreamSynchronize(c->stream);
+    }
     drop_graphs(c);
     void* bufs[] = {c->d_fields, c->d_mat, c->d_inv_eps, c->d_lut, c->d_psi[0], c->d_psi[1],
                     c->d_psi[2], c->d_coef, c->d_ctr, c->d_flux, c->d_partial, c->d_energy,
@@ -535,6 +545,10 @@ int mb_destroy(mb_ctx* c) {
     if (c->aux_stream) cudaStreamDestroy(c->aux_stream);
     for (cudaEvent_t ev : c->fork_ev) cudaEventDestroy(ev);
     for (cudaEvent_t ev : c->join_ev) cudaEventDestroy(ev);
+    for (int q = 0; q < 2; ++q) {
+        if (c->probe_fork[q]) cudaEventDestroy(c->probe_fork[q]);
+        if (c->probe_done[q]) cudaEventDestroy(c->probe_done[q]);
+    }
     delete c;
     return MB_OK;
 }
@@ -548,14 +562,17 @@ int mb_set_material(mb_ctx* c, const float* eps_map, const uint8_t* gain_mask, d
         return fail(c, MB_ERR_ARG, "N_a and pump must be finite and >= 0");
     const int64_t N = c->ncell;
     // Material ids by the bit pattern of eps_r: up to 128 distinct values
-    // share a LUT, more switch to a dense 1/eps map.  Host threads over
-    // chunks of cells.  Pass A: each thread validates its cells, gives them
-    // ids in a table of its own (a packing holds a few values in long runs:
-    // the last value is checked first, then the short table), sets the gain
-    // bit and counts its gain cells.  The tables merge in chunk order (ids =
-    // order of first appearance).  Pass B: each thread maps its ids to the
-    // merged ones and writes its gain cells, in increasing order, into its
-    // segment of the list.
+    // share a LUT, more switch to a dense 1/eps map.  One pool of host
+    // threads over chunks of cells, two passes with a barrier between.
+    // Pass A: each thread validates its cells, gives them ids in a table of
+    // its own (a packing holds a few values in long runs: the last value is
+    // checked first, then the short table), sets the gain bit and counts its
+    // gain cells.  Thread 0 then merges the tables in chunk order (ids =
+    // order of first appearance) and places the threads' gain-list segments.
+    // Pass B: each thread maps its ids to the merged ones and writes its gain
+    // cells, in increasing order, into its segment.  The material bytes and
+    // the list go to buffers the context keeps (allocated once, not zeroed);
+    // the material bytes replace the host copy only when every check passed.
     const bool gain_on = N_a > 0.0;
     const int nthr = (int)std::max<int64_t>(1, std::min<int64_t>(
         {(int64_t)std::max(1u, std::thread::hardware_concurrency()), 16, N / (1 << 18) + 1}));
@@ -563,89 +580,109 @@ int mb_set_material(mb_ctx* c, const float* eps_map, const uint8_t* gain_mask, d
     for (int t = 0; t < nthr; ++t) chunk[t] = {N * t / nthr, N * (t + 1) / nthr};
     std::vector<std::vector<uint32_t>> seen(nthr);
     std::vector<char> bad(nthr, 0), over(nthr, 0);
-    std::vector<int64_t> ngain(nthr, 0);
-    std::unique_ptr<uint8_t[]> mat(new uint8_t[(size_t)N]);
+    std::vector<int64_t> ngain(nthr, 0), goff(nthr + 1, 0);
+    if (c->h_mat_next.size() != (size_t)N) c->h_mat_next.resize((size_t)N);
+    uint8_t* mat = c->h_mat_next.data();
     auto find_key = [](const std::vector<uint32_t>& keys, uint32_t bits) -> int {
         for (size_t t = 0; t < keys.size(); ++t)
             if (keys[t] == bits) return (int)t;
         return -1;
     };
-    auto run = [&](auto&& body) {
-        std::vector<std::thread> pool;
-        for (int t = 0; t < nthr; ++t) pool.emplace_back(body, t);
-        for (auto& th : pool) th.join();
-    };
-    run([&](int t) {
-        std::vector<uint32_t>& keys = seen[t];
-        uint32_t last = 0;
-        int last_id = -1;
-        int64_t cnt = 0;
-        for (int64_t q = chunk[t].first; q < chunk[t].second; ++q) {
-            const float v = eps_map[q];
-            if (!(v >= 1.0f) || !std::isfinite(v)) {
-                bad[t] = 1;
-                return;
-            }
-            uint32_t bits;
-            std::memcpy(&bits, &v, 4);
-            if (last_id < 0 || bits != last) {
-                last = bits;
-                last_id = find_key(keys, bits);
-                if (last_id < 0) {
-                    if (keys.size() < 128) {
-                        last_id = (int)keys.size();
-                        keys.push_back(bits);
-                    } else {
-                        over[t] = 1;   // more than 128 values: dense map
-                        last_id = 0;
-                    }
-                }
-            }
-            const bool g = gain_on && gain_mask[q] != 0;
-            c->h_gain[q] = g ? 1 : 0;
-            mat[q] = (uint8_t)last_id | (g ? 0x80 : 0x00);
-            cnt += g;
-        }
-        ngain[t] = cnt;
-    });
-    for (int t = 0; t < nthr; ++t)
-        if (bad[t]) return fail(c, MB_ERR_MATERIALS, "eps_r must be finite and >= 1");
     std::vector<uint32_t> keys;
-    bool dense = false;
-    for (int t = 0; t < nthr && !dense; ++t) {
-        dense = over[t] != 0;
-        for (uint32_t bits : seen[t])
-            if (!dense && find_key(keys, bits) < 0) {
-                if (keys.size() == 128) {
-                    dense = true;
+    bool dense = false, any_bad = false;
+    std::mutex mu;
+    std::condition_variable cv;
+    int arrived = 0;
+    bool merged = false;
+    auto body = [&](int t) {
+        {
+            std::vector<uint32_t>& tk = seen[t];
+            uint32_t last = 0;
+            int last_id = -1;
+            int64_t cnt = 0;
+            for (int64_t q = chunk[t].first; q < chunk[t].second; ++q) {
+                const float v = eps_map[q];
+                if (!(v >= 1.0f) || !std::isfinite(v)) {
+                    bad[t] = 1;
                     break;
                 }
-                keys.push_back(bits);
+                uint32_t bits;
+                std::memcpy(&bits, &v, 4);
+                if (last_id < 0 || bits != last) {
+                    last = bits;
+                    last_id = find_key(tk, bits);
+                    if (last_id < 0) {
+                        if (tk.size() < 128) {
+                            last_id = (int)tk.size();
+                            tk.push_back(bits);
+                        } else {
+                            over[t] = 1;   // more than 128 values: dense map
+                            last_id = 0;
+                        }
+                    }
+                }
+                const bool g = gain_on && gain_mask[q] != 0;
+                mat[q] = (uint8_t)last_id | (g ? 0x80 : 0x00);
+                cnt += g;
             }
-    }
-    std::vector<float> lut_eps;
-    for (uint32_t bits : keys) {
-        float v;
-        std::memcpy(&v, &bits, 4);
-        lut_eps.push_back(v);
-    }
-    std::vector<int64_t> goff(nthr + 1, 0);
-    for (int t = 0; t < nthr; ++t) goff[t + 1] = goff[t] + ngain[t];
-    std::vector<uint32_t> glist((size_t)goff[nthr]);
-    run([&](int t) {
+            ngain[t] = cnt;
+        }
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            if (++arrived == nthr) {
+                // every thread finished pass A: merge (on the last to arrive)
+                for (int r = 0; r < nthr; ++r) any_bad |= bad[r] != 0;
+                for (int r = 0; r < nthr && !dense; ++r) {
+                    dense = over[r] != 0;
+                    for (uint32_t bits : seen[r])
+                        if (!dense && find_key(keys, bits) < 0) {
+                            if (keys.size() == 128) {
+                                dense = true;
+                                break;
+                            }
+                            keys.push_back(bits);
+                        }
+                }
+                for (int r = 0; r < nthr; ++r) goff[r + 1] = goff[r] + ngain[r];
+                const size_t need = (size_t)std::max<int64_t>(goff[nthr], 1);
+                if (!any_bad && c->h_glist_cap < need) {
+                    c->h_glist.reset(new uint32_t[need]);
+                    c->h_glist_cap = need;
+                }
+                merged = true;
+                cv.notify_all();
+            } else {
+                cv.wait(lk, [&] { return merged; });
+            }
+        }
+        if (any_bad) return;
         uint8_t remap[128];
         bool identity = true;
         for (size_t q = 0; q < seen[t].size(); ++q) {
             remap[q] = dense ? 0 : (uint8_t)find_key(keys, seen[t][q]);
             identity &= remap[q] == (uint8_t)q;
         }
-        uint32_t* out = glist.data() + goff[t];
+        uint32_t* out = c->h_glist.get() + goff[t];
         for (int64_t q = chunk[t].first; q < chunk[t].second; ++q) {
             const uint8_t m = mat[q];
             if (!identity) mat[q] = (uint8_t)(remap[m & 0x7f] | (m & 0x80));
             if (m & 0x80) *out++ = (uint32_t)q;
         }
-    });
+    };
+    {
+        std::vector<std::thread> pool;
+        for (int t = 1; t < nthr; ++t) pool.emplace_back(body, t);
+        body(0);
+        for (auto& th : pool) th.join();
+    }
+    if (any_bad) return fail(c, MB_ERR_MATERIALS, "eps_r must be finite and >= 1");
+    std::vector<float> lut_eps;
+    for (uint32_t bits : keys) {
+        float v;
+        std::memcpy(&v, &bits, 4);
+        lut_eps.push_back(v);
+    }
+    const size_t n_gain = (size_t)goff[nthr];
     cudaStreamSynchronize(c->stream);
     std::vector<float> lut(256, 1.0f);
     c->h_lut_eps.assign(128, 1.0f);
@@ -654,7 +691,7 @@ int mb_set_material(mb_ctx* c, const float* eps_map, const uint8_t* gain_mask, d
         lut[128 + q] = lut_eps[q];
         c->h_lut_eps[q] = lut_eps[q];
     }
-    MB_CUDA(c, cudaMemcpy(c->d_mat, mat.get(), (size_t)N, cudaMemcpyHostToDevice));
+    MB_CUDA(c, cudaMemcpy(c->d_mat, mat, (size_t)N, cudaMemcpyHostToDevice));
     MB_CUDA(c, cudaMemcpy(c->d_lut, lut.data(), sizeof(float) * 256, cudaMemcpyHostToDevice));
     if (dense) {
         if (!c->d_inv_eps) {
@@ -670,21 +707,22 @@ int mb_set_material(mb_ctx* c, const float* eps_map, const uint8_t* gain_mask, d
     c->N_a = N_a;
     c->W_p = pump;
     // gain cells in increasing order: the Lorentz update runs over this list
-    if (glist.size() > c->glist_count || !c->d_glist) {
+    if (n_gain > c->glist_capacity || !c->d_glist) {
         if (c->d_glist) {
             cudaFree(c->d_glist);
             c->dev_bytes -= sizeof(uint32_t) * c->glist_capacity;
             c->d_glist = nullptr;
         }
-        const size_t cap = glist.empty() ? 1 : glist.size();
+        const size_t cap = n_gain ? n_gain : 1;
         cudaError_t e = cudaMalloc((void**)&c->d_glist, sizeof(uint32_t) * cap);
         if (e != cudaSuccess) { cudaGetLastError(); return fail(c, MB_ERR_OOM, "gain list allocation failed"); }
         c->glist_capacity = cap;
         c->dev_bytes += sizeof(uint32_t) * cap;
     }
-    if (!glist.empty())
-        MB_CUDA(c, cudaMemcpy(c->d_glist, glist.data(), sizeof(uint32_t) * glist.size(), cudaMemcpyHostToDevice));
-    c->glist_count = (uint32_t)glist.size();
+    if (n_gain)
+        MB_CUDA(c, cudaMemcpy(c->d_glist, c->h_glist.get(), sizeof(uint32_t) * n_gain, cudaMemcpyHostToDevice));
+    c->glist_count = (uint32_t)n_gain;
+    c->h_mat.swap(c->h_mat_next);
     // reset P, J and the populations (N0 = N_a, n1 = n2 = n3 = 0)
     MB_CUDA(c, cudaMemset(c->d_fields + 6 * N, 0, sizeof(float) * 9 * (size_t)N));
     c->have_material = true;
@@ -974,13 +1012,27 @@ int mb_flux(mb_ctx* c, double* out_flux6) {
 }
 
 int mb_flux_async(mb_ctx* c, double* host_out6) {
-    if (int rc = check_ctx(c)) return rc;
+    // the face sums are written by the field steps on the context's stream
+    // only, so this read need not wait for probes on the second stream
+    if (int rc = check_ctx_nojoin(c)) return rc;
     if (!host_out6) return fail(c, MB_ERR_ARG, "null output");
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, host_out6) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+        at.devicePointer) {
+        // page-locked host memory: the summing kernel writes it directly
+        const double f = c->dt * c->E0 * (c->E0 / c->eta0) * c->dx * c->dx;
+        mb::launch_flux_sum(c->d_flux, static_cast<double*>(at.devicePointer), f, c->stream);
+        MB_CUDA(c, cudaGetLastError());
+        return MB_OK;
+    }
+    cudaGetLastError();   // a failed attribute query leaves an error behind
     enqueue_flux_out(c);
     MB_CUDA(c, cudaMemcpyAsync(host_out6, c->d_flux_out, sizeof(double) * 6, cudaMemcpyDeviceToHost,
                                c->stream));
     return MB_OK;
 }
+
+int mb_join_probes(mb_ctx* c) { return check_ctx(c); }
 
 int mb_synchronize(mb_ctx* c) {
     if (int rc = check_ctx(c)) return rc;
@@ -1081,7 +1133,7 @@ int mb_get_field(mb_ctx* c, int which, float* host_out) {
         MB_CUDA(c, cudaMemcpyAsync(d.data(), field_ptr(c, MB_N3), 4 * N, cudaMemcpyDeviceToHost, c->stream));
         MB_CUDA(c, cudaStreamSynchronize(c->stream));
         for (int64_t q = 0; q < N; ++q)
-            host_out[q] = c->h_gain[q] ? (float)(c->N_a * (1.0 - (double)a[q] - (double)b[q] - (double)d[q])) : 0.0f;
+            host_out[q] = (c->h_mat[q] & 0x80) ? (float)(c->N_a * (1.0 - (double)a[q] - (double)b[q] - (double)d[q])) : 0.0f;
         return MB_OK;
     }
     MB_CUDA(c, cudaMemcpyAsync(tmp.data(), field_ptr(c, which), 4 * N, cudaMemcpyDeviceToHost, c->stream));

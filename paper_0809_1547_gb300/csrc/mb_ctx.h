@@ -41,7 +41,11 @@ int fail(mb_ctx* ctx, int code, const std::string& msg);
         }                                                                                     \
     } while (0)
 
+// Null check; check_ctx also orders the context's stream after the probe
+// launches mb_step may have left on the second stream (mb_step itself and
+// the face-energy read use check_ctx_nojoin).
 int check_ctx(mb_ctx* c);
+int check_ctx_nojoin(mb_ctx* c);
 // Device error flag (a bounded wait gave up): MB_ERR_TIMEOUT, flag cleared.
 int check_device_error(mb_ctx* c);
 

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <map>
+#include <memory>
 #include <string>
 #include <tuple>
 #include <utility>
@@ -222,6 +223,9 @@ cudaError_t enqueue_step(mb_ctx* c);
 // every later step runs in place; restore_single_pass undoes the switch.
 bool hold_in_place(mb_ctx* c);
 void restore_single_pass(mb_ctx* c, bool on);
+// Orders the context's stream after every probe launch that mb_step left
+// running on the second stream (event waits only; never blocks the host).
+void join_probes(mb_ctx* c);
 
 // d/dW_p of the reduced population propagator (g, G, mk of DevGain).
 void gain_pump_derivative(const mb_ctx* c, float dg[3], float dG[3][3], float dmk[3]);
@@ -302,7 +306,10 @@ struct mb_ctx {
     // material
     bool have_material = false;
     bool dense_eps = false;
-    std::vector<uint8_t> h_gain;       // gain flag per cell (for N0 read-out)
+    std::vector<uint8_t> h_mat;        // material byte per cell (bit 7: gain; N0 read-out)
+    std::vector<uint8_t> h_mat_next;   // mb_set_material's work buffer (swapped in on success)
+    std::unique_ptr<uint32_t[]> h_glist;   // mb_set_material's gain-list buffer
+    size_t h_glist_cap = 0;
     std::vector<float> h_lut_eps;      // eps_r per material id
     double N_a = 0, W_p = 0;
     uint64_t seed = 0;
@@ -334,6 +341,14 @@ struct mb_ctx {
     // with the next step (fork / join events of a captured chunk)
     cudaStream_t aux_stream = nullptr;
     std::vector<cudaEvent_t> fork_ev, join_ev;
+    // Probes of single steps (mb_step's remainder after whole chunks) are
+    // left running on the second stream: probe_pending[q] while the launch
+    // that reads copy q may still run (probe_done[q] recorded after it,
+    // probe_fork[q] orders it after its step).  The next step writing copy q
+    // waits for it; every other call joins first (join_probes).
+    bool probe_pending[2] = {false, false};
+    cudaEvent_t probe_fork[2] = {nullptr, nullptr};
+    cudaEvent_t probe_done[2] = {nullptr, nullptr};
     // per parity of the starting copy (the pointers baked into a graph)
     cudaGraphExec_t graph_chunk[2] = {nullptr, nullptr};
     cudaGraphExec_t graph_one[2] = {nullptr, nullptr};

@@ -137,17 +137,18 @@ int capture_steps(mb_ctx* c, int steps, int p, bool fused, cudaGraphExec_t* out)
     return MB_OK;
 }
 
-// The step graphs starting from copy p in the current mode (captured on
-// first use).
-int step_graphs(mb_ctx* c, int p, bool fused) {
+// The chunk and / or single-step graph starting from copy p in the current
+// mode (captured on first use; graphs of the other mode are dropped).
+int step_graphs(mb_ctx* c, int p, bool fused, bool chunk, bool one) {
     if (c->graph_fused != fused) {
         drop_graphs(c);
         c->graph_fused = fused;
     }
     int rc = MB_OK;
-    if (!c->graph_chunk[p] && (rc = capture_steps(c, c->graph_chunk_steps, p, fused, &c->graph_chunk[p])))
+    if (chunk && !c->graph_chunk[p] &&
+        (rc = capture_steps(c, c->graph_chunk_steps, p, fused, &c->graph_chunk[p])))
         return rc;
-    if (!c->graph_one[p] && (rc = capture_steps(c, 1, p, fused, &c->graph_one[p]))) return rc;
+    if (one && !c->graph_one[p] && (rc = capture_steps(c, 1, p, fused, &c->graph_one[p]))) return rc;
     return MB_OK;
 }
 
@@ -178,6 +179,44 @@ bool mb::hold_in_place(mb_ctx* c) {
 
 void mb::restore_single_pass(mb_ctx* c, bool on) { c->use_fused = on; }
 
+void mb::join_probes(mb_ctx* c) {
+    for (int q = 0; q < 2; ++q)
+        if (c->probe_pending[q]) {
+            cudaStreamWaitEvent(c->stream, c->probe_done[q], 0);
+            c->probe_pending[q] = false;
+        }
+}
+
+namespace mbi {
+
+// One single-pass step from copy p outside a graph, its probes left running
+// on the second stream: the step waits for the probes still reading the copy
+// it overwrites (those of the step before last), and its own probes read the
+// copy it writes, which the next step only reads.
+int single_step_deferred(mb_ctx* c, int p) {
+    for (int q = 0; q < 2; ++q) {
+        if (!c->probe_fork[q]) MB_CUDA(c, cudaEventCreateWithFlags(&c->probe_fork[q], cudaEventDisableTiming));
+        if (!c->probe_done[q]) MB_CUDA(c, cudaEventCreateWithFlags(&c->probe_done[q], cudaEventDisableTiming));
+    }
+    const int q = 1 - p;
+    const std::pair<mb::TmaFusedMaps, mb::TmaFusedMaps>* fm = fused_maps_for(c, c->tune_f);
+    if (!fm) return fail(c, MB_ERR_STATE, "single-pass step maps unavailable");
+    if (c->probe_pending[q]) {
+        MB_CUDA(c, cudaStreamWaitEvent(c->stream, c->probe_done[q], 0));
+        c->probe_pending[q] = false;
+    }
+    const mb::StepArgs in = view_of(c, p), out = view_of(c, q);
+    mb::launch_fused_step(in, ping_of(c, out, q), c->tune_f, p ? fm->second : fm->first, c->stream);
+    MB_CUDA(c, cudaEventRecord(c->probe_fork[q], c->stream));
+    MB_CUDA(c, cudaStreamWaitEvent(c->aux_stream, c->probe_fork[q], 0));
+    launch_probes(c, out, c->d_ctr + 2 + q, c->aux_stream);
+    MB_CUDA(c, cudaEventRecord(c->probe_done[q], c->aux_stream));
+    c->probe_pending[q] = true;
+    return MB_OK;
+}
+
+}  // namespace mbi
+
 cudaError_t mb::enqueue_step(mb_ctx* c) {
     mb::launch_h_pass(c->args, c->tune_h, tma_for(c, c->tune_h), c->stream);
     mb::launch_e_pass(c->args, c->tune_e, tma_for(c, c->tune_e), c->stream);
@@ -190,18 +229,28 @@ cudaError_t mb::enqueue_step(mb_ctx* c) {
 extern "C" {
 
 int mb_step(mb_ctx* c, int n) {
-    if (int rc = check_ctx(c)) return rc;
+    // probes of earlier single steps may keep running beside these steps
+    if (int rc = check_ctx_nojoin(c)) return rc;
     NvtxRange range("mb_step");
     if (n < 0) return fail(c, MB_ERR_ARG, "negative step count");
     if (n == 0) return MB_OK;
     const bool fused = fused_ready(c);
+    // single-pass steps outside whole chunks leave their probes on the second stream
+    const bool defer = fused && has_probes(c) && c->aux_stream;
     int p = c->parity;
     const int chunks = n / c->graph_chunk_steps, rem = n % c->graph_chunk_steps;
-    if (int rc = step_graphs(c, p, fused)) return rc;
+    if (chunks > 0 || !fused) mb::join_probes(c);
+    if (chunks > 0) {
+        if (int rc = step_graphs(c, p, fused, true, false)) return rc;
+    }
     for (int q = 0; q < chunks; ++q) MB_CUDA(c, cudaGraphLaunch(c->graph_chunk[p], c->stream));
     for (int q = 0; q < rem; ++q) {
-        if (int rc = step_graphs(c, p, fused)) return rc;
-        MB_CUDA(c, cudaGraphLaunch(c->graph_one[p], c->stream));
+        if (defer) {
+            if (int rc = single_step_deferred(c, p)) return rc;
+        } else {
+            if (int rc = step_graphs(c, p, fused, false, true)) return rc;
+            MB_CUDA(c, cudaGraphLaunch(c->graph_one[p], c->stream));
+        }
         if (fused) p = 1 - p;
     }
     MB_CUDA(c, cudaGetLastError());

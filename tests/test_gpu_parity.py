@@ -324,6 +324,41 @@ def test_nonfinite_fields_are_reported():
     g.close()
 
 
+def test_rejected_material_keeps_state():
+    """A rejected eps map (a NaN in the last host thread's chunk) changes
+    nothing: the N0 read-out and the next steps equal those of a twin that
+    never saw it; a later valid call replaces the material as usual."""
+    from paper_0809_1547_gb300 import inputs
+    from paper_0809_1547_gb300.binding import MBError, MB_ERR_MATERIALS
+    grid = (80, 64, 64)                       # 327,680 cells: two host threads
+    eps, gain = inputs.random_small(grid, seed=3, npml=4)
+    pkw = params_kw(npml=4)
+    sims = [make_pair(grid, eps, gain, 4e24, 1e13, 5, pkw)[1] for _ in range(2)]
+    g, r = sims
+    for sim in sims:
+        sim.step(6)
+    n0 = g.field("N0")
+    assert np.abs(n0).max() > 0
+    bad = eps.copy()
+    bad[60, 40, 7] = np.nan
+    with pytest.raises(MBError) as e:
+        g.set_material(bad, (1 - gain).astype(np.uint8), 2e24, 1e13)
+    assert e.value.code == MB_ERR_MATERIALS
+    np.testing.assert_array_equal(g.field("N0"), n0)
+    for sim in sims:
+        sim.step(5)
+    for name in FIELD_NAMES:
+        np.testing.assert_array_equal(g.field(name), r.field(name), err_msg=name)
+    eps2 = np.where(eps > 1.0, np.float32(6.25), np.float32(1.0))
+    for sim in sims:
+        sim.set_material(eps2, gain, 3e24, 1e13)
+        sim.step(4)
+    for name in FIELD_NAMES:
+        np.testing.assert_array_equal(g.field(name), r.field(name), err_msg=name)
+    g.close()
+    r.close()
+
+
 def test_argument_errors():
     from paper_0809_1547_gb300.binding import MBSimulation, mb_default_params, MBError, MB_ERR_ARG, \
         MB_ERR_MATERIALS

@@ -206,6 +206,73 @@ def test_flux_async_matches_flux():
     g.close()
 
 
+def test_flux_async_pinned_and_pageable():
+    """Page-locked output is written by the summing kernel directly, other
+    host memory through a copy: both equal the synchronous read."""
+    import torch
+    g = _setup((32, 20, 18), 4, seed=35)
+    g.set_single_pass((1, 32, 4, 4))
+    pinned = torch.zeros(6, dtype=torch.float64).pin_memory()
+    pageable = torch.zeros(6, dtype=torch.float64)
+    for _ in range(3):
+        g.step(3)
+        g.flux_async(pinned)
+        g.flux_async(pageable)
+        g.synchronize()
+        ref = g.flux()
+        np.testing.assert_array_equal(pinned.numpy(), ref)
+        np.testing.assert_array_equal(pageable.numpy(), ref)
+    assert np.abs(ref).max() > 0
+    g.close()
+
+
+def test_single_steps_with_deferred_probes_bitwise():
+    """Single steps leave their probe DFTs running beside the next step; reads
+    of spectra, fields and energies between them, face-energy reads after
+    every step, a save / load and an explicit join give the same bits as
+    whole chunks."""
+    import torch
+    grid, npml = (64, 20, 24), 4
+    g = _setup(grid, npml, seed=41)
+    r = _setup(grid, npml, seed=41)
+    for sim in (g, r):
+        sim.set_single_pass((1, 32, 4, 8))
+    r.step(37)
+    ref = _snapshot(r)
+    out = torch.zeros(6, dtype=torch.float64).pin_memory()
+    blob = None
+    for s in range(37):
+        g.step(1)
+        g.flux_async(out)
+        if s % 5 == 2:
+            g.probe_spectrum(0)
+            g.face_spectrum(3)
+        if s % 7 == 4:
+            g.field("Ez")
+            g.energy()
+        if s == 20:
+            blob = g.save_state()
+            g.load_state(blob)
+        if s % 6 == 1:
+            g.join_probes()
+            ev = torch.cuda.Event()
+            ev.record(torch.cuda.current_stream())
+            ev.synchronize()
+    g.synchronize()
+    _assert_same(ref, _snapshot(g), "single steps, deferred probes")
+    np.testing.assert_array_equal(out.numpy(), r.flux())
+    # from the saved state: single steps then a chunk, against the reference
+    g.load_state(blob)
+    for _ in range(3):
+        g.step(1)
+    g.step(16)                         # waits for the probes left by the single steps
+    r.load_state(blob)
+    r.step(19)
+    _assert_same(_snapshot(r), _snapshot(g), "single steps then a chunk")
+    g.close()
+    r.close()
+
+
 @pytest.mark.parametrize("grid,npml,tune", [
     ((16, 5, 3), 1, (1, 32, 4, 2)),     # narrower than a tile, ragged y, three planes
     ((32, 1, 1), 0, (1, 32, 8, 4)),     # one row, one plane, no CPML
