@@ -466,7 +466,8 @@ def bench_batched(stream, steps: int, warmup: int, n_pump: int = 16, n_seed: int
     import numpy as np
     import torch
     from paper_0809_1547_gb300 import inputs
-    from paper_0809_1547_gb300.binding import MBBatch, MBSimulation, mb_default_params
+    from paper_0809_1547_gb300.binding import MBBatch, MBSimulation, mb_default_params, \
+        MB_BATCH_PERSISTENT, MB_BATCH_CONCURRENT
     ws = inputs.workload_batch(n_pump=n_pump, n_seed=n_seed)
     p = mb_default_params(npml=ws[0].npml)
     cells = sum(int(np.prod(w.grid)) for w in ws)
@@ -489,13 +490,33 @@ def bench_batched(stream, steps: int, warmup: int, n_pump: int = 16, n_seed: int
         b.set_instance(q, w.eps, w.gain, w.N_a, w.pump, w.seed)
         b.instances[q].add_point_probe(centre(w), 128, 475e-9, 705e-9)
     if autotune:
-        b.autotune()
-    b.step(warmup)
+        b.autotune()                   # tile shape, the members' launches and the mode
+    mode = b.mode
+    # warm-up long enough to capture every graph chunk (32 steps persistent,
+    # 16 per member concurrent) outside the timed region
+    b.step(max(warmup, 32))
     b.synchronize()
     batch_ms = timed(lambda: b.step(steps))
     b.synchronize()
     tune = b.tuning()
+    if mode == MB_BATCH_CONCURRENT:
+        launches_per_call = sum(s_.launch_stats()[0] for s_ in b.instances) * steps
+        b.set_mode(MB_BATCH_PERSISTENT)
+        b.step(32)
+        b.synchronize()
+        other_ms = timed(lambda: b.step(steps))
+        b.synchronize()
+    else:
+        launches_per_call = 1
+        b.set_mode(MB_BATCH_CONCURRENT)
+        b.step(32)
+        b.synchronize()
+        other_ms = timed(lambda: b.step(steps))
+        b.synchronize()
     b.close()
+    mode_name = {MB_BATCH_PERSISTENT: "persistent", MB_BATCH_CONCURRENT: "concurrent"}
+    other = {"mode": mode_name[1 - mode], "value": round(cells * steps / (other_ms / 1e3) / 1e6, 2),
+             "unit": UNIT, "ms_per_step": round(other_ms / steps, 4)}
     if not plain:
         return {"instances": len(ws), "cells_per_step": cells, "steps": steps,
                 "value": round(cells * steps / (batch_ms / 1e3) / 1e6, 2), "unit": UNIT,
@@ -527,7 +548,8 @@ def bench_batched(stream, steps: int, warmup: int, n_pump: int = 16, n_seed: int
                         "probe (128 bins) each",
             "instances": len(ws), "cells_per_step": cells, "steps": steps, "warmup": warmup,
             "value": round(v_batch, 2), "unit": UNIT, "ms_per_step": round(batch_ms / steps, 4),
-            "launches_per_call": 1, "tile_bx_by_kz": list(tune),
+            "mode": mode_name[mode], "launches_per_call": launches_per_call,
+            "tile_bx_by_kz": list(tune), "other_mode": other,
             "plain_single_instance": {"value": round(v_plain, 2), "unit": UNIT,
                                       "ms_per_step": round(plain_ms / steps, 4),
                                       "how": "each realization's own context stepped by mb_step "

@@ -308,10 +308,16 @@ int mb_philox4x32_10(const uint32_t* ctr, const uint32_t key[2], uint32_t* out, 
  * Batched ensemble.  The paper's pump sweep ("spectra for two pumping
  * levels", Fig. 2b,c; linewidth versus pump, Fig. 5b) and disorder
  * averages need many realizations; a batch advances B of them, on grids of
- * any (uneven) sizes, together: every mb_batch_step launch runs n steps of
- * all instances in one persistent cooperative kernel (per step: all H tiles
- * and gain cells, a grid barrier, all E tiles, a grid barrier), replayed
- * from a CUDA graph.  Each instance is an ordinary context (obtained with
+ * any (uneven) sizes, together, in one of two modes.  MB_BATCH_PERSISTENT:
+ * every mb_batch_step launch runs n steps of all instances in one
+ * persistent cooperative kernel (per step: all H tiles and gain cells, a
+ * grid barrier, all E tiles, a grid barrier), replayed from a CUDA graph.
+ * MB_BATCH_CONCURRENT: each instance takes its own steps (its tuned
+ * single-context launches and graphs, as mb_step) on one of several
+ * streams that run side by side, forked from and joined back into the
+ * batch's stream; small instances then fill the GPU together.
+ * mb_batch_autotune times both and keeps the faster; the results are the
+ * same bits either way.  Each instance is an ordinary context (obtained with
  * mb_batch_instance) whose fields, probes and read-outs behave as with
  * mb_step — the fields are bit-identical to stepping the instance alone.
  * Supported inside a batch: point probes, sources, the face flux and energy;
@@ -341,9 +347,19 @@ int mb_batch_step(mb_batch* batch, int n);
 /* Wait for the batch's work; MB_ERR_TIMEOUT if a grid barrier gave up. */
 int mb_batch_synchronize(mb_batch* batch);
 
-/* Time the candidate tile shapes of the persistent kernel (states are saved
- * and restored around the trials) and keep the fastest. */
+/* Time the candidate tile shapes of the persistent kernel, tune each
+ * instance's own launches (mb_autotune), time the two modes over a few
+ * steps (states are saved and restored around every trial) and keep the
+ * fastest shape and mode. */
 int mb_batch_autotune(mb_batch* batch);
+
+#define MB_BATCH_PERSISTENT 0
+#define MB_BATCH_CONCURRENT 1
+
+/* Mode of mb_batch_step (MB_BATCH_PERSISTENT after creation).  Errors:
+ * MB_ERR_ARG (null batch or output, unknown mode). */
+int mb_batch_set_mode(mb_batch* batch, int mode);
+int mb_batch_get_mode(mb_batch* batch, int* mode);
 
 /* Tile shape of the persistent kernel: out3 = {bx, by, kz} (a block of bx x by
  * threads walks kz z-planes of one tile). */

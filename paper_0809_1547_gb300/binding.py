@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_PKG, "libmbfdtd.so")
 
 MB_OK, MB_ERR_ARG, MB_ERR_COURANT, MB_ERR_OOM, MB_ERR_MATERIALS = 0, -1, -2, -3, -4
 MB_ERR_TIMEOUT, MB_ERR_NONFINITE, MB_ERR_CUDA, MB_ERR_STATE = -5, -6, -7, -8
+MB_BATCH_PERSISTENT, MB_BATCH_CONCURRENT = 0, 1
 ERROR_NAMES = {MB_ERR_ARG: "MB_ERR_ARG", MB_ERR_COURANT: "MB_ERR_COURANT", MB_ERR_OOM: "MB_ERR_OOM",
                MB_ERR_MATERIALS: "MB_ERR_MATERIALS", MB_ERR_TIMEOUT: "MB_ERR_TIMEOUT",
                MB_ERR_NONFINITE: "MB_ERR_NONFINITE", MB_ERR_CUDA: "MB_ERR_CUDA",
@@ -104,6 +105,8 @@ _SIGS = [
     ("mb_batch_synchronize", C.c_int, [_P]),
     ("mb_batch_autotune", C.c_int, [_P]),
     ("mb_batch_get_tuning", C.c_int, [_P, C.POINTER(C.c_int)]),
+    ("mb_batch_set_mode", C.c_int, [_P, C.c_int]),
+    ("mb_batch_get_mode", C.c_int, [_P, C.POINTER(C.c_int)]),
     ("mb_gp_features", C.c_int, [_P, C.c_int, C.c_int, _P, _P, _P]),
     ("mb_selftest_bounded_waits", C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_int)]),
     ("mb_adjoint_energy_zface", C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P,
@@ -430,6 +433,18 @@ def mb_batch_get_tuning(h):
     return tuple(t)
 
 
+def mb_batch_set_mode(h, mode: int):
+    """MB_BATCH_PERSISTENT (one persistent launch per step call) or
+    MB_BATCH_CONCURRENT (the members' own launches on concurrent streams)."""
+    _check(load_library().mb_batch_set_mode(h, int(mode)))
+
+
+def mb_batch_get_mode(h) -> int:
+    m = C.c_int()
+    _check(load_library().mb_batch_get_mode(h, C.byref(m)))
+    return int(m.value)
+
+
 def mb_adjoint_energy_zface(h, n_steps, ckpt_every=200, z_plane=-1, d_grad_eps: int = 0):
     """(J, dJ/dW_p); dJ/deps_r written to the device array at d_grad_eps (if non-zero)."""
     gp = C.c_double()
@@ -634,7 +649,9 @@ class MBSimulation:
 
 class MBBatch:
     """An ensemble of realizations on grids of any sizes, advanced together by
-    one persistent launch per :meth:`step` (``mb_batch_*`` in the C ABI).
+    one persistent launch per :meth:`step`, or by the members' own launches
+    on concurrent streams (:meth:`set_mode`; :meth:`autotune` keeps the
+    faster) (``mb_batch_*`` in the C ABI).
     ``instances[b]`` is an :class:`MBSimulation` view of member b: set its
     probes and sources and read it out as usual, but step it only through the
     batch."""
@@ -689,3 +706,10 @@ class MBBatch:
 
     def tuning(self):
         return mb_batch_get_tuning(self._h)
+
+    @property
+    def mode(self):
+        return mb_batch_get_mode(self._h)
+
+    def set_mode(self, mode):
+        mb_batch_set_mode(self._h, mode)

@@ -1,9 +1,12 @@
 // C ABI of the batched ensemble: B realizations (ordinary contexts sharing
-// the batch's stream) advanced together by one persistent launch per call.
-#include "mb_host.h"
+// the batch's stream) advanced together, either by one persistent launch per
+// call or by their own launches on concurrent streams.
+#include "mb_ctx.h"
 
 #include <algorithm>
+#include <map>
 #include <string>
+#include <tuple>
 #include <vector>
 
 struct mb_batch {
@@ -30,6 +33,13 @@ struct mb_batch {
     int graph_steps = 32;
     bool graph_ok = true;
     int64_t n = 0;
+    // MB_BATCH_CONCURRENT: instance q steps on lanes[q % lanes.size()] (its
+    // own stream pointed there for the call); fork_ev / lane_ev join the
+    // lanes to the batch's stream
+    int mode = MB_BATCH_PERSISTENT;
+    std::vector<cudaStream_t> lanes;
+    std::vector<cudaEvent_t> lane_ev;
+    cudaEvent_t fork_ev = nullptr;
     std::string err;
 };
 
@@ -138,6 +148,50 @@ int rebuild(mb_batch* b) {
     return MB_OK;
 }
 
+// Streams of the concurrent mode (created on first use).
+constexpr int kLanes = 8;
+
+int ensure_lanes(mb_batch* b) {
+    if (!b->lanes.empty()) return MB_OK;
+    MB_BCUDA(b, cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming));
+    for (int l = 0; l < kLanes; ++l) {
+        cudaStream_t st = nullptr;
+        cudaEvent_t ev = nullptr;
+        MB_BCUDA(b, cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        b->lanes.push_back(st);
+        MB_BCUDA(b, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        b->lane_ev.push_back(ev);
+    }
+    return MB_OK;
+}
+
+// n steps of every instance by its own launches (as mb_step), the instances
+// spread over the lanes; the lanes start after the work already queued on
+// the batch's stream and the batch's stream waits for all of them (the
+// probes an instance leaves on its second stream included).
+int step_concurrent(mb_batch* b, int n) {
+    if (int rc = ensure_lanes(b)) return rc;
+    const int L = (int)b->lanes.size();
+    MB_BCUDA(b, cudaEventRecord(b->fork_ev, b->stream));
+    for (cudaStream_t st : b->lanes) MB_BCUDA(b, cudaStreamWaitEvent(st, b->fork_ev, 0));
+    int rc = MB_OK;
+    for (size_t q = 0; q < b->inst.size() && rc == MB_OK; ++q) {
+        mb_ctx* c = b->inst[q];
+        c->stream = b->lanes[q % L];
+        rc = mb_step(c, n);
+        if (rc == MB_OK) mb::join_probes(c);
+        c->stream = b->stream;
+        if (rc) rc = bfail(b, rc, mb_last_error(c));
+    }
+    for (int l = 0; l < L; ++l) {
+        cudaEventRecord(b->lane_ev[l], b->lanes[l]);
+        cudaStreamWaitEvent(b->stream, b->lane_ev[l], 0);
+    }
+    if (rc) return rc;
+    MB_BCUDA(b, cudaGetLastError());
+    return MB_OK;
+}
+
 int check_lockstep(mb_batch* b) {
     for (mb_ctx* c : b->inst)
         if (c->n != b->n)
@@ -197,6 +251,12 @@ int mb_batch_create(mb_batch** out, int B, const int* grids, double dx, double d
 int mb_batch_destroy(mb_batch* b) {
     if (!b) return MB_OK;
     if (b->stream) cudaStreamSynchronize(b->stream);
+    for (cudaStream_t st : b->lanes) {
+        cudaStreamSynchronize(st);
+        cudaStreamDestroy(st);
+    }
+    for (cudaEvent_t ev : b->lane_ev) cudaEventDestroy(ev);
+    if (b->fork_ev) cudaEventDestroy(b->fork_ev);
     free_arrays(b);
     for (mb_ctx* c : b->inst) mb_destroy(c);
     void* bufs[] = {b->d_bar, b->d_err, b->d_ctr, b->d_tick};
@@ -231,6 +291,11 @@ int mb_batch_step(mb_batch* b, int n) {
     if (int rc = check_lockstep(b)) return rc;
     if (b->dirty)
         if (int rc = rebuild(b)) return rc;
+    if (b->mode == MB_BATCH_CONCURRENT) {
+        const int rc = step_concurrent(b, n);   // advances each instance's count
+        if (rc == MB_OK) b->n += n;
+        return rc;
+    }
     // the batch counter follows the instances' own step count
     const long long n0 = (long long)b->n;
     MB_BCUDA(b, cudaMemcpyAsync(b->d_ctr, &n0, sizeof(long long), cudaMemcpyHostToDevice, b->stream));
@@ -271,6 +336,8 @@ int mb_batch_step(mb_batch* b, int n) {
 int mb_batch_synchronize(mb_batch* b) {
     if (!b) return bfail(nullptr, MB_ERR_ARG, "null batch");
     MB_BCUDA(b, cudaStreamSynchronize(b->stream));
+    for (mb_ctx* c : b->inst)   // bounded waits of the instances' own launches
+        if (int rc = mbi::check_device_error(c)) return bfail(b, rc, mb_last_error(c));
     int e = 0;
     MB_BCUDA(b, cudaMemcpy(&e, b->d_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (e) {
@@ -324,21 +391,88 @@ int mb_batch_autotune(mb_batch* b) {
             pick = cd;
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    {
+    auto restore_all = [&]() {
         const char* o = backup;
         for (mb_ctx* c : b->inst) {
             mb::state_restore(c, o);
             o += mb::state_device_bytes(c);
         }
-    }
-    cudaStreamSynchronize(b->stream);
-    cudaFree(backup);
+    };
     b->block = pick.block;
     b->kz = pick.kz;
+    // The instances' own launch shapes (tuned once per grid shape and CPML
+    // depth in the process), then each mode from the same state: a warm-up
+    // of 2 steps (graph captures) and 4 timed steps; even counts, so a
+    // single-pass instance ends in the copy it started from.
+    int rc = MB_OK;
+    {
+        std::map<std::tuple<int, int, int>, mb_ctx*> tuned;   // one trial set per grid shape
+        for (mb_ctx* c : b->inst) {
+            if (rc) break;
+            auto it = tuned.find({c->nx, c->ny, c->nz});
+            if (it == tuned.end()) {
+                if ((rc = mb_autotune(c))) rc = bfail(b, rc, mb_last_error(c));
+                tuned[{c->nx, c->ny, c->nz}] = c;
+            } else {
+                const mb_ctx* t = it->second;
+                c->tune_h = t->tune_h;
+                c->tune_e = t->tune_e;
+                c->tune_f = t->tune_f;
+                c->use_fused = t->use_fused;
+                mbi::drop_graphs(c);
+            }
+        }
+    }
+    std::vector<int64_t> n_keep, l_keep;
+    for (mb_ctx* c : b->inst) {
+        n_keep.push_back(c->n);
+        l_keep.push_back(c->launches);
+    }
+    float t_mode[2] = {1e30f, 1e30f};
+    for (int m = 0; m < 2 && rc == MB_OK; ++m) {
+        restore_all();
+        bool ok;
+        if (m == MB_BATCH_PERSISTENT) {
+            ok = rebuild(b) == MB_OK &&
+                 cudaMemcpyAsync(b->d_ctr, &n0, sizeof(long long), cudaMemcpyHostToDevice, b->stream) ==
+                     cudaSuccess &&
+                 launch_steps(b, 2) == MB_OK && cudaEventRecord(e0, b->stream) == cudaSuccess &&
+                 launch_steps(b, 4) == MB_OK;
+        } else {
+            ok = step_concurrent(b, 2) == MB_OK && cudaEventRecord(e0, b->stream) == cudaSuccess &&
+                 step_concurrent(b, 4) == MB_OK;
+        }
+        if (ok && cudaEventRecord(e1, b->stream) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess)
+            cudaEventElapsedTime(&t_mode[m], e0, e1);
+    }
+    for (size_t q = 0; q < b->inst.size(); ++q) {
+        b->inst[q]->n = n_keep[q];
+        b->inst[q]->launches = l_keep[q];
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    restore_all();
+    cudaStreamSynchronize(b->stream);
+    cudaFree(backup);
+    if (rc) return rc;
+    b->mode = t_mode[MB_BATCH_CONCURRENT] < t_mode[MB_BATCH_PERSISTENT] ? MB_BATCH_CONCURRENT
+                                                                         : MB_BATCH_PERSISTENT;
     b->dirty = true;
     MB_BCUDA(b, cudaGetLastError());
+    return MB_OK;
+}
+
+int mb_batch_set_mode(mb_batch* b, int mode) {
+    if (!b) return bfail(nullptr, MB_ERR_ARG, "null batch");
+    if (mode != MB_BATCH_PERSISTENT && mode != MB_BATCH_CONCURRENT)
+        return bfail(b, MB_ERR_ARG, "mode must be MB_BATCH_PERSISTENT or MB_BATCH_CONCURRENT");
+    b->mode = mode;
+    return MB_OK;
+}
+
+int mb_batch_get_mode(mb_batch* b, int* mode) {
+    if (!b || !mode) return bfail(b, MB_ERR_ARG, "null argument");
+    *mode = b->mode;
     return MB_OK;
 }
 

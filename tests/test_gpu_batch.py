@@ -147,3 +147,45 @@ def test_batch_rejects_out_of_lockstep_member():
         b.step(1)
     assert e.value.code == MB_ERR_STATE
     b.close()
+
+
+def test_batch_concurrent_mode_equals_persistent_bitwise():
+    """The members' own launches on concurrent streams give the bits of the
+    persistent launch, across graph chunks, tails and a mode switch between
+    calls; one member takes the single-pass step."""
+    from paper_0809_1547_gb300.binding import MB_BATCH_PERSISTENT, MB_BATCH_CONCURRENT, MBError, \
+        MB_ERR_ARG
+    pkw = params_kw(npml=4)
+    grids = GRIDS + [(48, 20, 18)]
+    members = _members(grids, 4)
+    a, c, d = (_batch(members, pkw) for _ in range(3))
+    assert a.mode == MB_BATCH_PERSISTENT
+    c.set_mode(MB_BATCH_CONCURRENT)
+    assert c.mode == MB_BATCH_CONCURRENT
+    c.instances[len(grids) - 1].set_single_pass((1, 32, 4, 8))
+    a.step(37)
+    c.step(37)
+    d.step(20)
+    d.set_mode(MB_BATCH_CONCURRENT)
+    d.step(17)
+    for bt in (a, c, d):
+        bt.synchronize()
+    for q in range(len(members)):
+        for other in (c, d):
+            inst = other.instances[q]
+            assert inst.n == 37
+            _assert_same(a.instances[q], inst, q)
+            if q % 2 == 0:
+                np.testing.assert_array_equal(inst.probe_spectrum(0)[0], a.instances[q].probe_spectrum(0)[0])
+            U_a, fl_a = a.instances[q].energy()
+            U_o, fl_o = inst.energy()
+            assert U_o == U_a
+            # the face flux adds FP32 per-warp partials, grouped by the tile
+            # shape (the members' own launch shapes here, the persistent
+            # kernel's there), into FP64 slots: equal to FP32 rounding
+            assert np.abs(fl_o - fl_a).max() <= 1e-6 * max(np.abs(fl_a).max(), 1e-300)
+    with pytest.raises(MBError) as e:
+        c.set_mode(7)
+    assert e.value.code == MB_ERR_ARG
+    for bt in (a, c, d):
+        bt.close()
