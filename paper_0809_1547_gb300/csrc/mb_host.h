@@ -165,7 +165,8 @@ void launch_point_dft(const DevPointProbes& pp, const DevFields& f, const long l
                       double dt, cudaStream_t s);
 void launch_face_dft(const DevFaceProbes& fp, const DevFields& f, const DevGrid& g,
                      const long long* ctr, double dt, cudaStream_t s);
-// Batched ensemble: instances advanced together by one persistent launch.
+// Batched ensemble, persistent mode: instances advanced together by one
+// persistent launch.
 // Work items (int4): x = instance, y = kind (0 H tile, 1 gain chunk, 2 E
 // tile), z = tile / chunk index.
 struct BatchArgs {

@@ -1,11 +1,13 @@
-"""Batched ensemble (one persistent launch over many realizations) against
-single-context stepping and the oracle.
+"""Batched ensemble (one persistent launch over many realizations, or the
+members' own launches on concurrent streams) against single-context
+stepping and the oracle.
 
 The batched kernel reuses the single path's per-cell updates, so every
 member's fields must equal, bit for bit, the same realization stepped alone;
 its point spectra too (each bin accumulates the same terms in the same
 order).  The face flux sums FP64 atomics in another order: 1e-9 relative.
-One member is also checked directly against the FP64 oracle.
+The two modes give the same bits.  One member is also checked directly
+against the FP64 oracle.
 """
 import numpy as np
 import pytest
