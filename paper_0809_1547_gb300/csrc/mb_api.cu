@@ -13,6 +13,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <new>
 #include <thread>
 
 using mb::kC0;
@@ -589,7 +590,7 @@ int mb_set_material(mb_ctx* c, const float* eps_map, const uint8_t* gain_mask, d
         return -1;
     };
     std::vector<uint32_t> keys;
-    bool dense = false, any_bad = false;
+    bool dense = false, any_bad = false, no_mem = false;
     std::mutex mu;
     std::condition_variable cv;
     int arrived = 0;
@@ -646,8 +647,9 @@ int mb_set_material(mb_ctx* c, const float* eps_map, const uint8_t* gain_mask, d
                 for (int r = 0; r < nthr; ++r) goff[r + 1] = goff[r] + ngain[r];
                 const size_t need = (size_t)std::max<int64_t>(goff[nthr], 1);
                 if (!any_bad && c->h_glist_cap < need) {
-                    c->h_glist.reset(new uint32_t[need]);
-                    c->h_glist_cap = need;
+                    c->h_glist.reset(new (std::nothrow) uint32_t[need]);
+                    c->h_glist_cap = c->h_glist ? need : 0;
+                    no_mem = !c->h_glist;
                 }
                 merged = true;
                 cv.notify_all();
@@ -655,7 +657,7 @@ int mb_set_material(mb_ctx* c, const float* eps_map, const uint8_t* gain_mask, d
                 cv.wait(lk, [&] { return merged; });
             }
         }
-        if (any_bad) return;
+        if (any_bad || no_mem) return;
         uint8_t remap[128];
         bool identity = true;
         for (size_t q = 0; q < seen[t].size(); ++q) {
@@ -676,6 +678,7 @@ int mb_set_material(mb_ctx* c, const float* eps_map, const uint8_t* gain_mask, d
         for (auto& th : pool) th.join();
     }
     if (any_bad) return fail(c, MB_ERR_MATERIALS, "eps_r must be finite and >= 1");
+    if (no_mem) return fail(c, MB_ERR_OOM, "host gain-list buffer allocation failed");
     std::vector<float> lut_eps;
     for (uint32_t bits : keys) {
         float v;
