@@ -601,30 +601,64 @@ int mb_set_material(mb_ctx* c, const float* eps_map, const uint8_t* gain_mask, d
             uint32_t last = 0;
             int last_id = -1;
             int64_t cnt = 0;
-            for (int64_t q = chunk[t].first; q < chunk[t].second; ++q) {
-                const float v = eps_map[q];
-                if (!(v >= 1.0f) || !std::isfinite(v)) {
-                    bad[t] = 1;
-                    break;
-                }
-                uint32_t bits;
-                std::memcpy(&bits, &v, 4);
-                if (last_id < 0 || bits != last) {
-                    last = bits;
-                    last_id = find_key(tk, bits);
-                    if (last_id < 0) {
-                        if (tk.size() < 128) {
-                            last_id = (int)tk.size();
-                            tk.push_back(bits);
-                        } else {
-                            over[t] = 1;   // more than 128 values: dense map
-                            last_id = 0;
-                        }
+            const int64_t end = chunk[t].second;
+            const unsigned gon = gain_on ? 1u : 0u;
+            for (int64_t q0 = chunk[t].first; q0 < end && !bad[t];) {
+                // Blocks of 64 cells whose values are all among the (at most
+                // four) already seen go through a branch-free loop the
+                // compiler vectorizes; a block with a new or invalid value
+                // takes the per-cell loop below.
+                if (q0 + 64 <= end && tk.size() <= 4) {
+                    uint32_t k[4] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu};
+                    for (size_t u = 0; u < tk.size(); ++u) k[u] = tk[u];
+                    const float* __restrict__ ep = eps_map + q0;
+                    const uint8_t* __restrict__ gp = gain_mask + q0;
+                    uint8_t* __restrict__ mp = mat + q0;
+                    unsigned all = 1, ok = 1, gc = 0;
+                    for (int u = 0; u < 64; ++u) {
+                        uint32_t b;
+                        std::memcpy(&b, ep + u, 4);
+                        // 1 <= eps_r <= FLT_MAX: sign clear, 0x3f800000 <= bits < 0x7f800000
+                        ok &= (b - 0x3f800000u) < 0x40000000u;
+                        const unsigned m1 = b == k[1], m2 = b == k[2], m3 = b == k[3];
+                        all &= (b == k[0]) | m1 | m2 | m3;
+                        const unsigned g = gon & (gp[u] != 0);
+                        mp[u] = (uint8_t)((m1 + 2 * m2 + 3 * m3) | (g << 7));
+                        gc += g;
+                    }
+                    if (ok && all) {
+                        cnt += gc;
+                        q0 += 64;
+                        continue;
                     }
                 }
-                const bool g = gain_on && gain_mask[q] != 0;
-                mat[q] = (uint8_t)last_id | (g ? 0x80 : 0x00);
-                cnt += g;
+                const int64_t qe = std::min<int64_t>(end, q0 + 64);
+                for (int64_t q = q0; q < qe; ++q) {
+                    const float v = eps_map[q];
+                    if (!(v >= 1.0f) || !std::isfinite(v)) {
+                        bad[t] = 1;
+                        break;
+                    }
+                    uint32_t bits;
+                    std::memcpy(&bits, &v, 4);
+                    if (last_id < 0 || bits != last) {
+                        last = bits;
+                        last_id = find_key(tk, bits);
+                        if (last_id < 0) {
+                            if (tk.size() < 128) {
+                                last_id = (int)tk.size();
+                                tk.push_back(bits);
+                            } else {
+                                over[t] = 1;   // more than 128 values: dense map
+                                last_id = 0;
+                            }
+                        }
+                    }
+                    const bool g = gain_on && gain_mask[q] != 0;
+                    mat[q] = (uint8_t)last_id | (g ? 0x80 : 0x00);
+                    cnt += g;
+                }
+                q0 = qe;
             }
             ngain[t] = cnt;
         }
@@ -664,11 +698,17 @@ int mb_set_material(mb_ctx* c, const float* eps_map, const uint8_t* gain_mask, d
             remap[q] = dense ? 0 : (uint8_t)find_key(keys, seen[t][q]);
             identity &= remap[q] == (uint8_t)q;
         }
+        if (!identity)
+            for (int64_t q = chunk[t].first; q < chunk[t].second; ++q)
+                mat[q] = (uint8_t)(remap[mat[q] & 0x7f] | (mat[q] & 0x80));
+        // gain cells in order, without a branch per cell: every index is
+        // written and the position advances on gain cells; the loop ends when
+        // the thread's segment is full, so no write leaves it
         uint32_t* out = c->h_glist.get() + goff[t];
-        for (int64_t q = chunk[t].first; q < chunk[t].second; ++q) {
-            const uint8_t m = mat[q];
-            if (!identity) mat[q] = (uint8_t)(remap[m & 0x7f] | (m & 0x80));
-            if (m & 0x80) *out++ = (uint32_t)q;
+        uint32_t* const out_end = c->h_glist.get() + goff[t + 1];
+        for (int64_t q = chunk[t].first; q < chunk[t].second && out < out_end; ++q) {
+            *out = (uint32_t)q;
+            out += mat[q] >> 7;
         }
     };
     {

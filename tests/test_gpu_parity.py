@@ -324,6 +324,32 @@ def test_nonfinite_fields_are_reported():
     g.close()
 
 
+def test_material_values_in_runs_parity():
+    """Six eps_r values in runs of random length (so 64-cell blocks see one,
+    several or a new value, and the value table outgrows four entries part
+    way through), over two host threads' chunks: 12 steps within the bound
+    of the oracle."""
+    grid = (80, 64, 64)                       # 327,680 cells: two host threads
+    rng = np.random.default_rng(77)
+    n = grid[0] * grid[1] * grid[2]
+    vals = np.array([1.0, 8.41, 2.25, 1.0, 5.5, 3.1, 6.25, 8.41], np.float32)
+    lens = rng.integers(1, 200, size=n // 20)
+    idx = np.repeat(rng.integers(0, 3, size=lens.size), lens)[:n]
+    idx[n // 3:] = np.repeat(rng.integers(0, len(vals), size=lens.size), lens)[:n - n // 3]
+    eps = vals[idx].reshape(grid[::-1])
+    gain = (rng.random(grid[::-1]) < 0.5).astype(np.uint8)
+    pkw = params_kw(npml=4)
+    o, g = make_pair(grid, eps, gain, 4e24, 1e13, 9, pkw)
+    g.set_source((40, 32, 32), 2, 532e-9, 1.0e-15, 0.4e-15, 1e9)
+    o.add_source((40, 32, 32), 2, 532e-9, 1.0e-15, 0.4e-15, 1e9)
+    g.step(12)
+    o.step(12)
+    assert_fields_match(o, g)
+    n0 = g.field("N0")
+    assert np.array_equal(n0 != 0, gain != 0)
+    g.close()
+
+
 def test_rejected_material_keeps_state():
     """A rejected eps map (a NaN in the last host thread's chunk) changes
     nothing: the N0 read-out and the next steps equal those of a twin that
