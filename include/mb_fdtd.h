@@ -298,6 +298,20 @@ void mb_debug_fail_alloc(int n);
 /* Device bytes the context holds. */
 int mb_device_bytes(mb_ctx* ctx, size_t* bytes);
 
+/* Diagnostic (host only, no device work): the material map mb_set_material
+ * builds from eps_map and gain_mask (host, n cells each), with at most
+ * max_threads host threads.  out_mat (n bytes): bits 0..6 the id of the
+ * cell's eps_r value (ids in order of first appearance), bit 7 set for a gain
+ * cell when gain_on; out_glist (capacity n): the gain cells' indices in
+ * increasing order, out_n_gain of them; out_lut_eps (capacity 128): the
+ * distinct values in id order, out_n_values of them; *out_dense = 1 when there
+ * are more than 128 values (every id 0, no values listed).  Errors:
+ * MB_ERR_ARG (null pointer, n < 1), MB_ERR_MATERIALS (a value not finite or
+ * below 1), MB_ERR_OOM. */
+int mb_material_map(const float* eps_map, const uint8_t* gain_mask, int64_t n, int gain_on,
+                    int max_threads, uint8_t* out_mat, uint32_t* out_glist, int64_t* out_n_gain,
+                    float* out_lut_eps, int* out_n_values, int* out_dense);
+
 /* Diagnostic: evaluate the device's Philox4x32-10 (the generator of the
  * Langevin force, Salmon et al. SC'11) on n counters.  ctr (host, 4n words),
  * key (host, 2 words), out (host, 4n words).  Runs one kernel on the current

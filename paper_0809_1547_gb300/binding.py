@@ -94,6 +94,8 @@ _SIGS = [
     ("mb_launch_stats", C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int64)]),
     ("mb_device_bytes", C.c_int, [_P, C.POINTER(C.c_size_t)]),
     ("mb_philox4x32_10", C.c_int, [_P, _P, _P, C.c_int]),
+    ("mb_material_map", C.c_int, [_P, _P, C.c_int64, C.c_int, C.c_int, _P, _P, C.POINTER(C.c_int64),
+                                  _P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     ("mb_energy_sum_noalloc", C.c_int, [_P, _P, _P, _P, _P, _P, _P, C.c_int64, _P, _P]),
     ("mb_batch_create", C.c_int, [C.POINTER(_P), C.c_int, C.POINTER(C.c_int), C.c_double,
                                   C.c_double, C.POINTER(mb_params), _P]),
@@ -253,6 +255,23 @@ def mb_flux_async(h, out_ptr: int):
 def mb_debug_fail_alloc(n: int):
     """Test hook: make the n-th device allocation from now on fail (n < 0: off)."""
     load_library().mb_debug_fail_alloc(int(n))
+
+
+def mb_material_map(eps_map, gain_mask, gain_on=True, max_threads=16):
+    """Host-only diagnostic: (material bytes, gain-cell indices, distinct
+    eps_r values in id order, dense flag) as mb_set_material builds them."""
+    eps = np.ascontiguousarray(eps_map, dtype=np.float32).reshape(-1)
+    gm = np.ascontiguousarray(gain_mask, dtype=np.uint8).reshape(-1)
+    if eps.size != gm.size or eps.size < 1:
+        raise ValueError("eps_map and gain_mask must have the same, non-zero size")
+    mat = np.empty(eps.size, np.uint8)
+    glist = np.empty(eps.size, np.uint32)
+    lut = np.empty(128, np.float32)
+    ng, nv, dense = C.c_int64(), C.c_int(), C.c_int()
+    _check(load_library().mb_material_map(_ptr(eps), _ptr(gm), eps.size, int(bool(gain_on)),
+                                          int(max_threads), _ptr(mat), _ptr(glist), C.byref(ng),
+                                          _ptr(lut), C.byref(nv), C.byref(dense)))
+    return mat, glist[:ng.value].copy(), lut[:nv.value].copy(), bool(dense.value)
 
 
 def mb_synchronize(h):

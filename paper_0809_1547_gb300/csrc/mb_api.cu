@@ -384,6 +384,184 @@ int mb::state_restore(mb_ctx* c, const void* d_src) {
     return MB_OK;
 }
 
+namespace mbi {
+
+// Host side of mb_set_material (no device work): the material byte of each
+// of the N cells (bits 0..6: id of its eps_r value, bit 7: gain cell when
+// gain_on) into mat, the gain cells' indices in increasing order into glist
+// (grown to glist_cap entries as needed, not zeroed), the distinct values in
+// id order into lut_eps (empty when dense: more than 128 values, every id 0),
+// and their count into n_gain.  Returns MB_OK, MB_ERR_MATERIALS (a value not
+// finite or below 1; mat is then partly written) or MB_ERR_OOM.
+int map_materials(const float* eps_map, const uint8_t* gain_mask, int64_t N, bool gain_on,
+                  int max_threads, uint8_t* mat, std::unique_ptr<uint32_t[]>& glist, size_t& glist_cap,
+                  std::vector<float>& lut_eps, bool& dense, size_t& n_gain) {
+    // Material ids by the bit pattern of eps_r: up to 128 distinct values
+    // share a LUT, more switch to a dense 1/eps map.  One pool of host
+    // threads over chunks of cells, two passes with a barrier between.
+    // Pass A: each thread validates its cells, gives them ids in a table of
+    // its own (a packing holds a few values in long runs: the last value is
+    // checked first, then the short table), sets the gain bit and counts its
+    // gain cells.  Thread 0 then merges the tables in chunk order (ids =
+    // order of first appearance) and places the threads' gain-list segments.
+    // Pass B: each thread maps its ids to the merged ones and writes its gain
+    // cells, in increasing order, into its segment.
+    const int nthr = (int)std::max<int64_t>(1, std::min<int64_t>(
+        {(int64_t)std::max(1u, std::thread::hardware_concurrency()), (int64_t)std::max(1, max_threads),
+         N / (1 << 18) + 1}));
+    std::vector<std::pair<int64_t, int64_t>> chunk(nthr);
+    for (int t = 0; t < nthr; ++t) chunk[t] = {N * t / nthr, N * (t + 1) / nthr};
+    std::vector<std::vector<uint32_t>> seen(nthr);
+    std::vector<char> bad(nthr, 0), over(nthr, 0);
+    std::vector<int64_t> ngain(nthr, 0), goff(nthr + 1, 0);
+    auto find_key = [](const std::vector<uint32_t>& keys, uint32_t bits) -> int {
+        for (size_t t = 0; t < keys.size(); ++t)
+            if (keys[t] == bits) return (int)t;
+        return -1;
+    };
+    std::vector<uint32_t> keys;
+    bool any_bad = false, no_mem = false;
+    dense = false;
+    std::mutex mu;
+    std::condition_variable cv;
+    int arrived = 0;
+    bool merged = false;
+    auto body = [&](int t) {
+        {
+            std::vector<uint32_t>& tk = seen[t];
+            uint32_t last = 0;
+            int last_id = -1;
+            int64_t cnt = 0;
+            const int64_t end = chunk[t].second;
+            const unsigned gon = gain_on ? 1u : 0u;
+            for (int64_t q0 = chunk[t].first; q0 < end && !bad[t];) {
+                // Blocks of 64 cells whose values are all among the (at most
+                // four) already seen go through a branch-free loop the
+                // compiler vectorizes; a block with a new or invalid value
+                // takes the per-cell loop below.
+                if (q0 + 64 <= end && tk.size() <= 4) {
+                    uint32_t k[4] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu};
+                    for (size_t u = 0; u < tk.size(); ++u) k[u] = tk[u];
+                    const float* __restrict__ ep = eps_map + q0;
+                    const uint8_t* __restrict__ gp = gain_mask + q0;
+                    uint8_t* __restrict__ mp = mat + q0;
+                    unsigned all = 1, ok = 1, gc = 0;
+                    for (int u = 0; u < 64; ++u) {
+                        uint32_t b;
+                        std::memcpy(&b, ep + u, 4);
+                        // 1 <= eps_r <= FLT_MAX: sign clear, 0x3f800000 <= bits < 0x7f800000
+                        ok &= (b - 0x3f800000u) < 0x40000000u;
+                        const unsigned m1 = b == k[1], m2 = b == k[2], m3 = b == k[3];
+                        all &= (b == k[0]) | m1 | m2 | m3;
+                        const unsigned g = gon & (gp[u] != 0);
+                        mp[u] = (uint8_t)((m1 + 2 * m2 + 3 * m3) | (g << 7));
+                        gc += g;
+                    }
+                    if (ok && all) {
+                        cnt += gc;
+                        q0 += 64;
+                        continue;
+                    }
+                }
+                const int64_t qe = std::min<int64_t>(end, q0 + 64);
+                for (int64_t q = q0; q < qe; ++q) {
+                    const float v = eps_map[q];
+                    if (!(v >= 1.0f) || !std::isfinite(v)) {
+                        bad[t] = 1;
+                        break;
+                    }
+                    uint32_t bits;
+                    std::memcpy(&bits, &v, 4);
+                    if (last_id < 0 || bits != last) {
+                        last = bits;
+                        last_id = find_key(tk, bits);
+                        if (last_id < 0) {
+                            if (tk.size() < 128) {
+                                last_id = (int)tk.size();
+                                tk.push_back(bits);
+                            } else {
+                                over[t] = 1;   // more than 128 values: dense map
+                                last_id = 0;
+                            }
+                        }
+                    }
+                    const bool g = gain_on && gain_mask[q] != 0;
+                    mat[q] = (uint8_t)last_id | (g ? 0x80 : 0x00);
+                    cnt += g;
+                }
+                q0 = qe;
+            }
+            ngain[t] = cnt;
+        }
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            if (++arrived == nthr) {
+                // every thread finished pass A: merge (on the last to arrive)
+                for (int r = 0; r < nthr; ++r) any_bad |= bad[r] != 0;
+                for (int r = 0; r < nthr && !dense; ++r) {
+                    dense = over[r] != 0;
+                    for (uint32_t bits : seen[r])
+                        if (!dense && find_key(keys, bits) < 0) {
+                            if (keys.size() == 128) {
+                                dense = true;
+                                break;
+                            }
+                            keys.push_back(bits);
+                        }
+                }
+                for (int r = 0; r < nthr; ++r) goff[r + 1] = goff[r] + ngain[r];
+                const size_t need = (size_t)std::max<int64_t>(goff[nthr], 1);
+                if (!any_bad && glist_cap < need) {
+                    glist.reset(new (std::nothrow) uint32_t[need]);
+                    glist_cap = glist ? need : 0;
+                    no_mem = !glist;
+                }
+                merged = true;
+                cv.notify_all();
+            } else {
+                cv.wait(lk, [&] { return merged; });
+            }
+        }
+        if (any_bad || no_mem) return;
+        uint8_t remap[128];
+        bool identity = true;
+        for (size_t q = 0; q < seen[t].size(); ++q) {
+            remap[q] = dense ? 0 : (uint8_t)find_key(keys, seen[t][q]);
+            identity &= remap[q] == (uint8_t)q;
+        }
+        if (!identity)
+            for (int64_t q = chunk[t].first; q < chunk[t].second; ++q)
+                mat[q] = (uint8_t)(remap[mat[q] & 0x7f] | (mat[q] & 0x80));
+        // gain cells in order, without a branch per cell: every index is
+        // written and the position advances on gain cells; the loop ends when
+        // the thread's segment is full, so no write leaves it
+        uint32_t* out = glist.get() + goff[t];
+        uint32_t* const out_end = glist.get() + goff[t + 1];
+        for (int64_t q = chunk[t].first; q < chunk[t].second && out < out_end; ++q) {
+            *out = (uint32_t)q;
+            out += mat[q] >> 7;
+        }
+    };
+    {
+        std::vector<std::thread> pool;
+        for (int t = 1; t < nthr; ++t) pool.emplace_back(body, t);
+        body(0);
+        for (auto& th : pool) th.join();
+    }
+    if (any_bad) return MB_ERR_MATERIALS;
+    if (no_mem) return MB_ERR_OOM;
+    lut_eps.clear();
+    for (uint32_t bits : keys) {
+        float v;
+        std::memcpy(&v, &bits, 4);
+        lut_eps.push_back(v);
+    }
+    n_gain = (size_t)goff[nthr];
+    return MB_OK;
+}
+
+}  // namespace mbi
+
 extern "C" {
 
 void mb_default_params(mb_params* p) {
@@ -562,170 +740,22 @@ int mb_set_material(mb_ctx* c, const float* eps_map, const uint8_t* gain_mask, d
     if (!(N_a >= 0) || !(pump >= 0) || !std::isfinite(N_a) || !std::isfinite(pump))
         return fail(c, MB_ERR_ARG, "N_a and pump must be finite and >= 0");
     const int64_t N = c->ncell;
-    // Material ids by the bit pattern of eps_r: up to 128 distinct values
-    // share a LUT, more switch to a dense 1/eps map.  One pool of host
-    // threads over chunks of cells, two passes with a barrier between.
-    // Pass A: each thread validates its cells, gives them ids in a table of
-    // its own (a packing holds a few values in long runs: the last value is
-    // checked first, then the short table), sets the gain bit and counts its
-    // gain cells.  Thread 0 then merges the tables in chunk order (ids =
-    // order of first appearance) and places the threads' gain-list segments.
-    // Pass B: each thread maps its ids to the merged ones and writes its gain
-    // cells, in increasing order, into its segment.  The material bytes and
-    // the list go to buffers the context keeps (allocated once, not zeroed);
-    // the material bytes replace the host copy only when every check passed.
-    const bool gain_on = N_a > 0.0;
-    const int nthr = (int)std::max<int64_t>(1, std::min<int64_t>(
-        {(int64_t)std::max(1u, std::thread::hardware_concurrency()), 16, N / (1 << 18) + 1}));
-    std::vector<std::pair<int64_t, int64_t>> chunk(nthr);
-    for (int t = 0; t < nthr; ++t) chunk[t] = {N * t / nthr, N * (t + 1) / nthr};
-    std::vector<std::vector<uint32_t>> seen(nthr);
-    std::vector<char> bad(nthr, 0), over(nthr, 0);
-    std::vector<int64_t> ngain(nthr, 0), goff(nthr + 1, 0);
     if (c->h_mat_next.size() != (size_t)N) c->h_mat_next.resize((size_t)N);
     uint8_t* mat = c->h_mat_next.data();
-    auto find_key = [](const std::vector<uint32_t>& keys, uint32_t bits) -> int {
-        for (size_t t = 0; t < keys.size(); ++t)
-            if (keys[t] == bits) return (int)t;
-        return -1;
-    };
-    std::vector<uint32_t> keys;
-    bool dense = false, any_bad = false, no_mem = false;
-    std::mutex mu;
-    std::condition_variable cv;
-    int arrived = 0;
-    bool merged = false;
-    auto body = [&](int t) {
-        {
-            std::vector<uint32_t>& tk = seen[t];
-            uint32_t last = 0;
-            int last_id = -1;
-            int64_t cnt = 0;
-            const int64_t end = chunk[t].second;
-            const unsigned gon = gain_on ? 1u : 0u;
-            for (int64_t q0 = chunk[t].first; q0 < end && !bad[t];) {
-                // Blocks of 64 cells whose values are all among the (at most
-                // four) already seen go through a branch-free loop the
-                // compiler vectorizes; a block with a new or invalid value
-                // takes the per-cell loop below.
-                if (q0 + 64 <= end && tk.size() <= 4) {
-                    uint32_t k[4] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu};
-                    for (size_t u = 0; u < tk.size(); ++u) k[u] = tk[u];
-                    const float* __restrict__ ep = eps_map + q0;
-                    const uint8_t* __restrict__ gp = gain_mask + q0;
-                    uint8_t* __restrict__ mp = mat + q0;
-                    unsigned all = 1, ok = 1, gc = 0;
-                    for (int u = 0; u < 64; ++u) {
-                        uint32_t b;
-                        std::memcpy(&b, ep + u, 4);
-                        // 1 <= eps_r <= FLT_MAX: sign clear, 0x3f800000 <= bits < 0x7f800000
-                        ok &= (b - 0x3f800000u) < 0x40000000u;
-                        const unsigned m1 = b == k[1], m2 = b == k[2], m3 = b == k[3];
-                        all &= (b == k[0]) | m1 | m2 | m3;
-                        const unsigned g = gon & (gp[u] != 0);
-                        mp[u] = (uint8_t)((m1 + 2 * m2 + 3 * m3) | (g << 7));
-                        gc += g;
-                    }
-                    if (ok && all) {
-                        cnt += gc;
-                        q0 += 64;
-                        continue;
-                    }
-                }
-                const int64_t qe = std::min<int64_t>(end, q0 + 64);
-                for (int64_t q = q0; q < qe; ++q) {
-                    const float v = eps_map[q];
-                    if (!(v >= 1.0f) || !std::isfinite(v)) {
-                        bad[t] = 1;
-                        break;
-                    }
-                    uint32_t bits;
-                    std::memcpy(&bits, &v, 4);
-                    if (last_id < 0 || bits != last) {
-                        last = bits;
-                        last_id = find_key(tk, bits);
-                        if (last_id < 0) {
-                            if (tk.size() < 128) {
-                                last_id = (int)tk.size();
-                                tk.push_back(bits);
-                            } else {
-                                over[t] = 1;   // more than 128 values: dense map
-                                last_id = 0;
-                            }
-                        }
-                    }
-                    const bool g = gain_on && gain_mask[q] != 0;
-                    mat[q] = (uint8_t)last_id | (g ? 0x80 : 0x00);
-                    cnt += g;
-                }
-                q0 = qe;
-            }
-            ngain[t] = cnt;
-        }
-        {
-            std::unique_lock<std::mutex> lk(mu);
-            if (++arrived == nthr) {
-                // every thread finished pass A: merge (on the last to arrive)
-                for (int r = 0; r < nthr; ++r) any_bad |= bad[r] != 0;
-                for (int r = 0; r < nthr && !dense; ++r) {
-                    dense = over[r] != 0;
-                    for (uint32_t bits : seen[r])
-                        if (!dense && find_key(keys, bits) < 0) {
-                            if (keys.size() == 128) {
-                                dense = true;
-                                break;
-                            }
-                            keys.push_back(bits);
-                        }
-                }
-                for (int r = 0; r < nthr; ++r) goff[r + 1] = goff[r] + ngain[r];
-                const size_t need = (size_t)std::max<int64_t>(goff[nthr], 1);
-                if (!any_bad && c->h_glist_cap < need) {
-                    c->h_glist.reset(new (std::nothrow) uint32_t[need]);
-                    c->h_glist_cap = c->h_glist ? need : 0;
-                    no_mem = !c->h_glist;
-                }
-                merged = true;
-                cv.notify_all();
-            } else {
-                cv.wait(lk, [&] { return merged; });
-            }
-        }
-        if (any_bad || no_mem) return;
-        uint8_t remap[128];
-        bool identity = true;
-        for (size_t q = 0; q < seen[t].size(); ++q) {
-            remap[q] = dense ? 0 : (uint8_t)find_key(keys, seen[t][q]);
-            identity &= remap[q] == (uint8_t)q;
-        }
-        if (!identity)
-            for (int64_t q = chunk[t].first; q < chunk[t].second; ++q)
-                mat[q] = (uint8_t)(remap[mat[q] & 0x7f] | (mat[q] & 0x80));
-        // gain cells in order, without a branch per cell: every index is
-        // written and the position advances on gain cells; the loop ends when
-        // the thread's segment is full, so no write leaves it
-        uint32_t* out = c->h_glist.get() + goff[t];
-        uint32_t* const out_end = c->h_glist.get() + goff[t + 1];
-        for (int64_t q = chunk[t].first; q < chunk[t].second && out < out_end; ++q) {
-            *out = (uint32_t)q;
-            out += mat[q] >> 7;
-        }
-    };
-    {
-        std::vector<std::thread> pool;
-        for (int t = 1; t < nthr; ++t) pool.emplace_back(body, t);
-        body(0);
-        for (auto& th : pool) th.join();
-    }
-    if (any_bad) return fail(c, MB_ERR_MATERIALS, "eps_r must be finite and >= 1");
-    if (no_mem) return fail(c, MB_ERR_OOM, "host gain-list buffer allocation failed");
     std::vector<float> lut_eps;
-    for (uint32_t bits : keys) {
-        float v;
-        std::memcpy(&v, &bits, 4);
-        lut_eps.push_back(v);
+    bool dense = false;
+    size_t n_gain = 0;
+    // into the context's work buffers; they replace the host copy only when
+    // every check passed
+    switch (map_materials(eps_map, gain_mask, N, N_a > 0.0, 16, mat, c->h_glist, c->h_glist_cap,
+                          lut_eps, dense, n_gain)) {
+        case MB_OK:
+            break;
+        case MB_ERR_OOM:
+            return fail(c, MB_ERR_OOM, "host gain-list buffer allocation failed");
+        default:
+            return fail(c, MB_ERR_MATERIALS, "eps_r must be finite and >= 1");
     }
-    const size_t n_gain = (size_t)goff[nthr];
     cudaStreamSynchronize(c->stream);
     std::vector<float> lut(256, 1.0f);
     c->h_lut_eps.assign(128, 1.0f);
@@ -1259,6 +1289,32 @@ int mb_device_bytes(mb_ctx* c, size_t* bytes) {
     if (int rc = check_ctx(c)) return rc;
     if (!bytes) return fail(c, MB_ERR_ARG, "null output");
     *bytes = c->dev_bytes;
+    return MB_OK;
+}
+
+int mb_material_map(const float* eps_map, const uint8_t* gain_mask, int64_t n, int gain_on,
+                    int max_threads, uint8_t* out_mat, uint32_t* out_glist, int64_t* out_n_gain,
+                    float* out_lut_eps, int* out_n_values, int* out_dense) {
+    if (!eps_map || !gain_mask || n < 1 || !out_mat || !out_glist || !out_n_gain || !out_lut_eps ||
+        !out_n_values || !out_dense) {
+        g_err = "bad material-map arguments";
+        return MB_ERR_ARG;
+    }
+    std::unique_ptr<uint32_t[]> glist;
+    size_t cap = 0, n_gain = 0;
+    std::vector<float> lut;
+    bool dense = false;
+    const int rc = map_materials(eps_map, gain_mask, n, gain_on != 0, max_threads, out_mat, glist, cap,
+                                 lut, dense, n_gain);
+    if (rc) {
+        g_err = rc == MB_ERR_OOM ? "host gain-list buffer allocation failed" : "eps_r must be finite and >= 1";
+        return rc;
+    }
+    if (n_gain) std::memcpy(out_glist, glist.get(), sizeof(uint32_t) * n_gain);
+    *out_n_gain = (int64_t)n_gain;
+    for (size_t q = 0; q < lut.size(); ++q) out_lut_eps[q] = lut[q];
+    *out_n_values = (int)lut.size();
+    *out_dense = dense ? 1 : 0;
     return MB_OK;
 }
 
