@@ -298,6 +298,17 @@ void mb_debug_fail_alloc(int n);
 /* Device bytes the context holds. */
 int mb_device_bytes(mb_ctx* ctx, size_t* bytes);
 
+/* Diagnostic (host only, no device work): the coefficient tables a context
+ * with these arguments steps with (p NULL: defaults), in device units.
+ * out_cpml (4 (n_x + n_y + n_z) floats): per axis x, y, z the CPML b and c of
+ * the E update (at cell positions i) and of the H update (at i + 1/2), each
+ * n_w values, zero outside the layers.  out_gain (20 floats, zero when
+ * N_a = 0): cJ1, cJE, cJP, cJN, nfloor, g[3], G[3][3] (row-major), mk[3] of
+ * the gain update n' = n + g + G n + mk S, n = (N1, N2, N3)/N_a.  out_E0: the
+ * field scale E0 (V/m).  Errors: MB_ERR_ARG. */
+int mb_host_tables(const int grid[3], double dx, double dt, const mb_params* p, double N_a,
+                   double pump, float* out_cpml, float* out_gain, double* out_E0);
+
 /* Diagnostic (host only, no device work): the material map mb_set_material
  * builds from eps_map and gain_mask (host, n cells each), with at most
  * max_threads host threads.  out_mat (n bytes): bits 0..6 the id of the

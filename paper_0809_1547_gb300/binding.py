@@ -94,6 +94,8 @@ _SIGS = [
     ("mb_launch_stats", C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int64)]),
     ("mb_device_bytes", C.c_int, [_P, C.POINTER(C.c_size_t)]),
     ("mb_philox4x32_10", C.c_int, [_P, _P, _P, C.c_int]),
+    ("mb_host_tables", C.c_int, [_P, C.c_double, C.c_double, _P, C.c_double, C.c_double, _P, _P,
+                                 C.POINTER(C.c_double)]),
     ("mb_material_map", C.c_int, [_P, _P, C.c_int64, C.c_int, C.c_int, _P, _P, C.POINTER(C.c_int64),
                                   _P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     ("mb_energy_sum_noalloc", C.c_int, [_P, _P, _P, _P, _P, _P, _P, C.c_int64, _P, _P]),
@@ -255,6 +257,25 @@ def mb_flux_async(h, out_ptr: int):
 def mb_debug_fail_alloc(n: int):
     """Test hook: make the n-th device allocation from now on fail (n < 0: off)."""
     load_library().mb_debug_fail_alloc(int(n))
+
+
+def mb_host_tables(grid, dx, dt, params: mb_params | None = None, N_a=0.0, pump=0.0):
+    """Host-only diagnostic: ({axis: (bE, cE, bH, cH)}, gain coefficients
+    dict, E0) exactly as a context with these arguments steps with them."""
+    g = (C.c_int * 3)(*[int(v) for v in grid])
+    cp = np.empty(4 * sum(int(v) for v in grid), np.float32)
+    gn = np.empty(20, np.float32)
+    E0 = C.c_double()
+    _check(load_library().mb_host_tables(g, float(dx), float(dt), C.byref(params) if params else None,
+                                         float(N_a), float(pump), _ptr(cp), _ptr(gn), C.byref(E0)))
+    out, o = {}, 0
+    for w, n in zip("xyz", grid):
+        n = int(n)
+        out[w] = tuple(cp[o + q * n:o + (q + 1) * n].copy() for q in range(4))
+        o += 4 * n
+    gain = {"cJ1": gn[0], "cJE": gn[1], "cJP": gn[2], "cJN": gn[3], "nfloor": gn[4], "g": gn[5:8].copy(),
+            "G": gn[8:17].reshape(3, 3).copy(), "mk": gn[17:20].copy()}
+    return out, gain, E0.value
 
 
 def mb_material_map(eps_map, gain_mask, gain_on=True, max_threads=16):

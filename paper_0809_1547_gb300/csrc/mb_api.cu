@@ -195,14 +195,10 @@ void cn_propagator(const mb_params& p, double W_p, double dt, double M[4][4], do
     solve4(Lm, e, m);
 }
 
-void gain_coefficients(mb_ctx* c) {
-    mb::DevGain& G = c->args.gain;
-    std::memset(&G, 0, sizeof(G));
-    G.key0 = (uint32_t)(c->seed & 0xffffffffu);
-    G.key1 = (uint32_t)(c->seed >> 32);
-    if (!(c->N_a > 0.0)) return;
-    const mb_params& p = c->p;
-    const double dt = c->dt, dx = c->dx, N_a = c->N_a;
+// The gain medium's step coefficients in device units (the fields of
+// DevGain but the noise keys) for N_a atoms per m^3 pumped at W_p.
+void gain_table(const mb_params& p, double dt, double dx, double N_a, double W_p, double E0,
+                mb::DevGain& G) {
     const double w0 = 2.0 * kPi * kC0 / p.lambda0;
     const double dw = 2.0 * kPi * kC0 * p.dlambda / (p.lambda0 * p.lambda0);
     const double xi = 6.0 * kPi * kEps0 * kC0 * kC0 * kC0 / (w0 * w0 * p.tau21);
@@ -213,17 +209,25 @@ void gain_coefficients(mb_ctx* c) {
     G.cJE = (float)(dt * dt * xi * N_a / (kEps0 * (1.0 + a)));
     G.cJP = (float)((w0 * dt) * (w0 * dt) / (1.0 + a));
     G.cJN = (float)(dt * dt * a_se * std::sqrt(N_a / (dx * dx * dx * dt)) /
-                    (kEps0 * c->E0 * (1.0 + a)));
+                    (kEps0 * E0 * (1.0 + a)));
     G.nfloor = (float)p.n_floor_rel;
     double M[4][4], m[4], Lm[4][4];
-    cn_propagator(p, c->W_p, dt, M, m, Lm);
-    const double smk = kEps0 * c->E0 * c->E0 / (kHbar * w0 * N_a);   // m s / N_a per S_pop
+    cn_propagator(p, W_p, dt, M, m, Lm);
+    const double smk = kEps0 * E0 * E0 / (kHbar * w0 * N_a);   // m s / N_a per S_pop
     for (int r = 0; r < 3; ++r) {
         G.g[r] = (float)M[r + 1][0];
         for (int q = 0; q < 3; ++q)
             G.G[r][q] = (float)(M[r + 1][q + 1] - M[r + 1][0] - (r == q ? 1.0 : 0.0));
         G.mk[r] = (float)(m[r + 1] * smk);
     }
+}
+
+void gain_coefficients(mb_ctx* c) {
+    mb::DevGain& G = c->args.gain;
+    std::memset(&G, 0, sizeof(G));
+    if (c->N_a > 0.0) gain_table(c->p, c->dt, c->dx, c->N_a, c->W_p, c->E0, G);
+    G.key0 = (uint32_t)(c->seed & 0xffffffffu);
+    G.key1 = (uint32_t)(c->seed >> 32);
 }
 
 int check_ctx_nojoin(mb_ctx* c) {
@@ -1289,6 +1293,41 @@ int mb_device_bytes(mb_ctx* c, size_t* bytes) {
     if (int rc = check_ctx(c)) return rc;
     if (!bytes) return fail(c, MB_ERR_ARG, "null output");
     *bytes = c->dev_bytes;
+    return MB_OK;
+}
+
+int mb_host_tables(const int grid[3], double dx, double dt, const mb_params* p, double N_a,
+                   double pump, float* out_cpml, float* out_gain, double* out_E0) {
+    if (!grid || grid[0] < 1 || grid[1] < 1 || grid[2] < 1 || !(dx > 0) || !(dt > 0) ||
+        !(N_a >= 0) || !(pump >= 0) || !out_cpml || !out_gain || !out_E0) {
+        g_err = "bad host-table arguments";
+        return MB_ERR_ARG;
+    }
+    mb_params prm;
+    if (p) prm = *p;
+    else mb_default_params(&prm);
+    float* t = out_cpml;
+    for (int w = 0; w < 3; ++w) {
+        cpml_table(grid[w], 0.0, prm.npml, dx, dt, prm, t, t + grid[w]);
+        cpml_table(grid[w], 0.5, prm.npml, dx, dt, prm, t + 2 * grid[w], t + 3 * grid[w]);
+        t += 4 * grid[w];
+    }
+    const double w0 = 2.0 * kPi * kC0 / prm.lambda0;
+    const double E0 = std::sqrt(kHbar * w0 * prm.n_ref / kEps0);
+    mb::DevGain G;
+    std::memset(&G, 0, sizeof(G));
+    if (N_a > 0.0) gain_table(prm, dt, dx, N_a, pump, E0, G);
+    float* o = out_gain;
+    *o++ = G.cJ1;
+    *o++ = G.cJE;
+    *o++ = G.cJP;
+    *o++ = G.cJN;
+    *o++ = G.nfloor;
+    for (int r = 0; r < 3; ++r) *o++ = G.g[r];
+    for (int r = 0; r < 3; ++r)
+        for (int q = 0; q < 3; ++q) *o++ = G.G[r][q];
+    for (int r = 0; r < 3; ++r) *o++ = G.mk[r];
+    *out_E0 = E0;
     return MB_OK;
 }
 
