@@ -60,3 +60,26 @@ def test_paper_workload_byte_count_at_320():
     ab = bench.algorithmic_bytes(w)
     assert ab["single_pass_launch"] == pytest.approx(85.3, abs=0.5)
     assert ab["step_reference"] == pytest.approx(117.6, abs=0.5)
+
+
+def test_reference_arm_prints_one_valid_line():
+    """`bench.py --impl reference` (the oracle timed on the host cores, the
+    arm run beside ours) prints one JSON line with our metric, unit and
+    direction, impl = reference, its cpu_baseline and an e2e without copies."""
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference",
+                        "--steps", "1", "--warmup", "3"], capture_output=True, text=True, timeout=600,
+                       cwd=root)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.strip().startswith("{")]
+    assert len(lines) == 1, r.stdout
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and "unavailable" not in d
+    assert d["metric"] == bench.METRIC and d["unit"] == bench.UNIT and d["higher_is_better"] is True
+    assert d["value"] > 0 and d["steps"] == 1 and d["warmup"] >= 3
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] >= 1 and d["cpu_baseline"]["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": bench.UNIT, "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
