@@ -18,7 +18,7 @@ import numpy as np
 import pytest
 import scipy.linalg
 
-from oracle.mb_oracle import (MBOracle, Params, C0, EPS0, HBAR, gain_constants, lorentz_update,
+from oracle.mb_oracle import (MBOracle, Params, C0, EPS0, MU0, HBAR, gain_constants, lorentz_update,
                               rate_matrix, crank_nicolson, population_update)
 
 DX = 20e-9
@@ -152,6 +152,41 @@ def test_field_transfer_direction():
         N = population_update(N, s, M, m)
     np.testing.assert_allclose(N[2], 10 * DT * s, rtol=1e-12)
     np.testing.assert_allclose(N[1], 1e24 - 10 * DT * s, rtol=1e-12)
+
+
+def test_field_and_atoms_exchange_energy_exactly():
+    """With decays and pump off (A ~ 0: M = I, m = dt e), the discrete Yee
+    energy theorem with a current, W^{n+1} - W^n = -dt dV sum J^{n+1/2} .
+    (E^n + E^{n+1})/2 for W^n = 1/2 sum eps|E^n|^2 dV + 1/2 sum mu0
+    H^{n-1/2}.H^{n+1/2} dV in a PEC box, and the population update
+    N2^{n+1} = N2^n + dt s make W^n + hbar w0 dV sum N2^n an invariant of the
+    coupled step.  Started from zero fields and zero N2, driven by the
+    Langevin currents alone, it stays zero to rounding while the field's
+    energy grows from nothing."""
+    grid = (10, 9, 11)
+    rng = np.random.default_rng(21)
+    p = Params(npml=0, tau32=1e300, tau21=1e300, tau10=1e300)
+    sim = MBOracle(grid, DX, DT, p)
+    gain = rng.random(grid[::-1]) < 0.5
+    eps = rng.uniform(1.0, 8.41, size=grid[::-1])
+    N_a = 2e25
+    sim.set_material(eps, gain, N_a, 0.0)
+    sim.set_seed(77)
+    dV = DX ** 3
+    hw = HBAR * gain_constants(p)["w0"]
+    inv, W_all = [], []
+    for _ in range(40):
+        E_n = [F.copy() for F in sim.E]
+        H_minus = [F.copy() for F in sim.H]
+        atoms = hw * dV * sim.N[2].sum()
+        sim.step(1)
+        W = 0.5 * EPS0 * sum(np.sum(eps * F * F) for F in E_n) * dV
+        W += 0.5 * MU0 * sum(np.sum(a * b) for a, b in zip(H_minus, sim.H)) * dV
+        inv.append(W + atoms)
+        W_all.append(W)
+    scale = max(abs(w) for w in W_all)
+    assert scale > 0 and W_all[-1] > 0          # the currents did put energy into the field
+    assert max(abs(v) for v in inv) <= 1e-11 * scale
 
 
 def _run_cavity(init_pop, steps=120):
