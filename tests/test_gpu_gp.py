@@ -26,8 +26,8 @@ def test_features_and_profiles_match_oracle():
     for q, E in enumerate(ES):
         tau, h, ph_o = G.solve(E)
         w_o, p_o = G.features(tau, h, ph_o)
-        assert w[q] == pytest.approx(w_o, rel=1e-9), E
-        assert p[q] == pytest.approx(p_o, rel=1e-9), E
+        assert w[q] == pytest.approx(w_o, rel=1e-9, abs=0), E
+        assert p[q] == pytest.approx(p_o, rel=1e-9, abs=0), E
         assert np.linalg.norm(phi[q] - ph_o) <= 1e-9 * np.linalg.norm(ph_o), E
 
 
@@ -53,11 +53,11 @@ def test_theory_curves():
     from paper_0809_1547_gb300 import gp
     kappa = 0.14                                  # the paper's best fit
     pth = gp.p_threshold(kappa)
-    assert pth == pytest.approx(G.p_threshold(kappa), rel=1e-15)
+    assert pth == pytest.approx(G.p_threshold(kappa), rel=1e-15, abs=0)
     p = pth * np.array([1.001, 1.5, 3.0, 10.0])
     c = gp.theory_curves(p, kappa)
     np.testing.assert_allclose(c["E"], G.E_of_p(p, kappa), rtol=1e-14)
     # near threshold the waist is the Gaussian one: W t_g -> sqrt(kappa/2) / (2 pi) / p^{1/4}
-    assert c["W_tg"][0] == pytest.approx(math.sqrt(kappa / 2) / (2 * math.pi) / p[0] ** 0.25, rel=1e-2)
+    assert c["W_tg"][0] == pytest.approx(math.sqrt(kappa / 2) / (2 * math.pi) / p[0] ** 0.25, rel=1e-2, abs=0)
     with pytest.raises(ValueError):
         gp.theory_curves([0.9 * pth], kappa)

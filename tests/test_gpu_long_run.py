@@ -35,11 +35,11 @@ def test_long_run_statistics_match_oracle():
     np.testing.assert_allclose(lam_g, lam, rtol=1e-15)
     om = O.omegas_of(lam)
     assert abs(O.peak(S_g, om)[0] - O.peak(S_o, om)[0]) <= abs(om[1] - om[0]) * 1.0001
-    assert O.std_width(S_g, om) == pytest.approx(O.std_width(S_o, om), rel=0.05)
+    assert O.std_width(S_g, om) == pytest.approx(O.std_width(S_o, om), rel=0.05, abs=0)
     _, fl_g = g.energy()
     emitted_o, emitted_g = float(np.sum(o.flux)), float(np.sum(fl_g))
     assert emitted_o > 0
-    assert emitted_g == pytest.approx(emitted_o, rel=0.05)
+    assert emitted_g == pytest.approx(emitted_o, rel=0.05, abs=0)
     # the populations moved (the run is pumped and noisy, not trivial)
     assert np.abs(o.field("N3")).max() > 0
     print(f"2000 steps: spectrum rel-L2 {rel_l2(S_g, S_o):.2e}, Ex rel-L2 "

@@ -69,7 +69,7 @@ def test_snapshot_planes_sum_to_the_energy():
     g.step(60)
     U, _ = g.energy()
     total = sum(g.plane_energy_density(k).sum() for k in range(grid[2])) * DX ** 3
-    assert total == pytest.approx(U, rel=1e-9)
+    assert total == pytest.approx(U, rel=1e-9, abs=0)
     g.close()
 
 

@@ -60,7 +60,7 @@ def _assert_same(ref, got, what):
     # energy is a sum of identical fields; the face flux adds FP32 per-warp
     # partials (grouped by the tile shape) into FP64 slots in launch order,
     # so it is fixed to FP32 rounding only
-    assert got["energy"][0] == pytest.approx(ref["energy"][0], rel=1e-12)
+    assert got["energy"][0] == pytest.approx(ref["energy"][0], rel=1e-12, abs=0)
     np.testing.assert_allclose(got["energy"][1], ref["energy"][1], rtol=1e-6,
                                atol=1e-6 * np.abs(ref["energy"][1]).max())
 
@@ -176,8 +176,8 @@ def test_single_pass_state_in_second_copy():
         sim.step(1)
     res = [sim.adjoint_energy_zface(12, 4) for sim in (g, r)]
     # same forward states; the FP64 sums of J and dJ/dW_p add in atomic order
-    assert res[0][0] == pytest.approx(res[1][0], rel=1e-12)
-    assert res[0][2] == pytest.approx(res[1][2], rel=1e-12)
+    assert res[0][0] == pytest.approx(res[1][0], rel=1e-12, abs=0)
+    assert res[0][2] == pytest.approx(res[1][2], rel=1e-12, abs=0)
     ga, gb = res[0][1].cpu().numpy(), res[1][1].cpu().numpy()
     np.testing.assert_allclose(ga, gb, rtol=1e-6, atol=1e-6 * np.abs(gb).max())
     assert g.single_pass() == (1, 64, 4, 7)

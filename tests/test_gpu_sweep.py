@@ -45,7 +45,7 @@ def test_small_sweep_matches_oracle():
         np.testing.assert_allclose(lam, lam_o, rtol=1e-15)
         assert rel_l2(spectra[q], S_o) <= 2e-5
         assert abs(st["peak_w"][q] - O.peak(S_o, w)[0]) <= abs(w[1] - w[0]) * 1.0001
-        assert st["std_w"][q] == pytest.approx(O.std_width(S_o, w), rel=1e-4)
+        assert st["std_w"][q] == pytest.approx(O.std_width(S_o, w), rel=1e-4, abs=0)
 
 
 def test_full_ensemble_sweep_runs():

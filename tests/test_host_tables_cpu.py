@@ -51,7 +51,7 @@ def test_gain_coefficients_match_the_oracle_model(N_a, W_p):
     P = Params(**pkw)
     gc = gain_constants(P)
     w0, dw, xi, a_se = gc["w0"], gc["dw"], gc["xi"], gc["a_se"]
-    assert E0 == pytest.approx(math.sqrt(HBAR * w0 * prm.n_ref / EPS0), rel=1e-14)
+    assert E0 == pytest.approx(math.sqrt(HBAR * w0 * prm.n_ref / EPS0), rel=1e-14, abs=0)
     a = 0.5 * dw * DT
     # J^{n+1/2} (1 + a) = (1 - a) J^{n-1/2} + dt (xi dN E - w0^2 P + sigma_F zeta),
     # sigma_F = a_se sqrt(N2 / (dx^3 dt)), in device units
@@ -61,7 +61,7 @@ def test_gain_coefficients_match_the_oracle_model(N_a, W_p):
               "cJN": DT * DT * a_se * math.sqrt(N_a / (DX ** 3 * DT)) / (EPS0 * E0 * (1 + a)),
               "nfloor": P.n_floor_rel}
     for k, v in expect.items():
-        assert g[k] == pytest.approx(v, rel=2e-7), k
+        assert g[k] == pytest.approx(v, rel=2e-7, abs=0), k
     M, m = crank_nicolson(rate_matrix(P, W_p), DT)
     # n_r' = M[r,0] (1 - sum n) + sum_q M[r,q] n_q  (r, q = 1..3), plus m_r S
     g_exp = M[1:, 0]

@@ -9,8 +9,10 @@ pins are the functions of tests/test_oracle_*.py, imported afresh so that
 they bind the mutant.  The files on disk are not touched, and the module
 table is restored afterwards.  Edits that change only a convention with no
 observable consequence (the sign of the DFT's exponent, which of sin / cos
-drives which normal) are not planted here: the oracle's convention there is
-fixed by the GPU path's bit-exact Philox and field parity instead.
+drives which normal, the direction of the CPML's alpha grading, the
+boundary condition at the ends of the envelope's domain, where the bound
+state has decayed to ~e^-32) are not planted here: the oracle's convention
+there is fixed by the GPU path's bit-exact Philox and field parity instead.
 """
 import importlib
 import os
@@ -22,7 +24,9 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 PIN_MODULES = ("test_oracle_maxwell", "test_oracle_gain", "test_oracle_cpml_probes",
-               "test_oracle_adjoint", "test_oracle_philox")
+               "test_oracle_adjoint", "test_oracle_philox", "test_oracle_gp", "test_oracle_analysis",
+               "test_oracle_modemap")
+ORACLE_MODULES = ("mb_oracle", "mb_adjoint", "mb_analysis", "gp_oracle")
 
 # pins: (test module, function, keyword arguments)
 CAVITY = [("test_oracle_maxwell", "test_pec_cavity_eigenmode",
@@ -46,6 +50,18 @@ PHILOX = [("test_oracle_philox", "test_philox_known_answers", "every known-answe
           ("test_oracle_philox", "test_philox_vectorised_matches_scalar", {}),
           ("test_oracle_philox", "test_unit_map_is_open_interval_and_exact_in_fp32", {}),
           ("test_oracle_philox", "test_box_muller_moments", {})]
+GP = [("test_oracle_gp", "test_near_threshold_closed_form", dict(E=1.01)),
+      ("test_oracle_gp", "test_discrete_and_virial_identities", dict(E=4.0)),
+      ("test_oracle_gp", "test_threshold_and_pump_relation", {}),
+      ("test_oracle_gp", "test_peak_grows_and_width_is_finite_above_threshold", {})]
+ANALYSIS = [("test_oracle_analysis", "test_sampled_gaussian_gives_back_centre_and_width", {}),
+            ("test_oracle_analysis", "test_flat_spectrum_std_width_is_uniform", {}),
+            ("test_oracle_analysis", "test_two_lines_std_width_is_half_the_spacing", {}),
+            ("test_oracle_analysis", "test_sweep_threshold_is_first_level_that_halves_the_width", {})]
+MODEMAP = [("test_oracle_modemap", "test_energy_density_planes_sum_to_the_energy", {}),
+           ("test_oracle_modemap", "test_plane_probe_equals_point_probes_on_its_cells", {}),
+           ("test_oracle_modemap", "test_plane_probe_sampling_interval_does_not_change_the_map", {}),
+           ("test_oracle_modemap", "test_cw_waveform_closed_form", {})]
 ADJ = [("test_oracle_adjoint", "test_adjoint_gradient_matches_central_differences", dict(case=c))
        for c in ("pulse", "noise", "strong")] + \
       [("test_oracle_adjoint", "test_objective_is_the_face_flux", {}),
@@ -90,6 +106,26 @@ MUTANTS = {
     "DFT: dt weight dropped": ("mb_oracle", "self.E[c][k, j, i], pr[\"omegas\"], t, self.dt)", "self.E[c][k, j, i], pr[\"omegas\"], t, 1.0)", PROBES),
     "flux: E x H pairing sign": ("mb_oracle", "F = float(np.sum(Ea * Hb - Eb * Ha)) * dA", "F = float(np.sum(Ea * Hb + Eb * Ha)) * dA", PROBES),
     "flux: outward sign of the low faces": ("mb_oracle", "out.append(F if face % 2 == 1 else -F)", "out.append(F)", PROBES),
+    # NEXT-1: CW source, plane probes, energy density
+    "CW: rise inverted": ("mb_oracle", "* (1.0 - math.exp(-((t - t0) / tau) ** 2))", "* math.exp(-((t - t0) / tau) ** 2)", MODEMAP),
+    "plane probe: sampling interval left out of the weight": ("mb_oracle", "ph = np.exp(1j * pp[\"omegas\"] * t) * (pp[\"every\"] * self.dt)",
+                                                              "ph = np.exp(1j * pp[\"omegas\"] * t) * self.dt", MODEMAP),
+    "plane probe: E^n sampled": ("mb_oracle", "pp[\"acc\"][:, c] += self.E[c][pp[\"k\"]]", "pp[\"acc\"][:, c] += E_old[c][pp[\"k\"]]", MODEMAP),
+    "energy density: eps_r dropped": ("mb_oracle", "* EPS0 * self.eps_r[k]", "* EPS0", MODEMAP),
+    # NEXT-4: bound state of -phi'' + tau^2 phi + phi^3 = E phi
+    "GP: potential sign": ("gp_oracle", "+ tau ** 2 * phi + phi ** 3 - E * phi", "- tau ** 2 * phi + phi ** 3 - E * phi", GP),
+    "GP: nonlinearity dropped": ("gp_oracle", "+ tau ** 2 * phi + phi ** 3 - E * phi", "+ tau ** 2 * phi - E * phi", GP),
+    "GP: spectral peak normalisation": ("gp_oracle", "p_phi = s_phi ** 2 / (4.0 * math.pi ** 2)", "p_phi = s_phi ** 2 / (2.0 * math.pi)", GP),
+    "GP: waist without the 2 pi": ("gp_oracle", "return math.sqrt(sig2) / (2.0 * math.pi), p_phi", "return math.sqrt(sig2), p_phi", GP),
+    "GP: E(p) with p for sqrt p": ("gp_oracle", "return (p - 1.0) / (kappa * np.sqrt(p))", "return (p - 1.0) / (kappa * p)", GP),
+    "GP: threshold root sign": ("gp_oracle", "+ kappa * math.sqrt(4.0 + kappa ** 2) / 2.0", "- kappa * math.sqrt(4.0 + kappa ** 2) / 2.0", GP),
+    # NEXT-2: spectral statistics
+    "analysis: unweighted mean": ("mb_analysis", "mean = (S * w).sum() / tot", "mean = w.mean()", ANALYSIS),
+    "analysis: width over bins": ("mb_analysis", "return math.sqrt((S * (w - mean) ** 2).sum() / tot)",
+                                  "return math.sqrt((S * (w - mean) ** 2).sum() / S.size)", ANALYSIS),
+    "analysis: fit centre sign": ("mb_analysis", "return float(x0 - b / (2.0 * c))", "return float(x0 + b / (2.0 * c))", ANALYSIS),
+    "analysis: fit width without the 2": ("mb_analysis", "float(math.sqrt(-1.0 / (2.0 * c)))", "float(math.sqrt(-1.0 / c))", ANALYSIS),
+    "analysis: threshold at a tenth off": ("mb_analysis", "if r[\"std_w\"] <= 0.5 * rows[0][\"std_w\"]:", "if r[\"std_w\"] <= 0.9 * rows[0][\"std_w\"]:", ANALYSIS),
     # the discrete adjoint
     "adjoint: psi_E memory coefficient dropped": ("mb_adjoint", "coef = sign * u[_COMP[c]] + cc * tot", "coef = sign * u[_COMP[c]]", ADJ),
     "adjoint: psi_H memory coefficient dropped": ("mb_adjoint", "coef = sign * v[_COMP[c]] + cc * tot\n            F = _COMP[_other(key)]\n            lE0",
@@ -122,14 +158,20 @@ def _mutant_module(name, old, new):
 
 
 def _fails_a_pin(name, old, new, pins):
-    keys = ("oracle.mb_oracle", "oracle.mb_adjoint") + PIN_MODULES
+    import oracle
+    keys = tuple("oracle." + m for m in ORACLE_MODULES) + PIN_MODULES
     saved = {k: sys.modules.get(k) for k in keys}
+    saved_attr = {m: getattr(oracle, m, None) for m in ORACLE_MODULES}
     try:
-        importlib.import_module("oracle.mb_oracle")
+        for m in ORACLE_MODULES:
+            importlib.import_module("oracle." + m)
         _mutant_module(name, old, new)
-        if name == "mb_oracle":             # the adjoint imports names from the forward oracle
-            sys.modules.pop("oracle.mb_adjoint", None)
-            importlib.import_module("oracle.mb_adjoint")
+        if name == "mb_oracle":             # modules that import names from the forward oracle
+            for m in ("mb_adjoint", "mb_analysis"):
+                sys.modules.pop("oracle." + m, None)
+                importlib.import_module("oracle." + m)
+        for m in ORACLE_MODULES:            # `from oracle import m` reads the package attribute
+            setattr(oracle, m, sys.modules["oracle." + m])
         for k in PIN_MODULES:
             sys.modules.pop(k, None)
         for module, fn, kwargs in pins:
@@ -151,11 +193,17 @@ def _fails_a_pin(name, old, new, pins):
                 sys.modules.pop(k, None)
             else:
                 sys.modules[k] = v
+        for m, v in saved_attr.items():
+            if v is None:
+                if hasattr(oracle, m):
+                    delattr(oracle, m)
+            else:
+                setattr(oracle, m, v)
 
 
 def test_pins_pass_on_the_oracle_itself():
     """The harness itself: with an edit that changes nothing, every pin set passes."""
-    for pins in (CAVITY, CPML, LORENTZ, NOISE, RATES, COUPLING, PROBES, PHILOX, ADJ):
+    for pins in (CAVITY, CPML, LORENTZ, NOISE, RATES, COUPLING, PROBES, PHILOX, MODEMAP, GP, ANALYSIS, ADJ):
         assert not _fails_a_pin("mb_oracle", "def rate_matrix(", "def rate_matrix(", pins)
 
 

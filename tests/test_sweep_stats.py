@@ -25,12 +25,12 @@ def test_stats_agree_with_oracle_definitions():
     for q in range(S.shape[0]):
         pw, pS = O.peak(S[q], w)
         assert st["peak_w"][q] == pw and st["peak_S"][q] == pS
-        assert st["std_w"][q] == pytest.approx(O.std_width(S[q], w), rel=1e-12)
+        assert st["std_w"][q] == pytest.approx(O.std_width(S[q], w), rel=1e-12, abs=0)
         c, sg = O.gaussian_fit(S[q], w)
         if sg is None:
             assert np.isnan(st["gauss_w"][q])
         else:
-            assert st["gauss_w"][q] == pytest.approx(sg, rel=1e-7)
+            assert st["gauss_w"][q] == pytest.approx(sg, rel=1e-7, abs=0)
 
 
 def test_summary_and_threshold_agree_with_oracle():
@@ -43,5 +43,5 @@ def test_summary_and_threshold_agree_with_oracle():
     assert thr == thr_o
     for r, ro in zip(rows, rows_o):
         assert r["N_a"] == ro["level"]
-        assert r["std_w"] == pytest.approx(ro["std_w"], rel=1e-12)
-        assert r["peak_w"] == pytest.approx(ro["peak_w"], rel=1e-12)
+        assert r["std_w"] == pytest.approx(ro["std_w"], rel=1e-12, abs=0)
+        assert r["peak_w"] == pytest.approx(ro["peak_w"], rel=1e-12, abs=0)
