@@ -140,16 +140,18 @@ def test_face_flux_balances_interior_energy_exactly():
     assert np.all(F2 - F1 > 0)
 
 
-@pytest.mark.parametrize("every", [1, 3])
-def test_face_spectra_parseval(every):
-    """sum_n dt F(t_n) = (1/pi) int_0^inf Re(E~ x H~*) . n dw for a pulse that has left."""
+@pytest.mark.parametrize("every,stride", [(1, 1), (3, 1), (1, 2)])
+def test_face_spectra_parseval(every, stride):
+    """sum_n dt F(t_n) = (1/pi) int_0^inf Re(E~ x H~*) . n dw for a pulse that
+    has left; a face sub-grid of every stride-th point (weighted by its
+    (stride dx)^2 area) is another quadrature of the same face integral."""
     grid = (26, 26, 26)
     sim = MBOracle(grid, DX, DT, Params(npml=8))
     shp = grid[::-1]
     sim.set_material(np.ones(shp), np.zeros(shp), 0.0, 0.0)
     tau = 2e-15
     sim.add_source((13, 13, 13), 0, 532e-9, 4 * tau, tau, 1e9)
-    sim.add_face_probes(1, every, 400, 330e-9, 1100e-9)
+    sim.add_face_probes(stride, every, 400, 330e-9, 1100e-9)
     sim.step(560)
     total_time = float(np.sum(sim.flux))
     total_freq = 0.0

@@ -46,6 +46,7 @@ COUPLING = [("test_oracle_gain", "test_field_and_atoms_exchange_energy_exactly",
             ("test_oracle_gain", "test_populations_conserved_in_noisy_run", {})]
 PROBES = [("test_oracle_cpml_probes", "test_point_probe_dft_of_cavity_mode", {}),
           ("test_oracle_cpml_probes", "test_face_flux_balances_interior_energy_exactly", {})]
+FACE = [("test_oracle_cpml_probes", "test_face_spectra_parseval", dict(every=1, stride=2))]
 PHILOX = [("test_oracle_philox", "test_philox_known_answers", "every known-answer row"),
           ("test_oracle_philox", "test_philox_vectorised_matches_scalar", {}),
           ("test_oracle_philox", "test_unit_map_is_open_interval_and_exact_in_fp32", {}),
@@ -106,6 +107,14 @@ MUTANTS = {
     "DFT: dt weight dropped": ("mb_oracle", "self.E[c][k, j, i], pr[\"omegas\"], t, self.dt)", "self.E[c][k, j, i], pr[\"omegas\"], t, 1.0)", PROBES),
     "flux: E x H pairing sign": ("mb_oracle", "F = float(np.sum(Ea * Hb - Eb * Ha)) * dA", "F = float(np.sum(Ea * Hb + Eb * Ha)) * dA", PROBES),
     "flux: outward sign of the low faces": ("mb_oracle", "out.append(F if face % 2 == 1 else -F)", "out.append(F)", PROBES),
+    "point spectrum: modulus not squared": ("mb_oracle", "return np.sum(np.abs(pr[\"acc\"]) ** 2, axis=0), pr[\"lams\"].copy()",
+                                            "return np.sum(np.abs(pr[\"acc\"]), axis=0), pr[\"lams\"].copy()", PROBES),
+    "face spectrum: E x H pairing sign": ("mb_oracle", "S = np.real(Ea * np.conj(Hb) - Eb * np.conj(Ha))",
+                                          "S = np.real(Ea * np.conj(Hb) + Eb * np.conj(Ha))", FACE),
+    "face spectrum: low faces not turned outward": ("mb_oracle", "return (S if face % 2 == 1 else -S), fp[\"lams\"].copy()",
+                                                    "return S, fp[\"lams\"].copy()", FACE),
+    "face spectrum: sub-grid area": ("mb_oracle", "S = S.reshape(-1, K).sum(axis=0) * (fp[\"stride\"] * self.dx) ** 2",
+                                     "S = S.reshape(-1, K).sum(axis=0) * self.dx ** 2", FACE),
     # NEXT-1: CW source, plane probes, energy density
     "CW: rise inverted": ("mb_oracle", "* (1.0 - math.exp(-((t - t0) / tau) ** 2))", "* math.exp(-((t - t0) / tau) ** 2)", MODEMAP),
     "plane probe: sampling interval left out of the weight": ("mb_oracle", "ph = np.exp(1j * pp[\"omegas\"] * t) * (pp[\"every\"] * self.dt)",
@@ -203,7 +212,7 @@ def _fails_a_pin(name, old, new, pins):
 
 def test_pins_pass_on_the_oracle_itself():
     """The harness itself: with an edit that changes nothing, every pin set passes."""
-    for pins in (CAVITY, CPML, LORENTZ, NOISE, RATES, COUPLING, PROBES, PHILOX, MODEMAP, GP, ANALYSIS, ADJ):
+    for pins in (CAVITY, CPML, LORENTZ, NOISE, RATES, COUPLING, PROBES, FACE, PHILOX, MODEMAP, GP, ANALYSIS, ADJ):
         assert not _fails_a_pin("mb_oracle", "def rate_matrix(", "def rate_matrix(", pins)
 
 
