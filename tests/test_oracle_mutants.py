@@ -51,8 +51,12 @@ PHILOX = [("test_oracle_philox", "test_philox_known_answers", "every known-answe
           ("test_oracle_philox", "test_philox_vectorised_matches_scalar", {}),
           ("test_oracle_philox", "test_unit_map_is_open_interval_and_exact_in_fp32", {}),
           ("test_oracle_philox", "test_box_muller_moments", {})]
-GP = [("test_oracle_gp", "test_near_threshold_closed_form", dict(E=1.01)),
-      ("test_oracle_gp", "test_discrete_and_virial_identities", dict(E=4.0)),
+GP = [("test_oracle_gp", "test_near_threshold_closed_form", {}),
+      ("test_oracle_gp", "test_integral_identities", dict(E=4.0)),
+      ("test_oracle_gp", "test_integral_identities", dict(E=20.0)),
+      ("test_oracle_gp", "test_thomas_fermi_limit", dict(E=150.0)),
+      ("test_oracle_gp", "test_shooting_and_boundary_value_solve_agree", {}),
+      ("test_oracle_gp", "test_features_from_the_fourier_transform", dict(E=20.0)),
       ("test_oracle_gp", "test_threshold_and_pump_relation", {}),
       ("test_oracle_gp", "test_peak_grows_and_width_is_finite_above_threshold", {})]
 ANALYSIS = [("test_oracle_analysis", "test_sampled_gaussian_gives_back_centre_and_width", {}),
@@ -122,9 +126,14 @@ MUTANTS = {
     "plane probe: E^n sampled": ("mb_oracle", "pp[\"acc\"][:, c] += self.E[c][pp[\"k\"]]", "pp[\"acc\"][:, c] += E_old[c][pp[\"k\"]]", MODEMAP),
     "energy density: eps_r dropped": ("mb_oracle", "* EPS0 * self.eps_r[k]", "* EPS0", MODEMAP),
     # NEXT-4: bound state of -phi'' + tau^2 phi + phi^3 = E phi
-    "GP: potential sign": ("gp_oracle", "+ tau ** 2 * phi + phi ** 3 - E * phi", "- tau ** 2 * phi + phi ** 3 - E * phi", GP),
-    "GP: nonlinearity dropped": ("gp_oracle", "+ tau ** 2 * phi + phi ** 3 - E * phi", "+ tau ** 2 * phi - E * phi", GP),
-    "GP: spectral peak normalisation": ("gp_oracle", "p_phi = s_phi ** 2 / (4.0 * math.pi ** 2)", "p_phi = s_phi ** 2 / (2.0 * math.pi)", GP),
+    "GP: potential sign": ("gp_oracle", "(tau * tau + phi * phi - E) * phi", "(-tau * tau + phi * phi - E) * phi", GP),
+    "GP: nonlinearity dropped": ("gp_oracle", "(tau * tau + phi * phi - E) * phi", "(tau * tau - E) * phi", GP),
+    "GP: nonlinearity sign": ("gp_oracle", "(tau * tau + phi * phi - E) * phi", "(tau * tau - phi * phi - E) * phi", GP),
+    "GP: carried int phi'^2 of phi": ("gp_oracle", "phi * phi, dphi * dphi, tau", "phi * phi, phi * dphi, tau", GP),
+    "GP: carried int tau^2 phi^2 without tau": ("gp_oracle", "tau * tau * phi * phi, phi ** 4", "phi * phi, phi ** 4", GP),
+    "GP: shooting verdicts swapped": ("gp_oracle", "        if kind < 0:\n            lo = mid", "        if kind > 0:\n            lo = mid", GP),
+    "GP: spectral peak normalisation": ("gp_oracle", "p_phi = st.I0 ** 2 / (4.0 * math.pi ** 2)", "p_phi = st.I0 ** 2 / (2.0 * math.pi)", GP),
+    "GP: waist from int phi^2": ("gp_oracle", "sig2 = st.I2 / st.I1", "sig2 = st.I3 / st.I1", GP),
     "GP: waist without the 2 pi": ("gp_oracle", "return math.sqrt(sig2) / (2.0 * math.pi), p_phi", "return math.sqrt(sig2), p_phi", GP),
     "GP: E(p) with p for sqrt p": ("gp_oracle", "return (p - 1.0) / (kappa * np.sqrt(p))", "return (p - 1.0) / (kappa * p)", GP),
     "GP: threshold root sign": ("gp_oracle", "+ kappa * math.sqrt(4.0 + kappa ** 2) / 2.0", "- kappa * math.sqrt(4.0 + kappa ** 2) / 2.0", GP),
