@@ -126,6 +126,8 @@ __global__ void __launch_bounds__(BX * BY) k_step_fused(StepArgs a, DevPing d,
     __syncthreads();
     if (tid == 0)
         for (int s = 0; s < S && s < total; ++s) issue(s, s);
+    int issued = min(S, total);   // planes issued into the ring so far
+    bool block_fail = false;
 
     uint32_t c = valid ? (uint32_t)i + (uint32_t)nx * j + nxy * k0 : 0u;
     // H^{n+1/2} of plane k0-1 at this cell (zero below the first plane)
@@ -297,20 +299,23 @@ __global__ void __launch_bounds__(BX * BY) k_step_fused(StepArgs a, DevPing d,
                 }
             }
         }
-        __syncthreads();   // ring slot s and the H tile are free again
-        if (tid == 0 && p + S < total) issue(s, p + S);
+        // ring slot s and the H tile are free again; the barrier also ORs the
+        // threads' wait verdicts, so every thread sees the same block_fail
+        block_fail = __syncthreads_or(fail);
+        if (block_fail) break;   // issue nothing more; drained below
+        if (p + S < total) {
+            if (tid == 0) issue(s, p + S);
+            issued = p + S + 1;
+        }
         pg = ng;
         c += nxy;
     }
     cp_async_wait_all();
-    if (fail) {
+    if (block_fail) {
         // A wait gave up: record it, then give the copies still in flight a
         // bounded chance to land before the block's shared memory is released.
         if (tid == 0) atomicOr(a.err, 1);
-        for (int s = 0; s < S && s < total; ++s) {
-            const int uses = (total - s + S - 1) / S;
-            mbar_wait_bounded(&bar[s], (uses - 1) & 1, kWaitLimit);
-        }
+        drain_ring(bar, S, issued, kWaitLimit);
     }
     if (face && (tid & 31) == 0) {
         const unsigned slot = warp_slot();

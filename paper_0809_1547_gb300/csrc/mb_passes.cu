@@ -344,6 +344,8 @@ __global__ void __launch_bounds__(BX * BY) k_e_tma(StepArgs a, const __grid_cons
     __syncthreads();
     if (tid == 0)
         for (int s = 0; s < S && k0 + s < k1; ++s) issue(s, k0 + s);
+    int issued = min(S, k1 - k0);   // planes issued into the ring so far
+    bool block_fail = false;
 
     uint32_t c = valid ? (uint32_t)i + (uint32_t)nx * j + nxy * k0 : 0u;
     float hx_km1 = 0.0f, hy_km1 = 0.0f;
@@ -422,21 +424,23 @@ __global__ void __launch_bounds__(BX * BY) k_e_tma(StepArgs a, const __grid_cons
                 }
             }
         }
-        __syncthreads();   // slot s is free again
-        if (tid == 0 && k + S < k1) issue(s, k + S);
+        // slot s is free again; the barrier also ORs the threads' wait
+        // verdicts, so every thread sees the same block_fail
+        block_fail = __syncthreads_or(fail);
+        if (block_fail) break;   // issue nothing more; drained below
+        if (k + S < k1) {
+            if (tid == 0) issue(s, k + S);
+            issued = it + S + 1;
+        }
         pg = ng;
         c += nxy;
     }
     cp_async_wait_all();
-    if (fail) {
+    if (block_fail) {
         // A wait gave up: record it, then give the copies still in flight a
         // bounded chance to land before the block's shared memory is released.
         if (tid == 0) atomicOr(a.err, 1);
-        const int planes = k1 - k0;
-        for (int s = 0; s < S && s < planes; ++s) {
-            const int uses = (planes - s + S - 1) / S;
-            mbar_wait_bounded(&bar[s], (uses - 1) & 1, kWaitLimit);
-        }
+        drain_ring(bar, S, issued, kWaitLimit);
     }
     if (face && (tid & 31) == 0) {
         const unsigned slot = warp_slot();
@@ -502,6 +506,8 @@ __global__ void __launch_bounds__(BX * BY) k_hg_tma(StepArgs a, const __grid_con
     __syncthreads();
     if (tid == 0)
         for (int s = 0; s < S && s < total; ++s) issue(s, s);
+    int issued = min(S, total);   // planes issued into the ring so far
+    bool block_fail = false;
 
     uint32_t c = valid ? (uint32_t)i + (uint32_t)nx * j + nxy * k0 : 0u;
     bool fail = !mbar_wait_bounded(&bar[0], 0, kWaitLimit);
@@ -532,18 +538,21 @@ __global__ void __launch_bounds__(BX * BY) k_hg_tma(StepArgs a, const __grid_con
             f.hy[c] = hy;
             f.hz[c] = hz;
         }
-        __syncthreads();   // slot s is free again
-        if (tid == 0 && p + S < total) issue(s, p + S);
+        // slot s is free again; the barrier also ORs the threads' wait
+        // verdicts, so every thread sees the same block_fail
+        block_fail = __syncthreads_or(fail);
+        if (block_fail) break;   // issue nothing more; drained below
+        if (p + S < total) {
+            if (tid == 0) issue(s, p + S);
+            issued = p + S + 1;
+        }
         c += nxy;
     }
-    if (fail) {
+    if (block_fail) {
         // A wait gave up: record it, then give the copies still in flight a
         // bounded chance to land before the block's shared memory is released.
         if (tid == 0) atomicOr(a.err, 1);
-        for (int s = 0; s < S && s < total; ++s) {
-            const int uses = (total - s + S - 1) / S;
-            mbar_wait_bounded(&bar[s], (uses - 1) & 1, kWaitLimit);
-        }
+        drain_ring(bar, S, issued, kWaitLimit);
     }
 }
 

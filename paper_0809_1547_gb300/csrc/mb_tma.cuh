@@ -48,6 +48,18 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     return false;
 }
 
+// Drain of a ring of S mbarrier slots after a bounded wait gave up in the
+// block: planes 0 .. issued-1 went to slot (plane % S); for each slot, wait
+// (bounded) for the phase of the last plane issued into it, so that no copy
+// is still landing in shared memory once the block exits.  Called by every
+// thread of the block after the plane loop stopped issuing.
+__device__ __forceinline__ void drain_ring(uint64_t* bar, int S, int issued, int limit) {
+    for (int s = 0; s < S && s < issued; ++s) {
+        const int last = s + ((issued - 1 - s) / S) * S;
+        mbar_wait_bounded(&bar[s], (uint32_t)((last / S) & 1), limit);
+    }
+}
+
 // 3-D tiled bulk copy of the tensor-map box at (x, y, z) into shared memory
 // `dst` (128-byte aligned); completes `bar` by the box's byte count.  Out of
 // range elements are filled with zeros.  x * element size must be a
