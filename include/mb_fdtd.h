@@ -463,7 +463,8 @@ int mb_gp_features(const double* E, int nE, int n_grid, double* w_phi, double* p
  * loading the library holds until exit; hence ncell <= 67,108,864
  * (MB_ERR_ARG beyond).  The first call on a device, with that device
  * current, looks up the array's device address; make that first call before
- * any stream capture.  Calls share the array: calls that overlap on the GPU
+ * any stream capture.  The address belongs to the device's context: after a
+ * device reset the next call looks it up again (also before any capture).  Calls share the array: calls that overlap on the GPU
  * (different streams or threads) race and must be serialised by the caller.
  * Errors: MB_ERR_ARG, MB_ERR_CUDA; the message is mb_last_error(NULL). */
 int mb_energy_sum_noalloc(const float* d_ex, const float* d_ey, const float* d_ez,

@@ -29,10 +29,44 @@ static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
 
 // In host code the name g_noalloc_scratch is a host-side stand-in, not a
 // device address: the kernels receive the address cudaGetSymbolAddress
-// returned for the current device.
+// returned for the current device.  That address belongs to the device's
+// context; a device reset (cudaDeviceReset) replaces the context and
+// reloads the module, so the cached address is kept with the context's
+// process-unique id and looked up again when the id changes.
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
-NoAllocScratch* g_noalloc_ptr[kMaxDevices] = {nullptr};
+struct NoAllocSlot {
+    NoAllocScratch* ptr;
+    unsigned long long ctx_id;
+};
+NoAllocSlot g_noalloc_slot[kMaxDevices] = {};
+
+using PfnCtxGetCurrent = CUresult (*)(CUcontext*);
+using PfnCtxGetId = CUresult (*)(CUcontext, unsigned long long*);
+
+// The current context's id (cuCtxGetId, through the runtime's driver
+// entry-point query); false when there is no current context yet or the
+// driver does not provide the calls.
+bool current_context_id(unsigned long long* id) {
+    static PfnCtxGetCurrent get_current = nullptr;
+    static PfnCtxGetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<PfnCtxGetCurrent>(p);
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<PfnCtxGetId>(p);
+    });
+    if (!get_current || !get_id) return false;
+    CUcontext ctx = nullptr;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return false;
+    return get_id(ctx, id) == CUDA_SUCCESS;
+}
 
 // Pass 1: block b sums w |E|^2 + |H|^2 over cells [b C, (b+1) C) in FP64.
 __global__ void __launch_bounds__(kNoAllocThreads)
@@ -87,22 +121,28 @@ int noalloc_fail(int code, const std::string& msg) {
     return code;
 }
 
-// Address of the array on the current device, looked up on the first call
-// made with that device current.
+// Address of the array on the current device: looked up on the first call
+// made with that device current, and again once the device's context has
+// been replaced (the cached context id no longer matches).
 int noalloc_scratch(NoAllocScratch** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return noalloc_fail(MB_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(MB_ERR_ARG, "device index beyond 64");
+    unsigned long long id = 0;
+    const bool have_id = current_context_id(&id);
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
+    NoAllocSlot& slot = g_noalloc_slot[dev];
+    if (!slot.ptr || !have_id || slot.ctx_id != id) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p)
             return noalloc_fail(MB_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-        g_noalloc_ptr[dev] = static_cast<NoAllocScratch*>(p);
+        slot.ptr = static_cast<NoAllocScratch*>(p);
+        // the lookup made the context current if it was not yet
+        slot.ctx_id = current_context_id(&id) ? id : 0ull;
     }
-    *out = g_noalloc_ptr[dev];
+    *out = slot.ptr;
     return MB_OK;
 }
 
