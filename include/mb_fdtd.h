@@ -237,6 +237,18 @@ int mb_flux(mb_ctx* ctx, double* out_flux6);
  * Errors: MB_ERR_ARG (null output), MB_ERR_CUDA. */
 int mb_flux_async(mb_ctx* ctx, double* host_out6);
 
+/* Diagnostic copy of the CPML memories of the slabs along one axis (0: x,
+ * 1: y, 2: z) to host memory, SI units (FP64).  *count receives the number
+ * of values (host_out may be NULL to query it; 0 without CPML).  Four planes
+ * f of equal size: f = 0, 1 the E-update memories (A/m^2; x: Ey, Ez, y: Ex,
+ * Ez, z: Ex, Ey), f = 2, 3 the H-update memories (V/m^2; x: Hy, Hz, y: Hx,
+ * Hz, z: Hx, Hy), each the running convolution psi <- b psi + c dF/dw of the
+ * derivative along the axis (Roden & Gedney 2000).  Index of slab layer s
+ * (s = i for i < npml, i - n + 2 npml for i >= n - npml):
+ *   x: ((f n_z + k) n_y + j) 2 npml + s,   y: ((f n_z + k) 2 npml + s) n_x + i,
+ *   z: ((f zn + s) n_y + j) n_x + i with zn = 2 npml layers (s as above). */
+int mb_get_cpml(mb_ctx* ctx, int axis, double* host_out, size_t* count);
+
 /* Copy one field (MB_EX..MB_N3) to / from host memory (n cells, SI units).
  * N0 is derived (N_a minus the other three) and cannot be set. */
 int mb_get_field(mb_ctx* ctx, int which, float* host_out);
@@ -389,6 +401,66 @@ int mb_batch_get_mode(mb_batch* batch, int* mode);
 /* Tile shape of the persistent kernel: out3 = {bx, by, kz} (a block of bx x by
  * threads walks kz z-planes of one tile). */
 int mb_batch_get_tuning(mb_batch* batch, int* out3);
+
+/* ------------------------------------------------------------------------
+ * One grid split along z into slabs.  The paper runs its FDTD grid
+ * "distributed on (typically) 256 processors" ("Simulations" paragraph);
+ * here each slab is a context of its own (on one GPU or on several) and
+ * neighbouring slabs exchange one plane each way per step.
+ *
+ * A slab context holds the planes z_begin .. z_end-1 of a grid of grid[2]
+ * planes (its own planes) plus a ghost plane next to each neighbour: local
+ * plane 0 is plane z_begin - 1 when z_begin > 0, and the last local plane
+ * is plane z_end when z_end < grid[2].  All other calls address the
+ * context's local planes (host arrays of mb_set_material, mb_get_field,
+ * probe and source cells are n_x x n_y x local n_z, ghost planes included;
+ * mb_set_material must be given the whole grid's values on the ghost planes
+ * too).  The whole grid's boundaries hold: PEC walls and the CPML profile of
+ * the whole grid along z, the Langevin noise keyed by each cell's index in
+ * the whole grid (so a split run draws the same noise as the whole grid),
+ * the face-flux box of the whole grid cut to the own planes, mb_energy over
+ * the own planes only.  Face probes and the adjoint are not available on a
+ * slab (MB_ERR_STATE).
+ *
+ * Step protocol (what makes the split run equal, cell by cell, to the whole
+ * grid): before every step, for each pair of neighbouring slabs A (below)
+ * and B (above), mb_halo_pack(A, 1, buf) then mb_halo_unpack(B, 0, buf), and
+ * mb_halo_pack(B, 0, buf') then mb_halo_unpack(A, 1, buf'); then mb_step(ctx,
+ * 1) on every slab.  A packed plane is the whole time-n state of a boundary
+ * plane (E, H, P, J, populations, x / y CPML memories).  The own cells'
+ * fields then equal the whole grid's bit for bit; the FP64 read-outs (energy,
+ * face flux) summed over the slabs equal the whole grid's up to the order of
+ * summation.  mb_step(ctx, n > 1) without exchanges in between leaves the
+ * boundary planes wrong.
+ * ------------------------------------------------------------------------ */
+
+/* Create the slab context of planes [z_begin, z_end) of a grid[0] x grid[1]
+ * x grid[2] grid; other arguments as mb_create.  A cut plane z_begin > 0 or
+ * z_end < grid[2] must lie in [npml + 1, grid[2] - npml - 1] (ghost planes
+ * outside the z-CPML), and the whole grid must have fewer than 2^32 cells
+ * (the noise counter).  Errors: as mb_create, MB_ERR_ARG for a bad range or
+ * cut. */
+int mb_create_slab(mb_ctx** out, const int grid[3], int z_begin, int z_end, double dx,
+                   double dt, const mb_params* p, void* cuda_stream);
+
+/* info = (whole grid's n_z, whole-grid plane of local plane 0, first own
+ * local plane, one past the last own local plane); for a context made by
+ * mb_create: (n_z, 0, 0, n_z). */
+int mb_slab_info(mb_ctx* ctx, int info[4]);
+
+/* Bytes of one packed boundary plane: 4 (15 n_x n_y + 8 npml (n_x + n_y)). */
+int mb_halo_bytes(mb_ctx* ctx, size_t* bytes);
+
+/* Pack the state of the lowest (side 0) or highest (side 1) own plane into
+ * d_buf, a device buffer of mb_halo_bytes on the context's device; queued
+ * on the context's stream.  Errors: MB_ERR_ARG, MB_ERR_STATE (not a slab). */
+int mb_halo_pack(mb_ctx* ctx, int side, void* d_buf);
+
+/* Write a neighbour's packed plane (d_buf, as mb_halo_pack wrote it) into
+ * the ghost plane below (side 0) or above (side 1); queued on the context's
+ * stream, which must be ordered after the pack.  Errors: MB_ERR_ARG,
+ * MB_ERR_STATE (not a slab, or no ghost plane on that side). */
+int mb_halo_unpack(mb_ctx* ctx, int side, const void* d_buf);
 
 /* ------------------------------------------------------------------------
  * Adjoint gradient of emitted energy.  The paper observes emission through

@@ -57,6 +57,12 @@ _SIGS = [
     ("mb_create", C.c_int, [C.POINTER(_P), C.POINTER(C.c_int), C.c_double, C.c_double,
                             C.POINTER(mb_params), _P]),
     ("mb_destroy", C.c_int, [_P]),
+    ("mb_create_slab", C.c_int, [C.POINTER(_P), C.POINTER(C.c_int), C.c_int, C.c_int, C.c_double,
+                                 C.c_double, C.POINTER(mb_params), _P]),
+    ("mb_slab_info", C.c_int, [_P, C.POINTER(C.c_int)]),
+    ("mb_halo_bytes", C.c_int, [_P, C.POINTER(C.c_size_t)]),
+    ("mb_halo_pack", C.c_int, [_P, C.c_int, _P]),
+    ("mb_halo_unpack", C.c_int, [_P, C.c_int, _P]),
     ("mb_set_material", C.c_int, [_P, _P, _P, C.c_double, C.c_double]),
     ("mb_set_seed", C.c_int, [_P, C.c_uint64]),
     ("mb_add_point_probe", C.c_int, [_P, C.POINTER(C.c_int), C.c_int, C.c_double, C.c_double,
@@ -80,6 +86,7 @@ _SIGS = [
     ("mb_face_spectrum", C.c_int, [_P, C.c_int, _P, _P]),
     ("mb_energy", C.c_int, [_P, C.POINTER(C.c_double), _P]),
     ("mb_get_field", C.c_int, [_P, C.c_int, _P]),
+    ("mb_get_cpml", C.c_int, [_P, C.c_int, _P, C.POINTER(C.c_size_t)]),
     ("mb_set_field", C.c_int, [_P, C.c_int, _P]),
     ("mb_get_field_device", C.c_int, [_P, C.c_int, _P, C.POINTER(C.c_double)]),
     ("mb_save_state", C.c_int, [_P, _P, C.POINTER(C.c_size_t)]),
@@ -177,6 +184,39 @@ def mb_create(grid, dx, dt, params: mb_params | None = None, stream: int | None 
 def mb_destroy(h):
     if h:
         _check(load_library().mb_destroy(h))
+
+
+def mb_create_slab(grid, z_begin, z_end, dx, dt, params: mb_params | None = None,
+                   stream: int | None = None):
+    lib = load_library()
+    h = C.c_void_p()
+    g = (C.c_int * 3)(*[int(v) for v in grid])
+    _check(lib.mb_create_slab(C.byref(h), g, int(z_begin), int(z_end), float(dx), float(dt),
+                              C.byref(params) if params is not None else None,
+                              C.c_void_p(stream) if stream else None))
+    return h
+
+
+def mb_slab_info(h):
+    """(whole grid's n_z, whole-grid plane of local plane 0, first own local
+    plane, one past the last own local plane)."""
+    out = (C.c_int * 4)()
+    _check(load_library().mb_slab_info(h, out), h)
+    return tuple(out)
+
+
+def mb_halo_bytes(h) -> int:
+    b = C.c_size_t()
+    _check(load_library().mb_halo_bytes(h, C.byref(b)), h)
+    return b.value
+
+
+def mb_halo_pack(h, side: int, dev_ptr: int):
+    _check(load_library().mb_halo_pack(h, int(side), C.c_void_p(dev_ptr)), h)
+
+
+def mb_halo_unpack(h, side: int, dev_ptr: int):
+    _check(load_library().mb_halo_unpack(h, int(side), C.c_void_p(dev_ptr)), h)
 
 
 def mb_set_material(h, eps_map, gain_mask, N_a, pump):
@@ -330,6 +370,20 @@ def mb_energy(h):
     fl = np.zeros(6)
     _check(load_library().mb_energy(h, C.byref(U), _ptr(fl)), h)
     return U.value, fl
+
+
+def mb_get_cpml(h, axis: int):
+    """CPML memories of the slabs along `axis` (SI, FP64), shaped (4, ...) by
+    the layout of mb_get_cpml: x (4, n_z, n_y, 2L), y (4, n_z, 2L, n_x),
+    z (4, zn, n_y, n_x); None without CPML."""
+    lib = load_library()
+    n = C.c_size_t()
+    _check(lib.mb_get_cpml(h, int(axis), None, C.byref(n)), h)
+    if n.value == 0:
+        return None
+    out = np.zeros(n.value, dtype=np.float64)
+    _check(lib.mb_get_cpml(h, int(axis), _ptr(out), C.byref(n)), h)
+    return out
 
 
 def mb_get_field(h, which, shape):
@@ -637,6 +691,20 @@ class MBSimulation:
 
     def field(self, name):
         return mb_get_field(self._h, name, self.shape)
+
+    def cpml(self, axis: int):
+        """CPML memories along `axis` (SI), shaped (4, ...) as in mb_get_cpml:
+        x (4, n_z, n_y, 2L), y (4, n_z, 2L, n_x), z (4, zn, n_y, n_x)."""
+        v = mb_get_cpml(self._h, axis)
+        if v is None:
+            return None
+        nx, ny, nz = self.grid
+        per = v.size // 4
+        if axis == 0:
+            return v.reshape(4, nz, ny, per // (nz * ny))
+        if axis == 1:
+            return v.reshape(4, nz, per // (nz * nx), nx)
+        return v.reshape(4, per // (ny * nx), ny, nx)
 
     def set_field(self, name, values):
         mb_set_field(self._h, name, np.asarray(values).reshape(-1))

@@ -490,6 +490,7 @@ extern "C" int mb_adjoint_energy_zface(mb_ctx* c, int n_steps, int ckpt_every, i
     mb::join_probes(c);
     if (n_steps < 1) return afail(c, MB_ERR_ARG, "n_steps must be >= 1");
     if (!c->have_material) return afail(c, MB_ERR_STATE, "no material set");
+    if (c->slab) return afail(c, MB_ERR_STATE, "the adjoint runs on a whole grid, not on a z-slab");
     const int zp = z_plane < 0 ? c->args.flux.phi[2] : z_plane;
     if (zp < 1 || zp >= c->nz) return afail(c, MB_ERR_ARG, "z plane must satisfy 1 <= p < n_z");
     const int K = std::min(ckpt_every > 0 ? ckpt_every : 200, n_steps);

@@ -126,6 +126,17 @@ double field_scale(const mb_ctx* c, int which) {
     return c->N_a;
 }
 
+// The z-CPML region of the context's planes: the whole grid's CPML planes
+// (k < L or k >= gnz - L in the grid's numbering) in local planes, and the
+// layers the context stores for them (see DevCpml).
+void z_cpml_bounds(const mb_ctx* c, mb::DevCpml& m) {
+    const int L = c->p.npml;
+    m.zlo = L - c->kz0;
+    m.zhi = c->gnz - L - c->kz0;
+    m.zs = std::max(0, m.zlo);
+    m.zn = L ? m.zs + std::max(0, c->nz - m.zhi) : 0;
+}
+
 void build_args(mb_ctx* c) {
     mb::StepArgs& a = c->args;
     a.g = {c->nx, c->ny, c->nz, (uint32_t)c->nx * (uint32_t)c->ny, (uint32_t)c->ncell};
@@ -139,6 +150,7 @@ void build_args(mb_ctx* c) {
     a.f.lut_inv_eps = c->d_lut;
     const int L = c->p.npml;
     a.pml.L = L;
+    z_cpml_bounds(c, a.pml);
     point_args_at(a, c, c->parity);
     const float* t = c->d_coef;
     const int n3[3] = {c->nx, c->ny, c->nz};
@@ -158,6 +170,16 @@ void build_args(mb_ctx* c) {
         a.flux.r1[w] = r.second;
         a.flux.plo[w] = r.first;
         a.flux.phi[w] = r.second;
+    }
+    if (c->slab) {
+        // the whole grid's box in local planes, cut to the slab's own planes
+        // (face planes outside them become -1: never met)
+        const auto r = interior(c->gnz, L);
+        const int lo = r.first - c->kz0, hi = r.second - c->kz0;
+        a.flux.r0[2] = std::max(lo, c->own_lo);
+        a.flux.r1[2] = std::min(hi, c->own_hi);
+        a.flux.plo[2] = (lo >= c->own_lo && lo < c->own_hi) ? lo : -1;
+        a.flux.phi[2] = (hi >= c->own_lo && hi < c->own_hi) ? hi : -1;
     }
     a.flux.acc = c->d_flux;
     a.S = (float)c->S;
@@ -228,6 +250,7 @@ void gain_coefficients(mb_ctx* c) {
     if (c->N_a > 0.0) gain_table(c->p, c->dt, c->dx, c->N_a, c->W_p, c->E0, G);
     G.key0 = (uint32_t)(c->seed & 0xffffffffu);
     G.key1 = (uint32_t)(c->seed >> 32);
+    G.cell0 = (uint32_t)((int64_t)c->kz0 * c->nx * c->ny);
 }
 
 int check_ctx_nojoin(mb_ctx* c) {
@@ -589,8 +612,8 @@ const char* mb_last_error(const mb_ctx* ctx) {
     return ctx ? ctx->err.c_str() : g_err.c_str();
 }
 
-int mb_create(mb_ctx** out, const int grid[3], double dx, double dt, const mb_params* p,
-              void* cuda_stream) {
+static int check_create_args(mb_ctx** out, const int grid[3], double dx, double dt,
+                             const mb_params* p, mb_params& prm) {
     if (!out || !grid) return fail(nullptr, MB_ERR_ARG, "null argument");
     *out = nullptr;
     if (grid[0] < 1 || grid[1] < 1 || grid[2] < 1) return fail(nullptr, MB_ERR_ARG, "grid sizes must be >= 1");
@@ -598,18 +621,30 @@ int mb_create(mb_ctx** out, const int grid[3], double dx, double dt, const mb_pa
     if (ncell >= (int64_t(1) << 32)) return fail(nullptr, MB_ERR_ARG, "more than 2^32 cells");
     if (!(dx > 0) || !(dt > 0)) return fail(nullptr, MB_ERR_ARG, "dx and dt must be > 0");
     if (dt > dx / (kC0 * std::sqrt(3.0))) return fail(nullptr, MB_ERR_COURANT, "dt above the 3D Courant limit dx/(c sqrt 3)");
-    mb_params prm;
     mb_default_params(&prm);
     if (p) prm = *p;
     if (prm.npml < 0 || !(prm.lambda0 > 0) || !(prm.dlambda > 0) || !(prm.tau21 > 0) ||
         !(prm.tau32 > 0) || !(prm.tau10 > 0) || !(prm.n_ref > 0) || prm.n_floor_rel < 0)
         return fail(nullptr, MB_ERR_ARG, "invalid parameter");
+    return MB_OK;
+}
 
+// A context over grid (local planes); its z-window is planes kz0 .. kz0 +
+// grid[2] - 1 of a grid of gnz planes, of which [own_lo, own_hi) are its own
+// (the whole grid: gnz = grid[2], kz0 = own_lo = 0, own_hi = grid[2]).
+static int create_ctx(mb_ctx** out, const int grid[3], int gnz, int kz0, int own_lo, int own_hi,
+                      bool slab, double dx, double dt, const mb_params& prm, void* cuda_stream) {
+    const int64_t ncell = (int64_t)grid[0] * grid[1] * grid[2];
     mb_ctx* c = new mb_ctx();
     c->nx = grid[0];
     c->ny = grid[1];
     c->nz = grid[2];
     c->ncell = ncell;
+    c->slab = slab;
+    c->gnz = gnz;
+    c->kz0 = kz0;
+    c->own_lo = own_lo;
+    c->own_hi = own_hi;
     c->dx = dx;
     c->dt = dt;
     c->p = prm;
@@ -647,7 +682,9 @@ int mb_create(mb_ctx** out, const int grid[3], double dx, double dt, const mb_pa
     const int L = prm.npml;
     c->psi_elems[0] = L ? (size_t)4 * c->nz * c->ny * 2 * L : 0;
     c->psi_elems[1] = L ? (size_t)4 * c->nz * 2 * L * c->nx : 0;
-    c->psi_elems[2] = L ? (size_t)4 * 2 * L * c->ny * c->nx : 0;
+    mb::DevCpml zb{};
+    z_cpml_bounds(c, zb);
+    c->psi_elems[2] = (size_t)4 * zb.zn * c->ny * c->nx;
     for (int w = 0; w < 3; ++w)
         if ((rc = alloc((void**)&c->d_psi[w], sizeof(float) * c->psi_elems[w]))) return bail(rc);
     const size_t ncoef = 4 * (size_t)(c->nx + c->ny + c->nz);
@@ -665,10 +702,19 @@ int mb_create(mb_ctx** out, const int grid[3], double dx, double dt, const mb_pa
     std::vector<float> coef(ncoef);
     float* t = coef.data();
     const int n3[3] = {c->nx, c->ny, c->nz};
-    for (int w = 0; w < 3; ++w) {
+    for (int w = 0; w < 2; ++w) {
         cpml_table(n3[w], 0.0, L, dx, dt, prm, t, t + n3[w]);
         cpml_table(n3[w], 0.5, L, dx, dt, prm, t + 2 * n3[w], t + 3 * n3[w]);
         t += 4 * n3[w];
+    }
+    {
+        // z: the whole grid's profile, the context's planes of it
+        std::vector<float> zt(4 * (size_t)gnz);
+        cpml_table(gnz, 0.0, L, dx, dt, prm, zt.data(), zt.data() + gnz);
+        cpml_table(gnz, 0.5, L, dx, dt, prm, zt.data() + 2 * gnz, zt.data() + 3 * gnz);
+        for (int q = 0; q < 4; ++q)
+            std::copy(zt.begin() + (size_t)q * gnz + kz0, zt.begin() + (size_t)q * gnz + kz0 + c->nz,
+                      t + (size_t)q * c->nz);
     }
     std::vector<float> lut(256, 1.0f);
     c->h_lut_eps.assign(128, 1.0f);
@@ -703,6 +749,41 @@ int mb_create(mb_ctx** out, const int grid[3], double dx, double dt, const mb_pa
         }
     }
     *out = c;
+    return MB_OK;
+}
+
+int mb_create(mb_ctx** out, const int grid[3], double dx, double dt, const mb_params* p,
+              void* cuda_stream) {
+    mb_params prm;
+    if (int rc = check_create_args(out, grid, dx, dt, p, prm)) return rc;
+    return create_ctx(out, grid, grid[2], 0, 0, grid[2], false, dx, dt, prm, cuda_stream);
+}
+
+int mb_create_slab(mb_ctx** out, const int grid[3], int z_begin, int z_end, double dx, double dt,
+                   const mb_params* p, void* cuda_stream) {
+    mb_params prm;
+    if (int rc = check_create_args(out, grid, dx, dt, p, prm)) return rc;
+    const int gnz = grid[2], L = prm.npml;
+    if (z_begin < 0 || z_end > gnz || z_begin >= z_end)
+        return fail(nullptr, MB_ERR_ARG, "need 0 <= z_begin < z_end <= grid[2]");
+    // a cut plane c leaves ghost planes c - 1 and c, which must lie outside
+    // the z-CPML (their CPML memories along z are not exchanged)
+    auto bad_cut = [&](int cut) { return cut < L + 1 || cut > gnz - L - 1; };
+    if ((z_begin > 0 && bad_cut(z_begin)) || (z_end < gnz && bad_cut(z_end)))
+        return fail(nullptr, MB_ERR_ARG, "cut planes must lie in [npml + 1, grid[2] - npml - 1]");
+    const int below = z_begin > 0 ? 1 : 0, above = z_end < gnz ? 1 : 0;
+    const int local[3] = {grid[0], grid[1], z_end - z_begin + below + above};
+    return create_ctx(out, local, gnz, z_begin - below, below, below + z_end - z_begin,
+                      true, dx, dt, prm, cuda_stream);
+}
+
+int mb_slab_info(mb_ctx* c, int info[4]) {
+    if (int rc = check_ctx_nojoin(c)) return rc;
+    if (!info) return fail(c, MB_ERR_ARG, "null output");
+    info[0] = c->gnz;
+    info[1] = c->kz0;
+    info[2] = c->own_lo;
+    info[3] = c->own_hi;
     return MB_OK;
 }
 
@@ -870,6 +951,7 @@ int mb_add_point_probe(mb_ctx* c, const int ijk[3], int n_freq, double lam_min, 
 
 int mb_add_face_probes(mb_ctx* c, int stride, int every, int n_freq, double lam_min, double lam_max) {
     if (int rc = check_ctx(c)) return rc;
+    if (c->slab) return fail(c, MB_ERR_STATE, "face probes are not available on a z-slab context");
     if (stride < 1 || every < 1 || n_freq < 1 || n_freq > 4096 || !(lam_min > 0) || !(lam_max > 0))
         return fail(c, MB_ERR_ARG, "bad face-probe arguments (1 <= n_freq <= 4096)");
     cudaStreamSynchronize(c->stream);
@@ -1179,8 +1261,17 @@ int mb_energy(mb_ctx* c, double* out_U, double* out_flux6) {
     if (int rc = check_ctx(c)) return rc;
     if (!out_U) return fail(c, MB_ERR_ARG, "null output");
     MB_CUDA(c, cudaMemsetAsync(c->d_nonfinite, 0, sizeof(int), c->stream));
-    mb::launch_energy(c->args.f, c->ncell, c->d_lut + 128, c->d_partial, c->n_partial,
-                      c->d_nonfinite, c->d_energy, c->stream);
+    // the context's own planes (all of them but a z-slab's ghost planes)
+    const int64_t off = (int64_t)c->own_lo * c->nx * c->ny;
+    const int64_t own = (int64_t)(c->own_hi - c->own_lo) * c->nx * c->ny;
+    mb::DevFields f = c->args.f;
+    for (float** q : {&f.ex, &f.ey, &f.ez, &f.hx, &f.hy, &f.hz, &f.px, &f.py, &f.pz, &f.jx, &f.jy,
+                      &f.jz, &f.n1, &f.n2, &f.n3})
+        *q += off;
+    f.mat += off;
+    if (f.inv_eps) f.inv_eps += off;
+    mb::launch_energy(f, own, c->d_lut + 128, c->d_partial, c->n_partial, c->d_nonfinite,
+                      c->d_energy, c->stream);
     MB_CUDA(c, cudaGetLastError());
     double U = 0, slots[6 * mb::kFluxSlots], fl[6];
     int bad = 0;
@@ -1196,6 +1287,25 @@ int mb_energy(mb_ctx* c, double* out_U, double* out_flux6) {
     }
     if (bad) return fail(c, MB_ERR_NONFINITE, "non-finite field values");
     return check_device_error(c);
+}
+
+int mb_get_cpml(mb_ctx* c, int axis, double* host_out, size_t* count) {
+    if (int rc = check_ctx(c)) return rc;
+    if (axis < 0 || axis > 2) return fail(c, MB_ERR_ARG, "axis must be 0, 1 or 2");
+    const size_t n = c->psi_elems[axis];
+    if (count) *count = n;
+    if (!host_out || n == 0) return MB_OK;
+    std::vector<float> tmp(n);
+    MB_CUDA(c, cudaMemcpyAsync(tmp.data(), psi_of(c, c->parity, axis), sizeof(float) * n,
+                               cudaMemcpyDeviceToHost, c->stream));
+    MB_CUDA(c, cudaStreamSynchronize(c->stream));
+    // planes f = 0, 1 hold E-update memories (H differences), f = 2, 3 the
+    // H-update ones (E differences): psi_E = psi_E,s E0 / (eta0 dx),
+    // psi_H = psi_H,s E0 / dx
+    const size_t per_f = n / 4;
+    const double se = c->E0 / (c->eta0 * c->dx), sh = c->E0 / c->dx;
+    for (size_t q = 0; q < n; ++q) host_out[q] = (q / per_f < 2 ? se : sh) * (double)tmp[q];
+    return MB_OK;
 }
 
 int mb_get_field(mb_ctx* c, int which, float* host_out) {

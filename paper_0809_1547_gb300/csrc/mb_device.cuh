@@ -43,9 +43,15 @@ struct DevFields {
 // s = i (i < L) or s = i - n + 2L (i >= n - L).  Four planes per slab axis:
 // f = 0, 1: the two E components with a w-derivative, f = 2, 3: the two H
 // components.  x-slab index ((f nz + k) ny + j) 2L + s, y-slab
-// ((f nz + k) 2L + s) nx + i, z-slab ((f 2L + s) ny + j) nx + i.
+// ((f nz + k) 2L + s) nx + i, z-slab ((f zn + s) ny + j) nx + i.
+// Along z the slab region is stated by its bounds: plane k lies in it when
+// k < zlo or k >= zhi, at layer s = k (k < zlo) or s = k - zhi + zs, with zn
+// layers stored.  A whole grid has zlo = L, zhi = nz - L, zs = L, zn = 2L
+// (the same layers as x and y); a z-slab of a grid split along z holds only
+// the CPML planes of the whole grid that fall inside it.
 struct DevCpml {
     int L;
+    int zlo, zhi, zs, zn;
     float *psx, *psy, *psz;
     const float *bex, *cex, *bhx, *chx;
     const float *bey, *cey, *bhy, *chy;
@@ -62,6 +68,10 @@ struct DevGain {
     float G[3][3];
     float mk[3];
     uint32_t key0, key1;
+    // index of the realization's cell that local cell 0 is: the noise is
+    // keyed by the cell's index in the whole grid (0 unless this is a
+    // z-slab of a grid split along z)
+    uint32_t cell0;
 };
 
 // Soft current source: the scaled current of step n is wave[n - n0] for
@@ -276,9 +286,9 @@ __device__ __forceinline__ void h_pml(const StepArgs& a, int i, int j, int k, co
         cx += psi_xy;
         cz -= psi_zy;
     }
-    if (k < L || k >= nz - L) {
-        const uint32_t s = slab_index(k, nz, L);
-        const uint32_t plane = (uint32_t)L2 * ny * nx;
+    if (k < a.pml.zlo || k >= a.pml.zhi) {
+        const uint32_t s = (k < a.pml.zlo) ? k : k - a.pml.zhi + a.pml.zs;
+        const uint32_t plane = (uint32_t)a.pml.zn * ny * nx;
         const uint32_t q = (s * ny + j) * nx + i;
         const float b = __ldg(a.pml.bhz + k), cc = __ldg(a.pml.chz + k);
         const float* p = a.pml.psz;
@@ -355,7 +365,7 @@ __device__ __forceinline__ void lorentz_step(const DevGain& G, uint32_t c, long 
     const float dn = n1 - n2;
     const float amp = G.cJN * sqrtf(fmaxf(n2, 0.0f) + G.nfloor);
     float z0, z1, z2;
-    langevin_normals(c, (uint32_t)n, G.key0, G.key1, z0, z1, z2);
+    langevin_normals(c + G.cell0, (uint32_t)n, G.key0, G.key1, z0, z1, z2);
     const float kE = G.cJE * dn;
     jx = fmaf(amp, z0, fmaf(-G.cJP, px, fmaf(kE, ex0, G.cJ1 * jx)));
     jy = fmaf(amp, z1, fmaf(-G.cJP, py, fmaf(kE, ey0, G.cJ1 * jy)));
@@ -418,9 +428,9 @@ __device__ __forceinline__ void e_pml(const StepArgs& a, int i, int j, int k, co
         cx += psi_xy;
         cz -= psi_zy;
     }
-    if (k < L || k >= nz - L) {
-        const uint32_t s = slab_index(k, nz, L);
-        const uint32_t plane = (uint32_t)L2 * ny * nx;
+    if (k < a.pml.zlo || k >= a.pml.zhi) {
+        const uint32_t s = (k < a.pml.zlo) ? k : k - a.pml.zhi + a.pml.zs;
+        const uint32_t plane = (uint32_t)a.pml.zn * ny * nx;
         const uint32_t q = (s * ny + j) * nx + i;
         const float b = __ldg(a.pml.bez + k), cc = __ldg(a.pml.cez + k);
         const float* p = a.pml.psz;

@@ -255,6 +255,14 @@ struct PointProbeHost {
 struct mb_ctx {
     int nx = 0, ny = 0, nz = 0;
     int64_t ncell = 0;
+    // z-window.  A context may hold one z-slab of a grid split along z
+    // (mb_create_slab): local plane k is plane k + kz0 of the whole grid of
+    // gnz planes; planes [own_lo, own_hi) are the slab's own, the others (at
+    // most one below and one above) are ghost planes that receive the
+    // neighbouring slabs' boundary planes before every step.  A whole grid
+    // has gnz = nz, kz0 = 0, own_lo = 0, own_hi = nz.
+    bool slab = false;
+    int gnz = 0, kz0 = 0, own_lo = 0, own_hi = 0;
     double dx = 0, dt = 0;
     mb_params p{};
     int device = 0;

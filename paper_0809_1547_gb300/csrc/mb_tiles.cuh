@@ -85,8 +85,7 @@ __device__ __forceinline__ bool tile_in_xy_slab(const StepArgs& a, int i0, int b
 }
 
 __device__ __forceinline__ bool plane_in_z_slab(const StepArgs& a, int k) {
-    const int L = a.pml.L;
-    return L > 0 && (k < L || k >= a.g.nz - L);
+    return a.pml.L > 0 && (k < a.pml.zlo || k >= a.pml.zhi);
 }
 
 // ------------------------------------------------------------ H tiles
