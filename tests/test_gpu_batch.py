@@ -191,3 +191,41 @@ def test_batch_concurrent_mode_equals_persistent_bitwise():
     assert e.value.code == MB_ERR_ARG
     for bt in (a, c, d):
         bt.close()
+
+
+@pytest.mark.parametrize("mode", ["persistent", "concurrent"])
+def test_full_size_members_sampled_parity(mode):
+    """Three members of the ensemble workload (uneven sides, ~45 % fill,
+    gain in the voids, noise) stepped in the batch: after 20 steps, one more
+    batched step checked against the oracle on sub-blocks of the first
+    member at its walls, corners, CPML interfaces and centre (fields and
+    CPML memories; the block oracle gets the member's own CPML profiles,
+    noise counters and step index)."""
+    from paper_0809_1547_gb300 import inputs
+    from paper_0809_1547_gb300.binding import MBBatch, mb_default_params, \
+        MB_BATCH_PERSISTENT, MB_BATCH_CONCURRENT
+    from parity_util import check_blocks_one_step
+    ws = inputs.workload_batch(n_pump=16, n_seed=5)
+    # members whose sides are not multiples of 16 (the padded layouts' case)
+    picks, sides = [], set()
+    for w in ws:
+        if w.grid[0] % 16 and w.grid[0] not in sides and len(picks) < 3:
+            picks.append(w)
+            sides.add(w.grid[0])
+    b = MBBatch([w.grid for w in picks], picks[0].dx, picks[0].dt,
+                mb_default_params(npml=picks[0].npml))
+    for q, w in enumerate(picks):
+        b.set_instance(q, w.eps, w.gain, w.N_a, w.pump, w.seed)
+    b.set_mode(MB_BATCH_PERSISTENT if mode == "persistent" else MB_BATCH_CONCURRENT)
+    b.step(20)
+    b.synchronize()
+    w, g = picks[0], b.instances[0]
+    n, size = w.grid[0], 18
+    hi, mid = n - size, n // 2 - size // 2
+    los = [(0, 0, 0), (hi, hi, hi), (0, mid, hi), (hi, 0, mid), (mid, hi, 0), (mid, mid, mid)]
+
+    def one():
+        b.step(1)
+        b.synchronize()
+    check_blocks_one_step(g, w, one, los, size, params_kw(npml=w.npml))
+    b.close()

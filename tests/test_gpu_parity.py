@@ -13,7 +13,8 @@ import numpy as np
 import pytest
 
 from oracle.mb_oracle import MBOracle, Params, philox4x32_10, FIELD_NAMES, C0, MU0
-from parity_util import DX, DT, REL_L2_TOL, params_kw, make_pair, rel_l2, assert_fields_match
+from parity_util import DX, DT, REL_L2_TOL, params_kw, make_pair, rel_l2, assert_fields_match, \
+    check_blocks_one_step
 
 pytestmark = pytest.mark.gpu
 
@@ -407,73 +408,59 @@ def test_argument_errors():
     g.close()
 
 
-def _global_state_block(g, lo, size):
-    """Every field of the sub-block [lo, lo + size) (SI, [k, j, i]) read on the device."""
-    i0, j0, k0 = lo
-    out = {}
-    for name in FIELD_NAMES:
-        if name == "N0":
-            continue
-        t, scale = g.field_device(name)
-        out[name] = t[k0:k0 + size, j0:j0 + size, i0:i0 + size].double().cpu().numpy() * scale
-    return out
-
-
 def _sampled_step_parity(w, n_pre, los, B):
     """Advance workload w by n_pre steps in the launch configuration the
-    benchmark times (autotuned), then check one more GPU step on the interior
-    sub-blocks starting at los (edge B) against the oracle's step of the same
-    sub-block (with a one-cell halo; noise counters and step index taken from
-    the full grid); then properties that hold at any size."""
+    benchmark times (autotuned), then check one more GPU step on the
+    sub-blocks of edge B + 2 starting at los against the oracle's step of the
+    same block (the whole grid's CPML profiles, the GPU's CPML memories, the
+    whole grid's noise counters and step index; a one-cell halo left out
+    except along the grid's own walls); then properties that hold at any
+    size."""
     import torch
     from paper_0809_1547_gb300.workloads import setup_simulation
-    nx, ny, nz = w.grid
     g = setup_simulation(w, autotune=True)
     g.step(n_pre)
     g.synchronize()
-    before = [_global_state_block(g, lo, B + 2) for lo in los]
-    n_before = g.n
-    g.step(1)
-    g.synchronize()
-    after = [_global_state_block(g, lo, B + 2) for lo in los]
-    pkw = params_kw(npml=0)
-    for lo, st0, st1 in zip(los, before, after):
-        i0, j0, k0 = lo
-        sl = (slice(k0, k0 + B + 2), slice(j0, j0 + B + 2), slice(i0, i0 + B + 2))
-        o = MBOracle((B + 2,) * 3, w.dx, w.dt, Params(**pkw))
-        o.set_material(w.eps[sl], w.gain[sl], w.N_a, w.pump)
-        o.set_seed(w.seed)
-        kk, jj, ii = np.meshgrid(np.arange(k0, k0 + B + 2), np.arange(j0, j0 + B + 2),
-                                 np.arange(i0, i0 + B + 2), indexing="ij")
-        o.cell_index = (ii + nx * (jj + ny * kk)).astype(np.uint64)
-        o.n = n_before
-        for name, v in st0.items():
-            o.set_field(name, v)
-        gain = w.gain[sl] != 0
-        o.N[0] = np.where(gain, w.N_a - st0["N1"] - st0["N2"] - st0["N3"], 0.0)
-        o.step(1)
-        core = (slice(1, B + 1),) * 3
-        for name, v in st1.items():
-            ref = o.field(name)[core]
-            err = rel_l2(v[core], ref)
-            assert err <= REL_L2_TOL or np.abs(ref).max() == 0 == np.abs(v[core]).max(), (lo, name, err)
+
+    def one():
+        g.step(1)
+        g.synchronize()
+    worst = check_blocks_one_step(g, w, one, los, B + 2, params_kw(npml=w.npml))
     U, fl = g.energy()
     assert math.isfinite(U) and np.all(np.isfinite(fl))
     t, _ = g.field_device("Jx")
     nongain = torch.from_numpy(w.gain == 0).cuda()
     assert float(t[nongain].abs().max()) == 0.0
     g.close()
+    return worst
+
+
+def _boundary_blocks(n, L, size):
+    """Blocks of edge `size` touching the grid's boundary layers: both
+    corners (the PEC walls and all six CPML slabs with their interfaces and
+    the flux box's face planes), and one straddling each CPML interface on
+    each axis away from the corners."""
+    hi = n - size
+    mid = n // 2 - size // 2
+    cut_lo = max(0, L - size // 2)            # straddles the interface at L
+    cut_hi = min(n - size, n - L - size // 2)  # straddles the interface at n - L
+    return [(0, 0, 0), (hi, hi, hi),
+            (cut_lo, mid, mid), (cut_hi, mid, mid), (mid, cut_lo, mid), (mid, cut_hi, mid),
+            (mid, mid, cut_lo), (mid, mid, cut_hi), (0, hi, mid), (hi, mid, 0)]
 
 
 def test_full_size_320_sampled_parity():
     """The 320^3 workload (~8100 spheres, 32.8 M cells) after 24 steps: one
-    more step checked on three random interior sub-blocks and the centre."""
+    more step checked on three random interior sub-blocks, the centre and
+    ten blocks on the walls, corners and CPML interfaces (fields and CPML
+    memories)."""
     from paper_0809_1547_gb300 import inputs
     w = inputs.workload_paper_320()
     B = 20
     rng = np.random.default_rng(12)
     los = [tuple(int(v) for v in rng.integers(9, 320 - 9 - B - 2, size=3)) for _ in range(3)]
     los.append((150, 150, 150))
+    los += _boundary_blocks(320, w.npml, B + 2)
     _sampled_step_parity(w, 24, los, B)
 
 
@@ -481,11 +468,13 @@ def test_full_size_448_sampled_parity():
     """The 448^3 sweep workload (~22.9k spheres, 89.9 M cells, 5.8 GB of
     state) after 16 steps: one more step checked on sub-blocks at random
     interior positions, across tile and plane-chunk boundaries (x = 31|32,
-    y = 3|4, z = 15|16 of the launch's tiles) and at the far interior corner."""
+    y = 3|4, z = 15|16 of the launch's tiles), at the far interior corner
+    and on the walls, corners and CPML interfaces."""
     from paper_0809_1547_gb300 import inputs
     w = inputs.workload_large_448()
     B = 16
     rng = np.random.default_rng(448)
     los = [tuple(int(v) for v in rng.integers(9, 448 - 9 - B - 2, size=3)) for _ in range(2)]
     los += [(216, 214, 214), (448 - 9 - B - 2,) * 3]
+    los += _boundary_blocks(448, w.npml, B + 2)
     _sampled_step_parity(w, 16, los, B)
