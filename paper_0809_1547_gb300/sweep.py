@@ -70,12 +70,23 @@ def summarize(levels, stats: dict) -> tuple[list, float | None]:
     return rows, thr
 
 
-def run_pump_sweep(workloads, steps: int, stream=None, autotune: bool = True):
+def run_pump_sweep(workloads, steps: int, stream=None, autotune: bool = True, record=()):
     """Advance every workload of the ensemble `steps` steps in one MBBatch
-    and return (levels, spectra, lam, seconds)."""
+    and return (levels, spectra, lam, seconds).  With `record` (ascending
+    step counts below `steps`), also the spectra at each of those counts:
+    then returns (levels, spectra, lam, seconds, [(step, spectra), ...])."""
     from .binding import MBBatch, mb_default_params
     b = MBBatch([w.grid for w in workloads], workloads[0].dx, workloads[0].dt,
                 mb_default_params(npml=workloads[0].npml), stream=stream)
+
+    def read():
+        out, lam_ = [], None
+        for inst in b.instances:
+            S, lam_ = inst.probe_spectrum(0)
+            out.append(S)
+        return np.array(out), lam_
+
+    snaps = []
     try:
         for q, w in enumerate(workloads):
             b.set_instance(q, w.eps, w.gain, w.N_a, w.pump, w.seed)
@@ -83,16 +94,22 @@ def run_pump_sweep(workloads, steps: int, stream=None, autotune: bool = True):
         if autotune:
             b.autotune()
         t0 = time.perf_counter()
-        b.step(steps)
+        done = 0
+        for r in [int(v) for v in record if 0 < int(v) < steps]:
+            b.step(r - done)
+            b.synchronize()
+            done = r
+            snaps.append((r, read()[0]))
+        b.step(steps - done)
         b.synchronize()
         secs = time.perf_counter() - t0
-        spectra, lam = [], None
-        for inst in b.instances:
-            S, lam = inst.probe_spectrum(0)
-            spectra.append(S)
+        spectra, lam = read()
     finally:
         b.close()
-    return [w.N_a for w in workloads], np.array(spectra), lam, secs
+    levels = [w.N_a for w in workloads]
+    if record:
+        return levels, spectra, lam, secs, snaps
+    return levels, spectra, lam, secs
 
 
 def main():
@@ -101,16 +118,36 @@ def main():
     ap.add_argument("--n-pump", type=int, default=16)
     ap.add_argument("--n-seed", type=int, default=5)
     ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--pump", type=float, default=0.0,
+                    help="pump rate W_p (1/s) of every realization (default: the workload's)")
+    ap.add_argument("--top-levels", type=int, default=0,
+                    help="keep only the highest N_a levels (all seeds of each)")
+    ap.add_argument("--record", default="",
+                    help="comma-separated step counts at which the statistics are also taken "
+                         "(spectra accumulated from step 0)")
     ap.add_argument("--out", default="")
     args = ap.parse_args()
     ws = inputs.workload_batch(n_pump=args.n_pump, n_seed=args.n_seed)
-    levels, spectra, lam, secs = run_pump_sweep(ws, args.steps)
+    if args.pump > 0:
+        for w in ws:
+            w.pump = args.pump
+    if args.top_levels > 0:
+        keep = sorted({w.N_a for w in ws})[-args.top_levels:]
+        ws = [w for w in ws if w.N_a in keep]
+    record = [int(v) for v in args.record.split(",") if v.strip()]
+    res = run_pump_sweep(ws, args.steps, record=record)
+    levels, spectra, lam, secs = res[:4]
+    snaps = res[4] if record else []
     stats = spectral_stats(spectra, lam)
     rows, thr = summarize(levels, stats)
     cells = sum(int(np.prod(w.grid)) for w in ws)
-    out = {"instances": len(ws), "steps": args.steps, "seconds": secs,
+    dt = ws[0].dt
+    out = {"instances": len(ws), "steps": args.steps, "t_ps": args.steps * dt * 1e12,
+           "pump_W_p": ws[0].pump, "seconds": secs,
            "mcell_updates_per_s": cells * args.steps / secs / 1e6, "threshold_N_a": thr,
-           "levels": rows}
+           "levels": rows,
+           "history": [{"step": st, "t_ps": st * dt * 1e12,
+                        "levels": summarize(levels, spectral_stats(S, lam))[0]} for st, S in snaps]}
     text = json.dumps(out, indent=1)
     if args.out:
         with open(args.out, "w") as f:
