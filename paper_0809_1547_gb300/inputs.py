@@ -111,14 +111,26 @@ def rasterize(grid, dx: float, centers, radii) -> np.ndarray:
 
 def material_maps(grid, inside: np.ndarray, npml: int, eps_sphere: float = EPS_TIO2,
                   eps_void: float = 1.0):
-    """eps_r (float32) and gain mask (uint8): gain in the voids outside the CPML."""
+    """eps_r (float32) and gain mask (uint8) of the sample in the interior
+    box; the CPML layers hold the background (eps_void, no gain): spheres are
+    cut at the layers' inner faces.
+
+    A PML absorbs without reflection, and stays stable, only in a medium
+    that is homogeneous along the layer's normal; a dense packing inside
+    the layers supports modes that the layer amplifies (a passive pulse in
+    a 97^3 realization at 45 % fill grows by e every ~340 steps from step
+    ~2000, localised in a slab, while the same run with the background in
+    the layers decays)."""
     nx, ny, nz = grid
+    inside = np.asarray(inside, dtype=bool)
+    if npml > 0:
+        core = np.zeros(inside.shape, dtype=bool)
+        core[npml:max(npml, nz - npml), npml:max(npml, ny - npml), npml:max(npml, nx - npml)] = True
+        inside = inside & core
     eps = np.where(inside, np.float32(eps_sphere), np.float32(eps_void)).astype(np.float32)
     gain = (~inside).astype(np.uint8)
     if npml > 0:
-        core = np.zeros_like(gain)
-        core[npml:max(npml, nz - npml), npml:max(npml, ny - npml), npml:max(npml, nx - npml)] = 1
-        gain &= core
+        gain &= core.astype(np.uint8)
     return eps, gain
 
 

@@ -118,6 +118,8 @@ def main():
     ap.add_argument("--n-pump", type=int, default=16)
     ap.add_argument("--n-seed", type=int, default=5)
     ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--na-min", type=float, default=5e23, help="lowest N_a level (m^-3)")
+    ap.add_argument("--na-max", type=float, default=2e25, help="highest N_a level (m^-3)")
     ap.add_argument("--pump", type=float, default=0.0,
                     help="pump rate W_p (1/s) of every realization (default: the workload's)")
     ap.add_argument("--top-levels", type=int, default=0,
@@ -127,7 +129,8 @@ def main():
                          "(spectra accumulated from step 0)")
     ap.add_argument("--out", default="")
     args = ap.parse_args()
-    ws = inputs.workload_batch(n_pump=args.n_pump, n_seed=args.n_seed)
+    ws = inputs.workload_batch(n_pump=args.n_pump, n_seed=args.n_seed, N_a_lo=args.na_min,
+                               N_a_hi=args.na_max)
     if args.pump > 0:
         for w in ws:
             w.pump = args.pump

@@ -45,3 +45,45 @@ def test_long_run_statistics_match_oracle():
     print(f"2000 steps: spectrum rel-L2 {rel_l2(S_g, S_o):.2e}, Ex rel-L2 "
           f"{rel_l2(g.field('Ex'), o.field('Ex')):.2e}")
     g.close()
+
+
+def test_dense_packing_stays_stable_over_long_runs():
+    """A 97^3 ensemble member (45 % fill of eps 8.41, the CPML holding the
+    background): after a single-cycle pulse the passive energy decays over
+    12000 steps with no growing mode (with the packing reaching into the
+    CPML it grew by e every ~340 steps from step ~2000), and the pumped,
+    noisy run at the ensemble's highest N_a lases but stays within what
+    energy conservation allows: the field can never hold more than the
+    atoms could have emitted, hbar w0 N_a V_gain (1 + W_p t) (each atom at
+    most once per pump cycle); an instability overflows that bound."""
+    import math
+    from paper_0809_1547_gb300 import inputs
+    from paper_0809_1547_gb300.binding import MBSimulation, mb_default_params
+    ws = inputs.workload_batch(n_pump=16, n_seed=5)
+    m = [w for w in ws if w.grid[0] == 97][0]
+    mid = tuple(v // 2 for v in m.grid)
+    s = MBSimulation(m.grid, m.dx, m.dt, mb_default_params(npml=m.npml))
+    s.set_material(m.eps, m.gain, 0.0, 0.0)
+    s.set_source(mid, 2, 532e-9, 4e-15, 1e-15, 1e9)
+    s.step(1000)
+    U = [s.energy()[0]]
+    for _ in range(22):
+        s.step(500)
+        U.append(s.energy()[0])
+    s.close()
+    assert all(math.isfinite(u) for u in U)
+    assert all(b <= 1.02 * a for a, b in zip(U, U[1:])), U      # never grows
+    assert U[-1] < 0.1 * U[0], U
+    N_a = max(w.N_a for w in ws)                                # the ensemble's highest level
+    s = MBSimulation(m.grid, m.dx, m.dt, mb_default_params(npml=m.npml))
+    s.set_material(m.eps, m.gain, N_a, m.pump)
+    s.set_seed(m.seed)
+    hbar_w0 = 1.054571817e-34 * 2.0 * math.pi * 299_792_458.0 / 590e-9
+    v_gain = float(m.gain.sum()) * m.dx ** 3
+    V = []
+    for q in range(10):
+        s.step(1000)
+        V.append(s.energy()[0])
+        t = (q + 1) * 1000 * m.dt
+        assert math.isfinite(V[-1]) and 0 < V[-1] <= hbar_w0 * N_a * v_gain * (1.0 + m.pump * t), (q, V)
+    s.close()

@@ -38,6 +38,22 @@ def test_material_maps_clear_gain_in_cpml():
     assert gain[3:9, 3:9, 3:9].sum() == 6 ** 3 - 8
 
 
+def test_material_maps_hold_the_background_in_the_cpml():
+    # a sphere reaching into the layers is cut at their inner faces
+    inside = np.zeros((12, 12, 12), bool)
+    inside[1:6, 4:8, 4:8] = True          # k = 1, 2 lie in the z layers (npml = 3)
+    eps, gain = inputs.material_maps((12, 12, 12), inside, 3)
+    assert np.all(eps[:3] == 1) and np.all(eps[-3:] == 1)
+    assert np.all(eps[:, :3] == 1) and np.all(eps[:, :, -3:] == 1)
+    assert np.all(eps[3:6, 4:8, 4:8] == np.float32(8.41))
+    assert gain[3:6, 4:8, 4:8].sum() == 0 and gain[:3].sum() == 0
+    for w in (inputs.workload_small_48(), inputs.workload_adjoint_96()):
+        L = w.npml
+        for sl in ((slice(0, L),), (slice(-L, None),), (slice(None), slice(0, L)),
+                   (slice(None), slice(None), slice(-L, None))):
+            assert np.all(w.eps[sl] == 1) and w.gain[sl].sum() == 0
+
+
 def test_workload_48_matches_its_description():
     w = inputs.workload_small_48()
     assert w.grid == (48, 48, 48) and w.n_spheres == 8 and w.steps == 500
