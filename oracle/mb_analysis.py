@@ -18,10 +18,18 @@ spectrum S_k sampled on angular frequencies w_k:
     threshold:   the lowest pump level whose mean std width is at most half
                  the mean std width at the lowest level (gain narrowing), or
                  None when no level narrows that far.
+    emission threshold: with E_q the mean emitted energy (sum of S) at the
+                 q-th level L_q (ascending), the lowest L_q from which the
+                 log-log slope ln(E_{q+1}/E_q) / ln(L_{q+1}/L_q) exceeds 2,
+                 or None: spontaneous emission grows in proportion to the
+                 number of atoms (slope ~1), stimulated emission above
+                 threshold makes the growth super-linear.
 
 Pins (tests/test_oracle_analysis.py): a sampled Gaussian gives back its
 centre and width; a flat spectrum's std width is that of a uniform
-distribution; a two-line spectrum's std width is half the line spacing.
+distribution; a two-line spectrum's std width is half the line spacing; a
+synthetic S-curve gives back its kink, and power laws up to slope 2 have
+no emission threshold.
 """
 from __future__ import annotations
 
@@ -79,11 +87,23 @@ def sweep_table(levels, spectra, w):
         sd = [std_width(spectra[i], w) for i in idx]
         gf = [gaussian_fit(spectra[i], w)[1] for i in idx]
         gf = [g for g in gf if g is not None]
+        em = [float(np.sum(spectra[i])) for i in idx]
         rows.append({"level": L, "peak_w": float(np.mean(pk)), "std_w": float(np.mean(sd)),
-                     "gauss_w": float(np.mean(gf)) if gf else None, "n": len(idx)})
+                     "gauss_w": float(np.mean(gf)) if gf else None, "n": len(idx),
+                     "emitted": float(np.mean(em))})
     thr = None
     for r in rows:
         if r["std_w"] <= 0.5 * rows[0]["std_w"]:
             thr = r["level"]
             break
     return rows, thr
+
+
+def emission_threshold(levels, emitted, slope: float = 2.0):
+    """The lowest level L_q (levels ascending) from which the emitted energy
+    grows faster than L^slope to the next level, or None."""
+    for q in range(len(levels) - 1):
+        g = math.log(emitted[q + 1] / emitted[q]) / math.log(levels[q + 1] / levels[q])
+        if g > slope:
+            return float(levels[q])
+    return None

@@ -14,6 +14,9 @@ reductions of a few hundred numbers per realization:
                sigma = sqrt(-1 / (2 c)) for the quadratic coefficient c < 0
     threshold  the lowest N_a whose mean std width is at most half of the
                lowest level's (gain narrowing)
+    emission   the lowest N_a from which the mean emitted energy grows faster
+    threshold  than N_a^2 to the next level (spontaneous emission grows as
+               N_a, stimulated emission above threshold faster)
 
     python -m paper_0809_1547_gb300.sweep --steps 8000 --out sweep.json
 """
@@ -68,6 +71,17 @@ def summarize(levels, stats: dict) -> tuple[list, float | None]:
     base = rows[0]["std_w"]
     thr = next((r["N_a"] for r in rows if r["std_w"] <= 0.5 * base), None)
     return rows, thr
+
+
+def emission_threshold(rows, slope: float = 2.0):
+    """The lowest N_a (rows ascending, as summarize returns them) from which
+    the log-log slope of the mean emitted energy to the next level exceeds
+    `slope`, or None."""
+    L = np.array([r["N_a"] for r in rows])
+    E = np.array([r["emitted"] for r in rows])
+    g = np.log(E[1:] / E[:-1]) / np.log(L[1:] / L[:-1])
+    hit = np.nonzero(g > slope)[0]
+    return float(L[hit[0]]) if hit.size else None
 
 
 def run_pump_sweep(workloads, steps: int, stream=None, autotune: bool = True, record=()):
@@ -148,9 +162,13 @@ def main():
     out = {"instances": len(ws), "steps": args.steps, "t_ps": args.steps * dt * 1e12,
            "pump_W_p": ws[0].pump, "seconds": secs,
            "mcell_updates_per_s": cells * args.steps / secs / 1e6, "threshold_N_a": thr,
+           "emission_threshold_N_a": emission_threshold(rows),
            "levels": rows,
-           "history": [{"step": st, "t_ps": st * dt * 1e12,
-                        "levels": summarize(levels, spectral_stats(S, lam))[0]} for st, S in snaps]}
+           "history": []}
+    for st, S in snaps:
+        r_, thr_ = summarize(levels, spectral_stats(S, lam))
+        out["history"].append({"step": st, "t_ps": st * dt * 1e12, "threshold_N_a": thr_,
+                               "emission_threshold_N_a": emission_threshold(r_), "levels": r_})
     text = json.dumps(out, indent=1)
     if args.out:
         with open(args.out, "w") as f:

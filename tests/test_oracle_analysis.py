@@ -4,7 +4,7 @@ import math
 import numpy as np
 import pytest
 
-from oracle.mb_analysis import gaussian_fit, peak, std_width, sweep_table
+from oracle.mb_analysis import emission_threshold, gaussian_fit, peak, std_width, sweep_table
 
 
 def test_sampled_gaussian_gives_back_centre_and_width():
@@ -42,3 +42,18 @@ def test_sweep_threshold_is_first_level_that_halves_the_width():
     assert [r["level"] for r in rows] == [1.0, 2.0, 3.0]
     assert thr == 3.0
     assert rows[2]["gauss_w"] == pytest.approx(8.0, rel=1e-8, abs=0)
+
+
+def test_emission_threshold_finds_the_kink_of_an_s_curve():
+    # E = L below L = 4 (spontaneous, slope 1), E = L exp(3 (L - 4)) from it on
+    levels = [1.0, 2.0, 3.0, 4.0, 5.0, 6.0]
+    E = [L if L < 4 else L * math.exp(3.0 * (L - 4.0)) for L in levels]
+    assert emission_threshold(levels, E) == 4.0
+    # power laws up to the critical slope have no threshold
+    assert emission_threshold(levels, [L ** 1.5 for L in levels]) is None
+    assert emission_threshold(levels, [L ** 1.95 for L in levels]) is None
+    assert emission_threshold(levels, [L ** 2.2 for L in levels]) == 1.0
+    # the per-level mean emitted energy of the sweep table is the mean of sum S
+    w = np.linspace(-50.0, 50.0, 201)
+    rows, _ = sweep_table([1, 1, 2], [np.ones(201), 3 * np.ones(201), np.ones(201)], w)
+    assert rows[0]["emitted"] == pytest.approx(2 * 201, rel=1e-15, abs=0)

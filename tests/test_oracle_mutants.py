@@ -62,7 +62,8 @@ GP = [("test_oracle_gp", "test_near_threshold_closed_form", {}),
 ANALYSIS = [("test_oracle_analysis", "test_sampled_gaussian_gives_back_centre_and_width", {}),
             ("test_oracle_analysis", "test_flat_spectrum_std_width_is_uniform", {}),
             ("test_oracle_analysis", "test_two_lines_std_width_is_half_the_spacing", {}),
-            ("test_oracle_analysis", "test_sweep_threshold_is_first_level_that_halves_the_width", {})]
+            ("test_oracle_analysis", "test_sweep_threshold_is_first_level_that_halves_the_width", {}),
+            ("test_oracle_analysis", "test_emission_threshold_finds_the_kink_of_an_s_curve", {})]
 MODEMAP = [("test_oracle_modemap", "test_energy_density_planes_sum_to_the_energy", {}),
            ("test_oracle_modemap", "test_plane_probe_equals_point_probes_on_its_cells", {}),
            ("test_oracle_modemap", "test_plane_probe_sampling_interval_does_not_change_the_map", {}),
@@ -138,6 +139,11 @@ MUTANTS = {
     "GP: E(p) with p for sqrt p": ("gp_oracle", "return (p - 1.0) / (kappa * np.sqrt(p))", "return (p - 1.0) / (kappa * p)", GP),
     "GP: threshold root sign": ("gp_oracle", "+ kappa * math.sqrt(4.0 + kappa ** 2) / 2.0", "- kappa * math.sqrt(4.0 + kappa ** 2) / 2.0", GP),
     # NEXT-2: spectral statistics
+    "analysis: emission slope against the energy ratio alone": ("mb_analysis",
+        "g = math.log(emitted[q + 1] / emitted[q]) / math.log(levels[q + 1] / levels[q])",
+        "g = math.log(emitted[q + 1] / emitted[q])", ANALYSIS),
+    "analysis: emitted energy from the peak bin": ("mb_analysis",
+        "em = [float(np.sum(spectra[i])) for i in idx]", "em = [float(np.max(spectra[i])) for i in idx]", ANALYSIS),
     "analysis: unweighted mean": ("mb_analysis", "mean = (S * w).sum() / tot", "mean = w.mean()", ANALYSIS),
     "analysis: width over bins": ("mb_analysis", "return math.sqrt((S * (w - mean) ** 2).sum() / tot)",
                                   "return math.sqrt((S * (w - mean) ** 2).sum() / S.size)", ANALYSIS),

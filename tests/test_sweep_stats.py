@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 from oracle import mb_analysis as O
-from paper_0809_1547_gb300.sweep import spectral_stats, summarize
+from paper_0809_1547_gb300.sweep import emission_threshold, spectral_stats, summarize
 
 
 def _spectra(n=12, seed=0):
@@ -45,3 +45,18 @@ def test_summary_and_threshold_agree_with_oracle():
         assert r["N_a"] == ro["level"]
         assert r["std_w"] == pytest.approx(ro["std_w"], rel=1e-12, abs=0)
         assert r["peak_w"] == pytest.approx(ro["peak_w"], rel=1e-12, abs=0)
+
+
+def test_emission_threshold_agrees_with_oracle():
+    S, lam, w = _spectra(n=8, seed=5)
+    levels = [1e24, 1e24, 3e24, 3e24, 1e25, 1e25, 2e25, 2e25]
+    # scale the spectra into an S-curve of emitted energy
+    scale = np.array([1.0, 1.1, 3.0, 2.9, 80.0, 75.0, 9e3, 8e3])
+    S = S / S.sum(axis=1, keepdims=True) * scale[:, None]
+    rows, _ = summarize(levels, spectral_stats(S, lam))
+    rows_o, _ = O.sweep_table(levels, list(S), w)
+    for r, ro in zip(rows, rows_o):
+        assert r["emitted"] == pytest.approx(ro["emitted"], rel=1e-12, abs=0)
+    thr = emission_threshold(rows)
+    assert thr == O.emission_threshold([r["level"] for r in rows_o], [r["emitted"] for r in rows_o])
+    assert thr == 3e24
