@@ -6,7 +6,8 @@
 // (Figs. 3, 5).  Second-order differences on tau_i = -L + i h (i = 1..n,
 // h = 2L/(n+1)), Newton's method with a tridiagonal (Thomas) solve per
 // iteration, all in FP64; one thread per eigenvalue, its arrays in global
-// scratch.  Newton starts from the larger of the Thomas-Fermi profile
+// scratch interleaved across the eigenvalues (element i of eigenvalue q at
+// i nE + q), so that the threads of a warp touch consecutive addresses.  Newton starts from the larger of the Thomas-Fermi profile
 // sqrt(max(E - tau^2, 0)) and the first-order solution near threshold
 // 2^{1/4} sqrt(E - 1) exp(-tau^2 / 2) and stops when the residual is below
 // 1e-12 max(1, E) or the step stagnates at rounding level; a result whose
@@ -22,22 +23,30 @@ namespace {
 
 constexpr int kGpMaxIter = 100;
 
-__device__ double gp_residual(const double* phi, int i, int n, double t2, double ih2, double E) {
+// A thread's array with its elements nE apart (the interleaved layout).
+struct Strided {
+    double* p;
+    size_t s;
+    __device__ double& operator[](int i) const { return p[(size_t)i * s]; }
+};
+
+__device__ double gp_residual(const Strided& phi, int i, int n, double t2, double ih2, double E) {
     const double l = i > 0 ? phi[i - 1] : 0.0;
     const double r = i < n - 1 ? phi[i + 1] : 0.0;
     const double p = phi[i];
     return -(l - 2.0 * p + r) * ih2 + t2 * p + p * p * p - E * p;
 }
 
-// One thread per eigenvalue: phi (n), and the Thomas sweep's scratch (2n).
+// One thread per eigenvalue: phi (n), and the Thomas sweep's scratch (2n),
+// all interleaved across the eigenvalues.
 __global__ void k_gp_solve(const double* Es, int nE, int n, double* phi_all, double* scratch,
                            double* w_out, double* p_out, int* status) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= nE) return;
     const double E = Es[q];
-    double* phi = phi_all + (size_t)q * n;
-    double* cp = scratch + (size_t)q * 2 * n;
-    double* dp = cp + n;
+    const Strided phi{phi_all + q, (size_t)nE};
+    const Strided cp{scratch + q, (size_t)nE};
+    const Strided dp{scratch + (size_t)n * nE + q, (size_t)nE};
     const double L = sqrt(E) + 8.0;
     const double h = 2.0 * L / (n + 1);
     const double ih2 = 1.0 / (h * h);
@@ -148,8 +157,13 @@ extern "C" int mb_gp_features(const double* E, int nE, int n_grid, double* w_phi
     if (e == cudaSuccess) e = cudaMemcpy(w_phi, dw, sizeof(double) * nE, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemcpy(p_phi, dp, sizeof(double) * nE, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemcpy(st.data(), dst, sizeof(int) * nE, cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess && phi_out)
-        e = cudaMemcpy(phi_out, dphi, sizeof(double) * n * nE, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && phi_out) {
+        // device layout [i][q] -> caller's [q][i]
+        std::vector<double> t(n * (size_t)nE);
+        e = cudaMemcpy(t.data(), dphi, sizeof(double) * n * nE, cudaMemcpyDeviceToHost);
+        for (int q = 0; q < nE && e == cudaSuccess; ++q)
+            for (size_t i = 0; i < n; ++i) phi_out[(size_t)q * n + i] = t[i * nE + q];
+    }
     if (e != cudaSuccess) {
         mb::set_thread_error(std::string("gp solve: ") + cudaGetErrorString(e));
         rc = e == cudaErrorMemoryAllocation ? MB_ERR_OOM : MB_ERR_CUDA;
