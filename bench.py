@@ -565,6 +565,8 @@ def bench_ours(args):
         out["batched"] = bench_batched(stream, args.batched_steps, args.warmup)
     if not args.no_adjoint:
         out["adjoint"] = bench_adjoint(stream, args.warmup)
+    if not args.no_split and args.grid == 320:
+        out["split_z"] = bench_split(stream, max(50, args.steps // 4), args.warmup)
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.grid == 320:
         try:
             out["cpu_baseline"] = cpu_baseline(w)
@@ -687,6 +689,56 @@ def bench_batched(stream, steps: int, warmup: int, n_pump: int = 16, n_seed: int
                                              "(autotuned, graph replay), one after another"},
             "ratio_vs_plain": round(v_batch / v_plain, 4),
             "l2": "inputs larger than L2"}
+
+
+# ------------------------------------------------------- grid split along z
+
+def bench_split(stream, steps: int, warmup: int, parts_list=(2, 4)):
+    """The 320^3 workload split along z into slab contexts on this one GPU
+    (ghost planes exchanged before every step through the C ABI, then one
+    step of every slab), against the same grid as one context: the cost of
+    the split path's exchange and per-slab launches.  Scaling over several
+    GPUs is not measured here."""
+    import torch
+    from paper_0809_1547_gb300 import inputs
+    from paper_0809_1547_gb300.binding import mb_default_params
+    from paper_0809_1547_gb300.sharded import SlabGrid
+    from paper_0809_1547_gb300.workloads import setup_simulation
+    w = inputs.workload_paper_320()
+    cells = w.ncell
+
+    def timed(fn, st):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    whole = setup_simulation(w, autotune=True, face_probes=False, stream=stream.cuda_stream)
+    whole.step(warmup)
+    t_whole = timed(lambda: (whole.step(steps), whole.join_probes()), stream)
+    whole.close()
+    out = {"workload": f"{w.name}: {w.grid[0]}^3, point probe, no face probes (slab contexts do not take them)",
+           "steps": steps, "whole_grid": {"value": round(cells * steps / (t_whole / 1e3) / 1e6, 2),
+                                          "unit": UNIT, "ms_per_step": round(t_whole / steps, 5)}}
+    for parts in parts_list:
+        sg = SlabGrid(w.grid, w.dx, w.dt, parts, mb_default_params(npml=w.npml))
+        sg.set_material(w.eps, w.gain, w.N_a, w.pump)
+        sg.set_seed(w.seed)
+        sg.add_point_probe(tuple(v // 2 for v in w.grid), 128, 475e-9, 705e-9)
+        for s_ in sg.slabs:
+            s_.autotune()
+        sg.step(warmup)
+        t = timed(lambda: (sg.step(steps), [s_.join_probes() for s_ in sg.slabs]), sg._stream)
+        out[f"slabs_{parts}"] = {"value": round(cells * steps / (t / 1e3) / 1e6, 2), "unit": UNIT,
+                                 "ms_per_step": round(t / steps, 5), "bounds": sg.bounds,
+                                 "ratio_vs_whole": round(t_whole / t, 4),
+                                 "halo_bytes_per_interface_per_step": 2 * sg.slabs[0].halo_bytes}
+        sg.close()
+    return out
 
 
 # ------------------------------------------------------------- theory side
@@ -933,6 +985,8 @@ def run_only(args):
         out = bench_passive(rank_workload(0, 320), stream, max(50, args.steps // 3), args.warmup)
     elif args.only == "large":
         out = bench_large(stream, max(50, args.steps // 6), args.warmup)
+    elif args.only == "split":
+        out = bench_split(stream, max(50, args.steps // 4), args.warmup)
     else:
         out = bench_gp()
     print(json.dumps(out), flush=True)
@@ -952,7 +1006,8 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint leg")
     ap.add_argument("--no-passive", action="store_true", help="skip the passive (pulse, CW) leg")
     ap.add_argument("--no-large", action="store_true", help="skip the 448^3 leg")
-    ap.add_argument("--only", choices=("batched", "adjoint", "passive", "large", "gp"), default="",
+    ap.add_argument("--no-split", action="store_true", help="skip the z-slab split leg")
+    ap.add_argument("--only", choices=("batched", "adjoint", "passive", "large", "gp", "split"), default="",
                     help="run one leg alone and print its result (profiling)")
     ap.add_argument("--batched-pump", type=int, default=16, help="N_a levels of the ensemble")
     ap.add_argument("--batched-seeds", type=int, default=5, help="disorder seeds of the ensemble")

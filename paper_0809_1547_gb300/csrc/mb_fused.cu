@@ -72,8 +72,19 @@ __global__ void __launch_bounds__(BX * BY) k_step_fused(StepArgs a, DevPing d,
     float* gbuf = reinterpret_cast<float*>(smem + S * Lay::kStage);
     float* hn = reinterpret_cast<float*>(smem + S * Lay::kStage + Lay::kGBytes);
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + S * Lay::kStage + Lay::kGBytes + Lay::kNBytes);
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + BX * ty;
+    static_assert(BX % 8 == 0 && BY % 4 == 0, "x-edge tiles map warps onto 8 x 4 cells");
+    const int tid = threadIdx.x + BX * threadIdx.y;
     const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
+    // The thread's cell (tx, ty) in the tile.  In tiles that hold x-CPML
+    // columns a warp covers 8 columns x 4 rows, so that the slab's columns
+    // fill whole warps and the other warps skip the slab's work as a body;
+    // elsewhere a warp covers one row.  Each warp access still covers whole
+    // 32-byte sectors; the cell updates are the same either way.
+    const bool xedge = a.pml.L > 0 && (x0 < a.pml.L || x0 + BX > a.g.nx - a.pml.L);
+    const int wq = tid >> 5, ln = tid & 31;
+    const int tx = xedge ? 8 * (wq % (BX / 8)) + (ln & 7) : tid % BX;
+    const int ty = xedge ? 4 * (wq / (BX / 8)) + (ln >> 3) : tid / BX;
+    const int tcell = tx + BX * ty;   // the cell's place in the tile's row-major shared arrays
     const int i = x0 + tx, j = y0 + ty;
     const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
     const uint32_t nxy = a.g.nxy;
@@ -103,7 +114,7 @@ __global__ void __launch_bounds__(BX * BY) k_step_fused(StepArgs a, DevPing d,
         }
     };
     auto mat_of = [&](int s) -> uint8_t {
-        return (smem + s * Lay::kStage + 3 * Lay::kEBytes + 3 * Lay::kHBytes)[tid];
+        return (smem + s * Lay::kStage + 3 * Lay::kEBytes + 3 * Lay::kHBytes)[tcell];
     };
     auto gslot = [&](int b, int q) -> float* { return gbuf + (b * 9 + q) * T + tid; };
     auto prefetch_gain = [&](int b, uint32_t cc) {
