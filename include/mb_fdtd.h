@@ -419,8 +419,11 @@ int mb_batch_get_tuning(mb_batch* batch, int* out3);
  * the whole grid along z, the Langevin noise keyed by each cell's index in
  * the whole grid (so a split run draws the same noise as the whole grid),
  * the face-flux box of the whole grid cut to the own planes, mb_energy over
- * the own planes only.  Face probes and the adjoint are not available on a
- * slab (MB_ERR_STATE).
+ * the own planes only, face probes (mb_add_face_probes) on the whole grid's
+ * lattice of points cut to the own planes (a z face is kept by the slab
+ * owning the plane below it), so that a face spectrum of the whole grid is
+ * the sum of the slabs' mb_face_spectrum.  The adjoint is not available on
+ * a slab (MB_ERR_STATE).
  *
  * Step protocol (what makes the split run equal, cell by cell, to the whole
  * grid): before every step, for each pair of neighbouring slabs A (below)

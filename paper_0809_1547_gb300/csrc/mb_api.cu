@@ -951,7 +951,6 @@ int mb_add_point_probe(mb_ctx* c, const int ijk[3], int n_freq, double lam_min, 
 
 int mb_add_face_probes(mb_ctx* c, int stride, int every, int n_freq, double lam_min, double lam_max) {
     if (int rc = check_ctx(c)) return rc;
-    if (c->slab) return fail(c, MB_ERR_STATE, "face probes are not available on a z-slab context");
     if (stride < 1 || every < 1 || n_freq < 1 || n_freq > 4096 || !(lam_min > 0) || !(lam_max > 0))
         return fail(c, MB_ERR_ARG, "bad face-probe arguments (1 <= n_freq <= 4096)");
     cudaStreamSynchronize(c->stream);
@@ -970,10 +969,33 @@ int mb_add_face_probes(mb_ctx* c, int stride, int every, int n_freq, double lam_
         const int ta = ax == 0 ? 1 : 0;
         const int tb = ax == 2 ? 1 : 2;
         auto ra = interior(n3[ta], L), rb = interior(n3[tb], L);
-        const int na = (ra.second - ra.first + stride - 1) / stride;
-        const int nb = (rb.second - rb.first + stride - 1) / stride;
+        int na = (ra.second - ra.first + stride - 1) / stride;
+        int nb = (rb.second - rb.first + stride - 1) / stride;
         F.r0a[face] = ra.first;
         F.r0b[face] = rb.first;
+        if (c->slab) {
+            // the whole grid's lattice of points, cut to the slab's own planes
+            // (local coordinates): x and y faces keep the lattice rows whose
+            // z lies in them (their samples stay in the plane), a z face
+            // belongs to the slab owning the plane below it, where its H is
+            // sampled (the plane itself, holding E, is then own too, or the
+            // grid's end: a cut never falls next to the z-CPML)
+            const int zlo = c->kz0 + c->own_lo, zhi = c->kz0 + c->own_hi;   // whole-grid planes
+            if (ax == 2) {
+                auto rz = interior(c->gnz, L);
+                const int gp = (face % 2) ? rz.second : rz.first;
+                const int gq = std::max(gp - 1, 0);
+                F.plane[face] = gp - c->kz0;
+                if (gq < zlo || gq >= zhi) nb = 0;
+            } else {
+                auto rz = interior(c->gnz, L);
+                const int nbg = (rz.second - rz.first + stride - 1) / stride;
+                const int qlo = std::max(0, (zlo - rz.first + stride - 1) / stride);
+                const int qhi = std::min(nbg, std::max(0, (zhi - rz.first + stride - 1) / stride));
+                nb = std::max(0, qhi - qlo);
+                F.r0b[face] = rz.first + qlo * stride - c->kz0;
+            }
+        }
         F.na[face] = na;
         F.npts[face] = na * nb;
         F.offset[face] = (int)off;

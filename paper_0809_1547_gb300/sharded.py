@@ -171,6 +171,21 @@ class SlabGrid:
         self.probes[key] = (q, pid)
         return key
 
+    def add_face_probes(self, stride, every, n_freq, lam_min, lam_max):
+        """The whole grid's face probes: each slab keeps the lattice points on
+        its own planes (a z face: the slab owning the plane below it)."""
+        for s in self.slabs:
+            s.add_face_probes(stride, every, n_freq, lam_min, lam_max)
+
+    def face_spectrum(self, face):
+        """(S, lam) of one face of the whole grid: the slabs' spectra summed
+        (FP64; the per-point accumulators equal the whole grid's)."""
+        S, lam = None, None
+        for s in self.slabs:
+            Sq, lam = s.face_spectrum(face)
+            S = np.asarray(Sq, dtype=np.float64) if S is None else S + Sq
+        return S, lam
+
     def set_source(self, ijk, comp, lam, t0, tau, amp):
         q = self.owner(ijk[2])
         self.slabs[q].set_source(self.slabs[q].to_local(ijk), comp, lam, t0, tau, amp)
@@ -308,6 +323,17 @@ class DistributedSlab:
         with torch.cuda.stream(self.stream):
             v = reduce_readouts([u] + list(f), device=self.device, group=self.group)
         return float(v[0]), v[1:]
+
+    def add_face_probes(self, stride, every, n_freq, lam_min, lam_max):
+        self.sim.add_face_probes(stride, every, n_freq, lam_min, lam_max)
+
+    def face_spectrum(self, face):
+        """(S, lam) of one face of the whole grid (FP64 sum over the ranks)."""
+        import torch
+        S, lam = self.sim.face_spectrum(face)
+        with torch.cuda.stream(self.stream):
+            S = reduce_readouts(S, device=self.device, group=self.group)
+        return S, lam
 
     def close(self):
         self.sim.close()

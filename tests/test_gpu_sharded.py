@@ -24,7 +24,7 @@ def _lib():
 
 
 def _pair(grid, dx, dt, npml, eps, gain, N_a, pump, seed, parts=2, bounds=None, single=None,
-          probe=None, source=None):
+          probe=None, source=None, faces=None):
     from paper_0809_1547_gb300.binding import MBSimulation, mb_default_params
     from paper_0809_1547_gb300.sharded import SlabGrid
     p = mb_default_params(npml=npml)
@@ -44,7 +44,21 @@ def _pair(grid, dx, dt, npml, eps, gain, N_a, pump, seed, parts=2, bounds=None, 
     if source is not None:
         whole.set_source(*source)
         split.set_source(*source)
+    if faces is not None:                      # (stride, every)
+        for s in (whole, split):
+            s.add_face_probes(faces[0], faces[1], 24, 475e-9, 705e-9)
     return whole, split, pw, ps
+
+
+def _compare_faces(whole, split):
+    for face in range(6):
+        Sw, lw = whole.face_spectrum(face)
+        Ss, ls = split.face_spectrum(face)
+        assert np.array_equal(lw, ls)
+        scale = float(np.max(np.abs(Sw)))
+        assert scale > 0, face                 # every face saw the field
+        # the same per-point accumulators, summed over the slabs in another order
+        assert np.max(np.abs(Ss - Sw)) <= 1e-10 * scale, (face, Ss, Sw)
 
 
 def _compare(whole, split, pw, ps, flux_rel=1e-5):
@@ -68,11 +82,12 @@ def test_48_workload_two_slabs_500_steps(single):
     w = inputs.workload_small_48()
     mid = tuple(v // 2 for v in w.grid)
     whole, split, pw, ps = _pair(w.grid, w.dx, w.dt, w.npml, w.eps, w.gain, w.N_a, w.pump, w.seed,
-                                 parts=2, single=single, probe=mid)
+                                 parts=2, single=single, probe=mid, faces=(4, 2))
     assert [s.z_end - s.z_begin for s in split.slabs] == [24, 24]
     whole.step(w.steps)
     split.step(w.steps)
     _compare(whole, split, pw, ps)
+    _compare_faces(whole, split)
     whole.close()
     split.close()
 
@@ -85,11 +100,15 @@ def test_ragged_grid_three_slabs_with_source_and_cuts_at_the_cpml():
     dt = inputs.courant_dt(dx)
     bounds = [(0, 5), (5, 32), (32, 37)]
     src = ((20, 4, 18), 2, 532e-9, 4e-15, 1e-15, 1e9)
+    # face lattice stride 3: z rows 4, 7, .., 31 fall on the first two slabs;
+    # the low z face (plane 4, H from 3) on the first, the high one (33, H
+    # from 32) on the last
     whole, split, pw, ps = _pair(grid, dx, dt, npml, eps, gain, 3e24, 1e13, 0xABCD, parts=3,
-                                 bounds=bounds, probe=(11, 5, 33), source=src)
+                                 bounds=bounds, probe=(11, 5, 33), source=src, faces=(3, 1))
     whole.step(300)
     split.step(300)
     _compare(whole, split, pw, ps)
+    _compare_faces(whole, split)
     whole.close()
     split.close()
 
@@ -100,10 +119,11 @@ def test_four_slabs_of_a_single_pass_grid():
     dx = 20e-9
     dt = inputs.courant_dt(dx)
     whole, split, pw, ps = _pair(grid, dx, dt, npml, eps, gain, 5e24, 1e13, 77, parts=4,
-                                 single=(1, 32, 8, 5), probe=(30, 16, 29))
+                                 single=(1, 32, 8, 5), probe=(30, 16, 29), faces=(2, 3))
     whole.step(120)
     split.step(120)
     _compare(whole, split, pw, ps)
+    _compare_faces(whole, split)
     whole.close()
     split.close()
 
@@ -128,9 +148,6 @@ def test_slab_errors():
     assert e.value.code == MB_ERR_STATE
     with pytest.raises(MBError) as e:
         hi.unpack(1, buf)                 # nor the last one above
-    assert e.value.code == MB_ERR_STATE
-    with pytest.raises(MBError) as e:
-        lo.add_face_probes(8, 4, 16, 475e-9, 705e-9)
     assert e.value.code == MB_ERR_STATE
     w = inputs.workload_small_48()
     lo.set_material(w.eps[:25], w.gain[:25], w.N_a, w.pump)
