@@ -939,16 +939,20 @@ def bench_reference(args):
     """The reference arm: the FP64 oracle (the paper has no implementation to
     run) on the benchmark's workload, on every host core; each step is one
     step of a slab of the workload per core, sized so the whole run takes
-    about 100 s."""
+    about --ref-budget seconds (100 by default)."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
     try:
         w = rank_workload(0)
-        cores = host_cores()
+        cores = min(host_cores(), args.ref_cores) if args.ref_cores > 0 else host_cores()
+        # calibration on every core at once (the children share the memory
+        # bandwidth, so one child alone would overstate each child's rate)
         with tempfile.TemporaryDirectory() as d:
-            r1, _, _ = run_oracle_children([(save_part(w, d, "cal", 150, 20), 1, 1, "forward")])
-        budget_s = 100.0
+            part = save_part(w, d, "cal", 150, 17)
+            rall, _, _ = run_oracle_children([(part, 1, 1, "forward")] * cores)
+        r1 = rall / cores
+        budget_s = float(args.ref_budget)
         cells_per_child = r1 * 1e6 * budget_s / max(1, args.steps + args.warmup)
         thickness = int(max(17, min(48, round(cells_per_child / (w.grid[0] * w.grid[1])))))
         rate, secs, ncell, cores = cpu_slab_rate(w, thickness, args.steps, args.warmup, cores)
@@ -998,6 +1002,10 @@ def main():
     ap.add_argument("--steps", type=int, default=600)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--ref-budget", type=float, default=100.0,
+                    help="--impl reference: seconds of oracle stepping the run is sized for")
+    ap.add_argument("--ref-cores", type=int, default=0,
+                    help="--impl reference: oracle processes (default: one per host core)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cpu-configs", action="store_true",
                     help="skip the oracle rates of the 48^3, 448^3, ensemble and adjoint configs")

@@ -164,6 +164,25 @@ __global__ void __launch_bounds__(BX * BY) k_step_fused(StepArgs a, DevPing d,
     const int halo_e = row ? tid + 4 : (tid - BX + 1) * Lay::kEX + 3;
     const int halo_h = row ? tid + 4 : (tid - BX + 1) * Lay::kHX + 3;
     const int halo_n = row ? tid + 1 : (tid - BX + 1) * Lay::kNX;
+    // Warp-uniform path choices (a path taken for cells it does not need
+    // gives the same bits: the CPML code leaves cells outside the slabs
+    // alone, and the flux terms of cells off the faces are zero): the CPML
+    // code for the warp's own cells and for its halo cells where one of them
+    // lies in an x or y slab (or the plane in a z slab), the flux terms where
+    // one of its cells lies on an x or y face of the flux box (within the
+    // box's z range) or the plane is a z face.
+    const unsigned full = 0xffffffffu;
+    const DevFlux& F = a.flux;
+    const int L = a.pml.L;
+    auto in_xy_slab = [&](int ci, int cj) {
+        return L > 0 && (ci < L || ci >= nx - L || cj < L || cj >= ny - L);
+    };
+    const bool w_pml = __any_sync(full, pml_xy && valid && in_xy_slab(i, j));
+    const bool w_pml_halo = __any_sync(full, pml_xy && halo && in_xy_slab(hi, hj));
+    const bool on_xy_face = F.on && valid &&
+                            (((i == F.plo[0] || i == F.phi[0]) && j >= F.r0[1] && j < F.r1[1]) ||
+                             ((j == F.plo[1] || j == F.phi[1]) && i >= F.r0[0] && i < F.r1[0]));
+    const bool w_face_xy = __any_sync(full, face && on_xy_face);
     const int own_e = (ty + 1) * Lay::kEX + tx + 4;
     const int own_h = (ty + 1) * Lay::kHX + tx + 4;
     const int own_n = (ty + 1) * Lay::kNX + tx + 1;
@@ -173,11 +192,13 @@ __global__ void __launch_bounds__(BX * BY) k_step_fused(StepArgs a, DevPing d,
     bool pg = valid && gain_on && !fail && (mat_of(0) & 0x80);
     if (pg) prefetch_gain(0, c);
     cp_async_commit();
+    // ring slots of planes p and p + 1, and the phase parity of plane p + 1
+    int s = 0, s1 = 1 % S;
+    uint32_t ph1 = (1 / S) & 1;
     for (int p = 0; p < planes; ++p) {
-        const int s = p % S, s1 = (p + 1) % S;
         const int k = k0 + p;
         cp_async_wait_all();   // this plane's gain values (own thread's copies)
-        fail |= !mbar_wait_bounded(&bar[s1], ((p + 1) / S) & 1, kWaitLimit);
+        fail |= !mbar_wait_bounded(&bar[s1], ph1, kWaitLimit);
         bool ng = false;
         if (p + 1 < planes) {
             ng = valid && gain_on && !fail && (mat_of(s1) & 0x80);
@@ -187,7 +208,10 @@ __global__ void __launch_bounds__(BX * BY) k_step_fused(StepArgs a, DevPing d,
         const float* E0 = reinterpret_cast<const float*>(smem + s * Lay::kStage);
         const float* E1 = reinterpret_cast<const float*>(smem + s1 * Lay::kStage);
         const float* H0 = reinterpret_cast<const float*>(smem + s * Lay::kStage + 3 * Lay::kEBytes);
-        const bool pml = pml_xy || plane_in_z_slab(a, k);
+        const bool zpml = plane_in_z_slab(a, k);
+        const bool pml = w_pml || zpml, pml_h = w_pml_halo || zpml;
+        const bool fk = (w_face_xy && k >= F.r0[2] && k < F.r1[2]) ||
+                        (face && (k == F.plo[2] || k == F.phi[2]));
 
         // 1. H^{n+1/2}: own cell, then the halo row / column
         float hx = 0.0f, hy = 0.0f, hz = 0.0f;
@@ -231,7 +255,7 @@ __global__ void __launch_bounds__(BX * BY) k_step_fused(StepArgs a, DevPing d,
                 qy = H0[HW + halo_h];
                 qz = H0[2 * HW + halo_h];
                 const PsiOut none{nullptr, nullptr, nullptr};
-                if (pml) h_compute_to<true, false>(a, hi, hj, k, e, qx, qy, qz, none);
+                if (pml_h) h_compute_to<true, false>(a, hi, hj, k, e, qx, qy, qz, none);
                 else h_compute_to<false, false>(a, hi, hj, k, e, qx, qy, qz, none);
             }
             hn[halo_n] = qx;
@@ -277,7 +301,7 @@ __global__ void __launch_bounds__(BX * BY) k_step_fused(StepArgs a, DevPing d,
             const uint8_t m = mat_of(s);
             const float ex0 = E0[own_e], ey0 = E0[EW + own_e], ez0 = E0[2 * EW + own_e];
             float ex1, ey1, ez1;
-            if (face)
+            if (fk)
                 e_compute_to<true, true>(a, i, j, k, c, h, m, ex0, ey0, ez0, pg, jx, jy, jz, n1, n2,
                                          n3, n, fl, ex1, ey1, ez1, d.psi);
             else if (pml)
@@ -297,9 +321,8 @@ __global__ void __launch_bounds__(BX * BY) k_step_fused(StepArgs a, DevPing d,
             hx_km1 = hx;
             hy_km1 = hy;
         }
-        if (face) {
+        if (fk) {
             // this plane's flux terms: warp sums, added to the warp's partials
-            const unsigned full = 0xffffffffu;
 #pragma unroll
             for (int q = 0; q < 6; ++q) {
                 float v = fl[q];
@@ -320,6 +343,9 @@ __global__ void __launch_bounds__(BX * BY) k_step_fused(StepArgs a, DevPing d,
         }
         pg = ng;
         c += nxy;
+        s = s1;
+        s1 = (s1 + 1 == S) ? 0 : s1 + 1;
+        if (s1 == 0) ph1 ^= 1u;
     }
     cp_async_wait_all();
     if (block_fail) {

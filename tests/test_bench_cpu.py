@@ -70,8 +70,8 @@ def test_reference_arm_prints_one_valid_line():
     import sys
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference",
-                        "--steps", "1", "--warmup", "3"], capture_output=True, text=True, timeout=600,
-                       cwd=root)
+                        "--steps", "1", "--warmup", "3", "--ref-budget", "8", "--ref-cores", "2"],
+                       capture_output=True, text=True, timeout=600, cwd=root)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [l for l in r.stdout.splitlines() if l.strip().startswith("{")]
     assert len(lines) == 1, r.stdout
