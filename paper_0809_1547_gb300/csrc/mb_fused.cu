@@ -172,17 +172,9 @@ __global__ void __launch_bounds__(BX * BY) k_step_fused(StepArgs a, DevPing d,
     // one of its cells lies on an x or y face of the flux box (within the
     // box's z range) or the plane is a z face.
     const unsigned full = 0xffffffffu;
-    const DevFlux& F = a.flux;
-    const int L = a.pml.L;
-    auto in_xy_slab = [&](int ci, int cj) {
-        return L > 0 && (ci < L || ci >= nx - L || cj < L || cj >= ny - L);
-    };
-    const bool w_pml = __any_sync(full, pml_xy && valid && in_xy_slab(i, j));
-    const bool w_pml_halo = __any_sync(full, pml_xy && halo && in_xy_slab(hi, hj));
-    const bool on_xy_face = F.on && valid &&
-                            (((i == F.plo[0] || i == F.phi[0]) && j >= F.r0[1] && j < F.r1[1]) ||
-                             ((j == F.plo[1] || j == F.phi[1]) && i >= F.r0[0] && i < F.r1[0]));
-    const bool w_face_xy = __any_sync(full, face && on_xy_face);
+    const bool w_pml = __any_sync(full, pml_xy && valid && cell_in_xy_slab(a, i, j));
+    const bool w_pml_halo = __any_sync(full, pml_xy && halo && cell_in_xy_slab(a, hi, hj));
+    const bool w_xy = __any_sync(full, face && valid && cells_on_xy_face(a.flux, i, 1, j));
     const int own_e = (ty + 1) * Lay::kEX + tx + 4;
     const int own_h = (ty + 1) * Lay::kHX + tx + 4;
     const int own_n = (ty + 1) * Lay::kNX + tx + 1;
@@ -210,8 +202,7 @@ __global__ void __launch_bounds__(BX * BY) k_step_fused(StepArgs a, DevPing d,
         const float* H0 = reinterpret_cast<const float*>(smem + s * Lay::kStage + 3 * Lay::kEBytes);
         const bool zpml = plane_in_z_slab(a, k);
         const bool pml = w_pml || zpml, pml_h = w_pml_halo || zpml;
-        const bool fk = (w_face_xy && k >= F.r0[2] && k < F.r1[2]) ||
-                        (face && (k == F.plo[2] || k == F.phi[2]));
+        const bool fk = plane_has_flux(a.flux, face, w_xy, k);
 
         // 1. H^{n+1/2}: own cell, then the halo row / column
         float hx = 0.0f, hy = 0.0f, hz = 0.0f;

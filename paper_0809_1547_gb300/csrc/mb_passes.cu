@@ -202,7 +202,7 @@ __device__ __forceinline__ void e_quad(const StepArgs& a, int i0, int j, int k, 
 
 template <bool FACE>
 __device__ __forceinline__ void e_vec_walk(const StepArgs& a, int i0, int j, int k0, int k1, bool valid,
-                                           bool pml_xy, long long n, float fl[6]) {
+                                           bool pml_xy, long long n, float fl[6], bool w_xy) {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int nx = a.g.nx;
@@ -235,9 +235,12 @@ __device__ __forceinline__ void e_vec_walk(const StepArgs& a, int i0, int j, int
                 n1 = ld4(f.n1 + c); n2 = ld4(f.n2 + c); n3 = ld4(f.n3 + c);
             }
             float4 ex1, ey1, ez1;
-            if (FACE || pml_xy || plane_in_z_slab(a, k))
-                e_quad<FACE, true>(a, i0, j, k, c, hx, hy, hz, hxj, hzj, hxk, hyk, hy_p, hz_p, ex, ey,
+            if (FACE && plane_has_flux(a.flux, true, w_xy, k))
+                e_quad<true, true>(a, i0, j, k, c, hx, hy, hz, hxj, hzj, hxk, hyk, hy_p, hz_p, ex, ey,
                                    ez, m4, jx, jy, jz, n1, n2, n3, n, fl, ex1, ey1, ez1);
+            else if (pml_xy || plane_in_z_slab(a, k))
+                e_quad<false, true>(a, i0, j, k, c, hx, hy, hz, hxj, hzj, hxk, hyk, hy_p, hz_p, ex, ey,
+                                    ez, m4, jx, jy, jz, n1, n2, n3, n, fl, ex1, ey1, ez1);
             else
                 e_quad<false, false>(a, i0, j, k, c, hx, hy, hz, hxj, hzj, hxk, hyk, hy_p, hz_p, ex,
                                      ey, ez, m4, jx, jy, jz, n1, n2, n3, n, fl, ex1, ey1, ez1);
@@ -268,10 +271,11 @@ __global__ void __launch_bounds__(256) k_e_vec(StepArgs a, int kz) {
     const bool pml_xy = tile_in_xy_slab(a, x0, xw, y0, blockDim.y);
     if (face) {
         float fl[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        e_vec_walk<true>(a, i0, j, k0, k1, valid, pml_xy, n, fl);
+        const bool w_xy = __any_sync(0xffffffffu, valid && cells_on_xy_face(a.flux, i0, 4, j));
+        e_vec_walk<true>(a, i0, j, k0, k1, valid, pml_xy, n, fl, w_xy);
         flux_warp_reduce(a.flux, fl, warp_slot());
     } else {
-        e_vec_walk<false>(a, i0, j, k0, k1, valid, pml_xy, n, nullptr);
+        e_vec_walk<false>(a, i0, j, k0, k1, valid, pml_xy, n, nullptr, false);
     }
     finish_step(a);
 }
@@ -307,6 +311,9 @@ __global__ void __launch_bounds__(BX * BY) k_e_tma(StepArgs a, const __grid_cons
     const long long n = a.step_ctr[0];
     const bool face = tile_on_face(a.flux, x0, x0 + BX, y0, y0 + BY, k0, k1);
     const bool pml_xy = tile_in_xy_slab(a, x0, BX, y0, BY);
+    // warp-uniform: the warp holds cells of an x or y face / of an x or y slab
+    const bool w_xy = __any_sync(0xffffffffu, face && valid && cells_on_xy_face(a.flux, i, 1, j));
+    const bool w_pml = __any_sync(0xffffffffu, pml_xy && valid && cell_in_xy_slab(a, i, j));
     const bool gain_on = a.gain.on;
     const DevFields& f = a.f;
 
@@ -369,6 +376,7 @@ __global__ void __launch_bounds__(BX * BY) k_e_tma(StepArgs a, const __grid_cons
         }
         cp_async_commit();
         float fl[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        const bool fk = plane_has_flux(a.flux, face, w_xy, k);
         if (valid && !fail) {
             const unsigned char* p = smem + s * Lay::kStage;
             const float* Hx = reinterpret_cast<const float*>(p);
@@ -399,10 +407,10 @@ __global__ void __launch_bounds__(BX * BY) k_e_tma(StepArgs a, const __grid_cons
                 n2 = *gslot(b, 4);
                 n3 = *gslot(b, 5);
             }
-            if (face)
+            if (fk)
                 e_apply<true, true>(a, i, j, k, c, h, m, Ex[tid], Ey[tid], Ez[tid], pg, jx, jy, jz, n1,
                                     n2, n3, n, fl);
-            else if (pml_xy || plane_in_z_slab(a, k))
+            else if (w_pml || plane_in_z_slab(a, k))
                 e_apply<false, true>(a, i, j, k, c, h, m, Ex[tid], Ey[tid], Ez[tid], pg, jx, jy, jz, n1,
                                      n2, n3, n, fl);
             else
@@ -411,7 +419,7 @@ __global__ void __launch_bounds__(BX * BY) k_e_tma(StepArgs a, const __grid_cons
             hx_km1 = h.hx;
             hy_km1 = h.hy;
         }
-        if (face) {
+        if (fk) {
             // this plane's flux terms: warp sums, added to the warp's partials
             const unsigned full = 0xffffffffu;
 #pragma unroll

@@ -88,6 +88,29 @@ __device__ __forceinline__ bool plane_in_z_slab(const StepArgs& a, int k) {
     return a.pml.L > 0 && (k < a.pml.zlo || k >= a.pml.zhi);
 }
 
+// Cell (i, j) lies in an x or y CPML slab.
+__device__ __forceinline__ bool cell_in_xy_slab(const StepArgs& a, int i, int j) {
+    const int L = a.pml.L;
+    return L > 0 && (i < L || i >= a.g.nx - L || j < L || j >= a.g.ny - L);
+}
+
+// Cells (i0 .. i0+w-1, j) can hold terms of an x or y face of the flux box
+// (on some plane of the box's z range).
+__device__ __forceinline__ bool cells_on_xy_face(const DevFlux& F, int i0, int w, int j) {
+    if (!F.on) return false;
+    const bool xf = ((F.plo[0] >= i0 && F.plo[0] < i0 + w) || (F.phi[0] >= i0 && F.phi[0] < i0 + w)) &&
+                    j >= F.r0[1] && j < F.r1[1];
+    const bool yf = (j == F.plo[1] || j == F.phi[1]) && i0 + w > F.r0[0] && i0 < F.r1[0];
+    return xf || yf;
+}
+
+// Plane k of a block holding face cells (face) needs the flux terms in a
+// warp: the warp holds cells of an x or y face (w_xy) and k lies in the
+// box's z range, or k is a z face.  Elsewhere every term is zero.
+__device__ __forceinline__ bool plane_has_flux(const DevFlux& F, bool face, bool w_xy, int k) {
+    return face && ((w_xy && k >= F.r0[2] && k < F.r1[2]) || k == F.plo[2] || k == F.phi[2]);
+}
+
 // ------------------------------------------------------------ H tiles
 
 // H walk of tile (bx, by, bz): a 2-D block over (x, y), kz planes per thread.
