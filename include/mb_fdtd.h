@@ -120,8 +120,9 @@ int mb_set_material(mb_ctx* ctx, const float* eps_map, const uint8_t* gain_mask,
 int mb_set_seed(mb_ctx* ctx, uint64_t seed);
 
 /* Running-DFT point probe on the three E components of cell ijk:
- * E~_c(w_k) += E_c(t_{n+1}) exp(i w_k t_{n+1}) dt after every step, FP64 on
- * the device, n_freq wavelengths uniformly from lam_min to lam_max.
+ * E~_c(w_k) += E_c(t_{n+1}) exp(i w_k t_{n+1}) dt after every step, summed in
+ * FP64 on the device (the factor exp(i w t) is formed in FP32 from the angle
+ * reduced in FP64), n_freq wavelengths uniformly from lam_min to lam_max.
  * *probe_id receives the probe index.  Errors: MB_ERR_ARG. */
 int mb_add_point_probe(mb_ctx* ctx, const int ijk[3], int n_freq,
                        double lam_min, double lam_max, int* probe_id);
@@ -129,8 +130,9 @@ int mb_add_point_probe(mb_ctx* ctx, const int ijk[3], int n_freq,
 /* Face probes on the six faces of the interior box [npml, n - npml)^3: on
  * every stride-th point of each face, the tangential E (on the face plane,
  * at t_{n+1}) and H (half a cell outside, at t_{n+1/2}) are accumulated into
- * FP64 running DFTs every `every` steps (1 <= n_freq <= 4096).  Replaces
- * earlier face probes. */
+ * running DFTs every `every` steps (1 <= n_freq <= 4096): FP32 sums over 16
+ * consecutive accumulations, each added into FP64 sums on the device (the
+ * spectrum reads both).  Replaces earlier face probes. */
 int mb_add_face_probes(mb_ctx* ctx, int stride, int every, int n_freq,
                        double lam_min, double lam_max);
 

@@ -277,8 +277,10 @@ std::vector<StatePart> state_parts(mb_ctx* c) {
     v.push_back({c->d_flux, sizeof(double) * 6 * mb::kFluxSlots});
     if (!c->probes.empty())
         v.push_back({c->d_probe_acc, sizeof(double2) * 3 * c->probes.size() * c->probe_nfreq});
-    if (c->face.on && c->face_points)
+    if (c->face.on && c->face_points) {
         v.push_back({c->d_face_acc, sizeof(double2) * 4 * (size_t)c->face_points * c->face.nfreq});
+        v.push_back({c->d_face_acc32, sizeof(float2) * 4 * (size_t)c->face_points * c->face.nfreq});
+    }
     for (const mb::DevPlaneProbe& q : c->planes)
         v.push_back({q.acc, sizeof(double2) * 3 * (size_t)q.nfreq * c->nx * c->ny});
     return v;
@@ -797,7 +799,7 @@ int mb_destroy(mb_ctx* c) {
     void* bufs[] = {c->d_fields, c->d_mat, c->d_inv_eps, c->d_lut, c->d_psi[0], c->d_psi[1],
                     c->d_psi[2], c->d_coef, c->d_ctr, c->d_flux, c->d_partial, c->d_energy,
                     c->d_nonfinite, c->d_probe_cell, c->d_probe_omega, c->d_probe_acc,
-                    c->d_face_omega, c->d_face_acc, c->d_glist, c->d_src_wave, c->d_err,
+                    c->d_face_omega, c->d_face_acc, c->d_face_acc32, c->d_glist, c->d_src_wave, c->d_err,
                     c->d_fields2, c->d_psi2[0], c->d_psi2[1], c->d_psi2[2], c->d_flux_out};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -955,6 +957,7 @@ int mb_add_face_probes(mb_ctx* c, int stride, int every, int n_freq, double lam_
         return fail(c, MB_ERR_ARG, "bad face-probe arguments (1 <= n_freq <= 4096)");
     cudaStreamSynchronize(c->stream);
     if (c->d_face_acc) { cudaFree(c->d_face_acc); c->d_face_acc = nullptr; }
+    if (c->d_face_acc32) { cudaFree(c->d_face_acc32); c->d_face_acc32 = nullptr; }
     if (c->d_face_omega) { cudaFree(c->d_face_omega); c->d_face_omega = nullptr; }
     mb::DevFaceProbes& F = c->face;
     std::memset(&F, 0, sizeof(F));
@@ -1019,8 +1022,11 @@ int mb_add_face_probes(mb_ctx* c, int stride, int every, int n_freq, double lam_
     const size_t accn = 4 * (size_t)off * n_freq;
     MB_CUDA(c, cudaMalloc((void**)&c->d_face_acc, sizeof(double2) * (accn ? accn : 1)));
     MB_CUDA(c, cudaMemset(c->d_face_acc, 0, sizeof(double2) * (accn ? accn : 1)));
+    MB_CUDA(c, cudaMalloc((void**)&c->d_face_acc32, sizeof(float2) * (accn ? accn : 1)));
+    MB_CUDA(c, cudaMemset(c->d_face_acc32, 0, sizeof(float2) * (accn ? accn : 1)));
     F.omega = c->d_face_omega;
     F.acc = c->d_face_acc;
+    F.acc32 = c->d_face_acc32;
     drop_graphs(c);
     return MB_OK;
 }
@@ -1257,10 +1263,19 @@ int mb_face_spectrum(mb_ctx* c, int face, double* out_S, double* out_lam) {
     const int K = c->face.nfreq;
     const int np = c->face.npts[face];
     std::vector<double2> acc((size_t)np * 4 * K);
+    std::vector<float2> acc32((size_t)np * 4 * K);
     if (np) {
-        MB_CUDA(c, cudaMemcpyAsync(acc.data(), c->d_face_acc + (size_t)c->face.offset[face] * 4 * K,
-                                   sizeof(double2) * acc.size(), cudaMemcpyDeviceToHost, c->stream));
+        const size_t at = (size_t)c->face.offset[face] * 4 * K;
+        MB_CUDA(c, cudaMemcpyAsync(acc.data(), c->d_face_acc + at, sizeof(double2) * acc.size(),
+                                   cudaMemcpyDeviceToHost, c->stream));
+        MB_CUDA(c, cudaMemcpyAsync(acc32.data(), c->d_face_acc32 + at, sizeof(float2) * acc32.size(),
+                                   cudaMemcpyDeviceToHost, c->stream));
         MB_CUDA(c, cudaStreamSynchronize(c->stream));
+        // the FP64 sums plus the FP32 sums since their last flush
+        for (size_t q = 0; q < acc.size(); ++q) {
+            acc[q].x += (double)acc32[q].x;
+            acc[q].y += (double)acc32[q].y;
+        }
     }
     const double w = c->face.every * c->dt;
     const double scale = (c->E0 * w) * (c->E0 / c->eta0 * w) * std::pow(c->face.stride * c->dx, 2);

@@ -17,6 +17,20 @@
 
 namespace mb {
 
+// exp(i w t) as an FP32 pair (cos, sin): the angle w t is reduced to
+// [-pi, pi] in FP64 (w t stays below ~1e6 rad in any run here, so the
+// reduction is exact to ~1e-10 rad), then its FP32 sine and cosine are
+// taken.  The factor multiplies FP32 field values, so FP32 is its natural
+// precision; the FP64 sincos it replaces is slow on this GPU's FP64 pipe.
+__device__ __forceinline__ float2 phase_f32(double w, double t) {
+    const double two_pi = 6.283185307179586476925;
+    const double x = w * t;
+    const double r = fma(-two_pi, rint(x * (1.0 / two_pi)), x);
+    float s, c;
+    sincosf((float)r, &s, &c);
+    return make_float2(c, s);
+}
+
 struct DevPointProbes {
     int count;
     int nfreq;          // bins per probe (all probes share one count)
@@ -38,19 +52,23 @@ __device__ __forceinline__ void point_dft_block(const DevPointProbes& pp, int p,
     const int T = blockDim.x * blockDim.y * blockDim.z;
     const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
     for (int kk = k_begin + tid; kk < K; kk += (k_step > 0 ? k_step : T)) {
-        double s, co;
-        sincos(pp.omega[p * K + kk] * t, &s, &co);
+        const float2 w = phase_f32(pp.omega[p * K + kk], t);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             double2* acc = pp.acc + ((int64_t)p * 3 + c) * K + kk;
             double2 v = *acc;
-            v.x += (double)e[c] * co;
-            v.y += (double)e[c] * s;
+            v.x += (double)e[c] * (double)w.x;
+            v.y += (double)e[c] * (double)w.y;
             *acc = v;
         }
     }
 }
 
+// Face probes: the running DFT sums of each point are kept in FP64 (acc);
+// each call adds its terms to FP32 partial sums (acc32), which are added
+// into acc and cleared on every kFaceChunk-th call, so the FP64 pipe works
+// once per kFaceChunk calls.  A spectrum reads acc + acc32.
+constexpr int kFaceChunk = 16;
 struct DevFaceProbes {
     int on;
     int stride, every, nfreq, pts_per_block;
@@ -60,6 +78,7 @@ struct DevFaceProbes {
     int offset[6];      // first point of each face in acc
     const double* omega;
     double2* acc;       // [point][4][nfreq]: Ea, Eb, Ha, Hb
+    float2* acc32;      // the same layout: the sums since the last flush
 };
 
 // Whole-plane probe: running DFT of (Ex, Ey, Ez) on every cell of the plane
@@ -310,6 +329,7 @@ struct mb_ctx {
     std::vector<double> face_lam;
     double* d_face_omega = nullptr;
     double2* d_face_acc = nullptr;
+    float2* d_face_acc32 = nullptr;
     int64_t face_points = 0;
 
     // material

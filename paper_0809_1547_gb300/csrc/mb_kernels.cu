@@ -16,8 +16,8 @@
 
 namespace mb {
 
-// Blocks (probe, group of 32 bins), a thread per bin (the FP64 sincos of
-// every bin spread over many SMs):
+// Blocks (probe, group of 32 bins), a thread per bin (the phase factors of
+// the bins spread over several SMs):
 // acc[p][c][k] += E_c(t_{n+1}) exp(i w_k t_{n+1})   (scaled; times dt E0 on read-out)
 __global__ void __launch_bounds__(32) k_point_dft(DevPointProbes pp, const float* ex, const float* ey,
                                                   const float* ez, const long long* step_ctr, double dt) {
@@ -27,14 +27,16 @@ __global__ void __launch_bounds__(32) k_point_dft(DevPointProbes pp, const float
 
 // Face DFT: block (chunk of points, face).  The block first forms the
 // phase factors exp(i w_k t) of every bin at the E and H sample times in
-// shared memory (one FP64 sincos per thread: FP64 is a slow pipe on this
-// GPU), then its threads run over (point, bin) pairs, bins fastest, so each
-// warp touches contiguous accumulators.
+// shared memory, then its threads run over (point, bin) pairs, bins fastest,
+// so each warp touches contiguous accumulators.  The terms go into the FP32
+// partial sums; every kFaceChunk-th call of the run (by the step counter)
+// adds those into the FP64 sums and clears them.
 __global__ void __launch_bounds__(256) k_face_dft(DevFaceProbes fp, DevFields f, DevGrid g,
                                                   const long long* step_ctr, double dt) {
     const long long n1 = step_ctr[0];         // n + 1
     if (n1 % fp.every != 0) return;
-    extern __shared__ double2 ph[];           // [0, K): E times, [K, 2K): H times
+    const bool flush = (n1 / fp.every) % kFaceChunk == kFaceChunk - 1;
+    extern __shared__ float2 ph[];            // [0, K): E times, [K, 2K): H times
     const int face = blockIdx.y;
     const int axis = face >> 1;
     const int np = fp.npts[face];
@@ -45,60 +47,68 @@ __global__ void __launch_bounds__(256) k_face_dft(DevFaceProbes fp, DevFields f,
     const int K = fp.nfreq;
     const int na = fp.na[face];
     const double tE = (double)n1 * dt, tH = tE - 0.5 * dt;
-    for (int q = threadIdx.x; q < 2 * K; q += blockDim.x) {
-        double s_, c_;
-        sincos(fp.omega[q % K] * (q < K ? tE : tH), &s_, &c_);
-        ph[q] = make_double2(c_, s_);
-    }
+    for (int q = threadIdx.x; q < 2 * K; q += blockDim.x)
+        ph[q] = phase_f32(fp.omega[q % K], q < K ? tE : tH);
     __syncthreads();
     const int work = K * (p1 - p0);
     for (int q = threadIdx.x; q < work; q += blockDim.x) {
         const int kk = q % K, p = p0 + q / K;
-        const double cE = ph[kk].x, sE = ph[kk].y, cH = ph[K + kk].x, sH = ph[K + kk].y;
-        {
-            const int ia = p % na, ib = p / na;
-            // transverse coordinates of point (ia, ib): (a, b) axes per face
-            int i, j, k;
-            const int ca = fp.r0a[face] + ia * fp.stride, cb = fp.r0b[face] + ib * fp.stride;
-            float Ea = 0.f, Eb = 0.f, Ha = 0.f, Hb = 0.f;
-            if (axis == 0) {        // x-face: points (j = ca, k = cb); (a, b) = (y, z)
-                j = ca; k = cb;
-                if (plane < g.nx) {
-                    const int64_t c = plane + (int64_t)g.nx * j + g.nxy * k;
-                    Ea = f.ey[c]; Eb = f.ez[c];
-                }
-                if (plane >= 1) {
-                    const int64_t c = (plane - 1) + (int64_t)g.nx * j + g.nxy * k;
-                    Ha = f.hy[c]; Hb = f.hz[c];
-                }
-            } else if (axis == 1) { // y-face: points (i = ca, k = cb); (a, b) = (z, x)
-                i = ca; k = cb;
-                if (plane < g.ny) {
-                    const int64_t c = i + (int64_t)g.nx * plane + g.nxy * k;
-                    Ea = f.ez[c]; Eb = f.ex[c];
-                }
-                if (plane >= 1) {
-                    const int64_t c = i + (int64_t)g.nx * (plane - 1) + g.nxy * k;
-                    Ha = f.hz[c]; Hb = f.hx[c];
-                }
-            } else {                // z-face: points (i = ca, j = cb); (a, b) = (x, y)
-                i = ca; j = cb;
-                if (plane < g.nz) {
-                    const int64_t c = i + (int64_t)g.nx * j + g.nxy * plane;
-                    Ea = f.ex[c]; Eb = f.ey[c];
-                }
-                if (plane >= 1) {
-                    const int64_t c = i + (int64_t)g.nx * j + g.nxy * (plane - 1);
-                    Ha = f.hx[c]; Hb = f.hy[c];
-                }
+        const float2 wE = ph[kk], wH = ph[K + kk];
+        const int ia = p % na, ib = p / na;
+        // transverse coordinates of point (ia, ib): (a, b) axes per face
+        const int ca = fp.r0a[face] + ia * fp.stride, cb = fp.r0b[face] + ib * fp.stride;
+        float Ea = 0.f, Eb = 0.f, Ha = 0.f, Hb = 0.f;
+        if (axis == 0) {        // x-face: points (j = ca, k = cb); (a, b) = (y, z)
+            if (plane < g.nx) {
+                const int64_t c = plane + (int64_t)g.nx * ca + g.nxy * cb;
+                Ea = f.ey[c]; Eb = f.ez[c];
             }
-            double2* acc = fp.acc + (((int64_t)fp.offset[face] + p) * 4) * K + kk;
-            double2 v;
-            v = acc[0];     v.x += (double)Ea * cE; v.y += (double)Ea * sE; acc[0] = v;
-            v = acc[K];     v.x += (double)Eb * cE; v.y += (double)Eb * sE; acc[K] = v;
-            v = acc[2 * K]; v.x += (double)Ha * cH; v.y += (double)Ha * sH; acc[2 * K] = v;
-            v = acc[3 * K]; v.x += (double)Hb * cH; v.y += (double)Hb * sH; acc[3 * K] = v;
+            if (plane >= 1) {
+                const int64_t c = (plane - 1) + (int64_t)g.nx * ca + g.nxy * cb;
+                Ha = f.hy[c]; Hb = f.hz[c];
+            }
+        } else if (axis == 1) { // y-face: points (i = ca, k = cb); fields (z, x)
+            if (plane < g.ny) {
+                const int64_t c = ca + (int64_t)g.nx * plane + g.nxy * cb;
+                Ea = f.ez[c]; Eb = f.ex[c];
+            }
+            if (plane >= 1) {
+                const int64_t c = ca + (int64_t)g.nx * (plane - 1) + g.nxy * cb;
+                Ha = f.hz[c]; Hb = f.hx[c];
+            }
+        } else {                // z-face: points (i = ca, j = cb); (a, b) = (x, y)
+            if (plane < g.nz) {
+                const int64_t c = ca + (int64_t)g.nx * cb + g.nxy * plane;
+                Ea = f.ex[c]; Eb = f.ey[c];
+            }
+            if (plane >= 1) {
+                const int64_t c = ca + (int64_t)g.nx * cb + g.nxy * (plane - 1);
+                Ha = f.hx[c]; Hb = f.hy[c];
+            }
         }
+        const int64_t at = (((int64_t)fp.offset[face] + p) * 4) * K + kk;
+        float2* a32 = fp.acc32 + at;
+        float2 v[4] = {a32[0], a32[K], a32[2 * K], a32[3 * K]};
+        const float val[4] = {Ea, Eb, Ha, Hb};
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const float2 w = r < 2 ? wE : wH;
+            v[r].x = fmaf(val[r], w.x, v[r].x);
+            v[r].y = fmaf(val[r], w.y, v[r].y);
+        }
+        if (flush) {
+            double2* a = fp.acc + at;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                double2 d = a[r * K];
+                d.x += (double)v[r].x;
+                d.y += (double)v[r].y;
+                a[r * K] = d;
+                v[r] = make_float2(0.f, 0.f);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) a32[r * K] = v[r];
     }
 }
 
@@ -172,7 +182,7 @@ void launch_face_dft(const DevFaceProbes& fp, const DevFields& f, const DevGrid&
     for (int q = 0; q < 6; ++q) maxpts = fp.npts[q] > maxpts ? fp.npts[q] : maxpts;
     if (maxpts == 0) return;
     dim3 grid((maxpts + fp.pts_per_block - 1) / fp.pts_per_block, 6);
-    const size_t smem = sizeof(double2) * 2 * (size_t)fp.nfreq;
+    const size_t smem = sizeof(float2) * 2 * (size_t)fp.nfreq;
     static size_t attr_set = 48 * 1024;   // largest dynamic shared memory allowed so far
     if (smem > attr_set) {
         cudaFuncSetAttribute(k_face_dft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -190,9 +200,8 @@ __global__ void k_plane_dft(DevPlaneProbe pp, DevFields f, DevGrid g, const long
     __shared__ double2 ph[kPlaneMaxFreq];
     const double t = (double)n1 * dt;
     for (int kk = threadIdx.x; kk < pp.nfreq; kk += blockDim.x) {
-        double s_, c_;
-        sincos(pp.omega[kk] * t, &s_, &c_);
-        ph[kk] = make_double2(c_, s_);
+        const float2 w = phase_f32(pp.omega[kk], t);
+        ph[kk] = make_double2(w.x, w.y);
     }
     __syncthreads();
     const uint32_t nxy = g.nxy;
