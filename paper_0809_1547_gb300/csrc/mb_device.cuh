@@ -161,9 +161,12 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     return c;
 }
 
-// u = ((x >> 9) + 1/2) 2^-23: exact in FP32, strictly inside (0, 1).
+// u = ((x >> 9) + 1/2) 2^-23: exact in FP32, strictly inside (0, 1).  Formed
+// as (1 + (x >> 9) 2^-23) - (1 - 2^-24), the first term by placing the 23
+// bits under the exponent of 1; both terms lie in [1/2, 2], so the
+// difference is exact (Sterbenz).
 __device__ __forceinline__ float u32_to_unit(uint32_t x) {
-    return (static_cast<float>(x >> 9) + 0.5f) * 1.1920928955078125e-07f;
+    return __uint_as_float((x >> 9) | 0x3F800000u) - 0.99999994039535522f;
 }
 
 // Three standard normals of cell `cell` at step `step`: Box–Muller,
@@ -533,10 +536,10 @@ __device__ __forceinline__ void e_compute_ie(const StepArgs& a, int i, int j, in
                                              float ez0, bool gain, float jx, float jy, float jz,
                                              float& n1, float& n2, float& n3, long long n,
                                              float fl[6], float& ex1, float& ey1, float& ez1,
-                                             const PsiOut& o) {
+                                             const PsiOut& o, bool flux_plane = true) {
     e_field_step<PML>(a, i, j, k, c, h, ie, ex0, ey0, ez0, jx, jy, jz, n, ex1, ey1, ez1, o);
     if (gain) population_step(a.gain, ex0, ey0, ez0, ex1, ey1, ez1, jx, jy, jz, n1, n2, n3);
-    if (FLUX && a.flux.on) flux_terms(a.flux, i, j, k, h, ex0, ey0, ez0, ex1, ey1, ez1, fl);
+    if (FLUX && a.flux.on && flux_plane) flux_terms(a.flux, i, j, k, h, ex0, ey0, ez0, ex1, ey1, ez1, fl);
 }
 
 // The advanced CPML memories go to o.
@@ -546,11 +549,11 @@ __device__ __forceinline__ void e_compute_to(const StepArgs& a, int i, int j, in
                                              float ez0, bool gain, float jx, float jy, float jz,
                                              float& n1, float& n2, float& n3, long long n,
                                              float fl[6], float& ex1, float& ey1, float& ez1,
-                                             const PsiOut& o) {
+                                             const PsiOut& o, bool flux_plane = true) {
     const DevFields& f = a.f;
     const float ie = f.inv_eps ? __ldg(f.inv_eps + c) : __ldg(f.lut_inv_eps + (m & 0x7f));
     e_compute_ie<FLUX, PML>(a, i, j, k, c, h, ie, ex0, ey0, ez0, gain, jx, jy, jz, n1, n2, n3, n,
-                            fl, ex1, ey1, ez1, o);
+                            fl, ex1, ey1, ez1, o, flux_plane);
 }
 
 template <bool FLUX, bool PML>
@@ -558,20 +561,21 @@ __device__ __forceinline__ void e_compute(const StepArgs& a, int i, int j, int k
                                           const HNb& h, uint8_t m, float ex0, float ey0, float ez0,
                                           bool gain, float jx, float jy, float jz, float& n1,
                                           float& n2, float& n3, long long n, float fl[6],
-                                          float& ex1, float& ey1, float& ez1) {
+                                          float& ex1, float& ey1, float& ez1,
+                                          bool flux_plane = true) {
     e_compute_to<FLUX, PML>(a, i, j, k, c, h, m, ex0, ey0, ez0, gain, jx, jy, jz, n1, n2, n3, n,
-                            fl, ex1, ey1, ez1, psi_in_place(a));
+                            fl, ex1, ey1, ez1, psi_in_place(a), flux_plane);
 }
 
 template <bool FLUX, bool PML>
 __device__ __forceinline__ void e_apply(const StepArgs& a, int i, int j, int k, uint32_t c,
                                         const HNb& h, uint8_t m, float ex0, float ey0, float ez0,
                                         bool gain, float jx, float jy, float jz, float n1, float n2,
-                                        float n3, long long n, float fl[6]) {
+                                        float n3, long long n, float fl[6], bool flux_plane = true) {
     const DevFields& f = a.f;
     float ex1, ey1, ez1;
     e_compute<FLUX, PML>(a, i, j, k, c, h, m, ex0, ey0, ez0, gain, jx, jy, jz, n1, n2, n3, n, fl,
-                         ex1, ey1, ez1);
+                         ex1, ey1, ez1, flux_plane);
     f.ex[c] = ex1;
     f.ey[c] = ey1;
     f.ez[c] = ez1;
@@ -584,7 +588,8 @@ __device__ __forceinline__ void e_apply(const StepArgs& a, int i, int j, int k, 
 
 template <bool FLUX, bool PML>
 __device__ __forceinline__ void e_core(const StepArgs& a, int i, int j, int k, uint32_t c,
-                                       const HNb& h, long long n, float fl[6]) {
+                                       const HNb& h, long long n, float fl[6],
+                                       bool flux_plane = true) {
     const DevFields& f = a.f;
     const uint8_t m = __ldg(f.mat + c);
     const bool gain = a.gain.on && (m & 0x80);
@@ -599,7 +604,8 @@ __device__ __forceinline__ void e_core(const StepArgs& a, int i, int j, int k, u
         n2 = f.n2[c];
         n3 = f.n3[c];
     }
-    e_apply<FLUX, PML>(a, i, j, k, c, h, m, ex0, ey0, ez0, gain, jx, jy, jz, n1, n2, n3, n, fl);
+    e_apply<FLUX, PML>(a, i, j, k, c, h, m, ex0, ey0, ez0, gain, jx, jy, jz, n1, n2, n3, n, fl,
+                       flux_plane);
 }
 
 template <bool FLUX>

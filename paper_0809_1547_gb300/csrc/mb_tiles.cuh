@@ -212,12 +212,12 @@ __device__ __forceinline__ void finish_step(const StepArgs& a, long long* sample
 }
 
 // Walk of one column (i, j) over planes [k0, k1).  FACE: the block holds
-// face-plane cells (flux terms summed into fl over the walk); PML_XY: the
-// tile touches an x or y CPML slab (else only z-slab planes take the CPML
-// code).
+// face-plane cells (flux terms summed into fl over the walk, taken on the
+// planes plane_has_flux names; w_xy is warp-uniform); PML_XY: the tile
+// touches an x or y CPML slab (else only z-slab planes take the CPML code).
 template <bool FACE, bool PML_XY>
 __device__ __forceinline__ void e_walk(const StepArgs& a, int i, int j, int k0, int k1, long long n,
-                                       float fl[6]) {
+                                       float fl[6], bool w_xy = false) {
     const int nx = a.g.nx;
     const uint32_t nxy = a.g.nxy;
     const float* __restrict__ Hx = a.f.hx;
@@ -240,7 +240,8 @@ __device__ __forceinline__ void e_walk(const StepArgs& a, int i, int j, int k0, 
         h.hz_j = (j > 0) ? __ldg(Hz + c - nx) : 0.0f;
         h.hy_i = (i > 0) ? __ldg(Hy + c - 1) : 0.0f;
         h.hz_i = (i > 0) ? __ldg(Hz + c - 1) : 0.0f;
-        if (FACE || PML_XY) e_core<FACE, true>(a, i, j, k, c, h, n, fl);
+        if (FACE || PML_XY) e_core<FACE, true>(a, i, j, k, c, h, n, fl,
+                                               !FACE || plane_has_flux(a.flux, true, w_xy, k));
         else if (plane_in_z_slab(a, k)) e_core<false, true>(a, i, j, k, c, h, n, fl);
         else e_core<false, false>(a, i, j, k, c, h, n, fl);
         hx_km1 = h.hx;
@@ -263,7 +264,8 @@ __device__ __forceinline__ void e_tile_zmarch(const StepArgs& a, int bx, int by,
     const bool pml_xy = tile_in_xy_slab(a, i0, blockDim.x, j0, blockDim.y);
     if (face) {
         float fl[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        if (valid) e_walk<true, true>(a, i, j, k0, k1, n, fl);
+        const bool w_xy = __any_sync(0xffffffffu, valid && cells_on_xy_face(a.flux, i, 1, j));
+        if (valid) e_walk<true, true>(a, i, j, k0, k1, n, fl, w_xy);
         flux_warp_reduce(a.flux, fl, slot);
     } else if (valid) {
         float* none = nullptr;
