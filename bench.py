@@ -703,7 +703,8 @@ def bench_split(stream, steps: int, warmup: int, parts_list=(2, 4)):
     from paper_0809_1547_gb300 import inputs
     from paper_0809_1547_gb300.binding import mb_default_params
     from paper_0809_1547_gb300.sharded import SlabGrid
-    from paper_0809_1547_gb300.workloads import setup_simulation
+    from paper_0809_1547_gb300.workloads import (FACE_EVERY, FACE_STRIDE, LAM_MAX, LAM_MIN, N_FREQ,
+                                                 setup_simulation)
     w = inputs.workload_paper_320()
     cells = w.ncell
 
@@ -717,18 +718,20 @@ def bench_split(stream, steps: int, warmup: int, parts_list=(2, 4)):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1)
 
-    whole = setup_simulation(w, autotune=True, face_probes=False, stream=stream.cuda_stream)
+    whole = setup_simulation(w, autotune=True, stream=stream.cuda_stream)
     whole.step(warmup)
     t_whole = timed(lambda: (whole.step(steps), whole.join_probes()), stream)
     whole.close()
-    out = {"workload": f"{w.name}: {w.grid[0]}^3, point probe, no face probes (slab contexts do not take them)",
+    out = {"workload": f"{w.name}: {w.grid[0]}^3, centre probe + 6 face probes (each slab keeps "
+                       f"the face points on its own planes)",
            "steps": steps, "whole_grid": {"value": round(cells * steps / (t_whole / 1e3) / 1e6, 2),
                                           "unit": UNIT, "ms_per_step": round(t_whole / steps, 5)}}
     for parts in parts_list:
         sg = SlabGrid(w.grid, w.dx, w.dt, parts, mb_default_params(npml=w.npml))
         sg.set_material(w.eps, w.gain, w.N_a, w.pump)
         sg.set_seed(w.seed)
-        sg.add_point_probe(tuple(v // 2 for v in w.grid), 128, 475e-9, 705e-9)
+        sg.add_point_probe(tuple(v // 2 for v in w.grid), N_FREQ, LAM_MIN, LAM_MAX)
+        sg.add_face_probes(FACE_STRIDE, FACE_EVERY, N_FREQ, LAM_MIN, LAM_MAX)
         for s_ in sg.slabs:
             s_.autotune()
         sg.step(warmup)
