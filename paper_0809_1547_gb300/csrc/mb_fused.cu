@@ -89,7 +89,12 @@ __global__ void __launch_bounds__(BX * BY) k_step_fused(StepArgs a, DevPing d,
     const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
     const uint32_t nxy = a.g.nxy;
     const bool valid = i < nx && j < ny;
-    const int k0 = blockIdx.z * kz, k1 = min(nz, k0 + kz);
+    // The z chunk of the block: the first and the last chunk (the z-CPML
+    // planes, the heaviest) are issued first, so the launch does not end on
+    // them; the other chunks follow in order.
+    const int nzb = gridDim.z, qz = blockIdx.z;
+    const int bz = qz == 0 ? 0 : (qz == 1 ? nzb - 1 : qz - 1);
+    const int k0 = bz * kz, k1 = min(nz, k0 + kz);
     const int planes = k1 - k0, total = planes + 1;
     const long long n = a.step_ctr[0];
     const bool face = tile_on_face(a.flux, x0, x0 + BX, y0, y0 + BY, k0, k1);
