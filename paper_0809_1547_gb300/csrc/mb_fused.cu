@@ -57,6 +57,29 @@ struct FusedLayout {
     }
 };
 
+// Planes [k0, k1) of z block q of a launch with nq z blocks, for chunks of
+// kz planes (nzb = ceil(nz / kz) of them; the last one may be shorter).
+// Issue order: chunk 0, chunk nzb-1 (the two that hold the z-CPML), chunks
+// 1 .. nzb-3, then chunk nzb-2 as two halves (nq = nzb + 1 when nzb >= 3
+// and kz >= 2, else nq = nzb and chunks in the first order).
+__host__ __device__ inline int fused_z_blocks(int nz, int kz) {
+    const int nzb = (nz + kz - 1) / kz;
+    return (nzb >= 3 && kz >= 2) ? nzb + 1 : nzb;
+}
+__device__ __forceinline__ void fused_chunk(int q, int nq, int nz, int kz, int& k0, int& k1) {
+    const int nzb = (nz + kz - 1) / kz;
+    int c = q == 0 ? 0 : (q == 1 ? nzb - 1 : q - 1);
+    int lo = 0, hi = kz;
+    if (nq == nzb + 1 && q >= nzb - 1) {   // the two halves of chunk nzb - 2
+        c = nzb - 2;
+        const int h = kz / 2;
+        lo = q == nzb - 1 ? 0 : h;
+        hi = q == nzb - 1 ? h : kz;
+    }
+    k0 = c * kz + lo;
+    k1 = min(nz, c * kz + hi);
+}
+
 template <int BX, int BY, int S>
 __global__ void __launch_bounds__(BX * BY) k_step_fused(StepArgs a, DevPing d,
                                                         const __grid_constant__ TmaFusedMaps maps,
@@ -89,12 +112,11 @@ __global__ void __launch_bounds__(BX * BY) k_step_fused(StepArgs a, DevPing d,
     const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
     const uint32_t nxy = a.g.nxy;
     const bool valid = i < nx && j < ny;
-    // The z chunk of the block: the first and the last chunk (the z-CPML
-    // planes, the heaviest) are issued first, so the launch does not end on
-    // them; the other chunks follow in order.
-    const int nzb = gridDim.z, qz = blockIdx.z;
-    const int bz = qz == 0 ? 0 : (qz == 1 ? nzb - 1 : qz - 1);
-    const int k0 = bz * kz, k1 = min(nz, k0 + kz);
+    // The planes of the block (fused_chunk): the z-CPML chunks, the
+    // heaviest, are issued first and the last-issued chunk is cut in two, so
+    // the launch does not end on heavy or long blocks.
+    int k0, k1;
+    fused_chunk(blockIdx.z, gridDim.z, nz, kz, k0, k1);
     const int planes = k1 - k0, total = planes + 1;
     const long long n = a.step_ctr[0];
     const bool face = tile_on_face(a.flux, x0, x0 + BX, y0, y0 + BY, k0, k1);
@@ -370,7 +392,7 @@ static void launch_fused(const StepArgs& a, const DevPing& d, int kz, const TmaF
                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         attr_set = true;
     }
-    dim3 grid((a.g.nx + BX - 1) / BX, (a.g.ny + BY - 1) / BY, (a.g.nz + kz - 1) / kz);
+    dim3 grid((a.g.nx + BX - 1) / BX, (a.g.ny + BY - 1) / BY, fused_z_blocks(a.g.nz, kz));
     k_step_fused<BX, BY, kTmaStages><<<grid, dim3(BX, BY, 1), smem, s>>>(a, d, maps, kz);
 }
 
