@@ -405,7 +405,7 @@ int mb_autotune(mb_ctx* c) {
         };
         std::vector<std::pair<float, mb::PassTune>> tf;
         for (dim3 b : {dim3(32, 4, 1), dim3(32, 8, 1), dim3(64, 4, 1), dim3(64, 8, 1)})
-            for (int kz : {8, 16, 32, 64}) {
+            for (int kz : {8, 12, 16, 20, 24, 32, 48, 64}) {
                 const mb::PassTune t{mb::kVariantTma, b, kz};
                 if (kz > 2 * c->nz) continue;
                 tf.push_back({time_fused(t, reps), t});
