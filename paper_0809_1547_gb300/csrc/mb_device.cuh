@@ -306,6 +306,37 @@ __device__ __forceinline__ void h_pml(const StepArgs& a, int i, int j, int k, co
     }
 }
 
+// Prefetch into L1 the lines of the CPML memories that the update of cell
+// (i, j, k) will read (the E memories, planes 0 and 1 of each slab array,
+// or the H memories, planes 2 and 3), so a later load finds them on chip.
+__device__ __forceinline__ void prefetch_l1(const float* p) {
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+__device__ __forceinline__ void prefetch_psi(const StepArgs& a, int i, int j, int k, int f0) {
+    const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
+    const int L = a.pml.L;
+    const int L2 = 2 * L;
+    if (i < L || i >= nx - L) {
+        const uint32_t plane = (uint32_t)nz * ny * L2;
+        const uint32_t q = ((uint32_t)k * ny + j) * L2 + slab_index(i, nx, L);
+        prefetch_l1(a.pml.psx + q + f0 * plane);
+        prefetch_l1(a.pml.psx + q + (f0 + 1) * plane);
+    }
+    if (j < L || j >= ny - L) {
+        const uint32_t plane = (uint32_t)nz * L2 * nx;
+        const uint32_t q = ((uint32_t)k * L2 + slab_index(j, ny, L)) * nx + i;
+        prefetch_l1(a.pml.psy + q + f0 * plane);
+        prefetch_l1(a.pml.psy + q + (f0 + 1) * plane);
+    }
+    if (k < a.pml.zlo || k >= a.pml.zhi) {
+        const uint32_t s = (k < a.pml.zlo) ? k : k - a.pml.zhi + a.pml.zs;
+        const uint32_t plane = (uint32_t)a.pml.zn * ny * nx;
+        const uint32_t q = (s * ny + j) * nx + i;
+        prefetch_l1(a.pml.psz + q + f0 * plane);
+        prefetch_l1(a.pml.psz + q + (f0 + 1) * plane);
+    }
+}
+
 // H^{n+1/2} = H^{n-1/2} - S (curl_fwd E^n + psi_H) for cell (i, j, k), on
 // H values held in registers.  PML: the cell may lie in a CPML slab (false
 // only when it surely does not).  The advanced CPML memories go to o (WR).

@@ -252,6 +252,8 @@ __global__ void __launch_bounds__(BX * BY) k_step_fused(StepArgs a, DevPing d,
             d.hx[c] = hx;
             d.hy[c] = hy;
             d.hz[c] = hz;
+            // the CPML memories the E update reads after the barrier
+            if (pml) prefetch_psi(a, i, j, k, 0);
         }
         hn[own_n] = hx;
         hn[NN + own_n] = hy;
@@ -338,6 +340,8 @@ __global__ void __launch_bounds__(BX * BY) k_step_fused(StepArgs a, DevPing d,
             }
             hx_km1 = hx;
             hy_km1 = hy;
+            // the CPML memories the next plane's H update reads
+            if (p + 1 < planes && (w_pml || plane_in_z_slab(a, k + 1))) prefetch_psi(a, i, j, k + 1, 2);
         }
         if (fk) {
             // this plane's flux terms: warp sums, added to the warp's partials
