@@ -251,6 +251,13 @@ int mb_flux_async(mb_ctx* ctx, double* host_out6);
  *   z: ((f zn + s) n_y + j) n_x + i with zn = 2 npml layers (s as above). */
 int mb_get_cpml(mb_ctx* ctx, int axis, double* host_out, size_t* count);
 
+/* Diagnostic copy of the context's gain-cell list (the cells whose material
+ * byte has the gain bit, in increasing order, built on the device by
+ * mb_set_material for the two-pass step's Lorentz blocks) to host memory.
+ * *count receives the number of entries (host_out may be NULL to query it).
+ * Errors: MB_ERR_STATE before mb_set_material. */
+int mb_gain_list(mb_ctx* ctx, uint32_t* host_out, int64_t* count);
+
 /* Copy one field (MB_EX..MB_N3) to / from host memory (n cells, SI units).
  * N0 is derived (N_a minus the other three) and cannot be set. */
 int mb_get_field(mb_ctx* ctx, int which, float* host_out);

@@ -87,6 +87,7 @@ _SIGS = [
     ("mb_energy", C.c_int, [_P, C.POINTER(C.c_double), _P]),
     ("mb_get_field", C.c_int, [_P, C.c_int, _P]),
     ("mb_get_cpml", C.c_int, [_P, C.c_int, _P, C.POINTER(C.c_size_t)]),
+    ("mb_gain_list", C.c_int, [_P, _P, C.POINTER(C.c_int64)]),
     ("mb_set_field", C.c_int, [_P, C.c_int, _P]),
     ("mb_get_field_device", C.c_int, [_P, C.c_int, _P, C.POINTER(C.c_double)]),
     ("mb_save_state", C.c_int, [_P, _P, C.POINTER(C.c_size_t)]),
@@ -370,6 +371,17 @@ def mb_energy(h):
     fl = np.zeros(6)
     _check(load_library().mb_energy(h, C.byref(U), _ptr(fl)), h)
     return U.value, fl
+
+
+def mb_gain_list(h):
+    """The context's gain-cell list (uint32 cell indices, increasing)."""
+    lib = load_library()
+    n = C.c_int64()
+    _check(lib.mb_gain_list(h, None, C.byref(n)), h)
+    out = np.zeros(n.value, dtype=np.uint32)
+    if n.value:
+        _check(lib.mb_gain_list(h, _ptr(out), C.byref(n)), h)
+    return out
 
 
 def mb_get_cpml(h, axis: int):
@@ -691,6 +703,10 @@ class MBSimulation:
 
     def field(self, name):
         return mb_get_field(self._h, name, self.shape)
+
+    def gain_list(self):
+        """The gain cells the two-pass step's Lorentz blocks run over."""
+        return mb_gain_list(self._h)
 
     def cpml(self, axis: int):
         """CPML memories along `axis` (SI), shaped (4, ...) as in mb_get_cpml:

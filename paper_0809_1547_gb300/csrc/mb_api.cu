@@ -417,14 +417,15 @@ namespace mbi {
 
 // Host side of mb_set_material (no device work): the material byte of each
 // of the N cells (bits 0..6: id of its eps_r value, bit 7: gain cell when
-// gain_on) into mat, the gain cells' indices in increasing order into glist
-// (grown to glist_cap entries as needed, not zeroed), the distinct values in
+// gain_on) into mat, with want_list the gain cells' indices in increasing
+// order into glist (grown to glist_cap entries as needed, not zeroed; the
+// context builds its list on the device instead), the distinct values in
 // id order into lut_eps (empty when dense: more than 128 values, every id 0),
 // and their count into n_gain.  Returns MB_OK, MB_ERR_MATERIALS (a value not
 // finite or below 1; mat is then partly written) or MB_ERR_OOM.
 int map_materials(const float* eps_map, const uint8_t* gain_mask, int64_t N, bool gain_on,
                   int max_threads, uint8_t* mat, std::unique_ptr<uint32_t[]>& glist, size_t& glist_cap,
-                  std::vector<float>& lut_eps, bool& dense, size_t& n_gain) {
+                  std::vector<float>& lut_eps, bool& dense, size_t& n_gain, bool want_list) {
     // Material ids by the bit pattern of eps_r: up to 128 distinct values
     // share a LUT, more switch to a dense 1/eps map.  One pool of host
     // threads over chunks of cells, two passes with a barrier between.
@@ -540,7 +541,7 @@ int map_materials(const float* eps_map, const uint8_t* gain_mask, int64_t N, boo
                 }
                 for (int r = 0; r < nthr; ++r) goff[r + 1] = goff[r] + ngain[r];
                 const size_t need = (size_t)std::max<int64_t>(goff[nthr], 1);
-                if (!any_bad && glist_cap < need) {
+                if (want_list && !any_bad && glist_cap < need) {
                     glist.reset(new (std::nothrow) uint32_t[need]);
                     glist_cap = glist ? need : 0;
                     no_mem = !glist;
@@ -561,6 +562,7 @@ int map_materials(const float* eps_map, const uint8_t* gain_mask, int64_t N, boo
         if (!identity)
             for (int64_t q = chunk[t].first; q < chunk[t].second; ++q)
                 mat[q] = (uint8_t)(remap[mat[q] & 0x7f] | (mat[q] & 0x80));
+        if (!want_list) return;
         // gain cells in order, without a branch per cell: every index is
         // written and the position advances on gain cells; the loop ends when
         // the thread's segment is full, so no write leaves it
@@ -799,7 +801,8 @@ int mb_destroy(mb_ctx* c) {
     void* bufs[] = {c->d_fields, c->d_mat, c->d_inv_eps, c->d_lut, c->d_psi[0], c->d_psi[1],
                     c->d_psi[2], c->d_coef, c->d_ctr, c->d_flux, c->d_partial, c->d_energy,
                     c->d_nonfinite, c->d_probe_cell, c->d_probe_omega, c->d_probe_acc,
-                    c->d_face_omega, c->d_face_acc, c->d_face_acc32, c->d_glist, c->d_src_wave, c->d_err,
+                    c->d_face_omega, c->d_face_acc, c->d_face_acc32, c->d_glist, c->d_glist_scratch,
+                    c->d_src_wave, c->d_err,
                     c->d_fields2, c->d_psi2[0], c->d_psi2[1], c->d_psi2[2], c->d_flux_out};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -834,8 +837,9 @@ int mb_set_material(mb_ctx* c, const float* eps_map, const uint8_t* gain_mask, d
     size_t n_gain = 0;
     // into the context's work buffers; they replace the host copy only when
     // every check passed
+    // the gain-cell list is built on the device from the material bytes
     switch (map_materials(eps_map, gain_mask, N, N_a > 0.0, 16, mat, c->h_glist, c->h_glist_cap,
-                          lut_eps, dense, n_gain)) {
+                          lut_eps, dense, n_gain, false)) {
         case MB_OK:
             break;
         case MB_ERR_OOM:
@@ -879,8 +883,19 @@ int mb_set_material(mb_ctx* c, const float* eps_map, const uint8_t* gain_mask, d
         c->glist_capacity = cap;
         c->dev_bytes += sizeof(uint32_t) * cap;
     }
-    if (n_gain)
-        MB_CUDA(c, cudaMemcpy(c->d_glist, c->h_glist.get(), sizeof(uint32_t) * n_gain, cudaMemcpyHostToDevice));
+    if (n_gain) {
+        const size_t nsc = mb::gain_list_scratch(N);
+        if (nsc > c->glist_scratch_n) {
+            if (c->d_glist_scratch) cudaFree(c->d_glist_scratch);
+            c->d_glist_scratch = nullptr;
+            c->glist_scratch_n = 0;
+            cudaError_t e = cudaMalloc((void**)&c->d_glist_scratch, sizeof(uint32_t) * nsc);
+            if (e != cudaSuccess) { cudaGetLastError(); return fail(c, MB_ERR_OOM, "gain list allocation failed"); }
+            c->glist_scratch_n = nsc;
+        }
+        mb::launch_gain_list(c->d_mat, N, c->d_glist_scratch, c->d_glist, c->stream);
+        MB_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
     c->glist_count = (uint32_t)n_gain;
     c->h_mat.swap(c->h_mat_next);
     // reset P, J and the populations (N0 = N_a, n1 = n2 = n3 = 0)
@@ -1326,6 +1341,17 @@ int mb_energy(mb_ctx* c, double* out_U, double* out_flux6) {
     return check_device_error(c);
 }
 
+int mb_gain_list(mb_ctx* c, uint32_t* host_out, int64_t* count) {
+    if (int rc = check_ctx(c)) return rc;
+    if (!count) return fail(c, MB_ERR_ARG, "null count");
+    if (!c->have_material) return fail(c, MB_ERR_STATE, "no material set");
+    *count = (int64_t)c->glist_count;
+    if (!host_out || c->glist_count == 0) return MB_OK;
+    MB_CUDA(c, cudaStreamSynchronize(c->stream));
+    MB_CUDA(c, cudaMemcpy(host_out, c->d_glist, sizeof(uint32_t) * c->glist_count, cudaMemcpyDeviceToHost));
+    return MB_OK;
+}
+
 int mb_get_cpml(mb_ctx* c, int axis, double* host_out, size_t* count) {
     if (int rc = check_ctx(c)) return rc;
     if (axis < 0 || axis > 2) return fail(c, MB_ERR_ARG, "axis must be 0, 1 or 2");
@@ -1491,7 +1517,7 @@ int mb_material_map(const float* eps_map, const uint8_t* gain_mask, int64_t n, i
     std::vector<float> lut;
     bool dense = false;
     const int rc = map_materials(eps_map, gain_mask, n, gain_on != 0, max_threads, out_mat, glist, cap,
-                                 lut, dense, n_gain);
+                                 lut, dense, n_gain, true);
     if (rc) {
         g_err = rc == MB_ERR_OOM ? "host gain-list buffer allocation failed" : "eps_r must be finite and >= 1";
         return rc;

@@ -224,6 +224,11 @@ void launch_plane_energy(const DevFields& f, const DevGrid& g, int k, const floa
 void launch_philox(const uint4* ctr, uint32_t k0, uint32_t k1, uint4* out, int n, cudaStream_t s);
 // out[q] = scale * sum_t slots[q kFluxSlots + t] (slots in order), q < 6.
 void launch_flux_sum(const double* slots, double* out, double scale, cudaStream_t s);
+// The gain cells (material bit 7) of mat[0, N) in increasing order into
+// list (n_gain entries, n_gain known); scratch holds gain_list_scratch(N)
+// counters.
+size_t gain_list_scratch(int64_t N);
+void launch_gain_list(const uint8_t* mat, int64_t N, uint32_t* scratch, uint32_t* list, cudaStream_t s);
 void launch_energy(const DevFields& f, int64_t ncell, const float* lut_eps, double* partial,
                    int nparts, int* nonfinite, double* out, cudaStream_t s);
 
@@ -302,6 +307,8 @@ struct mb_ctx {
     uint32_t* d_glist = nullptr;       // gain cells, increasing order
     uint32_t glist_count = 0;
     size_t glist_capacity = 0;
+    uint32_t* d_glist_scratch = nullptr;   // per-chunk counters of the list build
+    size_t glist_scratch_n = 0;
     // step counters: [0] steps completed, [1] finished blocks of the current
     // launch, [2 + q] the step count when copy q was last written by the
     // single-pass step (the probes of that copy sample it)

@@ -253,6 +253,98 @@ __global__ void k_flux_sum(const double* slots, double* out, double scale) {
     out[q] = v * scale;
 }
 
+// ------------------------------------------------------------ gain-cell list
+// Three passes over chunks of kGainChunk cells: the gain cells of each chunk
+// counted (warp ballots), the counts turned into each chunk's first list
+// position (one block, in order), then each chunk's gain cells written in
+// increasing order (per 1024-cell tile: ballots, the warps' counts summed
+// in shared memory, every gain cell placed after those before it).
+constexpr int kGainChunk = 1 << 16;
+
+__global__ void __launch_bounds__(1024) k_gain_count(const uint8_t* mat, int64_t N, uint32_t* counts) {
+    __shared__ uint32_t wsum[32];
+    const int64_t c0 = (int64_t)blockIdx.x * kGainChunk;
+    const int64_t c1 = min(N, c0 + kGainChunk);
+    uint32_t n = 0;
+    for (int64_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) n += (mat[c] >> 7);
+    for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = n;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wsum[w];
+        counts[blockIdx.x] = t;
+    }
+}
+
+// counts[0, nchunks) -> exclusive prefix sums, in place (one block).
+__global__ void __launch_bounds__(1024) k_gain_scan(uint32_t* counts, int nchunks) {
+    __shared__ uint32_t wsum[32];
+    __shared__ uint32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int base = 0; base < nchunks; base += blockDim.x) {
+        const int q = base + threadIdx.x;
+        const uint32_t v = q < nchunks ? counts[q] : 0u;
+        uint32_t x = v;   // inclusive scan within the warp
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t z = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0u;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, z, o);
+                if (lane >= o) z += y;
+            }
+            wsum[lane] = z;   // inclusive prefix of the warp totals
+        }
+        __syncthreads();
+        const uint32_t before = carry + (warp > 0 ? wsum[warp - 1] : 0u) + (x - v);
+        if (q < nchunks) counts[q] = before;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry += wsum[(blockDim.x >> 5) - 1];
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_gain_scatter(const uint8_t* mat, int64_t N, const uint32_t* first,
+                                                       uint32_t* list) {
+    __shared__ uint32_t wsum[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int64_t c0 = (int64_t)blockIdx.x * kGainChunk;
+    const int64_t c1 = min(N, c0 + kGainChunk);
+    uint32_t pos = first[blockIdx.x];
+    for (int64_t base = c0; base < c1; base += blockDim.x) {
+        const int64_t c = base + threadIdx.x;
+        const bool g = c < c1 && (mat[c] & 0x80);
+        const unsigned b = __ballot_sync(0xffffffffu, g);
+        if (lane == 0) wsum[warp] = __popc(b);
+        __syncthreads();
+        uint32_t before = 0, total = 0;
+        for (int w = 0; w < nw; ++w) {
+            before += w < warp ? wsum[w] : 0u;
+            total += wsum[w];
+        }
+        if (g) list[pos + before + __popc(b & ((1u << lane) - 1u))] = (uint32_t)c;
+        pos += total;
+        __syncthreads();
+    }
+}
+
+size_t gain_list_scratch(int64_t N) { return (size_t)((N + kGainChunk - 1) / kGainChunk); }
+
+void launch_gain_list(const uint8_t* mat, int64_t N, uint32_t* scratch, uint32_t* list, cudaStream_t s) {
+    const int nchunks = (int)gain_list_scratch(N);
+    if (nchunks == 0) return;
+    k_gain_count<<<nchunks, 1024, 0, s>>>(mat, N, scratch);
+    k_gain_scan<<<1, 1024, 0, s>>>(scratch, nchunks);
+    k_gain_scatter<<<nchunks, 1024, 0, s>>>(mat, N, scratch, list);
+}
+
 void launch_flux_sum(const double* slots, double* out, double scale, cudaStream_t s) {
     k_flux_sum<<<1, 32, 0, s>>>(slots, out, scale);
 }

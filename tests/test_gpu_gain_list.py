@@ -1,0 +1,40 @@
+"""The gain-cell list mb_set_material builds on the device (chunked counts,
+an ordered scan, an ordered scatter) against the host material map's list
+(mb_material_map, a separate implementation): equal, in increasing order,
+on grids whose cell counts end inside a 65536-cell chunk, span several
+chunks, or fit in one; empty with the gain off."""
+import numpy as np
+import pytest
+
+from paper_0809_1547_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_0809_1547_gb300 import build
+    build.build()
+
+
+@pytest.mark.parametrize("grid,seed", [((48, 48, 48), 1), ((97, 61, 33), 2), ((16, 16, 8), 3),
+                                       ((160, 96, 80), 4)])
+def test_device_gain_list_equals_the_host_map(grid, seed):
+    from paper_0809_1547_gb300.binding import MBSimulation, mb_default_params, mb_material_map
+    eps, gain = inputs.random_small(grid, seed=seed, npml=4)
+    sim = MBSimulation(grid, 20e-9, inputs.courant_dt(20e-9), mb_default_params(npml=4))
+    sim.set_material(eps, gain, 3e24, 1e13)
+    dev = sim.gain_list()
+    _, host, _, _ = mb_material_map(eps, gain, True, 16)
+    assert dev.dtype == np.uint32 and dev.size == int(np.count_nonzero(gain.ravel()))
+    assert np.array_equal(dev, np.asarray(host, dtype=np.uint32))
+    assert np.all(np.diff(dev.astype(np.int64)) > 0)
+    # the gain off: no gain cells
+    sim.set_material(eps, gain, 0.0, 1e13)
+    assert sim.gain_list().size == 0
+    # a second map on the same context: the list follows it
+    gain2 = np.ascontiguousarray(gain[::-1])
+    sim.set_material(eps, gain2, 3e24, 1e13)
+    _, host2, _, _ = mb_material_map(eps, gain2, True, 16)
+    assert np.array_equal(sim.gain_list(), np.asarray(host2, dtype=np.uint32))
+    sim.close()
