@@ -477,6 +477,10 @@ def bench_ours(args):
     sim2.add_face_probes(8, 4, 128, 475e-9, 705e-9)
     sim2.set_material(eps_h, gain_h, w.N_a, w.pump)
     sim2.set_seed(w.seed)
+    # the launch shapes the timed run was tuned to (set-up, like the graphs)
+    sim2.set_tuning(blk_h, blk_e)
+    if single[0]:
+        sim2.set_single_pass(single)
     sim2.step(2)          # graph capture outside the timed region
     sim2.set_material(eps_h, gain_h, w.N_a, w.pump)
     sim2.synchronize()
