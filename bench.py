@@ -487,6 +487,13 @@ def bench_ours(args):
     barrier(world)
     bufs = [torch.zeros(6, dtype=torch.float64).pin_memory() for _ in range(2)]
     evs = [torch.cuda.Event() for _ in range(2)]
+    # the loop's host-side calls once before the timed region (first-use
+    # initialisation of the read-back path and of the host sum)
+    sim2.flux_async(bufs[0])
+    evs[0].record(stream)
+    evs[0].synchronize()
+    float(bufs[0].sum())
+    sim2.probe_spectrum(pid)
     emitted = []
     t0 = time.perf_counter()
     sim2.set_material(eps_h, gain_h, w.N_a, w.pump)
