@@ -242,17 +242,25 @@ def test_save_load_state_roundtrip_bitwise():
     eps, gain = inputs.random_small(grid, seed=3, npml=4)
     _, g = make_pair(grid, eps, gain, 4e24, 1e13, 6, params_kw(npml=4))
     g.add_point_probe((10, 10, 10), 8, 500e-9, 650e-9)
+    # face probes every step: the save at step 10 falls between two flushes
+    # of their FP32 partial sums (every 16th call), so the blob must hold them
+    g.add_face_probes(2, 1, 8, 500e-9, 650e-9)
+    g.set_source((11, 10, 10), 2, 532e-9, 1.5e-15, 0.5e-15, 1e9)
     g.step(10)
     blob = g.save_state()
     g.step(15)
     ref = {name: g.field(name) for name in FIELD_NAMES}
     S_ref, _ = g.probe_spectrum(0)
+    F_ref = [g.face_spectrum(face)[0] for face in range(6)]
+    assert max(float(np.abs(F).max()) for F in F_ref) > 0
     g.load_state(blob)
     assert g.n == 10
     g.step(15)
     for name in FIELD_NAMES:
         np.testing.assert_array_equal(g.field(name), ref[name])
     np.testing.assert_array_equal(g.probe_spectrum(0)[0], S_ref)
+    for face in range(6):
+        np.testing.assert_array_equal(g.face_spectrum(face)[0], F_ref[face])
     g.close()
 
 
