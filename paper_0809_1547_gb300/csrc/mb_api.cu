@@ -148,6 +148,9 @@ void build_args(mb_ctx* c) {
     a.f.mat = c->d_mat;
     a.f.inv_eps = c->dense_eps ? c->d_inv_eps : nullptr;
     a.f.lut_inv_eps = c->d_lut;
+    a.f.n_lut = c->n_lut;
+    a.f.ie0 = c->h_lut_ie[0];
+    a.f.ie1 = c->h_lut_ie[1];
     const int L = c->p.npml;
     a.pml.L = L;
     z_cpml_bounds(c, a.pml);
@@ -855,6 +858,10 @@ int mb_set_material(mb_ctx* c, const float* eps_map, const uint8_t* gain_mask, d
         lut[128 + q] = lut_eps[q];
         c->h_lut_eps[q] = lut_eps[q];
     }
+    // dense maps (no table) take the per-cell array; n_lut counts the table
+    c->n_lut = dense ? 128 : (int)lut_eps.size();
+    c->h_lut_ie[0] = lut[0];
+    c->h_lut_ie[1] = lut[1];
     MB_CUDA(c, cudaMemcpy(c->d_mat, mat, (size_t)N, cudaMemcpyHostToDevice));
     MB_CUDA(c, cudaMemcpy(c->d_lut, lut.data(), sizeof(float) * 256, cudaMemcpyHostToDevice));
     if (dense) {

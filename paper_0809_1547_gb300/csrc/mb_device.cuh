@@ -37,6 +37,10 @@ struct DevFields {
     const uint8_t* mat;        // bits 0..6: material id, bit 7: gain medium
     const float* inv_eps;      // dense 1/eps_r per cell, or nullptr
     const float* lut_inv_eps;  // 1/eps_r per material id (128 entries)
+    // a map of at most two eps_r values (n_lut <= 2): 1/eps_r of ids 0 and 1
+    // (the table's first entries), chosen by a select instead of a load
+    int n_lut;
+    float ie0, ie1;
 };
 
 // CPML memories live only in the slabs: for axis w, 2 L layers indexed by
@@ -582,7 +586,9 @@ __device__ __forceinline__ void e_compute_to(const StepArgs& a, int i, int j, in
                                              float fl[6], float& ex1, float& ey1, float& ez1,
                                              const PsiOut& o, bool flux_plane = true) {
     const DevFields& f = a.f;
-    const float ie = f.inv_eps ? __ldg(f.inv_eps + c) : __ldg(f.lut_inv_eps + (m & 0x7f));
+    const float ie = f.inv_eps       ? __ldg(f.inv_eps + c)
+                     : f.n_lut <= 2 ? ((m & 0x7f) ? f.ie1 : f.ie0)
+                                    : __ldg(f.lut_inv_eps + (m & 0x7f));
     e_compute_ie<FLUX, PML>(a, i, j, k, c, h, ie, ex0, ey0, ez0, gain, jx, jy, jz, n1, n2, n3, n,
                             fl, ex1, ey1, ez1, o, flux_plane);
 }

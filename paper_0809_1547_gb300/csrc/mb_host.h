@@ -347,6 +347,8 @@ struct mb_ctx {
     std::unique_ptr<uint32_t[]> h_glist;   // mb_set_material's gain-list buffer
     size_t h_glist_cap = 0;
     std::vector<float> h_lut_eps;      // eps_r per material id
+    int n_lut = 128;                   // entries of the table (128: unknown or dense)
+    float h_lut_ie[2] = {1.0f, 1.0f};  // 1/eps_r of ids 0 and 1
     double N_a = 0, W_p = 0;
     uint64_t seed = 0;
 
