@@ -46,6 +46,8 @@ struct AdjArgs {
     const uint8_t* mat;
     const float* inv_eps;
     const float* lut_inv_eps;
+    int n_lut;                  // at most two eps_r values: 1/eps_r of ids 0, 1 below
+    float ie0, ie1;
     DevCpml pml;                // forward tables (psi pointers unused)
     float *lpsx, *lpsy, *lpsz;  // adjoint CPML memories, forward layout
     FwdFields x0, x1;           // states at n and n+1
@@ -62,7 +64,9 @@ struct AdjArgs {
 constexpr int kAccSlots = 64;
 
 __device__ __forceinline__ float ie_of(const AdjArgs& a, uint32_t c) {
-    return a.inv_eps ? __ldg(a.inv_eps + c) : __ldg(a.lut_inv_eps + (__ldg(a.mat + c) & 0x7f));
+    if (a.inv_eps) return __ldg(a.inv_eps + c);
+    const int id = __ldg(a.mat + c) & 0x7f;
+    return a.n_lut <= 2 ? (id ? a.ie1 : a.ie0) : __ldg(a.lut_inv_eps + id);
 }
 
 __device__ __forceinline__ bool in_slab(int i, int n, int L) { return L > 0 && (i < L || i >= n - L); }
@@ -657,6 +661,9 @@ extern "C" int mb_adjoint_energy_zface(mb_ctx* c, int n_steps, int ckpt_every, i
     a.mat = c->d_mat;
     a.inv_eps = c->args.f.inv_eps;
     a.lut_inv_eps = c->args.f.lut_inv_eps;
+    a.n_lut = c->args.f.n_lut;
+    a.ie0 = c->args.f.ie0;
+    a.ie1 = c->args.f.ie1;
     a.pml = c->args.pml;
     a.lpsx = adj + 18 * N;
     a.lpsy = a.lpsx + c->psi_elems[0];
