@@ -258,6 +258,13 @@ int mb_get_cpml(mb_ctx* ctx, int axis, double* host_out, size_t* count);
  * Errors: MB_ERR_STATE before mb_set_material. */
 int mb_gain_list(mb_ctx* ctx, uint32_t* host_out, int64_t* count);
 
+/* Diagnostic copy of the context's material bytes (n cells, x fastest; bits
+ * 0..6: the id of the cell's eps_r value in order of first appearance in
+ * the map, 0 for a dense map; bit 7: gain cell), as mb_set_material built
+ * them on the device: equal to mb_material_map's.  Errors: MB_ERR_STATE
+ * before mb_set_material. */
+int mb_get_material(mb_ctx* ctx, uint8_t* host_out);
+
 /* Copy one field (MB_EX..MB_N3) to / from host memory (n cells, SI units).
  * N0 is derived (N_a minus the other three) and cannot be set. */
 int mb_get_field(mb_ctx* ctx, int which, float* host_out);

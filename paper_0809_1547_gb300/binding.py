@@ -88,6 +88,7 @@ _SIGS = [
     ("mb_get_field", C.c_int, [_P, C.c_int, _P]),
     ("mb_get_cpml", C.c_int, [_P, C.c_int, _P, C.POINTER(C.c_size_t)]),
     ("mb_gain_list", C.c_int, [_P, _P, C.POINTER(C.c_int64)]),
+    ("mb_get_material", C.c_int, [_P, _P]),
     ("mb_set_field", C.c_int, [_P, C.c_int, _P]),
     ("mb_get_field_device", C.c_int, [_P, C.c_int, _P, C.POINTER(C.c_double)]),
     ("mb_save_state", C.c_int, [_P, _P, C.POINTER(C.c_size_t)]),
@@ -382,6 +383,13 @@ def mb_gain_list(h):
     if n.value:
         _check(lib.mb_gain_list(h, _ptr(out), C.byref(n)), h)
     return out
+
+
+def mb_get_material(h, shape):
+    """The context's material bytes [k, j, i] (uint8; bit 7: gain cell)."""
+    out = np.zeros(int(np.prod(shape)), dtype=np.uint8)
+    _check(load_library().mb_get_material(h, _ptr(out)), h)
+    return out.reshape(shape)
 
 
 def mb_get_cpml(h, axis: int):
@@ -707,6 +715,10 @@ class MBSimulation:
     def gain_list(self):
         """The gain cells the two-pass step's Lorentz blocks run over."""
         return mb_gain_list(self._h)
+
+    def material(self):
+        """The material bytes [k, j, i] mb_set_material built on the device."""
+        return mb_get_material(self._h, self.grid[::-1])
 
     def cpml(self, axis: int):
         """CPML memories along `axis` (SI), shaped (4, ...) as in mb_get_cpml:

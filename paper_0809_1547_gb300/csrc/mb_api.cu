@@ -420,15 +420,14 @@ namespace mbi {
 
 // Host side of mb_set_material (no device work): the material byte of each
 // of the N cells (bits 0..6: id of its eps_r value, bit 7: gain cell when
-// gain_on) into mat, with want_list the gain cells' indices in increasing
-// order into glist (grown to glist_cap entries as needed, not zeroed; the
-// context builds its list on the device instead), the distinct values in
+// gain_on) into mat, the gain cells' indices in increasing order into glist
+// (grown to glist_cap entries as needed, not zeroed), the distinct values in
 // id order into lut_eps (empty when dense: more than 128 values, every id 0),
 // and their count into n_gain.  Returns MB_OK, MB_ERR_MATERIALS (a value not
 // finite or below 1; mat is then partly written) or MB_ERR_OOM.
 int map_materials(const float* eps_map, const uint8_t* gain_mask, int64_t N, bool gain_on,
                   int max_threads, uint8_t* mat, std::unique_ptr<uint32_t[]>& glist, size_t& glist_cap,
-                  std::vector<float>& lut_eps, bool& dense, size_t& n_gain, bool want_list) {
+                  std::vector<float>& lut_eps, bool& dense, size_t& n_gain) {
     // Material ids by the bit pattern of eps_r: up to 128 distinct values
     // share a LUT, more switch to a dense 1/eps map.  One pool of host
     // threads over chunks of cells, two passes with a barrier between.
@@ -544,7 +543,7 @@ int map_materials(const float* eps_map, const uint8_t* gain_mask, int64_t N, boo
                 }
                 for (int r = 0; r < nthr; ++r) goff[r + 1] = goff[r] + ngain[r];
                 const size_t need = (size_t)std::max<int64_t>(goff[nthr], 1);
-                if (want_list && !any_bad && glist_cap < need) {
+                if (!any_bad && glist_cap < need) {
                     glist.reset(new (std::nothrow) uint32_t[need]);
                     glist_cap = glist ? need : 0;
                     no_mem = !glist;
@@ -565,7 +564,6 @@ int map_materials(const float* eps_map, const uint8_t* gain_mask, int64_t N, boo
         if (!identity)
             for (int64_t q = chunk[t].first; q < chunk[t].second; ++q)
                 mat[q] = (uint8_t)(remap[mat[q] & 0x7f] | (mat[q] & 0x80));
-        if (!want_list) return;
         // gain cells in order, without a branch per cell: every index is
         // written and the position advances on gain cells; the loop ends when
         // the thread's segment is full, so no write leaves it
@@ -741,7 +739,6 @@ static int create_ctx(mb_ctx** out, const int grid[3], int gnz, int kz0, int own
     MB_CREATE_CUDA(cudaMemset(c->d_err, 0, sizeof(int)));
     MB_CREATE_CUDA(cudaMemset(c->d_flux, 0, sizeof(double) * 6 * mb::kFluxSlots));
 #undef MB_CREATE_CUDA
-    c->h_mat.assign((size_t)ncell, 0);
     c->face.on = 0;
     build_args(c);
     gain_coefficients(c);
@@ -805,7 +802,7 @@ int mb_destroy(mb_ctx* c) {
                     c->d_psi[2], c->d_coef, c->d_ctr, c->d_flux, c->d_partial, c->d_energy,
                     c->d_nonfinite, c->d_probe_cell, c->d_probe_omega, c->d_probe_acc,
                     c->d_face_omega, c->d_face_acc, c->d_face_acc32, c->d_glist, c->d_glist_scratch,
-                    c->d_src_wave, c->d_err,
+                    c->d_upload, c->d_keys, c->d_src_wave, c->d_err,
                     c->d_fields2, c->d_psi2[0], c->d_psi2[1], c->d_psi2[2], c->d_flux_out};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -833,24 +830,62 @@ int mb_set_material(mb_ctx* c, const float* eps_map, const uint8_t* gain_mask, d
     if (!(N_a >= 0) || !(pump >= 0) || !std::isfinite(N_a) || !std::isfinite(pump))
         return fail(c, MB_ERR_ARG, "N_a and pump must be finite and >= 0");
     const int64_t N = c->ncell;
-    if (c->h_mat_next.size() != (size_t)N) c->h_mat_next.resize((size_t)N);
-    uint8_t* mat = c->h_mat_next.data();
+    // The map on the device: the eps_r map and the gain mask uploaded into
+    // scratch, their distinct values found (checked before any state of the
+    // context changes), the table sorted on the host, the material bytes and
+    // the gain-cell list built from it.
+    auto grow = [&](void** p, size_t& have, size_t need) -> bool {
+        if (have >= need && *p) return true;
+        if (*p) cudaFree(*p);
+        *p = nullptr;
+        have = 0;
+        if (cudaMalloc(p, need) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        have = need;
+        return true;
+    };
+    const size_t up_bytes = 5 * (size_t)N;
+    const size_t key_bytes = 2 * sizeof(uint32_t) * mb::kMatKeys + 2 * sizeof(int);
+    if (!grow((void**)&c->d_upload, c->upload_bytes, up_bytes) ||
+        !grow((void**)&c->d_keys, c->keys_bytes, key_bytes))
+        return fail(c, MB_ERR_OOM, "material map scratch allocation failed");
+    float* d_eps = reinterpret_cast<float*>(c->d_upload);
+    uint8_t* d_gain = c->d_upload + 4 * (size_t)N;
+    uint32_t* d_first = c->d_keys + mb::kMatKeys;
+    int* d_flags = reinterpret_cast<int*>(c->d_keys + 2 * mb::kMatKeys);
+    MB_CUDA(c, cudaMemsetAsync(c->d_keys, 0xff, 2 * sizeof(uint32_t) * mb::kMatKeys, c->stream));
+    MB_CUDA(c, cudaMemsetAsync(d_flags, 0, 2 * sizeof(int), c->stream));
+    MB_CUDA(c, cudaMemcpyAsync(d_eps, eps_map, sizeof(float) * (size_t)N, cudaMemcpyHostToDevice, c->stream));
+    MB_CUDA(c, cudaMemcpyAsync(d_gain, gain_mask, (size_t)N, cudaMemcpyHostToDevice, c->stream));
+    mb::launch_mat_keys(d_eps, N, c->d_keys, d_first, d_flags, c->stream);
+    uint32_t h_keys[2 * mb::kMatKeys + 2];
+    MB_CUDA(c, cudaMemcpyAsync(h_keys, c->d_keys, key_bytes, cudaMemcpyDeviceToHost, c->stream));
+    MB_CUDA(c, cudaStreamSynchronize(c->stream));
+    const int* h_flags = reinterpret_cast<const int*>(h_keys + 2 * mb::kMatKeys);
+    if (h_flags[0]) return fail(c, MB_ERR_MATERIALS, "eps_r must be finite and >= 1");
+    const bool dense = h_flags[1] != 0;
+    // the table in order of first appearance in the map (the ids do not
+    // depend on the order in which the device filled it, and equal those of
+    // the host statement of the map, mb_material_map)
     std::vector<float> lut_eps;
-    bool dense = false;
-    size_t n_gain = 0;
-    // into the context's work buffers; they replace the host copy only when
-    // every check passed
-    // the gain-cell list is built on the device from the material bytes
-    switch (map_materials(eps_map, gain_mask, N, N_a > 0.0, 16, mat, c->h_glist, c->h_glist_cap,
-                          lut_eps, dense, n_gain, false)) {
-        case MB_OK:
-            break;
-        case MB_ERR_OOM:
-            return fail(c, MB_ERR_OOM, "host gain-list buffer allocation failed");
-        default:
-            return fail(c, MB_ERR_MATERIALS, "eps_r must be finite and >= 1");
+    std::vector<uint32_t> keys;
+    if (!dense) {
+        std::vector<std::pair<uint32_t, uint32_t>> kf;   // (first cell, bits)
+        for (int q = 0; q < mb::kMatKeys && h_keys[q] != mb::kNoKey; ++q)
+            kf.push_back({h_keys[mb::kMatKeys + q], h_keys[q]});
+        std::sort(kf.begin(), kf.end());
+        for (const auto& p : kf) keys.push_back(p.second);
+        for (uint32_t k : keys) {
+            float v;
+            std::memcpy(&v, &k, 4);
+            lut_eps.push_back(v);
+        }
+        if (!keys.empty())
+            MB_CUDA(c, cudaMemcpyAsync(c->d_keys, keys.data(), sizeof(uint32_t) * keys.size(),
+                                       cudaMemcpyHostToDevice, c->stream));
     }
-    cudaStreamSynchronize(c->stream);
     std::vector<float> lut(256, 1.0f);
     c->h_lut_eps.assign(128, 1.0f);
     for (size_t q = 0; q < lut_eps.size(); ++q) {
@@ -858,26 +893,30 @@ int mb_set_material(mb_ctx* c, const float* eps_map, const uint8_t* gain_mask, d
         lut[128 + q] = lut_eps[q];
         c->h_lut_eps[q] = lut_eps[q];
     }
-    // dense maps (no table) take the per-cell array; n_lut counts the table
-    c->n_lut = dense ? 128 : (int)lut_eps.size();
-    c->h_lut_ie[0] = lut[0];
-    c->h_lut_ie[1] = lut[1];
-    MB_CUDA(c, cudaMemcpy(c->d_mat, mat, (size_t)N, cudaMemcpyHostToDevice));
-    MB_CUDA(c, cudaMemcpy(c->d_lut, lut.data(), sizeof(float) * 256, cudaMemcpyHostToDevice));
-    if (dense) {
-        if (!c->d_inv_eps) {
-            cudaError_t e = cudaMalloc((void**)&c->d_inv_eps, sizeof(float) * (size_t)N);
-            if (e != cudaSuccess) { cudaGetLastError(); return fail(c, MB_ERR_OOM, "dense eps map allocation failed"); }
-            c->dev_bytes += sizeof(float) * (size_t)N;
-        }
-        std::vector<float> inv((size_t)N);
-        for (int64_t q = 0; q < N; ++q) inv[q] = (float)(1.0 / (double)eps_map[q]);
-        MB_CUDA(c, cudaMemcpy(c->d_inv_eps, inv.data(), sizeof(float) * (size_t)N, cudaMemcpyHostToDevice));
+    if (dense && !c->d_inv_eps) {
+        cudaError_t e = cudaMalloc((void**)&c->d_inv_eps, sizeof(float) * (size_t)N);
+        if (e != cudaSuccess) { cudaGetLastError(); return fail(c, MB_ERR_OOM, "dense eps map allocation failed"); }
+        c->dev_bytes += sizeof(float) * (size_t)N;
     }
-    c->dense_eps = dense;
-    c->N_a = N_a;
-    c->W_p = pump;
-    // gain cells in increasing order: the Lorentz update runs over this list
+    const size_t nsc = mb::gain_list_scratch(N);
+    if (nsc > c->glist_scratch_n) {
+        if (c->d_glist_scratch) cudaFree(c->d_glist_scratch);
+        c->d_glist_scratch = nullptr;
+        c->glist_scratch_n = 0;
+        cudaError_t e = cudaMalloc((void**)&c->d_glist_scratch, sizeof(uint32_t) * nsc);
+        if (e != cudaSuccess) { cudaGetLastError(); return fail(c, MB_ERR_OOM, "gain list allocation failed"); }
+        c->glist_scratch_n = nsc;
+    }
+    mb::launch_mat_ids(d_eps, d_gain, N, c->d_keys, (int)keys.size(), dense, N_a > 0.0, c->d_mat,
+                       c->d_inv_eps, c->stream);
+    MB_CUDA(c, cudaMemcpyAsync(c->d_lut, lut.data(), sizeof(float) * 256, cudaMemcpyHostToDevice, c->stream));
+    // gain cells in increasing order: the two-pass step's Lorentz blocks run over this list
+    mb::launch_gain_count(c->d_mat, N, c->d_glist_scratch, c->stream);
+    uint32_t n_gain32 = 0;
+    MB_CUDA(c, cudaMemcpyAsync(&n_gain32, c->d_glist_scratch + (nsc - 2), sizeof(uint32_t),
+                               cudaMemcpyDeviceToHost, c->stream));
+    MB_CUDA(c, cudaStreamSynchronize(c->stream));
+    const size_t n_gain = n_gain32;
     if (n_gain > c->glist_capacity || !c->d_glist) {
         if (c->d_glist) {
             cudaFree(c->d_glist);
@@ -890,23 +929,18 @@ int mb_set_material(mb_ctx* c, const float* eps_map, const uint8_t* gain_mask, d
         c->glist_capacity = cap;
         c->dev_bytes += sizeof(uint32_t) * cap;
     }
-    if (n_gain) {
-        const size_t nsc = mb::gain_list_scratch(N);
-        if (nsc > c->glist_scratch_n) {
-            if (c->d_glist_scratch) cudaFree(c->d_glist_scratch);
-            c->d_glist_scratch = nullptr;
-            c->glist_scratch_n = 0;
-            cudaError_t e = cudaMalloc((void**)&c->d_glist_scratch, sizeof(uint32_t) * nsc);
-            if (e != cudaSuccess) { cudaGetLastError(); return fail(c, MB_ERR_OOM, "gain list allocation failed"); }
-            c->glist_scratch_n = nsc;
-        }
-        mb::launch_gain_list(c->d_mat, N, c->d_glist_scratch, c->d_glist, c->stream);
-        MB_CUDA(c, cudaStreamSynchronize(c->stream));
-    }
+    if (n_gain) mb::launch_gain_scatter(c->d_mat, N, c->d_glist_scratch, c->d_glist, c->stream);
+    // dense maps (no table) take the per-cell array; n_lut counts the table
+    c->n_lut = dense ? 128 : (int)lut_eps.size();
+    c->h_lut_ie[0] = lut[0];
+    c->h_lut_ie[1] = lut[1];
+    c->dense_eps = dense;
+    c->N_a = N_a;
+    c->W_p = pump;
     c->glist_count = (uint32_t)n_gain;
-    c->h_mat.swap(c->h_mat_next);
     // reset P, J and the populations (N0 = N_a, n1 = n2 = n3 = 0)
-    MB_CUDA(c, cudaMemset(c->d_fields + 6 * N, 0, sizeof(float) * 9 * (size_t)N));
+    MB_CUDA(c, cudaMemsetAsync(c->d_fields + 6 * N, 0, sizeof(float) * 9 * (size_t)N, c->stream));
+    MB_CUDA(c, cudaStreamSynchronize(c->stream));
     c->have_material = true;
     build_args(c);
     gain_coefficients(c);
@@ -1359,6 +1393,15 @@ int mb_gain_list(mb_ctx* c, uint32_t* host_out, int64_t* count) {
     return MB_OK;
 }
 
+int mb_get_material(mb_ctx* c, uint8_t* host_out) {
+    if (int rc = check_ctx(c)) return rc;
+    if (!host_out) return fail(c, MB_ERR_ARG, "null output");
+    if (!c->have_material) return fail(c, MB_ERR_STATE, "no material set");
+    MB_CUDA(c, cudaStreamSynchronize(c->stream));
+    MB_CUDA(c, cudaMemcpy(host_out, c->d_mat, (size_t)c->ncell, cudaMemcpyDeviceToHost));
+    return MB_OK;
+}
+
 int mb_get_cpml(mb_ctx* c, int axis, double* host_out, size_t* count) {
     if (int rc = check_ctx(c)) return rc;
     if (axis < 0 || axis > 2) return fail(c, MB_ERR_ARG, "axis must be 0, 1 or 2");
@@ -1385,12 +1428,15 @@ int mb_get_field(mb_ctx* c, int which, float* host_out) {
     std::vector<float> tmp((size_t)N);
     if (which == MB_N0) {
         std::vector<float> a((size_t)N), b((size_t)N), d((size_t)N);
+        std::vector<uint8_t> m((size_t)N, 0);
         MB_CUDA(c, cudaMemcpyAsync(a.data(), field_ptr(c, MB_N1), 4 * N, cudaMemcpyDeviceToHost, c->stream));
         MB_CUDA(c, cudaMemcpyAsync(b.data(), field_ptr(c, MB_N2), 4 * N, cudaMemcpyDeviceToHost, c->stream));
         MB_CUDA(c, cudaMemcpyAsync(d.data(), field_ptr(c, MB_N3), 4 * N, cudaMemcpyDeviceToHost, c->stream));
+        if (c->have_material)
+            MB_CUDA(c, cudaMemcpyAsync(m.data(), c->d_mat, (size_t)N, cudaMemcpyDeviceToHost, c->stream));
         MB_CUDA(c, cudaStreamSynchronize(c->stream));
         for (int64_t q = 0; q < N; ++q)
-            host_out[q] = (c->h_mat[q] & 0x80) ? (float)(c->N_a * (1.0 - (double)a[q] - (double)b[q] - (double)d[q])) : 0.0f;
+            host_out[q] = (m[q] & 0x80) ? (float)(c->N_a * (1.0 - (double)a[q] - (double)b[q] - (double)d[q])) : 0.0f;
         return MB_OK;
     }
     MB_CUDA(c, cudaMemcpyAsync(tmp.data(), field_ptr(c, which), 4 * N, cudaMemcpyDeviceToHost, c->stream));
@@ -1524,7 +1570,7 @@ int mb_material_map(const float* eps_map, const uint8_t* gain_mask, int64_t n, i
     std::vector<float> lut;
     bool dense = false;
     const int rc = map_materials(eps_map, gain_mask, n, gain_on != 0, max_threads, out_mat, glist, cap,
-                                 lut, dense, n_gain, true);
+                                 lut, dense, n_gain);
     if (rc) {
         g_err = rc == MB_ERR_OOM ? "host gain-list buffer allocation failed" : "eps_r must be finite and >= 1";
         return rc;

@@ -225,10 +225,25 @@ void launch_philox(const uint4* ctr, uint32_t k0, uint32_t k1, uint4* out, int n
 // out[q] = scale * sum_t slots[q kFluxSlots + t] (slots in order), q < 6.
 void launch_flux_sum(const double* slots, double* out, double scale, cudaStream_t s);
 // The gain cells (material bit 7) of mat[0, N) in increasing order into
-// list (n_gain entries, n_gain known); scratch holds gain_list_scratch(N)
-// counters.
+// list: launch_gain_count leaves their number in scratch[gain_list_scratch(N)
+// - 2] (scratch holds gain_list_scratch(N) counters), launch_gain_scatter
+// then writes the list.
 size_t gain_list_scratch(int64_t N);
-void launch_gain_list(const uint8_t* mat, int64_t N, uint32_t* scratch, uint32_t* list, cudaStream_t s);
+void launch_gain_count(const uint8_t* mat, int64_t N, uint32_t* scratch, cudaStream_t s);
+void launch_gain_scatter(const uint8_t* mat, int64_t N, const uint32_t* scratch, uint32_t* list,
+                         cudaStream_t s);
+// The material map on the device: the distinct eps_r values into keys
+// (kMatKeys entries, kNoKey where unused, filled as a prefix) with the first
+// cell of each into first (initialised to kNoKey; flags[0]: a value not
+// finite or below 1, flags[1]: more than kMatKeys values), then the material
+// bytes from the table put in order of first appearance (launch_mat_ids;
+// dense: 1/eps_r per cell into inv_eps and id 0).
+constexpr int kMatKeys = 128;
+constexpr uint32_t kNoKey = 0xffffffffu;
+void launch_mat_keys(const float* eps, int64_t N, uint32_t* keys, uint32_t* first, int* flags,
+                     cudaStream_t s);
+void launch_mat_ids(const float* eps, const uint8_t* gain, int64_t N, const uint32_t* keys, int n,
+                    bool dense, bool gain_on, uint8_t* mat, float* inv_eps, cudaStream_t s);
 void launch_energy(const DevFields& f, int64_t ncell, const float* lut_eps, double* partial,
                    int nparts, int* nonfinite, double* out, cudaStream_t s);
 
@@ -342,10 +357,12 @@ struct mb_ctx {
     // material
     bool have_material = false;
     bool dense_eps = false;
-    std::vector<uint8_t> h_mat;        // material byte per cell (bit 7: gain; N0 read-out)
-    std::vector<uint8_t> h_mat_next;   // mb_set_material's work buffer (swapped in on success)
-    std::unique_ptr<uint32_t[]> h_glist;   // mb_set_material's gain-list buffer
-    size_t h_glist_cap = 0;
+    // mb_set_material's device scratch: the uploaded eps_r map and gain mask
+    // (5 bytes per cell), the table of distinct values and two flags
+    uint8_t* d_upload = nullptr;
+    size_t upload_bytes = 0;
+    uint32_t* d_keys = nullptr;
+    size_t keys_bytes = 0;
     std::vector<float> h_lut_eps;      // eps_r per material id
     int n_lut = 128;                   // entries of the table (128: unknown or dense)
     float h_lut_ie[2] = {1.0f, 1.0f};  // 1/eps_r of ids 0 and 1

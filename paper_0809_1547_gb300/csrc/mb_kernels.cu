@@ -335,14 +335,140 @@ __global__ void __launch_bounds__(1024) k_gain_scatter(const uint8_t* mat, int64
     }
 }
 
-size_t gain_list_scratch(int64_t N) { return (size_t)((N + kGainChunk - 1) / kGainChunk); }
+// counts[nchunks] = the total (after the scan: the last chunk's first
+// position plus its count, kept aside before the scan overwrites it).
+__global__ void k_gain_total(uint32_t* counts, int nchunks) {
+    if (threadIdx.x == 0) counts[nchunks + 1] = counts[nchunks - 1];
+}
+__global__ void k_gain_total2(uint32_t* counts, int nchunks) {
+    if (threadIdx.x == 0) counts[nchunks] = counts[nchunks - 1] + counts[nchunks + 1];
+}
 
-void launch_gain_list(const uint8_t* mat, int64_t N, uint32_t* scratch, uint32_t* list, cudaStream_t s) {
-    const int nchunks = (int)gain_list_scratch(N);
+static int gain_chunks(int64_t N) { return (int)((N + kGainChunk - 1) / kGainChunk); }
+
+size_t gain_list_scratch(int64_t N) { return (size_t)gain_chunks(N) + 2; }
+
+void launch_gain_count(const uint8_t* mat, int64_t N, uint32_t* scratch, cudaStream_t s) {
+    const int nchunks = gain_chunks(N);
     if (nchunks == 0) return;
     k_gain_count<<<nchunks, 1024, 0, s>>>(mat, N, scratch);
+    k_gain_total<<<1, 32, 0, s>>>(scratch, nchunks);
     k_gain_scan<<<1, 1024, 0, s>>>(scratch, nchunks);
+    k_gain_total2<<<1, 32, 0, s>>>(scratch, nchunks);
+}
+
+void launch_gain_scatter(const uint8_t* mat, int64_t N, const uint32_t* scratch, uint32_t* list,
+                         cudaStream_t s) {
+    const int nchunks = gain_chunks(N);
+    if (nchunks == 0) return;
     k_gain_scatter<<<nchunks, 1024, 0, s>>>(mat, N, scratch, list);
+}
+
+// ------------------------------------------------------------ material map
+// The eps_r map's distinct values (bit patterns) into a table of kMatKeys
+// entries by compare-and-swap on the first free slot, so the table fills as
+// a prefix, with the first cell holding each value (atomic minimum);
+// flags[0] is set by a value not finite or below 1, flags[1] by a value that
+// finds the table full.  Each warp walks its own contiguous stretch of the
+// map 32 cells at a time; of the lanes holding one value only the lowest
+// (the value's lowest cell of those 32) goes to the table, and only for a
+// value the warp has not recorded yet (a short list of the warp's values,
+// the same in every lane), so the table sees a few requests per warp.
+constexpr int kWarpSeen = 8;
+
+__device__ __forceinline__ bool eps_bits_valid(uint32_t b) {
+    return (b - 0x3f800000u) < 0x40000000u;   // 1 <= eps_r < inf, sign clear
+}
+
+__global__ void __launch_bounds__(256) k_mat_keys(const float* eps, int64_t N, uint32_t* keys,
+                                                  uint32_t* first, int* flags) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int64_t span = ((N + nwarps - 1) / nwarps + 31) / 32 * 32;
+    const int64_t c0 = w * span, c1 = min(N, c0 + span);
+    uint32_t seen[kWarpSeen];
+    int nseen = 0;
+    for (int64_t base = c0; base < c1; base += 32) {
+        const int64_t c = base + lane;
+        const bool in = c < c1;
+        const uint32_t b = in ? __float_as_uint(eps[c]) : kNoKey;
+        const bool ok = !in || eps_bits_valid(b);
+        if (!ok) flags[0] = 1;
+        const uint32_t bb = ok ? b : kNoKey;   // invalid and absent lanes take no part
+        const unsigned same = __match_any_sync(full, bb);
+        const bool leader = bb != kNoKey && lane == __ffs(same) - 1;
+        bool known = false;
+        for (int q = 0; q < nseen; ++q) known |= seen[q] == bb;
+        const bool ask = leader && !known;
+        if (ask) {
+            int at = -1;
+            for (int q = 0; q < kMatKeys && at < 0; ++q) {
+                uint32_t k = *reinterpret_cast<volatile uint32_t*>(keys + q);
+                if (k == kNoKey) {
+                    const uint32_t old = atomicCAS(keys + q, kNoKey, bb);
+                    k = old == kNoKey ? bb : old;
+                }
+                if (k == bb) at = q;
+            }
+            if (at < 0) flags[1] = 1;
+            else atomicMin(first + at, (uint32_t)c);
+        }
+        // the values just recorded join the warp's list (in every lane)
+        unsigned fresh = __ballot_sync(full, ask);
+        while (fresh) {
+            const int src = __ffs(fresh) - 1;
+            fresh &= fresh - 1;
+            const uint32_t v = __shfl_sync(full, bb, src);
+            if (nseen < kWarpSeen) seen[nseen++] = v;
+        }
+    }
+}
+
+// The material bytes from the (sorted) table: the cell's id in keys[0, n)
+// (0 for a dense map, whose 1/eps_r goes per cell into inv_eps) and bit 7 for
+// a gain cell.
+__global__ void __launch_bounds__(256) k_mat_ids(const float* eps, const uint8_t* gain, int64_t N,
+                                                 const uint32_t* keys, int n, int dense, int gain_on,
+                                                 uint8_t* mat, float* inv_eps) {
+    __shared__ uint32_t sk[kMatKeys];
+    for (int q = threadIdx.x; q < kMatKeys; q += blockDim.x) sk[q] = q < n ? keys[q] : kNoKey;
+    __syncthreads();
+    uint32_t last = kNoKey;
+    uint8_t last_id = 0;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < N;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const float v = eps[c];
+        uint8_t id = 0;
+        if (dense) {
+            inv_eps[c] = (float)(1.0 / (double)v);
+        } else {
+            const uint32_t b = __float_as_uint(v);
+            if (b == last) {
+                id = last_id;
+            } else {
+                for (int q = 0; q < n; ++q)
+                    if (sk[q] == b) {
+                        id = (uint8_t)q;
+                        break;
+                    }
+                last = b;
+                last_id = id;
+            }
+        }
+        mat[c] = (uint8_t)(id | ((gain_on && gain[c] != 0) ? 0x80 : 0x00));
+    }
+}
+
+void launch_mat_keys(const float* eps, int64_t N, uint32_t* keys, uint32_t* first, int* flags,
+                     cudaStream_t s) {
+    k_mat_keys<<<1216, 256, 0, s>>>(eps, N, keys, first, flags);
+}
+
+void launch_mat_ids(const float* eps, const uint8_t* gain, int64_t N, const uint32_t* keys, int n,
+                    bool dense, bool gain_on, uint8_t* mat, float* inv_eps, cudaStream_t s) {
+    k_mat_ids<<<1216, 256, 0, s>>>(eps, gain, N, keys, n, dense ? 1 : 0, gain_on ? 1 : 0, mat, inv_eps);
 }
 
 void launch_flux_sum(const double* slots, double* out, double scale, cudaStream_t s) {

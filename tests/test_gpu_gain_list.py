@@ -1,8 +1,10 @@
-"""The gain-cell list mb_set_material builds on the device (chunked counts,
-an ordered scan, an ordered scatter) against the host material map's list
-(mb_material_map, a separate implementation): equal, in increasing order,
+"""The material bytes and the gain-cell list mb_set_material builds on the
+device (distinct values by compare-and-swap, ids by first appearance;
+chunked counts, an ordered scan, an ordered scatter) against the host
+statement of the map (mb_material_map, a separate implementation): equal,
 on grids whose cell counts end inside a 65536-cell chunk, span several
-chunks, or fit in one; empty with the gain off."""
+chunks, or fit in one, with two, six or more than 128 distinct values;
+empty lists with the gain off."""
 import numpy as np
 import pytest
 
@@ -25,7 +27,8 @@ def test_device_gain_list_equals_the_host_map(grid, seed):
     sim = MBSimulation(grid, 20e-9, inputs.courant_dt(20e-9), mb_default_params(npml=4))
     sim.set_material(eps, gain, 3e24, 1e13)
     dev = sim.gain_list()
-    _, host, _, _ = mb_material_map(eps, gain, True, 16)
+    mat_h, host, _, _ = mb_material_map(eps, gain, True, 16)
+    assert np.array_equal(sim.material().ravel(), np.asarray(mat_h).ravel())
     assert dev.dtype == np.uint32 and dev.size == int(np.count_nonzero(gain.ravel()))
     assert np.array_equal(dev, np.asarray(host, dtype=np.uint32))
     assert np.all(np.diff(dev.astype(np.int64)) > 0)
@@ -37,4 +40,24 @@ def test_device_gain_list_equals_the_host_map(grid, seed):
     sim.set_material(eps, gain2, 3e24, 1e13)
     _, host2, _, _ = mb_material_map(eps, gain2, True, 16)
     assert np.array_equal(sim.gain_list(), np.asarray(host2, dtype=np.uint32))
+    sim.close()
+
+
+@pytest.mark.parametrize("n_values", [6, 200])
+def test_device_material_bytes_with_many_values(n_values):
+    """Six values in runs across the grid, or more than 128 (a dense map):
+    the device bytes equal the host map's."""
+    from paper_0809_1547_gb300.binding import MBSimulation, mb_default_params, mb_material_map
+    grid = (40, 36, 30)
+    eps, gain = inputs.random_small(grid, seed=12, npml=4)
+    rng = np.random.default_rng(n_values)
+    vals = (1.0 + rng.random(n_values) * 9.0).astype(np.float32)
+    runs = rng.integers(0, n_values, size=eps.size // 37 + 1)
+    eps = np.repeat(vals[runs], 37)[:eps.size].reshape(eps.shape).astype(np.float32)
+    sim = MBSimulation(grid, 20e-9, inputs.courant_dt(20e-9), mb_default_params(npml=4))
+    sim.set_material(eps, gain, 3e24, 1e13)
+    mat_h, host, values, dense = mb_material_map(eps, gain, True, 16)
+    assert bool(dense) == (n_values > 128)
+    assert np.array_equal(sim.material().ravel(), np.asarray(mat_h).ravel())
+    assert np.array_equal(sim.gain_list(), np.asarray(host, dtype=np.uint32))
     sim.close()
