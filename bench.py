@@ -470,8 +470,11 @@ def bench_ours(args):
     # (host -> device), K steps each followed by a read of the six face
     # energies (device -> host, 48 bytes into pinned memory, consumed on the
     # host one step later while the next step runs), the final spectrum read.
-    eps_h = np.ascontiguousarray(w.eps, dtype=np.float32)
-    gain_h = np.ascontiguousarray(w.gain, dtype=np.uint8)
+    # the host buffers are page-locked (pinned), as a user streaming inputs
+    # to the GPU would hold them
+    eps_pin = torch.from_numpy(np.ascontiguousarray(w.eps, dtype=np.float32)).pin_memory()
+    gain_pin = torch.from_numpy(np.ascontiguousarray(w.gain, dtype=np.uint8)).pin_memory()
+    eps_h, gain_h = eps_pin.numpy(), gain_pin.numpy()
     sim2 = MBSimulation(w.grid, w.dx, w.dt, mb_default_params(npml=w.npml), stream=stream.cuda_stream)
     pid = sim2.add_point_probe(w.extra.get("probe", (160, 160, 160)), 128, 475e-9, 705e-9)
     sim2.add_face_probes(8, 4, 128, 475e-9, 705e-9)
@@ -890,16 +893,21 @@ def bench_passive(w, stream, steps: int, warmup: int):
 
 # ---------------------------------------------------------------- adjoint
 
-def bench_adjoint(stream, warmup: int, autotune: bool = True):
+def bench_adjoint(stream, warmup: int, autotune: bool = True, steps: int = 0, ckpt: int = 0):
     """Gradient of the energy through the +z face w.r.t. eps (per cell) and the
     pump on the 96^3 workload (225 spheres, 45 % fill, gain in the voids,
     fixed pump and noise seed), 4000 steps with checkpoints every 200 steps,
-    against the plain step of the same realization over the same steps."""
+    against the plain step of the same realization over the same steps
+    (steps, ckpt > 0: a shorter case of the same workload, for profiling)."""
+    import copy
     import torch
     from paper_0809_1547_gb300 import inputs
     from paper_0809_1547_gb300.binding import MBSimulation, mb_default_params
     w = inputs.workload_adjoint_96()
-    K = w.extra["ckpt_every"]
+    K = ckpt if ckpt > 0 else w.extra["ckpt_every"]
+    if steps > 0:
+        w = copy.copy(w)
+        w.steps = steps
     cells = w.ncell
 
     def make():
@@ -931,6 +939,9 @@ def bench_adjoint(stream, warmup: int, autotune: bool = True):
     p_.step(warmup)
     plain_ms, _ = timed(lambda: (p_.step(w.steps), p_.join_probes()))
     p_.close()
+    # one store slot per step of a segment: E, J, n1..n3 of every cell and two H planes
+    store_gb = (9 * cells + 2 * w.grid[0] * w.grid[1]) * 4 * (K + 1) / 1e9
+    state_mb = 16 * cells * 4 / 1e6
     v_adj = cells * w.steps / (adj_ms / 1e3) / 1e6
     v_plain = cells * w.steps / (plain_ms / 1e3) / 1e6
     return {"workload": f"{w.name}: {w.grid[0]}^3 (dx 20 nm, 8-cell CPML), {w.n_spheres} TiO2 spheres "
@@ -944,7 +955,7 @@ def bench_adjoint(stream, warmup: int, autotune: bool = True):
                                       "ms_per_step": round(plain_ms / w.steps, 5)},
             "ratio_vs_plain": round(v_adj / v_plain, 4),
             "objective_J": J, "grad_pump": gp,
-            "l2": "state (57 MB) below L2 size; segment store (8.5 GB) above"}
+            "l2": f"state ({state_mb:.0f} MB) below L2 size; segment store ({store_gb:.1f} GB) above"}
 
 
 # --------------------------------------------------------- reference arm
@@ -998,7 +1009,8 @@ def run_only(args):
         out = bench_batched(stream, args.batched_steps, args.warmup, args.batched_pump,
                             args.batched_seeds, autotune=not args.no_autotune, plain=False)
     elif args.only == "adjoint":
-        out = bench_adjoint(stream, args.warmup, autotune=not args.no_autotune)
+        out = bench_adjoint(stream, args.warmup, autotune=not args.no_autotune, steps=args.adj_steps,
+                            ckpt=args.adj_ckpt)
     elif args.only == "passive":
         out = bench_passive(rank_workload(0, 320), stream, max(50, args.steps // 3), args.warmup)
     elif args.only == "large":
@@ -1033,6 +1045,10 @@ def main():
                     help="run one leg alone and print its result (profiling)")
     ap.add_argument("--batched-pump", type=int, default=16, help="N_a levels of the ensemble")
     ap.add_argument("--batched-seeds", type=int, default=5, help="disorder seeds of the ensemble")
+    ap.add_argument("--adj-steps", type=int, default=0,
+                    help="--only adjoint: steps of the gradient call (default: the workload's 4000)")
+    ap.add_argument("--adj-ckpt", type=int, default=0,
+                    help="--only adjoint: checkpoint interval (default: the workload's 200)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="--only batched/adjoint: default launch shapes (no tuning launches)")
     ap.add_argument("--tune", default="",

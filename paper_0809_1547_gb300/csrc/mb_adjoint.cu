@@ -86,11 +86,12 @@ __device__ __forceinline__ unsigned block_slot() {
 
 // ------------------------------------------------------------------- R1
 // Pointwise part of the reverse of the step (x0 -> x1) at cell (i, j, k),
-// given lambda_E of x1 in l1x..l1z; every lane of the warp must call it
-// (valid false for lanes outside the grid).
+// given lambda_E of x1 in l1x..l1z; returns the cell's objective and pump
+// terms in obj, gw (zero for lanes outside the grid: valid false).
 __device__ __forceinline__ void adj_point_cell(const AdjArgs& a, int i, int j, int k, bool valid,
-                                               float l1x, float l1y, float l1z) {
-    float obj = 0.0f, gw = 0.0f;
+                                               float l1x, float l1y, float l1z, float& obj, float& gw) {
+    obj = 0.0f;
+    gw = 0.0f;
     if (valid) {
         const uint32_t N = a.g.ncell;
         const uint32_t c = (uint32_t)i + (uint32_t)a.g.nx * j + a.g.nxy * k;
@@ -210,9 +211,6 @@ __device__ __forceinline__ void adj_point_cell(const AdjArgs& a, int i, int j, i
         a.le[c + N] = l0y;
         a.le[c + 2 * N] = l0z;
     }
-    const unsigned slot = block_slot();
-    warp_acc(a.acc, obj, slot);
-    warp_acc(a.acc + kAccSlots, gw, slot);
 }
 
 __global__ void __launch_bounds__(256) k_adj_point(AdjArgs a) {
@@ -228,7 +226,11 @@ __global__ void __launch_bounds__(256) k_adj_point(AdjArgs a) {
         l1y = a.le[c + N];
         l1z = a.le[c + 2 * N];
     }
-    adj_point_cell(a, i, j, k, valid, l1x, l1y, l1z);
+    float obj, gw;
+    adj_point_cell(a, i, j, k, valid, l1x, l1y, l1z, obj, gw);
+    const unsigned slot = block_slot();
+    warp_acc(a.acc, obj, slot);
+    warp_acc(a.acc + kAccSlots, gw, slot);
 }
 
 // ------------------------------------------------------------------- R2
@@ -287,13 +289,32 @@ __device__ __forceinline__ WCoef w_coef(const AdjArgs& a, int i, int j, int k) {
     return w;
 }
 
+// The coefficients of an interior cell (no CPML memory): S mu with the curl's signs.
+__device__ __forceinline__ WCoef w_plain(float S, float ux, float uy, float uz) {
+    WCoef w;
+    w.xy = S * ux;
+    w.xz = -S * ux;
+    w.yz = S * uy;
+    w.yx = -S * uy;
+    w.zx = S * uz;
+    w.zy = -S * uz;
+    return w;
+}
+
 __global__ void __launch_bounds__(256) k_adj_h(AdjArgs a) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k = blockIdx.z;
-    if (i >= a.g.nx || j >= a.g.ny) return;
+    const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz, L = a.L;
+    const bool valid = i < nx && j < ny;
+    // a warp none of whose cells or +1 neighbours lies in a CPML slab takes
+    // the coefficients without the memories (the same values)
+    const bool pml = __any_sync(0xffffffffu, valid && (in_slab(i, nx, L) || in_slab(i + 1, nx, L) ||
+                                                       in_slab(j, ny, L) || in_slab(j + 1, ny, L) ||
+                                                       in_slab(k, nz, L) || in_slab(k + 1, nz, L)));
+    if (!valid) return;
     const uint32_t N = a.g.ncell;
-    const uint32_t c = (uint32_t)i + (uint32_t)a.g.nx * j + a.g.nxy * k;
+    const uint32_t c = (uint32_t)i + (uint32_t)nx * j + a.g.nxy * k;
     float hx = a.lh[c], hy = a.lh[c + N], hz = a.lh[c + 2 * N];
     // objective: H sites of the layer k = zp - 1
     if (k + 1 == a.zp && i >= a.rx0 && i < a.rx1 && j >= a.ry0 && j < a.ry1) {
@@ -301,18 +322,38 @@ __global__ void __launch_bounds__(256) k_adj_h(AdjArgs a) {
         hy += 0.5f * (__ldcs(a.x0.ex + cu) + __ldcs(a.x1.ex + cu));
         hx -= 0.5f * (__ldcs(a.x0.ey + cu) + __ldcs(a.x1.ey + cu));
     }
-    const WCoef w0 = w_coef(a, i, j, k);
-    const WCoef wi = w_coef(a, i + 1, j, k);
-    const WCoef wj = w_coef(a, i, j + 1, k);
-    const WCoef wk = w_coef(a, i, j, k + 1);
+    WCoef w0, wi, wj, wk;
+    if (!pml) {
+        const float S = a.S;
+        w0 = w_plain(S, a.mu[c], a.mu[c + N], a.mu[c + 2 * N]);
+        wi = wj = wk = WCoef{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (i + 1 < nx) {
+            wi.yx = -S * a.mu[c + 1 + N];
+            wi.zx = S * a.mu[c + 1 + 2 * N];
+        }
+        if (j + 1 < ny) {
+            wj.xy = S * a.mu[c + nx];
+            wj.zy = -S * a.mu[c + nx + 2 * N];
+        }
+        if (k + 1 < nz) {
+            wk.xz = -S * a.mu[c + a.g.nxy];
+            wk.yz = S * a.mu[c + a.g.nxy + N];
+        }
+    } else {
+        w0 = w_coef(a, i, j, k);
+        wi = w_coef(a, i + 1, j, k);
+        wj = w_coef(a, i, j + 1, k);
+        wk = w_coef(a, i, j, k + 1);
+    }
     hz += (w0.xy - wj.xy) + (w0.yx - wi.yx);
     hy += (w0.xz - wk.xz) + (w0.zx - wi.zx);
     hx += (w0.yz - wk.yz) + (w0.zy - wj.zy);
     a.lh[c] = hx;
     a.lh[c + N] = hy;
     a.lh[c + 2 * N] = hz;
+    if (!pml) return;
     // psi_H adjoint memories: lambda_tot = b lambda_prev - sign S lambda_H
-    const int L = a.L, L2 = 2 * L, nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
+    const int L2 = 2 * L;
     const float S = a.S;
     if (in_slab(i, nx, L)) {
         const uint32_t plane = (uint32_t)nz * ny * L2;
@@ -372,15 +413,56 @@ __device__ __forceinline__ WCoef v_coef(const AdjArgs& a, int i, int j, int k) {
     return v;
 }
 
+// The coefficients of an interior cell (no CPML memory): -S lambda_H with the curl's signs.
+__device__ __forceinline__ WCoef v_plain(float S, float hx, float hy, float hz) {
+    WCoef v;
+    v.xy = -S * hx;
+    v.xz = S * hx;
+    v.yz = -S * hy;
+    v.yx = S * hy;
+    v.zx = -S * hz;
+    v.zy = S * hz;
+    return v;
+}
+
+// The lane's cell or one of its -1 neighbours lies in a CPML slab.
+__device__ __forceinline__ bool near_slab_lo(const AdjArgs& a, int i, int j, int k) {
+    const int L = a.L;
+    return in_slab(i, a.g.nx, L) || in_slab(i - 1, a.g.nx, L) || in_slab(j, a.g.ny, L) ||
+           in_slab(j - 1, a.g.ny, L) || in_slab(k, a.g.nz, L) || in_slab(k - 1, a.g.nz, L);
+}
+
 // lambda_E of x^n at cell (i, j, k): the partial value left in le by R1 plus
 // the transposed H update (backward differences of the V coefficients).
-__device__ __forceinline__ void adj_e_gather(const AdjArgs& a, int i, int j, int k, uint32_t c,
+// pml false (the whole warp away from the CPML slabs): the coefficients
+// without the memories, the same values.
+__device__ __forceinline__ void adj_e_gather(const AdjArgs& a, int i, int j, int k, uint32_t c, bool pml,
                                              float& lx, float& ly, float& lz) {
     const uint32_t N = a.g.ncell;
-    const WCoef v0 = v_coef(a, i, j, k);
-    const WCoef vi = v_coef(a, i - 1, j, k);
-    const WCoef vj = v_coef(a, i, j - 1, k);
-    const WCoef vk = v_coef(a, i, j, k - 1);
+    WCoef v0, vi, vj, vk;
+    if (!pml) {
+        const float S = a.S;
+        const uint32_t nx = a.g.nx, nxy = a.g.nxy;
+        v0 = v_plain(S, a.lh[c], a.lh[c + N], a.lh[c + 2 * N]);
+        vi = vj = vk = WCoef{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (i >= 1) {
+            vi.zx = -S * a.lh[c - 1 + 2 * N];
+            vi.yx = S * a.lh[c - 1 + N];
+        }
+        if (j >= 1) {
+            vj.zy = S * a.lh[c - nx + 2 * N];
+            vj.xy = -S * a.lh[c - nx];
+        }
+        if (k >= 1) {
+            vk.yz = -S * a.lh[c - nxy + N];
+            vk.xz = S * a.lh[c - nxy];
+        }
+    } else {
+        v0 = v_coef(a, i, j, k);
+        vi = v_coef(a, i - 1, j, k);
+        vj = v_coef(a, i, j - 1, k);
+        vk = v_coef(a, i, j, k - 1);
+    }
     lx = a.le[c] + ((vk.yz - v0.yz) + (vj.zy - v0.zy));
     ly = a.le[c + N] + ((vk.xz - v0.xz) + (vi.zx - v0.zx));
     lz = a.le[c + 2 * N] + ((vj.xy - v0.xy) + (vi.yx - v0.yx));
@@ -394,7 +476,7 @@ __global__ void __launch_bounds__(256) k_adj_e(AdjArgs a) {
     const uint32_t N = a.g.ncell;
     const uint32_t c = (uint32_t)i + (uint32_t)a.g.nx * j + a.g.nxy * k;
     float lx, ly, lz;
-    adj_e_gather(a, i, j, k, c, lx, ly, lz);
+    adj_e_gather(a, i, j, k, c, true, lx, ly, lz);
     a.le[c] = lx;
     a.le[c + N] = ly;
     a.le[c + 2 * N] = lz;
@@ -402,15 +484,22 @@ __global__ void __launch_bounds__(256) k_adj_e(AdjArgs a) {
 
 // R3 of step n fused with R1 of step n - 1 (a's x0, x1, n_ptr describe
 // step n - 1): lambda_E of x^n stays in registers.  R3 reads lambda_H and the
-// psi_H memories of neighbours, which R1 does not write.
-__global__ void __launch_bounds__(256) k_adj_e_point(AdjArgs a) {
+// psi_H memories of neighbours, which R1 does not write.  Bounded to 40
+// registers (6 blocks per SM, a few spilled bytes): the launch is latency
+// bound, and the added warps gain more than the spills cost.
+__global__ void __launch_bounds__(256, 6) k_adj_e_point(AdjArgs a) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k = blockIdx.z;
     const bool valid = i < a.g.nx && j < a.g.ny;
+    const bool pml = __any_sync(0xffffffffu, valid && near_slab_lo(a, i, j, k));
     float lx = 0.0f, ly = 0.0f, lz = 0.0f;
-    if (valid) adj_e_gather(a, i, j, k, (uint32_t)i + (uint32_t)a.g.nx * j + a.g.nxy * k, lx, ly, lz);
-    adj_point_cell(a, i, j, k, valid, lx, ly, lz);
+    if (valid) adj_e_gather(a, i, j, k, (uint32_t)i + (uint32_t)a.g.nx * j + a.g.nxy * k, pml, lx, ly, lz);
+    float obj, gw;
+    adj_point_cell(a, i, j, k, valid, lx, ly, lz, obj, gw);
+    const unsigned slot = block_slot();
+    warp_acc(a.acc, obj, slot);
+    warp_acc(a.acc + kAccSlots, gw, slot);
 }
 
 // Store slot of one step: E (arrays 0..2) and J, n1..n3 (arrays 9..14) of
