@@ -255,18 +255,46 @@ __global__ void k_flux_sum(const double* slots, double* out, double scale) {
 
 // ------------------------------------------------------------ gain-cell list
 // Three passes over chunks of kGainChunk cells: the gain cells of each chunk
-// counted (warp ballots), the counts turned into each chunk's first list
-// position (one block, in order), then each chunk's gain cells written in
-// increasing order (per 1024-cell tile: ballots, the warps' counts summed
-// in shared memory, every gain cell placed after those before it).
-constexpr int kGainChunk = 1 << 16;
+// counted, the counts turned into each chunk's first list position (one
+// block, in order), then each chunk's gain cells written in increasing
+// order.  A block of kGainThreads threads takes one chunk, each thread 16
+// consecutive material bytes (one uint4; a chunk starts 16-byte aligned); in
+// the scatter a block-wide prefix sum of the threads' counts places every
+// gain cell after those before it in shared memory, and the chunk's list is
+// then copied out whole (coalesced stores).
+constexpr int kGainVec = 16;   // material bytes per thread
+constexpr int kGainThreads = 512;
+constexpr int kGainChunk = kGainVec * kGainThreads;
 
-__global__ void __launch_bounds__(1024) k_gain_count(const uint8_t* mat, int64_t N, uint32_t* counts) {
+// Bit 7 of each of the 16 bytes in v (the gain flag): bit e of the result
+// for byte e.
+__device__ __forceinline__ unsigned gain_bits16(uint4 v) {
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+    unsigned m = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const uint32_t g = (w[q] >> 7) & 0x01010101u;   // byte e -> bit 8 e
+        m |= ((g | (g >> 7) | (g >> 14) | (g >> 21)) & 0xfu) << (4 * q);
+    }
+    return m;
+}
+
+// The gain bits of the 16 cells [c, c + 16) (cells at or past c1 read as
+// not gain).
+__device__ __forceinline__ unsigned gain_bits_at(const uint8_t* mat, int64_t c, int64_t c1) {
+    if (c + kGainVec <= c1) return gain_bits16(*reinterpret_cast<const uint4*>(mat + c));
+    unsigned m = 0;
+    for (int e = 0; e < kGainVec && c + e < c1; ++e) m |= (unsigned)(mat[c + e] >> 7) << e;
+    return m;
+}
+
+__global__ void __launch_bounds__(kGainThreads) k_gain_count(const uint8_t* mat, int64_t N, uint32_t* counts) {
     __shared__ uint32_t wsum[32];
     const int64_t c0 = (int64_t)blockIdx.x * kGainChunk;
     const int64_t c1 = min(N, c0 + kGainChunk);
     uint32_t n = 0;
-    for (int64_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) n += (mat[c] >> 7);
+    for (int64_t c = c0 + (int64_t)kGainVec * threadIdx.x; c < c1; c += (int64_t)kGainVec * blockDim.x)
+        n += __popc(gain_bits_at(mat, c, c1));
     for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
     if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = n;
     __syncthreads();
@@ -311,28 +339,41 @@ __global__ void __launch_bounds__(1024) k_gain_scan(uint32_t* counts, int nchunk
     }
 }
 
-__global__ void __launch_bounds__(1024) k_gain_scatter(const uint8_t* mat, int64_t N, const uint32_t* first,
-                                                       uint32_t* list) {
+__global__ void __launch_bounds__(kGainThreads) k_gain_scatter(const uint8_t* mat, int64_t N,
+                                                               const uint32_t* first, uint32_t* list) {
     __shared__ uint32_t wsum[32];
+    __shared__ uint32_t cells[kGainChunk];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int64_t c0 = (int64_t)blockIdx.x * kGainChunk;
     const int64_t c1 = min(N, c0 + kGainChunk);
-    uint32_t pos = first[blockIdx.x];
-    for (int64_t base = c0; base < c1; base += blockDim.x) {
-        const int64_t c = base + threadIdx.x;
-        const bool g = c < c1 && (mat[c] & 0x80);
-        const unsigned b = __ballot_sync(0xffffffffu, g);
-        if (lane == 0) wsum[warp] = __popc(b);
-        __syncthreads();
-        uint32_t before = 0, total = 0;
-        for (int w = 0; w < nw; ++w) {
-            before += w < warp ? wsum[w] : 0u;
-            total += wsum[w];
-        }
-        if (g) list[pos + before + __popc(b & ((1u << lane) - 1u))] = (uint32_t)c;
-        pos += total;
-        __syncthreads();
+    const int64_t c = c0 + (int64_t)kGainVec * threadIdx.x;
+    unsigned m = c < c1 ? gain_bits_at(mat, c, c1) : 0u;
+    const uint32_t cnt = __popc(m);
+    uint32_t x = cnt;   // inclusive scan of the counts within the warp
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
     }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t z = lane < nw ? wsum[lane] : 0u;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, z, o);
+            if (lane >= o) z += y;
+        }
+        wsum[lane] = z;   // inclusive prefix of the warp totals
+    }
+    __syncthreads();
+    uint32_t at = (warp > 0 ? wsum[warp - 1] : 0u) + (x - cnt);
+    while (m) {
+        const int e = __ffs(m) - 1;
+        m &= m - 1;
+        cells[at++] = (uint32_t)(c + e);
+    }
+    __syncthreads();
+    const uint32_t total = wsum[nw - 1], pos = first[blockIdx.x];
+    for (uint32_t q = threadIdx.x; q < total; q += blockDim.x) list[pos + q] = cells[q];
 }
 
 // counts[nchunks] = the total (after the scan: the last chunk's first
@@ -351,7 +392,7 @@ size_t gain_list_scratch(int64_t N) { return (size_t)gain_chunks(N) + 2; }
 void launch_gain_count(const uint8_t* mat, int64_t N, uint32_t* scratch, cudaStream_t s) {
     const int nchunks = gain_chunks(N);
     if (nchunks == 0) return;
-    k_gain_count<<<nchunks, 1024, 0, s>>>(mat, N, scratch);
+    k_gain_count<<<nchunks, kGainThreads, 0, s>>>(mat, N, scratch);
     k_gain_total<<<1, 32, 0, s>>>(scratch, nchunks);
     k_gain_scan<<<1, 1024, 0, s>>>(scratch, nchunks);
     k_gain_total2<<<1, 32, 0, s>>>(scratch, nchunks);
@@ -361,7 +402,7 @@ void launch_gain_scatter(const uint8_t* mat, int64_t N, const uint32_t* scratch,
                          cudaStream_t s) {
     const int nchunks = gain_chunks(N);
     if (nchunks == 0) return;
-    k_gain_scatter<<<nchunks, 1024, 0, s>>>(mat, N, scratch, list);
+    k_gain_scatter<<<nchunks, kGainThreads, 0, s>>>(mat, N, scratch, list);
 }
 
 // ------------------------------------------------------------ material map
@@ -370,11 +411,13 @@ void launch_gain_scatter(const uint8_t* mat, int64_t N, const uint32_t* scratch,
 // a prefix, with the first cell holding each value (atomic minimum);
 // flags[0] is set by a value not finite or below 1, flags[1] by a value that
 // finds the table full.  Each warp walks its own contiguous stretch of the
-// map 32 cells at a time; of the lanes holding one value only the lowest
-// (the value's lowest cell of those 32) goes to the table, and only for a
-// value the warp has not recorded yet (a short list of the warp's values,
-// the same in every lane), so the table sees a few requests per warp.
+// map 128 cells at a time (four coalesced loads issued together, then taken
+// 32 cells at a time in cell order); of the lanes holding one value only the
+// lowest (the value's lowest cell of those 32) goes to the table, and only
+// for a value the warp has not recorded yet (a short list of the warp's
+// values, the same in every lane), so the table sees a few requests per warp.
 constexpr int kWarpSeen = 8;
+constexpr int kKeysUnroll = 4;
 
 __device__ __forceinline__ bool eps_bits_valid(uint32_t b) {
     return (b - 0x3f800000u) < 0x40000000u;   // 1 <= eps_r < inf, sign clear
@@ -386,49 +429,91 @@ __global__ void __launch_bounds__(256) k_mat_keys(const float* eps, int64_t N, u
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int64_t span = ((N + nwarps - 1) / nwarps + 31) / 32 * 32;
+    constexpr int kStep = 32 * kKeysUnroll;
+    const int64_t span = ((N + nwarps - 1) / nwarps + kStep - 1) / kStep * kStep;
     const int64_t c0 = w * span, c1 = min(N, c0 + span);
     uint32_t seen[kWarpSeen];
     int nseen = 0;
-    for (int64_t base = c0; base < c1; base += 32) {
-        const int64_t c = base + lane;
-        const bool in = c < c1;
-        const uint32_t b = in ? __float_as_uint(eps[c]) : kNoKey;
-        const bool ok = !in || eps_bits_valid(b);
-        if (!ok) flags[0] = 1;
-        const uint32_t bb = ok ? b : kNoKey;   // invalid and absent lanes take no part
-        const unsigned same = __match_any_sync(full, bb);
-        const bool leader = bb != kNoKey && lane == __ffs(same) - 1;
-        bool known = false;
-        for (int q = 0; q < nseen; ++q) known |= seen[q] == bb;
-        const bool ask = leader && !known;
-        if (ask) {
-            int at = -1;
-            for (int q = 0; q < kMatKeys && at < 0; ++q) {
-                uint32_t k = *reinterpret_cast<volatile uint32_t*>(keys + q);
-                if (k == kNoKey) {
-                    const uint32_t old = atomicCAS(keys + q, kNoKey, bb);
-                    k = old == kNoKey ? bb : old;
-                }
-                if (k == bb) at = q;
-            }
-            if (at < 0) flags[1] = 1;
-            else atomicMin(first + at, (uint32_t)c);
+    for (int64_t base = c0; base < c1; base += kStep) {
+        uint32_t bv[kKeysUnroll];
+#pragma unroll
+        for (int u = 0; u < kKeysUnroll; ++u) {
+            const int64_t c = base + 32 * u + lane;
+            bv[u] = c < c1 ? __float_as_uint(__ldcs(eps + c)) : kNoKey;
         }
-        // the values just recorded join the warp's list (in every lane)
-        unsigned fresh = __ballot_sync(full, ask);
-        while (fresh) {
-            const int src = __ffs(fresh) - 1;
-            fresh &= fresh - 1;
-            const uint32_t v = __shfl_sync(full, bb, src);
-            if (nseen < kWarpSeen) seen[nseen++] = v;
+#pragma unroll
+        for (int u = 0; u < kKeysUnroll; ++u) {
+            const int64_t c = base + 32 * u + lane;
+            const bool in = c < c1;
+            const uint32_t b = bv[u];
+            const bool ok = !in || eps_bits_valid(b);
+            if (!ok) flags[0] = 1;
+            const uint32_t bb = ok ? b : kNoKey;   // invalid and absent lanes take no part
+            // 32 cells of one value the warp has recorded already (the
+            // inside of a sphere or a void): nothing to do
+            const uint32_t b0 = __shfl_sync(full, bb, 0);
+            if (__all_sync(full, bb == b0)) {
+                bool have = b0 == kNoKey;
+                for (int q = 0; q < nseen; ++q) have |= seen[q] == b0;
+                if (have) continue;
+            }
+            const unsigned same = __match_any_sync(full, bb);
+            const bool leader = bb != kNoKey && lane == __ffs(same) - 1;
+            bool known = false;
+            for (int q = 0; q < nseen; ++q) known |= seen[q] == bb;
+            const bool ask = leader && !known;
+            if (ask) {
+                int at = -1;
+                for (int q = 0; q < kMatKeys && at < 0; ++q) {
+                    uint32_t k = *reinterpret_cast<volatile uint32_t*>(keys + q);
+                    if (k == kNoKey) {
+                        const uint32_t old = atomicCAS(keys + q, kNoKey, bb);
+                        k = old == kNoKey ? bb : old;
+                    }
+                    if (k == bb) at = q;
+                }
+                if (at < 0) flags[1] = 1;
+                else atomicMin(first + at, (uint32_t)c);
+            }
+            // the values just recorded join the warp's list (in every lane)
+            unsigned fresh = __ballot_sync(full, ask);
+            while (fresh) {
+                const int src = __ffs(fresh) - 1;
+                fresh &= fresh - 1;
+                const uint32_t v = __shfl_sync(full, bb, src);
+                if (nseen < kWarpSeen) seen[nseen++] = v;
+            }
         }
     }
 }
 
-// The material bytes from the (sorted) table: the cell's id in keys[0, n)
-// (0 for a dense map, whose 1/eps_r goes per cell into inv_eps) and bit 7 for
-// a gain cell.
+// The material byte of one cell from the (sorted) table: its id in keys[0,
+// n) (0 for a dense map, whose 1/eps_r goes per cell into inv_eps) and bit 7
+// for a gain cell; last / last_id remember the previous lookup (runs of one
+// value skip the table search).
+__device__ __forceinline__ uint8_t mat_byte(float v, uint8_t g, const uint32_t* sk, int n, int dense,
+                                            int gain_on, uint32_t& last, uint8_t& last_id) {
+    uint8_t id = 0;
+    if (!dense) {
+        const uint32_t b = __float_as_uint(v);
+        if (b == last) {
+            id = last_id;
+        } else {
+            for (int q = 0; q < n; ++q)
+                if (sk[q] == b) {
+                    id = (uint8_t)q;
+                    break;
+                }
+            last = b;
+            last_id = id;
+        }
+    }
+    return (uint8_t)(id | ((gain_on && g != 0) ? 0x80 : 0x00));
+}
+
+// The material bytes of the map, four cells per thread and pass (the eps_r
+// map, the gain mask and the material bytes start 16- / 4-byte aligned; the
+// last N % 4 cells one at a time).
 __global__ void __launch_bounds__(256) k_mat_ids(const float* eps, const uint8_t* gain, int64_t N,
                                                  const uint32_t* keys, int n, int dense, int gain_on,
                                                  uint8_t* mat, float* inv_eps) {
@@ -437,27 +522,26 @@ __global__ void __launch_bounds__(256) k_mat_ids(const float* eps, const uint8_t
     __syncthreads();
     uint32_t last = kNoKey;
     uint8_t last_id = 0;
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < N;
-         c += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t n4 = N / 4;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n4; t += stride) {
+        const float4 v = __ldcs(reinterpret_cast<const float4*>(eps) + t);
+        const uchar4 g = __ldcs(reinterpret_cast<const uchar4*>(gain) + t);
+        if (dense)
+            reinterpret_cast<float4*>(inv_eps)[t] =
+                make_float4((float)(1.0 / (double)v.x), (float)(1.0 / (double)v.y),
+                            (float)(1.0 / (double)v.z), (float)(1.0 / (double)v.w));
+        uchar4 m;
+        m.x = mat_byte(v.x, g.x, sk, n, dense, gain_on, last, last_id);
+        m.y = mat_byte(v.y, g.y, sk, n, dense, gain_on, last, last_id);
+        m.z = mat_byte(v.z, g.z, sk, n, dense, gain_on, last, last_id);
+        m.w = mat_byte(v.w, g.w, sk, n, dense, gain_on, last, last_id);
+        reinterpret_cast<uchar4*>(mat)[t] = m;
+    }
+    for (int64_t c = 4 * n4 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < N; c += stride) {
         const float v = eps[c];
-        uint8_t id = 0;
-        if (dense) {
-            inv_eps[c] = (float)(1.0 / (double)v);
-        } else {
-            const uint32_t b = __float_as_uint(v);
-            if (b == last) {
-                id = last_id;
-            } else {
-                for (int q = 0; q < n; ++q)
-                    if (sk[q] == b) {
-                        id = (uint8_t)q;
-                        break;
-                    }
-                last = b;
-                last_id = id;
-            }
-        }
-        mat[c] = (uint8_t)(id | ((gain_on && gain[c] != 0) ? 0x80 : 0x00));
+        if (dense) inv_eps[c] = (float)(1.0 / (double)v);
+        mat[c] = mat_byte(v, gain[c], sk, n, dense, gain_on, last, last_id);
     }
 }
 
