@@ -2,9 +2,9 @@
 device (distinct values by compare-and-swap, ids by first appearance;
 chunked counts, an ordered scan, an ordered scatter) against the host
 statement of the map (mb_material_map, a separate implementation): equal,
-on grids whose cell counts end inside a 65536-cell chunk, span several
-chunks, or fit in one, with two, six or more than 128 distinct values;
-empty lists with the gain off."""
+on grids whose cell counts end inside an 8192-cell chunk, span several
+chunks, or fit in one, with two, six or more than 128 distinct values, and
+at the benchmarked 320^3 size; empty lists with the gain off."""
 import numpy as np
 import pytest
 
@@ -60,4 +60,21 @@ def test_device_material_bytes_with_many_values(n_values):
     assert bool(dense) == (n_values > 128)
     assert np.array_equal(sim.material().ravel(), np.asarray(mat_h).ravel())
     assert np.array_equal(sim.gain_list(), np.asarray(host, dtype=np.uint32))
+    sim.close()
+
+
+def test_device_map_at_full_size():
+    """The 320^3 packing the benchmark steps (32.8 M cells, 14.4 M gain
+    cells, 4000 chunks of the gain list): material bytes and gain-cell list
+    equal to the host map's, and the gain cells' count to the mask's."""
+    from paper_0809_1547_gb300.binding import MBSimulation, mb_default_params, mb_material_map
+    w = inputs.workload_paper_320()
+    sim = MBSimulation(w.grid, w.dx, w.dt, mb_default_params(npml=w.npml))
+    sim.set_material(w.eps, w.gain, w.N_a, w.pump)
+    mat_h, host, _, dense = mb_material_map(w.eps, w.gain, True, 16)
+    assert not dense
+    assert np.array_equal(sim.material().ravel(), np.asarray(mat_h).ravel())
+    dev = sim.gain_list()
+    assert dev.size == int(np.count_nonzero(w.gain))
+    assert np.array_equal(dev, np.asarray(host, dtype=np.uint32))
     sim.close()
