@@ -190,6 +190,15 @@ int mb_step(mb_ctx* ctx, int n);
  * the context's work so far.  Errors: MB_ERR_ARG (null context). */
 int mb_join_probes(mb_ctx* ctx);
 
+/* Zero the running DFT sums of every probe of the context (point, face and
+ * plane probes), on the context's stream after the probe launches still
+ * running: the spectra read afterwards cover the steps taken after this call
+ * only (a time window of the run; the phases keep the absolute time t_n, so
+ * |S|^2 is that of the window's samples).  The face energies (mb_energy's
+ * flux) and the fields are untouched.  Errors: MB_ERR_ARG (null context),
+ * MB_ERR_CUDA. */
+int mb_reset_probes(mb_ctx* ctx);
+
 /* Advance n >= 0 steps like mb_step, but with direct launches bracketed by
  * CUDA events on the context's stream; synchronizes, then adds the summed
  * device time (ms) of each pass over the n steps to ms_out[0..3]: H pass,

@@ -81,6 +81,7 @@ _SIGS = [
     ("mb_flux", C.c_int, [_P, _P]),
     ("mb_synchronize", C.c_int, [_P]),
     ("mb_join_probes", C.c_int, [_P]),
+    ("mb_reset_probes", C.c_int, [_P]),
     ("mb_get_step", C.c_int, [_P, C.POINTER(C.c_int64)]),
     ("mb_probe_spectrum", C.c_int, [_P, C.c_int, _P, _P]),
     ("mb_face_spectrum", C.c_int, [_P, C.c_int, _P, _P]),
@@ -345,6 +346,12 @@ def mb_join_probes(h):
     """Order the context's stream after probe launches mb_step left running
     on its second stream (no host wait)."""
     _check(load_library().mb_join_probes(h), h)
+
+
+def mb_reset_probes(h):
+    """Zero every probe's running DFT sums: later spectra cover the steps
+    taken after this call (a time window)."""
+    _check(load_library().mb_reset_probes(h), h)
 
 
 def mb_get_step(h) -> int:
@@ -695,6 +702,11 @@ class MBSimulation:
         """Make the simulation's stream wait for the probe DFTs that step()
         left running beside later steps (enqueued only)."""
         mb_join_probes(self._h)
+
+    def reset_probes(self):
+        """Start the probes' spectra afresh: they cover the steps taken from
+        here on (mb_reset_probes)."""
+        mb_reset_probes(self._h)
 
     @property
     def n(self):

@@ -1277,6 +1277,21 @@ int mb_flux_async(mb_ctx* c, double* host_out6) {
 
 int mb_join_probes(mb_ctx* c) { return check_ctx(c); }
 
+int mb_reset_probes(mb_ctx* c) {
+    if (int rc = check_ctx(c)) return rc;   // after the probe launches still running
+    if (!c->probes.empty())
+        MB_CUDA(c, cudaMemsetAsync(c->d_probe_acc, 0, sizeof(double2) * 3 * c->probes.size() * c->probe_nfreq,
+                                   c->stream));
+    if (c->face.on && c->face_points) {
+        const size_t accn = 4 * (size_t)c->face_points * c->face.nfreq;
+        MB_CUDA(c, cudaMemsetAsync(c->d_face_acc, 0, sizeof(double2) * accn, c->stream));
+        MB_CUDA(c, cudaMemsetAsync(c->d_face_acc32, 0, sizeof(float2) * accn, c->stream));
+    }
+    for (const mb::DevPlaneProbe& q : c->planes)
+        MB_CUDA(c, cudaMemsetAsync(q.acc, 0, sizeof(double2) * 3 * (size_t)q.nfreq * c->nx * c->ny, c->stream));
+    return MB_OK;
+}
+
 int mb_synchronize(mb_ctx* c) {
     if (int rc = check_ctx(c)) return rc;
     MB_CUDA(c, cudaStreamSynchronize(c->stream));

@@ -19,6 +19,10 @@ reductions of a few hundred numbers per realization:
                N_a, stimulated emission above threshold faster)
 
     python -m paper_0809_1547_gb300.sweep --steps 8000 --out sweep.json
+
+`--window-from S` restarts the probes at step S, so the spectra are those of
+the emission after S (the spontaneous background of the first steps left
+out).
 """
 from __future__ import annotations
 
@@ -84,11 +88,14 @@ def emission_threshold(rows, slope: float = 2.0):
     return float(L[hit[0]]) if hit.size else None
 
 
-def run_pump_sweep(workloads, steps: int, stream=None, autotune: bool = True, record=()):
+def run_pump_sweep(workloads, steps: int, stream=None, autotune: bool = True, record=(),
+                   window_from: int = 0):
     """Advance every workload of the ensemble `steps` steps in one MBBatch
     and return (levels, spectra, lam, seconds).  With `record` (ascending
     step counts below `steps`), also the spectra at each of those counts:
-    then returns (levels, spectra, lam, seconds, [(step, spectra), ...])."""
+    then returns (levels, spectra, lam, seconds, [(step, spectra), ...]).
+    With window_from > 0 the probes restart at that step (mb_reset_probes),
+    so the spectra read later cover the window [window_from, step) only."""
     from .binding import MBBatch, mb_default_params
     b = MBBatch([w.grid for w in workloads], workloads[0].dx, workloads[0].dt,
                 mb_default_params(npml=workloads[0].npml), stream=stream)
@@ -109,11 +116,18 @@ def run_pump_sweep(workloads, steps: int, stream=None, autotune: bool = True, re
             b.autotune()
         t0 = time.perf_counter()
         done = 0
-        for r in [int(v) for v in record if 0 < int(v) < steps]:
+        rec = {int(v) for v in record if 0 < int(v) < steps}
+        marks = sorted(rec |
+                       ({int(window_from)} if 0 < window_from < steps else set()))
+        for r in marks:
             b.step(r - done)
             b.synchronize()
             done = r
-            snaps.append((r, read()[0]))
+            if r in rec:
+                snaps.append((r, read()[0]))
+            if r == window_from:
+                for inst in b.instances:
+                    inst.reset_probes()
         b.step(steps - done)
         b.synchronize()
         secs = time.perf_counter() - t0
@@ -141,6 +155,8 @@ def main():
     ap.add_argument("--record", default="",
                     help="comma-separated step counts at which the statistics are also taken "
                          "(spectra accumulated from step 0)")
+    ap.add_argument("--window-from", type=int, default=0,
+                    help="restart the probes at this step: the spectra cover the later steps only")
     ap.add_argument("--out", default="")
     args = ap.parse_args()
     ws = inputs.workload_batch(n_pump=args.n_pump, n_seed=args.n_seed, N_a_lo=args.na_min,
@@ -152,7 +168,7 @@ def main():
         keep = sorted({w.N_a for w in ws})[-args.top_levels:]
         ws = [w for w in ws if w.N_a in keep]
     record = [int(v) for v in args.record.split(",") if v.strip()]
-    res = run_pump_sweep(ws, args.steps, record=record)
+    res = run_pump_sweep(ws, args.steps, record=record, window_from=args.window_from)
     levels, spectra, lam, secs = res[:4]
     snaps = res[4] if record else []
     stats = spectral_stats(spectra, lam)
@@ -160,6 +176,7 @@ def main():
     cells = sum(int(np.prod(w.grid)) for w in ws)
     dt = ws[0].dt
     out = {"instances": len(ws), "steps": args.steps, "t_ps": args.steps * dt * 1e12,
+           "spectra_from_step": args.window_from,
            "pump_W_p": ws[0].pump, "seconds": secs,
            "mcell_updates_per_s": cells * args.steps / secs / 1e6, "threshold_N_a": thr,
            "emission_threshold_N_a": emission_threshold(rows),

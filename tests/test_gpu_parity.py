@@ -99,6 +99,55 @@ def test_ragged_grid_parity(grid, npml, steps):
     g.close()
 
 
+def test_reset_probes_gives_the_window_spectra():
+    """mb_reset_probes after 50 of 110 steps (a source pulse centred near
+    step 39): the point-, face- and plane-probe spectra equal the oracle's
+    with its DFT sums zeroed at the same step (the window's samples only);
+    the face energies are kept."""
+    from paper_0809_1547_gb300 import inputs
+    grid, npml = (24, 20, 28), 4
+    eps, gain = inputs.random_small(grid, seed=7, npml=npml, fill=0.35, d_cells=5)
+    o, g = make_pair(grid, eps, gain, 5e24, 1e13, 0xBEEF, params_kw(npml=npml))
+    src = (12, 10, 14)
+    for sim in (o, g):
+        sim.add_point_probe((8, 10, 14), 24, 450e-9, 750e-9)
+        sim.add_face_probes(2, 3, 16, 480e-9, 700e-9)
+        sim.add_plane_probe(14, 2, 4, 500e-9, 650e-9)
+    o.add_source(src, 1, 532e-9, 1.5e-15, 0.5e-15, 1e9)
+    g.set_source(src, 1, 532e-9, 1.5e-15, 0.5e-15, 1e9)
+    o.step(50)
+    g.step(50)
+    S_first, _ = g.probe_spectrum(0)
+    g.reset_probes()
+    for pr in o.point_probes:
+        pr["acc"][:] = 0
+    for pp in o.plane_probes:
+        pp["acc"][:] = 0
+    for acc in o.face_probes["faces"].values():
+        acc[:] = 0
+    flux_before = o.flux.copy()
+    o.step(60)
+    g.step(60)
+    assert_fields_match(o, g)
+    _spectrum_check(o, g, 0)
+    _energy_check(o, g)
+    assert np.abs(o.flux - flux_before).max() > 0 and np.abs(flux_before).max() > 0
+    for face in range(6):
+        S_o, _ = o.face_spectrum(face)
+        S_g, _ = g.face_spectrum(face)
+        scale = max(np.abs(S_o).max(), 1e-300)
+        assert np.abs(S_g - S_o).max() <= 4 * REL_L2_TOL * scale, face
+    for b in range(4):
+        M_o = o.plane_mode_map(0, b)
+        M_g = g.plane_mode_map(0, b)
+        assert M_o.max() > 0
+        assert rel_l2(M_g, M_o) <= 4 * REL_L2_TOL, b
+    # the sums did restart: the window's spectrum is not the first 50 steps'
+    S_win, _ = g.probe_spectrum(0)
+    assert S_first.max() > 0 and rel_l2(S_win, S_first) > 1e-3
+    g.close()
+
+
 @pytest.mark.parametrize("grid,npml", [((1, 1, 40), 0), ((1, 1, 40), 8), ((8, 8, 8), 8), ((2, 3, 1), 1)])
 def test_degenerate_grids_parity(grid, npml):
     """One-cell columns (PEC zeroes every E), overlapping CPML slabs, a 1-cell-thick slab."""

@@ -48,6 +48,32 @@ def test_small_sweep_matches_oracle():
         assert st["std_w"][q] == pytest.approx(O.std_width(S_o, w), rel=1e-4, abs=0)
 
 
+def test_windowed_sweep_matches_oracle():
+    """Probes restarted at step 180 of 300 in every member of the batch
+    (mb_reset_probes on the instances): the spectra equal the oracle's DFT of
+    steps 181-300 only, and records taken before the restart keep the
+    spectra from step 0."""
+    from paper_0809_1547_gb300.sweep import run_pump_sweep, N_FREQ, LAM_MIN, LAM_MAX
+    ws = _ensemble()[:2]
+    levels, spectra, lam, _, snaps = run_pump_sweep(ws, 300, autotune=False, record=(120,),
+                                                    window_from=180)
+    assert [st for st, _ in snaps] == [120]
+    for q, wl in enumerate(ws):
+        o = MBOracle(wl.grid, DX, DT, Params(npml=wl.npml))
+        o.set_material(wl.eps, wl.gain, wl.N_a, wl.pump)
+        o.set_seed(wl.seed)
+        pid = o.add_point_probe(tuple(v // 2 for v in wl.grid), N_FREQ, LAM_MIN, LAM_MAX)
+        o.step(120)
+        S_120, _ = o.probe_spectrum(pid)
+        assert rel_l2(snaps[0][1][q], S_120) <= 2e-5
+        o.step(60)
+        o.point_probes[pid]["acc"][:] = 0
+        o.step(120)
+        S_o, _ = o.probe_spectrum(pid)
+        assert S_o.max() > 0
+        assert rel_l2(spectra[q], S_o) <= 2e-5
+
+
 def test_full_ensemble_sweep_runs():
     """The 80-realization ensemble (16 N_a levels x 5 seeds, cubes of side
     97-148) for 200 steps: every spectrum finite and non-zero, one row per
