@@ -40,16 +40,30 @@ __device__ bool grid_barrier(unsigned* bar, unsigned nblocks, int limit = kBarri
 
 // Arguments of the item's instance, copied into shared memory: global
 // stores cannot alias them there, so the field pointers need not stay in
-// registers or be reloaded after every store.
+// registers or be reloaded after every store.  One copy per item kind
+// (TAG); an item of the instance whose arguments the copy already holds
+// (a block's consecutive items are often tiles of one instance) skips the
+// copy.  The arguments do not change during a launch.
+__shared__ int staged_inst[3];   // instance held by each copy, -1: none
+
+__device__ __forceinline__ void staged_reset() {
+    if (linear_tid() < 3) staged_inst[linear_tid()] = -1;
+    __syncthreads();
+}
+
 template <int TAG>
-__device__ __forceinline__ const StepArgs& stage_args(const StepArgs* src) {
+__device__ __forceinline__ const StepArgs& stage_args(const StepArgs* inst, int p) {
     static_assert(sizeof(StepArgs) % 8 == 0, "StepArgs is copied in 8-byte words");
     __shared__ StepArgs sa;
-    const unsigned long long* s8 = reinterpret_cast<const unsigned long long*>(src);
-    unsigned long long* d8 = reinterpret_cast<unsigned long long*>(&sa);
-    const int T = blockDim.x * blockDim.y * blockDim.z;
-    for (int t = linear_tid(); t < (int)(sizeof(StepArgs) / 8); t += T) d8[t] = s8[t];
-    __syncthreads();
+    if (staged_inst[TAG] != p) {   // uniform: read after the caller's barrier
+        const unsigned long long* s8 = reinterpret_cast<const unsigned long long*>(inst + p);
+        unsigned long long* d8 = reinterpret_cast<unsigned long long*>(&sa);
+        const int T = blockDim.x * blockDim.y * blockDim.z;
+        for (int t = linear_tid(); t < (int)(sizeof(StepArgs) / 8); t += T) d8[t] = s8[t];
+        __syncthreads();   // every thread has read staged_inst before it changes
+        if (linear_tid() == 0) staged_inst[TAG] = p;
+        __syncthreads();
+    }
     return sa;
 }
 
@@ -63,17 +77,17 @@ __device__ __noinline__ void batch_probe_item(const BatchArgs& B, int p, long lo
 }
 
 __device__ __noinline__ void batch_h_item(const BatchArgs& B, int4 it) {
-    const StepArgs& a = stage_args<0>(B.inst + it.x);
+    const StepArgs& a = stage_args<0>(B.inst, it.x);
     const int gx = B.tiles[2 * it.x], gy = B.tiles[2 * it.x + 1];
     h_tile_zmarch(a, it.z % gx, (it.z / gx) % gy, it.z / (gx * gy), B.kz);
 }
 
 __device__ __noinline__ void batch_gain_item(const BatchArgs& B, int4 it, long long n) {
-    gain_block<kBatchGainPerThread>(stage_args<1>(B.inst + it.x), (unsigned)it.z, B.gq, n);
+    gain_block<kBatchGainPerThread>(stage_args<1>(B.inst, it.x), (unsigned)it.z, B.gq, n);
 }
 
 __device__ __noinline__ void batch_e_item(const BatchArgs& B, int4 it, long long n, unsigned slot) {
-    const StepArgs& a = stage_args<2>(B.inst + it.x);
+    const StepArgs& a = stage_args<2>(B.inst, it.x);
     const int gx = B.tiles[2 * it.x], gy = B.tiles[2 * it.x + 1];
     e_tile_zmarch(a, it.z % gx, (it.z / gx) % gy, it.z / (gx * gy), B.kz, n, slot);
 }
@@ -102,6 +116,7 @@ __device__ __forceinline__ int next_item(unsigned long long* tick, unsigned long
 // flag and the block leaves; the other blocks then time out at their next
 // barrier, so the launch always ends.
 __global__ void __launch_bounds__(256, 4) k_batch(const __grid_constant__ BatchArgs B) {
+    staged_reset();
     const unsigned nb = gridDim.x;
     const long long n0 = B.ctr[0];
     unsigned long long base = 0;
