@@ -116,7 +116,9 @@ int rebuild(mb_batch* b) {
         tiles.push_back(gx);
         tiles.push_back(gy);
         const long long nH = (long long)gx * gy * gz;
-        const long long nG = (c->args.gain.on && c->glist_count) ? (c->glist_count + gq - 1) / gq : 0;
+        // a gain item takes kBatchGainSub consecutive blocks of gq list entries
+        const long long gi = (long long)gq * mb::kBatchGainSub;
+        const long long nG = (c->args.gain.on && c->glist_count) ? (c->glist_count + gi - 1) / gi : 0;
         // H tiles and gain chunks interleaved by progress through the
         // instance (a gain chunk re-reads E^n where the H tiles next to it in
         // the list read it, so the line is still in L2); E tiles in tile order

@@ -82,8 +82,15 @@ __device__ __noinline__ void batch_h_item(const BatchArgs& B, int4 it) {
     h_tile_zmarch(a, it.z % gx, (it.z / gx) % gy, it.z / (gx * gy), B.kz);
 }
 
+// kBatchGainSub consecutive blocks of B.gq gain-list entries (the block's
+// threads one entry each, block after block): fewer, larger items than one
+// block of entries each, so the ticket and the barriers around an item are
+// paid less often.
 __device__ __noinline__ void batch_gain_item(const BatchArgs& B, int4 it, long long n) {
-    gain_block<kBatchGainPerThread>(stage_args<1>(B.inst, it.x), (unsigned)it.z, B.gq, n);
+    const StepArgs& a = stage_args<1>(B.inst, it.x);
+#pragma unroll 1
+    for (int s = 0; s < kBatchGainSub; ++s)
+        gain_block<kBatchGainPerThread>(a, (unsigned)it.z * kBatchGainSub + s, B.gq, n);
 }
 
 __device__ __noinline__ void batch_e_item(const BatchArgs& B, int4 it, long long n, unsigned slot) {

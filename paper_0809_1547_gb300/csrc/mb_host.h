@@ -208,6 +208,7 @@ struct BatchArgs {
 constexpr int kBarrierSpinLimit = 1 << 22;   // ~0.3-1 s with 64 ns sleeps
 constexpr int kGainPerThread = 2;             // gain cells per thread in a gain block
 constexpr int kBatchGainPerThread = 1;        // the same inside the persistent kernel
+constexpr int kBatchGainSub = 8;              // gain blocks per work item of the persistent kernel
 cudaError_t launch_batch(const BatchArgs& b, dim3 block, int blocks, cudaStream_t s);
 // Bounded-wait self-tests: a grid barrier that one phantom block never
 // reaches, an mbarrier that is never completed; gave_up counts the blocks
