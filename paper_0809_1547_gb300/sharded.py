@@ -190,6 +190,11 @@ class SlabGrid:
         q = self.owner(ijk[2])
         self.slabs[q].set_source(self.slabs[q].to_local(ijk), comp, lam, t0, tau, amp)
 
+    def reset_probes(self):
+        """Restart every slab's probe sums (spectra of the steps from here on)."""
+        for s in self.slabs:
+            s.reset_probes()
+
     def exchange(self):
         """Every interface: the lower slab's top own plane into the upper
         slab's ghost below, the upper slab's bottom own plane into the lower
@@ -326,6 +331,10 @@ class DistributedSlab:
 
     def add_face_probes(self, stride, every, n_freq, lam_min, lam_max):
         self.sim.add_face_probes(stride, every, n_freq, lam_min, lam_max)
+
+    def reset_probes(self):
+        """Restart this rank's probe sums (every rank calls it at the same step)."""
+        self.sim.reset_probes()
 
     def face_spectrum(self, face):
         """(S, lam) of one face of the whole grid (FP64 sum over the ranks)."""
