@@ -125,13 +125,19 @@ __global__ void __launch_bounds__(BX * BY) k_step_fused(StepArgs a, DevPing d,
     const bool gain_on = a.gain.on;
     const DevFields& f = a.f;
 
+    // The E box's lines are read again by the neighbouring tiles (its halo
+    // rows and columns) and by the block of the next z chunk (its top
+    // plane): they are kept in L2 ahead of the rest (evict-last), and the
+    // block's writes, which nothing in the launch reads again, go out
+    // evict-first (streaming stores).
+    const uint64_t keep_l2 = l2_policy_evict_last();
     auto issue = [&](int s, int p) {
         unsigned char* q = smem + s * Lay::kStage;
         const int k = k0 + p;
         mbar_arrive_expect_tx(&bar[s], p < planes ? Lay::kTx : Lay::kTxE);
-        tma_load_3d(q + 0 * Lay::kEBytes, &maps.ex, x0 - 4, y0 - 1, k, &bar[s]);
-        tma_load_3d(q + 1 * Lay::kEBytes, &maps.ey, x0 - 4, y0 - 1, k, &bar[s]);
-        tma_load_3d(q + 2 * Lay::kEBytes, &maps.ez, x0 - 4, y0 - 1, k, &bar[s]);
+        tma_load_3d_hint(q + 0 * Lay::kEBytes, &maps.ex, x0 - 4, y0 - 1, k, &bar[s], keep_l2);
+        tma_load_3d_hint(q + 1 * Lay::kEBytes, &maps.ey, x0 - 4, y0 - 1, k, &bar[s], keep_l2);
+        tma_load_3d_hint(q + 2 * Lay::kEBytes, &maps.ez, x0 - 4, y0 - 1, k, &bar[s], keep_l2);
         if (p < planes) {
             unsigned char* h = q + 3 * Lay::kEBytes;
             tma_load_3d(h + 0 * Lay::kHBytes, &maps.hx, x0 - 4, y0 - 1, k, &bar[s]);
@@ -249,9 +255,9 @@ __global__ void __launch_bounds__(BX * BY) k_step_fused(StepArgs a, DevPing d,
             hz = H0[2 * HW + own_h];
             if (pml) h_compute_to<true, true>(a, i, j, k, e, hx, hy, hz, d.psi);
             else h_compute_to<false, true>(a, i, j, k, e, hx, hy, hz, d.psi);
-            d.hx[c] = hx;
-            d.hy[c] = hy;
-            d.hz[c] = hz;
+            __stcs(d.hx + c, hx);
+            __stcs(d.hy + c, hy);
+            __stcs(d.hz + c, hz);
             // the CPML memories the E update reads after the barrier
             if (pml) prefetch_psi(a, i, j, k, 0);
         }
@@ -296,12 +302,12 @@ __global__ void __launch_bounds__(BX * BY) k_step_fused(StepArgs a, DevPing d,
             n3 = *gslot(b, 8);
             lorentz_step(a.gain, c, n, E0[own_e], E0[EW + own_e], E0[2 * EW + own_e], n1, n2, jx,
                          jy, jz, px, py, pz);
-            f.px[c] = px;
-            f.py[c] = py;
-            f.pz[c] = pz;
-            f.jx[c] = jx;
-            f.jy[c] = jy;
-            f.jz[c] = jz;
+            __stcs(f.px + c, px);
+            __stcs(f.py + c, py);
+            __stcs(f.pz + c, pz);
+            __stcs(f.jx + c, jx);
+            __stcs(f.jy + c, jy);
+            __stcs(f.jz + c, jz);
         }
         __syncthreads();   // the H tile is complete
 
@@ -330,13 +336,13 @@ __global__ void __launch_bounds__(BX * BY) k_step_fused(StepArgs a, DevPing d,
             else
                 e_compute_to<false, false>(a, i, j, k, c, h, m, ex0, ey0, ez0, pg, jx, jy, jz, n1,
                                            n2, n3, n, fl, ex1, ey1, ez1, d.psi);
-            d.ex[c] = ex1;
-            d.ey[c] = ey1;
-            d.ez[c] = ez1;
+            __stcs(d.ex + c, ex1);
+            __stcs(d.ey + c, ey1);
+            __stcs(d.ez + c, ez1);
             if (pg) {
-                f.n1[c] = n1;
-                f.n2[c] = n2;
-                f.n3[c] = n3;
+                __stcs(f.n1 + c, n1);
+                __stcs(f.n2 + c, n2);
+                __stcs(f.n3 + c, n3);
             }
             hx_km1 = hx;
             hy_km1 = hy;
