@@ -242,14 +242,18 @@ def host_cores() -> int:
         return os.cpu_count() or 1
 
 
-def save_part(w, directory: str, tag: str, z0: int = 0, thickness: int | None = None) -> str:
+def save_part(w, directory: str, tag: str, z0: int = 0, thickness: int | None = None,
+              rows: int | None = None) -> str:
     """Planes z0 .. z0+thickness-1 of workload w (all of it by default) with
-    its parameters, as an .npz an oracle child reads."""
+    its parameters, as an .npz an oracle child reads; with `rows`, only the
+    middle `rows` rows (y) of those planes."""
     import numpy as np
     t = w.grid[2] - z0 if thickness is None else thickness
+    r = w.grid[1] if rows is None else rows
+    y0 = (w.grid[1] - r) // 2
     path = os.path.join(directory, f"{tag}.npz")
-    np.savez(path, eps=np.ascontiguousarray(w.eps[z0:z0 + t]),
-             gain=np.ascontiguousarray(w.gain[z0:z0 + t]),
+    np.savez(path, eps=np.ascontiguousarray(w.eps[z0:z0 + t, y0:y0 + r]),
+             gain=np.ascontiguousarray(w.gain[z0:z0 + t, y0:y0 + r]),
              real=np.array([w.dx, w.dt, w.N_a, w.pump], dtype=np.float64),
              npml=np.array([w.npml], dtype=np.int64), seed=np.array([w.seed], dtype=np.uint64))
     return path
@@ -325,11 +329,12 @@ def slab_offsets(n: int, thickness: int, parts: int):
 
 
 def cpu_slab_rate(w, thickness: int, steps: int, warm: int = 1, cores: int | None = None,
-                  kind: str = "forward"):
-    """The oracle on `cores` slabs (thickness planes each) of workload w, one child per core."""
+                  kind: str = "forward", rows: int | None = None):
+    """The oracle on `cores` slabs (thickness planes each, all rows or the
+    middle `rows`) of workload w, one child per core."""
     cores = cores or host_cores()
     with tempfile.TemporaryDirectory() as d:
-        jobs = [(save_part(w, d, f"slab{q}", z0, thickness), steps, warm, kind)
+        jobs = [(save_part(w, d, f"slab{q}", z0, thickness, rows), steps, warm, kind)
                 for q, z0 in enumerate(slab_offsets(w.grid[2], thickness, cores))]
         rate, secs, res = run_oracle_children(jobs)
     return rate, secs, res[0][0], cores
@@ -964,7 +969,9 @@ def bench_reference(args):
     """The reference arm: the FP64 oracle (the paper has no implementation to
     run) on the benchmark's workload, on every host core; each step is one
     step of a slab of the workload per core, sized so the whole run takes
-    about --ref-budget seconds (100 by default)."""
+    about --ref-budget seconds (100 by default): 17 to 48 whole planes, and
+    for runs too long for 17 whole planes, 17 planes of fewer rows (at least
+    64, so the 8-cell CPML takes at most a quarter of the sample's rows)."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
@@ -980,18 +987,22 @@ def bench_reference(args):
         budget_s = float(args.ref_budget)
         cells_per_child = r1 * 1e6 * budget_s / max(1, args.steps + args.warmup)
         thickness = int(max(17, min(48, round(cells_per_child / (w.grid[0] * w.grid[1])))))
-        rate, secs, ncell, cores = cpu_slab_rate(w, thickness, args.steps, args.warmup, cores)
+        rows = w.grid[1]
+        if cells_per_child < thickness * w.grid[0] * w.grid[1]:
+            rows = int(max(min(64, w.grid[1]), min(w.grid[1], round(cells_per_child / (thickness * w.grid[0])))))
+        rate, secs, ncell, cores = cpu_slab_rate(w, thickness, args.steps, args.warmup, cores,
+                                                 rows=rows)
     except Exception as e:
         print(json.dumps({"impl": "reference", "unavailable": "oracle run failed: " + str(e)[-300:]}))
         return
-    sample = (f"each step: {cores} slabs of {w.grid[0]}x{w.grid[1]}x{thickness} planes ({ncell} cells "
+    sample = (f"each step: {cores} slabs of {w.grid[0]}x{rows}x{thickness} planes ({ncell} cells "
               f"each, spread over the depth, each with its own 8-cell CPML) of the {w.name} workload, "
               f"FP64 numpy oracle, {cores} single-thread processes at once")
     out = {"impl": "reference", "metric": METRIC, "value": round(rate, 4), "unit": UNIT,
            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": round(secs / args.steps * 1e3, 3), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": f"{w.name} (sampled slabs)", "grid": [w.grid[0], w.grid[1], thickness],
+           "config": {"workload": f"{w.name} (sampled slabs)", "grid": [w.grid[0], rows, thickness],
                       "slabs_per_step": cores},
            "cpu_baseline": {"value": round(rate, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
                             "sample": sample},
